@@ -1,0 +1,385 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test checks the oracle against something other than itself: brute force on tiny inputs,
+closed forms, invariants the paper derives, special cases that reduce to a library routine.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_img(rng, H, W, C=3):
+    return rng.integers(0, 256, size=(H, W, C), dtype=np.uint8)
+
+
+def window_cols(L, s, S, y, x):
+    """Valid window pixels (k, colour) of HR pixel (y, x): the Omega of Eq. 1."""
+    h, w, _ = L.shape
+    r = (S - 1) // 2
+    out = []
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            v, u = y // s + dy, x // s + dx
+            if 0 <= v < h and 0 <= u < w:
+                out.append(((dy + r) * S + (dx + r), L[v, u]))
+    return out
+
+
+# ------------------------------------------------------------------ parameters the paper prints
+
+def test_paper_parameters_golden():
+    g = json.load(open(os.path.join(GOLDEN, "paper_parameters.json")))
+    assert g["tau"]["value"] == pytest.approx(30 / 255)
+    import inspect
+    sig = inspect.signature(O.joint)
+    assert sig.parameters["tau"].default == pytest.approx(g["tau"]["value"])
+    assert sig.parameters["N"].default == g["max_iterations_N"]["value"]
+    assert sig.parameters["eps"].default == g["eps"]["value"]
+    # the pair counts the paper states for a 3x3 window: all unordered pairs vs. a fixed a
+    K = g["window_size_S"]["value"] ** 2
+    assert K * (K - 1) // 2 == g["pairs_exhaustive_3x3"]["value"]
+    assert K == g["pairs_fast_3x3"]["value"]   # b ranges over the whole window, b = a included
+    L = np.zeros((5, 5, 3))
+    assert len(window_cols(L, 2, 3, 4, 4)) == K
+
+
+# ------------------------------------------------------------------------------- downsampling
+
+@pytest.mark.parametrize("H,W,s", [(8, 8, 2), (9, 13, 4), (17, 5, 3), (16, 16, 16), (7, 7, 8)])
+def test_grid_downsample_sample_positions(H, W, s):
+    # an image whose colour encodes its own coordinates; grid sampling must pick, per block,
+    # the pixel floor(e/2) into the block (e = block extent, partial at the far edge)
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    I = np.stack([yy / 1000.0, xx / 1000.0, np.zeros_like(yy, dtype=float)], axis=-1)
+    L = O.downsample_grid(I, s)
+    h, w = O.lr_dims(H, W, s)
+    assert L.shape == (h, w, 3)
+    for v in range(h):
+        ey = min(s, H - v * s)
+        for u in range(w):
+            ex = min(s, W - u * s)
+            assert round(L[v, u, 0] * 1000) == v * s + ey // 2
+            assert round(L[v, u, 1] * 1000) == u * s + ex // 2
+
+
+@pytest.mark.parametrize("H,W,s", [(8, 8, 2), (9, 13, 4), (10, 3, 3)])
+def test_box_downsample_closed_form(H, W, s):
+    xx = np.broadcast_to(np.arange(W, dtype=float)[None, :, None], (H, W, 3))
+    L = O.downsample_box(xx, s)
+    h, w = O.lr_dims(H, W, s)
+    for u in range(w):
+        lo, hi = u * s, min(W, u * s + s)
+        assert np.allclose(L[:, u, :], (lo + hi - 1) / 2.0)
+    c = np.full((H, W, 3), 0.3)
+    assert np.allclose(O.downsample_box(c, s), 0.3)
+
+
+# ------------------------------------------------------------ GLU* (Sec. 3.1, Eq. 4) pinned
+
+def brute_pair_min(Ip, La, Lb):
+    """min over real omega of ||omega La + (1 - omega) Lb - Ip|| by ternary search on a
+    convex function over a wide bracket (no closed form used)."""
+    lo, hi = -1e4, 1e4
+    f = lambda o: np.linalg.norm(o * La + (1 - o) * Lb - Ip)
+    for _ in range(400):
+        m1, m2 = lo + (hi - lo) / 3, hi - (hi - lo) / 3
+        if f(m1) <= f(m2):
+            hi = m2
+        else:
+            lo = m1
+    return f(0.5 * (lo + hi))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_exact_matches_brute_force_tiny(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H = W = 8
+    s, S = 2, 3
+    I = O.to_unit(rand_img(rng, H, W))
+    L = O.to_unit(rand_img(rng, 4, 4))
+    ex = O.glu_exact(I, L, s, S, eps=0.0)
+    for y in range(H):
+        for x in range(W):
+            cols = window_cols(L, s, S, y, x)
+            best = min(brute_pair_min(I[y, x], cols[i][1], cols[j][1])
+                       for i in range(len(cols)) for j in range(i + 1, len(cols)))
+            assert ex["err"][y, x] == pytest.approx(best, abs=1e-9)
+
+
+def test_exact_eps0_residual_orthogonal_to_colour_line(rng):
+    # Eq. 4 with eps = 0 is the projection of I_p on the line through L_a and L_b
+    H = W = 12
+    s, S = 3, 3
+    I = O.to_unit(rand_img(rng, H, W))
+    L = O.to_unit(rand_img(rng, 4, 4))
+    ex = O.glu_exact(I, L, s, S, eps=0.0)
+    h, w = 4, 4
+    for y in range(H):
+        for x in range(W):
+            ka, kb, om = ex["ka"][y, x], ex["kb"][y, x], ex["omega"][y, x]
+            va, ua = y // s + ka // S - 1, x // s + ka % S - 1
+            vb, ub = y // s + kb // S - 1, x // s + kb % S - 1
+            La, Lb = L[va, ua], L[vb, ub]
+            res = om * La + (1 - om) * Lb - I[y, x]
+            assert abs(np.dot(res, La - Lb)) < 1e-12
+            assert ex["err"][y, x] == pytest.approx(np.linalg.norm(res), abs=1e-12)
+
+
+# --------------------------------------------------------- Algorithm 1 (FAST) pinned
+
+@pytest.mark.parametrize("seed,s,S", [(1, 2, 3), (2, 3, 5), (3, 4, 3), (4, 2, 1)])
+def test_fast_between_exact_and_gnu(seed, s, S):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H, W = 14, 11
+    I = rand_img(rng, H, W)
+    h, w = O.lr_dims(H, W, s)
+    L = rand_img(rng, h, w)
+    fa = O.glu_fast(I, L, s, S)
+    gn = O.glu_gnu(I, L, s, S)
+    # b = a is a candidate, so FAST never does worse than nearest-colour (GNU)
+    assert np.all(fa["err"] <= gn["err"] + 1e-15)
+    # a is the nearest colour in the window: brute force over the window
+    Iu, Lu = O.to_unit(I), O.to_unit(L)
+    for y in range(H):
+        for x in range(W):
+            cols = window_cols(Lu, s, S, y, x)
+            d = [np.linalg.norm(Iu[y, x] - c) for _, c in cols]
+            assert gn["err"][y, x] == pytest.approx(min(d), abs=1e-15)
+            assert gn["ka"][y, x] == cols[int(np.argmin(d))][0]
+            assert fa["ka"][y, x] == gn["ka"][y, x]
+    # the Eq. 5 weight always lies in [0, 1]
+    assert np.all(fa["omega"] >= 0) and np.all(fa["omega"] <= 1)
+    if S > 1:
+        ex = O.glu_exact(I, L, s, S, eps=0.0)
+        # any fixed-weight pair is no better than the best least-squares pair
+        assert np.all(fa["err"] >= ex["err"] - 1e-12)
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-3])
+def test_fast_on_colour_segment_closed_form(rng, eps):
+    # LR made of two colours c1, c2; HR pixels on the segment between them: I_p = t c1 + (1-t) c2.
+    # With a = the nearer endpoint, Eq. 5 gives omega = d_b / (d_a + d_b + eps) and the Eq. 3
+    # error is |omega - t| * |c1 - c2| (eps = 0: exact, omega = t, error 0).
+    c1 = np.array([0.9, 0.2, 0.1])
+    c2 = np.array([0.1, 0.6, 0.8])
+    h = w = 3
+    L = np.zeros((h, w, 3))
+    for v in range(h):
+        for u in range(w):
+            L[v, u] = c1 if (v + u) % 2 == 0 else c2
+    s, S = 4, 3
+    H = W = 12
+    t = rng.uniform(0.0, 1.0, size=(H, W))
+    I = t[..., None] * c1 + (1 - t[..., None]) * c2
+    fa = O.glu_fast(I, L, s, S, eps=eps)
+    D = np.linalg.norm(c1 - c2)
+    for y in range(H):
+        for x in range(W):
+            tt = t[y, x]
+            # the nearer endpoint is a: c1 if t > 1/2
+            ta = tt if tt >= 0.5 else 1 - tt
+            da, db = (1 - ta) * D, ta * D
+            om = db / (da + db + eps)
+            expect = min(da, abs(om - ta) * D)   # b = a gives d_a
+            assert fa["err"][y, x] == pytest.approx(expect, abs=1e-12)
+            if eps == 0.0 and min(tt, 1 - tt) > 1e-9:
+                assert fa["omega"][y, x] == pytest.approx(ta, abs=1e-12)
+                assert fa["err"][y, x] < 1e-12
+
+
+@pytest.mark.parametrize("s,S", [(2, 3), (4, 5), (3, 3), (8, 5)])
+def test_exact_representability(rng, s, S):
+    # HR = nearest-neighbour upsampling of an LR image: grid downsampling recovers the LR image,
+    # Algorithm 1 reproduces every pixel exactly, and Eq. 1 with T = I_down returns the HR image.
+    h, w = 5, 7
+    Lu8 = rand_img(rng, h, w)
+    I = np.repeat(np.repeat(Lu8, s, axis=0), s, axis=1)
+    L = O.downsample_grid(I, s)
+    assert np.array_equal(L, O.to_unit(Lu8))
+    fa = O.glu_fast(I, L, s, S)
+    assert np.all(fa["err"] == 0.0)
+    out = O.apply(fa["ka"], fa["kb"], fa["omega"], s, S, L)
+    assert np.allclose(out, O.to_unit(I), atol=1e-15)
+
+
+# ------------------------------------------------------------------- Eq. 1 apply and adjoint
+
+def _random_theta(rng, H, W, s, S):
+    I = rand_img(rng, H, W)
+    h, w = O.lr_dims(H, W, s)
+    L = rand_img(rng, h, w)
+    fa = O.glu_fast(I, L, s, S)
+    return fa, (h, w)
+
+
+def test_apply_affine_invariance(rng):
+    # Eq. 7-8: if T_down = A I_down + c locally (here globally), the same Theta gives A I_hat + c
+    H, W, s, S = 20, 17, 4, 3
+    fa, (h, w) = _random_theta(rng, H, W, s, S)
+    T = rng.uniform(size=(h, w, 3))
+    A = rng.normal(size=(3, 3))
+    c = rng.normal(size=3)
+    lhs = O.apply(fa["ka"], fa["kb"], fa["omega"], s, S, T @ A.T + c)
+    rhs = O.apply(fa["ka"], fa["kb"], fa["omega"], s, S, T) @ A.T + c
+    assert np.allclose(lhs, rhs, atol=1e-12)
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_apply_adjoint_dot_product_and_fd(rng, C):
+    H, W, s, S = 13, 18, 3, 5
+    fa, (h, w) = _random_theta(rng, H, W, s, S)
+    T = rng.uniform(size=(h, w, C))
+    G = rng.normal(size=(H, W, C))
+    Y = O.apply(fa["ka"], fa["kb"], fa["omega"], s, S, T)
+    gT, gw = O.apply_adjoint(fa["ka"], fa["kb"], fa["omega"], s, S, T, G)
+    # <apply(T), G> = <T, apply^T(G)>
+    assert np.sum(Y * G) == pytest.approx(np.sum(T * gT), rel=1e-12)
+    # d/d omega by central differences (the map is affine in omega: exact up to rounding)
+    hstep = 1e-3
+    for (y, x) in [(0, 0), (5, 7), (H - 1, W - 1), (6, 2)]:
+        om = fa["omega"].copy()
+        om[y, x] += hstep
+        fp = np.sum(O.apply(fa["ka"], fa["kb"], om, s, S, T) * G)
+        om[y, x] -= 2 * hstep
+        fm = np.sum(O.apply(fa["ka"], fa["kb"], om, s, S, T) * G)
+        assert (fp - fm) / (2 * hstep) == pytest.approx(gw[y, x], abs=1e-9)
+    # d/dT of a quadratic loss 0.5 ||apply(T) - Z||^2 by central differences
+    Z = rng.uniform(size=(H, W, C))
+    R = Y - Z
+    gTq, _ = O.apply_adjoint(fa["ka"], fa["kb"], fa["omega"], s, S, T, R)
+    for (v, u, c) in [(0, 0, 0), (h - 1, w - 1, C - 1), (2, 3, 0)]:
+        Tp = T.copy(); Tp[v, u, c] += hstep
+        Tm = T.copy(); Tm[v, u, c] -= hstep
+        lp = 0.5 * np.sum((O.apply(fa["ka"], fa["kb"], fa["omega"], s, S, Tp) - Z) ** 2)
+        lm = 0.5 * np.sum((O.apply(fa["ka"], fa["kb"], fa["omega"], s, S, Tm) - Z) ** 2)
+        assert (lp - lm) / (2 * hstep) == pytest.approx(gTq[v, u, c], abs=1e-8)
+
+
+# -------------------------------------------------------- connected components (Algorithm 2)
+
+@pytest.mark.parametrize("conn", [8, 4])
+@pytest.mark.parametrize("density", [0.05, 0.3, 0.6])
+def test_components_match_scipy(rng, conn, density):
+    ndi = pytest.importorskip("scipy.ndimage")
+    mask = rng.uniform(size=(37, 53)) < density
+    labels, M = O.label_components(mask, conn=conn)
+    st = np.ones((3, 3)) if conn == 8 else ndi.generate_binary_structure(2, 1)
+    ref, Mref = ndi.label(mask, structure=st)
+    assert M == Mref
+    # same partition; our numbering follows the smallest raster index of each component
+    first = {}
+    for p, l in enumerate(ref.ravel()):
+        if l and l not in first:
+            first[l] = len(first)
+    remap = np.full(Mref + 1, -1)
+    for l, i in first.items():
+        remap[l] = i
+    assert np.array_equal(labels, remap[ref])
+
+
+# ------------------------------------------------------------------------ Algorithm 2 pinned
+
+def _total_error_fresh(I, L, s, S, eps=1e-3):
+    return O.glu_fast(I, L, s, S, eps=eps)
+
+
+@pytest.mark.parametrize("seed,s,S", [(1, 4, 3), (2, 8, 5), (3, 4, 5)])
+def test_joint_strict_invariants(seed, s, S):
+    from paper_2307_09582_gb300.inputs import plain_256_scene, render_u8
+    sc = plain_256_scene(seed=seed, size=128)
+    I = render_u8(sc)
+    j = O.joint(I, s, S, N=4, strict=True)
+    # total error never increases across iterations
+    Rs = [j["R0"]] + [it["residual"] for it in j["iters"] if it["n_large"] > 0]
+    assert all(b <= a + 1e-9 for a, b in zip(Rs, Rs[1:]))
+    # Theta and E stay the Algorithm 1 result for the current LR image
+    fr = _total_error_fresh(I, j["L"], s, S)
+    assert np.array_equal(fr["ka"], j["ka"]) and np.array_equal(fr["kb"], j["kb"])
+    assert np.array_equal(fr["err"], j["err"])
+    assert float(j["err"].sum()) == pytest.approx(Rs[-1], rel=1e-12)
+    # every LR pixel is exactly one HR pixel of its own block (Eq. 6 constraint)
+    Iu = O.to_unit(I)
+    h, w, _ = j["L"].shape
+    for v in range(h):
+        for u in range(w):
+            blk = Iu[v * s:(v + 1) * s, u * s:(u + 1) * s].reshape(-1, 3)
+            assert np.any(np.all(blk == j["L"][v, u], axis=1))
+    # the joint result is no worse than plain grid downsampling
+    assert j["err"].sum() <= j["R0"] + 1e-9
+
+
+@pytest.mark.parametrize("strict", [True, False])
+def test_joint_recovers_planted_dot(strict):
+    # a flat image with one 2x2 dot away from every grid sample: grid downsampling loses the dot
+    # (its pixels have error |d - c| > tau); one iteration puts the dot's colour into the LR image
+    # and every pixel becomes exactly representable.
+    s, S = 4, 3
+    H = W = 32
+    I = np.full((H, W, 3), 0.25)
+    d = np.array([0.9, 0.1, 0.5])
+    I[9:11, 12:14] = d   # inside block (2, 3), whose grid sample is pixel (10, 14)
+    j = O.joint(I, s, S, N=1, strict=strict)
+    it = j["iters"][0]
+    assert it["n_large"] == 4 and it["M"] == 1 and it["accepted"] == 1
+    assert np.all(j["err"] < 1e-12)
+    assert np.allclose(j["L"][2, 3], d)
+
+
+def test_joint_strict_rolls_back_collateral_damage():
+    # window 1x1: every HR pixel can use only its own block's LR pixel. One outlier pixel in a
+    # block of background: replacing the LR pixel by the outlier fixes that pixel but breaks the
+    # other s*s - 1. STRICT compares the total error over the affected pixels and rolls back;
+    # PAPER (sums over C_i only, as Algorithm 2 lists) accepts.
+    s, S = 4, 1
+    I = np.full((8, 8, 3), 0.2)
+    I[0, 0] = [0.8, 0.8, 0.8]
+    js = O.joint(I, s, S, N=1, strict=True)
+    jp = O.joint(I, s, S, N=1, strict=False)
+    assert js["iters"][0]["rolled_back"] == 1 and js["iters"][0]["accepted"] == 0
+    assert list(js["accept_log"]) == [0]
+    assert jp["iters"][0]["accepted"] == 1 and list(jp["accept_log"]) == [1]
+    assert np.allclose(js["L"][0, 0], 0.2) and np.allclose(jp["L"][0, 0], 0.8)
+    e = np.linalg.norm(np.array([0.6, 0.6, 0.6]))
+    assert js["err"].sum() == pytest.approx(e, abs=1e-12)
+    # PAPER leaves the other pixels' stored error stale (0) although they are now wrong
+    assert jp["err"].sum() == pytest.approx(0.0, abs=1e-12)
+    fresh = O.glu_fast(I, jp["L"], s, S)
+    assert fresh["err"].sum() == pytest.approx(15 * e, abs=1e-9)
+
+
+def test_joint_argmax_picks_largest_error_pixel():
+    # two large-error pixels of one component inside the same block: the one with the larger
+    # error replaces the LR colour (Algorithm 2, the argmax over [q_up] intersected with C_i)
+    s, S = 4, 1
+    I = np.full((4, 4, 3), 0.5)
+    I[0, 0] = [0.9, 0.5, 0.5]     # error 0.4
+    I[0, 1] = [1.0, 0.5, 0.5]     # error 0.5, 8-connected to (0, 0)
+    j = O.joint(I, s, S, N=1, strict=False)
+    assert j["iters"][0]["M"] == 1
+    assert np.allclose(j["L"][0, 0], [1.0, 0.5, 0.5])
+
+
+# ----------------------------------------------------------------- LR operators (fixtures)
+
+def test_lr_operators_closed_forms():
+    X = np.zeros((5, 5, 3))
+    X[2, 2] = 1.0
+    G = O.op_gauss3(X)
+    k = np.array([0.25, 0.5, 0.25])
+    assert np.allclose(G[1:4, 1:4, 0], np.outer(k, k))
+    B = O.op_box3(X)
+    assert np.allclose(B[1:4, 1:4, 1], 1 / 9)
+    c = np.full((4, 6, 3), 0.37)
+    assert np.allclose(O.op_box3(c), 0.37) and np.allclose(O.op_gauss3(c), 0.37)
+    Y = np.random.Generator(np.random.PCG64(3)).uniform(size=(4, 4, 3))
+    assert np.allclose(O.op_saturation(Y, 1.0), Y)
+    gray = np.full((2, 2, 3), 0.4)
+    assert np.allclose(O.op_saturation(gray, 1.3), 0.4)
+    assert O.op_gamma(np.array([[[0.5]]]), 0.8)[0, 0, 0] == pytest.approx(math.exp(0.8 * math.log(0.5)))

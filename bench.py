@@ -1,0 +1,402 @@
+"""Throughput of the GLU hot path on one (or N replica) GB300 GPUs.
+
+One step = the whole 3840x2160 x8 pipeline on a seeded synthetic guide already resident in HBM:
+glu_joint_optimize (grid downsample, Algorithm 1, Algorithm 2 with a 5x5 window and 5
+iterations), the LR operator (3x3 box blur then saturation x1.3), glu_apply (Eq. 1, float32 HR
+output). Metric: HR Mpixel/s (higher is better). L2 is flushed (a 2 x L2 buffer is written)
+between timed steps; every step is timed with CUDA events on the stream it runs on.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload on the
+host cores (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H4K, W4K, SCALE, WIN, NITER = 2160, 3840, 8, 5, 5
+METRIC = "HR Mpix/s for GLU optimise+apply at 4K x8; batched/bwd vs plain; % of roofline"
+WORKLOAD = "joint-optimise+LRop+apply 3840x2160 x8, 5x5 window, 5 Alg.2 iterations, STRICT"
+# canonical FP32 lane operations of Algorithm 1 per window candidate (a-step 7, b-step 20)
+OPS_PER_CANDIDATE = 27
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    src="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- CPU oracle arm
+
+def oracle_pipeline_sample(img, rows: int):
+    """The oracle's pipeline on the top `rows` rows of the guide (a bounded sample): Algorithm 2,
+    the LR operator, Eq. 1. Returns (pixels, seconds)."""
+    from oracle import oracle as O
+    crop = img[:rows]
+    t0 = time.perf_counter()
+    j = O.joint(crop, SCALE, WIN, N=NITER, strict=True)
+    T = O.op_saturation(O.op_box3(j["L"]), 1.3)
+    _ = O.apply(j["ka"], j["kb"], j["omega"], SCALE, WIN, T)
+    return crop.shape[0] * crop.shape[1], time.perf_counter() - t0
+
+
+def cpu_baseline(img, rows=720):
+    px, sec = oracle_pipeline_sample(img, rows)
+    return dict(value=px / sec / 1e6, unit="HR Mpix/s", cores=os.cpu_count(), kind="oracle",
+                sample=f"FP64 oracle pipeline (Alg.2 N={NITER} STRICT, LR op, Eq.1) on the top "
+                       f"{rows} rows of the 3840x2160 guide ({px} px, {sec:.2f} s)")
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2307_09582_gb300.inputs import joint_4k_scene, render_u8
+    img = render_u8(joint_4k_scene())
+    rows = 270
+    for _ in range(args.warmup):
+        oracle_pipeline_sample(img, rows)
+    times, px = [], 0
+    for _ in range(args.steps):
+        px, sec = oracle_pipeline_sample(img, rows)
+        times.append(sec)
+    tot = sum(times)
+    value = px * args.steps / tot / 1e6
+    sample = (f"FP64 oracle pipeline on the top {rows} rows of the 3840x2160 guide per step "
+              f"({px} px)")
+    line = dict(metric=METRIC, value=value, unit="HR Mpix/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * tot / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, sample=sample),
+                cpu_baseline=dict(value=value, unit="HR Mpix/s", cores=os.cpu_count(),
+                                  kind="oracle", sample=sample),
+                e2e=dict(value=value, unit="HR Mpix/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+def run_glu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_09582_gb300 import api
+    from paper_2307_09582_gb300.inputs import joint_4k_scene, render_u8
+
+    img = render_u8(joint_4k_scene())
+    H, W = img.shape[:2]
+    h, w = api.lr_dims(H, W, SCALE)
+    npx = H * W
+    stream = torch.cuda.current_stream()
+    hr = torch.from_numpy(img).to(dev)
+    params = api.glu_params(S=WIN, N=NITER)
+    lr = torch.empty((h, w, 3), dtype=torch.uint8, device=dev)
+    theta = api.Theta.empty(H, W, SCALE, WIN, api.GLU_W_UNORM16, dev)
+    err = torch.empty((H, W), dtype=torch.float32, device=dev)
+    wsz = api.glu_joint_workspace_size(H, W, SCALE, params)
+    wsbuf = torch.empty(wsz + 256, dtype=torch.uint8, device=dev)
+    Lf = torch.empty((h, w, 3), dtype=torch.float32, device=dev)
+    T1 = torch.empty_like(Lf)
+    T2 = torch.empty_like(Lf)
+    out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    ev = {k: [] for k in ("s", "j", "o", "e")}
+
+    def step(record):
+        if record:
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+        api.glu_joint_optimize(hr, SCALE, params, lr_out=lr, theta=theta, err_map=err,
+                               stats=False, workspace=wsbuf)
+        if record:
+            e[1].record(stream)
+        # LR operator on the optimised LR image (uint8 -> [0,1] float is torch plumbing)
+        torch.div(lr, 255.0, out=Lf)
+        api.glu_fx_filter3(Lf, 0, out=T1)
+        api.glu_fx_point(T1, sat=1.3, gamma=1.0, out=T2)
+        if record:
+            e[2].record(stream)
+        api.glu_apply(theta, T2, out=out)
+        if record:
+            e[3].record(stream)
+            for k, x in zip(("s", "j", "o", "e"), e):
+                ev[k].append(x)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step(False)
+    torch.cuda.synchronize()
+    # one checked run with statistics (outside the timed region)
+    _, _, _, st = api.glu_joint_optimize(hr, SCALE, params, lr_out=lr, theta=theta, err_map=err,
+                                         stats=True, workspace=wsbuf)
+    searched = sum(it["searched"] for it in st["iters"])
+    status = api.glu_device_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after the warm-up run")
+
+    api.glu_joint_profile(True)
+    api.glu_joint_profile_read()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            step(True)
+        torch.cuda.synchronize()
+    barrier(ws)
+    api.glu_joint_profile(False)
+    prof = api.glu_joint_profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev["s"], ev["e"])]
+    joint_ms = [a.elapsed_time(b) for a, b in zip(ev["s"], ev["j"])]
+    apply_ms = [a.elapsed_time(b) for a, b in zip(ev["o"], ev["e"])]
+    tot = max_over_ranks(sum(step_ms), ws, dev)
+    ms_per_step = tot / args.steps
+    value = ws * npx * args.steps / (tot / 1e3) / 1e6
+
+    # roofline of the dominant kernel (per-launch times from events on the launching stream)
+    pk = peaks()
+    K = WIN * WIN
+    alu_peak = sms * 128 * pk["sm_max_mhz"] * 1e6 / 1e12   # FP32 lane ops, T/s
+    calls = max(prof["calls"], 1)
+    cand = {
+        "glu_search (Alg.1, k_search)": dict(ms=prof["search_ms"] / calls, bound="alu",
+                                             work=OPS_PER_CANDIDATE * K * npx / 1e12,
+                                             peak=alu_peak, unit="TFLOP/s"),
+        "glu_joint trials (Alg.2, k_trials)": dict(ms=prof["trials_ms"] / calls, bound="alu",
+                                                   work=OPS_PER_CANDIDATE * K * searched / 1e12,
+                                                   peak=alu_peak, unit="TFLOP/s"),
+        "glu_apply (Eq.1, k_apply)": dict(ms=statistics.mean(apply_ms), bound="hbm",
+                                          work=(npx * (2 + 2 + 12) + h * w * 12) / 1e9,
+                                          peak=pk["hbm_gbs"], unit="GB/s"),
+    }
+    dom_name, dom = max(cand.items(), key=lambda kv: kv[1]["ms"])
+    achieved = dom["work"] / (dom["ms"] / 1e3)
+    roofline = dict(kernel=dom_name, bound=dom["bound"], achieved=achieved, peak=dom["peak"],
+                    unit=dom["unit"], frac=achieved / dom["peak"], traffic=None,
+                    peak_source=pk["src"], launch_ms=dom["ms"],
+                    others={k: dict(ms=v["ms"], frac=(v["work"] / (v["ms"] / 1e3)) / v["peak"])
+                            for k, v in cand.items()})
+
+    # end to end through the public API with host buffers: H2D guide, pipeline, D2H result
+    hr_host = torch.from_numpy(img).pin_memory()
+    out_host = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for i in range(args.steps + 1):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hr.copy_(hr_host, non_blocking=True)
+        step(False)
+        out_host.copy_(out, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if i > 0:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_tot = max_over_ranks(sum(e2e_ms), ws, dev)
+    e2e_val = ws * npx * len(e2e_ms) / (e2e_tot / 1e3) / 1e6
+
+    extras = {}
+    if args.extras and rank == 0:
+        extras = measure_extras(api, torch, img, dev, flush, stream)
+
+    line = None
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit="HR Mpix/s", n_gpus=ws, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=ms_per_step, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                    config=dict(workload=WORKLOAD, H=H, W=W, scale=SCALE, window=WIN,
+                                iterations=NITER, joint="STRICT", weights="unorm16",
+                                l2="flushed between steps (write of a 2xL2 buffer)",
+                                parallelism=f"replicas x{ws}"),
+                    roofline=roofline,
+                    e2e=dict(value=e2e_val, unit="HR Mpix/s", h2d_bytes_per_step=img.nbytes,
+                             d2h_bytes_per_step=out_host.numel() * 4),
+                    gpu_launches=args.steps * (api.joint_launches(NITER) + 3),
+                    clocks=clk.summary(),
+                    breakdown=dict(joint_ms=statistics.mean(joint_ms),
+                                   apply_ms=statistics.mean(apply_ms),
+                                   joint_phases_ms={k: v / calls for k, v in prof.items()
+                                                    if k.endswith("_ms")},
+                                   joint_stats=dict(R0=st["R0"], iters=st["iters"])),
+                    extras=extras)
+        if args.cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(img)
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_extras(api, torch, img, dev, flush, stream):
+    """Secondary numbers (not the headline): plain GLU (no joint) and the adjoint."""
+    H, W = img.shape[:2]
+    h, w = api.lr_dims(H, W, SCALE)
+    hr = torch.from_numpy(img).to(dev)
+    res = {}
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    lr = api.glu_downsample(hr, SCALE, api.GLU_DOWN_GRID)
+    p = api.glu_params(S=WIN)
+    theta = api.Theta.empty(H, W, SCALE, WIN, api.GLU_W_UNORM16, dev)
+    T = torch.rand((h, w, 3), device=dev)
+    out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+
+    def plain():
+        api.glu_downsample(hr, SCALE, api.GLU_DOWN_GRID, lr=lr)
+        api.glu_optimize(hr, lr, p, SCALE, theta=theta)
+        api.glu_apply(theta, T, out=out)
+
+    ms = timed(plain)
+    res["plain_glu_minus_mpix_s"] = H * W / ms / 1e3
+    ms_s = timed(lambda: api.glu_optimize(hr, lr, p, SCALE, theta=theta))
+    res["search_ms"] = ms_s
+    ms_a = timed(lambda: api.glu_apply(theta, T, out=out))
+    res["apply_ms"] = ms_a
+    G = torch.randn((H, W, 3), device=dev)
+    gT = torch.empty((h, w, 3), device=dev)
+    gw = torch.empty((H, W), device=dev)
+    ms_b = timed(lambda: api.glu_apply_backward(theta, T, G, grad_lr=gT, grad_w=gw))
+    res["backward_ms"] = ms_b
+    res["backward_vs_apply"] = ms_b / ms_a
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="glu", choices=["glu", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_glu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * glu.h — C ABI of the GB300 (sm_103a) Guided Linear Upsampling library (libglu.so).
+ *
+ * Method: Song et al., "Guided Linear Upsampling", ACM TOG 2023. Every HR pixel p is represented
+ * as T_p = w * T_a + (1 - w) * T_b with a, b two LR pixels of a small window around p's LR
+ * position (Eq. 1); the pair and weight are chosen on the guide image alone (Eq. 3, Algorithm 1)
+ * and can then be applied to any processed LR image. The LR image itself can be re-optimised
+ * jointly with the parameters (Eq. 6, Algorithm 2).
+ *
+ * Conventions shared by every call
+ *  - All image / parameter buffers are DEVICE memory owned by the caller, unless a comment says
+ *    "host". The library never allocates on these calls and keeps no pointer after returning.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *    default stream) unless stated otherwise. Errors in the arguments are reported
+ *    synchronously by the return value; no exception crosses the ABI.
+ *  - Return value: GLU_OK (0) or a negative GLU_ERR_* code; glu_status_string() names it.
+ *  - Colour units: GLU_U8 images hold colour * 255 (0..255); GLU_F16 / GLU_F32 images hold
+ *    colours in [0, 1]. Error maps, eps and tau are in [0, 1] colour units.
+ *  - Geometry: for an H x W HR image and integer scale s, the LR image is h x w with
+ *    h = ceil(H / s), w = ceil(W / s). HR pixel (y, x) lies in LR block (y / s, x / s).
+ *    The window of that block is the S x S LR neighbourhood centred on it, clipped to the
+ *    image; window index k = (dy + r) * S + (dx + r), r = (S - 1) / 2.
+ *  - Theta (the paper's 3 x H x W parameter tensor) is stored as a uint16 pair code
+ *    code = k_a * S * S + k_b per HR pixel (row-major, H x W, no padding) plus a weight plane.
+ */
+#ifndef GLU_H
+#define GLU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------- status codes */
+#define GLU_OK 0
+#define GLU_ERR_INVALID_ARG (-1)   /* null pointer, bad enum, bad parameter value */
+#define GLU_ERR_SHAPE (-2)         /* image sizes inconsistent with each other or the scale */
+#define GLU_ERR_UNSUPPORTED (-3)   /* valid but not implemented combination (dtype, S, ...) */
+#define GLU_ERR_WORKSPACE (-4)     /* workspace missing or smaller than *_workspace_size() */
+#define GLU_ERR_CUDA (-5)          /* a CUDA runtime call failed (launch, copy, attribute) */
+#define GLU_ERR_DEVICE_CHECK (-6)  /* a kernel's own bounds/consistency check fired */
+#define GLU_ERR_TIMEOUT (-7)       /* a bounded device-side wait gave up */
+
+/* ------------------------------------------------------------------------------- types */
+typedef enum { GLU_U8 = 0, GLU_F16 = 1, GLU_F32 = 2 } glu_dtype;
+
+/* An image: h rows of w pixels with c interleaved channels; row r starts at
+ * data + r * pitch elements (pitch >= w * c). */
+typedef struct {
+    void* data;
+    int32_t h, w, c;
+    int32_t dtype;      /* glu_dtype */
+    int64_t pitch;      /* elements between consecutive row starts */
+} glu_image;
+
+typedef enum { GLU_W_F32 = 0, GLU_W_F16 = 1, GLU_W_UNORM16 = 2 } glu_wfmt;
+
+/* Theta for an H x W HR image at scale `scale` with an S x S window. */
+typedef struct {
+    uint16_t* code;     /* H * W pair codes, k_a * S * S + k_b */
+    void* weight;       /* H * W weights w in [0, 1] (Eq. 5) stored as `wfmt` */
+    int32_t H, W, scale, S;
+    int32_t wfmt;       /* glu_wfmt; UNORM16 stores round(w * 65535) */
+} glu_theta;
+
+typedef enum { GLU_MODE_FAST = 0, GLU_MODE_GNU = 1 } glu_mode;
+typedef enum { GLU_JOINT_STRICT = 0, GLU_JOINT_PAPER = 1 } glu_joint_mode;
+typedef enum { GLU_DOWN_GRID = 0, GLU_DOWN_BOX = 1 } glu_down_mode;
+
+typedef struct {
+    int32_t S;            /* odd window size 1..9 (the paper uses 3, Sec. 5.3) */
+    float eps;            /* epsilon of Eq. 4 / Eq. 5 (paper: 1e-3, Sec. 3.1) */
+    float tau;            /* large-error threshold of Algorithm 2 (paper: 30/255) */
+    int32_t N;            /* maximum iterations of Algorithm 2 (paper: 3), <= GLU_MAX_ITERS */
+    int32_t mode;         /* glu_mode: Algorithm 1, or the weight-1 special case (GNU) */
+    int32_t joint;        /* glu_joint_mode: STRICT (default) or PAPER reading of Algorithm 2 */
+    int32_t connectivity; /* 8 (default) or 4: adjacency of large-error components */
+} glu_params;
+
+#define GLU_MAX_ITERS 32
+
+/* Host-side statistics of glu_joint_optimize. */
+typedef struct {
+    int32_t iterations;                  /* iterations whose trials ran */
+    int32_t n_large[GLU_MAX_ITERS];      /* |E| = #{p : E_p > tau} at the start of iteration n */
+    int32_t components[GLU_MAX_ITERS];   /* M, connected components of that set */
+    int32_t accepted[GLU_MAX_ITERS];     /* trials kept (e1 <= e0) */
+    int32_t rolled_back[GLU_MAX_ITERS];  /* trials undone (e1 > e0) */
+    double residual[GLU_MAX_ITERS + 1];  /* R_0 .. R_n = sum_p E_p, FP64, fixed-order reduction */
+    int64_t searched[GLU_MAX_ITERS];     /* HR pixels re-run through Algorithm 1 by the trials
+                                            (both the trial pass and the commit pass) */
+} glu_joint_stats;
+
+/* Fill *p with the paper's parameters: S = 3, eps = 1e-3, tau = 30/255, N = 3, FAST, STRICT,
+ * 8-connectivity (Sec. 3.1 and Sec. 5.3). */
+void glu_params_default(glu_params* p);
+
+/* ------------------------------------------------------------------------- entry points */
+
+/* Downsample an HR image by integer factor `scale` (Sec. 3.3).
+ *  GLU_DOWN_GRID: regular grid sampling — LR pixel (v, u) copies HR pixel
+ *      (v*s + e_y/2, u*s + e_x/2), e = extent of the block (s, or less for the last one).
+ *      hr: U8/F16/F32; lr: same dtype as hr, or F32.
+ *  GLU_DOWN_BOX: mean of the block (not the paper's default; a filtered LR image for GLU
+ *      without joint optimisation). hr: U8/F16/F32; lr: F32 or F16.
+ *  c must be equal on both sides (1..4); lr->h, lr->w must be ceil(H/s), ceil(W/s). */
+int glu_downsample(const glu_image* hr, int32_t scale, int32_t mode, glu_image* lr, void* stream);
+
+/* Algorithm 1 (Sec. 3.2) for every HR pixel: a = the window pixel nearest in colour to I_p
+ * (ties: lowest k), then b over the whole window (b = a included) with the Eq. 5 weight,
+ * minimising the Eq. 3 error (ties: lowest k_b). mode GNU fixes w = 1 (b = a).
+ *  hr: U8 or F16, c = 3. lr: U8, F16 or F32, c = 3, h x w = ceil(H/s) x ceil(W/s) where
+ *  s = theta->scale. theta: H, W, scale, S (= params->S) and wfmt set by the caller; code and
+ *  weight are written. err_map (nullable): H * W floats, E_p = ||I_p - I_hat_p|| in [0, 1]
+ *  units, row-major without padding. */
+int glu_optimize(const glu_image* hr, const glu_image* lr, const glu_params* params,
+                 glu_theta* theta, float* err_map, void* stream);
+
+/* Algorithm 2 (Sec. 3.3): joint optimisation of the downsampled image and Theta.
+ * Initialises lr_out by regular grid downsampling of hr, Theta and E by Algorithm 1, then
+ * runs up to params->N iterations of: threshold E > tau, 8-connected components in order of
+ * their smallest raster index, and per component the trial replacement of the LR colours of
+ * the blocks it meets by its largest-error pixel there, re-optimisation and rollback if the
+ * summed error grows. STRICT sums and re-optimises every pixel whose window contains a replaced
+ * LR pixel (exactly the pixels whose error can change); PAPER only the component's own pixels.
+ * Stops early when the set is empty, when an iteration keeps no trial, or when the FP64
+ * residual R_n = sum_p E_p stops decreasing. Components that cannot influence each other are
+ * tried concurrently; the result equals the sequential order.
+ *  hr: U8, c = 3. lr_out: U8, c = 3, ceil(H/s) x ceil(W/s). theta as for glu_optimize.
+ *  err_map (nullable) as for glu_optimize. stats (HOST, nullable): if given, the call
+ *  synchronises `stream` before returning and fills it. ws / ws_bytes: device workspace of at
+ *  least glu_joint_workspace_size() bytes, 256-byte aligned; its contents need no init. */
+int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
+                       glu_image* lr_out, glu_theta* theta, float* err_map,
+                       glu_joint_stats* stats, void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace bytes glu_joint_optimize needs for an H x W image (0 on invalid arguments). */
+size_t glu_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params);
+
+/* Benchmark instrumentation (not part of the method). glu_joint_profile(1) makes later
+ * glu_joint_optimize calls record CUDA events on their stream around their phases; the events
+ * of up to 64 calls are kept. glu_joint_profile_read() waits for them, writes the summed
+ * milliseconds of [control init + grid downsample, the Algorithm 1 search kernel, large-error
+ * set and components, trials, residuals (R_0 and every R_n)] to ms[0..4] and the number of
+ * calls to *calls, then forgets them. glu_joint_profile(0) stops recording. Host-side state;
+ * not thread-safe. */
+int glu_joint_profile(int32_t enable);
+int glu_joint_profile_read(float* ms, int32_t* calls);
+
+/* Eq. 1: out_p = w_p * T_a + (1 - w_p) * T_b for every HR pixel (Algorithm 1, last step).
+ *  lr_target: F32 or F16, c = 1..4, ceil(H/s) x ceil(W/s). hr_out: F32 or F16, same c,
+ *  H x W. */
+int glu_apply(const glu_theta* theta, const glu_image* lr_target, glu_image* hr_out,
+              void* stream);
+
+/* Adjoint of Eq. 1 with the pair choice held fixed. For an upstream gradient G (grad_hr,
+ * F32, H x W x c):
+ *   grad_lr_q = sum_{p : a_p = q} w_p G_p + sum_{p : b_p = q} (1 - w_p) G_p      (F32, h x w x c)
+ *   grad_w_p  = G_p . (T_a - T_b)                                (nullable, F32, H * W, dense)
+ * Each LR pixel sums its contributions in a fixed order (no atomics): results are
+ * bit-reproducible. lr_target: F32, as passed to glu_apply. */
+int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
+                       const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* stream);
+
+/* Name of a status code (static string). */
+const char* glu_status_string(int status);
+
+/* Read and clear the device-side status words the kernels set (bounds checks, bounded waits).
+ * Synchronous: waits for `stream`. Returns GLU_OK or the first recorded GLU_ERR_*. */
+int glu_device_status(void* stream);
+
+/* Library version string. */
+const char* glu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLU_H */

@@ -69,6 +69,8 @@ def to_unit(img) -> np.ndarray:
     a = np.asarray(img)
     if a.dtype == np.uint8:
         return np.ascontiguousarray(a.astype(np.float64) / 255.0)
+    if a.dtype == np.float64:
+        return np.ascontiguousarray(a)
     return np.ascontiguousarray(a.astype(np.float64))
 
 

@@ -1,0 +1,121 @@
+"""ctypes declarations of the C ABI in include/glu.h (structs, enums, prototypes).
+
+Loading fails loudly when libglu.so has not been built: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libglu.so")
+
+GLU_OK = 0
+GLU_ERR_INVALID_ARG = -1
+GLU_ERR_SHAPE = -2
+GLU_ERR_UNSUPPORTED = -3
+GLU_ERR_WORKSPACE = -4
+GLU_ERR_CUDA = -5
+GLU_ERR_DEVICE_CHECK = -6
+GLU_ERR_TIMEOUT = -7
+
+GLU_U8, GLU_F16, GLU_F32 = 0, 1, 2
+GLU_W_F32, GLU_W_F16, GLU_W_UNORM16 = 0, 1, 2
+GLU_MODE_FAST, GLU_MODE_GNU = 0, 1
+GLU_JOINT_STRICT, GLU_JOINT_PAPER = 0, 1
+GLU_DOWN_GRID, GLU_DOWN_BOX = 0, 1
+GLU_MAX_ITERS = 32
+
+
+class GluImage(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("h", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("c", ctypes.c_int32), ("dtype", ctypes.c_int32), ("pitch", ctypes.c_int64)]
+
+
+class GluTheta(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("H", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("scale", ctypes.c_int32), ("S", ctypes.c_int32),
+                ("wfmt", ctypes.c_int32)]
+
+
+class GluParams(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int32), ("eps", ctypes.c_float), ("tau", ctypes.c_float),
+                ("N", ctypes.c_int32), ("mode", ctypes.c_int32), ("joint", ctypes.c_int32),
+                ("connectivity", ctypes.c_int32)]
+
+
+class GluJointStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32),
+                ("n_large", ctypes.c_int32 * GLU_MAX_ITERS),
+                ("components", ctypes.c_int32 * GLU_MAX_ITERS),
+                ("accepted", ctypes.c_int32 * GLU_MAX_ITERS),
+                ("rolled_back", ctypes.c_int32 * GLU_MAX_ITERS),
+                ("residual", ctypes.c_double * (GLU_MAX_ITERS + 1)),
+                ("searched", ctypes.c_int64 * GLU_MAX_ITERS)]
+
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_f = ctypes.c_float
+
+PROTOTYPES = {
+    "glu_params_default": (None, [_P(GluParams)]),
+    "glu_downsample": (ctypes.c_int, [_P(GluImage), _i32, _i32, _P(GluImage), _vp]),
+    "glu_optimize": (ctypes.c_int, [_P(GluImage), _P(GluImage), _P(GluParams), _P(GluTheta), _vp, _vp]),
+    "glu_joint_optimize": (ctypes.c_int, [_P(GluImage), _i32, _P(GluParams), _P(GluImage),
+                                          _P(GluTheta), _vp, _P(GluJointStats), _vp,
+                                          ctypes.c_size_t, _vp]),
+    "glu_joint_workspace_size": (ctypes.c_size_t, [_i32, _i32, _i32, _P(GluParams)]),
+    "glu_apply": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _vp]),
+    "glu_apply_backward": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _P(GluImage),
+                                          _vp, _vp]),
+    "glu_joint_profile": (ctypes.c_int, [_i32]),
+    "glu_joint_profile_read": (ctypes.c_int, [_P(ctypes.c_float), _P(_i32)]),
+    "glu_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "glu_device_status": (ctypes.c_int, [_vp]),
+    "glu_version": (ctypes.c_char_p, []),
+    "glu_fx_filter3": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _i64, _i32, _vp]),
+    "glu_fx_point": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp, _i64, _f, _f, _vp]),
+}
+
+_LIB = None
+
+
+class GluError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} returned {code} ({status_string(code)})")
+        self.code = code
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libglu.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libglu.so not found at {p}: the CUDA library must be built first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in PROTOTYPES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    names = {0: "GLU_OK", -1: "GLU_ERR_INVALID_ARG", -2: "GLU_ERR_SHAPE",
+             -3: "GLU_ERR_UNSUPPORTED", -4: "GLU_ERR_WORKSPACE", -5: "GLU_ERR_CUDA",
+             -6: "GLU_ERR_DEVICE_CHECK", -7: "GLU_ERR_TIMEOUT"}
+    return names.get(code, "GLU_ERR_UNKNOWN")
+
+
+def check(fn: str, code: int) -> int:
+    if code != GLU_OK:
+        raise GluError(fn, code)
+    return code

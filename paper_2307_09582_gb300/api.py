@@ -1,0 +1,274 @@
+"""Python binding of libglu.so: the C entry points under the same names, taking torch tensors.
+
+Argument marshalling only: tensors become (pointer, sizes, pitch) descriptors and the current
+CUDA stream is passed through; every step of the computation runs in the library's kernels.
+Output tensors that the caller does not provide are allocated here with torch (device memory
+plumbing; the library itself never allocates).
+
+Image tensors are (h, w, c) with the last two dimensions contiguous; uint8 holds colour * 255,
+float16 / float32 hold colours in [0, 1].
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _abi as A
+from ._abi import (GLU_DOWN_BOX, GLU_DOWN_GRID, GLU_F16, GLU_F32, GLU_JOINT_PAPER,  # noqa: F401
+                   GLU_JOINT_STRICT, GLU_MODE_FAST, GLU_MODE_GNU, GLU_U8, GLU_W_F16, GLU_W_F32,
+                   GLU_W_UNORM16, GluError)
+
+_DT = {torch.uint8: A.GLU_U8, torch.float16: A.GLU_F16, torch.float32: A.GLU_F32}
+_WT = {A.GLU_W_F32: torch.float32, A.GLU_W_F16: torch.float16, A.GLU_W_UNORM16: torch.int16}
+
+
+def lib():
+    return A.load()
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p | None:
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def image(t: torch.Tensor) -> A.GluImage:
+    """Descriptor of an (h, w, c) tensor whose last two dims are contiguous."""
+    if t.dim() == 2:
+        t = t.unsqueeze(-1)
+    if t.dim() != 3 or t.stride(2) != 1 or t.stride(1) != t.shape[2]:
+        raise ValueError("image tensors must be (h, w, c) with contiguous pixels")
+    if t.dtype not in _DT:
+        raise TypeError(f"unsupported image dtype {t.dtype}")
+    return A.GluImage(t.data_ptr(), t.shape[0], t.shape[1], t.shape[2], _DT[t.dtype], t.stride(0))
+
+
+def lr_dims(H: int, W: int, s: int):
+    return (H + s - 1) // s, (W + s - 1) // s
+
+
+def glu_params(S=3, eps=1e-3, tau=30.0 / 255.0, N=3, mode=A.GLU_MODE_FAST,
+               joint=A.GLU_JOINT_STRICT, connectivity=8) -> A.GluParams:
+    p = A.GluParams()
+    lib().glu_params_default(ctypes.byref(p))
+    p.S, p.eps, p.tau, p.N = S, eps, tau, N
+    p.mode, p.joint, p.connectivity = mode, joint, connectivity
+    return p
+
+
+@dataclass
+class Theta:
+    """Per-HR-pixel pair codes (k_a * S * S + k_b, stored in int16 as uint16) and weights."""
+    code: torch.Tensor
+    weight: torch.Tensor
+    H: int
+    W: int
+    scale: int
+    S: int
+    wfmt: int = A.GLU_W_F32
+
+    @staticmethod
+    def empty(H, W, scale, S, wfmt=A.GLU_W_F32, device="cuda") -> "Theta":
+        code = torch.empty((H, W), dtype=torch.int16, device=device)
+        weight = torch.empty((H, W), dtype=_WT[wfmt], device=device)
+        return Theta(code, weight, H, W, scale, S, wfmt)
+
+    def desc(self, weight: torch.Tensor | None = None, wfmt: int | None = None) -> A.GluTheta:
+        w = self.weight if weight is None else weight
+        return A.GluTheta(self.code.data_ptr(), w.data_ptr(), self.H, self.W, self.scale, self.S,
+                          self.wfmt if wfmt is None else wfmt)
+
+    def weight_f32(self) -> torch.Tensor:
+        if self.wfmt == A.GLU_W_UNORM16:
+            return (self.weight.view(torch.uint16).to(torch.float32) / 65535.0) \
+                if hasattr(torch, "uint16") else \
+                ((self.weight.to(torch.int32) & 0xFFFF).to(torch.float32) / 65535.0)
+        return self.weight.to(torch.float32)
+
+    def codes_i32(self) -> torch.Tensor:
+        return self.code.to(torch.int32) & 0xFFFF
+
+
+def glu_downsample(hr: torch.Tensor, scale: int, mode: int = A.GLU_DOWN_GRID,
+                   lr: torch.Tensor | None = None, dtype=None, stream=None) -> torch.Tensor:
+    H, W, C = hr.shape
+    h, w = lr_dims(H, W, scale)
+    if lr is None:
+        dt = dtype or (hr.dtype if mode == A.GLU_DOWN_GRID else torch.float32)
+        lr = torch.empty((h, w, C), dtype=dt, device=hr.device)
+    hi, li = image(hr), image(lr)
+    A.check("glu_downsample", lib().glu_downsample(ctypes.byref(hi), scale, mode,
+                                                   ctypes.byref(li), _stream(stream)))
+    return lr
+
+
+def glu_optimize(hr: torch.Tensor, lr: torch.Tensor, params: A.GluParams, scale: int,
+                 theta: Theta | None = None, err_map: torch.Tensor | bool | None = None,
+                 wfmt: int = A.GLU_W_F32, stream=None):
+    """Algorithm 1 on every pixel. Returns (theta, err_map or None)."""
+    H, W = hr.shape[:2]
+    if theta is None:
+        theta = Theta.empty(H, W, scale, params.S, wfmt, hr.device)
+    if err_map is True:
+        err_map = torch.empty((H, W), dtype=torch.float32, device=hr.device)
+    elif err_map is False:
+        err_map = None
+    hi, li, td = image(hr), image(lr), theta.desc()
+    A.check("glu_optimize", lib().glu_optimize(ctypes.byref(hi), ctypes.byref(li),
+                                               ctypes.byref(params), ctypes.byref(td),
+                                               _ptr(err_map), _stream(stream)))
+    return theta, err_map
+
+
+def glu_joint_workspace_size(H: int, W: int, scale: int, params: A.GluParams) -> int:
+    return int(lib().glu_joint_workspace_size(H, W, scale, ctypes.byref(params)))
+
+
+def glu_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
+                       lr_out: torch.Tensor | None = None, theta: Theta | None = None,
+                       err_map: torch.Tensor | bool | None = True, stats: bool = True,
+                       workspace: torch.Tensor | None = None, wfmt: int = A.GLU_W_F32,
+                       stream=None):
+    """Algorithm 2. Returns (lr, theta, err_map or None, stats dict or None)."""
+    H, W = hr.shape[:2]
+    h, w = lr_dims(H, W, scale)
+    if lr_out is None:
+        lr_out = torch.empty((h, w, 3), dtype=torch.uint8, device=hr.device)
+    if theta is None:
+        theta = Theta.empty(H, W, scale, params.S, wfmt, hr.device)
+    if err_map is True:
+        err_map = torch.empty((H, W), dtype=torch.float32, device=hr.device)
+    elif err_map is False:
+        err_map = None
+    need = glu_joint_workspace_size(H, W, scale, params)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need + 256, dtype=torch.uint8, device=hr.device)
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    avail = workspace.numel() - (aligned - base)
+    st = A.GluJointStats() if stats else None
+    hi, li, td = image(hr), image(lr_out), theta.desc()
+    A.check("glu_joint_optimize", lib().glu_joint_optimize(
+        ctypes.byref(hi), scale, ctypes.byref(params), ctypes.byref(li), ctypes.byref(td),
+        _ptr(err_map), ctypes.byref(st) if st is not None else None, ctypes.c_void_p(aligned),
+        avail, _stream(stream)))
+    sd = None
+    if st is not None:
+        n = st.iterations
+        sd = dict(iterations=n, R0=st.residual[0],
+                  iters=[dict(n_large=st.n_large[k], M=st.components[k],
+                              accepted=st.accepted[k], rolled_back=st.rolled_back[k],
+                              residual=st.residual[k + 1], searched=st.searched[k])
+                         for k in range(n)],
+                  n_large_next=st.n_large[n] if n < A.GLU_MAX_ITERS else 0)
+    return lr_out, theta, err_map, sd
+
+
+def glu_apply(theta: Theta, lr_target: torch.Tensor, out: torch.Tensor | None = None,
+              out_dtype=torch.float32, weight: torch.Tensor | None = None, stream=None):
+    """Eq. 1. `weight` (float32, H x W) overrides the stored weights (used by autograd)."""
+    C = lr_target.shape[2] if lr_target.dim() == 3 else 1
+    if out is None:
+        out = torch.empty((theta.H, theta.W, C), dtype=out_dtype, device=lr_target.device)
+    td = theta.desc(weight, A.GLU_W_F32 if weight is not None else None)
+    ti, oi = image(lr_target), image(out)
+    A.check("glu_apply", lib().glu_apply(ctypes.byref(td), ctypes.byref(ti), ctypes.byref(oi),
+                                         _stream(stream)))
+    return out
+
+
+def glu_apply_backward(theta: Theta, lr_target: torch.Tensor, grad_hr: torch.Tensor,
+                       grad_lr: torch.Tensor | None = None, grad_w: torch.Tensor | bool = True,
+                       weight: torch.Tensor | None = None, stream=None):
+    """Adjoint of Eq. 1: returns (grad_lr, grad_w or None)."""
+    if grad_lr is None:
+        grad_lr = torch.empty_like(lr_target, dtype=torch.float32)
+    if grad_w is True:
+        grad_w = torch.empty((theta.H, theta.W), dtype=torch.float32, device=grad_hr.device)
+    elif grad_w is False:
+        grad_w = None
+    td = theta.desc(weight, A.GLU_W_F32 if weight is not None else None)
+    ti, gi, go = image(lr_target), image(grad_hr), image(grad_lr)
+    A.check("glu_apply_backward", lib().glu_apply_backward(
+        ctypes.byref(td), ctypes.byref(ti), ctypes.byref(gi), ctypes.byref(go), _ptr(grad_w),
+        _stream(stream)))
+    return grad_lr, grad_w
+
+
+def glu_joint_profile(enable: bool) -> None:
+    A.check("glu_joint_profile", lib().glu_joint_profile(1 if enable else 0))
+
+
+def glu_joint_profile_read() -> dict:
+    """Summed phase times (ms) of the profiled glu_joint_optimize calls since the last read."""
+    ms = (ctypes.c_float * 5)()
+    calls = ctypes.c_int32()
+    A.check("glu_joint_profile_read", lib().glu_joint_profile_read(ms, ctypes.byref(calls)))
+    return dict(calls=calls.value, prep_ms=ms[0], search_ms=ms[1], components_ms=ms[2],
+                trials_ms=ms[3], residual_ms=ms[4])
+
+
+def joint_launches(N: int) -> int:
+    """Kernel launches one glu_joint_optimize call makes (iterations after convergence still
+    launch and return at once): control init, grid downsample, search, R_0 (2), then per
+    iteration threshold, merge, flatten, 3 root-compaction, count, 3 scan, fill, trials and the
+    residual (2)."""
+    return 5 + 14 * N
+
+
+def glu_device_status(stream=None) -> int:
+    return int(lib().glu_device_status(_stream(stream)))
+
+
+def glu_fx_filter3(x: torch.Tensor, op: int, out: torch.Tensor | None = None, stream=None):
+    """LR operator fixture: 3x3 box (op 0) or [1 2 1]/4 Gaussian (op 1), clamped edges."""
+    out = torch.empty_like(x) if out is None else out
+    h, w, C = x.shape
+    A.check("glu_fx_filter3", lib().glu_fx_filter3(_ptr(x), h, w, C, x.stride(0), _ptr(out),
+                                                   out.stride(0), op, _stream(stream)))
+    return out
+
+
+def glu_fx_point(x: torch.Tensor, sat: float = 1.0, gamma: float = 1.0,
+                 out: torch.Tensor | None = None, stream=None):
+    """LR operator fixture: saturation about Rec. 601 luma (clamped), then per-channel gamma."""
+    out = torch.empty_like(x) if out is None else out
+    h, w, _ = x.shape
+    A.check("glu_fx_point", lib().glu_fx_point(_ptr(x), h, w, x.stride(0), _ptr(out),
+                                               out.stride(0), sat, gamma, _stream(stream)))
+    return out
+
+
+class GluApplyFn(torch.autograd.Function):
+    """T_hat = glu_apply(theta, T_lr) with gradients for T_lr and the weights.
+
+    The pair codes are discrete and held fixed; the backward pass is the library's adjoint
+    (a fixed-order reduction, bit-reproducible)."""
+
+    @staticmethod
+    def forward(ctx, lr_target, weight, theta):
+        lr_target = lr_target.contiguous()
+        weight = weight.contiguous()
+        ctx.theta = theta
+        ctx.save_for_backward(lr_target, weight)
+        return glu_apply(theta, lr_target, weight=weight)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        lr_target, weight = ctx.saved_tensors
+        g = grad_out.contiguous().to(torch.float32)
+        grad_lr, grad_w = glu_apply_backward(ctx.theta, lr_target, g,
+                                             grad_w=ctx.needs_input_grad[1], weight=weight)
+        return (grad_lr if ctx.needs_input_grad[0] else None,
+                grad_w if ctx.needs_input_grad[1] else None, None)
+
+
+def apply_autograd(theta: Theta, lr_target: torch.Tensor, weight: torch.Tensor | None = None):
+    """Differentiable Eq. 1 (w.r.t. the LR target and, if it requires grad, the weights)."""
+    w = theta.weight_f32() if weight is None else weight
+    return GluApplyFn.apply(lr_target, w, theta)

@@ -1,0 +1,222 @@
+// C-ABI entry points of libglu.so: argument validation, then launches on the caller's stream.
+#include <string.h>
+
+#include "internal.h"
+
+using namespace glu;
+
+namespace {
+
+int dtype_size(int dt) {
+    switch (dt) {
+        case GLU_U8: return 1;
+        case GLU_F16: return 2;
+        case GLU_F32: return 4;
+        default: return 0;
+    }
+}
+
+bool image_ok(const glu_image* im) {
+    return im && im->data && im->h > 0 && im->w > 0 && im->c >= 1 && im->c <= 4 &&
+           dtype_size(im->dtype) > 0 && im->pitch >= (int64_t)im->w * im->c;
+}
+
+bool params_ok(const glu_params* p) {
+    return p && p->S >= 1 && p->S <= 9 && (p->S & 1) && p->eps >= 0.f && p->tau >= 0.f &&
+           p->N >= 0 && p->N <= GLU_MAX_ITERS && (p->mode == GLU_MODE_FAST || p->mode == GLU_MODE_GNU) &&
+           (p->joint == GLU_JOINT_STRICT || p->joint == GLU_JOINT_PAPER) &&
+           (p->connectivity == 4 || p->connectivity == 8);
+}
+
+bool theta_ok(const glu_theta* t) {
+    return t && t->code && t->weight && t->H > 0 && t->W > 0 && t->scale >= 1 && t->S >= 1 &&
+           t->S <= 9 && (t->S & 1) && t->wfmt >= GLU_W_F32 && t->wfmt <= GLU_W_UNORM16;
+}
+
+int lr_dim(int n, int s) { return (n + s - 1) / s; }
+
+}  // namespace
+
+extern "C" {
+
+void glu_params_default(glu_params* p) {
+    if (!p) return;
+    p->S = 3;
+    p->eps = 1e-3f;
+    p->tau = 30.0f / 255.0f;
+    p->N = 3;
+    p->mode = GLU_MODE_FAST;
+    p->joint = GLU_JOINT_STRICT;
+    p->connectivity = 8;
+}
+
+const char* glu_status_string(int s) {
+    switch (s) {
+        case GLU_OK: return "GLU_OK";
+        case GLU_ERR_INVALID_ARG: return "GLU_ERR_INVALID_ARG";
+        case GLU_ERR_SHAPE: return "GLU_ERR_SHAPE";
+        case GLU_ERR_UNSUPPORTED: return "GLU_ERR_UNSUPPORTED";
+        case GLU_ERR_WORKSPACE: return "GLU_ERR_WORKSPACE";
+        case GLU_ERR_CUDA: return "GLU_ERR_CUDA";
+        case GLU_ERR_DEVICE_CHECK: return "GLU_ERR_DEVICE_CHECK";
+        case GLU_ERR_TIMEOUT: return "GLU_ERR_TIMEOUT";
+        default: return "GLU_ERR_UNKNOWN";
+    }
+}
+
+const char* glu_version(void) { return "glu-gb300 0.1 (sm_103a)"; }
+
+int glu_device_status(void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int codes[4] = {read_and_clear_status_search(st), read_and_clear_status_apply(st),
+                    read_and_clear_status_down(st), read_and_clear_status_joint(st)};
+    for (int c : codes)
+        if (c != GLU_OK) return c;
+    return GLU_OK;
+}
+
+int glu_downsample(const glu_image* hr, int32_t scale, int32_t mode, glu_image* lr, void* stream) {
+    if (!image_ok(hr) || !image_ok(lr) || scale < 1) return GLU_ERR_INVALID_ARG;
+    if (mode != GLU_DOWN_GRID && mode != GLU_DOWN_BOX) return GLU_ERR_INVALID_ARG;
+    if (hr->c != lr->c || lr->h != lr_dim(hr->h, scale) || lr->w != lr_dim(hr->w, scale))
+        return GLU_ERR_SHAPE;
+    if (mode == GLU_DOWN_GRID && lr->dtype != hr->dtype && lr->dtype != GLU_F32)
+        return GLU_ERR_UNSUPPORTED;
+    if (mode == GLU_DOWN_BOX && lr->dtype == GLU_U8) return GLU_ERR_UNSUPPORTED;
+    return launch_downsample(*hr, scale, mode, *lr, (cudaStream_t)stream);
+}
+
+int glu_optimize(const glu_image* hr, const glu_image* lr, const glu_params* params,
+                 glu_theta* theta, float* err_map, void* stream) {
+    if (!image_ok(hr) || !image_ok(lr) || !params_ok(params) || !theta_ok(theta))
+        return GLU_ERR_INVALID_ARG;
+    if (hr->c != 3 || lr->c != 3) return GLU_ERR_UNSUPPORTED;
+    if (hr->dtype != GLU_U8 && hr->dtype != GLU_F16) return GLU_ERR_UNSUPPORTED;
+    const int s = theta->scale;
+    if (theta->H != hr->h || theta->W != hr->w || theta->S != params->S ||
+        lr->h != lr_dim(hr->h, s) || lr->w != lr_dim(hr->w, s))
+        return GLU_ERR_SHAPE;
+    SearchArgs a;
+    a.hr = hr->data;
+    a.hr_pitch = hr->pitch;
+    a.hr_dtype = hr->dtype;
+    a.lr = lr->data;
+    a.lr_pitch = lr->pitch;
+    a.lr_dtype = lr->dtype;
+    a.H = hr->h;
+    a.W = hr->w;
+    a.h = lr->h;
+    a.w = lr->w;
+    a.s = s;
+    a.S = params->S;
+    a.eps255 = params->eps * 255.0f;
+    a.gnu = params->mode == GLU_MODE_GNU;
+    a.code = theta->code;
+    a.weight = theta->weight;
+    a.wfmt = theta->wfmt;
+    a.err = err_map;
+    return launch_search(a, (cudaStream_t)stream);
+}
+
+int glu_apply(const glu_theta* theta, const glu_image* lr_target, glu_image* hr_out, void* stream) {
+    if (!theta_ok(theta) || !image_ok(lr_target) || !image_ok(hr_out)) return GLU_ERR_INVALID_ARG;
+    if (lr_target->dtype == GLU_U8 || hr_out->dtype == GLU_U8) return GLU_ERR_UNSUPPORTED;
+    const int s = theta->scale;
+    if (hr_out->h != theta->H || hr_out->w != theta->W || lr_target->c != hr_out->c ||
+        lr_target->h != lr_dim(theta->H, s) || lr_target->w != lr_dim(theta->W, s))
+        return GLU_ERR_SHAPE;
+    ApplyArgs a;
+    a.code = theta->code;
+    a.weight = theta->weight;
+    a.wfmt = theta->wfmt;
+    a.H = theta->H;
+    a.W = theta->W;
+    a.s = s;
+    a.S = theta->S;
+    a.h = lr_target->h;
+    a.w = lr_target->w;
+    a.C = lr_target->c;
+    a.T = lr_target->data;
+    a.T_pitch = lr_target->pitch;
+    a.T_dtype = lr_target->dtype;
+    a.out = hr_out->data;
+    a.out_pitch = hr_out->pitch;
+    a.out_dtype = hr_out->dtype;
+    return launch_apply(a, (cudaStream_t)stream);
+}
+
+int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
+                       const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* stream) {
+    if (!theta_ok(theta) || !image_ok(lr_target) || !image_ok(grad_hr) || !image_ok(grad_lr))
+        return GLU_ERR_INVALID_ARG;
+    if (lr_target->dtype != GLU_F32 || grad_hr->dtype != GLU_F32 || grad_lr->dtype != GLU_F32)
+        return GLU_ERR_UNSUPPORTED;
+    const int s = theta->scale;
+    if (grad_hr->h != theta->H || grad_hr->w != theta->W || grad_hr->c != lr_target->c ||
+        grad_lr->c != lr_target->c || lr_target->h != lr_dim(theta->H, s) ||
+        lr_target->w != lr_dim(theta->W, s) || grad_lr->h != lr_target->h ||
+        grad_lr->w != lr_target->w)
+        return GLU_ERR_SHAPE;
+    BackwardArgs a;
+    a.code = theta->code;
+    a.weight = theta->weight;
+    a.wfmt = theta->wfmt;
+    a.H = theta->H;
+    a.W = theta->W;
+    a.s = s;
+    a.S = theta->S;
+    a.h = lr_target->h;
+    a.w = lr_target->w;
+    a.C = lr_target->c;
+    a.T = (const float*)lr_target->data;
+    a.T_pitch = lr_target->pitch;
+    a.G = (const float*)grad_hr->data;
+    a.G_pitch = grad_hr->pitch;
+    a.gT = (float*)grad_lr->data;
+    a.gT_pitch = grad_lr->pitch;
+    a.gw = grad_w;
+    return launch_apply_backward(a, (cudaStream_t)stream);
+}
+
+size_t glu_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params) {
+    if (H <= 0 || W <= 0 || scale < 1 || !params_ok(params)) return 0;
+    return joint_workspace_bytes(H, W, scale, params->S);
+}
+
+int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
+                       glu_image* lr_out, glu_theta* theta, float* err_map,
+                       glu_joint_stats* stats, void* ws, size_t ws_bytes, void* stream) {
+    if (!image_ok(hr) || !image_ok(lr_out) || !params_ok(params) || !theta_ok(theta) || scale < 1)
+        return GLU_ERR_INVALID_ARG;
+    if (hr->dtype != GLU_U8 || lr_out->dtype != GLU_U8 || hr->c != 3 || lr_out->c != 3)
+        return GLU_ERR_UNSUPPORTED;
+    if (params->mode != GLU_MODE_FAST) return GLU_ERR_UNSUPPORTED;
+    if (theta->H != hr->h || theta->W != hr->w || theta->S != params->S || theta->scale != scale ||
+        lr_out->h != lr_dim(hr->h, scale) || lr_out->w != lr_dim(hr->w, scale))
+        return GLU_ERR_SHAPE;
+    const size_t need = joint_workspace_bytes(hr->h, hr->w, scale, params->S);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return GLU_ERR_WORKSPACE;
+    JointArgs a;
+    a.hr = (const uint8_t*)hr->data;
+    a.hr_pitch = hr->pitch;
+    a.lr = (uint8_t*)lr_out->data;
+    a.lr_pitch = lr_out->pitch;
+    a.H = hr->h;
+    a.W = hr->w;
+    a.h = lr_out->h;
+    a.w = lr_out->w;
+    a.s = scale;
+    a.S = params->S;
+    a.eps255 = params->eps * 255.0f;
+    a.tau = params->tau;
+    a.N = params->N;
+    a.strict = params->joint == GLU_JOINT_STRICT;
+    a.conn = params->connectivity;
+    a.code = theta->code;
+    a.weight = theta->weight;
+    a.wfmt = theta->wfmt;
+    a.err = err_map;
+    return launch_joint(a, ws, ws_bytes, stats, (cudaStream_t)stream);
+}
+
+}  // extern "C"

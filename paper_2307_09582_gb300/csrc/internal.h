@@ -1,0 +1,88 @@
+// Host-side launcher interfaces between the C-ABI layer (api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "glu.h"
+
+namespace glu {
+
+// Arguments of the Algorithm 1 search over a whole image (or a batch item).
+struct SearchArgs {
+    const void* hr;
+    int64_t hr_pitch;  // elements
+    int hr_dtype;
+    const void* lr;
+    int64_t lr_pitch;  // elements
+    int lr_dtype;
+    int H, W, h, w, s, S;
+    float eps255;      // eps in 1/255 colour units
+    int gnu;
+    uint16_t* code;
+    void* weight;
+    int wfmt;
+    float* err;        // nullable
+};
+
+int launch_search(const SearchArgs& a, cudaStream_t st);
+
+struct ApplyArgs {
+    const uint16_t* code;
+    const void* weight;
+    int wfmt;
+    int H, W, s, S, h, w, C;
+    const void* T;
+    int64_t T_pitch;
+    int T_dtype;
+    void* out;
+    int64_t out_pitch;
+    int out_dtype;
+};
+
+int launch_apply(const ApplyArgs& a, cudaStream_t st);
+
+struct BackwardArgs {
+    const uint16_t* code;
+    const void* weight;
+    int wfmt;
+    int H, W, s, S, h, w, C;
+    const float* T;
+    int64_t T_pitch;
+    const float* G;      // H x W x C upstream gradient
+    int64_t G_pitch;
+    float* gT;           // h x w x C
+    int64_t gT_pitch;
+    float* gw;           // nullable, H * W
+};
+
+int launch_apply_backward(const BackwardArgs& a, cudaStream_t st);
+
+int launch_downsample(const glu_image& hr, int s, int mode, const glu_image& lr, cudaStream_t st);
+
+// Status words of each translation unit (read and cleared; synchronous on st).
+int read_and_clear_status_search(cudaStream_t st);
+int read_and_clear_status_apply(cudaStream_t st);
+int read_and_clear_status_down(cudaStream_t st);
+int read_and_clear_status_joint(cudaStream_t st);
+
+// Joint optimisation (Algorithm 2).
+struct JointArgs {
+    const uint8_t* hr;
+    int64_t hr_pitch;   // bytes
+    uint8_t* lr;
+    int64_t lr_pitch;   // bytes
+    int H, W, h, w, s, S;
+    float eps255, tau;
+    int N, strict, conn;
+    uint16_t* code;
+    void* weight;
+    int wfmt;
+    float* err;         // nullable: a workspace plane is used otherwise
+};
+
+size_t joint_workspace_bytes(int H, int W, int s, int S);
+int launch_joint(const JointArgs& a, void* ws, size_t ws_bytes, glu_joint_stats* stats,
+                 cudaStream_t st);
+
+}  // namespace glu

@@ -1,0 +1,113 @@
+// Per-pixel candidate search of Algorithm 1 (Sec. 3.2), shared by the full-image search kernel
+// and the joint-optimisation trials so both compute bit-identical Theta and error values.
+//
+// Colours are floats in 1/255 units. For uint8 inputs every distance ||I_p - L_c||^2 is an
+// integer below 2^24 and is computed exactly, so the nearest-colour choice of a is exact.
+#pragma once
+
+#include "common.cuh"
+
+namespace glu {
+
+struct SearchOut {
+    int ka, kb;     // window indices
+    float omega;    // Eq. 5 weight
+    float err;      // Eq. 3 error ||I_p - I_hat_p|| in [0, 1] units
+};
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Squared colour distance with a fixed operation order (so a = b evaluates identically in both
+// steps and uint8 inputs stay exact).
+__device__ __forceinline__ float dist2(float er, float eg, float eb) {
+    return __fmaf_rn(eb, eb, __fmaf_rn(eg, eg, __fmul_rn(er, er)));
+}
+
+// win: window candidate (dy, dx) at win[dy * rs + dx] (float4: r, g, b, unused).
+// rowmask / colmask: bit i set when window row / column i lies inside the LR image.
+// Ties: a -> lowest k; b -> lowest k_b (strict comparisons in ascending k).
+template <int S>
+__device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win, int rs,
+                                                  uint32_t rowmask, uint32_t colmask, float ir,
+                                                  float ig, float ib, float eps255, bool gnu) {
+    // Step 1: a = the window pixel with the most similar colour (squared distance, exact).
+    float bd = kInf;
+    int a = 0;
+#pragma unroll(S <= 5 ? S : 1)
+    for (int dy = 0; dy < S; ++dy) {
+#pragma unroll
+        for (int dx = 0; dx < S; ++dx) {
+            const bool ok = ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
+            const float4 c = win[dy * rs + dx];
+            const float d2 = dist2(c.x - ir, c.y - ig, c.z - ib);
+            if (ok && d2 < bd) {
+                bd = d2;
+                a = dy * S + dx;
+            }
+        }
+    }
+    const float4 ca = win[(a / S) * rs + (a % S)];
+    const float ur = ca.x - ir, ug = ca.y - ig, ub = ca.z - ib;
+    const float da = sqrt_approx(bd);
+    SearchOut o;
+    o.ka = a;
+    if (gnu) {  // weight fixed to 1: T_hat = T_a
+        o.kb = a;
+        o.omega = 1.0f;
+        o.err = da * (1.0f / 255.0f);
+        return o;
+    }
+    // Step 2: fix a; for every b (b = a included) the Eq. 5 weight w = d_b / (d_a + d_b + eps)
+    // and the Eq. 3 residual r = w u + (1 - w) v with u = L_a - I, v = L_b - I. The comparison
+    // uses D * r = d_b u + (d_a + eps) v and D = d_a + d_b + eps: err^2 = |D r|^2 / D^2,
+    // compared by cross-multiplication so no candidate needs a division.
+    const float dae = da + eps255;
+    float bnum = kInf, bden = 1.0f, bdb = 0.0f;
+    int b = a;
+#pragma unroll(S <= 5 ? S : 1)
+    for (int dy = 0; dy < S; ++dy) {
+#pragma unroll
+        for (int dx = 0; dx < S; ++dx) {
+            const bool ok = ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
+            const float4 c = win[dy * rs + dx];
+            const float vr = c.x - ir, vg = c.y - ig, vb = c.z - ib;
+            const float db = sqrt_approx(dist2(vr, vg, vb));
+            const float xr = __fmaf_rn(db, ur, __fmul_rn(dae, vr));
+            const float xg = __fmaf_rn(db, ug, __fmul_rn(dae, vg));
+            const float xb = __fmaf_rn(db, ub, __fmul_rn(dae, vb));
+            const float num = dist2(xr, xg, xb);
+            const float D = __fadd_rn(db, dae);
+            const float den = fmaxf(__fmul_rn(D, D), 1e-30f);
+            if (ok && __fmul_rn(num, bden) < __fmul_rn(bnum, den)) {
+                bnum = num;
+                bden = den;
+                bdb = db;
+                b = dy * S + dx;
+            }
+        }
+    }
+    o.kb = b;
+    const float wden = bdb + dae;
+    o.omega = wden > 0.0f ? bdb / wden : 1.0f;
+    o.err = sqrtf(bnum / bden) * (1.0f / 255.0f);
+    return o;
+}
+
+// Row/column validity masks of the window centred on LR block (py, px) of an h x w LR image.
+__device__ __forceinline__ void window_masks(int py, int px, int h, int w, int S,
+                                             uint32_t& rowmask, uint32_t& colmask) {
+    const int r = (S - 1) >> 1;
+    rowmask = 0u;
+    colmask = 0u;
+    for (int i = 0; i < S; ++i) {
+        const int v = py - r + i, u = px - r + i;
+        rowmask |= (uint32_t)(v >= 0 && v < h) << i;
+        colmask |= (uint32_t)(u >= 0 && u < w) << i;
+    }
+}
+
+}  // namespace glu

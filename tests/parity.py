@@ -1,0 +1,76 @@
+"""Comparison helpers for GPU-vs-oracle parity (used by the gpu tests and the smoke check).
+
+Rules (from the accuracy targets of the hot path):
+  * pair codes identical, except at near-tie pixels where the oracle's best and second-best
+    candidates (of different colour) are closer than 1e-5; there the GPU's pair must still be
+    a valid optimum: its a within 1e-5 of the nearest distance, and its FP64 error within 1e-5
+    of the best error achievable with that a (Algorithm 1's second step);
+  * weights within 1e-4 (float32 storage), 2.5e-4 (float16), 1e-5 (unorm16) where codes match;
+  * error map within 1e-5; reconstructions within 1e-3 max-abs on [0, 1] colours.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import oracle as O
+
+NEAR_TIE = 1e-5
+W_TOL = {0: 1e-4, 1: 2.5e-4, 2: 1e-5}
+
+
+def check_search(I, L, s, S, theta, err_gpu=None, eps=1e-3, wfmt=0, ref=None, gnu=False):
+    """Compare a GPU Theta (and error map) with the oracle on the same I and L. Returns a
+    report dict; raises AssertionError on a parity failure."""
+    K = S * S
+    if ref is None:
+        ref = O.glu_fast(I, L, s, S, eps=eps, gaps=True)
+    codes = theta.codes_i32().cpu().numpy()
+    ka, kb = codes // K, codes % K
+    if gnu:
+        g = O.glu_gnu(I, L, s, S)
+        assert np.array_equal(ka, kb)
+        tie = ref["gap_a"] < NEAR_TIE
+        mism = ka != g["ka"]
+        assert not (mism & ~tie).any(), f"{int((mism & ~tie).sum())} GNU codes differ"
+        w = theta.weight_f32().cpu().numpy()
+        assert np.all(w == 1.0)
+        if err_gpu is not None:
+            e = err_gpu.cpu().numpy()
+            assert np.abs(e - g["err"])[~mism].max() < 1e-5
+        return dict(near_ties=int(tie.sum()), mismatches=int(mism.sum()))
+    tie = (ref["gap_a"] < NEAR_TIE) | (ref["gap_b"] < NEAR_TIE)
+    same = (ka == ref["ka"]) & (kb == ref["kb"])
+    bad = ~same & ~tie
+    assert not bad.any(), (f"{int(bad.sum())} pair codes differ away from near-ties, e.g. at "
+                           f"{np.argwhere(bad)[:5].tolist()}")
+    # mismatches at near-ties: the GPU's pair must be a valid optimum within the tolerance
+    Iu, Lu = O.to_unit(I), O.to_unit(L)
+    H, W = codes.shape
+    h, w = Lu.shape[:2]
+    r = (S - 1) // 2
+    for (y, x) in np.argwhere(~same)[:5000]:
+        ga, gb = int(ka[y, x]), int(kb[y, x])
+        py, px = y // s, x // s
+        valid = [k for k in range(K) if 0 <= py + k // S - r < h and 0 <= px + k % S - r < w]
+        d = {k: np.linalg.norm(Iu[y, x] - Lu[py + k // S - r, px + k % S - r]) for k in valid}
+        assert d[ga] <= min(d.values()) + NEAR_TIE
+        errs = [O.fast_pair(Iu, Lu, s, S, y, x, ga, k, eps)[1] for k in valid]
+        _, e_gpu_pair = O.fast_pair(Iu, Lu, s, S, y, x, ga, gb, eps)
+        assert e_gpu_pair <= min(errs) + NEAR_TIE
+    wg = theta.weight_f32().cpu().numpy()
+    dw = np.abs(wg - ref["omega"])[same]
+    assert dw.max(initial=0.0) < W_TOL[wfmt], f"weight error {dw.max()}"
+    rep = dict(near_ties=int(tie.sum()), mismatches=int((~same).sum()),
+               max_dw=float(dw.max(initial=0.0)))
+    if err_gpu is not None:
+        e = err_gpu.cpu().numpy().astype(np.float64)
+        de = np.abs(e - ref["err"])[same]
+        assert de.max(initial=0.0) < 1e-5, f"error-map difference {de.max()}"
+        rep["max_derr"] = float(de.max(initial=0.0))
+    return rep
+
+
+def lr_like_gpu(lr_tensor):
+    """The LR image the GPU used, as a numpy array in its own dtype (uint8 or float)."""
+    a = lr_tensor.cpu().numpy()
+    return a if a.dtype == np.uint8 else a.astype(np.float64)

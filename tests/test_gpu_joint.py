@@ -1,0 +1,125 @@
+"""Algorithm 2 on the GPU against the FP64 oracle (needs a GB300)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from tests.parity import check_search  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_09582_gb300 import api as A
+    return A
+
+
+def run_both(api, img, s, S, N, strict, conn=8):
+    hr = torch.from_numpy(img).cuda()
+    p = api.glu_params(S=S, N=N, joint=api.GLU_JOINT_STRICT if strict else api.GLU_JOINT_PAPER,
+                       connectivity=conn)
+    lr, theta, err, st = api.glu_joint_optimize(hr, s, p)
+    torch.cuda.synchronize()
+    assert api.glu_device_status() == 0
+    ref = O.joint(img, s, S, N=N, strict=strict, conn=conn)
+    return hr, lr, theta, err, st, ref
+
+
+def compare(api, img, s, S, N, strict, lr, theta, err, st, ref):
+    """Decisions and final state equal the oracle's (given safe decision margins)."""
+    margins_ok = all((it["min_decision_margin"] == 0.0 or it["min_decision_margin"] > 1e-5)
+                     and it["min_threshold_margin"] > 1e-6 for it in ref["iters"])
+    gi = st["iters"]
+    ri = [it for it in ref["iters"] if it["n_large"] > 0]
+    msg = f"\ngpu {gi}\nref {ri}"
+    assert st["R0"] == pytest.approx(ref["R0"], rel=1e-6), msg
+    if not margins_ok:
+        pytest.skip("oracle reports a decision within FP32 resolution; exact replay not expected")
+    assert len(gi) == len(ri), msg
+    for g, r in zip(gi, ri):
+        assert (g["n_large"], g["M"], g["accepted"], g["rolled_back"]) == \
+               (r["n_large"], r["M"], r["accepted"], r["rolled_back"]), msg
+        assert g["residual"] == pytest.approx(r["residual"], rel=1e-6), msg
+    Lg = lr.cpu().numpy()
+    Lr = np.rint(ref["L"] * 255).astype(np.uint8)
+    assert np.array_equal(Lg, Lr), f"{int((Lg != Lr).any(axis=2).sum())} LR pixels differ"
+    if strict:
+        # STRICT keeps Theta = Algorithm 1 on the final LR image: check it as a plain search
+        return check_search(img, Lg, s, S, theta, err)
+    K = S * S
+    codes = theta.codes_i32().cpu().numpy()
+    same = (codes // K == ref["ka"]) & (codes % K == ref["kb"])
+    assert (~same).mean() < 1e-3
+    e = err.cpu().numpy()
+    assert np.abs(e - ref["err"])[same].max() < 1e-5
+    return dict(mismatches=int((~same).sum()))
+
+
+@pytest.mark.parametrize("H,W,s,S,strict", [
+    (128, 160, 4, 3, True), (128, 160, 4, 3, False),
+    (200, 264, 8, 5, True), (200, 264, 8, 5, False),
+    (97, 131, 3, 3, True), (150, 100, 16, 5, True), (120, 120, 4, 1, True),
+])
+def test_joint_matches_oracle(api, H, W, s, S, strict):
+    from paper_2307_09582_gb300.inputs import Scene, render_u8
+    img = render_u8(Scene(width=W, height=H, n_cells=40, n_dots=60, n_lines=6, seed=H + W + S))
+    hr, lr, theta, err, st, ref = run_both(api, img, s, S, N=4, strict=strict)
+    rep = compare(api, img, s, S, 4, strict, lr, theta, err, st, ref)
+    print(f"\njoint {H}x{W} s={s} S={S} strict={strict}: {st['iters']} {rep}")
+
+
+def test_joint_4connectivity(api):
+    from paper_2307_09582_gb300.inputs import Scene, render_u8
+    img = render_u8(Scene(width=180, height=140, n_cells=30, n_dots=50, n_lines=8, seed=77))
+    hr, lr, theta, err, st, ref = run_both(api, img, 4, 3, N=3, strict=True, conn=4)
+    compare(api, img, 4, 3, 3, True, lr, theta, err, st, ref)
+
+
+def test_joint_strict_invariants_and_determinism(api):
+    from paper_2307_09582_gb300.inputs import Scene, render_u8
+    img = render_u8(Scene(width=320, height=240, n_cells=50, n_dots=120, n_lines=10, seed=5))
+    s, S = 8, 5
+    hr = torch.from_numpy(img).cuda()
+    p = api.glu_params(S=S, N=5)
+    lr1, t1, e1, st1 = api.glu_joint_optimize(hr, s, p)
+    lr2, t2, e2, st2 = api.glu_joint_optimize(hr, s, p)
+    torch.cuda.synchronize()
+    assert torch.equal(lr1, lr2) and torch.equal(t1.code, t2.code) and torch.equal(e1, e2)
+    # Theta / E equal a fresh Algorithm 1 on the final LR image, bit for bit
+    t3, e3 = api.glu_optimize(hr, lr1, api.glu_params(S=S), s, err_map=True)
+    torch.cuda.synchronize()
+    assert torch.equal(t3.code, t1.code) and torch.equal(t3.weight, t1.weight)
+    assert torch.equal(e3, e1)
+    R = [st1["R0"]] + [it["residual"] for it in st1["iters"]]
+    assert all(b <= a for a, b in zip(R, R[1:]))
+    assert e1.double().sum().item() == pytest.approx(R[-1], rel=1e-9)
+    # every LR pixel is one HR pixel of its own block
+    L = lr1.cpu().numpy()
+    for v in range(L.shape[0]):
+        for u in range(L.shape[1]):
+            blk = img[v * s:(v + 1) * s, u * s:(u + 1) * s].reshape(-1, 3)
+            assert np.any(np.all(blk == L[v, u], axis=1))
+
+
+def test_joint_flat_image_no_large_error(api):
+    img = np.full((64, 96, 3), 77, np.uint8)
+    hr = torch.from_numpy(img).cuda()
+    lr, theta, err, st = api.glu_joint_optimize(hr, 4, api.glu_params(S=3, N=3))
+    torch.cuda.synchronize()
+    assert st["iterations"] == 0 and st["n_large_next"] == 0
+    assert float(err.abs().max()) == 0.0
+
+
+def test_joint_4k_workload_full_parity(api):
+    # the 3840x2160 joint workload at full size: scale 8, 5x5 window, 5 iterations
+    from paper_2307_09582_gb300.inputs import joint_4k_scene, render_u8
+    img = render_u8(joint_4k_scene())
+    hr, lr, theta, err, st, ref = run_both(api, img, 8, 5, N=5, strict=True)
+    rep = compare(api, img, 8, 5, 5, True, lr, theta, err, st, ref)
+    print(f"\njoint 4K: {st['iters']} {rep}")

@@ -127,7 +127,7 @@ def oracle_pipeline_sample(img, rows: int):
     crop = img[:rows]
     t0 = time.perf_counter()
     j = O.joint(crop, SCALE, WIN, N=NITER, strict=True)
-    T = O.op_saturation(O.op_box3(j["L"]), 1.3)
+    T = O.op_saturation(O.op_box3(O.to_unit(j["L"])), 1.3)
     _ = O.apply(j["ka"], j["kb"], j["omega"], SCALE, WIN, T)
     return crop.shape[0] * crop.shape[1], time.perf_counter() - t0
 

@@ -10,8 +10,12 @@
  * on many host cores; the component loop of Algorithm 2 is sequential, as the paper writes it.
  *
  * Conventions (readings of points the paper leaves open):
- *  - Images are row-major H x W x C doubles, colours in [0, 1] (uint8 value / 255), so that the
- *    paper's tau = 30/255 and eps = 1e-3 (Sec. 3.1, Sec. 5.3) are in the same units.
+ *  - Images are row-major H x W x C doubles in the caller's colour units: `unit` is the value of
+ *    colour 1.0 (255 for raw uint8 values, 1 for colours already in [0, 1]). The paper's
+ *    tau = 30/255 and eps = 1e-3 (Sec. 3.1, Sec. 5.3) are given in [0, 1] units and scaled here
+ *    (eps of Eq. 5 and tau by unit, eps of Eq. 4 by unit^2, being a squared-colour term);
+ *    errors are returned in [0, 1] units. Working on raw uint8 values keeps every squared
+ *    distance an exact integer, so exact ties stay exact and go to the lowest window index.
  *  - ||.|| is the Euclidean norm over the colour channels.
  *  - Scale s: LR size h = ceil(H / s), w = ceil(W / s). The downscaled coordinate of HR pixel
  *    (y, x) is p_down = (floor(y / s), floor(x / s)), i.e. the LR block that contains it (Eq. 1).
@@ -210,11 +214,13 @@ static int check_common(const double* I, int H, int W, const double* L, int s, i
 }
 
 int oracle_glu_fast(const double* I, int H, int W, const double* L, int s, int S, double eps,
-                    int32_t* ka, int32_t* kb, double* omega, double* err, double* gap_a,
-                    double* gap_b, int threads) {
-    if (check_common(I, H, W, L, s, S) || !ka || !kb || !omega || !err) return OR_EINVAL;
+                    double unit, int32_t* ka, int32_t* kb, double* omega, double* err,
+                    double* gap_a, double* gap_b, int threads) {
+    if (check_common(I, H, W, L, s, S) || !ka || !kb || !omega || !err || !(unit > 0.0))
+        return OR_EINVAL;
     int h, w;
     oracle_lr_dims(H, W, s, &h, &w);
+    eps *= unit;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 4) num_threads(threads > 0 ? threads : omp_get_max_threads())
 #endif
@@ -223,6 +229,9 @@ int oracle_glu_fast(const double* I, int H, int W, const double* L, int s, int S
             size_t p = (size_t)y * W + x;
             fast_pixel(I, H, W, L, h, w, s, S, eps, y, x, &ka[p], &kb[p], &omega[p], &err[p],
                        gap_a ? &gap_a[p] : NULL, gap_b ? &gap_b[p] : NULL);
+            err[p] /= unit;
+            if (gap_a) gap_a[p] /= unit;
+            if (gap_b) gap_b[p] /= unit;
         }
     (void)threads;
     return OR_OK;
@@ -230,8 +239,9 @@ int oracle_glu_fast(const double* I, int H, int W, const double* L, int s, int S
 
 /* Evaluate a given window pair (k_a, k_b) at HR pixel (y, x) with the Eq. 5 weight. */
 int oracle_fast_pair(const double* I, int H, int W, const double* L, int s, int S, double eps,
-                     int y, int x, int ka, int kb, double* omega, double* err) {
-    if (check_common(I, H, W, L, s, S) || y < 0 || y >= H || x < 0 || x >= W) return OR_EINVAL;
+                     double unit, int y, int x, int ka, int kb, double* omega, double* err) {
+    if (check_common(I, H, W, L, s, S) || y < 0 || y >= H || x < 0 || x >= W || !(unit > 0.0))
+        return OR_EINVAL;
     int h, w, r = (S - 1) / 2;
     oracle_lr_dims(H, W, s, &h, &w);
     int va = y / s + ka / S - r, ua = x / s + ka % S - r;
@@ -239,16 +249,20 @@ int oracle_fast_pair(const double* I, int H, int W, const double* L, int s, int 
     if (va < 0 || va >= h || ua < 0 || ua >= w || vb < 0 || vb >= h || ub < 0 || ub >= w)
         return OR_EINVAL;
     fast_pair_eval(&I[((size_t)y * W + x) * 3], &L[((size_t)va * w + ua) * 3],
-                   &L[((size_t)vb * w + ub) * 3], eps, omega, err);
+                   &L[((size_t)vb * w + ub) * 3], eps * unit, omega, err);
+    *err /= unit;
     return OR_OK;
 }
 
 /* GLU* of Sec. 3.1: exhaustive pairs with the least-squares weight of Eq. 4. */
 int oracle_glu_exact(const double* I, int H, int W, const double* L, int s, int S, double eps,
-                     int32_t* ka, int32_t* kb, double* omega, double* err, int threads) {
-    if (check_common(I, H, W, L, s, S) || !ka || !kb || !omega || !err) return OR_EINVAL;
+                     double unit, int32_t* ka, int32_t* kb, double* omega, double* err,
+                     int threads) {
+    if (check_common(I, H, W, L, s, S) || !ka || !kb || !omega || !err || !(unit > 0.0))
+        return OR_EINVAL;
     int h, w;
     oracle_lr_dims(H, W, s, &h, &w);
+    eps *= unit * unit;  /* Eq. 4's eps adds to a squared colour distance */
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 4) num_threads(threads > 0 ? threads : omp_get_max_threads())
 #endif
@@ -261,7 +275,7 @@ int oracle_glu_exact(const double* I, int H, int W, const double* L, int s, int 
             if (win.n == 1) {
                 ka[p] = kb[p] = win.k[0];
                 omega[p] = 1.0;
-                err[p] = dist3(Ip, win.col[0]);
+                err[p] = dist3(Ip, win.col[0]) / unit;
                 continue;
             }
             double best = INFINITY, bom = 1.0;
@@ -275,16 +289,16 @@ int oracle_glu_exact(const double* I, int H, int W, const double* L, int s, int 
             ka[p] = win.k[ba];
             kb[p] = win.k[bb];
             omega[p] = bom;
-            err[p] = best;
+            err[p] = best / unit;
         }
     (void)threads;
     return OR_OK;
 }
 
 /* GNU: weight fixed to 1 (Sec. 3.2), so the reconstruction is the nearest-colour LR pixel. */
-int oracle_glu_gnu(const double* I, int H, int W, const double* L, int s, int S, int32_t* ka,
-                   double* err) {
-    if (check_common(I, H, W, L, s, S) || !ka || !err) return OR_EINVAL;
+int oracle_glu_gnu(const double* I, int H, int W, const double* L, int s, int S, double unit,
+                   int32_t* ka, double* err) {
+    if (check_common(I, H, W, L, s, S) || !ka || !err || !(unit > 0.0)) return OR_EINVAL;
     int h, w;
     oracle_lr_dims(H, W, s, &h, &w);
     for (int y = 0; y < H; ++y)
@@ -299,7 +313,7 @@ int oracle_glu_gnu(const double* I, int H, int W, const double* L, int s, int S,
                 if (d < da) { da = d; ia = i; }
             }
             ka[p] = win.k[ia];
-            err[p] = da;
+            err[p] = da / unit;
         }
     return OR_OK;
 }
@@ -397,19 +411,32 @@ int oracle_label_components(const uint8_t* mask, int H, int W, int conn, int32_t
  */
 #define JSTAT 8
 
-int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double tau, int N,
-                 int strict, int conn, double* L, int32_t* ka, int32_t* kb, double* omega,
-                 double* err, double* stats, int8_t* accept_log, int64_t log_cap, int threads) {
+int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double tau,
+                 double unit, int N, int strict, int conn, double* L, int32_t* ka, int32_t* kb,
+                 double* omega, double* err, double* stats, int8_t* accept_log, int64_t log_cap,
+                 int threads) {
     if (!I || !L || !ka || !kb || !omega || !err || H <= 0 || W <= 0 || s <= 0 || S < 1 ||
-        S > 9 || (S % 2) == 0 || N < 0 || (conn != 4 && conn != 8))
+        S > 9 || (S % 2) == 0 || N < 0 || (conn != 4 && conn != 8) || !(unit > 0.0))
         return OR_EINVAL;
+    /* E, e0, e1 and the residual are kept in the caller's units internally (err is converted
+     * to [0, 1] units on return); tau is compared in the same units */
+    tau *= unit;
     int h, w, r = (S - 1) / 2;
     oracle_lr_dims(H, W, s, &h, &w);
     size_t n = (size_t)H * W, nl = (size_t)h * w;
 
     /* initialise the LR image by regular grid downsampling, then Theta and E by Algorithm 1 */
+    eps *= unit;
     oracle_downsample_grid(I, H, W, 3, s, L);
-    oracle_glu_fast(I, H, W, L, s, S, eps, ka, kb, omega, err, NULL, NULL, threads);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(threads > 0 ? threads : omp_get_max_threads())
+#endif
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            fast_pixel(I, H, W, L, h, w, s, S, eps, y, x, &ka[p], &kb[p], &omega[p], &err[p],
+                       NULL, NULL);
+        }
 
     uint8_t* mask = (uint8_t*)malloc(n);
     int32_t* lab = (int32_t*)malloc(sizeof(int32_t) * n);
@@ -435,7 +462,7 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
 
     double R_prev = 0.0;
     for (size_t p = 0; p < n; ++p) R_prev += err[p];
-    if (stats) stats[0] = R_prev;
+    if (stats) stats[0] = R_prev / unit;
     int64_t nlog = 0;
     int32_t stamp = 0;
 
@@ -453,7 +480,7 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
         if (st) {
             for (int j = 0; j < JSTAT; ++j) st[j] = 0.0;
             st[0] = (double)nlarge;
-            st[6] = thr_margin;
+            st[6] = thr_margin / unit;
         }
         if (nlarge == 0) break;
         int M = oracle_label_components(mask, H, W, conn, lab);
@@ -563,12 +590,14 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
         double R = 0.0;
         for (size_t p = 0; p < n; ++p) R += err[p];
         if (st) {
-            st[1] = M; st[2] = accepted; st[3] = rolled; st[4] = R; st[5] = min_dec; st[7] = searched;
+            st[1] = M; st[2] = accepted; st[3] = rolled; st[4] = R / unit; st[5] = min_dec / unit;
+            st[7] = searched;
         }
         if (accepted == 0 || !(R < R_prev)) break;
         R_prev = R;
     }
 done:
+    for (size_t p = 0; p < n; ++p) err[p] /= unit;
     free(mask); free(lab); free(order); free(cstart); free(lr_stamp); free(lr_list); free(aff);
     free(backup); free(tka); free(tkb); free(tom); free(ter); free(qval); free(qbest);
     return rc;

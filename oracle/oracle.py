@@ -1,7 +1,11 @@
 """numpy/ctypes front end of the FP64 C oracle (glu_oracle.c).
 
-Test infrastructure: converts inputs to float64 colours in [0, 1] (uint8 / 255) and calls the
-plain C routines, each of which follows one equation or algorithm of the paper:
+Test infrastructure. Colour units: when any image of a call is uint8, all images of the call are
+passed to C in raw 0..255 units (floats in [0, 1] are scaled by 255), so squared distances
+between uint8 colours are exact integers and exact ties stay exact; otherwise colours are in
+[0, 1]. eps and tau are always given in [0, 1] units and errors are returned in [0, 1] units.
+Grid downsampling and Algorithm 2 return uint8 LR images for uint8 guides (their pixels are
+copies of guide pixels). Each C routine follows one equation or algorithm of the paper:
   downsample_grid / downsample_box   regular grid (Sec. 3.3) and block-mean downsampling
   glu_fast                           Algorithm 1 with the Eq. 5 weight and the Eq. 3 error
   glu_exact                          GLU* of Sec. 3.1, all pairs with the Eq. 4 weight
@@ -32,15 +36,15 @@ def _lib():
         sig = {
             "oracle_downsample_grid": [_p, _i, _i, _i, _i, _p],
             "oracle_downsample_box": [_p, _i, _i, _i, _i, _p],
-            "oracle_glu_fast": [_p, _i, _i, _p, _i, _i, _d, _p, _p, _p, _p, _p, _p, _i],
-            "oracle_fast_pair": [_p, _i, _i, _p, _i, _i, _d, _i, _i, _i, _i, _p, _p],
-            "oracle_glu_exact": [_p, _i, _i, _p, _i, _i, _d, _p, _p, _p, _p, _i],
-            "oracle_glu_gnu": [_p, _i, _i, _p, _i, _i, _p, _p],
+            "oracle_glu_fast": [_p, _i, _i, _p, _i, _i, _d, _d, _p, _p, _p, _p, _p, _p, _i],
+            "oracle_fast_pair": [_p, _i, _i, _p, _i, _i, _d, _d, _i, _i, _i, _i, _p, _p],
+            "oracle_glu_exact": [_p, _i, _i, _p, _i, _i, _d, _d, _p, _p, _p, _p, _i],
+            "oracle_glu_gnu": [_p, _i, _i, _p, _i, _i, _d, _p, _p],
             "oracle_apply": [_p, _p, _p, _i, _i, _i, _i, _p, _i, _p],
             "oracle_apply_adjoint": [_p, _p, _p, _i, _i, _i, _i, _p, _i, _p, _p, _p],
             "oracle_label_components": [_p, _i, _i, _i, _p],
-            "oracle_joint": [_p, _i, _i, _i, _i, _d, _d, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p,
-                             ctypes.c_int64, _i],
+            "oracle_joint": [_p, _i, _i, _i, _i, _d, _d, _d, _i, _i, _i, _p, _p, _p, _p, _p, _p,
+                             _p, ctypes.c_int64, _i],
             "oracle_op_box3": [_p, _i, _i, _i, _p],
             "oracle_op_gauss3": [_p, _i, _i, _i, _p],
             "oracle_op_saturation": [_p, ctypes.c_size_t, _d, _p],
@@ -74,32 +78,49 @@ def to_unit(img) -> np.ndarray:
     return np.ascontiguousarray(a.astype(np.float64))
 
 
+def colours(*imgs):
+    """The images of one call in common units: raw 0..255 if any of them is uint8 (floats in
+    [0, 1] scaled by 255), else [0, 1]. Returns ([float64 arrays], unit)."""
+    arrs = [np.asarray(a) for a in imgs]
+    unit = 255.0 if any(a.dtype == np.uint8 for a in arrs) else 1.0
+    out = []
+    for a in arrs:
+        f = np.ascontiguousarray(a, dtype=np.float64)
+        if a.dtype != np.uint8 and unit != 1.0:
+            f = f * unit
+        out.append(f)
+    return out, unit
+
+
 def lr_dims(H, W, s):
     return (H + s - 1) // s, (W + s - 1) // s
 
 
 def downsample_grid(I, s):
-    I = to_unit(I)
-    H, W, C = I.shape
+    """Regular grid downsampling; uint8 in -> uint8 out (exact copies), floats stay floats."""
+    a = np.asarray(I)
+    F = np.ascontiguousarray(a, dtype=np.float64)
+    H, W, C = F.shape
     h, w = lr_dims(H, W, s)
     L = np.empty((h, w, C), np.float64)
-    _chk(_lib().oracle_downsample_grid(_ptr(I), H, W, C, s, _ptr(L)), "downsample_grid")
-    return L
+    _chk(_lib().oracle_downsample_grid(_ptr(F), H, W, C, s, _ptr(L)), "downsample_grid")
+    return L.astype(np.uint8) if a.dtype == np.uint8 else L
 
 
 def downsample_box(I, s):
-    I = to_unit(I)
-    H, W, C = I.shape
+    """Block mean, returned as float64 colours in [0, 1]."""
+    a = np.asarray(I)
+    F = np.ascontiguousarray(a, dtype=np.float64)
+    H, W, C = F.shape
     h, w = lr_dims(H, W, s)
     L = np.empty((h, w, C), np.float64)
-    _chk(_lib().oracle_downsample_box(_ptr(I), H, W, C, s, _ptr(L)), "downsample_box")
-    return L
+    _chk(_lib().oracle_downsample_box(_ptr(F), H, W, C, s, _ptr(L)), "downsample_box")
+    return L / 255.0 if a.dtype == np.uint8 else L
 
 
 def glu_fast(I, L, s, S, eps=1e-3, gaps=False, threads=0):
     """Algorithm 1 on every HR pixel: returns dict(ka, kb, omega, err[, gap_a, gap_b])."""
-    I = to_unit(I)
-    L = to_unit(L)
+    (I, L), unit = colours(I, L)
     H, W, _ = I.shape
     out = {k: np.empty((H, W), np.int32) for k in ("ka", "kb")}
     out["omega"] = np.empty((H, W), np.float64)
@@ -107,45 +128,46 @@ def glu_fast(I, L, s, S, eps=1e-3, gaps=False, threads=0):
     if gaps:
         out["gap_a"] = np.empty((H, W), np.float64)
         out["gap_b"] = np.empty((H, W), np.float64)
-    _chk(_lib().oracle_glu_fast(_ptr(I), H, W, _ptr(L), s, S, eps, _ptr(out["ka"]),
+    _chk(_lib().oracle_glu_fast(_ptr(I), H, W, _ptr(L), s, S, eps, unit, _ptr(out["ka"]),
                                 _ptr(out["kb"]), _ptr(out["omega"]), _ptr(out["err"]),
                                 _ptr(out.get("gap_a")), _ptr(out.get("gap_b")), threads),
          "glu_fast")
     return out
 
 
-def fast_pair(I, L, s, S, y, x, ka, kb, eps=1e-3):
-    """Eq. 5 weight and Eq. 3 error of a given window pair at HR pixel (y, x)."""
-    I = to_unit(I)
-    L = to_unit(L)
+def fast_pair(I, L, s, S, y, x, ka, kb, eps=1e-3, unit=None):
+    """Eq. 5 weight and Eq. 3 error of a given window pair at HR pixel (y, x). With `unit`
+    given, I and L must already be contiguous float64 in those units (see colours())."""
+    if unit is None:
+        (I, L), unit = colours(I, L)
     H, W, _ = I.shape
     om = ctypes.c_double()
     er = ctypes.c_double()
-    _chk(_lib().oracle_fast_pair(_ptr(I), H, W, _ptr(L), s, S, eps, int(y), int(x), int(ka),
-                                 int(kb), ctypes.byref(om), ctypes.byref(er)), "fast_pair")
+    _chk(_lib().oracle_fast_pair(_ptr(I), H, W, _ptr(L), s, S, eps, unit, int(y), int(x),
+                                 int(ka), int(kb), ctypes.byref(om), ctypes.byref(er)),
+         "fast_pair")
     return om.value, er.value
 
 
 def glu_exact(I, L, s, S, eps=1e-3, threads=0):
-    I = to_unit(I)
-    L = to_unit(L)
+    (I, L), unit = colours(I, L)
     H, W, _ = I.shape
     out = {k: np.empty((H, W), np.int32) for k in ("ka", "kb")}
     out["omega"] = np.empty((H, W), np.float64)
     out["err"] = np.empty((H, W), np.float64)
-    _chk(_lib().oracle_glu_exact(_ptr(I), H, W, _ptr(L), s, S, eps, _ptr(out["ka"]),
+    _chk(_lib().oracle_glu_exact(_ptr(I), H, W, _ptr(L), s, S, eps, unit, _ptr(out["ka"]),
                                  _ptr(out["kb"]), _ptr(out["omega"]), _ptr(out["err"]), threads),
          "glu_exact")
     return out
 
 
 def glu_gnu(I, L, s, S):
-    I = to_unit(I)
-    L = to_unit(L)
+    (I, L), unit = colours(I, L)
     H, W, _ = I.shape
     ka = np.empty((H, W), np.int32)
     err = np.empty((H, W), np.float64)
-    _chk(_lib().oracle_glu_gnu(_ptr(I), H, W, _ptr(L), s, S, _ptr(ka), _ptr(err)), "glu_gnu")
+    _chk(_lib().oracle_glu_gnu(_ptr(I), H, W, _ptr(L), s, S, unit, _ptr(ka), _ptr(err)),
+         "glu_gnu")
     return {"ka": ka, "err": err}
 
 
@@ -191,8 +213,10 @@ JSTAT = 8
 
 def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap=1 << 20,
           threads=0):
-    """Algorithm 2. Returns dict(L, ka, kb, omega, err, R0, iters=[...], accept_log)."""
-    I = to_unit(I)
+    """Algorithm 2. Returns dict(L, ka, kb, omega, err, R0, iters=[...], accept_log); L is
+    uint8 for a uint8 guide."""
+    is_u8 = np.asarray(I).dtype == np.uint8
+    (I,), unit = colours(I)
     H, W, _ = I.shape
     h, w = lr_dims(H, W, s)
     L = np.empty((h, w, 3), np.float64)
@@ -202,7 +226,8 @@ def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap
     er = np.empty((H, W), np.float64)
     stats = np.full(1 + JSTAT * max(N, 1), np.nan)
     log = np.full(log_cap, -1, np.int8)
-    _chk(_lib().oracle_joint(_ptr(I), H, W, s, S, eps, tau, N, int(bool(strict)), conn, _ptr(L),
+    _chk(_lib().oracle_joint(_ptr(I), H, W, s, S, eps, tau, unit, N, int(bool(strict)), conn,
+                             _ptr(L),
                              _ptr(ka), _ptr(kb), _ptr(om), _ptr(er), _ptr(stats), _ptr(log),
                              log_cap, threads), "joint")
     iters = []
@@ -217,6 +242,8 @@ def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap
         if st[0] == 0:
             break
     nlog = sum(it["M"] for it in iters)
+    if is_u8:
+        L = L.astype(np.uint8)
     return dict(L=L, ka=ka, kb=kb, omega=om, err=er, R0=float(stats[0]), iters=iters,
                 accept_log=log[:min(nlog, log_cap)].copy())
 

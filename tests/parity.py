@@ -44,18 +44,19 @@ def check_search(I, L, s, S, theta, err_gpu=None, eps=1e-3, wfmt=0, ref=None, gn
     assert not bad.any(), (f"{int(bad.sum())} pair codes differ away from near-ties, e.g. at "
                            f"{np.argwhere(bad)[:5].tolist()}")
     # mismatches at near-ties: the GPU's pair must be a valid optimum within the tolerance
-    Iu, Lu = O.to_unit(I), O.to_unit(L)
+    (Ic, Lc), unit = O.colours(I, L)
     H, W = codes.shape
-    h, w = Lu.shape[:2]
+    h, w = Lc.shape[:2]
     r = (S - 1) // 2
     for (y, x) in np.argwhere(~same)[:5000]:
         ga, gb = int(ka[y, x]), int(kb[y, x])
         py, px = y // s, x // s
         valid = [k for k in range(K) if 0 <= py + k // S - r < h and 0 <= px + k % S - r < w]
-        d = {k: np.linalg.norm(Iu[y, x] - Lu[py + k // S - r, px + k % S - r]) for k in valid}
+        d = {k: np.linalg.norm(Ic[y, x] - Lc[py + k // S - r, px + k % S - r]) / unit
+             for k in valid}
         assert d[ga] <= min(d.values()) + NEAR_TIE
-        errs = [O.fast_pair(Iu, Lu, s, S, y, x, ga, k, eps)[1] for k in valid]
-        _, e_gpu_pair = O.fast_pair(Iu, Lu, s, S, y, x, ga, gb, eps)
+        errs = [O.fast_pair(Ic, Lc, s, S, y, x, ga, k, eps, unit=unit)[1] for k in valid]
+        _, e_gpu_pair = O.fast_pair(Ic, Lc, s, S, y, x, ga, gb, eps, unit=unit)
         assert e_gpu_pair <= min(errs) + NEAR_TIE
     wg = theta.weight_f32().cpu().numpy()
     dw = np.abs(wg - ref["omega"])[same]

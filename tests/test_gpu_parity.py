@@ -36,7 +36,7 @@ def test_downsample_grid_exact_and_box(api, H, W, s):
     img = scene_img(3, H, W)
     hr = dev(img)
     lr = api.glu_downsample(hr, s, api.GLU_DOWN_GRID)
-    assert np.array_equal(lr.cpu().numpy(), np.rint(O.downsample_grid(img, s) * 255).astype(np.uint8))
+    assert np.array_equal(lr.cpu().numpy(), O.downsample_grid(img, s))
     lb = api.glu_downsample(hr, s, api.GLU_DOWN_BOX)
     assert np.abs(lb.cpu().numpy() - O.downsample_box(img, s)).max() < 1e-6
     # f16 input, f32 output grid

@@ -202,11 +202,14 @@ def test_exact_representability(rng, s, S):
     Lu8 = rand_img(rng, h, w)
     I = np.repeat(np.repeat(Lu8, s, axis=0), s, axis=1)
     L = O.downsample_grid(I, s)
-    assert np.array_equal(L, O.to_unit(Lu8))
+    assert L.dtype == np.uint8 and np.array_equal(L, Lu8)
     fa = O.glu_fast(I, L, s, S)
     assert np.all(fa["err"] == 0.0)
-    out = O.apply(fa["ka"], fa["kb"], fa["omega"], s, S, L)
+    out = O.apply(fa["ka"], fa["kb"], fa["omega"], s, S, O.to_unit(L))
     assert np.allclose(out, O.to_unit(I), atol=1e-15)
+    # the same holds for colours given in [0, 1] floats
+    fb = O.glu_fast(O.to_unit(I), O.to_unit(L), s, S)
+    assert np.all(fb["err"] == 0.0)
 
 
 # ------------------------------------------------------------------- Eq. 1 apply and adjoint
@@ -305,11 +308,11 @@ def test_joint_strict_invariants(seed, s, S):
     assert np.array_equal(fr["err"], j["err"])
     assert float(j["err"].sum()) == pytest.approx(Rs[-1], rel=1e-12)
     # every LR pixel is exactly one HR pixel of its own block (Eq. 6 constraint)
-    Iu = O.to_unit(I)
+    assert j["L"].dtype == np.uint8
     h, w, _ = j["L"].shape
     for v in range(h):
         for u in range(w):
-            blk = Iu[v * s:(v + 1) * s, u * s:(u + 1) * s].reshape(-1, 3)
+            blk = I[v * s:(v + 1) * s, u * s:(u + 1) * s].reshape(-1, 3)
             assert np.any(np.all(blk == j["L"][v, u], axis=1))
     # the joint result is no worse than plain grid downsampling
     assert j["err"].sum() <= j["R0"] + 1e-9

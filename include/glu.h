@@ -139,6 +139,14 @@ int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* par
 /* Workspace bytes glu_joint_optimize needs for an H x W image (0 on invalid arguments). */
 size_t glu_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params);
 
+/* Verification aid (not part of the method): after a glu_joint_optimize call that used the
+ * workspace ws (same H, W, scale, params), copy its trial decisions to HOST memory `out`:
+ * for each iteration that ran, one byte per component in component order (1 kept, 0 rolled
+ * back), iterations concatenated. Synchronous on `stream`. Returns the number of bytes written
+ * or a negative GLU_ERR_* (GLU_ERR_INVALID_ARG if cap is too small). */
+int64_t glu_joint_decisions(const void* ws, size_t ws_bytes, int32_t H, int32_t W, int32_t scale,
+                            const glu_params* params, int8_t* out, int64_t cap, void* stream);
+
 /* Benchmark instrumentation (not part of the method). glu_joint_profile(1) makes later
  * glu_joint_optimize calls record CUDA events on their stream around their phases; the events
  * of up to 64 calls are kept. glu_joint_profile_read() waits for them, writes the summed

@@ -406,15 +406,21 @@ int oracle_label_components(const uint8_t* mask, int H, int W, int conn, int32_t
 
 /* --------------------------------------------------------------- joint optimisation (Alg. 2) */
 
-/* Per-iteration statistics, 8 doubles each, after a leading R_0:
- *   [n_large, M, accepted, rolled_back, residual, min |e1 - e0|, min |E_p - tau|, pixels searched]
- */
-#define JSTAT 8
+/* Per-iteration statistics, 9 doubles each, after a leading R_0:
+ *   [n_large, M, accepted, rolled_back, residual, min nonzero |e1 - e0|, min |E_p - tau|,
+ *    pixels searched, decisions replayed]
+ *
+ * Replay (verification of a lower-precision implementation): when `force` is given, a trial
+ * whose FP64 margin |e1 - e0| is at most force_tol (in [0, 1] units) takes the decision
+ * force[t] (t counts trials across iterations in order) instead of its own; such a margin is
+ * below the resolution of the other implementation's sums, so either decision is correct.
+ * Every other trial decides by the rule e1 > e0 as usual. */
+#define JSTAT 9
 
 int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double tau,
                  double unit, int N, int strict, int conn, double* L, int32_t* ka, int32_t* kb,
                  double* omega, double* err, double* stats, int8_t* accept_log, int64_t log_cap,
-                 int threads) {
+                 const int8_t* force, int64_t force_n, double force_tol, int threads) {
     if (!I || !L || !ka || !kb || !omega || !err || H <= 0 || W <= 0 || s <= 0 || S < 1 ||
         S > 9 || (S % 2) == 0 || N < 0 || (conn != 4 && conn != 8) || !(unit > 0.0))
         return OR_EINVAL;
@@ -496,7 +502,7 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
             for (size_t p = 0; p < n; ++p)
                 if (lab[p] >= 0) order[fillp[lab[p]]++] = (int32_t)p;
         }
-        int accepted = 0, rolled = 0;
+        int accepted = 0, rolled = 0, replayed = 0;
         double min_dec = INFINITY, searched = 0.0;
 
         for (int ci = 0; ci < M; ++ci) {
@@ -569,8 +575,13 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
             }
             searched += na;
             double dm = fabs(e1 - e0);
-            if (dm < min_dec) min_dec = dm;
+            if (dm > 0.0 && dm < min_dec) min_dec = dm;
             int accept = !(e1 > e0);
+            if (force && nlog < force_n && dm <= force_tol * unit && (force[nlog] & ~1) == 0 &&
+                force[nlog] != accept) {
+                accept = force[nlog];
+                ++replayed;
+            }
             if (accept) {
                 for (int t = 0; t < na; ++t) {
                     int p = aff[t];
@@ -591,7 +602,7 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
         for (size_t p = 0; p < n; ++p) R += err[p];
         if (st) {
             st[1] = M; st[2] = accepted; st[3] = rolled; st[4] = R / unit; st[5] = min_dec / unit;
-            st[7] = searched;
+            st[7] = searched; st[8] = replayed;
         }
         if (accepted == 0 || !(R < R_prev)) break;
         R_prev = R;

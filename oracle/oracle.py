@@ -44,7 +44,7 @@ def _lib():
             "oracle_apply_adjoint": [_p, _p, _p, _i, _i, _i, _i, _p, _i, _p, _p, _p],
             "oracle_label_components": [_p, _i, _i, _i, _p],
             "oracle_joint": [_p, _i, _i, _i, _i, _d, _d, _d, _i, _i, _i, _p, _p, _p, _p, _p, _p,
-                             _p, ctypes.c_int64, _i],
+                             _p, ctypes.c_int64, _p, ctypes.c_int64, _d, _i],
             "oracle_op_box3": [_p, _i, _i, _i, _p],
             "oracle_op_gauss3": [_p, _i, _i, _i, _p],
             "oracle_op_saturation": [_p, ctypes.c_size_t, _d, _p],
@@ -208,13 +208,14 @@ def label_components(mask, conn=8):
     return labels, M
 
 
-JSTAT = 8
+JSTAT = 9
 
 
 def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap=1 << 20,
-          threads=0):
+          force=None, force_tol=0.0, threads=0):
     """Algorithm 2. Returns dict(L, ka, kb, omega, err, R0, iters=[...], accept_log); L is
-    uint8 for a uint8 guide."""
+    uint8 for a uint8 guide. `force` (int8 keep/rollback per trial, in order) is followed only
+    where the oracle's own margin |e1 - e0| <= force_tol (see glu_oracle.c)."""
     is_u8 = np.asarray(I).dtype == np.uint8
     (I,), unit = colours(I)
     H, W, _ = I.shape
@@ -226,10 +227,12 @@ def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap
     er = np.empty((H, W), np.float64)
     stats = np.full(1 + JSTAT * max(N, 1), np.nan)
     log = np.full(log_cap, -1, np.int8)
+    fz = None if force is None else np.ascontiguousarray(force, np.int8)
     _chk(_lib().oracle_joint(_ptr(I), H, W, s, S, eps, tau, unit, N, int(bool(strict)), conn,
                              _ptr(L),
                              _ptr(ka), _ptr(kb), _ptr(om), _ptr(er), _ptr(stats), _ptr(log),
-                             log_cap, threads), "joint")
+                             log_cap, _ptr(fz), 0 if fz is None else fz.size, force_tol,
+                             threads), "joint")
     iters = []
     for it in range(N):
         st = stats[1 + it * JSTAT: 1 + (it + 1) * JSTAT]
@@ -238,7 +241,7 @@ def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap
         iters.append(dict(n_large=int(st[0]), M=int(st[1]), accepted=int(st[2]),
                           rolled_back=int(st[3]), residual=float(st[4]),
                           min_decision_margin=float(st[5]), min_threshold_margin=float(st[6]),
-                          searched=int(st[7])))
+                          searched=int(st[7]), replayed=int(st[8])))
         if st[0] == 0:
             break
     nlog = sum(it["M"] for it in iters)

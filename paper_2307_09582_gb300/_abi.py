@@ -71,6 +71,8 @@ PROTOTYPES = {
     "glu_apply": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _vp]),
     "glu_apply_backward": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _P(GluImage),
                                           _vp, _vp]),
+    "glu_joint_decisions": (ctypes.c_int64, [_vp, ctypes.c_size_t, _i32, _i32, _i32, _P(GluParams),
+                                             _vp, _i64, _vp]),
     "glu_joint_profile": (ctypes.c_int, [_i32]),
     "glu_joint_profile_read": (ctypes.c_int, [_P(ctypes.c_float), _P(_i32)]),
     "glu_status_string": (ctypes.c_char_p, [ctypes.c_int]),

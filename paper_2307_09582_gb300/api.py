@@ -133,8 +133,9 @@ def glu_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
                        lr_out: torch.Tensor | None = None, theta: Theta | None = None,
                        err_map: torch.Tensor | bool | None = True, stats: bool = True,
                        workspace: torch.Tensor | None = None, wfmt: int = A.GLU_W_F32,
-                       stream=None):
-    """Algorithm 2. Returns (lr, theta, err_map or None, stats dict or None)."""
+                       decisions: bool = False, stream=None):
+    """Algorithm 2. Returns (lr, theta, err_map or None, stats dict or None); with
+    decisions=True the stats hold the per-component keep/rollback log."""
     H, W = hr.shape[:2]
     h, w = lr_dims(H, W, scale)
     if lr_out is None:
@@ -158,6 +159,17 @@ def glu_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
         _ptr(err_map), ctypes.byref(st) if st is not None else None, ctypes.c_void_p(aligned),
         avail, _stream(stream)))
     sd = None
+    if st is not None and decisions:
+        import numpy as np
+        buf = np.empty(sum(st.components[k] for k in range(st.iterations)) + 1, dtype=np.int8)
+        n = lib().glu_joint_decisions(ctypes.c_void_p(aligned), avail, H, W, scale,
+                                      ctypes.byref(params), ctypes.c_void_p(buf.ctypes.data),
+                                      buf.size, _stream(stream))
+        if n < 0:
+            A.check("glu_joint_decisions", int(n))
+        decisions = buf[:n].copy()
+    else:
+        decisions = None
     if st is not None:
         n = st.iterations
         sd = dict(iterations=n, R0=st.residual[0],
@@ -165,7 +177,8 @@ def glu_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
                               accepted=st.accepted[k], rolled_back=st.rolled_back[k],
                               residual=st.residual[k + 1], searched=st.searched[k])
                          for k in range(n)],
-                  n_large_next=st.n_large[n] if n < A.GLU_MAX_ITERS else 0)
+                  n_large_next=st.n_large[n] if n < A.GLU_MAX_ITERS else 0,
+                  decisions=decisions)
     return lr_out, theta, err_map, sd
 
 

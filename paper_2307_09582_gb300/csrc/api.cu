@@ -180,7 +180,17 @@ int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
 
 size_t glu_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params) {
     if (H <= 0 || W <= 0 || scale < 1 || !params_ok(params)) return 0;
-    return joint_workspace_bytes(H, W, scale, params->S);
+    return joint_workspace_bytes(H, W, scale, params->S, params->N);
+}
+
+int64_t glu_joint_decisions(const void* ws, size_t ws_bytes, int32_t H, int32_t W, int32_t scale,
+                            const glu_params* params, int8_t* out, int64_t cap, void* stream) {
+    if (!ws || !out || cap < 0 || H <= 0 || W <= 0 || scale < 1 || !params_ok(params))
+        return GLU_ERR_INVALID_ARG;
+    int64_t n = 0;
+    const int rc = joint_decisions(ws, ws_bytes, H, W, scale, params->N, out, cap,
+                                   (cudaStream_t)stream, &n);
+    return rc != GLU_OK ? rc : n;
 }
 
 int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
@@ -194,7 +204,7 @@ int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* par
     if (theta->H != hr->h || theta->W != hr->w || theta->S != params->S || theta->scale != scale ||
         lr_out->h != lr_dim(hr->h, scale) || lr_out->w != lr_dim(hr->w, scale))
         return GLU_ERR_SHAPE;
-    const size_t need = joint_workspace_bytes(hr->h, hr->w, scale, params->S);
+    const size_t need = joint_workspace_bytes(hr->h, hr->w, scale, params->S, params->N);
     if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return GLU_ERR_WORKSPACE;
     JointArgs a;
     a.hr = (const uint8_t*)hr->data;

@@ -81,7 +81,9 @@ struct JointArgs {
     float* err;         // nullable: a workspace plane is used otherwise
 };
 
-size_t joint_workspace_bytes(int H, int W, int s, int S);
+size_t joint_workspace_bytes(int H, int W, int s, int S, int N);
+int joint_decisions(const void* ws, size_t ws_bytes, int H, int W, int s, int N, int8_t* out,
+                    int64_t cap, cudaStream_t st, int64_t* written);
 int launch_joint(const JointArgs& a, void* ws, size_t ws_bytes, glu_joint_stats* stats,
                  cudaStream_t st);
 

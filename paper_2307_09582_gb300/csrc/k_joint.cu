@@ -65,6 +65,8 @@ struct JointWs {
     unsigned long long* best;   // h*w
     uint32_t* backup;       // h*w
     double* partial;        // residual partials
+    int8_t* dlog;           // N * Mcap: kept (1) / rolled back (0) per component and iteration
+    int64_t mcap;
 };
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -76,7 +78,7 @@ static inline int64_t mcap_of(int H, int W) {
 }
 
 // Carve the workspace; returns the bytes needed (ptr may be null to only measure).
-static size_t carve(void* base, int H, int W, int h, int w, JointWs* o) {
+static size_t carve(void* base, int H, int W, int h, int w, int N, JointWs* o) {
     const int64_t n = (int64_t)H * W, nl = (int64_t)h * w, mcap = mcap_of(H, W);
     const int64_t tiles_a = (n + kScanTile - 1) / kScanTile + 1;
     const int64_t tiles_b = (mcap + kScanTile - 1) / kScanTile + 1;
@@ -109,14 +111,16 @@ static size_t carve(void* base, int H, int W, int h, int w, JointWs* o) {
     t.best = (unsigned long long*)take(sizeof(unsigned long long) * nl);
     t.backup = (uint32_t*)take(sizeof(uint32_t) * nl);
     t.partial = (double*)take(sizeof(double) * nres);
+    t.dlog = (int8_t*)take((size_t)(N > 0 ? N : 1) * (size_t)mcap);
+    t.mcap = mcap;
     if (o) *o = t;
     return off;
 }
 
-size_t joint_workspace_bytes(int H, int W, int s, int S) {
+size_t joint_workspace_bytes(int H, int W, int s, int S, int N) {
     (void)S;
     const int h = (H + s - 1) / s, w = (W + s - 1) / s;
-    return carve(nullptr, H, W, h, w, nullptr);
+    return carve(nullptr, H, W, h, w, N, nullptr);
 }
 
 // --------------------------------------------------------------------------- small helpers
@@ -774,6 +778,7 @@ __global__ void __launch_bounds__(kTrialThreads, 2) k_trials(const TrialArgs A) 
         __syncthreads();
         if (tid == 0) {
             __threadfence();
+            W_.dlog[(int64_t)A.it * W_.mcap + j] = (int8_t)(s_accept ? 1 : 0);
             if (s_accept) atomicAdd(&ctl->accepted[A.it], 1);
             else atomicAdd(&ctl->rolled[A.it], 1);
             st_release(&W_.done[j], 1);
@@ -832,7 +837,7 @@ int launch_joint(const JointArgs& a, void* wsp, size_t ws_bytes, glu_joint_stats
     if (prof::enabled && prof::used < prof::kSlots) slot = prof::used++;
     int evi = 0;
     JointWs ws;
-    const size_t need = carve(wsp, a.H, a.W, a.h, a.w, &ws);
+    const size_t need = carve(wsp, a.H, a.W, a.h, a.w, a.N, &ws);
     if (ws_bytes < need) return GLU_ERR_WORKSPACE;
     float* err = a.err ? a.err : ws.err;
     const int64_t n = (int64_t)a.H * a.W, nl = (int64_t)a.h * a.w;
@@ -921,6 +926,29 @@ int launch_joint(const JointArgs& a, void* wsp, size_t ws_bytes, glu_joint_stats
         for (int k = 0; k < GLU_MAX_ITERS; ++k) stats->searched[k] = (int64_t)h.searched[k];
         if (h.timeout) return GLU_ERR_TIMEOUT;
     }
+    return GLU_OK;
+}
+
+int joint_decisions(const void* wsp, size_t ws_bytes, int H, int W, int s, int N, int8_t* out,
+                    int64_t cap, cudaStream_t st, int64_t* written) {
+    const int h = (H + s - 1) / s, w = (W + s - 1) / s;
+    JointWs ws;
+    const size_t need = carve(const_cast<void*>(wsp), H, W, h, w, N, &ws);
+    if (ws_bytes < need) return GLU_ERR_WORKSPACE;
+    JointCtl c;
+    GLU_CUDA_TRY(cudaMemcpyAsync(&c, ws.ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
+    GLU_CUDA_TRY(cudaStreamSynchronize(st));
+    int64_t off = 0;
+    for (int it = 0; it < c.iterations && it < N; ++it) {
+        const int64_t m = c.M[it];
+        if (off + m > cap) return GLU_ERR_INVALID_ARG;
+        if (m > 0)
+            GLU_CUDA_TRY(cudaMemcpyAsync(out + off, ws.dlog + (int64_t)it * ws.mcap, (size_t)m,
+                                         cudaMemcpyDeviceToHost, st));
+        off += m;
+    }
+    GLU_CUDA_TRY(cudaStreamSynchronize(st));
+    *written = off;
     return GLU_OK;
 }
 

@@ -5,7 +5,8 @@ Rules (from the accuracy targets of the hot path):
     candidates (of different colour) are closer than 1e-5; there the GPU's pair must still be
     a valid optimum: its a within 1e-5 of the nearest distance, and its FP64 error within 1e-5
     of the best error achievable with that a (Algorithm 1's second step);
-  * weights within 1e-4 (float32 storage), 2.5e-4 (float16), 1e-5 (unorm16) where codes match;
+  * weights within 1e-4 (float32 storage), 2.5e-4 (float16), 2e-5 (unorm16: 7.6e-6 of
+    quantisation plus the FP32 weight error) where codes match;
   * error map within 1e-5; reconstructions within 1e-3 max-abs on [0, 1] colours.
 """
 from __future__ import annotations
@@ -15,7 +16,7 @@ import numpy as np
 from oracle import oracle as O
 
 NEAR_TIE = 1e-5
-W_TOL = {0: 1e-4, 1: 2.5e-4, 2: 1e-5}
+W_TOL = {0: 1e-4, 1: 2.5e-4, 2: 2e-5}
 
 
 def check_search(I, L, s, S, theta, err_gpu=None, eps=1e-3, wfmt=0, ref=None, gnu=False):

@@ -20,45 +20,62 @@ def api():
     return A
 
 
+# trials whose FP64 margin |e1 - e0| is below this follow the GPU's logged decision in the
+# oracle (ten times the FP32 resolution of a sum of ~1e3 errors of ~0.1); all others must agree
+REPLAY_TOL = 1e-4
+
+
 def run_both(api, img, s, S, N, strict, conn=8):
     hr = torch.from_numpy(img).cuda()
     p = api.glu_params(S=S, N=N, joint=api.GLU_JOINT_STRICT if strict else api.GLU_JOINT_PAPER,
                        connectivity=conn)
-    lr, theta, err, st = api.glu_joint_optimize(hr, s, p)
+    lr, theta, err, st = api.glu_joint_optimize(hr, s, p, decisions=True)
     torch.cuda.synchronize()
     assert api.glu_device_status() == 0
-    ref = O.joint(img, s, S, N=N, strict=strict, conn=conn)
+    ref = O.joint(img, s, S, N=N, strict=strict, conn=conn, force=st["decisions"],
+                  force_tol=REPLAY_TOL)
     return hr, lr, theta, err, st, ref
 
 
 def compare(api, img, s, S, N, strict, lr, theta, err, st, ref):
-    """Decisions and final state equal the oracle's (given safe decision margins)."""
-    margins_ok = all((it["min_decision_margin"] == 0.0 or it["min_decision_margin"] > 1e-5)
-                     and it["min_threshold_margin"] > 1e-6 for it in ref["iters"])
+    """Decisions and final state equal the oracle's. Trials within REPLAY_TOL of a tie follow
+    the GPU's decision in the oracle (counted); every other decision must agree."""
+    thr_ok = all(it["min_threshold_margin"] > 1e-6 for it in ref["iters"])
     gi = st["iters"]
     ri = [it for it in ref["iters"] if it["n_large"] > 0]
     msg = f"\ngpu {gi}\nref {ri}"
     assert st["R0"] == pytest.approx(ref["R0"], rel=1e-6), msg
-    if not margins_ok:
-        pytest.skip("oracle reports a decision within FP32 resolution; exact replay not expected")
+    if not thr_ok:
+        pytest.skip("a pixel's error is within FP32 resolution of tau; exact replay not expected")
     assert len(gi) == len(ri), msg
     for g, r in zip(gi, ri):
         assert (g["n_large"], g["M"], g["accepted"], g["rolled_back"]) == \
                (r["n_large"], r["M"], r["accepted"], r["rolled_back"]), msg
         assert g["residual"] == pytest.approx(r["residual"], rel=1e-6), msg
+    assert np.array_equal(st["decisions"], ref["accept_log"][:len(st["decisions"])])
     Lg = lr.cpu().numpy()
     Lr = ref["L"]
     assert np.array_equal(Lg, Lr), f"{int((Lg != Lr).any(axis=2).sum())} LR pixels differ"
+    replayed = sum(it["replayed"] for it in ri)
     if strict:
         # STRICT keeps Theta = Algorithm 1 on the final LR image: check it as a plain search
-        return check_search(img, Lg, s, S, theta, err)
-    K = S * S
-    codes = theta.codes_i32().cpu().numpy()
-    same = (codes // K == ref["ka"]) & (codes % K == ref["kb"])
-    assert (~same).mean() < 1e-3
-    e = err.cpu().numpy()
-    assert np.abs(e - ref["err"])[same].max() < 1e-5
-    return dict(mismatches=int((~same).sum()))
+        rep = check_search(img, Lg, s, S, theta, err)
+    else:
+        # PAPER leaves Theta stale outside the components: a pixel's pair may differ only where
+        # it is a near-tie of Algorithm 1 on the initial or on the final LR image
+        K = S * S
+        codes = theta.codes_i32().cpu().numpy()
+        same = (codes // K == ref["ka"]) & (codes % K == ref["kb"])
+        tie = np.zeros_like(same)
+        for L in (O.downsample_grid(img, s), Lg):
+            f = O.glu_fast(img, L, s, S, gaps=True)
+            tie |= (f["gap_a"] < 1e-5) | (f["gap_b"] < 1e-5)
+        assert not (~same & ~tie).any()
+        e = err.cpu().numpy()
+        assert np.abs(e - ref["err"])[same].max() < 1e-5
+        rep = dict(mismatches=int((~same).sum()))
+    rep["replayed_decisions"] = replayed
+    return rep
 
 
 @pytest.mark.parametrize("H,W,s,S,strict", [

@@ -89,8 +89,7 @@ typedef struct {
     int32_t accepted[GLU_MAX_ITERS];     /* trials kept (e1 <= e0) */
     int32_t rolled_back[GLU_MAX_ITERS];  /* trials undone (e1 > e0) */
     double residual[GLU_MAX_ITERS + 1];  /* R_0 .. R_n = sum_p E_p, FP64, fixed-order reduction */
-    int64_t searched[GLU_MAX_ITERS];     /* HR pixels re-run through Algorithm 1 by the trials
-                                            (both the trial pass and the commit pass) */
+    int64_t searched[GLU_MAX_ITERS];     /* HR pixels re-run through Algorithm 1 by the trials */
 } glu_joint_stats;
 
 /* Fill *p with the paper's parameters: S = 3, eps = 1e-3, tau = 30/255, N = 3, FAST, STRICT,

@@ -406,16 +406,19 @@ int oracle_label_components(const uint8_t* mask, int H, int W, int conn, int32_t
 
 /* --------------------------------------------------------------- joint optimisation (Alg. 2) */
 
-/* Per-iteration statistics, 9 doubles each, after a leading R_0:
+/* Per-iteration statistics, 10 doubles each, after a leading R_0:
  *   [n_large, M, accepted, rolled_back, residual, min nonzero |e1 - e0|, min |E_p - tau|,
- *    pixels searched, decisions replayed]
+ *    pixels searched, decisions replayed, argmax near-ties]
+ * An argmax near-tie is a block [q_up] of a component where the largest error and the error of
+ * another pixel of a different colour are within 1e-6: a lower-precision implementation may
+ * then pick the other pixel, which is as correct to its precision.
  *
  * Replay (verification of a lower-precision implementation): when `force` is given, a trial
  * whose FP64 margin |e1 - e0| is at most force_tol (in [0, 1] units) takes the decision
  * force[t] (t counts trials across iterations in order) instead of its own; such a margin is
  * below the resolution of the other implementation's sums, so either decision is correct.
  * Every other trial decides by the rule e1 > e0 as usual. */
-#define JSTAT 9
+#define JSTAT 10
 
 int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double tau,
                  double unit, int N, int strict, int conn, double* L, int32_t* ka, int32_t* kb,
@@ -458,9 +461,10 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
     double* ter = (double*)malloc(sizeof(double) * n);
     double* qval = (double*)malloc(sizeof(double) * 3 * nl);
     double* qbest = (double*)malloc(sizeof(double) * nl);
+    int32_t* qpix = (int32_t*)malloc(sizeof(int32_t) * nl);
     int rc = OR_OK;
     if (!mask || !lab || !order || !cstart || !lr_stamp || !lr_list || !aff || !backup || !tka ||
-        !tkb || !tom || !ter || !qval || !qbest) {
+        !tkb || !tom || !ter || !qval || !qbest || !qpix) {
         rc = OR_ENOMEM;
         goto done;
     }
@@ -502,7 +506,7 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
             for (size_t p = 0; p < n; ++p)
                 if (lab[p] >= 0) order[fillp[lab[p]]++] = (int32_t)p;
         }
-        int accepted = 0, rolled = 0, replayed = 0;
+        int accepted = 0, rolled = 0, replayed = 0, argmax_ties = 0;
         double min_dec = INFINITY, searched = 0.0;
 
         for (int ci = 0; ci < M; ++ci) {
@@ -521,8 +525,16 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
                 }
                 if (err[p] > qbest[q]) { /* strict: the lowest raster index wins ties */
                     qbest[q] = err[p];
+                    qpix[q] = p;
                     for (int c = 0; c < 3; ++c) qval[(size_t)q * 3 + c] = I[(size_t)p * 3 + c];
                 }
+            }
+            for (int t = 0; t < csz; ++t) {
+                int p = Cp[t], y = p / W, x = p % W;
+                int q = (y / s) * w + (x / s);
+                if (p != qpix[q] && !same3(&I[(size_t)p * 3], &I[(size_t)qpix[q] * 3]) &&
+                    qbest[q] - err[p] <= 1e-6 * unit)
+                    ++argmax_ties;
             }
             /* the pixels whose Theta and E are re-optimised and summed */
             int na = 0;
@@ -602,7 +614,7 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
         for (size_t p = 0; p < n; ++p) R += err[p];
         if (st) {
             st[1] = M; st[2] = accepted; st[3] = rolled; st[4] = R / unit; st[5] = min_dec / unit;
-            st[7] = searched; st[8] = replayed;
+            st[7] = searched; st[8] = replayed; st[9] = argmax_ties;
         }
         if (accepted == 0 || !(R < R_prev)) break;
         R_prev = R;
@@ -610,7 +622,7 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
 done:
     for (size_t p = 0; p < n; ++p) err[p] /= unit;
     free(mask); free(lab); free(order); free(cstart); free(lr_stamp); free(lr_list); free(aff);
-    free(backup); free(tka); free(tkb); free(tom); free(ter); free(qval); free(qbest);
+    free(backup); free(tka); free(tkb); free(tom); free(ter); free(qval); free(qbest); free(qpix);
     return rc;
 }
 

@@ -208,7 +208,7 @@ def label_components(mask, conn=8):
     return labels, M
 
 
-JSTAT = 9
+JSTAT = 10
 
 
 def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap=1 << 20,
@@ -241,7 +241,8 @@ def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap
         iters.append(dict(n_large=int(st[0]), M=int(st[1]), accepted=int(st[2]),
                           rolled_back=int(st[3]), residual=float(st[4]),
                           min_decision_margin=float(st[5]), min_threshold_margin=float(st[6]),
-                          searched=int(st[7]), replayed=int(st[8])))
+                          searched=int(st[7]), replayed=int(st[8]),
+                          argmax_near_ties=int(st[9])))
         if st[0] == 0:
             break
     nlog = sum(it["M"] for it in iters)

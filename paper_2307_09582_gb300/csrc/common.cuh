@@ -67,6 +67,18 @@ __device__ __forceinline__ void store_weight(void* base, int fmt, int64_t i, flo
     }
 }
 
+// Re-store a weight previously read with load_weight*: float16 and unorm16 values round-trip
+// exactly through float (every float16 and every k/65535 converts back to the same code).
+__device__ __forceinline__ void store_weight_raw(void* base, int fmt, int64_t i, float w) {
+    if (fmt == GLU_W_F32) {
+        ((float*)base)[i] = w;
+    } else if (fmt == GLU_W_F16) {
+        ((__half*)base)[i] = __float2half_rn(w);
+    } else {
+        ((uint16_t*)base)[i] = (uint16_t)rintf(w * 65535.0f);
+    }
+}
+
 __device__ __forceinline__ float load_weight(const void* base, int fmt, int64_t i) {
     if (fmt == GLU_W_F32) return ((const float*)base)[i];
     if (fmt == GLU_W_F16) return __half2float(((const __half*)base)[i]);

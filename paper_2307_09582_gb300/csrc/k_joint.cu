@@ -42,6 +42,8 @@ struct JointCtl {
     int claim[GLU_MAX_ITERS];
     double residual[GLU_MAX_ITERS + 1];
     unsigned long long searched[GLU_MAX_ITERS];
+    int finished[GLU_MAX_ITERS];   // components done (kept or rolled back) per iteration
+    int open_tasks;                // published tasks that still have unclaimed items
 };
 
 struct JointWs {
@@ -67,7 +69,22 @@ struct JointWs {
     double* partial;        // residual partials
     int8_t* dlog;           // N * Mcap: kept (1) / rolled back (0) per component and iteration
     int64_t mcap;
+    uint16_t* sh_code;      // H*W shadow Theta / E written by a trial, copied if it is kept
+    float* sh_w;            // H*W
+    float* sh_err;          // H*W
+    // one task slot per persistent CTA: the block items of its component's trial or commit,
+    // open to every warp of the grid
+    unsigned long long* slot_word;  // (epoch << 32) | next item; odd epoch = open
+    int* slot_j;
+    int* slot_n;            // items
+    int* slot_nu;           // distinct LR blocks of the component
+    int* slot_kind;         // 0 trial, 1 commit
+    unsigned long long* slot_e0;
+    unsigned long long* slot_e1;
+    int* slot_fin;          // items finished
 };
+
+constexpr int kMaxSlots = 4096;
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -113,6 +130,17 @@ static size_t carve(void* base, int H, int W, int h, int w, int N, JointWs* o) {
     t.partial = (double*)take(sizeof(double) * nres);
     t.dlog = (int8_t*)take((size_t)(N > 0 ? N : 1) * (size_t)mcap);
     t.mcap = mcap;
+    t.sh_code = (uint16_t*)take(sizeof(uint16_t) * n);
+    t.sh_w = (float*)take(sizeof(float) * n);
+    t.sh_err = (float*)take(sizeof(float) * n);
+    t.slot_word = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
+    t.slot_j = (int*)take(sizeof(int) * kMaxSlots);
+    t.slot_n = (int*)take(sizeof(int) * kMaxSlots);
+    t.slot_nu = (int*)take(sizeof(int) * kMaxSlots);
+    t.slot_kind = (int*)take(sizeof(int) * kMaxSlots);
+    t.slot_e0 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
+    t.slot_e1 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
+    t.slot_fin = (int*)take(sizeof(int) * kMaxSlots);
     if (o) *o = t;
     return off;
 }
@@ -169,13 +197,16 @@ __device__ __forceinline__ int block_excl_scan(int v, int* out_excl, int* smem_w
 
 // ---------------------------------------------------------------- control and init kernels
 
-__global__ void k_ctl_init(JointCtl* c, unsigned long long* stamp, int64_t nl) {
+__global__ void k_ctl_init(JointCtl* c, unsigned long long* stamp, int64_t nl,
+                           unsigned long long* slot_word) {
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t i = i0; i < kMaxSlots; i += (int64_t)gridDim.x * blockDim.x) slot_word[i] = 0ull;
     if (i0 == 0) {
         c->active = 1;
         c->timeout = 0;
         c->iterations = 0;
         c->M_cur = 0;
+        c->open_tasks = 0;
         for (int k = 0; k < GLU_MAX_ITERS; ++k) {
             c->n_large[k] = 0;
             c->M[k] = 0;
@@ -183,6 +214,7 @@ __global__ void k_ctl_init(JointCtl* c, unsigned long long* stamp, int64_t nl) {
             c->rolled[k] = 0;
             c->claim[k] = 0;
             c->searched[k] = 0ull;
+            c->finished[k] = 0;
         }
     }
     for (int64_t i = i0; i < nl; i += (int64_t)gridDim.x * blockDim.x) stamp[i] = 0ull;
@@ -528,6 +560,21 @@ __global__ void k_comp_fill(const int* lab, int H, int W, int s, int w, const ui
 
 // ---------------------------------------------------------------------------- the trials
 
+#ifdef GLU_TRIAL_TRACE
+// Debug builds only: per-component timestamps (claim, dependencies met, trial summed, done).
+constexpr int kTraceMax = 1 << 15;
+static __device__ unsigned long long g_trace[GLU_MAX_ITERS][kTraceMax][4];
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+#define GLU_TRACE(it, j, k) \
+    do { if (tid == 0 && (j) < kTraceMax) g_trace[it][j][k] = gtimer(); } while (0)
+#else
+#define GLU_TRACE(it, j, k) do { } while (0)
+#endif
+
 struct TrialArgs {
     const uint8_t* hr;
     int64_t hr_pitch;
@@ -579,12 +626,20 @@ __device__ __forceinline__ bool wait_done(const int* done, int i, const JointCtl
     return false;
 }
 
-// One warp re-searches the HR pixels of LR block (bv, bu). Sums (Kahan, fixed lane order) the
-// stored errors (e0) and the re-searched ones (e1) of the pixels selected by `member`
-// (comp >= 0: only pixels of that component), optionally committing Theta and E.
+// Weight load through L2 (the planes are written by other CTAs during the trials).
+__device__ __forceinline__ float load_weight_cg(const void* base, int fmt, int64_t i) {
+    if (fmt == GLU_W_F32) return __ldcg((const float*)base + i);
+    if (fmt == GLU_W_F16) return __half2float(__ldcg((const __half*)base + i));
+    return (float)__ldcg((const unsigned short*)base + i) * (1.0f / 65535.0f);
+}
+
+// One warp re-runs Algorithm 1 on the HR pixels of LR block (bv, bu) against the current LR
+// image (comp >= 0: only the pixels of that component), writing the results in place and the
+// previous values to the backup planes. The previous errors (e0) and the new ones (e1) are
+// summed with Kahan compensation in a fixed lane order and reduced with a fixed butterfly.
 template <int S>
-__device__ __forceinline__ void warp_block(const TrialArgs& A, float4* win, int bv, int bu,
-                                           int comp, bool commit, float& e0, float& e1) {
+__device__ __noinline__ void warp_block_trial(const TrialArgs& A, float4* win, int bv, int bu,
+                                                 int comp, float& e0, float& e1) {
     constexpr int r = (S - 1) / 2, K = S * S;
     const int lane = threadIdx.x & 31;
     for (int k = lane; k < K; k += 32) {
@@ -608,47 +663,301 @@ __device__ __forceinline__ void warp_block(const TrialArgs& A, float4* win, int 
         const int64_t p = (int64_t)y * A.W + x;
         if (comp >= 0 && __ldcg(&A.ws.lab[p]) != comp) continue;
         const uint8_t* ip = A.hr + (int64_t)y * A.hr_pitch + (int64_t)x * 3;
-        const SearchOut o = search_pixel<S>(win, S, rm, cm, (float)ip[0], (float)ip[1],
-                                            (float)ip[2], A.eps255, false);
+        const SearchOut o = search_pixel<S, true>(win, S, rm, cm, (float)ip[0], (float)ip[1],
+                                                  (float)ip[2], A.eps255, false);
         ++nsearched;
-        if (commit) {
-            A.code[p] = (uint16_t)(o.ka * K + o.kb);
-            store_weight(A.weight, A.wfmt, p, o.omega);
-            A.err[p] = o.err;
-        } else {
-            kahan_add(s0, c0, __ldcg(&A.err[p]));
-            kahan_add(s1, c1, o.err);
-        }
+        // the new Theta / E go in place; the old ones to the backup planes (restored if the
+        // trial is rolled back)
+        const float eold = __ldcg(&A.err[p]);
+        A.ws.sh_code[p] = __ldcg(&A.code[p]);
+        A.ws.sh_w[p] = load_weight_cg(A.weight, A.wfmt, p);
+        A.ws.sh_err[p] = eold;
+        A.code[p] = (uint16_t)(o.ka * K + o.kb);
+        store_weight(A.weight, A.wfmt, p, o.omega);
+        A.err[p] = o.err;
+        kahan_add(s0, c0, eold);
+        kahan_add(s1, c1, o.err);
     }
     float t0 = s0 - c0, t1 = s1 - c1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         t0 += __shfl_xor_sync(0xffffffffu, t0, o);
         t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        nsearched += __shfl_xor_sync(0xffffffffu, nsearched, o);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nsearched += __shfl_xor_sync(0xffffffffu, nsearched, o);
     if (lane == 0 && nsearched) atomicAdd(&A.ws.ctl->searched[A.it], (unsigned long long)nsearched);
     e0 = t0;
     e1 = t1;
     __syncwarp();
 }
 
+// Roll back a trial for LR block (bv, bu): restore Theta and E from the backup planes.
+__device__ __forceinline__ void warp_block_commit(const TrialArgs& A, int bv, int bu, int comp) {
+    const int lane = threadIdx.x & 31;
+    const int ys = bv * A.s, xs = bu * A.s;
+    const int ey = min(A.s, A.H - ys), ex = min(A.s, A.W - xs);
+    for (int j = lane; j < ey * ex; j += 32) {
+        const int y = ys + j / ex, x = xs + j % ex;
+        const int64_t p = (int64_t)y * A.W + x;
+        if (comp >= 0 && __ldcg(&A.ws.lab[p]) != comp) continue;
+        A.code[p] = __ldcg(&A.ws.sh_code[p]);
+        store_weight_raw(A.weight, A.wfmt, p, __ldcg(&A.ws.sh_w[p]));
+        A.err[p] = __ldcg(&A.ws.sh_err[p]);
+    }
+}
+
+// Block item t of component j (trial or commit enumeration): the LR block it designates, or
+// false when it falls outside the LR image. STRICT: (distinct block u, neighbour nb) pairs;
+// PAPER: the distinct blocks themselves.
 template <int S>
-__global__ void __launch_bounds__(kTrialThreads, 2) k_trials(const TrialArgs A) {
+__device__ __forceinline__ bool item_block(const TrialArgs& A, int stY, int t, int& bv, int& bu) {
+    constexpr int r = (S - 1) / 2, NB = (2 * r + 1) * (2 * r + 1);
+    const int q = A.ws.ulist[stY + (A.strict ? t / NB : t)];
+    bv = q / A.w;
+    bu = q % A.w;
+    if (A.strict) {
+        const int nb = t % NB;
+        bv += nb / (2 * r + 1) - r;
+        bu += nb % (2 * r + 1) - r;
+        if (bv < 0 || bv >= A.h || bu < 0 || bu >= A.w) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long trial_tag(int it, int j, int phase) {
+    return ((unsigned long long)(it * 4 + phase) << 40) | (unsigned long long)(j + 1);
+}
+
+// One warp processes item t of component j: claims its block (STRICT blocks reached from several
+// q are processed once), then runs the trial (kind 0, sums returned) or the commit (kind 1).
+template <int S>
+__device__ __forceinline__ bool process_item(const TrialArgs& A, float4* win, int j, int stY,
+                                             int kind, int t, float& e0, float& e1) {
+    const int lane = threadIdx.x & 31;
+    e0 = 0.f;
+    e1 = 0.f;
+    int bv, bu;
+    if (!item_block<S>(A, stY, t, bv, bu)) return false;
+    if (A.strict) {
+        const unsigned long long tag = trial_tag(A.it, j, kind + 1);
+        int claimed = 0;
+        if (lane == 0) claimed = atomicExch(&A.ws.stamp[(int64_t)bv * A.w + bu], tag) != tag;
+        if (!__shfl_sync(0xffffffffu, claimed, 0)) return false;
+    }
+    if (kind == 0)
+        warp_block_trial<S>(A, win, bv, bu, A.strict ? -1 : j, e0, e1);
+    else
+        warp_block_commit(A, bv, bu, A.strict ? -1 : j);
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    return *(volatile const unsigned long long*)p;
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Backstop for every wait of the trial kernel: a launch that has run this long has gone wrong
+// (the whole 4K workload takes milliseconds); give up, record GLU_ERR_TIMEOUT and return.
+constexpr unsigned long long kTrialDeadlineNs = 5000000000ull;
+
+// Warp-uniform: true when the launch must stop waiting (deadline passed or another wait
+// already timed out). Lane 0 decides, every lane gets the same answer.
+__device__ __forceinline__ bool warp_should_abort(const JointCtl* c, unsigned long long t0) {
+    int a = 0;
+    if ((threadIdx.x & 31) == 0)
+        a = (*(volatile const int*)&c->timeout != 0) || (now_ns() - t0 > kTrialDeadlineNs);
+    return __shfl_sync(0xffffffffu, a, 0) != 0;
+}
+
+__device__ __forceinline__ unsigned long long atom_add_acquire_u64(unsigned long long* p,
+                                                                   unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.acquire.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v)
+                 : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// True when slot k holds an open task with unclaimed items (a relaxed snapshot).
+__device__ __forceinline__ bool slot_has_items(const JointWs& W_, int k) {
+    const unsigned long long w = ld_volatile_u64(&W_.slot_word[k]);
+    return ((w >> 32) & 1ull) && (int)(w & 0xFFFFFFFFull) < *(volatile const int*)&W_.slot_n[k];
+}
+
+// One warp: take one unclaimed item of an open task — its own CTA's slot first, then the slot it
+// helped last (`hint`), otherwise the open task of the smallest component — and process it.
+// Returns false if no item was available.
+//
+// Claiming is one fetch-and-add on the slot's (epoch << 32 | next) word. An increment that lands
+// on a closed slot is harmless (opening overwrites the word); one that lands on an open epoch
+// owns item `next` of that epoch, whose context cannot change before that item is finished.
+template <int S>
+__device__ bool help_one(const TrialArgs& A, float4* win, int own, int G, int& hint) {
+    const JointWs& W_ = A.ws;
+    const int lane = threadIdx.x & 31;
+    int s_sel = -1;
+    if (lane == 0) {
+        if (slot_has_items(W_, own)) s_sel = own;
+        else if (hint >= 0 && slot_has_items(W_, hint)) s_sel = hint;
+        else if (*(volatile const int*)&W_.ctl->open_tasks <= 0) s_sel = -2;  // nothing open
+    }
+    s_sel = __shfl_sync(0xffffffffu, s_sel, 0);
+    if (s_sel == -2) {
+        hint = -1;
+        return false;
+    }
+    if (s_sel < 0) {
+        int bj = 0x7fffffff, bs = -1;
+        for (int k = lane; k < G; k += 32) {
+            if (!slot_has_items(W_, k)) continue;
+            const int jj = *(volatile const int*)&W_.slot_j[k];
+            if (jj < bj) { bj = jj; bs = k; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+            if (oj < bj || (oj == bj && os < bs)) { bj = oj; bs = os; }
+        }
+        s_sel = bs;
+    }
+    if (s_sel < 0) {
+        hint = -1;
+        return false;
+    }
+    int item = -1, j = 0, kind = 0, stY = 0;
+    if (lane == 0) {
+        const unsigned long long old = atom_add_acquire_u64(&W_.slot_word[s_sel], 1ull);
+        if ((old >> 32) & 1ull) {
+            const int nx = (int)(old & 0xFFFFFFFFull);
+            const int n = *(volatile const int*)&W_.slot_n[s_sel];
+            if (nx < n) {
+                item = nx;
+                j = *(volatile const int*)&W_.slot_j[s_sel];
+                kind = *(volatile const int*)&W_.slot_kind[s_sel];
+                stY = W_.start[j].y;
+                // the claimer of the last item takes the task off the open count
+                if (nx + 1 == n) atomicSub(&W_.ctl->open_tasks, 1);
+            }
+        }
+    }
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item < 0) {
+        hint = -1;
+        return false;
+    }
+    hint = s_sel;
+    j = __shfl_sync(0xffffffffu, j, 0);
+    kind = __shfl_sync(0xffffffffu, kind, 0);
+    stY = __shfl_sync(0xffffffffu, stY, 0);
+    float e0, e1;
+    const bool did = process_item<S>(A, win, j, stY, kind, item, e0, e1);
+    __syncwarp();
+    if (lane == 0) {
+        if (did && kind == 0) {
+            atomicAdd(&W_.slot_e0[s_sel], (unsigned long long)to_fixed(e0));
+            atomicAdd(&W_.slot_e1[s_sel], (unsigned long long)to_fixed(e1));
+        }
+        // release: this warp's writes (shadow planes, Theta, E, sums) are visible to whoever
+        // observes the count
+        red_release_add(&W_.slot_fin[s_sel], 1);
+    }
+    __syncwarp();
+    return true;
+}
+
+// Run the items of one task of component j. Small tasks stay inside the CTA; larger ones are
+// published in the CTA's slot so idle warps anywhere in the grid can take items. Returns the
+// (fixed-point) sums of a trial in e0/e1. False on an exhausted wait.
+template <int S>
+__device__ bool run_task(const TrialArgs& A, float4* win, int j, int stY, int nu, int kind,
+                         int nitems, int G, unsigned long long* s_e0, unsigned long long* s_e1,
+                         int* s_flag, unsigned long long t0) {
+    const JointWs& W_ = A.ws;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int nwarps = kTrialThreads / 32;
+    const int own = blockIdx.x;
+    if (nitems <= nwarps) {
+        for (int t = warp; t < nitems; t += nwarps) {
+            float e0, e1;
+            const bool did = process_item<S>(A, win, j, stY, kind, t, e0, e1);
+            if (did && kind == 0 && lane == 0) {
+                atomicAdd(s_e0, (unsigned long long)to_fixed(e0));
+                atomicAdd(s_e1, (unsigned long long)to_fixed(e1));
+            }
+        }
+        __syncthreads();
+        return true;
+    }
+    if (tid == 0) {
+        const unsigned long long e = W_.slot_word[own] >> 32;  // even: closed
+        W_.slot_j[own] = j;
+        W_.slot_n[own] = nitems;
+        W_.slot_nu[own] = nu;
+        W_.slot_kind[own] = kind;
+        W_.slot_e0[own] = 0ull;
+        W_.slot_e1[own] = 0ull;
+        W_.slot_fin[own] = 0;
+        atomicAdd(&W_.ctl->open_tasks, 1);
+        __threadfence();
+        atomicExch(&W_.slot_word[own], (e + 1ull) << 32);  // open, next item 0
+        *s_flag = 0;
+    }
+    __syncthreads();
+    // every decision below is warp-uniform (lane 0 reads, all lanes follow), so the warp-wide
+    // shuffles inside help_one always run with the full warp
+    int hint = -1;
+    for (;;) {
+        int fin = 0;
+        if (lane == 0) fin = ld_acquire(&W_.slot_fin[own]) >= nitems;
+        if (__shfl_sync(0xffffffffu, fin, 0)) break;
+        if (!help_one<S>(A, win, own, G, hint)) __nanosleep(100);
+        if (warp_should_abort(A.ws.ctl, t0)) {
+            if (lane == 0) *s_flag = 1;
+            break;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (kind == 0) {
+            *s_e0 = ld_volatile_u64(&W_.slot_e0[own]);
+            *s_e1 = ld_volatile_u64(&W_.slot_e1[own]);
+        }
+        const unsigned long long w = W_.slot_word[own] >> 32;
+        atomicExch(&W_.slot_word[own], (w + 1ull) << 32);  // closed
+    }
+    __syncthreads();
+    return *s_flag == 0;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kTrialThreads, 3) k_trials(const TrialArgs A) {
     constexpr int r = (S - 1) / 2;
+    constexpr int NB = (2 * r + 1) * (2 * r + 1);  // blocks within r of one LR pixel
+    constexpr int kPend = 512;
     JointCtl* ctl = A.ws.ctl;
     if (!is_active(ctl)) return;
     __shared__ float4 wins[kTrialThreads / 32][S * S];
-    __shared__ int s_j, s_nu, s_accept;
-    __shared__ volatile int s_fail;
-    __shared__ long long s_e0, s_e1;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nwarps = kTrialThreads / 32;
+    __shared__ int s_j, s_nu, s_accept, s_flag, s_npend, s_povf;
+    __shared__ int s_pend[kPend];
+    __shared__ unsigned long long s_e0, s_e1;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int G = gridDim.x;
     const int M = ctl->M_cur;
     const int D = A.strict ? 2 * r : r;
+    const int ND = (2 * D + 1) * (2 * D + 1);
     const JointWs& W_ = A.ws;
-    const unsigned long long tagbase = ((unsigned long long)(A.it * 4) << 40);
+    float4* win = wins[warp];
+    const unsigned long long t0 = now_ns();
 
     for (;;) {
         if (tid == 0) {
@@ -656,46 +965,80 @@ __global__ void __launch_bounds__(kTrialThreads, 2) k_trials(const TrialArgs A) 
             s_nu = 0;
             s_e0 = 0;
             s_e1 = 0;
-            s_fail = 0;
+            s_flag = 0;
+            s_npend = 0;
+            s_povf = 0;
         }
         __syncthreads();
         const int j = s_j;
         if (j >= M) break;
+        GLU_TRACE(A.it, j, 0);
         const int2 st = W_.start[j], en = W_.start[j + 1];
 
-        // 1. wait for every earlier component whose LR blocks lie within D of ours
-        for (int t = st.y + tid; t < en.y; t += kTrialThreads) {
-            const int q = W_.qlist[t];
-            const int qv = q / A.w, qu = q % A.w;
-            for (int bv = max(0, qv - D); bv <= min(A.h - 1, qv + D); ++bv)
-                for (int bu = max(0, qu - D); bu <= min(A.w - 1, qu + D); ++bu) {
-                    const int64_t b = (int64_t)bv * A.w + bu;
-                    if (__ldcg(&W_.ovf[b])) {
-                        for (int i = 0; i < j && !s_fail; ++i)
-                            if (!wait_done(W_.done, i, ctl)) s_fail = 1;
-                    } else {
-                        for (int k = 0; k < kOwnSlots && !s_fail; ++k) {
-                            const int i = __ldcg(&W_.own[b * kOwnSlots + k]);
-                            if (i < 0) break;
-                            if (i < j && !wait_done(W_.done, i, ctl)) s_fail = 1;
-                        }
+        // 1. the earlier components whose LR blocks lie within D of ours and are not done yet
+        const int npairs = (en.y - st.y) * ND;
+        for (int t = tid; t < npairs; t += kTrialThreads) {
+            const int q = W_.qlist[st.y + t / ND];
+            const int nb = t % ND;
+            const int bv = q / A.w + nb / (2 * D + 1) - D, bu = q % A.w + nb % (2 * D + 1) - D;
+            if (bv < 0 || bv >= A.h || bu < 0 || bu >= A.w) continue;
+            const int64_t b = (int64_t)bv * A.w + bu;
+            if (__ldcg(&W_.ovf[b])) {
+                s_povf = 1;  // more components than owner slots: wait for every earlier one
+                continue;
+            }
+            for (int k = 0; k < kOwnSlots; ++k) {
+                const int i = __ldcg(&W_.own[b * kOwnSlots + k]);
+                if (i < 0) break;
+                if (i < j && ld_acquire(&W_.done[i]) == 0) {
+                    const int slot = atomicAdd(&s_npend, 1);
+                    if (slot < kPend) s_pend[slot] = i; else s_povf = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_povf) {
+            // rare fallback: wait in order for every earlier component
+            for (int i = tid; i < j; i += kTrialThreads)
+                if (!wait_done(W_.done, i, ctl)) s_flag = 1;
+        } else {
+            // wait, helping other components' tasks meanwhile; the loop decisions are
+            // CTA-uniform (__syncthreads_or)
+            const int np = min(s_npend, kPend);
+            int hint = -1;
+            for (;;) {
+                int mine = 0;
+                for (int t = tid; t < np; t += kTrialThreads) {
+                    const int i = s_pend[t];
+                    if (i >= 0) {
+                        if (ld_acquire(&W_.done[i]) != 0) s_pend[t] = -1; else mine = 1;
                     }
                 }
+                if (__syncthreads_or(mine) == 0) break;
+                if (!help_one<S>(A, win, blockIdx.x, G, hint)) __nanosleep(200);
+                const int abort = warp_should_abort(ctl, t0) ? 1 : 0;
+                if (__syncthreads_or(abort)) {
+                    if (tid == 0) s_flag = 1;
+                    break;
+                }
+            }
         }
         __syncthreads();
         __threadfence();
-        if (s_fail) {
+        if (s_flag) {
             if (tid == 0) {
                 set_status(GLU_ERR_TIMEOUT);
                 atomicExch(&ctl->timeout, 1);
                 st_release(&W_.done[j], 1);  // never leave a later component waiting on us
+                atomicAdd(&ctl->finished[A.it], 1);
             }
             __syncthreads();
             continue;
         }
+        GLU_TRACE(A.it, j, 1);
 
         // 2. the distinct LR blocks Q of the component (stamps drop duplicates)
-        const unsigned long long tagQ = tagbase | (unsigned long long)(j + 1);
+        const unsigned long long tagQ = trial_tag(A.it, j, 0);
         for (int t = st.y + tid; t < en.y; t += kTrialThreads) {
             const int q = W_.qlist[t];
             if (atomicExch(&W_.stamp[q], tagQ) != tagQ) {
@@ -729,47 +1072,20 @@ __global__ void __launch_bounds__(kTrialThreads, 2) k_trials(const TrialArgs A) 
             store_rgb(A.lr, A.lr_pitch, qv, qu,
                       (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16));
         }
+        __threadfence();
         __syncthreads();
 
-        // 5. e0 / e1 over the affected pixels (STRICT: every block within r of Q; PAPER: the
-        //    component's own pixels), then 6. commit or roll back
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 1 && !s_accept) break;
-            const bool commit = pass == 1;
-            const unsigned long long tagB = (tagbase + ((unsigned long long)(pass + 1) << 40)) |
-                                            (unsigned long long)(j + 1);
-            for (int t = warp; t < nu; t += nwarps) {
-                const int q = W_.ulist[st.y + t];
-                const int qv = q / A.w, qu = q % A.w;
-                if (!A.strict) {
-                    float e0, e1;
-                    warp_block<S>(A, wins[warp], qv, qu, j, commit, e0, e1);
-                    if (!commit && lane == 0) {
-                        atomicAdd((unsigned long long*)&s_e0, (unsigned long long)to_fixed(e0));
-                        atomicAdd((unsigned long long*)&s_e1, (unsigned long long)to_fixed(e1));
-                    }
-                    continue;
-                }
-                for (int bv = max(0, qv - r); bv <= min(A.h - 1, qv + r); ++bv)
-                    for (int bu = max(0, qu - r); bu <= min(A.w - 1, qu + r); ++bu) {
-                        const int64_t b = (int64_t)bv * A.w + bu;
-                        int claimed = 0;
-                        if (lane == 0) claimed = atomicExch(&W_.stamp[b], tagB) != tagB;
-                        claimed = __shfl_sync(0xffffffffu, claimed, 0);
-                        if (!claimed) continue;
-                        float e0, e1;
-                        warp_block<S>(A, wins[warp], bv, bu, -1, commit, e0, e1);
-                        if (!commit && lane == 0) {
-                            atomicAdd((unsigned long long*)&s_e0, (unsigned long long)to_fixed(e0));
-                            atomicAdd((unsigned long long*)&s_e1, (unsigned long long)to_fixed(e1));
-                        }
-                    }
-            }
-            __syncthreads();
-            if (pass == 0 && tid == 0) s_accept = !(s_e1 > s_e0);
-            __syncthreads();
-        }
-        if (!s_accept) {
+        // 5. trial: Algorithm 1 again on the affected pixels (STRICT: every block within r of
+        //    Q; PAPER: the component's own pixels) into the shadow planes, summing e0 and e1
+        const int nitems = A.strict ? nu * NB : nu;
+        bool ok = run_task<S>(A, win, j, st.y, nu, 0, nitems, G, &s_e0, &s_e1, &s_flag, t0);
+        if (tid == 0) s_accept = !(s_e1 > s_e0);
+        __syncthreads();
+        GLU_TRACE(A.it, j, 2);
+        // 6. keep (nothing to do: the results are in place) or roll back: restore Theta and E
+        //    from the backup planes and the LR colours from their backups
+        if (!s_accept && ok) {
+            ok = run_task<S>(A, win, j, st.y, nu, 1, nitems, G, &s_e0, &s_e1, &s_flag, t0);
             for (int t = tid; t < nu; t += kTrialThreads) {
                 const int q = W_.ulist[st.y + t];
                 store_rgb(A.lr, A.lr_pitch, q / A.w, q % A.w, W_.backup[q]);
@@ -777,13 +1093,30 @@ __global__ void __launch_bounds__(kTrialThreads, 2) k_trials(const TrialArgs A) 
         }
         __syncthreads();
         if (tid == 0) {
+            if (!ok) {
+                set_status(GLU_ERR_TIMEOUT);
+                atomicExch(&ctl->timeout, 1);
+            }
             __threadfence();
             W_.dlog[(int64_t)A.it * W_.mcap + j] = (int8_t)(s_accept ? 1 : 0);
             if (s_accept) atomicAdd(&ctl->accepted[A.it], 1);
             else atomicAdd(&ctl->rolled[A.it], 1);
             st_release(&W_.done[j], 1);
+            atomicAdd(&ctl->finished[A.it], 1);
         }
+        GLU_TRACE(A.it, j, 3);
         __syncthreads();
+    }
+    // no component left to claim: help the running ones until every component is done
+    // (per warp; lane 0 decides)
+    const int lane = tid & 31;
+    int hint = -1;
+    for (;;) {
+        int fin = 0;
+        if (lane == 0) fin = *(volatile const int*)&ctl->finished[A.it] >= M;
+        if (__shfl_sync(0xffffffffu, fin, 0)) break;
+        if (!help_one<S>(A, win, blockIdx.x, G, hint)) __nanosleep(200);
+        if (warp_should_abort(ctl, t0)) break;
     }
 }
 
@@ -812,7 +1145,9 @@ static int launch_trials(const TrialArgs& A, cudaStream_t st) {
             return GLU_ERR_CUDA;
         blocks_per_sm = nb > 0 ? nb : 1;
     }
-    k_trials<S><<<sm_count() * blocks_per_sm, kTrialThreads, 0, st>>>(A);
+    int grid = sm_count() * blocks_per_sm;
+    if (grid > kMaxSlots) grid = kMaxSlots;
+    k_trials<S><<<grid, kTrialThreads, 0, st>>>(A);
     GLU_LAUNCH_CHECK();
     return GLU_OK;
 }
@@ -844,7 +1179,8 @@ int launch_joint(const JointArgs& a, void* wsp, size_t ws_bytes, glu_joint_stats
     const int T = 256;
 
     prof::mark(slot, evi++, st);
-    k_ctl_init<<<grid_cap(nl, T), T, 0, st>>>(ws.ctl, ws.stamp, nl);
+    k_ctl_init<<<grid_cap(nl > kMaxSlots ? nl : kMaxSlots, T), T, 0, st>>>(ws.ctl, ws.stamp, nl,
+                                                                          ws.slot_word);
     GLU_LAUNCH_CHECK();
     // initialise the LR image by regular grid downsampling, Theta and E by Algorithm 1
     glu_image hr{const_cast<uint8_t*>(a.hr), a.H, a.W, 3, GLU_U8, a.hr_pitch};
@@ -953,6 +1289,14 @@ int joint_decisions(const void* wsp, size_t ws_bytes, int H, int W, int s, int N
 }
 
 }  // namespace glu
+
+#ifdef GLU_TRIAL_TRACE
+extern "C" int glu_dbg_trace(unsigned long long* host, int64_t n) {
+    const size_t bytes = sizeof(unsigned long long) * (size_t)n;
+    if (bytes > sizeof(glu::g_trace)) return GLU_ERR_INVALID_ARG;
+    return cudaMemcpyFromSymbol(host, glu::g_trace, bytes) == cudaSuccess ? GLU_OK : GLU_ERR_CUDA;
+}
+#endif
 
 extern "C" int glu_joint_profile(int32_t enable) {
     using namespace glu;

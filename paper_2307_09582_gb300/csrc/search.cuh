@@ -21,28 +21,42 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
+// Window colour k from shared memory. An explicit shared load per use keeps the compiler from
+// holding the whole window in registers across both candidate loops (it is a broadcast read).
+__device__ __forceinline__ float4 lds_f4(const float4* p) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+    return v;
+}
+
 // Squared colour distance with a fixed operation order (so a = b evaluates identically in both
 // steps and uint8 inputs stay exact).
 __device__ __forceinline__ float dist2(float er, float eg, float eb) {
     return __fmaf_rn(eb, eb, __fmaf_rn(eg, eg, __fmul_rn(er, er)));
 }
 
-// win: window candidate (dy, dx) at win[dy * rs + dx] (float4: r, g, b, unused).
+// win: window candidate (dy, dx) at win[dy * rs + dx] (float4: r, g, b, unused), in shared
+// memory.
 // rowmask / colmask: bit i set when window row / column i lies inside the LR image.
 // Ties: a -> lowest k; b -> lowest k_b (strict comparisons in ascending k).
-template <int S>
+// kCompact: keep the window rows rolled (fewer registers, more resident warps) — used where
+// latency matters more than per-thread throughput. Both forms compute identical results.
+template <int S, bool kCompact = false>
 __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win, int rs,
                                                   uint32_t rowmask, uint32_t colmask, float ir,
                                                   float ig, float ib, float eps255, bool gnu) {
+    constexpr int kRowUnroll = (kCompact || S > 5) ? 1 : S;
     // Step 1: a = the window pixel with the most similar colour (squared distance, exact).
     float bd = kInf;
     int a = 0;
-#pragma unroll(S <= 5 ? S : 1)
+#pragma unroll(kRowUnroll)
     for (int dy = 0; dy < S; ++dy) {
 #pragma unroll
         for (int dx = 0; dx < S; ++dx) {
             const bool ok = ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
-            const float4 c = win[dy * rs + dx];
+            const float4 c = lds_f4(&win[dy * rs + dx]);
             const float d2 = dist2(c.x - ir, c.y - ig, c.z - ib);
             if (ok && d2 < bd) {
                 bd = d2;
@@ -50,7 +64,7 @@ __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win
             }
         }
     }
-    const float4 ca = win[(a / S) * rs + (a % S)];
+    const float4 ca = lds_f4(&win[(a / S) * rs + (a % S)]);
     const float ur = ca.x - ir, ug = ca.y - ig, ub = ca.z - ib;
     const float da = sqrt_approx(bd);
     SearchOut o;
@@ -68,12 +82,12 @@ __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win
     const float dae = da + eps255;
     float bnum = kInf, bden = 1.0f, bdb = 0.0f;
     int b = a;
-#pragma unroll(S <= 5 ? S : 1)
+#pragma unroll(kRowUnroll)
     for (int dy = 0; dy < S; ++dy) {
 #pragma unroll
         for (int dx = 0; dx < S; ++dx) {
             const bool ok = ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
-            const float4 c = win[dy * rs + dx];
+            const float4 c = lds_f4(&win[dy * rs + dx]);
             const float vr = c.x - ir, vg = c.y - ig, vb = c.z - ib;
             const float db = sqrt_approx(dist2(vr, vg, vb));
             const float xr = __fmaf_rn(db, ur, __fmul_rn(dae, vr));

@@ -30,6 +30,7 @@ def run_both(api, img, s, S, N, strict, conn=8):
     p = api.glu_params(S=S, N=N, joint=api.GLU_JOINT_STRICT if strict else api.GLU_JOINT_PAPER,
                        connectivity=conn)
     lr, theta, err, st = api.glu_joint_optimize(hr, s, p, decisions=True)
+    st["strict"] = strict
     torch.cuda.synchronize()
     assert api.glu_device_status() == 0
     ref = O.joint(img, s, S, N=N, strict=strict, conn=conn, force=st["decisions"],
@@ -45,8 +46,10 @@ def compare(api, img, s, S, N, strict, lr, theta, err, st, ref):
     ri = [it for it in ref["iters"] if it["n_large"] > 0]
     msg = f"\ngpu {gi}\nref {ri}"
     assert st["R0"] == pytest.approx(ref["R0"], rel=1e-6), msg
-    if not thr_ok:
-        pytest.skip("a pixel's error is within FP32 resolution of tau; exact replay not expected")
+    if not thr_ok or any(it["argmax_near_ties"] for it in ri):
+        # a decision within FP32 resolution that replay does not cover (E_p within 1e-6 of tau,
+        # or an argmax near-tie): check what holds for any correct run instead
+        return compare_properties(api, img, s, S, lr, theta, err, st, ref, msg)
     assert len(gi) == len(ri), msg
     for g, r in zip(gi, ri):
         assert (g["n_large"], g["M"], g["accepted"], g["rolled_back"]) == \
@@ -76,6 +79,37 @@ def compare(api, img, s, S, N, strict, lr, theta, err, st, ref):
         rep = dict(mismatches=int((~same).sum()))
     rep["replayed_decisions"] = replayed
     return rep
+
+
+def compare_properties(api, img, s, S, lr, theta, err, st, ref, msg):
+    """When the oracle reports argmax near-ties (a block where the largest error of a component
+    is within 1e-6 of another pixel's) or a pixel error within 1e-6 of tau, the GPU may
+    legitimately decide the other way and the runs diverge from there. Check what must hold
+    anyway: the first iteration's component count agrees within the number of such pixels; in
+    STRICT mode the GPU state satisfies the invariants; the final residuals agree to 1e-4
+    relative; the LR images differ in at most 0.1 % of the pixels, each differing LR pixel being
+    a pixel of its own block."""
+    gi, ri = st["iters"], [it for it in ref["iters"] if it["n_large"] > 0]
+    assert abs(gi[0]["n_large"] - ri[0]["n_large"]) <= 2, msg
+    hr = torch.from_numpy(img).cuda()
+    strict = st.get("strict", True)
+    if strict:
+        t2, e2 = api.glu_optimize(hr, lr, api.glu_params(S=S), s, err_map=True)
+        torch.cuda.synchronize()
+        assert torch.equal(t2.code, theta.code) and torch.equal(e2, err)
+    R = [st["R0"]] + [it["residual"] for it in gi]
+    if strict:
+        assert all(b <= a for a, b in zip(R, R[1:]))
+    assert R[-1] == pytest.approx(ri[-1]["residual"], rel=1e-4), msg
+    Lg, Lr = lr.cpu().numpy(), ref["L"]
+    ndiff = int((Lg != Lr).any(axis=2).sum())
+    assert ndiff <= max(10, Lg.shape[0] * Lg.shape[1] // 1000), f"{ndiff} LR pixels differ"
+    ys, xs = np.nonzero((Lg != Lr).any(axis=2))
+    for v, u in zip(ys[:200], xs[:200]):
+        blk = img[v * s:(v + 1) * s, u * s:(u + 1) * s].reshape(-1, 3)
+        assert np.any(np.all(blk == Lg[v, u], axis=1))
+    return dict(argmax_near_ties=sum(it["argmax_near_ties"] for it in ri), lr_pixels_differ=ndiff,
+                R_gpu=R[-1], R_oracle=ri[-1]["residual"])
 
 
 @pytest.mark.parametrize("H,W,s,S,strict", [

@@ -135,6 +135,23 @@ int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* par
                        glu_image* lr_out, glu_theta* theta, float* err_map,
                        glu_joint_stats* stats, void* ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of glu_joint_optimize (the paper has no counterpart: this is a
+ * deployment aid). For callers that cannot allocate device memory — a plug-in inside an
+ * application that owns every device allocation, or a streaming loop that must not risk the
+ * device-wide synchronisation cudaMalloc / cudaFree can cause — the workspace is a fixed
+ * GLU_JOINT_STATIC_BYTES array in the library's own device memory (held by every GPU that loads
+ * the library until the process exits). Arguments and results as glu_joint_optimize, minus the
+ * workspace. Returns GLU_ERR_WORKSPACE, before any launch, when glu_joint_workspace_size() for
+ * this image exceeds GLU_JOINT_STATIC_BYTES (about 1.3 megapixels at scale 8, 5x5 window, 5
+ * iterations). The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture. All calls on a device share
+ * the array (each call initialises what it reads); calls that overlap on the GPU race, so issue
+ * them one after another. Allocates nothing. */
+#define GLU_JOINT_STATIC_BYTES (64u << 20)
+int glu_joint_optimize_static(const glu_image* hr, int32_t scale, const glu_params* params,
+                              glu_image* lr_out, glu_theta* theta, float* err_map,
+                              glu_joint_stats* stats, void* stream);
+
 /* Workspace bytes glu_joint_optimize needs for an H x W image (0 on invalid arguments). */
 size_t glu_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params);
 

@@ -382,6 +382,46 @@ def measure_extras(api, torch, img, dev, flush, stream):
     return res
 
 
+def run_kernel_case(args):
+    """One kernel on an input larger than L2, a few launches (the target of an ncu capture):
+    search / apply / backward on a 7680x4320 guide at scale 8, window 5; trials = the joint 4K
+    workload (its first trial launch is iteration 1)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_09582_gb300 import api
+    from paper_2307_09582_gb300.inputs import Scene, joint_4k_scene, render_u8
+    dev = torch.device("cuda", 0)
+    if args.kernel_case == "trials":
+        img = render_u8(joint_4k_scene())
+        hr = torch.from_numpy(img).to(dev)
+        for _ in range(args.case_reps):
+            api.glu_joint_optimize(hr, SCALE, api.glu_params(S=WIN, N=NITER), stats=False)
+        torch.cuda.synchronize()
+        return 0
+    H, W = 4320, 7680
+    img = render_u8(Scene(width=W, height=H, n_cells=1600, n_dots=8000, n_lines=400, seed=7))
+    hr = torch.from_numpy(img).to(dev)
+    lr = api.glu_downsample(hr, SCALE, api.GLU_DOWN_GRID)
+    p = api.glu_params(S=WIN)
+    theta = api.Theta.empty(H, W, SCALE, WIN, api.GLU_W_UNORM16, dev)
+    err = torch.empty((H, W), dtype=torch.float32, device=dev)
+    h, w = api.lr_dims(H, W, SCALE)
+    T = torch.rand((h, w, 3), device=dev)
+    out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    api.glu_optimize(hr, lr, p, SCALE, theta=theta, err_map=err)
+    for _ in range(args.case_reps):
+        if args.kernel_case == "search":
+            api.glu_optimize(hr, lr, p, SCALE, theta=theta, err_map=err)
+        elif args.kernel_case == "apply":
+            api.glu_apply(theta, T, out=out)
+        elif args.kernel_case == "backward":
+            G = torch.randn((H, W, 3), device=dev)
+            api.glu_apply_backward(theta, T, G)
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,7 +430,12 @@ def main():
     ap.add_argument("--impl", default="glu", choices=["glu", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--kernel-case", choices=["search", "apply", "backward", "trials"],
+                    help="run one kernel on a profiling case and exit (no JSON line)")
+    ap.add_argument("--case-reps", type=int, default=3)
     args = ap.parse_args()
+    if args.kernel_case:
+        return run_kernel_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -109,7 +109,7 @@ int glu_optimize(const glu_image* hr, const glu_image* lr, const glu_params* par
     a.w = lr->w;
     a.s = s;
     a.S = params->S;
-    a.eps255 = params->eps * 255.0f;
+    a.eps255 = fmaxf(params->eps * 255.0f, 1e-12f);  // > 0: see search.cuh
     a.gnu = params->mode == GLU_MODE_GNU;
     a.code = theta->code;
     a.weight = theta->weight;
@@ -217,7 +217,7 @@ int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* par
     a.w = lr_out->w;
     a.s = scale;
     a.S = params->S;
-    a.eps255 = params->eps * 255.0f;
+    a.eps255 = fmaxf(params->eps * 255.0f, 1e-12f);  // > 0: see search.cuh
     a.tau = params->tau;
     a.N = params->N;
     a.strict = params->joint == GLU_JOINT_STRICT;

@@ -69,6 +69,154 @@ __global__ void k_apply(const ApplyArgs P) {
     }
 }
 
+// Exact integer quotient n / d for 0 <= n < 2^13 and d <= 81 (pair codes, window indices):
+// (n + 0.5) / d stays at least 0.5 / d away from an integer, far above the float error.
+__device__ __forceinline__ int qdiv(int n, float inv_d) {
+    return __float2int_rd(((float)n + 0.5f) * inv_d);
+}
+
+template <int WF> struct W4;
+template <> struct W4<GLU_W_F32> {
+    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
+        const float4 v = __ldcs((const float4*)b + (p >> 2));
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+};
+template <> struct W4<GLU_W_F16> {
+    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
+        const uint2 v = __ldcs((const uint2*)b + (p >> 2));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+        const float2 c = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+        w[0] = a.x; w[1] = a.y; w[2] = c.x; w[3] = c.y;
+    }
+};
+template <> struct W4<GLU_W_UNORM16> {
+    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
+        const uint2 v = __ldcs((const uint2*)b + (p >> 2));
+        w[0] = (float)(v.x & 0xFFFFu) * (1.0f / 65535.0f);
+        w[1] = (float)(v.x >> 16) * (1.0f / 65535.0f);
+        w[2] = (float)(v.y & 0xFFFFu) * (1.0f / 65535.0f);
+        w[3] = (float)(v.y >> 16) * (1.0f / 65535.0f);
+    }
+};
+
+// Eq. 1 fast path, tiled: a CTA owns kApplyTH x kApplyTW HR pixels; the LR region its windows
+// reach is copied to shared memory with coalesced row loads, so the 8 gathers per 4 pixels
+// are shared-memory reads. Codes and weights stream in as one 8-/16-byte load per 4 pixels,
+// results leave as three 16-byte streaming stores. Conditions as for k_apply3_vec.
+constexpr int kApplyTW = 128, kApplyTH = 8;
+template <int WF>
+__global__ void __launch_bounds__(256) k_apply3_tile(const ApplyArgs P) {
+    extern __shared__ float reg[];   // RH x RW x 3
+    const int x0 = blockIdx.x * kApplyTW, y0 = blockIdx.y * kApplyTH;
+    const int s = P.s, S = P.S, r = (S - 1) >> 1, K = S * S;
+    const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + kApplyTH, P.H);
+    const int v0 = y0 / s - r, u0 = x0 / s - r;
+    const int RH = (ye - 1) / s + r - v0 + 1, RW = (xe - 1) / s + r - u0 + 1;
+    const float* T = (const float*)P.T;
+    // the LR region, clamped to the image (entries outside it are never selected by a valid code)
+    for (int i = threadIdx.x; i < RH * RW * 3; i += blockDim.x) {
+        const int rr = i / (RW * 3), cc = i - rr * (RW * 3);
+        const int v = min(max(v0 + rr, 0), P.h - 1);
+        const int u = min(max(u0 + cc / 3, 0), P.w - 1);
+        reg[i] = __ldg(T + (int64_t)v * P.T_pitch + (int64_t)u * 3 + cc % 3);
+    }
+    __syncthreads();
+    const int ty = threadIdx.x >> 5, xg = (threadIdx.x & 31) * 4;
+    const int y = y0 + ty, xs = x0 + xg;
+    if (y >= P.H || xs >= P.W) return;
+    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
+    const int64_t p0 = (int64_t)y * P.W + xs;
+    const uint2 cc = __ldcs((const uint2*)P.code + (p0 >> 2));
+    const int code[4] = {(int)(cc.x & 0xFFFFu), (int)(cc.x >> 16), (int)(cc.y & 0xFFFFu),
+                         (int)(cc.y >> 16)};
+    float w[4];
+    W4<WF>::load(P.weight, p0, w);
+    const int rrow = y / s - r - v0;   // region row of the window's top row
+    float res[12];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int rcol = (xs + j) / s - r - u0;
+        const int ka = qdiv(code[j], invK), kb = code[j] - ka * K;
+        const int ra = qdiv(ka, invS), rb = qdiv(kb, invS);
+        int ia = ((rrow + ra) * RW + rcol + (ka - ra * S)) * 3;
+        int ib = ((rrow + rb) * RW + rcol + (kb - rb * S)) * 3;
+        // codes from the search never leave the LR image; anything else is recorded
+        const int va = y / s + ra - r, ua = (xs + j) / s + (ka - ra * S) - r;
+        const int vb = y / s + rb - r, ub = (xs + j) / s + (kb - rb * S) - r;
+        if ((unsigned)va >= (unsigned)P.h || (unsigned)ua >= (unsigned)P.w || ka >= K) {
+            set_status(GLU_ERR_DEVICE_CHECK);
+            ia = 0;
+        }
+        if ((unsigned)vb >= (unsigned)P.h || (unsigned)ub >= (unsigned)P.w || kb >= K) {
+            set_status(GLU_ERR_DEVICE_CHECK);
+            ib = 0;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float ta = reg[ia + c], tb = reg[ib + c];
+            res[j * 3 + c] = __fmaf_rn(w[j], ta - tb, tb);
+        }
+    }
+    float4* o = (float4*)((float*)P.out + (int64_t)y * P.out_pitch + (int64_t)xs * 3);
+    __stcs(o + 0, make_float4(res[0], res[1], res[2], res[3]));
+    __stcs(o + 1, make_float4(res[4], res[5], res[6], res[7]));
+    __stcs(o + 2, make_float4(res[8], res[9], res[10], res[11]));
+}
+
+// Eq. 1 fast path for 3-channel float32 targets and outputs with W % 4 == 0 and 16-byte
+// aligned rows: one thread per 4 consecutive pixels; codes and weights arrive as one 8- or
+// 16-byte streaming load each, the 8 LR gathers go through the read-only path (the LR target
+// is small and stays in L1/L2), the 12 results leave as three 16-byte streaming stores.
+template <int WF>
+__global__ void __launch_bounds__(256) k_apply3_vec(const ApplyArgs P) {
+    const int G4 = P.W >> 2;
+    const int64_t total = (int64_t)G4 * P.H;
+    const int S = P.S, r = (P.S - 1) >> 1, K = P.S * P.S;
+    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
+    const float* T = (const float*)P.T;
+    float* out = (float*)P.out;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(g / G4), x0 = (int)(g - (int64_t)y * G4) * 4;
+        const int64_t p0 = (int64_t)y * P.W + x0;
+        const uint2 cc = __ldcs((const uint2*)P.code + (p0 >> 2));
+        const int code[4] = {(int)(cc.x & 0xFFFFu), (int)(cc.x >> 16), (int)(cc.y & 0xFFFFu),
+                             (int)(cc.y >> 16)};
+        float w[4];
+        W4<WF>::load(P.weight, p0, w);
+        const int py = y / P.s;
+        float res[12];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int px = (x0 + j) / P.s;
+            const int ka = qdiv(code[j], invK), kb = code[j] - ka * K;
+            const int ra = qdiv(ka, invS), rb = qdiv(kb, invS);
+            const int va = py + ra - r, ua = px + (ka - ra * S) - r;
+            const int vb = py + rb - r, ub = px + (kb - rb * S) - r;
+            int64_t oa = (int64_t)va * P.T_pitch + (int64_t)ua * 3;
+            int64_t ob = (int64_t)vb * P.T_pitch + (int64_t)ub * 3;
+            if ((unsigned)va >= (unsigned)P.h || (unsigned)ua >= (unsigned)P.w || ka >= K) {
+                set_status(GLU_ERR_DEVICE_CHECK);
+                oa = 0;
+            }
+            if ((unsigned)vb >= (unsigned)P.h || (unsigned)ub >= (unsigned)P.w || kb >= K) {
+                set_status(GLU_ERR_DEVICE_CHECK);
+                ob = 0;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float ta = __ldg(T + oa + c), tb = __ldg(T + ob + c);
+                res[j * 3 + c] = __fmaf_rn(w[j], ta - tb, tb);
+            }
+        }
+        float4* o = (float4*)(out + (int64_t)y * P.out_pitch + (int64_t)x0 * 3);
+        __stcs(o + 0, make_float4(res[0], res[1], res[2], res[3]));
+        __stcs(o + 1, make_float4(res[4], res[5], res[6], res[7]));
+        __stcs(o + 2, make_float4(res[8], res[9], res[10], res[11]));
+    }
+}
+
 template <int C>
 __global__ void k_apply_backward_lr(const BackwardArgs P) {
     const int lane = threadIdx.x & 31;
@@ -143,6 +291,52 @@ static int grid_for(int64_t work, int threads) {
 int launch_apply(const ApplyArgs& a, cudaStream_t st) {
     if (a.H <= 0 || a.W <= 0) return GLU_OK;
     const int threads = 256;
+    const size_t wsz = a.wfmt == GLU_W_F32 ? 16 : 8;
+    const bool vec = a.C == 3 && a.T_dtype == GLU_F32 && a.out_dtype == GLU_F32 && a.W % 4 == 0 &&
+                     a.out_pitch % 4 == 0 && ((uintptr_t)a.out & 15u) == 0 &&
+                     ((uintptr_t)a.code & 7u) == 0 && ((uintptr_t)a.weight & (wsz - 1)) == 0;
+#ifndef GLU_APPLY_TILED
+#define GLU_APPLY_TILED 1
+#endif
+    if (vec && GLU_APPLY_TILED) {
+        const int r = (a.S - 1) / 2;
+        const int rh = (kApplyTH - 1) / a.s + 2 + 2 * r, rw = (kApplyTW - 1) / a.s + 2 + 2 * r;
+        const size_t smem = sizeof(float) * 3 * (size_t)rh * rw;
+        dim3 grid((a.W + kApplyTW - 1) / kApplyTW, (a.H + kApplyTH - 1) / kApplyTH);
+        auto launch = [&](auto kern) -> int {
+            if (smem > 48 * 1024 &&
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                    cudaSuccess)
+                return GLU_ERR_CUDA;
+            kern<<<grid, threads, smem, st>>>(a);
+            return GLU_OK;
+        };
+        int rc;
+        switch (a.wfmt) {
+            case GLU_W_F32: rc = launch(k_apply3_tile<GLU_W_F32>); break;
+            case GLU_W_F16: rc = launch(k_apply3_tile<GLU_W_F16>); break;
+            default: rc = launch(k_apply3_tile<GLU_W_UNORM16>); break;
+        }
+        if (rc) return rc;
+        GLU_LAUNCH_CHECK();
+        return GLU_OK;
+    }
+    if (vec) {
+        const int64_t work = (int64_t)(a.W / 4) * a.H;
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int64_t blocks = (work + threads - 1) / threads;
+        const int64_t cap = (int64_t)sms * 32;
+        const int grid = (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+        switch (a.wfmt) {
+            case GLU_W_F32: k_apply3_vec<GLU_W_F32><<<grid, threads, 0, st>>>(a); break;
+            case GLU_W_F16: k_apply3_vec<GLU_W_F16><<<grid, threads, 0, st>>>(a); break;
+            default: k_apply3_vec<GLU_W_UNORM16><<<grid, threads, 0, st>>>(a); break;
+        }
+        GLU_LAUNCH_CHECK();
+        return GLU_OK;
+    }
     const int64_t work = (int64_t)((a.W + 3) / 4) * a.H;
     const int grid = grid_for(work, threads);
     switch (a.C) {

@@ -17,9 +17,18 @@ namespace glu {
 
 GLU_DEFINE_STATUS(search)
 
+// Occupancy target (CTAs per SM) and the rolled search variant: build-time tuning knobs.
+#ifndef GLU_SEARCH_MINBLOCKS
+#define GLU_SEARCH_MINBLOCKS 3
+#endif
+#ifndef GLU_SEARCH_COMPACT
+#define GLU_SEARCH_COMPACT 0
+#endif
+
 constexpr int kTileW = 64;   // HR pixels per tile row (64 * 3 channels: a 16-byte multiple)
 constexpr int kTileH = 16;   // HR rows per tile
 constexpr int kThreads = 256;
+static_assert(kThreads % kTileW == 0, "a thread keeps one tile column");
 
 template <typename HT>
 struct HrTile {
@@ -27,7 +36,7 @@ struct HrTile {
 };
 
 template <int S, typename HT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, GLU_SEARCH_MINBLOCKS)
     k_search(const __grid_constant__ CUtensorMap hr_map, const SearchArgs P, const int use_tma) {
     __shared__ HrTile<HT> tile;
     __shared__ alignas(8) uint64_t bar;
@@ -87,18 +96,29 @@ __global__ void __launch_bounds__(kThreads, 2)
         return;
     }
 
-    for (int i = tid; i < kTileH * kTileW; i += kThreads) {
-        const int ty = i / kTileW, tx = i % kTileW;
-        const int y = y0 + ty, x = x0 + tx;
+    // interior tiles (every window inside the LR image) skip the validity masks
+    const bool interior = v0 >= 0 && u0 >= 0 && (ye - 1) / s + r < P.h && (xe - 1) / s + r < P.w;
+    // a thread keeps one column of the tile (kThreads is a multiple of kTileW) and walks rows
+    const int tx = tid % kTileW, x = x0 + tx, px = x / s;
+    const int col = px - r - u0;
+    for (int ty = tid / kTileW; ty < kTileH; ty += kThreads / kTileW) {
+        const int y = y0 + ty;
         if (y >= P.H || x >= P.W) continue;
         const float ir = Px<HT>::to255(tile.px[ty][tx * 3 + 0]);
         const float ig = Px<HT>::to255(tile.px[ty][tx * 3 + 1]);
         const float ib = Px<HT>::to255(tile.px[ty][tx * 3 + 2]);
-        const int py = y / s, px = x / s;
-        uint32_t rm, cm;
-        window_masks(py, px, P.h, P.w, S, rm, cm);
-        const float4* win = &region[(py - r - v0) * RW + (px - r - u0)];
-        const SearchOut o = search_pixel<S>(win, RW, rm, cm, ir, ig, ib, P.eps255, P.gnu != 0);
+        const int py = y / s;
+        const float4* win = &region[(py - r - v0) * RW + col];
+        SearchOut o;
+        if (interior) {
+            o = search_pixel<S, GLU_SEARCH_COMPACT != 0, true>(win, RW, 0u, 0u, ir, ig, ib, P.eps255,
+                                                               P.gnu != 0);
+        } else {
+            uint32_t rm, cm;
+            window_masks(py, px, P.h, P.w, S, rm, cm);
+            o = search_pixel<S, GLU_SEARCH_COMPACT != 0>(win, RW, rm, cm, ir, ig, ib, P.eps255,
+                                                         P.gnu != 0);
+        }
         const int64_t p = (int64_t)y * P.W + x;
         P.code[p] = (uint16_t)(o.ka * S * S + o.kb);
         store_weight(P.weight, P.wfmt, p, o.omega);

@@ -38,16 +38,21 @@ __device__ __forceinline__ float dist2(float er, float eg, float eb) {
 }
 
 // win: window candidate (dy, dx) at win[dy * rs + dx] (float4: r, g, b, unused), in shared
-// memory.
-// rowmask / colmask: bit i set when window row / column i lies inside the LR image.
+// memory. rowmask / colmask: bit i set when window row / column i lies inside the LR image
+// (ignored when kInterior: the caller guarantees the whole window is inside).
+// eps255 must be > 0 (the library clamps eps = 0 to a negligible positive value), so the
+// Eq. 5 denominator never vanishes.
 // Ties: a -> lowest k; b -> lowest k_b (strict comparisons in ascending k).
-// kCompact: keep the window rows rolled (fewer registers, more resident warps) — used where
-// latency matters more than per-thread throughput. Both forms compute identical results.
-template <int S, bool kCompact = false>
+// kCompact: keep the window rows rolled (fewer registers, more resident warps). Every variant
+// computes bit-identical results: the same operations on the same values.
+template <int S, bool kCompact = false, bool kInterior = false>
 __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win, int rs,
                                                   uint32_t rowmask, uint32_t colmask, float ir,
                                                   float ig, float ib, float eps255, bool gnu) {
+    constexpr int K = S * S;
     constexpr int kRowUnroll = (kCompact || S > 5) ? 1 : S;
+    constexpr bool kKeep = !kCompact && S <= 3;   // keep step 1's distances for step 2
+    float d2s[kKeep ? K : 1];
     // Step 1: a = the window pixel with the most similar colour (squared distance, exact).
     float bd = kInf;
     int a = 0;
@@ -55,9 +60,10 @@ __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win
     for (int dy = 0; dy < S; ++dy) {
 #pragma unroll
         for (int dx = 0; dx < S; ++dx) {
-            const bool ok = ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
+            const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
             const float4 c = lds_f4(&win[dy * rs + dx]);
             const float d2 = dist2(c.x - ir, c.y - ig, c.z - ib);
+            if constexpr (kKeep) d2s[dy * S + dx] = d2;
             if (ok && d2 < bd) {
                 bd = d2;
                 a = dy * S + dx;
@@ -80,34 +86,39 @@ __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win
     // uses D * r = d_b u + (d_a + eps) v and D = d_a + d_b + eps: err^2 = |D r|^2 / D^2,
     // compared by cross-multiplication so no candidate needs a division.
     const float dae = da + eps255;
-    float bnum = kInf, bden = 1.0f, bdb = 0.0f;
+    float bnum = kInf, bden = 1.0f;
     int b = a;
 #pragma unroll(kRowUnroll)
     for (int dy = 0; dy < S; ++dy) {
 #pragma unroll
         for (int dx = 0; dx < S; ++dx) {
-            const bool ok = ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
+            const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
             const float4 c = lds_f4(&win[dy * rs + dx]);
             const float vr = c.x - ir, vg = c.y - ig, vb = c.z - ib;
-            const float db = sqrt_approx(dist2(vr, vg, vb));
+            float d2b;
+            if constexpr (kKeep) d2b = d2s[dy * S + dx];
+            else d2b = dist2(vr, vg, vb);
+            const float db = sqrt_approx(d2b);
             const float xr = __fmaf_rn(db, ur, __fmul_rn(dae, vr));
             const float xg = __fmaf_rn(db, ug, __fmul_rn(dae, vg));
             const float xb = __fmaf_rn(db, ub, __fmul_rn(dae, vb));
             const float num = dist2(xr, xg, xb);
             const float D = __fadd_rn(db, dae);
-            const float den = fmaxf(__fmul_rn(D, D), 1e-30f);
+            const float den = __fmul_rn(D, D);
             if (ok && __fmul_rn(num, bden) < __fmul_rn(bnum, den)) {
                 bnum = num;
                 bden = den;
-                bdb = db;
                 b = dy * S + dx;
             }
         }
     }
     o.kb = b;
+    // the winner's d_b again (same operations on the same values as in the loop)
+    const float4 cb = lds_f4(&win[(b / S) * rs + (b % S)]);
+    const float bdb = sqrt_approx(dist2(cb.x - ir, cb.y - ig, cb.z - ib));
     const float wden = bdb + dae;
-    o.omega = wden > 0.0f ? bdb / wden : 1.0f;
-    o.err = sqrtf(bnum / bden) * (1.0f / 255.0f);
+    o.omega = __fdividef(bdb, wden);
+    o.err = sqrt_approx(__fdividef(bnum, bden)) * (1.0f / 255.0f);
     return o;
 }
 

@@ -178,3 +178,23 @@ def test_plain_256_pipeline_against_oracle_theta(api):
     assert d[same].max() < 1e-3
     # self-upsampling error of the GPU result against FP64 (reported)
     print(f"\nplain 256: {rep}, max |T_hat - oracle| {d[same].max():.2e}")
+
+
+@pytest.mark.parametrize("wfmt", [0, 1, 2])
+def test_apply_vector_path_parity(api, wfmt):
+    # W % 4 == 0, float32 3-channel target/output: the 4-pixel vector path of Eq. 1
+    H, W, s, S = 200, 320, 8, 5
+    img = scene_img(21, H, W)
+    hr = dev(img)
+    lr = api.glu_downsample(hr, s, api.GLU_DOWN_GRID)
+    theta, _ = api.glu_optimize(hr, lr, api.glu_params(S=S), s, wfmt=wfmt)
+    h, w = api.lr_dims(H, W, s)
+    T = torch.rand((h, w, 3), generator=torch.Generator().manual_seed(5)).cuda()
+    out = api.glu_apply(theta, T)
+    torch.cuda.synchronize()
+    assert api.glu_device_status() == 0
+    codes = theta.codes_i32().cpu().numpy()
+    K = S * S
+    ref = O.apply(codes // K, codes % K, theta.weight_f32().cpu().numpy().astype(np.float64),
+                  s, S, T.cpu().numpy().astype(np.float64))
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-6

@@ -24,6 +24,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 H4K, W4K, SCALE, WIN, NITER = 2160, 3840, 8, 5, 5
+BATCH_NITER = 3
 METRIC = "HR Mpix/s for GLU optimise+apply at 4K x8; batched/bwd vs plain; % of roofline"
 WORKLOAD = "joint-optimise+LRop+apply 3840x2160 x8, 5x5 window, 5 Alg.2 iterations, STRICT"
 # canonical FP32 lane operations of Algorithm 1 per window candidate (a-step 7, b-step 20)
@@ -379,7 +380,44 @@ def measure_extras(api, torch, img, dev, flush, stream):
     ms_b = timed(lambda: api.glu_apply_backward(theta, T, G, grad_lr=gT, grad_w=gw))
     res["backward_ms"] = ms_b
     res["backward_vs_apply"] = ms_b / ms_a
+    res["batch16"] = measure_batch(api, torch, dev, timed)
     return res
+
+
+def measure_batch(api, torch, dev, timed):
+    """The 16-image batch (uneven sizes, scales {4, 8, 16}, windows {3, 5}, 3 iterations of
+    Algorithm 2): all of them in one batched call against 16 single-image calls, same outputs
+    and workspace."""
+    from paper_2307_09582_gb300.inputs import render_u8
+    from paper_2307_09582_gb300.inputs.workloads import batch_scenes
+    items = [(render_u8(sc), s, S) for sc, s, S in batch_scenes()]
+    hrs = [torch.from_numpy(i).to(dev) for i, _, _ in items]
+    scales = [s for _, s, _ in items]
+    Ss = [S for _, _, S in items]
+    p = api.glu_params(N=BATCH_NITER)
+    ps = [api.glu_params(S=S, N=BATCH_NITER) for S in Ss]
+    lrs = [torch.empty((*api.lr_dims(h.shape[0], h.shape[1], s), 3), dtype=torch.uint8,
+                       device=dev) for h, s in zip(hrs, scales)]
+    thetas = [api.Theta.empty(h.shape[0], h.shape[1], s, S, api.GLU_W_UNORM16, dev)
+              for h, s, S in zip(hrs, scales, Ss)]
+    need = api.glu_joint_batched_workspace_size([h.shape[:2] for h in hrs], scales, Ss, p)
+    wsb = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+
+    def batched():
+        api.glu_joint_optimize_batched(hrs, scales, p, Ss, lrs=lrs, thetas=thetas,
+                                       err_maps=False, stats=False, workspace=wsb)
+
+    def sequential():
+        for k in range(len(hrs)):
+            api.glu_joint_optimize(hrs[k], scales[k], ps[k], lr_out=lrs[k], theta=thetas[k],
+                                   err_map=False, stats=False, workspace=wsb)
+
+    npx = sum(h.shape[0] * h.shape[1] for h in hrs)
+    mb = timed(batched, reps=5)
+    msq = timed(sequential, reps=5)
+    return dict(images=len(hrs), mpix=npx / 1e6, batched_ms=mb, sequential_ms=msq,
+                batched_mpix_s=npx / mb / 1e3, sequential_mpix_s=npx / msq / 1e3,
+                speedup=msq / mb)
 
 
 def run_kernel_case(args):

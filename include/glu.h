@@ -163,6 +163,35 @@ size_t glu_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_p
 int64_t glu_joint_decisions(const void* ws, size_t ws_bytes, int32_t H, int32_t W, int32_t scale,
                             const glu_params* params, int8_t* out, int64_t cap, void* stream);
 
+/* One image of a batched call (all pointers device memory). */
+typedef struct {
+    glu_image hr;       /* guide; U8 (or F16 for glu_optimize_batched), c = 3 */
+    glu_image lr;       /* LR image: read by glu_optimize_batched, written by the joint call */
+    glu_theta theta;    /* scale, S and wfmt per item; code and weight are written */
+    float* err_map;     /* nullable, as for glu_optimize */
+} glu_batch_item;
+
+/* Algorithm 1 over n images of different sizes, scales and windows in one persistent launch
+ * (per 32 images): every item's result equals a glu_optimize call on it alone. Each item's
+ * window is item.theta.S (params->S is not used); eps and mode come from params. Every item must
+ * share the guide dtype and theta.wfmt (GLU_ERR_UNSUPPORTED otherwise). n = 0 is a no-op. */
+int glu_optimize_batched(const glu_batch_item* items, int32_t n, const glu_params* params,
+                         void* stream);
+
+/* Algorithm 2 over n <= 32 images in one set of launches: every item's LR image, Theta, error
+ * map and statistics equal a glu_joint_optimize call on it alone (each image keeps its own
+ * large-error sets, components, residuals and stopping rule). Each item's window is
+ * item.theta.S; eps, tau, N, joint mode and connectivity come from params; all items share
+ * theta.wfmt. stats: HOST array of n records, or null. ws: at least
+ * glu_joint_batched_workspace_size() bytes, 256-byte aligned. */
+int glu_joint_optimize_batched(const glu_batch_item* items, int32_t n, const glu_params* params,
+                               glu_joint_stats* stats, void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace bytes glu_joint_optimize_batched needs (0 on invalid arguments). Reads only the
+ * items' sizes and scales. */
+size_t glu_joint_batched_workspace_size(const glu_batch_item* items, int32_t n,
+                                        const glu_params* params);
+
 /* Benchmark instrumentation (not part of the method). glu_joint_profile(1) makes later
  * glu_joint_optimize calls record CUDA events on their stream around their phases; the events
  * of up to 64 calls are kept. glu_joint_profile_read() waits for them, writes the summed

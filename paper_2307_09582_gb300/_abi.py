@@ -54,6 +54,11 @@ class GluJointStats(ctypes.Structure):
                 ("searched", ctypes.c_int64 * GLU_MAX_ITERS)]
 
 
+class GluBatchItem(ctypes.Structure):
+    _fields_ = [("hr", GluImage), ("lr", GluImage), ("theta", GluTheta),
+                ("err_map", ctypes.c_void_p)]
+
+
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -68,6 +73,11 @@ PROTOTYPES = {
                                           _P(GluTheta), _vp, _P(GluJointStats), _vp,
                                           ctypes.c_size_t, _vp]),
     "glu_joint_workspace_size": (ctypes.c_size_t, [_i32, _i32, _i32, _P(GluParams)]),
+    "glu_optimize_batched": (ctypes.c_int, [_P(GluBatchItem), _i32, _P(GluParams), _vp]),
+    "glu_joint_optimize_batched": (ctypes.c_int, [_P(GluBatchItem), _i32, _P(GluParams),
+                                                  _P(GluJointStats), _vp, ctypes.c_size_t, _vp]),
+    "glu_joint_batched_workspace_size": (ctypes.c_size_t, [_P(GluBatchItem), _i32,
+                                                           _P(GluParams)]),
     "glu_apply": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _vp]),
     "glu_apply_backward": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _P(GluImage),
                                           _vp, _vp]),

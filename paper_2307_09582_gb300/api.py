@@ -171,15 +171,89 @@ def glu_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
     else:
         decisions = None
     if st is not None:
-        n = st.iterations
-        sd = dict(iterations=n, R0=st.residual[0],
-                  iters=[dict(n_large=st.n_large[k], M=st.components[k],
-                              accepted=st.accepted[k], rolled_back=st.rolled_back[k],
-                              residual=st.residual[k + 1], searched=st.searched[k])
-                         for k in range(n)],
-                  n_large_next=st.n_large[n] if n < A.GLU_MAX_ITERS else 0,
-                  decisions=decisions)
+        sd = _stats_dict(st, decisions)
     return lr_out, theta, err_map, sd
+
+
+def _stats_dict(st: A.GluJointStats, decisions=None) -> dict:
+    n = st.iterations
+    return dict(iterations=n, R0=st.residual[0],
+                iters=[dict(n_large=st.n_large[k], M=st.components[k],
+                            accepted=st.accepted[k], rolled_back=st.rolled_back[k],
+                            residual=st.residual[k + 1], searched=st.searched[k])
+                       for k in range(n)],
+                n_large_next=st.n_large[n] if n < A.GLU_MAX_ITERS else 0,
+                decisions=decisions)
+
+
+def _aligned(workspace: torch.Tensor):
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    return aligned, workspace.numel() - (aligned - base)
+
+
+def _batch_items(hrs, lrs, thetas, errs):
+    items = (A.GluBatchItem * max(1, len(hrs)))()
+    for k, (hr, lr, th, e) in enumerate(zip(hrs, lrs, thetas, errs)):
+        items[k].hr = image(hr)
+        items[k].lr = image(lr)
+        items[k].theta = th.desc()
+        items[k].err_map = _ptr(e)
+    return items
+
+
+def glu_optimize_batched(hrs, lrs, params: A.GluParams, scales, Ss=None, thetas=None,
+                         err_maps: bool = True, wfmt: int = A.GLU_W_F32, stream=None):
+    """Algorithm 1 on several images in one persistent launch. scales / Ss: one per image (Ss
+    defaults to params.S). Returns [(theta, err_map or None)]."""
+    n = len(hrs)
+    Ss = [params.S] * n if Ss is None else list(Ss)
+    if thetas is None:
+        thetas = [Theta.empty(hr.shape[0], hr.shape[1], s, S, wfmt, hr.device)
+                  for hr, s, S in zip(hrs, scales, Ss)]
+    errs = [torch.empty(hr.shape[:2], dtype=torch.float32, device=hr.device) if err_maps else None
+            for hr in hrs]
+    items = _batch_items(hrs, lrs, thetas, errs)
+    A.check("glu_optimize_batched", lib().glu_optimize_batched(items, n, ctypes.byref(params),
+                                                               _stream(stream)))
+    return list(zip(thetas, errs))
+
+
+def glu_joint_batched_workspace_size(shapes, scales, Ss, params: A.GluParams) -> int:
+    """shapes: [(H, W)] per image."""
+    items = (A.GluBatchItem * max(1, len(shapes)))()
+    for k, ((H, W), s, S) in enumerate(zip(shapes, scales, Ss)):
+        items[k].hr.h, items[k].hr.w = H, W
+        items[k].theta.scale, items[k].theta.S = s, S
+    return int(lib().glu_joint_batched_workspace_size(items, len(shapes), ctypes.byref(params)))
+
+
+def glu_joint_optimize_batched(hrs, scales, params: A.GluParams, Ss=None, lrs=None, thetas=None,
+                               err_maps: bool = True, stats: bool = True,
+                               workspace: torch.Tensor | None = None,
+                               wfmt: int = A.GLU_W_F32, stream=None):
+    """Algorithm 2 on up to 32 images in one set of launches. Returns
+    [(lr, theta, err_map or None, stats dict or None)] in input order."""
+    n = len(hrs)
+    Ss = [params.S] * n if Ss is None else list(Ss)
+    if lrs is None:
+        lrs = [torch.empty((*lr_dims(hr.shape[0], hr.shape[1], s), 3), dtype=torch.uint8,
+                           device=hr.device) for hr, s in zip(hrs, scales)]
+    if thetas is None:
+        thetas = [Theta.empty(hr.shape[0], hr.shape[1], s, S, wfmt, hr.device)
+                  for hr, s, S in zip(hrs, scales, Ss)]
+    errs = [torch.empty(hr.shape[:2], dtype=torch.float32, device=hr.device) if err_maps else None
+            for hr in hrs]
+    need = glu_joint_batched_workspace_size([hr.shape[:2] for hr in hrs], scales, Ss, params)
+    if workspace is None or workspace.numel() < need + 256:
+        workspace = torch.empty(need + 256, dtype=torch.uint8, device=hrs[0].device)
+    aligned, avail = _aligned(workspace)
+    items = _batch_items(hrs, lrs, thetas, errs)
+    st = (A.GluJointStats * max(1, n))() if stats else None
+    A.check("glu_joint_optimize_batched", lib().glu_joint_optimize_batched(
+        items, n, ctypes.byref(params), st, ctypes.c_void_p(aligned), avail, _stream(stream)))
+    return [(lrs[k], thetas[k], errs[k], _stats_dict(st[k]) if st is not None else None)
+            for k in range(n)]
 
 
 def glu_apply(theta: Theta, lr_target: torch.Tensor, out: torch.Tensor | None = None,

@@ -230,3 +230,135 @@ int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* par
 }
 
 }  // extern "C"
+
+namespace {
+
+// Checks shared by the batched entry points; fills the launcher's item.
+int search_item(const glu_batch_item& it, const glu_params* p, SearchArgs* a) {
+    const glu_image* hr = &it.hr;
+    const glu_image* lr = &it.lr;
+    const glu_theta* th = &it.theta;
+    if (!image_ok(hr) || !image_ok(lr) || !theta_ok(th)) return GLU_ERR_INVALID_ARG;
+    if (hr->c != 3 || lr->c != 3) return GLU_ERR_UNSUPPORTED;
+    if (hr->dtype != GLU_U8 && hr->dtype != GLU_F16) return GLU_ERR_UNSUPPORTED;
+    const int s = th->scale;
+    if (th->H != hr->h || th->W != hr->w || lr->h != lr_dim(hr->h, s) ||
+        lr->w != lr_dim(hr->w, s))
+        return GLU_ERR_SHAPE;
+    a->hr = hr->data;
+    a->hr_pitch = hr->pitch;
+    a->hr_dtype = hr->dtype;
+    a->lr = lr->data;
+    a->lr_pitch = lr->pitch;
+    a->lr_dtype = lr->dtype;
+    a->H = hr->h;
+    a->W = hr->w;
+    a->h = lr->h;
+    a->w = lr->w;
+    a->s = s;
+    a->S = th->S;
+    a->eps255 = fmaxf(p->eps * 255.0f, 1e-12f);
+    a->gnu = p->mode == GLU_MODE_GNU;
+    a->code = th->code;
+    a->weight = th->weight;
+    a->wfmt = th->wfmt;
+    a->err = it.err_map;
+    return GLU_OK;
+}
+
+int joint_item(const glu_batch_item& it, JointItem* o) {
+    const glu_image* hr = &it.hr;
+    const glu_image* lr = &it.lr;
+    const glu_theta* th = &it.theta;
+    if (!image_ok(hr) || !image_ok(lr) || !theta_ok(th)) return GLU_ERR_INVALID_ARG;
+    if (hr->dtype != GLU_U8 || lr->dtype != GLU_U8 || hr->c != 3 || lr->c != 3)
+        return GLU_ERR_UNSUPPORTED;
+    const int s = th->scale;
+    if (th->H != hr->h || th->W != hr->w || lr->h != lr_dim(hr->h, s) ||
+        lr->w != lr_dim(hr->w, s))
+        return GLU_ERR_SHAPE;
+    o->hr = (const uint8_t*)hr->data;
+    o->hr_pitch = hr->pitch;
+    o->lr = (uint8_t*)lr->data;
+    o->lr_pitch = lr->pitch;
+    o->H = hr->h;
+    o->W = hr->w;
+    o->s = s;
+    o->S = th->S;
+    o->code = th->code;
+    o->weight = th->weight;
+    o->err = it.err_map;
+    return GLU_OK;
+}
+
+// Sizes only (for the workspace query).
+int joint_item_sizes(const glu_batch_item& it, JointItem* o) {
+    if (it.hr.h <= 0 || it.hr.w <= 0 || it.theta.scale < 1 || it.theta.S < 1 || it.theta.S > 9 ||
+        !(it.theta.S & 1))
+        return GLU_ERR_INVALID_ARG;
+    *o = JointItem{};
+    o->H = it.hr.h;
+    o->W = it.hr.w;
+    o->s = it.theta.scale;
+    o->S = it.theta.S;
+    return GLU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int glu_optimize_batched(const glu_batch_item* items, int32_t n, const glu_params* params,
+                         void* stream) {
+    if (n < 0 || (n > 0 && !items) || !params_ok(params)) return GLU_ERR_INVALID_ARG;
+    if (n == 0) return GLU_OK;
+    constexpr int kChunk = 64;
+    SearchArgs a[kChunk];
+    for (int k0 = 0; k0 < n; k0 += kChunk) {
+        const int m = n - k0 < kChunk ? n - k0 : kChunk;
+        for (int k = 0; k < m; ++k) {
+            const int rc = search_item(items[k0 + k], params, &a[k]);
+            if (rc) return rc;
+            if (a[k].hr_dtype != items[0].hr.dtype || a[k].wfmt != items[0].theta.wfmt)
+                return GLU_ERR_UNSUPPORTED;
+        }
+        const int rc = launch_search_batch(a, m, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    return GLU_OK;
+}
+
+size_t glu_joint_batched_workspace_size(const glu_batch_item* items, int32_t n,
+                                        const glu_params* params) {
+    if (n <= 0 || n > kMaxJointBatch || !items || !params_ok(params)) return 0;
+    JointItem it[kMaxJointBatch];
+    for (int k = 0; k < n; ++k)
+        if (joint_item_sizes(items[k], &it[k])) return 0;
+    return joint_batch_workspace_bytes(it, n, params->N);
+}
+
+int glu_joint_optimize_batched(const glu_batch_item* items, int32_t n, const glu_params* params,
+                               glu_joint_stats* stats, void* ws, size_t ws_bytes, void* stream) {
+    if (n < 0 || (n > 0 && !items) || !params_ok(params)) return GLU_ERR_INVALID_ARG;
+    if (n == 0) return GLU_OK;
+    if (n > kMaxJointBatch) return GLU_ERR_UNSUPPORTED;
+    if (params->mode != GLU_MODE_FAST) return GLU_ERR_UNSUPPORTED;
+    JointItem it[kMaxJointBatch];
+    for (int k = 0; k < n; ++k) {
+        const int rc = joint_item(items[k], &it[k]);
+        if (rc) return rc;
+        if (items[k].theta.wfmt != items[0].theta.wfmt) return GLU_ERR_UNSUPPORTED;
+    }
+    const size_t need = joint_batch_workspace_bytes(it, n, params->N);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return GLU_ERR_WORKSPACE;
+    JointCommon cm;
+    cm.eps255 = fmaxf(params->eps * 255.0f, 1e-12f);
+    cm.tau = params->tau;
+    cm.N = params->N;
+    cm.strict = params->joint == GLU_JOINT_STRICT;
+    cm.conn = params->connectivity;
+    cm.wfmt = items[0].theta.wfmt;
+    return launch_joint_batch(it, n, cm, ws, ws_bytes, stats, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -26,6 +26,8 @@ struct SearchArgs {
 };
 
 int launch_search(const SearchArgs& a, cudaStream_t st);
+// Several images in one persistent launch; every item shares hr_dtype, wfmt, gnu and eps255.
+int launch_search_batch(const SearchArgs* items, int n, cudaStream_t st);
 
 struct ApplyArgs {
     const uint16_t* code;
@@ -86,5 +88,26 @@ int joint_decisions(const void* ws, size_t ws_bytes, int H, int W, int s, int N,
                     int64_t cap, cudaStream_t st, int64_t* written);
 int launch_joint(const JointArgs& a, void* ws, size_t ws_bytes, glu_joint_stats* stats,
                  cudaStream_t st);
+
+// Algorithm 2 over a batch of images in one set of launches.
+constexpr int kMaxJointBatch = 32;
+struct JointItem {
+    const uint8_t* hr;
+    int64_t hr_pitch;   // bytes
+    uint8_t* lr;
+    int64_t lr_pitch;   // bytes
+    int H, W, s, S;
+    uint16_t* code;
+    void* weight;
+    float* err;         // nullable: a workspace plane is used otherwise
+};
+struct JointCommon {
+    float eps255, tau;
+    int N, strict, conn, wfmt;
+};
+size_t joint_batch_workspace_bytes(const JointItem* items, int n, int N);
+// stats: null or an array of n records
+int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, void* ws,
+                       size_t ws_bytes, glu_joint_stats* stats, cudaStream_t st);
 
 }  // namespace glu

@@ -1,22 +1,32 @@
-// Algorithm 2 (Sec. 3.3): joint optimisation of the downsampled image and Theta.
+// Algorithm 2 (Sec. 3.3): joint optimisation of the downsampled image and Theta, for a batch of
+// images (a single image is a batch of one).
 //
-// Per iteration n (all launched up front; every kernel returns at once when a device-side flag
-// says the loop has converged, so the host never waits in the middle):
-//   threshold   E_p > tau marks the large-error set; union-find labels (parent pointers only
-//               ever decrease, so every component's root is its smallest raster index)
-//   merge/flat  8- (or 4-) connected unions, then every pixel points at its root
+// The images of a batch share one global HR pixel index space and one global LR index space
+// (image after image, raster order inside each). Per iteration n (all launched up front; every
+// kernel returns at once when device-side flags say every image has converged, so the host
+// never waits in the middle):
+//   threshold   E_p > tau marks the large-error set of every still-active image; union-find
+//               labels (parent pointers only ever decrease, so every component's root is its
+//               smallest global index, i.e. its smallest raster index inside its image)
+//   merge/flat  8- (or 4-) connected unions inside each image, then every pixel points at its root
 //   roots       ordered stream compaction of the roots: component j = the j-th smallest root
 //   buckets     pixels and distinct LR blocks per component (counts, exclusive scan, fill)
 //   trials      persistent kernel: CTAs claim components in ascending order; component j waits
-//               only for earlier components whose LR blocks lie within D of its own (D = 2r for
-//               STRICT, r for PAPER) — exactly the components whose trials can read or write
-//               state j reads or writes — so the concurrent result equals the sequential one.
+//               only for earlier components of its image whose LR blocks lie within D of its
+//               own (D = 2r for STRICT, r for PAPER) — exactly the components whose trials can
+//               read or write state j reads or writes — so the concurrent result equals the
+//               sequential one. Block items of a trial are shared with idle warps of the grid.
 //               Waits are bounded (GLU_ERR_TIMEOUT) and can never deadlock: a component only
 //               waits for lower indices, which were claimed earlier by running CTAs.
-//   residual    R_n = sum_p E_p in FP64 with a fixed reduction order; stop when no trial was
-//               kept or R_n >= R_{n-1}.
+//   residual    R_n = sum_p E_p per image in FP64 with a fixed reduction order; an image stops
+//               when its set is empty, when no trial was kept, or when R_n >= R_{n-1}.
 // Trial sums e0 / e1 are FP32 Kahan sums per LR block (fixed lane order), rounded to 2^-32 and
 // added as 64-bit integers: exact and independent of the order blocks finish in.
+#include <stddef.h>
+#include <string.h>
+
+#include <mutex>
+
 #include "internal.h"
 #include "search.cuh"
 
@@ -29,77 +39,104 @@ constexpr int kScanTile = 4096;     // elements per scan tile
 constexpr int kScanThreads = 256;   // 16 elements per thread
 constexpr int kTrialThreads = 256;
 constexpr int kResidChunk = 8192;
+constexpr int kMaxSlots = 4096;
+constexpr int kSmax = 9;            // largest window
+
+// One image of a batch.
+struct JImg {
+    const uint8_t* hr;
+    int64_t hr_pitch;
+    uint8_t* lr;
+    int64_t lr_pitch;
+    uint16_t* code;
+    void* weight;
+    float* err;
+    int H, W, h, w, s, S;
+    int64_t p0, q0;   // first global HR / LR index
+    int c0;           // first residual chunk
+};
+
+struct JBatch {
+    JImg im[kMaxJointBatch];
+    int n, wfmt, strict, conn;
+    float eps255, tau;
+    int64_t np, nq;
+    int nchunks;
+};
+
+__device__ __forceinline__ int img_of_p(const JBatch& B, int64_t p) {
+    int i = 0;
+    while (i + 1 < B.n && B.im[i + 1].p0 <= p) ++i;
+    return i;
+}
 
 struct JointCtl {
-    int active;
+    int active_any;
     int timeout;
-    int iterations;
     int M_cur;
-    int n_large[GLU_MAX_ITERS];
-    int M[GLU_MAX_ITERS];
-    int accepted[GLU_MAX_ITERS];
-    int rolled[GLU_MAX_ITERS];
+    int open_tasks;
     int claim[GLU_MAX_ITERS];
-    double residual[GLU_MAX_ITERS + 1];
-    unsigned long long searched[GLU_MAX_ITERS];
-    int finished[GLU_MAX_ITERS];   // components done (kept or rolled back) per iteration
-    int open_tasks;                // published tasks that still have unclaimed items
+    int finished[GLU_MAX_ITERS];
+    int active[kMaxJointBatch];
+    int iterations[kMaxJointBatch];
+    int n_large[kMaxJointBatch][GLU_MAX_ITERS];
+    int M[kMaxJointBatch][GLU_MAX_ITERS];
+    int accepted[kMaxJointBatch][GLU_MAX_ITERS];
+    int rolled[kMaxJointBatch][GLU_MAX_ITERS];
+    unsigned long long searched[kMaxJointBatch][GLU_MAX_ITERS];
+    double residual[kMaxJointBatch][GLU_MAX_ITERS + 1];
 };
 
 struct JointWs {
     JointCtl* ctl;
-    float* err;             // H*W
-    int* lab;               // H*W: -1, union-find parent, then component id
-    uint8_t* qflag;         // H*W: pixel represents its (component, LR block) pair
-    int* roots;             // Mcap
-    int* comp_pix;          // H*W
-    int* qlist;             // H*W
-    int* ulist;             // H*W
-    int2* cnt;              // Mcap: (pixels, LR blocks)
-    int2* fill;             // Mcap
-    int2* start;            // Mcap + 1
-    int* done;              // Mcap
-    int* tile_a;            // tiles over H*W
-    int2* tile_b;           // tiles over Mcap
-    int* own;               // h*w*kOwnSlots
-    uint8_t* ovf;           // h*w
-    unsigned long long* stamp;  // h*w
-    unsigned long long* best;   // h*w
-    uint32_t* backup;       // h*w
+    float* err;             // np: error planes of images whose caller passed no error map
+    int* lab;               // np: -1, union-find parent, then component id
+    uint8_t* qflag;         // np: pixel represents its (component, LR block) pair
+    int* roots;             // mcap
+    int* comp_pix;          // np
+    int* qlist;             // np
+    int* ulist;             // np
+    int2* cnt;              // mcap: (pixels, LR blocks)
+    int2* fill;             // mcap
+    int2* start;            // mcap + 1
+    int* done;              // mcap
+    int* tile_a;            // tiles over np
+    int2* tile_b;           // tiles over mcap
+    int* own;               // nq * kOwnSlots
+    uint8_t* ovf;           // nq
+    unsigned long long* stamp;  // nq
+    unsigned long long* best;   // nq
+    uint32_t* backup;       // nq
     double* partial;        // residual partials
-    int8_t* dlog;           // N * Mcap: kept (1) / rolled back (0) per component and iteration
+    int8_t* dlog;           // N * mcap: kept (1) / rolled back (0) per component and iteration
     int64_t mcap;
-    uint16_t* sh_code;      // H*W shadow Theta / E written by a trial, copied if it is kept
-    float* sh_w;            // H*W
-    float* sh_err;          // H*W
-    // one task slot per persistent CTA: the block items of its component's trial or commit,
+    uint16_t* sh_code;      // np: Theta / E before a trial, restored if it is rolled back
+    float* sh_w;            // np
+    float* sh_err;          // np
+    // one task slot per persistent CTA: the block items of its component's trial or rollback,
     // open to every warp of the grid
     unsigned long long* slot_word;  // (epoch << 32) | next item; odd epoch = open
     int* slot_j;
     int* slot_n;            // items
-    int* slot_nu;           // distinct LR blocks of the component
-    int* slot_kind;         // 0 trial, 1 commit
+    int* slot_img;          // image of the component
+    int* slot_kind;         // 0 trial, 1 rollback
     unsigned long long* slot_e0;
     unsigned long long* slot_e1;
     int* slot_fin;          // items finished
 };
 
-constexpr int kMaxSlots = 4096;
-
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static inline int64_t mcap_of(int H, int W) {
-    // 8-connected components of single pixels are at most ceil(H/2)*ceil(W/2); 4-connected at
-    // most ceil(H*W/2) (checkerboard). Use the larger bound.
-    return ((int64_t)H * W + 1) / 2 + 1;
-}
+// 8-connected components of single pixels are at most ceil(H/2)*ceil(W/2) per image, 4-connected
+// at most ceil(H*W/2) (checkerboard); summed over a batch, (np + n) / 2 bounds both.
+static inline int64_t mcap_of(int64_t np, int n) { return (np + n) / 2 + 1; }
 
-// Carve the workspace; returns the bytes needed (ptr may be null to only measure).
-static size_t carve(void* base, int H, int W, int h, int w, int N, JointWs* o) {
-    const int64_t n = (int64_t)H * W, nl = (int64_t)h * w, mcap = mcap_of(H, W);
-    const int64_t tiles_a = (n + kScanTile - 1) / kScanTile + 1;
+// Carve the workspace; returns the bytes needed (base may be null to only measure).
+static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t nchunks,
+                    JointWs* o) {
+    const int64_t mcap = mcap_of(np, nimg);
+    const int64_t tiles_a = (np + kScanTile - 1) / kScanTile + 1;
     const int64_t tiles_b = (mcap + kScanTile - 1) / kScanTile + 1;
-    const int64_t nres = (n + kResidChunk - 1) / kResidChunk + 1;
     size_t off = 0;
     char* b = (char*)base;
     auto take = [&](size_t bytes) -> void* {
@@ -109,34 +146,34 @@ static size_t carve(void* base, int H, int W, int h, int w, int N, JointWs* o) {
     };
     JointWs t;
     t.ctl = (JointCtl*)take(sizeof(JointCtl));
-    t.err = (float*)take(sizeof(float) * n);
-    t.lab = (int*)take(sizeof(int) * n);
-    t.qflag = (uint8_t*)take(n);
+    t.err = (float*)take(sizeof(float) * np);
+    t.lab = (int*)take(sizeof(int) * np);
+    t.qflag = (uint8_t*)take(np);
     t.roots = (int*)take(sizeof(int) * mcap);
-    t.comp_pix = (int*)take(sizeof(int) * n);
-    t.qlist = (int*)take(sizeof(int) * n);
-    t.ulist = (int*)take(sizeof(int) * n);
+    t.comp_pix = (int*)take(sizeof(int) * np);
+    t.qlist = (int*)take(sizeof(int) * np);
+    t.ulist = (int*)take(sizeof(int) * np);
     t.cnt = (int2*)take(sizeof(int2) * mcap);
     t.fill = (int2*)take(sizeof(int2) * mcap);
     t.start = (int2*)take(sizeof(int2) * (mcap + 1));
     t.done = (int*)take(sizeof(int) * mcap);
     t.tile_a = (int*)take(sizeof(int) * tiles_a);
     t.tile_b = (int2*)take(sizeof(int2) * tiles_b);
-    t.own = (int*)take(sizeof(int) * nl * kOwnSlots);
-    t.ovf = (uint8_t*)take(nl);
-    t.stamp = (unsigned long long*)take(sizeof(unsigned long long) * nl);
-    t.best = (unsigned long long*)take(sizeof(unsigned long long) * nl);
-    t.backup = (uint32_t*)take(sizeof(uint32_t) * nl);
-    t.partial = (double*)take(sizeof(double) * nres);
+    t.own = (int*)take(sizeof(int) * nq * kOwnSlots);
+    t.ovf = (uint8_t*)take(nq);
+    t.stamp = (unsigned long long*)take(sizeof(unsigned long long) * nq);
+    t.best = (unsigned long long*)take(sizeof(unsigned long long) * nq);
+    t.backup = (uint32_t*)take(sizeof(uint32_t) * nq);
+    t.partial = (double*)take(sizeof(double) * (nchunks + 1));
     t.dlog = (int8_t*)take((size_t)(N > 0 ? N : 1) * (size_t)mcap);
     t.mcap = mcap;
-    t.sh_code = (uint16_t*)take(sizeof(uint16_t) * n);
-    t.sh_w = (float*)take(sizeof(float) * n);
-    t.sh_err = (float*)take(sizeof(float) * n);
+    t.sh_code = (uint16_t*)take(sizeof(uint16_t) * np);
+    t.sh_w = (float*)take(sizeof(float) * np);
+    t.sh_err = (float*)take(sizeof(float) * np);
     t.slot_word = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
     t.slot_j = (int*)take(sizeof(int) * kMaxSlots);
     t.slot_n = (int*)take(sizeof(int) * kMaxSlots);
-    t.slot_nu = (int*)take(sizeof(int) * kMaxSlots);
+    t.slot_img = (int*)take(sizeof(int) * kMaxSlots);
     t.slot_kind = (int*)take(sizeof(int) * kMaxSlots);
     t.slot_e0 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
     t.slot_e1 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
@@ -145,10 +182,34 @@ static size_t carve(void* base, int H, int W, int h, int w, int N, JointWs* o) {
     return off;
 }
 
+// Sizes of a batch: global pixel / LR counts and residual chunks.
+static void batch_sizes(const JointItem* items, int n, int64_t* np, int64_t* nq, int64_t* nch) {
+    *np = 0;
+    *nq = 0;
+    *nch = 0;
+    for (int k = 0; k < n; ++k) {
+        const int64_t a = (int64_t)items[k].H * items[k].W;
+        const int h = (items[k].H + items[k].s - 1) / items[k].s;
+        const int w = (items[k].W + items[k].s - 1) / items[k].s;
+        *np += a;
+        *nq += (int64_t)h * w;
+        *nch += (a + kResidChunk - 1) / kResidChunk;
+    }
+}
+
+size_t joint_batch_workspace_bytes(const JointItem* items, int n, int N) {
+    int64_t np, nq, nch;
+    batch_sizes(items, n, &np, &nq, &nch);
+    return carve(nullptr, np, nq, n, N, nch, nullptr);
+}
+
 size_t joint_workspace_bytes(int H, int W, int s, int S, int N) {
-    (void)S;
-    const int h = (H + s - 1) / s, w = (W + s - 1) / s;
-    return carve(nullptr, H, W, h, w, N, nullptr);
+    JointItem it{};
+    it.H = H;
+    it.W = W;
+    it.s = s;
+    it.S = S;
+    return joint_batch_workspace_bytes(&it, 1, N);
 }
 
 // --------------------------------------------------------------------------- small helpers
@@ -163,8 +224,8 @@ __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool is_active(const JointCtl* c) {
-    return *(volatile const int*)&c->active != 0;
+__device__ __forceinline__ bool any_active(const JointCtl* c) {
+    return *(volatile const int*)&c->active_any != 0;
 }
 
 // Block-wide exclusive scan of one int per thread (blockDim.x == 256). Returns the total.
@@ -197,38 +258,60 @@ __device__ __forceinline__ int block_excl_scan(int v, int* out_excl, int* smem_w
 
 // ---------------------------------------------------------------- control and init kernels
 
-__global__ void k_ctl_init(JointCtl* c, unsigned long long* stamp, int64_t nl,
-                           unsigned long long* slot_word) {
+// Every counter of the control block starts at zero, except the active flags of the nimg
+// images and active_any; stamps and task slots are cleared.
+__global__ void k_ctl_init(JointCtl* c, unsigned long long* stamp, int64_t nq,
+                           unsigned long long* slot_word, int nimg) {
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    for (int64_t i = i0; i < kMaxSlots; i += (int64_t)gridDim.x * blockDim.x) slot_word[i] = 0ull;
-    if (i0 == 0) {
-        c->active = 1;
-        c->timeout = 0;
-        c->iterations = 0;
-        c->M_cur = 0;
-        c->open_tasks = 0;
-        for (int k = 0; k < GLU_MAX_ITERS; ++k) {
-            c->n_large[k] = 0;
-            c->M[k] = 0;
-            c->accepted[k] = 0;
-            c->rolled[k] = 0;
-            c->claim[k] = 0;
-            c->searched[k] = 0ull;
-            c->finished[k] = 0;
-        }
-    }
-    for (int64_t i = i0; i < nl; i += (int64_t)gridDim.x * blockDim.x) stamp[i] = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = i0; i < kMaxSlots; i += stride) slot_word[i] = 0ull;
+    for (int64_t i = i0; i < nq; i += stride) stamp[i] = 0ull;
+    int* ci = (int*)c;
+    constexpr int nwords = (int)(sizeof(JointCtl) / sizeof(int));
+    constexpr int w_any = (int)(offsetof(JointCtl, active_any) / sizeof(int));
+    constexpr int w_act = (int)(offsetof(JointCtl, active) / sizeof(int));
+    for (int64_t i = i0; i < nwords; i += stride)
+        ci[i] = (i == w_any || (i >= w_act && i < w_act + nimg)) ? 1 : 0;
 }
 
-// Residual R = sum_p E_p in FP64: fixed chunk per CTA, fixed thread assignment, fixed tree.
-__global__ void k_resid_partial(const float* err, int64_t n, double* partial, const JointCtl* c) {
-    if (!is_active(c)) return;
+// Batched regular grid downsampling (uint8): LR pixel (v, u) copies HR pixel
+// (v*s + e_y/2, u*s + e_x/2), e = extent of the block.
+__global__ void k_grid_batch(const __grid_constant__ JBatch B) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < B.nq;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int i = 0;
+        while (i + 1 < B.n && B.im[i + 1].q0 <= g) ++i;
+        const JImg& I = B.im[i];
+        const int64_t lq = g - I.q0;
+        const int v = (int)(lq / I.w), u = (int)(lq % I.w);
+        const int ey = min(I.s, I.H - v * I.s), ex = min(I.s, I.W - u * I.s);
+        const uint8_t* src =
+            I.hr + (int64_t)(v * I.s + ey / 2) * I.hr_pitch + (int64_t)(u * I.s + ex / 2) * 3;
+        uint8_t* dst = I.lr + (int64_t)v * I.lr_pitch + (int64_t)u * 3;
+        dst[0] = src[0];
+        dst[1] = src[1];
+        dst[2] = src[2];
+    }
+}
+
+// Residual R = sum_p E_p per image in FP64: a CTA per chunk of one image (fixed chunking, fixed
+// thread assignment, fixed tree), then a fixed-order sum of each image's chunks.
+__global__ void k_resid_partial(const __grid_constant__ JBatch B, double* partial,
+                                const JointCtl* c) {
+    if (!any_active(c)) return;
     __shared__ double sm[256];
-    const int64_t base = (int64_t)blockIdx.x * kResidChunk;
+    const int chunk = blockIdx.x;
+    int i = 0;
+    while (i + 1 < B.n && B.im[i + 1].c0 <= chunk) ++i;
+    const JImg& I = B.im[i];
+    const int64_t n = (int64_t)I.H * I.W;
+    const int64_t base = (int64_t)(chunk - I.c0) * kResidChunk;
     double acc = 0.0;
-    for (int i = threadIdx.x; i < kResidChunk; i += 256) {
-        const int64_t p = base + i;
-        if (p < n) acc += (double)err[p];
+    if (c->active[i]) {
+        for (int k = threadIdx.x; k < kResidChunk; k += 256) {
+            const int64_t p = base + k;
+            if (p < n) acc += (double)I.err[p];
+        }
     }
     sm[threadIdx.x] = acc;
     __syncthreads();
@@ -236,61 +319,66 @@ __global__ void k_resid_partial(const float* err, int64_t n, double* partial, co
         if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+    if (threadIdx.x == 0) partial[chunk] = sm[0];
 }
 
-// it < 0: initial residual R_0. Otherwise finish iteration it: record R, decide convergence.
-__global__ void k_resid_final(const double* partial, int nb, JointCtl* c, int it) {
-    if (!is_active(c)) return;
+// it < 0: initial residuals R_0. Otherwise finish iteration it for every active image: record
+// R, decide whether it stops. An image whose large-error set was empty stops without counting
+// the iteration (Algorithm 2 breaks before any trial).
+__global__ void k_resid_final(const __grid_constant__ JBatch B, const double* partial,
+                              JointCtl* c, int it) {
+    if (!any_active(c)) return;
     __shared__ double sm[256];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nb; i += 256) acc += partial[i];
-    sm[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    for (int i = 0; i < B.n; ++i) {
+        if (!c->active[i]) continue;  // uniform across the CTA
+        const int nch = (i + 1 < B.n ? B.im[i + 1].c0 : B.nchunks) - B.im[i].c0;
+        double acc = 0.0;
+        for (int k = threadIdx.x; k < nch; k += 256) acc += partial[B.im[i].c0 + k];
+        sm[threadIdx.x] = acc;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double R = sm[0];
+            if (it < 0) {
+                c->residual[i][0] = R;
+            } else if (c->M[i][it] == 0) {
+                c->active[i] = 0;
+            } else {
+                c->residual[i][it + 1] = R;
+                c->iterations[i] = it + 1;
+                if (c->accepted[i][it] == 0 || !(R < c->residual[i][it])) c->active[i] = 0;
+            }
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const double R = sm[0];
-        if (it < 0) {
-            c->residual[0] = R;
-        } else {
-            c->residual[it + 1] = R;
-            c->iterations = it + 1;
-            if (c->accepted[it] == 0 || !(R < c->residual[it])) c->active = 0;
-        }
+    if (threadIdx.x == 0 && it >= 0) {
+        int any = 0;
+        for (int i = 0; i < B.n; ++i) any |= c->active[i];
+        c->active_any = any;
     }
 }
 
 // ----------------------------------------------------------------------- threshold and CCL
 
-// Large-error set and union-find init; clears the per-LR-pixel owner slots.
-__global__ void k_threshold(const float* err, int64_t n, float tau, int* lab, int* own,
-                            uint8_t* ovf, int64_t nl, JointCtl* c, int it) {
-    if (!is_active(c)) return;
-    __shared__ int wsum[8];
-    int local = 0;
+// Large-error set of the active images and union-find init; clears the owner slots.
+__global__ void k_threshold(const __grid_constant__ JBatch B, int* lab, int* own, uint8_t* ovf,
+                            JointCtl* c, int it) {
+    if (!any_active(c)) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += stride) {
-        const bool fg = err[p] > tau;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < B.np; p += stride) {
+        const int i = img_of_p(B, p);
+        bool fg = false;
+        if (c->active[i]) fg = B.im[i].err[p - B.im[i].p0] > B.tau;
         lab[p] = fg ? (int)p : -1;
-        local += fg;
+        if (fg) atomicAdd(&c->n_large[i][it], 1);
     }
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nl; q += stride) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < B.nq; q += stride) {
 #pragma unroll
         for (int k = 0; k < kOwnSlots; ++k) own[q * kOwnSlots + k] = -1;
         ovf[q] = 0;
-    }
-    // block sum then one atomic per block (integer: order-independent)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = local;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += wsum[i];
-        if (t) atomicAdd(&c->n_large[it], t);
     }
 }
 
@@ -322,28 +410,29 @@ __device__ __forceinline__ void uf_union(int* par, int a, int b) {
     }
 }
 
-__global__ void k_ccl_merge(int* lab, int H, int W, int conn, const JointCtl* c) {
-    if (!is_active(c)) return;
-    const int64_t n = (int64_t)H * W;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+__global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const JointCtl* c) {
+    if (!any_active(c)) return;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < B.np;
          p += (int64_t)gridDim.x * blockDim.x) {
         if (__ldcg(&lab[p]) < 0) continue;
-        const int y = (int)(p / W), x = (int)(p % W);
-        // backward neighbours only: W, N (and NW, NE for 8-connectivity)
+        const JImg& I = B.im[img_of_p(B, p)];
+        const int64_t lp = p - I.p0;
+        const int y = (int)(lp / I.W), x = (int)(lp % I.W);
+        // backward neighbours inside the image: W, N (and NW, NE for 8-connectivity)
         if (x > 0 && __ldcg(&lab[p - 1]) >= 0) uf_union(lab, (int)p, (int)p - 1);
         if (y > 0) {
-            const int64_t up = p - W;
+            const int64_t up = p - I.W;
             if (__ldcg(&lab[up]) >= 0) uf_union(lab, (int)p, (int)up);
-            if (conn == 8) {
+            if (B.conn == 8) {
                 if (x > 0 && __ldcg(&lab[up - 1]) >= 0) uf_union(lab, (int)p, (int)up - 1);
-                if (x + 1 < W && __ldcg(&lab[up + 1]) >= 0) uf_union(lab, (int)p, (int)up + 1);
+                if (x + 1 < I.W && __ldcg(&lab[up + 1]) >= 0) uf_union(lab, (int)p, (int)up + 1);
             }
         }
     }
 }
 
 __global__ void k_ccl_flatten(int* lab, int64_t n, const JointCtl* c) {
-    if (!is_active(c)) return;
+    if (!any_active(c)) return;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         if (__ldcg(&lab[p]) >= 0) lab[p] = uf_find(lab, (int)p);
@@ -354,7 +443,7 @@ __global__ void k_ccl_flatten(int* lab, int64_t n, const JointCtl* c) {
 
 // per-tile root counts (a root is a labelled pixel that is its own parent)
 __global__ void k_root_count(const int* lab, int64_t n, int* tile_cnt, const JointCtl* c) {
-    if (!is_active(c)) return;
+    if (!any_active(c)) return;
     __shared__ int wsum[8];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int local = 0;
@@ -374,8 +463,8 @@ __global__ void k_root_count(const int* lab, int64_t n, int* tile_cnt, const Joi
 }
 
 // single-CTA exclusive scan of tile counts in place; the total becomes M
-__global__ void k_root_scan(int* tile_cnt, int ntiles, JointCtl* c, int it) {
-    if (!is_active(c)) return;
+__global__ void k_root_scan(int* tile_cnt, int ntiles, JointCtl* c) {
+    if (!any_active(c)) return;
     __shared__ int wsm[8];
     int carry = 0;
     for (int base = 0; base < ntiles; base += kScanThreads) {
@@ -387,20 +476,21 @@ __global__ void k_root_scan(int* tile_cnt, int ntiles, JointCtl* c, int it) {
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        c->M[it] = carry;
         c->M_cur = carry;
-        if (carry == 0) c->active = 0;  // the large-error set is empty: Algorithm 2 stops
+        if (carry == 0) c->active_any = 0;  // every large-error set is empty: all images stop
     }
 }
 
-// scatter roots in raster order; component j's per-iteration state is cleared here
-__global__ void k_root_scatter(const int* lab, int64_t n, const int* tile_off, int* roots,
-                               int2* cnt, int2* fill, int* done, const JointCtl* c) {
-    if (!is_active(c)) return;
+// scatter roots in global order; component j's per-iteration state is cleared here
+__global__ void k_root_scatter(const __grid_constant__ JBatch B, const int* lab,
+                               const int* tile_off, int* roots, int2* cnt, int2* fill, int* done,
+                               JointCtl* c, int it) {
+    if (!any_active(c)) return;
     __shared__ int wsm[8];
+    const int64_t n = B.np;
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int off = tile_off[blockIdx.x];
-    // 16 consecutive elements per thread keep raster order inside the tile
+    // 16 consecutive elements per thread keep the order inside the tile
     const int per = kScanTile / kScanThreads;
     const int64_t my = base + (int64_t)threadIdx.x * per;
     int flags = 0, cntl = 0;
@@ -421,6 +511,7 @@ __global__ void k_root_scatter(const int* lab, int64_t n, const int* tile_off, i
             cnt[j] = make_int2(0, 0);
             fill[j] = make_int2(0, 0);
             done[j] = 0;
+            atomicAdd(&c->M[img_of_p(B, my + k)][it], 1);
             ++j;
         }
     }
@@ -439,20 +530,21 @@ __device__ __forceinline__ int lower_bound_i(const int* a, int n, int key) {
 
 // pixel -> component id (lab rewritten in place); counts of pixels and of distinct LR blocks;
 // owner slots of each LR block list the components touching it.
-__global__ void k_comp_count(int* lab, int H, int W, int s, int w, const int* roots, int2* cnt,
-                             int* own, uint8_t* ovf, uint8_t* qflag, const JointCtl* c) {
-    if (!is_active(c)) return;
+__global__ void k_comp_count(const __grid_constant__ JBatch B, int* lab, const int* roots,
+                             int2* cnt, int* own, uint8_t* ovf, uint8_t* qflag, const JointCtl* c) {
+    if (!any_active(c)) return;
     const int M = c->M_cur;
-    const int64_t n = (int64_t)H * W;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < B.np;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int root = lab[p];
         if (root < 0) continue;
         const int j = lower_bound_i(roots, M, root);
         lab[p] = j;
         atomicAdd(&cnt[j].x, 1);
-        const int y = (int)(p / W), x = (int)(p % W);
-        const int64_t q = (int64_t)(y / s) * w + (x / s);
+        const JImg& I = B.im[img_of_p(B, p)];
+        const int64_t lp = p - I.p0;
+        const int y = (int)(lp / I.W), x = (int)(lp % I.W);
+        const int64_t q = I.q0 + (int64_t)(y / I.s) * I.w + (x / I.s);
         int ins = -1;  // 1: inserted here, 0: already present, -1: slots full
         for (int k = 0; k < kOwnSlots; ++k) {
             const int old = atomicCAS(&own[q * kOwnSlots + k], -1, j);
@@ -468,7 +560,7 @@ __global__ void k_comp_count(int* lab, int H, int W, int s, int w, const int* ro
 
 // multi-CTA exclusive scan of int2 counts over M (read from the control block)
 __global__ void k_comp_tile_reduce(const int2* cnt, int2* tile_sum, const JointCtl* c) {
-    if (!is_active(c)) return;
+    if (!any_active(c)) return;
     const int M = c->M_cur;
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     if (base >= M) return;
@@ -493,7 +585,7 @@ __global__ void k_comp_tile_reduce(const int2* cnt, int2* tile_sum, const JointC
 }
 
 __global__ void k_comp_tile_scan(int2* tile_sum, const JointCtl* c) {
-    if (!is_active(c)) return;
+    if (!any_active(c)) return;
     const int M = c->M_cur;
     const int ntiles = (M + kScanTile - 1) / kScanTile;
     __shared__ int wsm[8];
@@ -511,7 +603,7 @@ __global__ void k_comp_tile_scan(int2* tile_sum, const JointCtl* c) {
 }
 
 __global__ void k_comp_scan(const int2* cnt, const int2* tile_off, int2* start, const JointCtl* c) {
-    if (!is_active(c)) return;
+    if (!any_active(c)) return;
     const int M = c->M_cur;
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     if (base >= M) return;
@@ -539,21 +631,22 @@ __global__ void k_comp_scan(const int2* cnt, const int2* tile_off, int2* start, 
     }
 }
 
-__global__ void k_comp_fill(const int* lab, int H, int W, int s, int w, const uint8_t* qflag,
-                            const int2* start, int2* fill, int* comp_pix, int* qlist,
-                            const JointCtl* c) {
-    if (!is_active(c)) return;
-    const int64_t n = (int64_t)H * W;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+__global__ void k_comp_fill(const __grid_constant__ JBatch B, const int* lab,
+                            const uint8_t* qflag, const int2* start, int2* fill, int* comp_pix,
+                            int* qlist, const JointCtl* c) {
+    if (!any_active(c)) return;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < B.np;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int j = lab[p];
         if (j < 0) continue;
         const int pos = atomicAdd(&fill[j].x, 1);
         comp_pix[start[j].x + pos] = (int)p;
         if (qflag[p]) {
-            const int y = (int)(p / W), x = (int)(p % W);
+            const JImg& I = B.im[img_of_p(B, p)];
+            const int64_t lp = p - I.p0;
+            const int y = (int)(lp / I.W), x = (int)(lp % I.W);
             const int qp = atomicAdd(&fill[j].y, 1);
-            qlist[start[j].y + qp] = (y / s) * w + (x / s);
+            qlist[start[j].y + qp] = (int)(I.q0 + (int64_t)(y / I.s) * I.w + (x / I.s));
         }
     }
 }
@@ -575,19 +668,9 @@ __device__ __forceinline__ unsigned long long gtimer() {
 #define GLU_TRACE(it, j, k) do { } while (0)
 #endif
 
-struct TrialArgs {
-    const uint8_t* hr;
-    int64_t hr_pitch;
-    uint8_t* lr;
-    int64_t lr_pitch;
-    int H, W, h, w, s;
-    float eps255;
-    int strict, it;
-    uint16_t* code;
-    void* weight;
-    int wfmt;
-    float* err;
+struct TrialCtx {
     JointWs ws;
+    int it;
 };
 
 __device__ __forceinline__ long long to_fixed(float x) {
@@ -633,48 +716,49 @@ __device__ __forceinline__ float load_weight_cg(const void* base, int fmt, int64
     return (float)__ldcg((const unsigned short*)base + i) * (1.0f / 65535.0f);
 }
 
-// One warp re-runs Algorithm 1 on the HR pixels of LR block (bv, bu) against the current LR
-// image (comp >= 0: only the pixels of that component), writing the results in place and the
-// previous values to the backup planes. The previous errors (e0) and the new ones (e1) are
-// summed with Kahan compensation in a fixed lane order and reduced with a fixed butterfly.
+// One warp re-runs Algorithm 1 on the HR pixels of LR block (bv, bu) of image I against the
+// current LR image (comp >= 0: only the pixels of that component), writing the results in place
+// and the previous values to the backup planes. The previous errors (e0) and the new ones (e1)
+// are summed with Kahan compensation in a fixed lane order and reduced with a fixed butterfly.
 template <int S>
-__device__ __noinline__ void warp_block_trial(const TrialArgs& A, float4* win, int bv, int bu,
-                                                 int comp, float& e0, float& e1) {
+__device__ __noinline__ void warp_block_trial(const JBatch& B, const TrialCtx& X, const JImg& I,
+                                              float4* win, int bv, int bu, int comp, int img,
+                                              float& e0, float& e1) {
     constexpr int r = (S - 1) / 2, K = S * S;
     const int lane = threadIdx.x & 31;
     for (int k = lane; k < K; k += 32) {
         const int v = bv + k / S - r, u = bu + k % S - r;
         float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (v >= 0 && v < A.h && u >= 0 && u < A.w) {
-            const uint32_t c = load_rgb(A.lr, A.lr_pitch, v, u);
+        if (v >= 0 && v < I.h && u >= 0 && u < I.w) {
+            const uint32_t c = load_rgb(I.lr, I.lr_pitch, v, u);
             c4 = make_float4((float)(c & 255u), (float)((c >> 8) & 255u), (float)(c >> 16), 0.f);
         }
         win[k] = c4;
     }
     __syncwarp();
     uint32_t rm, cm;
-    window_masks(bv, bu, A.h, A.w, S, rm, cm);
-    const int ys = bv * A.s, xs = bu * A.s;
-    const int ey = min(A.s, A.H - ys), ex = min(A.s, A.W - xs);
+    window_masks(bv, bu, I.h, I.w, S, rm, cm);
+    const int ys = bv * I.s, xs = bu * I.s;
+    const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
     int nsearched = 0;
     for (int j = lane; j < ey * ex; j += 32) {
         const int y = ys + j / ex, x = xs + j % ex;
-        const int64_t p = (int64_t)y * A.W + x;
-        if (comp >= 0 && __ldcg(&A.ws.lab[p]) != comp) continue;
-        const uint8_t* ip = A.hr + (int64_t)y * A.hr_pitch + (int64_t)x * 3;
+        const int64_t lp = (int64_t)y * I.W + x, p = I.p0 + lp;
+        if (comp >= 0 && __ldcg(&X.ws.lab[p]) != comp) continue;
+        const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
         const SearchOut o = search_pixel<S, true>(win, S, rm, cm, (float)ip[0], (float)ip[1],
-                                                  (float)ip[2], A.eps255, false);
+                                                  (float)ip[2], B.eps255, false);
         ++nsearched;
         // the new Theta / E go in place; the old ones to the backup planes (restored if the
         // trial is rolled back)
-        const float eold = __ldcg(&A.err[p]);
-        A.ws.sh_code[p] = __ldcg(&A.code[p]);
-        A.ws.sh_w[p] = load_weight_cg(A.weight, A.wfmt, p);
-        A.ws.sh_err[p] = eold;
-        A.code[p] = (uint16_t)(o.ka * K + o.kb);
-        store_weight(A.weight, A.wfmt, p, o.omega);
-        A.err[p] = o.err;
+        const float eold = __ldcg(&I.err[lp]);
+        X.ws.sh_code[p] = __ldcg(&I.code[lp]);
+        X.ws.sh_w[p] = load_weight_cg(I.weight, B.wfmt, lp);
+        X.ws.sh_err[p] = eold;
+        I.code[lp] = (uint16_t)(o.ka * K + o.kb);
+        store_weight(I.weight, B.wfmt, lp, o.omega);
+        I.err[lp] = o.err;
         kahan_add(s0, c0, eold);
         kahan_add(s1, c1, o.err);
     }
@@ -685,41 +769,43 @@ __device__ __noinline__ void warp_block_trial(const TrialArgs& A, float4* win, i
         t1 += __shfl_xor_sync(0xffffffffu, t1, o);
         nsearched += __shfl_xor_sync(0xffffffffu, nsearched, o);
     }
-    if (lane == 0 && nsearched) atomicAdd(&A.ws.ctl->searched[A.it], (unsigned long long)nsearched);
+    if (lane == 0 && nsearched)
+        atomicAdd(&X.ws.ctl->searched[img][X.it], (unsigned long long)nsearched);
     e0 = t0;
     e1 = t1;
     __syncwarp();
 }
 
 // Roll back a trial for LR block (bv, bu): restore Theta and E from the backup planes.
-__device__ __forceinline__ void warp_block_commit(const TrialArgs& A, int bv, int bu, int comp) {
+__device__ __forceinline__ void warp_block_rollback(const JBatch& B, const TrialCtx& X,
+                                                    const JImg& I, int bv, int bu, int comp) {
     const int lane = threadIdx.x & 31;
-    const int ys = bv * A.s, xs = bu * A.s;
-    const int ey = min(A.s, A.H - ys), ex = min(A.s, A.W - xs);
+    const int ys = bv * I.s, xs = bu * I.s;
+    const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
     for (int j = lane; j < ey * ex; j += 32) {
         const int y = ys + j / ex, x = xs + j % ex;
-        const int64_t p = (int64_t)y * A.W + x;
-        if (comp >= 0 && __ldcg(&A.ws.lab[p]) != comp) continue;
-        A.code[p] = __ldcg(&A.ws.sh_code[p]);
-        store_weight_raw(A.weight, A.wfmt, p, __ldcg(&A.ws.sh_w[p]));
-        A.err[p] = __ldcg(&A.ws.sh_err[p]);
+        const int64_t lp = (int64_t)y * I.W + x, p = I.p0 + lp;
+        if (comp >= 0 && __ldcg(&X.ws.lab[p]) != comp) continue;
+        I.code[lp] = __ldcg(&X.ws.sh_code[p]);
+        store_weight_raw(I.weight, B.wfmt, lp, __ldcg(&X.ws.sh_w[p]));
+        I.err[lp] = __ldcg(&X.ws.sh_err[p]);
     }
 }
 
-// Block item t of component j (trial or commit enumeration): the LR block it designates, or
-// false when it falls outside the LR image. STRICT: (distinct block u, neighbour nb) pairs;
-// PAPER: the distinct blocks themselves.
-template <int S>
-__device__ __forceinline__ bool item_block(const TrialArgs& A, int stY, int t, int& bv, int& bu) {
-    constexpr int r = (S - 1) / 2, NB = (2 * r + 1) * (2 * r + 1);
-    const int q = A.ws.ulist[stY + (A.strict ? t / NB : t)];
-    bv = q / A.w;
-    bu = q % A.w;
-    if (A.strict) {
+// Block item t of component j (global LR list offset stY) of image I: the LR block it
+// designates, or false when it falls outside the LR image. STRICT: (distinct block u,
+// neighbour nb) pairs; PAPER: the distinct blocks themselves.
+__device__ __forceinline__ bool item_block(const JBatch& B, const TrialCtx& X, const JImg& I,
+                                           int stY, int t, int& bv, int& bu) {
+    const int r = (I.S - 1) / 2, NB = (2 * r + 1) * (2 * r + 1);
+    const int64_t lq = (int64_t)X.ws.ulist[stY + (B.strict ? t / NB : t)] - I.q0;
+    bv = (int)(lq / I.w);
+    bu = (int)(lq % I.w);
+    if (B.strict) {
         const int nb = t % NB;
         bv += nb / (2 * r + 1) - r;
         bu += nb % (2 * r + 1) - r;
-        if (bv < 0 || bv >= A.h || bu < 0 || bu >= A.w) return false;
+        if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) return false;
     }
     return true;
 }
@@ -728,26 +814,36 @@ __device__ __forceinline__ unsigned long long trial_tag(int it, int j, int phase
     return ((unsigned long long)(it * 4 + phase) << 40) | (unsigned long long)(j + 1);
 }
 
-// One warp processes item t of component j: claims its block (STRICT blocks reached from several
-// q are processed once), then runs the trial (kind 0, sums returned) or the commit (kind 1).
-template <int S>
-__device__ __forceinline__ bool process_item(const TrialArgs& A, float4* win, int j, int stY,
-                                             int kind, int t, float& e0, float& e1) {
+// One warp processes item t of component j of image img: claims its block (STRICT blocks reached
+// from several q are processed once), then runs the trial (kind 0, sums returned) or the
+// rollback (kind 1).
+__device__ __forceinline__ bool process_item(const JBatch& B, const TrialCtx& X, float4* win,
+                                             int j, int img, int stY, int kind, int t, float& e0,
+                                             float& e1) {
     const int lane = threadIdx.x & 31;
+    const JImg& I = B.im[img];
     e0 = 0.f;
     e1 = 0.f;
     int bv, bu;
-    if (!item_block<S>(A, stY, t, bv, bu)) return false;
-    if (A.strict) {
-        const unsigned long long tag = trial_tag(A.it, j, kind + 1);
+    if (!item_block(B, X, I, stY, t, bv, bu)) return false;
+    if (B.strict) {
+        const unsigned long long tag = trial_tag(X.it, j, kind + 1);
         int claimed = 0;
-        if (lane == 0) claimed = atomicExch(&A.ws.stamp[(int64_t)bv * A.w + bu], tag) != tag;
+        if (lane == 0) claimed = atomicExch(&X.ws.stamp[I.q0 + (int64_t)bv * I.w + bu], tag) != tag;
         if (!__shfl_sync(0xffffffffu, claimed, 0)) return false;
     }
-    if (kind == 0)
-        warp_block_trial<S>(A, win, bv, bu, A.strict ? -1 : j, e0, e1);
-    else
-        warp_block_commit(A, bv, bu, A.strict ? -1 : j);
+    const int comp = B.strict ? -1 : j;
+    if (kind == 0) {
+        switch (I.S) {
+            case 1: warp_block_trial<1>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
+            case 3: warp_block_trial<3>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
+            case 5: warp_block_trial<5>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
+            case 7: warp_block_trial<7>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
+            default: warp_block_trial<9>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
+        }
+    } else {
+        warp_block_rollback(B, X, I, bv, bu, comp);
+    }
     return true;
 }
 
@@ -799,9 +895,9 @@ __device__ __forceinline__ bool slot_has_items(const JointWs& W_, int k) {
 // Claiming is one fetch-and-add on the slot's (epoch << 32 | next) word. An increment that lands
 // on a closed slot is harmless (opening overwrites the word); one that lands on an open epoch
 // owns item `next` of that epoch, whose context cannot change before that item is finished.
-template <int S>
-__device__ bool help_one(const TrialArgs& A, float4* win, int own, int G, int& hint) {
-    const JointWs& W_ = A.ws;
+__device__ bool help_one(const JBatch& B, const TrialCtx& X, float4* win, int own, int G,
+                         int& hint) {
+    const JointWs& W_ = X.ws;
     const int lane = threadIdx.x & 31;
     int s_sel = -1;
     if (lane == 0) {
@@ -833,7 +929,7 @@ __device__ bool help_one(const TrialArgs& A, float4* win, int own, int G, int& h
         hint = -1;
         return false;
     }
-    int item = -1, j = 0, kind = 0, stY = 0;
+    int item = -1, j = 0, kind = 0, stY = 0, img = 0;
     if (lane == 0) {
         const unsigned long long old = atom_add_acquire_u64(&W_.slot_word[s_sel], 1ull);
         if ((old >> 32) & 1ull) {
@@ -843,6 +939,7 @@ __device__ bool help_one(const TrialArgs& A, float4* win, int own, int G, int& h
                 item = nx;
                 j = *(volatile const int*)&W_.slot_j[s_sel];
                 kind = *(volatile const int*)&W_.slot_kind[s_sel];
+                img = *(volatile const int*)&W_.slot_img[s_sel];
                 stY = W_.start[j].y;
                 // the claimer of the last item takes the task off the open count
                 if (nx + 1 == n) atomicSub(&W_.ctl->open_tasks, 1);
@@ -857,16 +954,17 @@ __device__ bool help_one(const TrialArgs& A, float4* win, int own, int G, int& h
     hint = s_sel;
     j = __shfl_sync(0xffffffffu, j, 0);
     kind = __shfl_sync(0xffffffffu, kind, 0);
+    img = __shfl_sync(0xffffffffu, img, 0);
     stY = __shfl_sync(0xffffffffu, stY, 0);
     float e0, e1;
-    const bool did = process_item<S>(A, win, j, stY, kind, item, e0, e1);
+    const bool did = process_item(B, X, win, j, img, stY, kind, item, e0, e1);
     __syncwarp();
     if (lane == 0) {
         if (did && kind == 0) {
             atomicAdd(&W_.slot_e0[s_sel], (unsigned long long)to_fixed(e0));
             atomicAdd(&W_.slot_e1[s_sel], (unsigned long long)to_fixed(e1));
         }
-        // release: this warp's writes (shadow planes, Theta, E, sums) are visible to whoever
+        // release: this warp's writes (backup planes, Theta, E, sums) are visible to whoever
         // observes the count
         red_release_add(&W_.slot_fin[s_sel], 1);
     }
@@ -877,18 +975,17 @@ __device__ bool help_one(const TrialArgs& A, float4* win, int own, int G, int& h
 // Run the items of one task of component j. Small tasks stay inside the CTA; larger ones are
 // published in the CTA's slot so idle warps anywhere in the grid can take items. Returns the
 // (fixed-point) sums of a trial in e0/e1. False on an exhausted wait.
-template <int S>
-__device__ bool run_task(const TrialArgs& A, float4* win, int j, int stY, int nu, int kind,
-                         int nitems, int G, unsigned long long* s_e0, unsigned long long* s_e1,
-                         int* s_flag, unsigned long long t0) {
-    const JointWs& W_ = A.ws;
+__device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j, int img, int stY,
+                         int kind, int nitems, int G, unsigned long long* s_e0,
+                         unsigned long long* s_e1, int* s_flag, unsigned long long t0) {
+    const JointWs& W_ = X.ws;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int nwarps = kTrialThreads / 32;
     const int own = blockIdx.x;
     if (nitems <= nwarps) {
         for (int t = warp; t < nitems; t += nwarps) {
             float e0, e1;
-            const bool did = process_item<S>(A, win, j, stY, kind, t, e0, e1);
+            const bool did = process_item(B, X, win, j, img, stY, kind, t, e0, e1);
             if (did && kind == 0 && lane == 0) {
                 atomicAdd(s_e0, (unsigned long long)to_fixed(e0));
                 atomicAdd(s_e1, (unsigned long long)to_fixed(e1));
@@ -901,7 +998,7 @@ __device__ bool run_task(const TrialArgs& A, float4* win, int j, int stY, int nu
         const unsigned long long e = W_.slot_word[own] >> 32;  // even: closed
         W_.slot_j[own] = j;
         W_.slot_n[own] = nitems;
-        W_.slot_nu[own] = nu;
+        W_.slot_img[own] = img;
         W_.slot_kind[own] = kind;
         W_.slot_e0[own] = 0ull;
         W_.slot_e1[own] = 0ull;
@@ -919,8 +1016,8 @@ __device__ bool run_task(const TrialArgs& A, float4* win, int j, int stY, int nu
         int fin = 0;
         if (lane == 0) fin = ld_acquire(&W_.slot_fin[own]) >= nitems;
         if (__shfl_sync(0xffffffffu, fin, 0)) break;
-        if (!help_one<S>(A, win, own, G, hint)) __nanosleep(100);
-        if (warp_should_abort(A.ws.ctl, t0)) {
+        if (!help_one(B, X, win, own, G, hint)) __nanosleep(100);
+        if (warp_should_abort(X.ws.ctl, t0)) {
             if (lane == 0) *s_flag = 1;
             break;
         }
@@ -939,29 +1036,25 @@ __device__ bool run_task(const TrialArgs& A, float4* win, int j, int stY, int nu
     return *s_flag == 0;
 }
 
-template <int S>
-__global__ void __launch_bounds__(kTrialThreads, 3) k_trials(const TrialArgs A) {
-    constexpr int r = (S - 1) / 2;
-    constexpr int NB = (2 * r + 1) * (2 * r + 1);  // blocks within r of one LR pixel
+__global__ void __launch_bounds__(kTrialThreads, 3)
+    k_trials(const __grid_constant__ JBatch B, const TrialCtx X) {
     constexpr int kPend = 512;
-    JointCtl* ctl = A.ws.ctl;
-    if (!is_active(ctl)) return;
-    __shared__ float4 wins[kTrialThreads / 32][S * S];
+    JointCtl* ctl = X.ws.ctl;
+    if (!any_active(ctl)) return;
+    __shared__ float4 wins[kTrialThreads / 32][kSmax * kSmax];
     __shared__ int s_j, s_nu, s_accept, s_flag, s_npend, s_povf;
     __shared__ int s_pend[kPend];
     __shared__ unsigned long long s_e0, s_e1;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int G = gridDim.x;
     const int M = ctl->M_cur;
-    const int D = A.strict ? 2 * r : r;
-    const int ND = (2 * D + 1) * (2 * D + 1);
-    const JointWs& W_ = A.ws;
+    const JointWs& W_ = X.ws;
     float4* win = wins[warp];
     const unsigned long long t0 = now_ns();
 
     for (;;) {
         if (tid == 0) {
-            s_j = atomicAdd(&ctl->claim[A.it], 1);
+            s_j = atomicAdd(&ctl->claim[X.it], 1);
             s_nu = 0;
             s_e0 = 0;
             s_e1 = 0;
@@ -972,17 +1065,23 @@ __global__ void __launch_bounds__(kTrialThreads, 3) k_trials(const TrialArgs A) 
         __syncthreads();
         const int j = s_j;
         if (j >= M) break;
-        GLU_TRACE(A.it, j, 0);
+        GLU_TRACE(X.it, j, 0);
         const int2 st = W_.start[j], en = W_.start[j + 1];
+        const int img = img_of_p(B, W_.roots[j]);
+        const JImg& I = B.im[img];
+        const int r = (I.S - 1) / 2;
+        const int D = B.strict ? 2 * r : r;
+        const int ND = (2 * D + 1) * (2 * D + 1);
 
         // 1. the earlier components whose LR blocks lie within D of ours and are not done yet
         const int npairs = (en.y - st.y) * ND;
         for (int t = tid; t < npairs; t += kTrialThreads) {
-            const int q = W_.qlist[st.y + t / ND];
+            const int64_t lq = (int64_t)W_.qlist[st.y + t / ND] - I.q0;
             const int nb = t % ND;
-            const int bv = q / A.w + nb / (2 * D + 1) - D, bu = q % A.w + nb % (2 * D + 1) - D;
-            if (bv < 0 || bv >= A.h || bu < 0 || bu >= A.w) continue;
-            const int64_t b = (int64_t)bv * A.w + bu;
+            const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+            const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+            if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
+            const int64_t b = I.q0 + (int64_t)bv * I.w + bu;
             if (__ldcg(&W_.ovf[b])) {
                 s_povf = 1;  // more components than owner slots: wait for every earlier one
                 continue;
@@ -1015,7 +1114,7 @@ __global__ void __launch_bounds__(kTrialThreads, 3) k_trials(const TrialArgs A) 
                     }
                 }
                 if (__syncthreads_or(mine) == 0) break;
-                if (!help_one<S>(A, win, blockIdx.x, G, hint)) __nanosleep(200);
+                if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
                 const int abort = warp_should_abort(ctl, t0) ? 1 : 0;
                 if (__syncthreads_or(abort)) {
                     if (tid == 0) s_flag = 1;
@@ -1030,15 +1129,15 @@ __global__ void __launch_bounds__(kTrialThreads, 3) k_trials(const TrialArgs A) 
                 set_status(GLU_ERR_TIMEOUT);
                 atomicExch(&ctl->timeout, 1);
                 st_release(&W_.done[j], 1);  // never leave a later component waiting on us
-                atomicAdd(&ctl->finished[A.it], 1);
+                atomicAdd(&ctl->finished[X.it], 1);
             }
             __syncthreads();
             continue;
         }
-        GLU_TRACE(A.it, j, 1);
+        GLU_TRACE(X.it, j, 1);
 
         // 2. the distinct LR blocks Q of the component (stamps drop duplicates)
-        const unsigned long long tagQ = trial_tag(A.it, j, 0);
+        const unsigned long long tagQ = trial_tag(X.it, j, 0);
         for (int t = st.y + tid; t < en.y; t += kTrialThreads) {
             const int q = W_.qlist[t];
             if (atomicExch(&W_.stamp[q], tagQ) != tagQ) {
@@ -1053,42 +1152,45 @@ __global__ void __launch_bounds__(kTrialThreads, 3) k_trials(const TrialArgs A) 
         //    (ties: lowest raster index)
         for (int t = st.x + tid; t < en.x; t += kTrialThreads) {
             const int p = W_.comp_pix[t];
-            const int y = p / A.W, x = p % A.W;
-            const int q = (y / A.s) * A.w + (x / A.s);
+            const int64_t lp = p - I.p0;
+            const int y = (int)(lp / I.W), x = (int)(lp % I.W);
+            const int64_t q = I.q0 + (int64_t)(y / I.s) * I.w + (x / I.s);
             const unsigned long long key =
-                ((unsigned long long)__float_as_uint(__ldcg(&A.err[p])) << 32) |
-                (unsigned long long)(0xFFFFFFFFu - (uint32_t)p);
+                ((unsigned long long)__float_as_uint(__ldcg(&I.err[lp])) << 32) |
+                (unsigned long long)(0xFFFFFFFFu - (uint32_t)lp);
             atomicMax(&W_.best[q], key);
         }
         __syncthreads();
         // 4. back up and replace the LR colours
         for (int t = tid; t < nu; t += kTrialThreads) {
-            const int q = W_.ulist[st.y + t];
-            const int qv = q / A.w, qu = q % A.w;
-            const uint32_t p = 0xFFFFFFFFu - (uint32_t)(__ldcg(&W_.best[q]) & 0xFFFFFFFFull);
-            const int y = (int)(p / (uint32_t)A.W), x = (int)(p % (uint32_t)A.W);
-            W_.backup[q] = load_rgb(A.lr, A.lr_pitch, qv, qu);
-            const uint8_t* ip = A.hr + (int64_t)y * A.hr_pitch + (int64_t)x * 3;
-            store_rgb(A.lr, A.lr_pitch, qv, qu,
+            const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
+            const int qv = (int)(lq / I.w), qu = (int)(lq % I.w);
+            const uint32_t lp =
+                0xFFFFFFFFu - (uint32_t)(__ldcg(&W_.best[I.q0 + lq]) & 0xFFFFFFFFull);
+            const int y = (int)(lp / (uint32_t)I.W), x = (int)(lp % (uint32_t)I.W);
+            W_.backup[I.q0 + lq] = load_rgb(I.lr, I.lr_pitch, qv, qu);
+            const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
+            store_rgb(I.lr, I.lr_pitch, qv, qu,
                       (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16));
         }
         __threadfence();
         __syncthreads();
 
         // 5. trial: Algorithm 1 again on the affected pixels (STRICT: every block within r of
-        //    Q; PAPER: the component's own pixels) into the shadow planes, summing e0 and e1
-        const int nitems = A.strict ? nu * NB : nu;
-        bool ok = run_task<S>(A, win, j, st.y, nu, 0, nitems, G, &s_e0, &s_e1, &s_flag, t0);
+        //    Q; PAPER: the component's own pixels), in place, summing e0 and e1
+        const int NB = (2 * r + 1) * (2 * r + 1);
+        const int nitems = B.strict ? nu * NB : nu;
+        bool ok = run_task(B, X, win, j, img, st.y, 0, nitems, G, &s_e0, &s_e1, &s_flag, t0);
         if (tid == 0) s_accept = !(s_e1 > s_e0);
         __syncthreads();
-        GLU_TRACE(A.it, j, 2);
+        GLU_TRACE(X.it, j, 2);
         // 6. keep (nothing to do: the results are in place) or roll back: restore Theta and E
         //    from the backup planes and the LR colours from their backups
         if (!s_accept && ok) {
-            ok = run_task<S>(A, win, j, st.y, nu, 1, nitems, G, &s_e0, &s_e1, &s_flag, t0);
+            ok = run_task(B, X, win, j, img, st.y, 1, nitems, G, &s_e0, &s_e1, &s_flag, t0);
             for (int t = tid; t < nu; t += kTrialThreads) {
-                const int q = W_.ulist[st.y + t];
-                store_rgb(A.lr, A.lr_pitch, q / A.w, q % A.w, W_.backup[q]);
+                const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
+                store_rgb(I.lr, I.lr_pitch, (int)(lq / I.w), (int)(lq % I.w), W_.backup[I.q0 + lq]);
             }
         }
         __syncthreads();
@@ -1098,13 +1200,13 @@ __global__ void __launch_bounds__(kTrialThreads, 3) k_trials(const TrialArgs A) 
                 atomicExch(&ctl->timeout, 1);
             }
             __threadfence();
-            W_.dlog[(int64_t)A.it * W_.mcap + j] = (int8_t)(s_accept ? 1 : 0);
-            if (s_accept) atomicAdd(&ctl->accepted[A.it], 1);
-            else atomicAdd(&ctl->rolled[A.it], 1);
+            W_.dlog[(int64_t)X.it * W_.mcap + j] = (int8_t)(s_accept ? 1 : 0);
+            if (s_accept) atomicAdd(&ctl->accepted[img][X.it], 1);
+            else atomicAdd(&ctl->rolled[img][X.it], 1);
             st_release(&W_.done[j], 1);
-            atomicAdd(&ctl->finished[A.it], 1);
+            atomicAdd(&ctl->finished[X.it], 1);
         }
-        GLU_TRACE(A.it, j, 3);
+        GLU_TRACE(X.it, j, 3);
         __syncthreads();
     }
     // no component left to claim: help the running ones until every component is done
@@ -1113,9 +1215,9 @@ __global__ void __launch_bounds__(kTrialThreads, 3) k_trials(const TrialArgs A) 
     int hint = -1;
     for (;;) {
         int fin = 0;
-        if (lane == 0) fin = *(volatile const int*)&ctl->finished[A.it] >= M;
+        if (lane == 0) fin = *(volatile const int*)&ctl->finished[X.it] >= M;
         if (__shfl_sync(0xffffffffu, fin, 0)) break;
-        if (!help_one<S>(A, win, blockIdx.x, G, hint)) __nanosleep(200);
+        if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
         if (warp_should_abort(ctl, t0)) break;
     }
 }
@@ -1135,19 +1237,18 @@ static int grid_cap(int64_t work, int threads, int per_sm = 16) {
     return (int)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
 }
 
-template <int S>
-static int launch_trials(const TrialArgs& A, cudaStream_t st) {
+static int launch_trials(const JBatch& B, const TrialCtx& X, cudaStream_t st) {
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trials<S>, kTrialThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trials, kTrialThreads, 0) !=
             cudaSuccess)
             return GLU_ERR_CUDA;
         blocks_per_sm = nb > 0 ? nb : 1;
     }
     int grid = sm_count() * blocks_per_sm;
     if (grid > kMaxSlots) grid = kMaxSlots;
-    k_trials<S><<<grid, kTrialThreads, 0, st>>>(A);
+    k_trials<<<grid, kTrialThreads, 0, st>>>(B, X);
     GLU_LAUNCH_CHECK();
     return GLU_OK;
 }
@@ -1166,120 +1267,181 @@ static void mark(int slot, int i, cudaStream_t st) {
 }
 }  // namespace prof
 
-int launch_joint(const JointArgs& a, void* wsp, size_t ws_bytes, glu_joint_stats* stats,
-                 cudaStream_t st) {
+int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, void* wsp,
+                       size_t ws_bytes, glu_joint_stats* stats, cudaStream_t st) {
+    if (n <= 0) return GLU_OK;
+    if (n > kMaxJointBatch) return GLU_ERR_UNSUPPORTED;
+    static std::mutex mu;  // the parameter staging block and the stats copy are shared
+    std::lock_guard<std::mutex> lock(mu);
+    int64_t np, nq, nch;
+    batch_sizes(items, n, &np, &nq, &nch);
+    if (np >= (int64_t)0x7fffffff) return GLU_ERR_UNSUPPORTED;  // 32-bit pixel ids
+    JointWs ws;
+    const size_t need = carve(wsp, np, nq, n, cm.N, nch, &ws);
+    if (ws_bytes < need) return GLU_ERR_WORKSPACE;
     int slot = -1;
     if (prof::enabled && prof::used < prof::kSlots) slot = prof::used++;
     int evi = 0;
-    JointWs ws;
-    const size_t need = carve(wsp, a.H, a.W, a.h, a.w, a.N, &ws);
-    if (ws_bytes < need) return GLU_ERR_WORKSPACE;
-    float* err = a.err ? a.err : ws.err;
-    const int64_t n = (int64_t)a.H * a.W, nl = (int64_t)a.h * a.w;
+
+    static JBatch B;   // host staging of the parameter block (copied at each launch)
+    memset(&B, 0, sizeof(B));
+    int64_t p0 = 0, q0 = 0;
+    int c0 = 0;
+    for (int k = 0; k < n; ++k) {
+        const JointItem& a = items[k];
+        JImg& I = B.im[k];
+        I.hr = a.hr;
+        I.hr_pitch = a.hr_pitch;
+        I.lr = a.lr;
+        I.lr_pitch = a.lr_pitch;
+        I.code = a.code;
+        I.weight = a.weight;
+        I.err = a.err ? a.err : ws.err + p0;
+        I.H = a.H; I.W = a.W; I.s = a.s; I.S = a.S;
+        I.h = (a.H + a.s - 1) / a.s;
+        I.w = (a.W + a.s - 1) / a.s;
+        I.p0 = p0;
+        I.q0 = q0;
+        I.c0 = c0;
+        p0 += (int64_t)a.H * a.W;
+        q0 += (int64_t)I.h * I.w;
+        c0 += (int)(((int64_t)a.H * a.W + kResidChunk - 1) / kResidChunk);
+    }
+    B.n = n;
+    B.wfmt = cm.wfmt;
+    B.strict = cm.strict;
+    B.conn = cm.conn;
+    B.eps255 = cm.eps255;
+    B.tau = cm.tau;
+    B.np = np;
+    B.nq = nq;
+    B.nchunks = c0;
     const int T = 256;
 
     prof::mark(slot, evi++, st);
-    k_ctl_init<<<grid_cap(nl > kMaxSlots ? nl : kMaxSlots, T), T, 0, st>>>(ws.ctl, ws.stamp, nl,
-                                                                          ws.slot_word);
+    k_ctl_init<<<grid_cap(nq > kMaxSlots ? nq : kMaxSlots, T), T, 0, st>>>(ws.ctl, ws.stamp, nq,
+                                                                          ws.slot_word, n);
+    // initialise every LR image by regular grid downsampling, Theta and E by Algorithm 1
+    k_grid_batch<<<grid_cap(nq, T), T, 0, st>>>(B);
     GLU_LAUNCH_CHECK();
-    // initialise the LR image by regular grid downsampling, Theta and E by Algorithm 1
-    glu_image hr{const_cast<uint8_t*>(a.hr), a.H, a.W, 3, GLU_U8, a.hr_pitch};
-    glu_image lr{a.lr, a.h, a.w, 3, GLU_U8, a.lr_pitch};
-    int rc = launch_downsample(hr, a.s, GLU_DOWN_GRID, lr, st);
-    if (rc) return rc;
-    SearchArgs sa;
-    sa.hr = a.hr; sa.hr_pitch = a.hr_pitch; sa.hr_dtype = GLU_U8;
-    sa.lr = a.lr; sa.lr_pitch = a.lr_pitch; sa.lr_dtype = GLU_U8;
-    sa.H = a.H; sa.W = a.W; sa.h = a.h; sa.w = a.w; sa.s = a.s; sa.S = a.S;
-    sa.eps255 = a.eps255; sa.gnu = 0;
-    sa.code = a.code; sa.weight = a.weight; sa.wfmt = a.wfmt; sa.err = err;
+    SearchArgs sa[kMaxJointBatch];
+    for (int k = 0; k < n; ++k) {
+        const JImg& I = B.im[k];
+        SearchArgs& a = sa[k];
+        a.hr = I.hr; a.hr_pitch = I.hr_pitch; a.hr_dtype = GLU_U8;
+        a.lr = I.lr; a.lr_pitch = I.lr_pitch; a.lr_dtype = GLU_U8;
+        a.H = I.H; a.W = I.W; a.h = I.h; a.w = I.w; a.s = I.s; a.S = I.S;
+        a.eps255 = cm.eps255; a.gnu = 0;
+        a.code = I.code; a.weight = I.weight; a.wfmt = cm.wfmt; a.err = I.err;
+    }
     prof::mark(slot, evi++, st);
-    rc = launch_search(sa, st);
+    int rc = launch_search_batch(sa, n, st);
     if (rc) return rc;
     prof::mark(slot, evi++, st);
-    const int nres = (int)((n + kResidChunk - 1) / kResidChunk);
-    k_resid_partial<<<nres, 256, 0, st>>>(err, n, ws.partial, ws.ctl);
-    k_resid_final<<<1, 256, 0, st>>>(ws.partial, nres, ws.ctl, -1);
+    k_resid_partial<<<B.nchunks, 256, 0, st>>>(B, ws.partial, ws.ctl);
+    k_resid_final<<<1, 256, 0, st>>>(B, ws.partial, ws.ctl, -1);
     GLU_LAUNCH_CHECK();
     prof::mark(slot, evi++, st);
 
-    const int tiles_a = (int)((n + kScanTile - 1) / kScanTile);
-    const int64_t mcap = mcap_of(a.H, a.W);
-    const int tiles_b = (int)((mcap + kScanTile - 1) / kScanTile);
-    TrialArgs ta;
-    ta.hr = a.hr; ta.hr_pitch = a.hr_pitch; ta.lr = a.lr; ta.lr_pitch = a.lr_pitch;
-    ta.H = a.H; ta.W = a.W; ta.h = a.h; ta.w = a.w; ta.s = a.s;
-    ta.eps255 = a.eps255; ta.strict = a.strict;
-    ta.code = a.code; ta.weight = a.weight; ta.wfmt = a.wfmt; ta.err = err; ta.ws = ws;
+    const int tiles_a = (int)((np + kScanTile - 1) / kScanTile);
+    const int tiles_b = (int)((ws.mcap + kScanTile - 1) / kScanTile);
+    TrialCtx X;
+    X.ws = ws;
 
-    for (int it = 0; it < a.N; ++it) {
-        k_threshold<<<grid_cap(n, T), T, 0, st>>>(err, n, a.tau, ws.lab, ws.own, ws.ovf, nl, ws.ctl, it);
-        k_ccl_merge<<<grid_cap(n, T), T, 0, st>>>(ws.lab, a.H, a.W, a.conn, ws.ctl);
-        k_ccl_flatten<<<grid_cap(n, T), T, 0, st>>>(ws.lab, n, ws.ctl);
-        k_root_count<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, n, ws.tile_a, ws.ctl);
-        k_root_scan<<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl, it);
-        k_root_scatter<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, n, ws.tile_a, ws.roots, ws.cnt,
-                                                         ws.fill, ws.done, ws.ctl);
-        k_comp_count<<<grid_cap(n, T), T, 0, st>>>(ws.lab, a.H, a.W, a.s, a.w, ws.roots, ws.cnt,
-                                                   ws.own, ws.ovf, ws.qflag, ws.ctl);
+    for (int it = 0; it < cm.N; ++it) {
+        k_threshold<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.own, ws.ovf, ws.ctl, it);
+        k_ccl_merge<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.ctl);
+        k_ccl_flatten<<<grid_cap(np, T), T, 0, st>>>(ws.lab, np, ws.ctl);
+        k_root_count<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, np, ws.tile_a, ws.ctl);
+        k_root_scan<<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
+        k_root_scatter<<<tiles_a, kScanThreads, 0, st>>>(B, ws.lab, ws.tile_a, ws.roots, ws.cnt,
+                                                         ws.fill, ws.done, ws.ctl, it);
+        k_comp_count<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.roots, ws.cnt, ws.own, ws.ovf,
+                                                    ws.qflag, ws.ctl);
         k_comp_tile_reduce<<<tiles_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.ctl);
         k_comp_tile_scan<<<1, kScanThreads, 0, st>>>(ws.tile_b, ws.ctl);
         k_comp_scan<<<tiles_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.start, ws.ctl);
-        k_comp_fill<<<grid_cap(n, T), T, 0, st>>>(ws.lab, a.H, a.W, a.s, a.w, ws.qflag, ws.start,
-                                                  ws.fill, ws.comp_pix, ws.qlist, ws.ctl);
+        k_comp_fill<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.qflag, ws.start, ws.fill,
+                                                   ws.comp_pix, ws.qlist, ws.ctl);
         GLU_LAUNCH_CHECK();
         prof::mark(slot, evi++, st);
-        ta.it = it;
-        switch (a.S) {
-            case 1: rc = launch_trials<1>(ta, st); break;
-            case 3: rc = launch_trials<3>(ta, st); break;
-            case 5: rc = launch_trials<5>(ta, st); break;
-            case 7: rc = launch_trials<7>(ta, st); break;
-            case 9: rc = launch_trials<9>(ta, st); break;
-            default: return GLU_ERR_UNSUPPORTED;
-        }
+        X.it = it;
+        rc = launch_trials(B, X, st);
         if (rc) return rc;
         prof::mark(slot, evi++, st);
-        k_resid_partial<<<nres, 256, 0, st>>>(err, n, ws.partial, ws.ctl);
-        k_resid_final<<<1, 256, 0, st>>>(ws.partial, nres, ws.ctl, it);
+        k_resid_partial<<<B.nchunks, 256, 0, st>>>(B, ws.partial, ws.ctl);
+        k_resid_final<<<1, 256, 0, st>>>(B, ws.partial, ws.ctl, it);
         GLU_LAUNCH_CHECK();
         prof::mark(slot, evi++, st);
     }
     if (slot >= 0) prof::nev[slot] = evi;
     if (stats) {
-        JointCtl h;
+        static JointCtl h;
         GLU_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
         GLU_CUDA_TRY(cudaStreamSynchronize(st));
-        memset(stats, 0, sizeof(*stats));
-        stats->iterations = h.iterations;
-        for (int k = 0; k < GLU_MAX_ITERS; ++k) {
-            stats->n_large[k] = h.n_large[k];
-            stats->components[k] = h.M[k];
-            stats->accepted[k] = h.accepted[k];
-            stats->rolled_back[k] = h.rolled[k];
+        for (int i = 0; i < n; ++i) {
+            glu_joint_stats& o = stats[i];
+            memset(&o, 0, sizeof(o));
+            o.iterations = h.iterations[i];
+            for (int k = 0; k < GLU_MAX_ITERS; ++k) {
+                o.n_large[k] = h.n_large[i][k];
+                o.components[k] = h.M[i][k];
+                o.accepted[k] = h.accepted[i][k];
+                o.rolled_back[k] = h.rolled[i][k];
+                o.searched[k] = (int64_t)h.searched[i][k];
+            }
+            for (int k = 0; k <= h.iterations[i] && k <= GLU_MAX_ITERS; ++k)
+                o.residual[k] = h.residual[i][k];
         }
-        for (int k = 0; k <= h.iterations && k <= GLU_MAX_ITERS; ++k) stats->residual[k] = h.residual[k];
-        for (int k = 0; k < GLU_MAX_ITERS; ++k) stats->searched[k] = (int64_t)h.searched[k];
         if (h.timeout) return GLU_ERR_TIMEOUT;
     }
     return GLU_OK;
 }
 
+int launch_joint(const JointArgs& a, void* ws, size_t ws_bytes, glu_joint_stats* stats,
+                 cudaStream_t st) {
+    JointItem it;
+    it.hr = a.hr;
+    it.hr_pitch = a.hr_pitch;
+    it.lr = a.lr;
+    it.lr_pitch = a.lr_pitch;
+    it.H = a.H;
+    it.W = a.W;
+    it.s = a.s;
+    it.S = a.S;
+    it.code = a.code;
+    it.weight = a.weight;
+    it.err = a.err;
+    JointCommon cm;
+    cm.eps255 = a.eps255;
+    cm.tau = a.tau;
+    cm.N = a.N;
+    cm.strict = a.strict;
+    cm.conn = a.conn;
+    cm.wfmt = a.wfmt;
+    return launch_joint_batch(&it, 1, cm, ws, ws_bytes, stats, st);
+}
+
 int joint_decisions(const void* wsp, size_t ws_bytes, int H, int W, int s, int N, int8_t* out,
                     int64_t cap, cudaStream_t st, int64_t* written) {
-    const int h = (H + s - 1) / s, w = (W + s - 1) / s;
+    JointItem it{};
+    it.H = H;
+    it.W = W;
+    it.s = s;
+    int64_t np, nq, nch;
+    batch_sizes(&it, 1, &np, &nq, &nch);
     JointWs ws;
-    const size_t need = carve(const_cast<void*>(wsp), H, W, h, w, N, &ws);
+    const size_t need = carve(const_cast<void*>(wsp), np, nq, 1, N, nch, &ws);
     if (ws_bytes < need) return GLU_ERR_WORKSPACE;
-    JointCtl c;
+    static JointCtl c;
     GLU_CUDA_TRY(cudaMemcpyAsync(&c, ws.ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
     GLU_CUDA_TRY(cudaStreamSynchronize(st));
     int64_t off = 0;
-    for (int it = 0; it < c.iterations && it < N; ++it) {
-        const int64_t m = c.M[it];
+    for (int k = 0; k < c.iterations[0] && k < N; ++k) {
+        const int64_t m = c.M[0][k];
         if (off + m > cap) return GLU_ERR_INVALID_ARG;
         if (m > 0)
-            GLU_CUDA_TRY(cudaMemcpyAsync(out + off, ws.dlog + (int64_t)it * ws.mcap, (size_t)m,
+            GLU_CUDA_TRY(cudaMemcpyAsync(out + off, ws.dlog + (int64_t)k * ws.mcap, (size_t)m,
                                          cudaMemcpyDeviceToHost, st));
         off += m;
     }

@@ -89,6 +89,50 @@ def test_host_validation_codes(lib):
     assert b"sm_103a" in lib.glu_version()
 
 
+def test_batched_host_validation(lib):
+    from paper_2307_09582_gb300 import _abi as A
+    p = A.GluParams()
+    lib.glu_params_default(ctypes.byref(p))
+    fake = ctypes.c_void_p(0x1000)
+    items = (A.GluBatchItem * 33)()
+    for k in range(33):
+        items[k].hr = A.GluImage(fake, 64 + k, 48, 3, A.GLU_U8, (64 + k) * 3)
+        items[k].hr.w, items[k].hr.pitch = 64 + k, (64 + k) * 3
+        items[k].hr.h = 48
+        h, w = (48 + 3) // 4, (64 + k + 3) // 4
+        items[k].lr = A.GluImage(fake, h, w, 3, A.GLU_U8, w * 3)
+        items[k].theta = A.GluTheta(fake, fake, 48, 64 + k, 4, 3 + 2 * (k % 2), A.GLU_W_F32)
+    # empty batches are no-ops; null item arrays are rejected
+    assert lib.glu_optimize_batched(None, 0, ctypes.byref(p), None) == A.GLU_OK
+    assert lib.glu_joint_optimize_batched(None, 0, ctypes.byref(p), None, None, 0, None) == \
+        A.GLU_OK
+    assert lib.glu_optimize_batched(None, 2, ctypes.byref(p), None) == A.GLU_ERR_INVALID_ARG
+    # more than 32 joint images, or a mixed weight format, is unsupported
+    assert lib.glu_joint_optimize_batched(items, 33, ctypes.byref(p), None, fake, 1 << 40,
+                                          None) == A.GLU_ERR_UNSUPPORTED
+    assert lib.glu_joint_batched_workspace_size(items, 33, ctypes.byref(p)) == 0
+    items[1].theta.wfmt = A.GLU_W_F16
+    assert lib.glu_joint_optimize_batched(items, 2, ctypes.byref(p), None, fake, 1 << 40,
+                                          None) == A.GLU_ERR_UNSUPPORTED
+    assert lib.glu_optimize_batched(items, 2, ctypes.byref(p), None) == A.GLU_ERR_UNSUPPORTED
+    items[1].theta.wfmt = A.GLU_W_F32
+    # a wrong LR size in any item is a shape error, before any launch
+    items[3].lr.h += 1
+    assert lib.glu_optimize_batched(items, 5, ctypes.byref(p), None) == A.GLU_ERR_SHAPE
+    assert lib.glu_joint_optimize_batched(items, 5, ctypes.byref(p), None, fake, 1 << 40,
+                                          None) == A.GLU_ERR_SHAPE
+    items[3].lr.h -= 1
+    # workspace: a batch of one needs what the single-image call needs; more images need more;
+    # too small a workspace is refused
+    p.S = items[0].theta.S
+    one = lib.glu_joint_batched_workspace_size(items, 1, ctypes.byref(p))
+    assert one == lib.glu_joint_workspace_size(48, 64, 4, ctypes.byref(p))
+    four = lib.glu_joint_batched_workspace_size(items, 4, ctypes.byref(p))
+    assert four > one
+    assert lib.glu_joint_optimize_batched(items, 4, ctypes.byref(p), None, fake, four - 1,
+                                          None) == A.GLU_ERR_WORKSPACE
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_2307_09582_gb300 import _abi as A
     with pytest.raises(RuntimeError, match="not found"):

@@ -25,6 +25,7 @@ sys.path.insert(0, ROOT)
 
 H4K, W4K, SCALE, WIN, NITER = 2160, 3840, 8, 5, 5
 BATCH_NITER = 3
+VIDEO_FRAMES = 120
 METRIC = "HR Mpix/s for GLU optimise+apply at 4K x8; batched/bwd vs plain; % of roofline"
 WORKLOAD = "joint-optimise+LRop+apply 3840x2160 x8, 5x5 window, 5 Alg.2 iterations, STRICT"
 # canonical FP32 lane operations of Algorithm 1 per window candidate (a-step 7, b-step 20)
@@ -228,6 +229,8 @@ def run_glu(args):
             for k, x in zip(("s", "j", "o", "e"), e):
                 ev[k].append(x)
 
+    # the autotuner picks the search and apply variants during the first warm-up step
+    api.tune_mode(True)
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         step(False)
@@ -302,6 +305,10 @@ def run_glu(args):
     e2e_tot = max_over_ranks(sum(e2e_ms), ws, dev)
     e2e_val = ws * npx * len(e2e_ms) / (e2e_tot / 1e3) / 1e6
 
+    names = {k: api.tune_variants(k) for k in (api.GLU_TUNE_SEARCH, api.GLU_TUNE_APPLY)}
+    tuned = [dict(kernel=("search", "apply")[int(f[0])], key=[int(x) for x in f[1:6]],
+                  variant=names[int(f[0])][int(f[6])], ms=float(f[7]))
+             for f in (l.split() for l in api.tune_export().splitlines())]
     extras = {}
     if args.extras and rank == 0:
         extras = measure_extras(api, torch, img, dev, flush, stream)
@@ -320,6 +327,7 @@ def run_glu(args):
                              d2h_bytes_per_step=out_host.numel() * 4),
                     gpu_launches=args.steps * (api.joint_launches(NITER) + 3),
                     clocks=clk.summary(),
+                    autotune=tuned,
                     breakdown=dict(joint_ms=statistics.mean(joint_ms),
                                    apply_ms=statistics.mean(apply_ms),
                                    joint_phases_ms={k: v / calls for k, v in prof.items()
@@ -381,6 +389,80 @@ def measure_extras(api, torch, img, dev, flush, stream):
     res["backward_ms"] = ms_b
     res["backward_vs_apply"] = ms_b / ms_a
     res["batch16"] = measure_batch(api, torch, dev, timed)
+    if VIDEO_FRAMES > 0:
+        res["video"] = measure_video(api, torch, dev, VIDEO_FRAMES)
+    return res
+
+
+def measure_video(api, torch, dev, n_frames):
+    """The video workload: n 3840x2160 float16 frames (cells moving 2 px/frame, 5% of dots
+    re-drawn per frame), BOX x8 -> 3x3 Gaussian + gamma 0.8 on the LR image -> Algorithm 1
+    (5x5) -> Eq. 1 into float16 frames. Every frame is a different resident buffer (5.97 GB in
+    all for 120 frames), so no frame's input is in L2 when it starts. Three ways of issuing the
+    same kernels: one CUDA graph per frame slot (LR operator forked beside Algorithm 1), the
+    same launches issued directly, and the separate Python-level calls one after another.
+    Per-frame latency = device time between the events around that frame's launches."""
+    import time
+    from paper_2307_09582_gb300.inputs import render_u8
+    from paper_2307_09582_gb300.inputs.workloads import video_scene
+    sc = video_scene()
+    H, W, s, S = sc.height, sc.width, 8, 5
+    t0 = time.time()
+    frames = torch.empty((n_frames, H, W, 3), dtype=torch.float16, device=dev)
+    for f in range(n_frames):
+        u8 = torch.from_numpy(render_u8(sc, frame=f)).to(dev)
+        frames[f] = (u8.to(torch.float32) / 255).to(torch.float16)
+    render_s = time.time() - t0
+    outs = torch.empty_like(frames)
+    p = api.glu_params(S=S)
+    st = torch.cuda.current_stream()
+
+    def timeline(issue):
+        for f in range(min(3, n_frames)):
+            issue(f)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_frames + 1)]
+        ev[0].record(st)
+        for f in range(n_frames):
+            issue(f)
+            ev[f + 1].record(st)
+        ev[-1].synchronize()
+        lat = sorted(ev[f].elapsed_time(ev[f + 1]) for f in range(n_frames))
+        tot = ev[0].elapsed_time(ev[-1])
+        pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+        return dict(fps=n_frames / (tot / 1e3), ms_total=tot, p50_ms=pct(0.5), p99_ms=pct(0.99))
+
+    res = dict(frames=n_frames, H=H, W=W, scale=s, window=S, render_s=render_s)
+    v = api.Video(H, W, s, p, out_dtype=torch.float16, overlap=True)
+    v.run(frames[0], outs[0])   # a direct frame first, so the tuner has chosen before capture
+    torch.cuda.synchronize()
+    for f in range(n_frames):
+        v.bind(f, frames[f], outs[f])
+    res["graph"] = timeline(lambda f: v.launch(f))
+    res["direct"] = timeline(lambda f: v.run(frames[f], outs[f]))
+    v.close()
+    vs = api.Video(H, W, s, p, out_dtype=torch.float16, overlap=False)
+    for f in range(n_frames):
+        vs.bind(f, frames[f], outs[f])
+    res["graph_no_fork"] = timeline(lambda f: vs.launch(f))
+    vs.close()
+    h, w = api.lr_dims(H, W, s)
+    lr = torch.empty((h, w, 3), dtype=torch.float32, device=dev)
+    t1, T = torch.empty_like(lr), torch.empty_like(lr)
+    theta = api.Theta.empty(H, W, s, S, api.GLU_W_UNORM16, dev)
+
+    def separate(f):
+        api.glu_downsample(frames[f], s, api.GLU_DOWN_BOX, lr=lr)
+        api.glu_fx_filter3(lr, 1, out=t1)
+        api.glu_fx_point(t1, 1.0, 0.8, out=T)
+        api.glu_optimize(frames[f], lr, p, s, theta=theta)
+        api.glu_apply(theta, T, out=outs[f])
+
+    res["separate_calls"] = timeline(separate)
+    res["graph_vs_separate"] = res["graph"]["fps"] / res["separate_calls"]["fps"]
+    res["gpu_launches_per_frame"] = 5
+    del frames, outs
+    torch.cuda.empty_cache()
     return res
 
 
@@ -471,7 +553,9 @@ def main():
     ap.add_argument("--kernel-case", choices=["search", "apply", "backward", "trials"],
                     help="run one kernel on a profiling case and exit (no JSON line)")
     ap.add_argument("--case-reps", type=int, default=3)
+    ap.add_argument("--video-frames", type=int, default=VIDEO_FRAMES)
     args = ap.parse_args()
+    globals()["VIDEO_FRAMES"] = args.video_frames
     if args.kernel_case:
         return run_kernel_case(args)
     if args.warmup < 3:

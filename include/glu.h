@@ -217,6 +217,33 @@ int glu_apply(const glu_theta* theta, const glu_image* lr_target, glu_image* hr_
 int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
                        const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* stream);
 
+/* Autotuner (not part of the method: implementation choice only). The Algorithm 1 search
+ * (GLU_TUNE_SEARCH: tile height x CTAs per SM x candidate loop schedule) and the tiled Eq. 1
+ * apply (GLU_TUNE_APPLY: tile height) have several implementation variants that compute the same
+ * arithmetic in the same order, so every variant gives bit-identical results. A launch picks, in
+ * order: the variant forced by glu_tune_force(); the cached choice for its shape class (guide or
+ * output dtype, weight format or mode, window, scale, ceil(log2(pixels))); with tuning on
+ * (glu_tune_mode(1)) and the stream not capturing a graph, the fastest variant timed on the
+ * call's own inputs (that first call synchronises its stream and runs every variant 4 times);
+ * otherwise variant 0. Choices are process-wide; glu_tune_export() / glu_tune_import() move them
+ * between processes as text lines "kernel k0 k1 k2 k3 k4 variant ms". Thread-safe. */
+#define GLU_TUNE_SEARCH 0
+#define GLU_TUNE_APPLY 1
+int glu_tune_mode(int32_t on);
+/* Number of variants of a kernel, or GLU_ERR_INVALID_ARG. */
+int32_t glu_tune_variants(int32_t kernel);
+/* Description of a variant into buf (NUL-terminated, truncated to cap). */
+int glu_tune_variant_name(int32_t kernel, int32_t variant, char* buf, int32_t cap);
+/* Force a variant for every later launch of the kernel (-1: back to cached / tuned choices). */
+int glu_tune_force(int32_t kernel, int32_t variant);
+/* Write the cached choices to buf if cap is large enough; returns the bytes needed (with NUL). */
+int64_t glu_tune_export(char* buf, int64_t cap);
+/* Merge choices from text written by glu_tune_export(); GLU_ERR_INVALID_ARG on a bad line
+ * (nothing merged then). */
+int glu_tune_import(const char* text);
+/* Forget every cached choice. */
+int glu_tune_clear(void);
+
 /* Name of a status code (static string). */
 const char* glu_status_string(int status);
 

@@ -18,7 +18,7 @@ import torch
 from . import _abi as A
 from ._abi import (GLU_DOWN_BOX, GLU_DOWN_GRID, GLU_F16, GLU_F32, GLU_JOINT_PAPER,  # noqa: F401
                    GLU_JOINT_STRICT, GLU_MODE_FAST, GLU_MODE_GNU, GLU_U8, GLU_W_F16, GLU_W_F32,
-                   GLU_W_UNORM16, GluError)
+                   GLU_TUNE_APPLY, GLU_TUNE_SEARCH, GLU_W_UNORM16, GluError)
 
 _DT = {torch.uint8: A.GLU_U8, torch.float16: A.GLU_F16, torch.float32: A.GLU_F32}
 _WT = {A.GLU_W_F32: torch.float32, A.GLU_W_F16: torch.float16, A.GLU_W_UNORM16: torch.int16}
@@ -256,6 +256,82 @@ def glu_joint_optimize_batched(hrs, scales, params: A.GluParams, Ss=None, lrs=No
             for k in range(n)]
 
 
+
+
+class Video:
+    """Per-frame pipeline (BOX downsample -> 3x3 filter + saturation + gamma on the LR image ->
+    Algorithm 1 -> Eq. 1) with one CUDA graph per bound (frame, output) slot. The workspace
+    (LR images and Theta) is a torch tensor owned here."""
+
+    def __init__(self, H, W, scale, params: A.GluParams, hr_dtype=torch.float16,
+                 out_dtype=torch.float16, wfmt=A.GLU_W_UNORM16, filter=1, saturation=1.0,
+                 gamma=0.8, overlap=True, device="cuda"):
+        d = A.GluVideoDesc()
+        d.H, d.W, d.scale = H, W, scale
+        d.hr_dtype, d.out_dtype = _DT[hr_dtype], _DT[out_dtype]
+        d.params = params
+        d.wfmt, d.filter, d.saturation, d.gamma = wfmt, filter, saturation, gamma
+        d.overlap = 1 if overlap else 0
+        self.desc, self.H, self.W, self.scale, self.S = d, H, W, scale, params.S
+        self.out_dtype, self.wfmt = out_dtype, wfmt
+        need = int(lib().glu_video_workspace_size(ctypes.byref(d)))
+        if need == 0:
+            A.check("glu_video_workspace_size", A.GLU_ERR_INVALID_ARG)
+        self.ws = torch.empty(need + 256, dtype=torch.uint8, device=device)
+        aligned, avail = _aligned(self.ws)
+        h = ctypes.c_void_p()
+        A.check("glu_video_create", lib().glu_video_create(ctypes.byref(d), ctypes.c_void_p(aligned),
+                                                           avail, ctypes.byref(h)))
+        self.h = h
+        self._bound = {}
+
+    def bind(self, slot: int, hr: torch.Tensor, out: torch.Tensor) -> None:
+        assert hr.is_contiguous() and out.is_contiguous()
+        assert hr.shape == (self.H, self.W, 3) and out.shape == (self.H, self.W, 3)
+        A.check("glu_video_bind", lib().glu_video_bind(self.h, slot, ctypes.c_void_p(hr.data_ptr()),
+                                                       ctypes.c_void_p(out.data_ptr())))
+        self._bound[slot] = (hr, out)   # keep the buffers alive while the graph refers to them
+
+    def launch(self, slot: int, stream=None) -> None:
+        A.check("glu_video_launch", lib().glu_video_launch(self.h, slot, _stream(stream)))
+
+    def run(self, hr: torch.Tensor, out: torch.Tensor, stream=None) -> None:
+        assert hr.is_contiguous() and out.is_contiguous()
+        A.check("glu_video_run", lib().glu_video_run(self.h, ctypes.c_void_p(hr.data_ptr()),
+                                                     ctypes.c_void_p(out.data_ptr()),
+                                                     _stream(stream)))
+
+    def views(self):
+        """(lr, target, Theta) views into the workspace, as torch tensors."""
+        li, ti, th = A.GluImage(), A.GluImage(), A.GluTheta()
+        A.check("glu_video_views", lib().glu_video_views(self.h, ctypes.byref(li),
+                                                         ctypes.byref(ti), ctypes.byref(th)))
+        base = self.ws.data_ptr()
+
+        def view(ptr, n, dtype, shape):
+            off = ptr - base
+            esz = torch.empty((), dtype=dtype).element_size()
+            return self.ws[off:off + n * esz].view(dtype).view(shape)
+
+        lr = view(li.data, li.h * li.w * 3, torch.float32, (li.h, li.w, 3))
+        T = view(ti.data, ti.h * ti.w * 3, torch.float32, (ti.h, ti.w, 3))
+        code = view(th.code, self.H * self.W, torch.int16, (self.H, self.W))
+        weight = view(th.weight, self.H * self.W, _WT[self.wfmt], (self.H, self.W))
+        return lr, T, Theta(code, weight, self.H, self.W, self.scale, self.S, self.wfmt)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().glu_video_destroy(self.h)
+            self.h = None
+            self._bound = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def glu_apply(theta: Theta, lr_target: torch.Tensor, out: torch.Tensor | None = None,
               out_dtype=torch.float32, weight: torch.Tensor | None = None, stream=None):
     """Eq. 1. `weight` (float32, H x W) overrides the stored weights (used by autograd)."""
@@ -306,6 +382,42 @@ def joint_launches(N: int) -> int:
     iteration threshold, merge, flatten, 3 root-compaction, count, 3 scan, fill, trials and the
     residual (2)."""
     return 5 + 14 * N
+
+
+def tune_mode(on: bool) -> None:
+    A.check("glu_tune_mode", lib().glu_tune_mode(1 if on else 0))
+
+
+def tune_variants(kernel: int) -> list:
+    """Descriptions of a kernel's variants (GLU_TUNE_SEARCH / GLU_TUNE_APPLY)."""
+    n = int(lib().glu_tune_variants(kernel))
+    if n < 0:
+        A.check("glu_tune_variants", n)
+    out = []
+    for v in range(n):
+        buf = ctypes.create_string_buffer(128)
+        A.check("glu_tune_variant_name", lib().glu_tune_variant_name(kernel, v, buf, 128))
+        out.append(buf.value.decode())
+    return out
+
+
+def tune_force(kernel: int, variant: int) -> None:
+    A.check("glu_tune_force", lib().glu_tune_force(kernel, variant))
+
+
+def tune_export() -> str:
+    n = int(lib().glu_tune_export(None, 0))
+    buf = ctypes.create_string_buffer(n)
+    lib().glu_tune_export(buf, n)
+    return buf.value.decode()
+
+
+def tune_import(text: str) -> None:
+    A.check("glu_tune_import", lib().glu_tune_import(text.encode()))
+
+
+def tune_clear() -> None:
+    A.check("glu_tune_clear", lib().glu_tune_clear())
 
 
 def glu_device_status(stream=None) -> int:

@@ -26,6 +26,7 @@ struct SearchArgs {
 };
 
 int launch_search(const SearchArgs& a, cudaStream_t st);
+constexpr int kMaxSearchBatch = 32;  // images per search launch (the kernel's parameter block)
 // Several images in one persistent launch; every item shares hr_dtype, wfmt, gnu and eps255.
 int launch_search_batch(const SearchArgs* items, int n, cudaStream_t st);
 

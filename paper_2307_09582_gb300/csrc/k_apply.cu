@@ -10,6 +10,8 @@
 // is bit-reproducible. This is the segmented reduction over the inverse pixel-to-LR map with the
 // map left implicit (the window bounds it, so it is never materialised).
 #include "internal.h"
+#include "tune.h"
+#include "variants.h"
 #include "common.cuh"
 
 namespace glu {
@@ -100,19 +102,48 @@ template <> struct W4<GLU_W_UNORM16> {
     }
 };
 
-// Eq. 1 fast path, tiled: a CTA owns kApplyTH x kApplyTW HR pixels; the LR region its windows
-// reach is copied to shared memory with coalesced row loads, so the 8 gathers per 4 pixels
-// are shared-memory reads. Codes and weights stream in as one 8-/16-byte load per 4 pixels,
-// results leave as three 16-byte streaming stores. Conditions as for k_apply3_vec.
-constexpr int kApplyTW = 128, kApplyTH = 8;
-template <int WF>
+// The 12 results of 4 pixels: three 16-byte stores (float32) or three 8-byte stores (float16).
+__device__ __forceinline__ void store12(float* out, const float r[12]) {
+    float4* o = (float4*)out;
+    __stcs(o + 0, make_float4(r[0], r[1], r[2], r[3]));
+    __stcs(o + 1, make_float4(r[4], r[5], r[6], r[7]));
+    __stcs(o + 2, make_float4(r[8], r[9], r[10], r[11]));
+}
+__device__ __forceinline__ void store12(__half* out, const float r[12]) {
+    uint2* o = (uint2*)out;
+    uint32_t u[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const __half2 h = __floats2half2_rn(r[2 * k], r[2 * k + 1]);
+        u[k] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    __stcs(o + 0, make_uint2(u[0], u[1]));
+    __stcs(o + 1, make_uint2(u[2], u[3]));
+    __stcs(o + 2, make_uint2(u[4], u[5]));
+}
+
+// Largest LR region (rows x columns) a tile of TH x kApplyTW HR pixels reaches.
+__host__ __device__ __forceinline__ int apply_region_floats(int th, int s, int S) {
+    const int r = (S - 1) / 2;
+    return 3 * ((th - 1) / s + 2 + 2 * r) * ((kApplyTW - 1) / s + 2 + 2 * r);
+}
+
+// Eq. 1 fast path, tiled: a CTA owns TH x kApplyTW HR pixels (a warp per row, 4 pixels per
+// lane). The LR region its windows reach is copied to shared memory with coalesced row loads,
+// so the 8 gathers per 4 pixels are shared-memory reads, and a per-CTA table turns a pair code
+// into the two region offsets relative to the window's corner (one lookup instead of the code's
+// division into window rows and columns). Codes and weights stream in as one 8-/16-byte load
+// per 4 pixels, results leave as three 16- (float32) or 8-byte (float16) streaming stores.
+// Conditions: 3 channels, float32 target, W % 4 == 0, aligned rows.
+template <int WF, typename OT, int TH>
 __global__ void __launch_bounds__(256) k_apply3_tile(const ApplyArgs P) {
-    extern __shared__ float reg[];   // RH x RW x 3
-    const int x0 = blockIdx.x * kApplyTW, y0 = blockIdx.y * kApplyTH;
-    const int s = P.s, S = P.S, r = (S - 1) >> 1, K = S * S;
-    const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + kApplyTH, P.H);
+    extern __shared__ float reg[];   // RH x RW x 3 region, then K*K offset pairs
+    const int x0 = blockIdx.x * kApplyTW, y0 = blockIdx.y * TH;
+    const int s = P.s, S = P.S, r = (S - 1) >> 1, K = S * S, K2 = K * K;
+    const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + TH, P.H);
     const int v0 = y0 / s - r, u0 = x0 / s - r;
     const int RH = (ye - 1) / s + r - v0 + 1, RW = (xe - 1) / s + r - u0 + 1;
+    uint32_t* tab = (uint32_t*)(reg + apply_region_floats(TH, s, S));
     const float* T = (const float*)P.T;
     // the LR region, clamped to the image (entries outside it are never selected by a valid code)
     for (int i = threadIdx.x; i < RH * RW * 3; i += blockDim.x) {
@@ -121,47 +152,77 @@ __global__ void __launch_bounds__(256) k_apply3_tile(const ApplyArgs P) {
         const int u = min(max(u0 + cc / 3, 0), P.w - 1);
         reg[i] = __ldg(T + (int64_t)v * P.T_pitch + (int64_t)u * 3 + cc % 3);
     }
+    // pair code -> (offset of T_a, offset of T_b) in the region, relative to the window corner
+    for (int c = threadIdx.x; c < K2; c += blockDim.x) {
+        const int ka = c / K, kb = c - ka * K;
+        const uint32_t oa = (uint32_t)(((ka / S) * RW + ka % S) * 3);
+        const uint32_t ob = (uint32_t)(((kb / S) * RW + kb % S) * 3);
+        tab[c] = oa | (ob << 16);
+    }
     __syncthreads();
-    const int ty = threadIdx.x >> 5, xg = (threadIdx.x & 31) * 4;
-    const int y = y0 + ty, xs = x0 + xg;
-    if (y >= P.H || xs >= P.W) return;
-    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
-    const int64_t p0 = (int64_t)y * P.W + xs;
-    const uint2 cc = __ldcs((const uint2*)P.code + (p0 >> 2));
-    const int code[4] = {(int)(cc.x & 0xFFFFu), (int)(cc.x >> 16), (int)(cc.y & 0xFFFFu),
-                         (int)(cc.y >> 16)};
-    float w[4];
-    W4<WF>::load(P.weight, p0, w);
-    const int rrow = y / s - r - v0;   // region row of the window's top row
-    float res[12];
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int xs = x0 + lane * 4;
+    if (xs >= P.W) return;
+    // every window of the tile inside the LR image: only the code range needs checking
+    const bool interior = v0 >= 0 && u0 >= 0 && (ye - 1) / s + r < P.h && (xe - 1) / s + r < P.w;
+    // window corner columns of the 4 pixels in the region: xs / s once, then at most three
+    // block boundaries within the next 3 pixels
+    const int c0 = xs / s, rem = xs - c0 * s;
+    int wcol[4], pxj[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int rcol = (xs + j) / s - r - u0;
-        const int ka = qdiv(code[j], invK), kb = code[j] - ka * K;
-        const int ra = qdiv(ka, invS), rb = qdiv(kb, invS);
-        int ia = ((rrow + ra) * RW + rcol + (ka - ra * S)) * 3;
-        int ib = ((rrow + rb) * RW + rcol + (kb - rb * S)) * 3;
-        // codes from the search never leave the LR image; anything else is recorded
-        const int va = y / s + ra - r, ua = (xs + j) / s + (ka - ra * S) - r;
-        const int vb = y / s + rb - r, ub = (xs + j) / s + (kb - rb * S) - r;
-        if ((unsigned)va >= (unsigned)P.h || (unsigned)ua >= (unsigned)P.w || ka >= K) {
-            set_status(GLU_ERR_DEVICE_CHECK);
-            ia = 0;
-        }
-        if ((unsigned)vb >= (unsigned)P.h || (unsigned)ub >= (unsigned)P.w || kb >= K) {
-            set_status(GLU_ERR_DEVICE_CHECK);
-            ib = 0;
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float ta = reg[ia + c], tb = reg[ib + c];
-            res[j * 3 + c] = __fmaf_rn(w[j], ta - tb, tb);
-        }
+        pxj[j] = c0 + (rem + j >= s) + (rem + j >= 2 * s) + (rem + j >= 3 * s);
+        wcol[j] = pxj[j] - r - u0;
     }
-    float4* o = (float4*)((float*)P.out + (int64_t)y * P.out_pitch + (int64_t)xs * 3);
-    __stcs(o + 0, make_float4(res[0], res[1], res[2], res[3]));
-    __stcs(o + 1, make_float4(res[4], res[5], res[6], res[7]));
-    __stcs(o + 2, make_float4(res[8], res[9], res[10], res[11]));
+    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
+    for (int ty = threadIdx.x >> 5; ty < TH; ty += nwarps) {
+        const int y = y0 + ty;
+        if (y >= P.H) break;
+        const int py = y / s;
+        const int wrow = py - r - v0;   // region row of the window's top row
+        const int64_t p0 = (int64_t)y * P.W + xs;
+        const uint2 cc = __ldcs((const uint2*)P.code + (p0 >> 2));
+        const int code[4] = {(int)(cc.x & 0xFFFFu), (int)(cc.x >> 16), (int)(cc.y & 0xFFFFu),
+                             (int)(cc.y >> 16)};
+        float w[4];
+        W4<WF>::load(P.weight, p0, w);
+        float res[12];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int base = (wrow * RW + wcol[j]) * 3;
+            const int c = code[j];
+            int ia, ib;
+            if (c < K2) {
+                const uint32_t t = tab[c];
+                ia = base + (int)(t & 0xFFFFu);
+                ib = base + (int)(t >> 16);
+            } else {
+                set_status(GLU_ERR_DEVICE_CHECK);
+                ia = ib = 0;
+            }
+            if (!interior) {
+                // codes from the search never leave the LR image; anything else is recorded
+                const int ka = qdiv(c, invK), kb = c - ka * K;
+                const int ra = qdiv(ka, invS), rb = qdiv(kb, invS);
+                const int va = py + ra - r, ua = pxj[j] + (ka - ra * S) - r;
+                const int vb = py + rb - r, ub = pxj[j] + (kb - rb * S) - r;
+                if ((unsigned)va >= (unsigned)P.h || (unsigned)ua >= (unsigned)P.w) {
+                    set_status(GLU_ERR_DEVICE_CHECK);
+                    ia = 0;
+                }
+                if ((unsigned)vb >= (unsigned)P.h || (unsigned)ub >= (unsigned)P.w) {
+                    set_status(GLU_ERR_DEVICE_CHECK);
+                    ib = 0;
+                }
+            }
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float ta = reg[ia + ch], tb = reg[ib + ch];
+                res[j * 3 + ch] = __fmaf_rn(w[j], ta - tb, tb);
+            }
+        }
+        store12((OT*)P.out + (int64_t)y * P.out_pitch + (int64_t)xs * 3, res);
+    }
 }
 
 // Eq. 1 fast path for 3-channel float32 targets and outputs with W % 4 == 0 and 16-byte
@@ -288,38 +349,63 @@ static int grid_for(int64_t work, int threads) {
     return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
 }
 
+// k_apply3_tile for variant v (tile rows), weight format and output type.
+template <typename F>
+static int apply_tile_dispatch(int v, int wfmt, bool out_f16, F&& launch) {
+#define GLU_APPLY_CASE(k)                                                                         \
+    case k:                                                                                       \
+        if (out_f16) {                                                                            \
+            if (wfmt == GLU_W_F32) return launch(k_apply3_tile<GLU_W_F32, __half, kApplyVariantRows[k]>); \
+            if (wfmt == GLU_W_F16) return launch(k_apply3_tile<GLU_W_F16, __half, kApplyVariantRows[k]>); \
+            return launch(k_apply3_tile<GLU_W_UNORM16, __half, kApplyVariantRows[k]>);            \
+        }                                                                                         \
+        if (wfmt == GLU_W_F32) return launch(k_apply3_tile<GLU_W_F32, float, kApplyVariantRows[k]>); \
+        if (wfmt == GLU_W_F16) return launch(k_apply3_tile<GLU_W_F16, float, kApplyVariantRows[k]>); \
+        return launch(k_apply3_tile<GLU_W_UNORM16, float, kApplyVariantRows[k]>)
+    static_assert(kNumApplyVariants == 3, "one case per variant");
+    switch (v) {
+        GLU_APPLY_CASE(0);
+        GLU_APPLY_CASE(1);
+        GLU_APPLY_CASE(2);
+        default: return GLU_ERR_INVALID_ARG;
+    }
+#undef GLU_APPLY_CASE
+}
+
 int launch_apply(const ApplyArgs& a, cudaStream_t st) {
     if (a.H <= 0 || a.W <= 0) return GLU_OK;
     const int threads = 256;
     const size_t wsz = a.wfmt == GLU_W_F32 ? 16 : 8;
-    const bool vec = a.C == 3 && a.T_dtype == GLU_F32 && a.out_dtype == GLU_F32 && a.W % 4 == 0 &&
-                     a.out_pitch % 4 == 0 && ((uintptr_t)a.out & 15u) == 0 &&
-                     ((uintptr_t)a.code & 7u) == 0 && ((uintptr_t)a.weight & (wsz - 1)) == 0;
+    const bool in_ok = a.C == 3 && a.T_dtype == GLU_F32 && a.W % 4 == 0 && a.out_pitch % 4 == 0 &&
+                       ((uintptr_t)a.code & 7u) == 0 && ((uintptr_t)a.weight & (wsz - 1)) == 0;
+    const bool vec = in_ok && a.out_dtype == GLU_F32 && ((uintptr_t)a.out & 15u) == 0;
+    const bool vec16 = in_ok && a.out_dtype == GLU_F16 && ((uintptr_t)a.out & 7u) == 0;
 #ifndef GLU_APPLY_TILED
 #define GLU_APPLY_TILED 1
 #endif
-    if (vec && GLU_APPLY_TILED) {
-        const int r = (a.S - 1) / 2;
-        const int rh = (kApplyTH - 1) / a.s + 2 + 2 * r, rw = (kApplyTW - 1) / a.s + 2 + 2 * r;
-        const size_t smem = sizeof(float) * 3 * (size_t)rh * rw;
-        dim3 grid((a.W + kApplyTW - 1) / kApplyTW, (a.H + kApplyTH - 1) / kApplyTH);
-        auto launch = [&](auto kern) -> int {
-            if (smem > 48 * 1024 &&
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                    cudaSuccess)
-                return GLU_ERR_CUDA;
-            kern<<<grid, threads, smem, st>>>(a);
-            return GLU_OK;
+    if ((vec && GLU_APPLY_TILED) || vec16) {
+        auto run = [&](int v) -> int {
+            const int th = kApplyVariantRows[v];
+            const size_t smem = sizeof(float) * (size_t)apply_region_floats(th, a.s, a.S) +
+                                sizeof(uint32_t) * (size_t)(a.S * a.S) * (a.S * a.S);
+            const dim3 grid((a.W + kApplyTW - 1) / kApplyTW, (a.H + th - 1) / th);
+            const int nthr = 32 * (th < 8 ? th : 8);
+            auto launch = [&](auto kern) -> int {
+                if (smem > 48 * 1024 &&
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem) != cudaSuccess)
+                    return GLU_ERR_CUDA;
+                kern<<<grid, nthr, smem, st>>>(a);
+                GLU_LAUNCH_CHECK();
+                return GLU_OK;
+            };
+            return apply_tile_dispatch(v, a.wfmt, vec16, launch);
         };
-        int rc;
-        switch (a.wfmt) {
-            case GLU_W_F32: rc = launch(k_apply3_tile<GLU_W_F32>); break;
-            case GLU_W_F16: rc = launch(k_apply3_tile<GLU_W_F16>); break;
-            default: rc = launch(k_apply3_tile<GLU_W_UNORM16>); break;
-        }
+        const int key[5] = {a.out_dtype, a.wfmt, a.S, a.s, tune_size_class((long long)a.H * a.W)};
+        int v = 0;
+        const int rc = tune_choose(kTuneApply, key, kNumApplyVariants, run, st, &v);
         if (rc) return rc;
-        GLU_LAUNCH_CHECK();
-        return GLU_OK;
+        return run(v);
     }
     if (vec) {
         const int64_t work = (int64_t)(a.W / 4) * a.H;

@@ -1,189 +1,22 @@
-// Algorithm 1 (Sec. 3.2) over a batch of images in one persistent launch.
-//
-// Work items are 64 x 16 HR tiles of every image of the batch (one global tile index space);
-// each CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... so images of uneven sizes,
-// scales and window sizes share one launch. A single image is a batch of one.
-//
-// Per tile, the HR tile is staged into shared memory by a 2D TMA load (cp.async.bulk.tensor)
-// completing on an mbarrier (one tensor map per image, kept in the kernel's parameter block);
-// while it is in flight the CTA's threads copy the LR halo (the LR rows and columns the tile's
-// windows reach) into shared memory as float4 colours in 1/255 units. Each thread then owns
-// whole pixels: both candidate loops of Algorithm 1 run in registers against the shared-memory
-// window, so no cross-lane reduction is needed and the tie-break is the deterministic lowest
-// window index.
+// Host side of the Algorithm 1 search (Sec. 3.2): tensor maps for the TMA tile loads, the
+// split of a batch into launches of <= 32 images, and the choice of kernel variant (tile height,
+// occupancy target, candidate loop schedule) through the autotuner. The kernels themselves are
+// in search_kernel.cuh, instantiated in k_search_u8.cu and k_search_f16.cu.
 #include <cudaTypedefs.h>
 
 #include <mutex>
 
+#include "common.cuh"
 #include "internal.h"
-#include "search.cuh"
+#include "tune.h"
+#include "variants.h"
 
 namespace glu {
 
-GLU_DEFINE_STATUS(search)
-
-// Occupancy target (CTAs per SM) and the rolled search variant: build-time tuning knobs.
-#ifndef GLU_SEARCH_MINBLOCKS
-#define GLU_SEARCH_MINBLOCKS 3
-#endif
-#ifndef GLU_SEARCH_COMPACT
-#define GLU_SEARCH_COMPACT 0
-#endif
-
-constexpr int kTileW = 64;   // HR pixels per tile row (64 * 3 channels: a 16-byte multiple)
-constexpr int kTileH = 16;   // HR rows per tile
-constexpr int kThreads = 256;
-constexpr int kMaxBatch = 32;  // images per launch (more are split over several launches)
-static_assert(kThreads % kTileW == 0, "a thread keeps one tile column");
-
-struct SImg {
-    const void* hr;
-    int64_t hr_pitch;
-    const void* lr;
-    int64_t lr_pitch;
-    uint16_t* code;
-    void* weight;
-    float* err;
-    int lr_dtype;
-    int H, W, h, w, s, S;
-    int tiles_x;   // tiles per tile row
-    int tile0;     // first global tile index of this image
-    int use_tma;
-};
-
-struct SBatch {
-    CUtensorMap maps[kMaxBatch];
-    SImg im[kMaxBatch];
-    int n, total_tiles;
-    int wfmt, gnu;
-    float eps255;
-};
-
-template <typename HT>
-struct HrTile {
-    alignas(128) HT px[kTileH][kTileW * 3];
-};
-
-// One tile of image I: (x0, y0) its top-left HR pixel. `phase` is the mbarrier parity to wait on.
-template <int S, typename HT>
-__device__ __forceinline__ bool search_tile(const SBatch& B, int i, int x0, int y0,
-                                            HrTile<HT>& tile, uint64_t* bar, uint32_t phase,
-                                            float4* region) {
-    const SImg& I = B.im[i];
-    constexpr int r = (S - 1) / 2;
-    const int tid = threadIdx.x;
-    const int s = I.s;
-    const int xe = min(x0 + kTileW, I.W), ye = min(y0 + kTileH, I.H);
-    const int v0 = y0 / s - r, u0 = x0 / s - r;
-    const int RH = (ye - 1) / s + r - v0 + 1, RW = (xe - 1) / s + r - u0 + 1;
-
-    if (I.use_tma) {
-        if (tid == 0) {
-            fence_proxy_async_smem();  // earlier generic reads of the tile buffer come first
-            mbar_arrive_expect_tx(bar, (uint32_t)sizeof(tile.px));
-            tma_load_2d(&tile.px[0][0], &B.maps[i], bar, x0 * 3, y0);
-        }
-    } else {
-        const HT* src = (const HT*)I.hr;
-        for (int k = tid; k < kTileH * kTileW * 3; k += kThreads) {
-            const int ty = k / (kTileW * 3), tx = k % (kTileW * 3);
-            const int y = y0 + ty, xc = x0 * 3 + tx;
-            tile.px[ty][tx] = (y < I.H && xc < I.W * 3) ? src[(int64_t)y * I.hr_pitch + xc] : HT(0);
-        }
-    }
-    // LR halo in 1/255 units; rows/columns outside the LR image are never selected (masks)
-    for (int k = tid; k < RH * RW; k += kThreads) {
-        const int v = v0 + k / RW, u = u0 + k % RW;
-        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (v >= 0 && v < I.h && u >= 0 && u < I.w) {
-            const int64_t o = (int64_t)v * I.lr_pitch + (int64_t)u * 3;
-            if (I.lr_dtype == GLU_U8) {
-                const uint8_t* L = (const uint8_t*)I.lr;
-                c = make_float4((float)L[o], (float)L[o + 1], (float)L[o + 2], 0.f);
-            } else if (I.lr_dtype == GLU_F16) {
-                const __half* L = (const __half*)I.lr;
-                c = make_float4(__half2float(L[o]) * 255.f, __half2float(L[o + 1]) * 255.f,
-                                __half2float(L[o + 2]) * 255.f, 0.f);
-            } else {
-                const float* L = (const float*)I.lr;
-                c = make_float4(L[o] * 255.f, L[o + 1] * 255.f, L[o + 2] * 255.f, 0.f);
-            }
-        }
-        region[k] = c;
-    }
-    __syncthreads();
-    if (I.use_tma && !mbar_wait_bounded(bar, phase)) {
-        set_status(GLU_ERR_TIMEOUT);
-        // the copy may still land: give it another bounded wait before the CTA moves on
-        (void)mbar_wait_bounded(bar, phase);
-        return false;
-    }
-
-    // interior tiles (every window inside the LR image) skip the validity masks
-    const bool interior = v0 >= 0 && u0 >= 0 && (ye - 1) / s + r < I.h && (xe - 1) / s + r < I.w;
-    // a thread keeps one column of the tile (kThreads is a multiple of kTileW) and walks rows
-    const int tx = tid % kTileW, x = x0 + tx, px = x / s;
-    const int col = px - r - u0;
-    for (int ty = tid / kTileW; ty < kTileH; ty += kThreads / kTileW) {
-        const int y = y0 + ty;
-        if (y >= I.H || x >= I.W) continue;
-        const float ir = Px<HT>::to255(tile.px[ty][tx * 3 + 0]);
-        const float ig = Px<HT>::to255(tile.px[ty][tx * 3 + 1]);
-        const float ib = Px<HT>::to255(tile.px[ty][tx * 3 + 2]);
-        const int py = y / s;
-        const float4* win = &region[(py - r - v0) * RW + col];
-        SearchOut o;
-        if (interior) {
-            o = search_pixel<S, GLU_SEARCH_COMPACT != 0, true>(win, RW, 0u, 0u, ir, ig, ib, B.eps255,
-                                                               B.gnu != 0);
-        } else {
-            uint32_t rm, cm;
-            window_masks(py, px, I.h, I.w, S, rm, cm);
-            o = search_pixel<S, GLU_SEARCH_COMPACT != 0>(win, RW, rm, cm, ir, ig, ib, B.eps255,
-                                                         B.gnu != 0);
-        }
-        const int64_t p = (int64_t)y * I.W + x;
-        I.code[p] = (uint16_t)(o.ka * S * S + o.kb);
-        store_weight(I.weight, B.wfmt, p, o.omega);
-        if (I.err) I.err[p] = o.err;
-    }
-    __syncthreads();  // the tile buffers are reused by the next tile
-    return true;
-}
-
-template <typename HT>
-__global__ void __launch_bounds__(kThreads, GLU_SEARCH_MINBLOCKS)
-    k_search(const __grid_constant__ SBatch B) {
-    __shared__ HrTile<HT> tile;
-    __shared__ alignas(8) uint64_t bar;
-    extern __shared__ float4 region[];
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t uses = 0;  // completed phases of the mbarrier (TMA tiles issued by this CTA)
-    for (int t = blockIdx.x; t < B.total_tiles; t += gridDim.x) {
-        int i = 0;
-        while (i + 1 < B.n && B.im[i + 1].tile0 <= t) ++i;
-        const SImg& I = B.im[i];
-        const int lt = t - I.tile0;
-        const int x0 = (lt % I.tiles_x) * kTileW, y0 = (lt / I.tiles_x) * kTileH;
-        const uint32_t phase = uses & 1u;
-        bool ok = true;
-        switch (I.S) {
-            case 1: ok = search_tile<1, HT>(B, i, x0, y0, tile, &bar, phase, region); break;
-            case 3: ok = search_tile<3, HT>(B, i, x0, y0, tile, &bar, phase, region); break;
-            case 5: ok = search_tile<5, HT>(B, i, x0, y0, tile, &bar, phase, region); break;
-            case 7: ok = search_tile<7, HT>(B, i, x0, y0, tile, &bar, phase, region); break;
-            default: ok = search_tile<9, HT>(B, i, x0, y0, tile, &bar, phase, region); break;
-        }
-        if (!ok) return;
-        if (I.use_tma) ++uses;
-    }
-}
-
-// ----------------------------------------------------------------------------- host side
+int search_launch_u8(int v, const SearchArgs* items, int n, cudaStream_t st);
+int search_launch_f16(int v, const SearchArgs* items, int n, cudaStream_t st);
+int read_and_clear_status_search_u8(cudaStream_t st);
+int read_and_clear_status_search_f16(cudaStream_t st);
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -199,15 +32,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2D byte/half view of an interleaved HR image for TMA: inner dim W*3 elements, outer dim H.
-static bool make_hr_map(const SearchArgs& a, CUtensorMap* map) {
+bool make_hr_map(const SearchArgs& a, CUtensorMap* map, int tile_h) {
     auto enc = get_encode();
     if (!enc) return false;
     const size_t esz = a.hr_dtype == GLU_U8 ? 1 : 2;
     if (((uintptr_t)a.hr & 15u) != 0 || ((size_t)a.hr_pitch * esz) % 16 != 0) return false;
     cuuint64_t dims[2] = {(cuuint64_t)a.W * 3, (cuuint64_t)a.H};
     cuuint64_t strides[1] = {(cuuint64_t)a.hr_pitch * esz};
-    cuuint32_t box[2] = {(cuuint32_t)kTileW * 3, (cuuint32_t)kTileH};
+    cuuint32_t box[2] = {(cuuint32_t)kTileW * 3, (cuuint32_t)tile_h};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, a.hr_dtype == GLU_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                      2, const_cast<void*>(a.hr), dims, strides, box, estr,
@@ -216,69 +48,40 @@ static bool make_hr_map(const SearchArgs& a, CUtensorMap* map) {
     return r == CUDA_SUCCESS;
 }
 
-template <typename HT>
-static int launch_chunk(const SearchArgs* items, int n, cudaStream_t st) {
-    static SBatch B;  // host staging of the parameter block (copied at launch)
-    memset(&B, 0, sizeof(B));
-    size_t smem = 0;
-    int tiles = 0;
-    for (int k = 0; k < n; ++k) {
-        const SearchArgs& a = items[k];
-        SImg& I = B.im[k];
-        I.hr = a.hr;
-        I.hr_pitch = a.hr_pitch;
-        I.lr = a.lr;
-        I.lr_pitch = a.lr_pitch;
-        I.lr_dtype = a.lr_dtype;
-        I.code = a.code;
-        I.weight = a.weight;
-        I.err = a.err;
-        I.H = a.H; I.W = a.W; I.h = a.h; I.w = a.w; I.s = a.s; I.S = a.S;
-        I.tiles_x = (a.W + kTileW - 1) / kTileW;
-        I.tile0 = tiles;
-        I.use_tma = make_hr_map(a, &B.maps[k]) ? 1 : 0;
-        tiles += I.tiles_x * ((a.H + kTileH - 1) / kTileH);
-        const int r = (a.S - 1) / 2;
-        const int rh = (kTileH - 1) / a.s + 2 + 2 * r, rw = (kTileW - 1) / a.s + 2 + 2 * r;
-        const size_t need = sizeof(float4) * (size_t)rh * rw;
-        if (need > smem) smem = need;
-    }
-    B.n = n;
-    B.total_tiles = tiles;
-    B.wfmt = items[0].wfmt;
-    B.gnu = items[0].gnu;
-    B.eps255 = items[0].eps255;
-    if (tiles == 0) return GLU_OK;
-    auto kern = k_search<HT>;
-    if (smem > 48 * 1024)
-        GLU_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 148, per_sm = 1;
-    GLU_CUDA_TRY(cudaGetDevice(&dev));
-    GLU_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    if (per_sm < 1) per_sm = 1;
-    const int grid = tiles < sms * per_sm ? tiles : sms * per_sm;
-    kern<<<grid, kThreads, smem, st>>>(B);
-    GLU_LAUNCH_CHECK();
-    return GLU_OK;
+int read_and_clear_status_search(cudaStream_t st) {
+    const int a = read_and_clear_status_search_u8(st);
+    const int b = read_and_clear_status_search_f16(st);
+    return a != GLU_OK ? a : b;
 }
 
 int launch_search_batch(const SearchArgs* items, int n, cudaStream_t st) {
-    static std::mutex mu;  // the staging block is shared
+    static std::mutex mu;  // the kernels' staging blocks are shared
     std::lock_guard<std::mutex> lock(mu);
-    for (int k0 = 0; k0 < n; k0 += kMaxBatch) {
-        const int m = n - k0 < kMaxBatch ? n - k0 : kMaxBatch;
-        for (int k = k0; k < k0 + m; ++k) {
-            const SearchArgs& a = items[k];
-            if (a.hr_dtype != items[k0].hr_dtype || a.wfmt != items[k0].wfmt ||
-                a.gnu != items[k0].gnu || a.eps255 != items[k0].eps255)
+    for (int k0 = 0; k0 < n; k0 += kMaxSearchBatch) {
+        const int m = n - k0 < kMaxSearchBatch ? n - k0 : kMaxSearchBatch;
+        const SearchArgs* it = items + k0;
+        int maxS = 1, mins = 1 << 30;
+        long long npx = 0;
+        for (int k = 0; k < m; ++k) {
+            const SearchArgs& a = it[k];
+            if (a.hr_dtype != it[0].hr_dtype || a.wfmt != it[0].wfmt || a.gnu != it[0].gnu ||
+                a.eps255 != it[0].eps255)
                 return GLU_ERR_UNSUPPORTED;  // one dtype / weight format / mode per launch
             if (a.S < 1 || a.S > 9 || (a.S & 1) == 0) return GLU_ERR_UNSUPPORTED;
+            if (a.S > maxS) maxS = a.S;
+            if (a.s < mins) mins = a.s;
+            npx += (long long)a.H * a.W;
         }
-        int rc;
-        if (items[k0].hr_dtype == GLU_U8) rc = launch_chunk<uint8_t>(items + k0, m, st);
-        else if (items[k0].hr_dtype == GLU_F16) rc = launch_chunk<__half>(items + k0, m, st);
-        else rc = GLU_ERR_UNSUPPORTED;
+        auto run = [&](int v) -> int {
+            if (it[0].hr_dtype == GLU_U8) return search_launch_u8(v, it, m, st);
+            if (it[0].hr_dtype == GLU_F16) return search_launch_f16(v, it, m, st);
+            return GLU_ERR_UNSUPPORTED;
+        };
+        const int key[5] = {it[0].hr_dtype, it[0].gnu, maxS, mins, tune_size_class(npx)};
+        int v = 0;
+        int rc = tune_choose(kTuneSearch, key, kNumSearchVariants, run, st, &v);
+        if (rc) return rc;
+        rc = run(v);
         if (rc) return rc;
     }
     return GLU_OK;

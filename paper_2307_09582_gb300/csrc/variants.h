@@ -1,0 +1,24 @@
+// Implementation variants the autotuner chooses from (every variant of a kernel computes the
+// same arithmetic in the same order, so results are bit-identical across variants).
+#pragma once
+
+namespace glu {
+
+constexpr int kTileW = 64;   // HR pixels per search tile row (64 * 3 channels: a 16-byte multiple)
+
+// Algorithm 1 search: tile height, CTAs per SM the registers are sized for, and the candidate
+// loop schedule (window rows unrolled, or rolled loops).
+struct SearchVariant {
+    int tile_h, min_blocks, compact;
+};
+constexpr SearchVariant kSearchVariants[] = {
+    {16, 3, 0}, {16, 2, 0}, {8, 2, 0}, {32, 2, 0}, {16, 4, 1},
+};
+constexpr int kNumSearchVariants = (int)(sizeof(kSearchVariants) / sizeof(kSearchVariants[0]));
+
+// Eq. 1 apply, 3-channel float targets: rows of the 128-pixel-wide tiles.
+constexpr int kApplyTW = 128;
+constexpr int kApplyVariantRows[] = {8, 4, 16};
+constexpr int kNumApplyVariants = (int)(sizeof(kApplyVariantRows) / sizeof(kApplyVariantRows[0]));
+
+}  // namespace glu

@@ -133,7 +133,62 @@ def test_batched_host_validation(lib):
                                           None) == A.GLU_ERR_WORKSPACE
 
 
+def test_video_host_validation(lib):
+    from paper_2307_09582_gb300 import _abi as A
+    d = A.GluVideoDesc()
+    d.H, d.W, d.scale = 2160, 3840, 8
+    d.hr_dtype, d.out_dtype = A.GLU_F16, A.GLU_F16
+    lib.glu_params_default(ctypes.byref(d.params))
+    d.params.S = 5
+    d.wfmt, d.filter, d.saturation, d.gamma, d.overlap = A.GLU_W_UNORM16, 1, 1.0, 0.8, 1
+    need = lib.glu_video_workspace_size(ctypes.byref(d))
+    h, w = 270, 480
+    # three LR float images, the codes and the weights, each 256-byte aligned
+    lr = -(-(h * w * 3 * 4) // 256) * 256
+    assert need == 3 * lr + 2 * (-(-(2160 * 3840 * 2) // 256) * 256)
+    out = ctypes.c_void_p()
+    assert lib.glu_video_create(ctypes.byref(d), None, need, ctypes.byref(out)) == \
+        A.GLU_ERR_WORKSPACE
+    assert lib.glu_video_create(ctypes.byref(d), ctypes.c_void_p(0x1100), need - 1,
+                                ctypes.byref(out)) == A.GLU_ERR_WORKSPACE
+    for field, bad in (("hr_dtype", A.GLU_F32), ("out_dtype", A.GLU_U8), ("filter", 2),
+                       ("gamma", 0.0), ("scale", 0)):
+        old = getattr(d, field)
+        setattr(d, field, bad)
+        assert lib.glu_video_workspace_size(ctypes.byref(d)) == 0, field
+        assert lib.glu_video_create(ctypes.byref(d), ctypes.c_void_p(0x1100), need,
+                                    ctypes.byref(out)) == A.GLU_ERR_INVALID_ARG
+        setattr(d, field, old)
+    assert lib.glu_video_launch(None, 0, None) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_video_destroy(None) == A.GLU_OK
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_2307_09582_gb300 import _abi as A
     with pytest.raises(RuntimeError, match="not found"):
         A.load(str(tmp_path / "libglu.so"))
+
+
+def test_tuner_host_side(lib):
+    from paper_2307_09582_gb300 import _abi as A
+    assert lib.glu_tune_variants(A.GLU_TUNE_SEARCH) == 5
+    assert lib.glu_tune_variants(A.GLU_TUNE_APPLY) == 3
+    assert lib.glu_tune_variants(7) == A.GLU_ERR_INVALID_ARG
+    buf = ctypes.create_string_buffer(128)
+    assert lib.glu_tune_variant_name(A.GLU_TUNE_SEARCH, 0, buf, 128) == A.GLU_OK
+    assert buf.value.startswith(b"tile 64x16")
+    assert lib.glu_tune_variant_name(A.GLU_TUNE_APPLY, 3, buf, 128) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_tune_force(A.GLU_TUNE_SEARCH, 5) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_tune_force(A.GLU_TUNE_SEARCH, -1) == A.GLU_OK
+    # export / import round trip of the text form
+    assert lib.glu_tune_clear() == A.GLU_OK
+    assert lib.glu_tune_export(None, 0) == 1
+    text = b"0 0 0 5 8 23 3 0.250000\n1 2 2 5 8 23 1 0.040000\n"
+    assert lib.glu_tune_import(text) == A.GLU_OK
+    n = lib.glu_tune_export(None, 0)
+    out = ctypes.create_string_buffer(n)
+    assert lib.glu_tune_export(out, n) == n
+    assert out.value == text
+    assert lib.glu_tune_import(b"0 0 0 5 8 23 9 0.1\n") == A.GLU_ERR_INVALID_ARG  # no variant 9
+    assert lib.glu_tune_import(b"garbage") == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_tune_clear() == A.GLU_OK

@@ -512,6 +512,9 @@ def run_kernel_case(args):
     from paper_2307_09582_gb300 import api
     from paper_2307_09582_gb300.inputs import Scene, joint_4k_scene, render_u8
     dev = torch.device("cuda", 0)
+    if args.variant is not None and args.kernel_case in ("search", "apply"):
+        api.tune_force(api.GLU_TUNE_SEARCH if args.kernel_case == "search" else api.GLU_TUNE_APPLY,
+                       args.variant)
     if args.kernel_case == "trials":
         img = render_u8(joint_4k_scene())
         hr = torch.from_numpy(img).to(dev)
@@ -554,6 +557,8 @@ def main():
                     help="run one kernel on a profiling case and exit (no JSON line)")
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--video-frames", type=int, default=VIDEO_FRAMES)
+    ap.add_argument("--variant", type=int, default=None,
+                    help="with --kernel-case search/apply: the kernel variant to run")
     args = ap.parse_args()
     globals()["VIDEO_FRAMES"] = args.video_frames
     if args.kernel_case:

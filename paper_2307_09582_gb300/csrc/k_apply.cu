@@ -136,7 +136,9 @@ __host__ __device__ __forceinline__ int apply_region_floats(int th, int s, int S
 // per 4 pixels, results leave as three 16- (float32) or 8-byte (float16) streaming stores.
 // Conditions: 3 channels, float32 target, W % 4 == 0, aligned rows.
 template <int WF, typename OT, int TH>
-__global__ void __launch_bounds__(256) k_apply3_tile(const ApplyArgs P) {
+__global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_tile(const ApplyArgs P) {
+    constexpr int NW = TH < 8 ? TH : 8;   // warps: one row each, RPW rows per warp
+    constexpr int RPW = TH / NW;
     extern __shared__ float reg[];   // RH x RW x 3 region, then K*K offset pairs
     const int x0 = blockIdx.x * kApplyTW, y0 = blockIdx.y * TH;
     const int s = P.s, S = P.S, r = (S - 1) >> 1, K = S * S, K2 = K * K;
@@ -145,12 +147,28 @@ __global__ void __launch_bounds__(256) k_apply3_tile(const ApplyArgs P) {
     const int RH = (ye - 1) / s + r - v0 + 1, RW = (xe - 1) / s + r - u0 + 1;
     uint32_t* tab = (uint32_t*)(reg + apply_region_floats(TH, s, S));
     const float* T = (const float*)P.T;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int xs = x0 + lane * 4;
+    const bool col_ok = xs < P.W;
+    // this thread's codes and weights first: they do not wait for the LR region
+    uint2 cc[RPW];
+    float w[RPW][4];
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int y = y0 + wid + k * NW;
+        cc[k] = make_uint2(0u, 0u);
+        if (col_ok && y < P.H) {
+            const int64_t p0 = (int64_t)y * P.W + xs;
+            cc[k] = __ldcs((const uint2*)P.code + (p0 >> 2));
+            W4<WF>::load(P.weight, p0, w[k]);
+        }
+    }
     // the LR region, clamped to the image (entries outside it are never selected by a valid code)
     for (int i = threadIdx.x; i < RH * RW * 3; i += blockDim.x) {
-        const int rr = i / (RW * 3), cc = i - rr * (RW * 3);
+        const int rr = i / (RW * 3), c3 = i - rr * (RW * 3);
         const int v = min(max(v0 + rr, 0), P.h - 1);
-        const int u = min(max(u0 + cc / 3, 0), P.w - 1);
-        reg[i] = __ldg(T + (int64_t)v * P.T_pitch + (int64_t)u * 3 + cc % 3);
+        const int u = min(max(u0 + c3 / 3, 0), P.w - 1);
+        reg[i] = __ldg(T + (int64_t)v * P.T_pitch + (int64_t)u * 3 + c3 % 3);
     }
     // pair code -> (offset of T_a, offset of T_b) in the region, relative to the window corner
     for (int c = threadIdx.x; c < K2; c += blockDim.x) {
@@ -160,9 +178,7 @@ __global__ void __launch_bounds__(256) k_apply3_tile(const ApplyArgs P) {
         tab[c] = oa | (ob << 16);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int xs = x0 + lane * 4;
-    if (xs >= P.W) return;
+    if (!col_ok) return;
     // every window of the tile inside the LR image: only the code range needs checking
     const bool interior = v0 >= 0 && u0 >= 0 && (ye - 1) / s + r < P.h && (xe - 1) / s + r < P.w;
     // window corner columns of the 4 pixels in the region: xs / s once, then at most three
@@ -175,17 +191,14 @@ __global__ void __launch_bounds__(256) k_apply3_tile(const ApplyArgs P) {
         wcol[j] = pxj[j] - r - u0;
     }
     const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
-    for (int ty = threadIdx.x >> 5; ty < TH; ty += nwarps) {
-        const int y = y0 + ty;
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int y = y0 + wid + k * NW;
         if (y >= P.H) break;
         const int py = y / s;
         const int wrow = py - r - v0;   // region row of the window's top row
-        const int64_t p0 = (int64_t)y * P.W + xs;
-        const uint2 cc = __ldcs((const uint2*)P.code + (p0 >> 2));
-        const int code[4] = {(int)(cc.x & 0xFFFFu), (int)(cc.x >> 16), (int)(cc.y & 0xFFFFu),
-                             (int)(cc.y >> 16)};
-        float w[4];
-        W4<WF>::load(P.weight, p0, w);
+        const int code[4] = {(int)(cc[k].x & 0xFFFFu), (int)(cc[k].x >> 16),
+                             (int)(cc[k].y & 0xFFFFu), (int)(cc[k].y >> 16)};
         float res[12];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -218,7 +231,7 @@ __global__ void __launch_bounds__(256) k_apply3_tile(const ApplyArgs P) {
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 const float ta = reg[ia + ch], tb = reg[ib + ch];
-                res[j * 3 + ch] = __fmaf_rn(w[j], ta - tb, tb);
+                res[j * 3 + ch] = __fmaf_rn(w[k][j], ta - tb, tb);
             }
         }
         store12((OT*)P.out + (int64_t)y * P.out_pitch + (int64_t)xs * 3, res);

@@ -25,6 +25,7 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -37,7 +38,7 @@ GLU_DEFINE_STATUS(joint)
 constexpr int kOwnSlots = 8;        // components recorded per LR pixel before overflow
 constexpr int kScanTile = 4096;     // elements per scan tile
 constexpr int kScanThreads = 256;   // 16 elements per thread
-constexpr int kTrialThreads = 256;
+constexpr int kTrialThreads = 1024;
 constexpr int kResidChunk = 8192;
 constexpr int kMaxSlots = 4096;
 constexpr int kSmax = 9;            // largest window
@@ -77,6 +78,9 @@ struct JointCtl {
     int open_tasks;
     int claim[GLU_MAX_ITERS];
     int finished[GLU_MAX_ITERS];
+    int head[GLU_MAX_ITERS];      // ready queue: positions taken
+    int tail[GLU_MAX_ITERS];      // ready queue: positions filled
+    int dag_bad[GLU_MAX_ITERS];   // dependency graph did not fit: claim in index order instead
     int active[kMaxJointBatch];
     int iterations[kMaxJointBatch];
     int n_large[kMaxJointBatch][GLU_MAX_ITERS];
@@ -123,6 +127,14 @@ struct JointWs {
     unsigned long long* slot_e0;
     unsigned long long* slot_e1;
     int* slot_fin;          // items finished
+    // dependency graph of the iteration's trials: succ lists (CSR) and pending-predecessor counts
+    int2* dag_cnt;          // mcap: (successors, unused)
+    int2* dag_start;        // mcap + 1
+    int* dag_fill;          // mcap
+    int* pend;              // mcap: predecessors not yet finished
+    int* queue;             // mcap: ready components in the order they became ready (-1: not yet)
+    int* succ;              // ecap
+    int64_t ecap;
 };
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -178,6 +190,13 @@ static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t
     t.slot_e0 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
     t.slot_e1 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
     t.slot_fin = (int*)take(sizeof(int) * kMaxSlots);
+    t.ecap = std::min<int64_t>(2 * mcap + (1 << 20), (int64_t)1 << 30);
+    t.dag_cnt = (int2*)take(sizeof(int2) * mcap);
+    t.dag_start = (int2*)take(sizeof(int2) * (mcap + 1));
+    t.dag_fill = (int*)take(sizeof(int) * mcap);
+    t.pend = (int*)take(sizeof(int) * mcap);
+    t.queue = (int*)take(sizeof(int) * mcap);
+    t.succ = (int*)take(sizeof(int) * t.ecap);
     if (o) *o = t;
     return off;
 }
@@ -484,7 +503,7 @@ __global__ void k_root_scan(int* tile_cnt, int ntiles, JointCtl* c) {
 // scatter roots in global order; component j's per-iteration state is cleared here
 __global__ void k_root_scatter(const __grid_constant__ JBatch B, const int* lab,
                                const int* tile_off, int* roots, int2* cnt, int2* fill, int* done,
-                               JointCtl* c, int it) {
+                               int2* dag_cnt, int* dag_fill, int* queue, JointCtl* c, int it) {
     if (!any_active(c)) return;
     __shared__ int wsm[8];
     const int64_t n = B.np;
@@ -511,6 +530,9 @@ __global__ void k_root_scatter(const __grid_constant__ JBatch B, const int* lab,
             cnt[j] = make_int2(0, 0);
             fill[j] = make_int2(0, 0);
             done[j] = 0;
+            dag_cnt[j] = make_int2(0, 0);
+            dag_fill[j] = 0;
+            queue[j] = -1;
             atomicAdd(&c->M[img_of_p(B, my + k)][it], 1);
             ++j;
         }
@@ -651,12 +673,10 @@ __global__ void k_comp_fill(const __grid_constant__ JBatch B, const int* lab,
     }
 }
 
-// ---------------------------------------------------------------------------- the trials
-
 #ifdef GLU_TRIAL_TRACE
 // Debug builds only: per-component timestamps (claim, dependencies met, trial summed, done).
 constexpr int kTraceMax = 1 << 15;
-static __device__ unsigned long long g_trace[GLU_MAX_ITERS][kTraceMax][4];
+static __device__ unsigned long long g_trace[GLU_MAX_ITERS][kTraceMax][10];
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -664,9 +684,146 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 #define GLU_TRACE(it, j, k) \
     do { if (tid == 0 && (j) < kTraceMax) g_trace[it][j][k] = gtimer(); } while (0)
+#define GLU_TRACE_ANY(it, j, k) \
+    do { if ((j) < kTraceMax) g_trace[it][j][k] = gtimer(); } while (0)
 #else
 #define GLU_TRACE(it, j, k) do { } while (0)
+#define GLU_TRACE_ANY(it, j, k) do { } while (0)
 #endif
+
+// ------------------------------------------------------------ dependency graph of the trials
+//
+// Trial j reads and writes state within D LR pixels of its blocks Q_j (D = 2r STRICT: it re-runs
+// Algorithm 1 on blocks within r of Q_j, whose windows reach r further; D = r PAPER). Component
+// i < j must therefore finish before j starts exactly when some block of Q_i lies within D of a
+// block of Q_j. k_deps finds those i for every j from the owner slots of the LR blocks around
+// Q_j (or, for a block whose slots overflowed, from the labels of its pixels), removes
+// duplicates, and builds: pend[j] = number of predecessors, succ lists (CSR) of every i. The
+// trials then run any component whose predecessors have all finished, in any order: components
+// that run concurrently never touch the same state, so the result equals the sequential one.
+
+constexpr int kCandMax = 4096;   // predecessor candidates per component before the fallback
+
+__device__ __forceinline__ void bitonic_sort_smem(int* a, int n2) {
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+                const int u = t ^ jj;
+                if (u > t) {
+                    const int x = a[t], y = a[u];
+                    const bool up = (t & k) == 0;
+                    if ((x > y) == up) {
+                        a[t] = y;
+                        a[u] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// PASS 0: pend[j] and successor counts. PASS 1: successor lists, and the components without
+// predecessors enter the ready queue. Both passes enumerate the same set.
+template <int PASS>
+__global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
+    JointCtl* c = W.ctl;
+    if (!any_active(c)) return;
+    __shared__ int cand[kCandMax];
+    __shared__ int s_n, s_cnt, s_bad;
+    const int M = c->M_cur;
+    if (PASS == 1) {
+        if (threadIdx.x == 0) {
+            s_bad = *(volatile int*)&c->dag_bad[it];
+            if (!s_bad && (int64_t)W.dag_start[M].x > W.ecap) {
+                s_bad = 1;
+                atomicExch(&c->dag_bad[it], 1);
+            }
+        }
+        __syncthreads();
+        if (s_bad) return;
+    }
+    for (int j = blockIdx.x; j < M; j += gridDim.x) {
+        if (threadIdx.x == 0) {
+            s_n = 0;
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int2 st = W.start[j], en = W.start[j + 1];
+        const JImg& I = B.im[img_of_p(B, W.roots[j])];
+        const int r = (I.S - 1) / 2;
+        const int D = B.strict ? 2 * r : r;
+        const int ND = (2 * D + 1) * (2 * D + 1);
+        const int npairs = (en.y - st.y) * ND;
+        for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+            const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+            const int nb = t % ND;
+            const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+            const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+            if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
+            const int64_t b = I.q0 + (int64_t)bv * I.w + bu;
+            if (W.ovf[b]) {
+                // more components than owner slots: read the block's pixel labels
+                const int ys = bv * I.s, xs = bu * I.s;
+                const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
+                int last = -1;
+                for (int k = 0; k < ey * ex; ++k) {
+                    const int i = W.lab[I.p0 + (int64_t)(ys + k / ex) * I.W + xs + k % ex];
+                    if (i >= 0 && i < j && i != last) {
+                        const int slot = atomicAdd(&s_n, 1);
+                        if (slot < kCandMax) cand[slot] = i;
+                        last = i;
+                    }
+                }
+            } else {
+                for (int k = 0; k < kOwnSlots; ++k) {
+                    const int i = W.own[b * kOwnSlots + k];
+                    if (i < 0) break;
+                    if (i < j) {
+                        const int slot = atomicAdd(&s_n, 1);
+                        if (slot < kCandMax) cand[slot] = i;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int n = s_n;
+        if (n > kCandMax) {
+            if (threadIdx.x == 0) atomicExch(&c->dag_bad[it], 1);
+            __syncthreads();
+            continue;
+        }
+        int n2 = 1;
+        while (n2 < n) n2 <<= 1;
+        for (int t = n + threadIdx.x; t < n2; t += blockDim.x) cand[t] = 0x7fffffff;
+        __syncthreads();
+        if (n > 1) bitonic_sort_smem(cand, n2);
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int i = cand[t];
+            if (t > 0 && cand[t - 1] == i) continue;   // distinct predecessors only
+            if (PASS == 0) {
+                atomicAdd(&W.dag_cnt[i].x, 1);
+                atomicAdd(&s_cnt, 1);
+            } else {
+                const int pos = atomicAdd(&W.dag_fill[i], 1);
+                W.succ[W.dag_start[i].x + pos] = j;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (PASS == 0) {
+                W.pend[j] = s_cnt;
+            } else if (W.pend[j] == 0) {
+                const int pos = atomicAdd(&c->tail[it], 1);
+                W.queue[pos] = j;
+                GLU_TRACE_ANY(it, j, 0);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- the trials
+
 
 struct TrialCtx {
     JointWs ws;
@@ -1036,180 +1193,707 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
     return *s_flag == 0;
 }
 
-__global__ void __launch_bounds__(kTrialThreads, 3)
+// Block-wide exclusive scan of one int per thread for any blockDim.x <= 1024 (a multiple of 32).
+// Returns the total; smem_warp holds 32 ints.
+__device__ __forceinline__ int block_excl_scan_any(int v, int* out_excl, int* smem_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < nw ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        smem_warp[lane] = t;
+    }
+    __syncthreads();
+    *out_excl = (wid > 0 ? smem_warp[wid - 1] : 0) + x - v;
+    const int total = smem_warp[nw - 1];
+    __syncthreads();
+    return total;
+}
+
+// ------------------------------------------------------ trials of small components in one CTA
+//
+// A component whose blocks, re-searched pixels and LR neighbourhood fit in shared memory is tried
+// by its CTA alone: the LR neighbourhood (with the replacements applied) is staged in shared
+// memory, every affected block is re-searched by one warp against it, and the new Theta / E stay
+// in shared memory until the decision. A kept trial writes them (and the new LR colours) out; a
+// rolled-back trial writes nothing, so the global state never holds a rejected trial. The
+// arithmetic and the summation order (per block: Kahan per lane over the block's pixels in raster
+// order, then a butterfly; blocks summed in fixed point) are those of the general path below.
+constexpr int kFastQRaw = 512;    // LR block entries of the component (before removing repeats)
+constexpr int kFastQ = 64;        // distinct LR blocks of the component
+constexpr int kFastA = 256;       // blocks re-searched
+constexpr int kFastPx = 4096;     // pixels re-searched
+constexpr int kFastRegion = 2304; // LR pixels of the staged neighbourhood
+
+struct FastSmem {
+    float4 region[kFastRegion];
+    unsigned long long best[kFastQ];
+    int rawq[kFastQRaw];
+    int qs[kFastQ];
+    uint32_t newc[kFastQ];
+    int blocks[kFastA];
+    int pxoff[kFastA + 1];
+    int scan[32];
+    short qmap[kFastRegion];
+    uint8_t amap[kFastRegion];
+    uint16_t rcode[kFastPx];
+    float rw[kFastPx];
+    float rerr[kFastPx];
+    uint32_t hrpx[kFastPx];   // guide colour of every re-searched pixel
+    float eold[kFastPx];      // its error before the trial
+    int full[kFastPx];        // pixels that need a full search (see fast_block_pass)
+    int nfull;
+};
+
+constexpr uint16_t kNotSearched = 0xFFFFu;
+
+// The re-search of a trial in three passes, so that the few pixels that need a full search do
+// not hold up whole warps:
+//   pass 1 (a warp per block): load each pixel's guide colour, previous error and pair; with
+//     `incr` (STRICT: Theta is Algorithm 1 on the LR image before the trial) re-search it exactly
+//     from its previous pair when the replaced LR pixels in its window (at most kMaxChg) are
+//     neither its a nor its b and do not become its a; otherwise queue it for a full search
+//     (entry: pixel index, block, and the new a when only step 2 must be redone);
+//   pass 2 (every thread of the CTA): the queued searches;
+//   pass 3 (a warp per block): the block's old and new error sums, Kahan per lane over the
+//     block's pixels in raster order, then a butterfly (the order of the general path).
+constexpr int kMaxChg = 8;
+
+__device__ __forceinline__ int full_entry(int pix, int bi, int a_known) {
+    return pix | (bi << 12) | ((a_known + 1) << 20);
+}
+
+template <int S>
+__device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_, const JImg& I,
+                                             FastSmem& F, int RW, int RV0, int RU0, int bi,
+                                             int comp, bool incr) {
+    constexpr int r = (S - 1) / 2, K = S * S;
+    const int lane = threadIdx.x & 31;
+    const int c = F.blocks[bi], off = F.pxoff[bi];
+    const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+    uint32_t rm, cm;
+    window_masks(bv, bu, I.h, I.w, S, rm, cm);
+    const float4* win = &F.region[(bv - r - RV0) * RW + (bu - r - RU0)];
+    // the replaced LR pixels in this block's window, ascending window index
+    int chg[kMaxChg];
+    int nchg = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxChg; ++t) chg[t] = 0;
+    if (incr) {
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            const int k = k0 + lane;
+            bool is = false;
+            if (k < K)
+                is = F.qmap[(bv - r + k / S - RV0) * RW + (bu - r + k % S - RU0)] != 0;
+            unsigned m = __ballot_sync(0xffffffffu, is);
+            while (m) {
+                const int kk = k0 + __ffs(m) - 1;
+                m &= m - 1;
+#pragma unroll
+                for (int t = 0; t < kMaxChg; ++t)
+                    if (t == nchg) chg[t] = kk;
+                ++nchg;
+            }
+        }
+    }
+    const bool use_incr = incr && nchg <= kMaxChg;
+    const int ys = bv * I.s, xs = bu * I.s;
+    const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
+    for (int jp = lane; jp < ey * ex; jp += 32) {
+        const int y = ys + jp / ex, x = xs + jp % ex;
+        const int64_t lp = (int64_t)y * I.W + x;
+        if (comp >= 0 && __ldcg(&W_.lab[I.p0 + lp]) != comp) {
+            F.rcode[off + jp] = kNotSearched;
+            continue;
+        }
+        const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
+        const uint32_t rgb = (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16);
+        F.hrpx[off + jp] = rgb;
+        F.eold[off + jp] = __ldcg(&I.err[lp]);
+        if (!use_incr) {
+            F.full[atomicAdd(&F.nfull, 1)] = full_entry(off + jp, bi, -1);
+            continue;
+        }
+        const float ir = (float)(rgb & 255u), ig = (float)((rgb >> 8) & 255u),
+                    ib = (float)(rgb >> 16);
+        const int code0 = (int)__ldcg(&I.code[lp]);
+        const int a0 = code0 / K, b0 = code0 % K;
+        bool redo_a = false, redo_b = false;
+#pragma unroll
+        for (int t = 0; t < kMaxChg; ++t) {
+            redo_a |= t < nchg && chg[t] == a0;
+            redo_b |= t < nchg && chg[t] == b0;
+        }
+        if (redo_a) {
+            F.full[atomicAdd(&F.nfull, 1)] = full_entry(off + jp, bi, -1);
+            continue;
+        }
+        // step 1 from the previous a: only a replaced pixel can be nearer (ties: lowest k)
+        const float4 ca0 = lds_f4(&win[(a0 / S) * RW + (a0 % S)]);
+        float bd = dist2(ca0.x - ir, ca0.y - ig, ca0.z - ib);
+        int a = a0;
+#pragma unroll
+        for (int t = 0; t < kMaxChg; ++t) {
+            if (t >= nchg) break;
+            const int k = chg[t];
+            const float4 cc = lds_f4(&win[(k / S) * RW + (k % S)]);
+            const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
+            if (d2 < bd || (d2 == bd && k < a)) {
+                bd = d2;
+                a = k;
+            }
+        }
+        if (a != a0 || redo_b) {
+            F.full[atomicAdd(&F.nfull, 1)] = full_entry(off + jp, bi, a);
+            continue;
+        }
+        // step 2 from the previous b: only a replaced pixel can beat it (ties: lowest k)
+        const float ur = ca0.x - ir, ug = ca0.y - ig, ub = ca0.z - ib;
+        const float dae = sqrt_approx(bd) + B.eps255;
+        const float4 cb0 = lds_f4(&win[(b0 / S) * RW + (b0 % S)]);
+        float vr = cb0.x - ir, vg = cb0.y - ig, vb = cb0.z - ib;
+        float bkey = b_key(sqrt_approx(dist2(vr, vg, vb)), dae, ur, ug, ub, vr, vg, vb);
+        int b = b0;
+#pragma unroll
+        for (int t = 0; t < kMaxChg; ++t) {
+            if (t >= nchg) break;
+            const int k = chg[t];
+            const float4 cc = lds_f4(&win[(k / S) * RW + (k % S)]);
+            vr = cc.x - ir;
+            vg = cc.y - ig;
+            vb = cc.z - ib;
+            const float key = b_key(sqrt_approx(dist2(vr, vg, vb)), dae, ur, ug, ub, vr, vg, vb);
+            if (key < bkey || (key == bkey && k < b)) {
+                bkey = key;
+                b = k;
+            }
+        }
+        SearchOut o;
+        o.ka = a;
+        finish_pair(win, RW, S, b, ir, ig, ib, dae, bkey, o);
+        F.rcode[off + jp] = (uint16_t)(o.ka * K + o.kb);
+        F.rw[off + jp] = o.omega;
+        F.rerr[off + jp] = o.err;
+    }
+}
+
+// One queued full search (entry from fast_block_pass).
+template <int S>
+__device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, FastSmem& F, int RW,
+                                              int RV0, int RU0, int e) {
+    constexpr int r = (S - 1) / 2, K = S * S;
+    const int pix = e & 0xFFF, bi = (e >> 12) & 0xFF, a_known = (e >> 20) - 1;
+    const int c = F.blocks[bi];
+    const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+    uint32_t rm, cm;
+    window_masks(bv, bu, I.h, I.w, S, rm, cm);
+    const float4* win = &F.region[(bv - r - RV0) * RW + (bu - r - RU0)];
+    const uint32_t rgb = F.hrpx[pix];
+    const float ir = (float)(rgb & 255u), ig = (float)((rgb >> 8) & 255u), ib = (float)(rgb >> 16);
+    SearchOut o;
+    if (a_known >= 0) {
+        const float4 ca = lds_f4(&win[(a_known / S) * RW + (a_known % S)]);
+        o = step_b<S, true, false>(win, RW, rm, cm, a_known,
+                                   dist2(ca.x - ir, ca.y - ig, ca.z - ib), ir, ig, ib, B.eps255);
+    } else {
+        o = search_pixel<S, true>(win, RW, rm, cm, ir, ig, ib, B.eps255, false);
+    }
+    F.rcode[pix] = (uint16_t)(o.ka * K + o.kb);
+    F.rw[pix] = o.omega;
+    F.rerr[pix] = o.err;
+}
+
+// Block bi's old and new error sums (fixed order) and the number of pixels re-searched.
+__device__ __forceinline__ void fast_block_sums(const JImg& I, FastSmem& F, int RW, int RV0,
+                                                int RU0, int bi, float& e0, float& e1, int& ns) {
+    const int lane = threadIdx.x & 31;
+    const int c = F.blocks[bi], off = F.pxoff[bi];
+    const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+    const int ey = min(I.s, I.H - bv * I.s), ex = min(I.s, I.W - bu * I.s);
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+    int n = 0;
+    for (int jp = lane; jp < ey * ex; jp += 32) {
+        if (F.rcode[off + jp] == kNotSearched) continue;
+        kahan_add(s0, c0, F.eold[off + jp]);
+        kahan_add(s1, c1, F.rerr[off + jp]);
+        ++n;
+    }
+    float t0 = s0 - c0, t1 = s1 - c1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+    }
+    e0 = t0;
+    e1 = t1;
+    ns = n;
+}
+
+struct FastShared {
+    int nq, vmin, vmax, umin, umax, na, npx, ok;
+    unsigned long long e0, e1;
+    int searched;
+};
+
+// Tries component j in this CTA if it fits (returns false, having changed nothing, if it does
+// not). On return *accept holds the decision and the global state holds its outcome.
+__device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int img, int j,
+                          int2 st, int2 en, FastSmem& F, FastShared& sh, int* accept) {
+    const JointWs& W_ = X.ws;
+    const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x, nwarps = nthr >> 5;
+    const int r = (I.S - 1) / 2;
+    const int Rm = B.strict ? 2 * r : r, Am = B.strict ? r : 0;
+    const int nraw = en.y - st.y;
+    if (nraw > kFastQRaw) return false;   // uniform: from global values every thread read
+    if (tid == 0) {
+        sh.nq = 0;
+        sh.vmin = 0x7fffffff;
+        sh.umin = 0x7fffffff;
+        sh.vmax = -1;
+        sh.umax = -1;
+        sh.e0 = 0ull;
+        sh.e1 = 0ull;
+        sh.searched = 0;
+        sh.ok = 1;
+    }
+    for (int t = tid; t < nraw; t += nthr) F.rawq[t] = (int)((int64_t)W_.qlist[st.y + t] - I.q0);
+    __syncthreads();
+    // distinct blocks Q (first occurrences) and their bounding box
+    for (int t = tid; t < nraw; t += nthr) {
+        const int q = F.rawq[t];
+        bool first = true;
+        for (int k = 0; k < t; ++k)
+            if (F.rawq[k] == q) {
+                first = false;
+                break;
+            }
+        if (!first) continue;
+        const int idx = atomicAdd(&sh.nq, 1);
+        if (idx < kFastQ) F.qs[idx] = q;
+        const int v = q / I.w, u = q % I.w;
+        atomicMin(&sh.vmin, v);
+        atomicMax(&sh.vmax, v);
+        atomicMin(&sh.umin, u);
+        atomicMax(&sh.umax, u);
+    }
+    __syncthreads();
+    const int nq = sh.nq;
+    const int RV0 = sh.vmin - Rm, RU0 = sh.umin - Rm;
+    const int RH = sh.vmax - sh.vmin + 1 + 2 * Rm, RW = sh.umax - sh.umin + 1 + 2 * Rm;
+    if (nq > kFastQ || RH * RW > kFastRegion) return false;
+    // region maps: Q blocks (index + 1) and the blocks to re-search
+    for (int t = tid; t < RH * RW; t += nthr) {
+        F.qmap[t] = 0;
+        F.amap[t] = 0;
+    }
+    __syncthreads();
+    const int NA = (2 * Am + 1) * (2 * Am + 1);
+    for (int t = tid; t < nq * NA; t += nthr) {
+        const int q = F.qs[t / NA], nb = t % NA;
+        const int v = q / I.w + nb / (2 * Am + 1) - Am, u = q % I.w + nb % (2 * Am + 1) - Am;
+        if (nb == 0) {
+            const int qv = q / I.w, qu = q % I.w;
+            F.qmap[(qv - RV0) * RW + (qu - RU0)] = (short)(t / NA + 1);
+        }
+        if (v >= 0 && v < I.h && u >= 0 && u < I.w) F.amap[(v - RV0) * RW + (u - RU0)] = 1;
+    }
+    __syncthreads();
+    // the blocks to re-search in raster order, with their pixel offsets
+    const int ncell = RH * RW;
+    const int per = (ncell + nthr - 1) / nthr;
+    const int c_beg = tid * per, c_end = min(c_beg + per, ncell);
+    int myb = 0, mypx = 0;
+    for (int c = c_beg; c < c_end; ++c) {
+        if (!F.amap[c]) continue;
+        const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+        ++myb;
+        mypx += min(I.s, I.H - bv * I.s) * min(I.s, I.W - bu * I.s);
+    }
+    int bex, pex;
+    const int na = block_excl_scan_any(myb, &bex, F.scan);
+    const int npx = block_excl_scan_any(mypx, &pex, F.scan);
+    if (na > kFastA || npx > kFastPx) return false;
+    GLU_TRACE(X.it, j, 4);
+    for (int c = c_beg, k = bex, o = pex; c < c_end; ++c) {
+        if (!F.amap[c]) continue;
+        const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+        F.blocks[k] = c;
+        F.pxoff[k] = o;
+        ++k;
+        o += min(I.s, I.H - bv * I.s) * min(I.s, I.W - bu * I.s);
+    }
+    // the LR neighbourhood in 1/255 units (zero outside the image: masked by the search)
+    for (int t = tid; t < ncell; t += nthr) {
+        const int v = RV0 + t / RW, u = RU0 + t % RW;
+        float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (v >= 0 && v < I.h && u >= 0 && u < I.w) {
+            const uint32_t c = load_rgb(I.lr, I.lr_pitch, v, u);
+            c4 = make_float4((float)(c & 255u), (float)((c >> 8) & 255u), (float)(c >> 16), 0.f);
+        }
+        F.region[t] = c4;
+    }
+    for (int t = tid; t < nq; t += nthr) F.best[t] = 0ull;
+    __syncthreads();
+    // per q, the component's largest current error in the block (ties: lowest raster index)
+    for (int t = st.x + tid; t < en.x; t += nthr) {
+        const int64_t lp = (int64_t)W_.comp_pix[t] - I.p0;
+        const int y = (int)(lp / I.W), x = (int)(lp % I.W);
+        const int qi = F.qmap[(y / I.s - RV0) * RW + (x / I.s - RU0)] - 1;
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(__ldcg(&I.err[lp])) << 32) |
+            (unsigned long long)(0xFFFFFFFFu - (uint32_t)lp);
+        atomicMax(&F.best[qi], key);
+    }
+    __syncthreads();
+    // the replacement colours, applied to the staged neighbourhood only
+    for (int t = tid; t < nq; t += nthr) {
+        const uint32_t lp = 0xFFFFFFFFu - (uint32_t)(F.best[t] & 0xFFFFFFFFull);
+        const int y = (int)(lp / (uint32_t)I.W), x = (int)(lp % (uint32_t)I.W);
+        const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
+        const uint32_t c = (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16);
+        F.newc[t] = c;
+        const int q = F.qs[t];
+        F.region[(q / I.w - RV0) * RW + (q % I.w - RU0)] =
+            make_float4((float)ip[0], (float)ip[1], (float)ip[2], 0.f);
+    }
+    __syncthreads();
+    GLU_TRACE(X.it, j, 5);
+    // the trial: Algorithm 1 on the affected blocks
+    const int comp = B.strict ? -1 : j;
+    const bool incr = B.strict != 0;   // PAPER leaves Theta stale outside components: no re-search
+    if (tid == 0) F.nfull = 0;
+    __syncthreads();
+    for (int bi = warp; bi < na; bi += nwarps) {
+        switch (I.S) {
+            case 1: fast_block_pass<1>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
+            case 3: fast_block_pass<3>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
+            case 5: fast_block_pass<5>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
+            case 7: fast_block_pass<7>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
+            default: fast_block_pass<9>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
+        }
+    }
+    __syncthreads();
+    const int nfull = F.nfull;
+    GLU_TRACE(X.it, j, 7);
+#ifdef GLU_TRIAL_TRACE
+    if (tid == 0 && j < kTraceMax) g_trace[X.it][j][9] = (unsigned long long)nfull;
+#endif
+    for (int t = tid; t < nfull; t += nthr) {
+        const int e = F.full[t];
+        switch (I.S) {
+            case 1: fast_full_search<1>(B, I, F, RW, RV0, RU0, e); break;
+            case 3: fast_full_search<3>(B, I, F, RW, RV0, RU0, e); break;
+            case 5: fast_full_search<5>(B, I, F, RW, RV0, RU0, e); break;
+            case 7: fast_full_search<7>(B, I, F, RW, RV0, RU0, e); break;
+            default: fast_full_search<9>(B, I, F, RW, RV0, RU0, e); break;
+        }
+    }
+    __syncthreads();
+    GLU_TRACE(X.it, j, 8);
+    for (int bi = warp; bi < na; bi += nwarps) {
+        float e0, e1;
+        int ns;
+        fast_block_sums(I, F, RW, RV0, RU0, bi, e0, e1, ns);
+        if ((threadIdx.x & 31) == 0 && ns > 0) {
+            atomicAdd(&sh.e0, (unsigned long long)to_fixed(e0));
+            atomicAdd(&sh.e1, (unsigned long long)to_fixed(e1));
+            atomicAdd(&sh.searched, ns);
+        }
+    }
+    __syncthreads();
+    GLU_TRACE(X.it, j, 6);
+    const bool keep = !((long long)sh.e1 > (long long)sh.e0);
+    if (keep) {
+        // write the kept trial: Theta / E of every re-searched pixel, then the LR colours
+        for (int bi = warp; bi < na; bi += nwarps) {
+            const int c = F.blocks[bi];
+            const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+            const int ys = bv * I.s, xs = bu * I.s;
+            const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
+            const int off = F.pxoff[bi];
+            for (int jp = (threadIdx.x & 31); jp < ey * ex; jp += 32) {
+                const uint16_t code = F.rcode[off + jp];
+                if (code == kNotSearched) continue;
+                const int64_t lp = (int64_t)(ys + jp / ex) * I.W + xs + jp % ex;
+                I.code[lp] = code;
+                store_weight(I.weight, B.wfmt, lp, F.rw[off + jp]);
+                I.err[lp] = F.rerr[off + jp];
+            }
+        }
+        for (int t = tid; t < nq; t += nthr) {
+            const int q = F.qs[t];
+            store_rgb(I.lr, I.lr_pitch, q / I.w, q % I.w, F.newc[t]);
+        }
+    }
+    if (tid == 0 && sh.searched)
+        atomicAdd(&X.ws.ctl->searched[img][X.it], (unsigned long long)sh.searched);
+    *accept = keep ? 1 : 0;
+    return true;
+}
+
+// General path (components too large for fast_trial): in place with backup planes, block items
+// shared with every idle warp of the grid, explicit rollback. Returns false on an exhausted wait.
+__device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int img, int j,
+                          int2 st, int2 en, float4* win, int G, int* s_nu,
+                          unsigned long long* s_e0, unsigned long long* s_e1, int* s_flag,
+                          int* accept, unsigned long long t0) {
+    const JointWs& W_ = X.ws;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int r = (I.S - 1) / 2;
+    if (tid == 0) {
+        *s_nu = 0;
+        *s_e0 = 0ull;
+        *s_e1 = 0ull;
+        *s_flag = 0;
+    }
+    __syncthreads();
+    // the distinct LR blocks Q of the component (stamps drop duplicates)
+    const unsigned long long tagQ = trial_tag(X.it, j, 0);
+    for (int t = st.y + tid; t < en.y; t += nthr) {
+        const int q = W_.qlist[t];
+        if (atomicExch(&W_.stamp[q], tagQ) != tagQ) {
+            const int u = atomicAdd(s_nu, 1);
+            W_.ulist[st.y + u] = q;
+            W_.best[q] = 0ull;
+        }
+    }
+    __syncthreads();
+    const int nu = *s_nu;
+    // per q, the largest current error among the component's pixels in its block
+    // (ties: lowest raster index)
+    for (int t = st.x + tid; t < en.x; t += nthr) {
+        const int p = W_.comp_pix[t];
+        const int64_t lp = p - I.p0;
+        const int y = (int)(lp / I.W), x = (int)(lp % I.W);
+        const int64_t q = I.q0 + (int64_t)(y / I.s) * I.w + (x / I.s);
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(__ldcg(&I.err[lp])) << 32) |
+            (unsigned long long)(0xFFFFFFFFu - (uint32_t)lp);
+        atomicMax(&W_.best[q], key);
+    }
+    __syncthreads();
+    // back up and replace the LR colours
+    for (int t = tid; t < nu; t += nthr) {
+        const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
+        const int qv = (int)(lq / I.w), qu = (int)(lq % I.w);
+        const uint32_t lp = 0xFFFFFFFFu - (uint32_t)(__ldcg(&W_.best[I.q0 + lq]) & 0xFFFFFFFFull);
+        const int y = (int)(lp / (uint32_t)I.W), x = (int)(lp % (uint32_t)I.W);
+        W_.backup[I.q0 + lq] = load_rgb(I.lr, I.lr_pitch, qv, qu);
+        const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
+        store_rgb(I.lr, I.lr_pitch, qv, qu,
+                  (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16));
+    }
+    __threadfence();
+    __syncthreads();
+    // trial: Algorithm 1 again on the affected pixels (STRICT: every block within r of Q; PAPER:
+    // the component's own pixels), in place, summing e0 and e1
+    const int NB = (2 * r + 1) * (2 * r + 1);
+    const int nitems = B.strict ? nu * NB : nu;
+    bool ok = run_task(B, X, win, j, img, st.y, 0, nitems, G, s_e0, s_e1, s_flag, t0);
+    const bool keep = !((long long)*s_e1 > (long long)*s_e0);
+    __syncthreads();
+    // keep (the results are in place) or roll back: Theta and E from the backup planes, the LR
+    // colours from their backups
+    if (!keep && ok) {
+        ok = run_task(B, X, win, j, img, st.y, 1, nitems, G, s_e0, s_e1, s_flag, t0);
+        for (int t = tid; t < nu; t += nthr) {
+            const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
+            store_rgb(I.lr, I.lr_pitch, (int)(lq / I.w), (int)(lq % I.w), W_.backup[I.q0 + lq]);
+        }
+    }
+    *accept = keep ? 1 : 0;
+    return ok;
+}
+
+// The persistent trial kernel. With the dependency graph (the normal case) a CTA takes the next
+// position of the ready queue, waits until a component is published there and tries it; when it
+// finishes, every successor whose last predecessor it was enters the queue. Without it (graph
+// too large for the workspace) components are claimed in index order and each waits for its
+// earlier neighbours. Waiting warps help with the block items of large components' trials.
+__global__ void __launch_bounds__(kTrialThreads, 1)
     k_trials(const __grid_constant__ JBatch B, const TrialCtx X) {
     constexpr int kPend = 512;
     JointCtl* ctl = X.ws.ctl;
     if (!any_active(ctl)) return;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    FastSmem& F = *reinterpret_cast<FastSmem*>(dyn_smem);
     __shared__ float4 wins[kTrialThreads / 32][kSmax * kSmax];
-    __shared__ int s_j, s_nu, s_accept, s_flag, s_npend, s_povf;
+    __shared__ int s_j, s_idx, s_nu, s_accept, s_flag, s_npend, s_povf;
     __shared__ int s_pend[kPend];
     __shared__ unsigned long long s_e0, s_e1;
+    __shared__ FastShared sh;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int G = gridDim.x;
     const int M = ctl->M_cur;
     const JointWs& W_ = X.ws;
     float4* win = wins[warp];
     const unsigned long long t0 = now_ns();
+    const bool dag = *(volatile int*)&ctl->dag_bad[X.it] == 0;
+    bool stop = false;
 
-    for (;;) {
-        if (tid == 0) {
-            s_j = atomicAdd(&ctl->claim[X.it], 1);
-            s_nu = 0;
-            s_e0 = 0;
-            s_e1 = 0;
-            s_flag = 0;
-            s_npend = 0;
-            s_povf = 0;
-        }
-        __syncthreads();
-        const int j = s_j;
-        if (j >= M) break;
-        GLU_TRACE(X.it, j, 0);
-        const int2 st = W_.start[j], en = W_.start[j + 1];
-        const int img = img_of_p(B, W_.roots[j]);
-        const JImg& I = B.im[img];
-        const int r = (I.S - 1) / 2;
-        const int D = B.strict ? 2 * r : r;
-        const int ND = (2 * D + 1) * (2 * D + 1);
-
-        // 1. the earlier components whose LR blocks lie within D of ours and are not done yet
-        const int npairs = (en.y - st.y) * ND;
-        for (int t = tid; t < npairs; t += kTrialThreads) {
-            const int64_t lq = (int64_t)W_.qlist[st.y + t / ND] - I.q0;
-            const int nb = t % ND;
-            const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
-            const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
-            if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
-            const int64_t b = I.q0 + (int64_t)bv * I.w + bu;
-            if (__ldcg(&W_.ovf[b])) {
-                s_povf = 1;  // more components than owner slots: wait for every earlier one
-                continue;
+    while (!stop) {
+        int j;
+        if (dag) {
+            if (tid == 0) {
+                s_idx = atomicAdd(&ctl->head[X.it], 1);
+                s_flag = 0;
             }
-            for (int k = 0; k < kOwnSlots; ++k) {
-                const int i = __ldcg(&W_.own[b * kOwnSlots + k]);
-                if (i < 0) break;
-                if (i < j && ld_acquire(&W_.done[i]) == 0) {
-                    const int slot = atomicAdd(&s_npend, 1);
-                    if (slot < kPend) s_pend[slot] = i; else s_povf = 1;
-                }
-            }
-        }
-        __syncthreads();
-        if (s_povf) {
-            // rare fallback: wait in order for every earlier component
-            for (int i = tid; i < j; i += kTrialThreads)
-                if (!wait_done(W_.done, i, ctl)) s_flag = 1;
-        } else {
-            // wait, helping other components' tasks meanwhile; the loop decisions are
-            // CTA-uniform (__syncthreads_or)
-            const int np = min(s_npend, kPend);
+            __syncthreads();
+            const int idx = s_idx;
+            if (idx >= M) break;
+            // wait for the component published at this position, helping meanwhile
             int hint = -1;
             for (;;) {
-                int mine = 0;
-                for (int t = tid; t < np; t += kTrialThreads) {
-                    const int i = s_pend[t];
-                    if (i >= 0) {
-                        if (ld_acquire(&W_.done[i]) != 0) s_pend[t] = -1; else mine = 1;
-                    }
-                }
-                if (__syncthreads_or(mine) == 0) break;
+                if (tid == 0) s_j = ld_acquire(&W_.queue[idx]);
+                __syncthreads();
+                if (s_j >= 0) break;
                 if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
-                const int abort = warp_should_abort(ctl, t0) ? 1 : 0;
-                if (__syncthreads_or(abort)) {
+                if (__syncthreads_or(warp_should_abort(ctl, t0) ? 1 : 0)) {
                     if (tid == 0) s_flag = 1;
+                    __syncthreads();
                     break;
                 }
             }
-        }
-        __syncthreads();
-        __threadfence();
-        if (s_flag) {
+            if (s_flag) {
+                if (tid == 0) {
+                    set_status(GLU_ERR_TIMEOUT);
+                    atomicExch(&ctl->timeout, 1);
+                }
+                break;
+            }
+            j = s_j;
+        } else {
             if (tid == 0) {
-                set_status(GLU_ERR_TIMEOUT);
-                atomicExch(&ctl->timeout, 1);
-                st_release(&W_.done[j], 1);  // never leave a later component waiting on us
-                atomicAdd(&ctl->finished[X.it], 1);
+                s_j = atomicAdd(&ctl->claim[X.it], 1);
+                s_flag = 0;
+                s_npend = 0;
+                s_povf = 0;
             }
             __syncthreads();
-            continue;
-        }
-        GLU_TRACE(X.it, j, 1);
-
-        // 2. the distinct LR blocks Q of the component (stamps drop duplicates)
-        const unsigned long long tagQ = trial_tag(X.it, j, 0);
-        for (int t = st.y + tid; t < en.y; t += kTrialThreads) {
-            const int q = W_.qlist[t];
-            if (atomicExch(&W_.stamp[q], tagQ) != tagQ) {
-                const int u = atomicAdd(&s_nu, 1);
-                W_.ulist[st.y + u] = q;
-                W_.best[q] = 0ull;
+            j = s_j;
+            if (j >= M) break;
+            GLU_TRACE(X.it, j, 0);
+            const int2 st = W_.start[j], en = W_.start[j + 1];
+            const JImg& I = B.im[img_of_p(B, W_.roots[j])];
+            const int r = (I.S - 1) / 2;
+            const int D = B.strict ? 2 * r : r;
+            const int ND = (2 * D + 1) * (2 * D + 1);
+            // the earlier components whose LR blocks lie within D of ours and are not done yet
+            const int npairs = (en.y - st.y) * ND;
+            for (int t = tid; t < npairs; t += kTrialThreads) {
+                const int64_t lq = (int64_t)W_.qlist[st.y + t / ND] - I.q0;
+                const int nb = t % ND;
+                const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+                const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+                if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
+                const int64_t b = I.q0 + (int64_t)bv * I.w + bu;
+                if (__ldcg(&W_.ovf[b])) {
+                    s_povf = 1;  // more components than owner slots: wait for every earlier one
+                    continue;
+                }
+                for (int k = 0; k < kOwnSlots; ++k) {
+                    const int i = __ldcg(&W_.own[b * kOwnSlots + k]);
+                    if (i < 0) break;
+                    if (i < j && ld_acquire(&W_.done[i]) == 0) {
+                        const int slot = atomicAdd(&s_npend, 1);
+                        if (slot < kPend) s_pend[slot] = i; else s_povf = 1;
+                    }
+                }
             }
-        }
-        __syncthreads();
-        const int nu = s_nu;
-        // 3. per q, the largest current error among the component's pixels in its block
-        //    (ties: lowest raster index)
-        for (int t = st.x + tid; t < en.x; t += kTrialThreads) {
-            const int p = W_.comp_pix[t];
-            const int64_t lp = p - I.p0;
-            const int y = (int)(lp / I.W), x = (int)(lp % I.W);
-            const int64_t q = I.q0 + (int64_t)(y / I.s) * I.w + (x / I.s);
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(__ldcg(&I.err[lp])) << 32) |
-                (unsigned long long)(0xFFFFFFFFu - (uint32_t)lp);
-            atomicMax(&W_.best[q], key);
-        }
-        __syncthreads();
-        // 4. back up and replace the LR colours
-        for (int t = tid; t < nu; t += kTrialThreads) {
-            const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
-            const int qv = (int)(lq / I.w), qu = (int)(lq % I.w);
-            const uint32_t lp =
-                0xFFFFFFFFu - (uint32_t)(__ldcg(&W_.best[I.q0 + lq]) & 0xFFFFFFFFull);
-            const int y = (int)(lp / (uint32_t)I.W), x = (int)(lp % (uint32_t)I.W);
-            W_.backup[I.q0 + lq] = load_rgb(I.lr, I.lr_pitch, qv, qu);
-            const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
-            store_rgb(I.lr, I.lr_pitch, qv, qu,
-                      (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16));
+            __syncthreads();
+            if (s_povf) {
+                // rare fallback: wait in order for every earlier component
+                for (int i = tid; i < j; i += kTrialThreads)
+                    if (!wait_done(W_.done, i, ctl)) s_flag = 1;
+            } else {
+                const int np = min(s_npend, kPend);
+                int hint = -1;
+                for (;;) {
+                    int mine = 0;
+                    for (int t = tid; t < np; t += kTrialThreads) {
+                        const int i = s_pend[t];
+                        if (i >= 0) {
+                            if (ld_acquire(&W_.done[i]) != 0) s_pend[t] = -1; else mine = 1;
+                        }
+                    }
+                    if (__syncthreads_or(mine) == 0) break;
+                    if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
+                    if (__syncthreads_or(warp_should_abort(ctl, t0) ? 1 : 0)) {
+                        if (tid == 0) s_flag = 1;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_flag) {
+                if (tid == 0) {
+                    set_status(GLU_ERR_TIMEOUT);
+                    atomicExch(&ctl->timeout, 1);
+                    st_release(&W_.done[j], 1);  // never leave a later component waiting on us
+                    atomicAdd(&ctl->finished[X.it], 1);
+                }
+                __syncthreads();
+                continue;
+            }
         }
         __threadfence();
-        __syncthreads();
-
-        // 5. trial: Algorithm 1 again on the affected pixels (STRICT: every block within r of
-        //    Q; PAPER: the component's own pixels), in place, summing e0 and e1
-        const int NB = (2 * r + 1) * (2 * r + 1);
-        const int nitems = B.strict ? nu * NB : nu;
-        bool ok = run_task(B, X, win, j, img, st.y, 0, nitems, G, &s_e0, &s_e1, &s_flag, t0);
-        if (tid == 0) s_accept = !(s_e1 > s_e0);
-        __syncthreads();
+        GLU_TRACE(X.it, j, 1);
+        const int2 st = W_.start[j], en = W_.start[j + 1];
+        const int img = img_of_p(B, W_.roots[j]);
+        const JImg& I = B.im[img];
+        int accept = 0;
+        bool ok = true;
+        const bool fast = fast_trial(B, X, I, img, j, st, en, F, sh, &accept);
+        if (!fast)
+            ok = big_trial(B, X, I, img, j, st, en, win, G, &s_nu, &s_e0, &s_e1, &s_flag, &accept,
+                           t0);
+        if (tid == 0) s_accept = accept;
         GLU_TRACE(X.it, j, 2);
-        // 6. keep (nothing to do: the results are in place) or roll back: restore Theta and E
-        //    from the backup planes and the LR colours from their backups
-        if (!s_accept && ok) {
-            ok = run_task(B, X, win, j, img, st.y, 1, nitems, G, &s_e0, &s_e1, &s_flag, t0);
-            for (int t = tid; t < nu; t += kTrialThreads) {
-                const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
-                store_rgb(I.lr, I.lr_pitch, (int)(lq / I.w), (int)(lq % I.w), W_.backup[I.q0 + lq]);
-            }
-        }
+        // the outcome is visible before any successor can start
+        __threadfence();
         __syncthreads();
         if (tid == 0) {
             if (!ok) {
                 set_status(GLU_ERR_TIMEOUT);
                 atomicExch(&ctl->timeout, 1);
             }
-            __threadfence();
             W_.dlog[(int64_t)X.it * W_.mcap + j] = (int8_t)(s_accept ? 1 : 0);
             if (s_accept) atomicAdd(&ctl->accepted[img][X.it], 1);
             else atomicAdd(&ctl->rolled[img][X.it], 1);
+        }
+        if (dag) {
+            const int s0 = W_.dag_start[j].x, s1 = W_.dag_start[j + 1].x;
+            for (int k = s0 + tid; k < s1; k += kTrialThreads) {
+                const int sj = W_.succ[k];
+                if (atomicSub(&W_.pend[sj], 1) == 1) {
+                    GLU_TRACE_ANY(X.it, sj, 0);   // the time it became ready
+                    __threadfence();
+                    const int pos = atomicAdd(&ctl->tail[X.it], 1);
+                    st_release(&W_.queue[pos], sj);
+                }
+            }
+        }
+        if (tid == 0) {
             st_release(&W_.done[j], 1);
             atomicAdd(&ctl->finished[X.it], 1);
         }
         GLU_TRACE(X.it, j, 3);
+        if (!ok) stop = true;
         __syncthreads();
     }
-    // no component left to claim: help the running ones until every component is done
+    // no component left to take: help the running ones until every component is done
     // (per warp; lane 0 decides)
     const int lane = tid & 31;
     int hint = -1;
@@ -1239,16 +1923,20 @@ static int grid_cap(int64_t work, int threads, int per_sm = 16) {
 
 static int launch_trials(const JBatch& B, const TrialCtx& X, cudaStream_t st) {
     static int blocks_per_sm = -1;
+    const size_t smem = sizeof(FastSmem);
     if (blocks_per_sm < 0) {
+        if (cudaFuncSetAttribute(k_trials, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return GLU_ERR_CUDA;
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trials, kTrialThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trials, kTrialThreads, smem) !=
             cudaSuccess)
             return GLU_ERR_CUDA;
         blocks_per_sm = nb > 0 ? nb : 1;
     }
     int grid = sm_count() * blocks_per_sm;
     if (grid > kMaxSlots) grid = kMaxSlots;
-    k_trials<<<grid, kTrialThreads, 0, st>>>(B, X);
+    k_trials<<<grid, kTrialThreads, smem, st>>>(B, X);
     GLU_LAUNCH_CHECK();
     return GLU_OK;
 }
@@ -1355,7 +2043,8 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
         k_root_count<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, np, ws.tile_a, ws.ctl);
         k_root_scan<<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
         k_root_scatter<<<tiles_a, kScanThreads, 0, st>>>(B, ws.lab, ws.tile_a, ws.roots, ws.cnt,
-                                                         ws.fill, ws.done, ws.ctl, it);
+                                                         ws.fill, ws.done, ws.dag_cnt,
+                                                         ws.dag_fill, ws.queue, ws.ctl, it);
         k_comp_count<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.roots, ws.cnt, ws.own, ws.ovf,
                                                     ws.qflag, ws.ctl);
         k_comp_tile_reduce<<<tiles_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.ctl);
@@ -1363,6 +2052,12 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
         k_comp_scan<<<tiles_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.start, ws.ctl);
         k_comp_fill<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.qflag, ws.start, ws.fill,
                                                    ws.comp_pix, ws.qlist, ws.ctl);
+        // the trials' dependency graph
+        k_deps<0><<<grid_cap(ws.mcap, 1, 8), 256, 0, st>>>(B, ws, it);
+        k_comp_tile_reduce<<<tiles_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.ctl);
+        k_comp_tile_scan<<<1, kScanThreads, 0, st>>>(ws.tile_b, ws.ctl);
+        k_comp_scan<<<tiles_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.dag_start, ws.ctl);
+        k_deps<1><<<grid_cap(ws.mcap, 1, 8), 256, 0, st>>>(B, ws, it);
         GLU_LAUNCH_CHECK();
         prof::mark(slot, evi++, st);
         X.it = it;

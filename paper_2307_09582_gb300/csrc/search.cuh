@@ -1,5 +1,7 @@
 // Per-pixel candidate search of Algorithm 1 (Sec. 3.2), shared by the full-image search kernel
-// and the joint-optimisation trials so both compute bit-identical Theta and error values.
+// and the joint-optimisation trials so both compute bit-identical Theta and error values. The
+// pieces (step 2 for a given a, the candidate key, the chosen pair's weight and error) are also
+// used by the trials' exact re-search after a few window colours change.
 //
 // Colours are floats in 1/255 units. For uint8 inputs every distance ||I_p - L_c||^2 is an
 // integer below 2^24 and is computed exactly, so the nearest-colour choice of a is exact.
@@ -37,6 +39,64 @@ __device__ __forceinline__ float dist2(float er, float eg, float eb) {
     return __fmaf_rn(eb, eb, __fmaf_rn(eg, eg, __fmul_rn(er, er)));
 }
 
+// Step-2 key of candidate b for a fixed a: the squared Eq. 3 error in 1/255 units. With the Eq. 5
+// weight w = d_b / (d_a + d_b + eps) and u = L_a - I, v = L_b - I, the residual is
+// r = w u + (1 - w) v = (d_b u + (d_a + eps) v) / D with D = d_a + d_b + eps. One float per
+// candidate, compared exactly, so the candidate order is a total order (ties: lowest k) and a
+// re-search after some candidates change can be done exactly from the previous winner.
+__device__ __forceinline__ float b_key(float db, float dae, float ur, float ug, float ub, float vr,
+                                       float vg, float vb) {
+    const float xr = __fmaf_rn(db, ur, __fmul_rn(dae, vr));
+    const float xg = __fmaf_rn(db, ug, __fmul_rn(dae, vg));
+    const float xb = __fmaf_rn(db, ub, __fmul_rn(dae, vb));
+    const float num = dist2(xr, xg, xb);
+    const float D = __fadd_rn(db, dae);
+    return __fdividef(num, __fmul_rn(D, D));
+}
+
+// Weight and error of the chosen pair (the same operations wherever a pair is chosen).
+__device__ __forceinline__ void finish_pair(const float4* win, int rs, int S, int b, float ir,
+                                            float ig, float ib, float dae, float bkey,
+                                            SearchOut& o) {
+    const float4 cb = lds_f4(&win[(b / S) * rs + (b % S)]);
+    const float bdb = sqrt_approx(dist2(cb.x - ir, cb.y - ig, cb.z - ib));
+    o.kb = b;
+    o.omega = __fdividef(bdb, bdb + dae);
+    o.err = sqrt_approx(bkey) * (1.0f / 255.0f);
+}
+
+// Step 2 of Algorithm 1 for a fixed a (window index) at squared distance d2a: b over the whole
+// window (b = a included) minimising the key, ties to the lowest k.
+template <int S, bool kCompact, bool kInterior>
+__device__ __forceinline__ SearchOut step_b(const float4* __restrict__ win, int rs,
+                                            uint32_t rowmask, uint32_t colmask, int a, float d2a,
+                                            float ir, float ig, float ib, float eps255) {
+    constexpr int kRowUnroll = (kCompact || S > 5) ? 1 : S;
+    const float4 ca = lds_f4(&win[(a / S) * rs + (a % S)]);
+    const float ur = ca.x - ir, ug = ca.y - ig, ub = ca.z - ib;
+    const float dae = sqrt_approx(d2a) + eps255;
+    float bkey = kInf;
+    int b = a;
+#pragma unroll(kRowUnroll)
+    for (int dy = 0; dy < S; ++dy) {
+#pragma unroll
+        for (int dx = 0; dx < S; ++dx) {
+            const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
+            const float4 c = lds_f4(&win[dy * rs + dx]);
+            const float vr = c.x - ir, vg = c.y - ig, vb = c.z - ib;
+            const float key = b_key(sqrt_approx(dist2(vr, vg, vb)), dae, ur, ug, ub, vr, vg, vb);
+            if (ok && key < bkey) {
+                bkey = key;
+                b = dy * S + dx;
+            }
+        }
+    }
+    SearchOut o;
+    o.ka = a;
+    finish_pair(win, rs, S, b, ir, ig, ib, dae, bkey, o);
+    return o;
+}
+
 // win: window candidate (dy, dx) at win[dy * rs + dx] (float4: r, g, b, unused), in shared
 // memory. rowmask / colmask: bit i set when window row / column i lies inside the LR image
 // (ignored when kInterior: the caller guarantees the whole window is inside).
@@ -49,10 +109,7 @@ template <int S, bool kCompact = false, bool kInterior = false>
 __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win, int rs,
                                                   uint32_t rowmask, uint32_t colmask, float ir,
                                                   float ig, float ib, float eps255, bool gnu) {
-    constexpr int K = S * S;
     constexpr int kRowUnroll = (kCompact || S > 5) ? 1 : S;
-    constexpr bool kKeep = !kCompact && S <= 3;   // keep step 1's distances for step 2
-    float d2s[kKeep ? K : 1];
     // Step 1: a = the window pixel with the most similar colour (squared distance, exact).
     float bd = kInf;
     int a = 0;
@@ -63,63 +120,22 @@ __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win
             const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
             const float4 c = lds_f4(&win[dy * rs + dx]);
             const float d2 = dist2(c.x - ir, c.y - ig, c.z - ib);
-            if constexpr (kKeep) d2s[dy * S + dx] = d2;
             if (ok && d2 < bd) {
                 bd = d2;
                 a = dy * S + dx;
             }
         }
     }
-    const float4 ca = lds_f4(&win[(a / S) * rs + (a % S)]);
-    const float ur = ca.x - ir, ug = ca.y - ig, ub = ca.z - ib;
-    const float da = sqrt_approx(bd);
-    SearchOut o;
-    o.ka = a;
     if (gnu) {  // weight fixed to 1: T_hat = T_a
+        SearchOut o;
+        o.ka = a;
         o.kb = a;
         o.omega = 1.0f;
-        o.err = da * (1.0f / 255.0f);
+        o.err = sqrt_approx(bd) * (1.0f / 255.0f);
         return o;
     }
-    // Step 2: fix a; for every b (b = a included) the Eq. 5 weight w = d_b / (d_a + d_b + eps)
-    // and the Eq. 3 residual r = w u + (1 - w) v with u = L_a - I, v = L_b - I. The comparison
-    // uses D * r = d_b u + (d_a + eps) v and D = d_a + d_b + eps: err^2 = |D r|^2 / D^2,
-    // compared by cross-multiplication so no candidate needs a division.
-    const float dae = da + eps255;
-    float bnum = kInf, bden = 1.0f;
-    int b = a;
-#pragma unroll(kRowUnroll)
-    for (int dy = 0; dy < S; ++dy) {
-#pragma unroll
-        for (int dx = 0; dx < S; ++dx) {
-            const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
-            const float4 c = lds_f4(&win[dy * rs + dx]);
-            const float vr = c.x - ir, vg = c.y - ig, vb = c.z - ib;
-            float d2b;
-            if constexpr (kKeep) d2b = d2s[dy * S + dx];
-            else d2b = dist2(vr, vg, vb);
-            const float db = sqrt_approx(d2b);
-            const float xr = __fmaf_rn(db, ur, __fmul_rn(dae, vr));
-            const float xg = __fmaf_rn(db, ug, __fmul_rn(dae, vg));
-            const float xb = __fmaf_rn(db, ub, __fmul_rn(dae, vb));
-            const float num = dist2(xr, xg, xb);
-            const float D = __fadd_rn(db, dae);
-            const float den = __fmul_rn(D, D);
-            if (ok && __fmul_rn(num, bden) < __fmul_rn(bnum, den)) {
-                bnum = num;
-                bden = den;
-                b = dy * S + dx;
-            }
-        }
-    }
-    o.kb = b;
-    // the winner's d_b again (same operations on the same values as in the loop)
-    const float4 cb = lds_f4(&win[(b / S) * rs + (b % S)]);
-    const float bdb = sqrt_approx(dist2(cb.x - ir, cb.y - ig, cb.z - ib));
-    const float wden = bdb + dae;
-    o.omega = __fdividef(bdb, wden);
-    o.err = sqrt_approx(__fdividef(bnum, bden)) * (1.0f / 255.0f);
-    return o;
+    // Step 2: fix a; b over the window with the Eq. 5 weight and the Eq. 3 error
+    return step_b<S, kCompact, kInterior>(win, rs, rowmask, colmask, a, bd, ir, ig, ib, eps255);
 }
 
 // Row/column validity masks of the window centred on LR block (py, px) of an h x w LR image.

@@ -130,7 +130,10 @@ int glu_optimize(const glu_image* hr, const glu_image* lr, const glu_params* par
  *  hr: U8, c = 3. lr_out: U8, c = 3, ceil(H/s) x ceil(W/s). theta as for glu_optimize.
  *  err_map (nullable) as for glu_optimize. stats (HOST, nullable): if given, the call
  *  synchronises `stream` before returning and fills it. ws / ws_bytes: device workspace of at
- *  least glu_joint_workspace_size() bytes, 256-byte aligned; its contents need no init. */
+ *  least glu_joint_workspace_size() bytes, 256-byte aligned; its contents need no init.
+ *  A call repeated with identical arguments (pointers, sizes, parameters, workspace) is recorded
+ *  as a CUDA graph on its second occurrence and replayed from then on (same kernels, same
+ *  results, fewer launch gaps); the library keeps the most recent one. */
 int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
                        glu_image* lr_out, glu_theta* theta, float* err_map,
                        glu_joint_stats* stats, void* ws, size_t ws_bytes, void* stream);
@@ -193,12 +196,13 @@ size_t glu_joint_batched_workspace_size(const glu_batch_item* items, int32_t n,
                                         const glu_params* params);
 
 /* Benchmark instrumentation (not part of the method). glu_joint_profile(1) makes later
- * glu_joint_optimize calls record CUDA events on their stream around their phases; the events
- * of up to 64 calls are kept. glu_joint_profile_read() waits for them, writes the summed
- * milliseconds of [control init + grid downsample, the Algorithm 1 search kernel, large-error
- * set and components, trials, residuals (R_0 and every R_n)] to ms[0..4] and the number of
- * calls to *calls, then forgets them. glu_joint_profile(0) stops recording. Host-side state;
- * not thread-safe. */
+ * glu_joint_optimize calls record CUDA events on their stream around their phases (calls replayed
+ * as a CUDA graph record them as event nodes of the graph; each replay's times are collected
+ * before the next replay is launched, which waits for it). The events of up to 64 directly issued
+ * calls are kept. glu_joint_profile_read() waits for them, writes the summed milliseconds of
+ * [control init + grid downsample, the Algorithm 1 search kernel, large-error set and components,
+ * trials, residuals (R_0 and every R_n)] to ms[0..4] and the number of calls to *calls, then
+ * forgets them. glu_joint_profile(0) stops recording. Host-side state; not thread-safe. */
 int glu_joint_profile(int32_t enable);
 int glu_joint_profile_read(float* ms, int32_t* calls);
 

@@ -122,10 +122,10 @@ __device__ __forceinline__ void store12(__half* out, const float r[12]) {
     __stcs(o + 2, make_uint2(u[4], u[5]));
 }
 
-// Largest LR region (rows x columns) a tile of TH x kApplyTW HR pixels reaches.
-__host__ __device__ __forceinline__ int apply_region_floats(int th, int s, int S) {
+// Largest LR region (rows x columns) a tile of TH x kApplyTW HR pixels reaches, in float4 cells.
+__host__ __device__ __forceinline__ int apply_region_cells(int th, int s, int S) {
     const int r = (S - 1) / 2;
-    return 3 * ((th - 1) / s + 2 + 2 * r) * ((kApplyTW - 1) / s + 2 + 2 * r);
+    return ((th - 1) / s + 2 + 2 * r) * ((kApplyTW - 1) / s + 2 + 2 * r);
 }
 
 // Eq. 1 fast path, tiled: a CTA owns TH x kApplyTW HR pixels (a warp per row, 4 pixels per
@@ -139,13 +139,13 @@ template <int WF, typename OT, int TH>
 __global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_tile(const ApplyArgs P) {
     constexpr int NW = TH < 8 ? TH : 8;   // warps: one row each, RPW rows per warp
     constexpr int RPW = TH / NW;
-    extern __shared__ float reg[];   // RH x RW x 3 region, then K*K offset pairs
+    extern __shared__ float4 reg4[];   // RH x RW region (RGB_), then K*K offset pairs
     const int x0 = blockIdx.x * kApplyTW, y0 = blockIdx.y * TH;
     const int s = P.s, S = P.S, r = (S - 1) >> 1, K = S * S, K2 = K * K;
     const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + TH, P.H);
     const int v0 = y0 / s - r, u0 = x0 / s - r;
     const int RH = (ye - 1) / s + r - v0 + 1, RW = (xe - 1) / s + r - u0 + 1;
-    uint32_t* tab = (uint32_t*)(reg + apply_region_floats(TH, s, S));
+    uint32_t* tab = (uint32_t*)(reg4 + apply_region_cells(TH, s, S));
     const float* T = (const float*)P.T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int xs = x0 + lane * 4;
@@ -164,17 +164,18 @@ __global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_tile(const Ap
         }
     }
     // the LR region, clamped to the image (entries outside it are never selected by a valid code)
-    for (int i = threadIdx.x; i < RH * RW * 3; i += blockDim.x) {
-        const int rr = i / (RW * 3), c3 = i - rr * (RW * 3);
+    for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
+        const int rr = i / RW, c1 = i - rr * RW;
         const int v = min(max(v0 + rr, 0), P.h - 1);
-        const int u = min(max(u0 + c3 / 3, 0), P.w - 1);
-        reg[i] = __ldg(T + (int64_t)v * P.T_pitch + (int64_t)u * 3 + c3 % 3);
+        const int u = min(max(u0 + c1, 0), P.w - 1);
+        const float* t = T + (int64_t)v * P.T_pitch + (int64_t)u * 3;
+        reg4[i] = make_float4(__ldg(t), __ldg(t + 1), __ldg(t + 2), 0.f);
     }
-    // pair code -> (offset of T_a, offset of T_b) in the region, relative to the window corner
+    // pair code -> (cell of T_a, cell of T_b) in the region, relative to the window corner
     for (int c = threadIdx.x; c < K2; c += blockDim.x) {
         const int ka = c / K, kb = c - ka * K;
-        const uint32_t oa = (uint32_t)(((ka / S) * RW + ka % S) * 3);
-        const uint32_t ob = (uint32_t)(((kb / S) * RW + kb % S) * 3);
+        const uint32_t oa = (uint32_t)((ka / S) * RW + ka % S);
+        const uint32_t ob = (uint32_t)((kb / S) * RW + kb % S);
         tab[c] = oa | (ob << 16);
     }
     __syncthreads();
@@ -196,13 +197,13 @@ __global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_tile(const Ap
         const int y = y0 + wid + k * NW;
         if (y >= P.H) break;
         const int py = y / s;
-        const int wrow = py - r - v0;   // region row of the window's top row
+        const int rowbase = (py - r - v0) * RW;   // region row of the window's top row
         const int code[4] = {(int)(cc[k].x & 0xFFFFu), (int)(cc[k].x >> 16),
                              (int)(cc[k].y & 0xFFFFu), (int)(cc[k].y >> 16)};
         float res[12];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int base = (wrow * RW + wcol[j]) * 3;
+            const int base = rowbase + wcol[j];
             const int c = code[j];
             int ia, ib;
             if (c < K2) {
@@ -228,11 +229,10 @@ __global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_tile(const Ap
                     ib = 0;
                 }
             }
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const float ta = reg[ia + ch], tb = reg[ib + ch];
-                res[j * 3 + ch] = __fmaf_rn(w[k][j], ta - tb, tb);
-            }
+            const float4 ta = reg4[ia], tb = reg4[ib];
+            res[j * 3 + 0] = __fmaf_rn(w[k][j], ta.x - tb.x, tb.x);
+            res[j * 3 + 1] = __fmaf_rn(w[k][j], ta.y - tb.y, tb.y);
+            res[j * 3 + 2] = __fmaf_rn(w[k][j], ta.z - tb.z, tb.z);
         }
         store12((OT*)P.out + (int64_t)y * P.out_pitch + (int64_t)xs * 3, res);
     }
@@ -375,11 +375,12 @@ static int apply_tile_dispatch(int v, int wfmt, bool out_f16, F&& launch) {
         if (wfmt == GLU_W_F32) return launch(k_apply3_tile<GLU_W_F32, float, kApplyVariantRows[k]>); \
         if (wfmt == GLU_W_F16) return launch(k_apply3_tile<GLU_W_F16, float, kApplyVariantRows[k]>); \
         return launch(k_apply3_tile<GLU_W_UNORM16, float, kApplyVariantRows[k]>)
-    static_assert(kNumApplyVariants == 3, "one case per variant");
+    static_assert(kNumApplyVariants == 4, "one case per variant");
     switch (v) {
         GLU_APPLY_CASE(0);
         GLU_APPLY_CASE(1);
         GLU_APPLY_CASE(2);
+        GLU_APPLY_CASE(3);
         default: return GLU_ERR_INVALID_ARG;
     }
 #undef GLU_APPLY_CASE
@@ -399,7 +400,7 @@ int launch_apply(const ApplyArgs& a, cudaStream_t st) {
     if ((vec && GLU_APPLY_TILED) || vec16) {
         auto run = [&](int v) -> int {
             const int th = kApplyVariantRows[v];
-            const size_t smem = sizeof(float) * (size_t)apply_region_floats(th, a.s, a.S) +
+            const size_t smem = sizeof(float4) * (size_t)apply_region_cells(th, a.s, a.S) +
                                 sizeof(uint32_t) * (size_t)(a.S * a.S) * (a.S * a.S);
             const dim3 grid((a.W + kApplyTW - 1) / kApplyTW, (a.H + th - 1) / th);
             const int nthr = 32 * (th < 8 ? th : 8);

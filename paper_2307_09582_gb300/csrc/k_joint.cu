@@ -89,6 +89,7 @@ struct JointCtl {
     int rolled[kMaxJointBatch][GLU_MAX_ITERS];
     unsigned long long searched[kMaxJointBatch][GLU_MAX_ITERS];
     double residual[kMaxJointBatch][GLU_MAX_ITERS + 1];
+    unsigned long long racc[kMaxJointBatch];   // residual accumulators (2^-32 units)
 };
 
 struct JointWs {
@@ -111,7 +112,6 @@ struct JointWs {
     unsigned long long* stamp;  // nq
     unsigned long long* best;   // nq
     uint32_t* backup;       // nq
-    double* partial;        // residual partials
     int8_t* dlog;           // N * mcap: kept (1) / rolled back (0) per component and iteration
     int64_t mcap;
     uint16_t* sh_code;      // np: Theta / E before a trial, restored if it is rolled back
@@ -176,7 +176,6 @@ static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t
     t.stamp = (unsigned long long*)take(sizeof(unsigned long long) * nq);
     t.best = (unsigned long long*)take(sizeof(unsigned long long) * nq);
     t.backup = (uint32_t*)take(sizeof(uint32_t) * nq);
-    t.partial = (double*)take(sizeof(double) * (nchunks + 1));
     t.dlog = (int8_t*)take((size_t)(N > 0 ? N : 1) * (size_t)mcap);
     t.mcap = mcap;
     t.sh_code = (uint16_t*)take(sizeof(uint16_t) * np);
@@ -313,67 +312,58 @@ __global__ void k_grid_batch(const __grid_constant__ JBatch B) {
     }
 }
 
-// Residual R = sum_p E_p per image in FP64: a CTA per chunk of one image (fixed chunking, fixed
-// thread assignment, fixed tree), then a fixed-order sum of each image's chunks.
-__global__ void k_resid_partial(const __grid_constant__ JBatch B, double* partial,
-                                const JointCtl* c) {
+// Residual R = sum_p E_p per image. Each E_p is rounded to a multiple of 2^-32 and the
+// multiples are added as 64-bit integers: the sum is exact and independent of the order the
+// CTAs add their chunks in (E_p <= sqrt(3), so 2^31 pixels cannot overflow), and its error
+// against the real-valued sum (at most 2^-33 per pixel, unbiased) is far below that of a plain
+// FP64 accumulation. The result is converted to FP64 once. A CTA per chunk of one image.
+__global__ void k_resid_partial(const __grid_constant__ JBatch B, JointCtl* c) {
     if (!any_active(c)) return;
-    __shared__ double sm[256];
+    __shared__ unsigned long long sm[8];
     const int chunk = blockIdx.x;
     int i = 0;
     while (i + 1 < B.n && B.im[i + 1].c0 <= chunk) ++i;
+    if (!c->active[i]) return;   // uniform across the CTA
     const JImg& I = B.im[i];
     const int64_t n = (int64_t)I.H * I.W;
     const int64_t base = (int64_t)(chunk - I.c0) * kResidChunk;
-    double acc = 0.0;
-    if (c->active[i]) {
-        for (int k = threadIdx.x; k < kResidChunk; k += 256) {
-            const int64_t p = base + k;
-            if (p < n) acc += (double)I.err[p];
-        }
+    unsigned long long acc = 0ull;
+    for (int k = threadIdx.x; k < kResidChunk; k += 256) {
+        const int64_t p = base + k;
+        if (p < n) acc += __float2ull_rn(__ldcg(&I.err[p]) * 4294967296.0f);
     }
-    sm[threadIdx.x] = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0ull;
+        for (int w = 0; w < 8; ++w) t += sm[w];
+        atomicAdd(&c->racc[i], t);
     }
-    if (threadIdx.x == 0) partial[chunk] = sm[0];
 }
 
 // it < 0: initial residuals R_0. Otherwise finish iteration it for every active image: record
 // R, decide whether it stops. An image whose large-error set was empty stops without counting
-// the iteration (Algorithm 2 breaks before any trial).
-__global__ void k_resid_final(const __grid_constant__ JBatch B, const double* partial,
-                              JointCtl* c, int it) {
-    if (!any_active(c)) return;
-    __shared__ double sm[256];
+// the iteration (Algorithm 2 breaks before any trial). The accumulators are cleared for the next
+// residual.
+__global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int it) {
+    if (!any_active(c) || threadIdx.x != 0) return;
     for (int i = 0; i < B.n; ++i) {
-        if (!c->active[i]) continue;  // uniform across the CTA
-        const int nch = (i + 1 < B.n ? B.im[i + 1].c0 : B.nchunks) - B.im[i].c0;
-        double acc = 0.0;
-        for (int k = threadIdx.x; k < nch; k += 256) acc += partial[B.im[i].c0 + k];
-        sm[threadIdx.x] = acc;
-        __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
-            if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
-            __syncthreads();
+        if (!c->active[i]) continue;
+        const double R = (double)c->racc[i] * (1.0 / 4294967296.0);
+        c->racc[i] = 0ull;
+        if (it < 0) {
+            c->residual[i][0] = R;
+        } else if (c->M[i][it] == 0) {
+            c->active[i] = 0;
+        } else {
+            c->residual[i][it + 1] = R;
+            c->iterations[i] = it + 1;
+            if (c->accepted[i][it] == 0 || !(R < c->residual[i][it])) c->active[i] = 0;
         }
-        if (threadIdx.x == 0) {
-            const double R = sm[0];
-            if (it < 0) {
-                c->residual[i][0] = R;
-            } else if (c->M[i][it] == 0) {
-                c->active[i] = 0;
-            } else {
-                c->residual[i][it + 1] = R;
-                c->iterations[i] = it + 1;
-                if (c->accepted[i][it] == 0 || !(R < c->residual[i][it])) c->active[i] = 0;
-            }
-        }
-        __syncthreads();
     }
-    if (threadIdx.x == 0 && it >= 0) {
+    if (it >= 0) {
         int any = 0;
         for (int i = 0; i < B.n; ++i) any |= c->active[i];
         c->active_any = any;
@@ -1245,15 +1235,18 @@ struct FastSmem {
     int blocks[kFastA];
     int pxoff[kFastA + 1];
     int scan[32];
-    short qmap[kFastRegion];
-    uint8_t amap[kFastRegion];
+    short qmap[kFastRegion];  // Q block: its index + 1
+    short amap[kFastRegion];  // block to re-search: its index + 1
     uint16_t rcode[kFastPx];
     float rw[kFastPx];
     float rerr[kFastPx];
     uint32_t hrpx[kFastPx];   // guide colour of every re-searched pixel
     float eold[kFastPx];      // its error before the trial
-    int full[kFastPx];        // pixels that need a full search (see fast_block_pass)
+    uint16_t code0[kFastPx];  // its pair before the trial
+    int full[kFastPx];        // the component's pixels, then the pixels needing a full search
     int nfull;
+    long long wsum[32][2];    // per-warp fixed-point error sums (old, new)
+    int wcnt[32];             // per-warp pixels re-searched
 };
 
 constexpr uint16_t kNotSearched = 0xFFFFu;
@@ -1310,61 +1303,67 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
     const bool use_incr = incr && nchg <= kMaxChg;
     const int ys = bv * I.s, xs = bu * I.s;
     const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
-    for (int jp = lane; jp < ey * ex; jp += 32) {
-        const int y = ys + jp / ex, x = xs + jp % ex;
-        const int64_t lp = (int64_t)y * I.W + x;
-        if (comp >= 0 && __ldcg(&W_.lab[I.p0 + lp]) != comp) {
-            F.rcode[off + jp] = kNotSearched;
-            continue;
-        }
-        const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
-        const uint32_t rgb = (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16);
-        F.hrpx[off + jp] = rgb;
-        F.eold[off + jp] = __ldcg(&I.err[lp]);
-        if (!use_incr) {
-            F.full[atomicAdd(&F.nfull, 1)] = full_entry(off + jp, bi, -1);
-            continue;
-        }
-        const float ir = (float)(rgb & 255u), ig = (float)((rgb >> 8) & 255u),
-                    ib = (float)(rgb >> 16);
-        const int code0 = (int)__ldcg(&I.code[lp]);
-        const int a0 = code0 / K, b0 = code0 % K;
-        bool redo_a = false, redo_b = false;
+    for (int jp0 = 0; jp0 < ey * ex; jp0 += 32) {
+        const int jp = jp0 + lane;
+        // queue decisions of the whole warp go out as one shared atomic per warp
+        int want = -2;   // -2: none; -1: full search; >= 0: step 2 for this a
+        int a = 0, b = 0;
+        float bd = 0.f, ir = 0.f, ig = 0.f, ib = 0.f;
+        float4 ca0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool live = jp < ey * ex && F.rcode[off + jp] != kNotSearched;
+        if (live) {
+            const uint32_t rgb = F.hrpx[off + jp];
+            ir = (float)(rgb & 255u);
+            ig = (float)((rgb >> 8) & 255u);
+            ib = (float)(rgb >> 16);
+            if (!use_incr) {
+                want = -1;
+            } else {
+                const int code0 = (int)F.code0[off + jp];
+                const int a0 = code0 / K, b0 = code0 % K;
+                bool redo_a = false, redo_b = false;
 #pragma unroll
-        for (int t = 0; t < kMaxChg; ++t) {
-            redo_a |= t < nchg && chg[t] == a0;
-            redo_b |= t < nchg && chg[t] == b0;
-        }
-        if (redo_a) {
-            F.full[atomicAdd(&F.nfull, 1)] = full_entry(off + jp, bi, -1);
-            continue;
-        }
-        // step 1 from the previous a: only a replaced pixel can be nearer (ties: lowest k)
-        const float4 ca0 = lds_f4(&win[(a0 / S) * RW + (a0 % S)]);
-        float bd = dist2(ca0.x - ir, ca0.y - ig, ca0.z - ib);
-        int a = a0;
+                for (int t = 0; t < kMaxChg; ++t) {
+                    redo_a |= t < nchg && chg[t] == a0;
+                    redo_b |= t < nchg && chg[t] == b0;
+                }
+                if (redo_a) {
+                    want = -1;
+                } else {
+                    // step 1 from the previous a: only a replaced pixel can be nearer
+                    // (ties: lowest k)
+                    ca0 = lds_f4(&win[(a0 / S) * RW + (a0 % S)]);
+                    bd = dist2(ca0.x - ir, ca0.y - ig, ca0.z - ib);
+                    a = a0;
 #pragma unroll
-        for (int t = 0; t < kMaxChg; ++t) {
-            if (t >= nchg) break;
-            const int k = chg[t];
-            const float4 cc = lds_f4(&win[(k / S) * RW + (k % S)]);
-            const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
-            if (d2 < bd || (d2 == bd && k < a)) {
-                bd = d2;
-                a = k;
+                    for (int t = 0; t < kMaxChg; ++t) {
+                        if (t >= nchg) break;
+                        const int k = chg[t];
+                        const float4 cc = lds_f4(&win[(k / S) * RW + (k % S)]);
+                        const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
+                        if (d2 < bd || (d2 == bd && k < a)) {
+                            bd = d2;
+                            a = k;
+                        }
+                    }
+                    if (a != a0 || redo_b) want = a;
+                    b = b0;
+                }
             }
         }
-        if (a != a0 || redo_b) {
-            F.full[atomicAdd(&F.nfull, 1)] = full_entry(off + jp, bi, a);
-            continue;
+        const unsigned q = __ballot_sync(0xffffffffu, want != -2);
+        if (q) {
+            int base = 0;
+            if (lane == __ffs(q) - 1) base = atomicAdd(&F.nfull, __popc(q));
+            base = __shfl_sync(0xffffffffu, base, __ffs(q) - 1);
+            if (want != -2) F.full[base + __popc(q & ((1u << lane) - 1u))] = full_entry(off + jp, bi, want);
         }
+        if (!live || want != -2) continue;
         // step 2 from the previous b: only a replaced pixel can beat it (ties: lowest k)
-        const float ur = ca0.x - ir, ug = ca0.y - ig, ub = ca0.z - ib;
-        const float dae = sqrt_approx(bd) + B.eps255;
-        const float4 cb0 = lds_f4(&win[(b0 / S) * RW + (b0 % S)]);
+        const StepB sb = step_b_setup(ca0, bd, ir, ig, ib, B.eps255);
+        const float4 cb0 = lds_f4(&win[(b / S) * RW + (b % S)]);
         float vr = cb0.x - ir, vg = cb0.y - ig, vb = cb0.z - ib;
-        float bkey = b_key(sqrt_approx(dist2(vr, vg, vb)), dae, ur, ug, ub, vr, vg, vb);
-        int b = b0;
+        float bkey = b_key(sb, dist2(vr, vg, vb), vr, vg, vb);
 #pragma unroll
         for (int t = 0; t < kMaxChg; ++t) {
             if (t >= nchg) break;
@@ -1373,7 +1372,7 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
             vr = cc.x - ir;
             vg = cc.y - ig;
             vb = cc.z - ib;
-            const float key = b_key(sqrt_approx(dist2(vr, vg, vb)), dae, ur, ug, ub, vr, vg, vb);
+            const float key = b_key(sb, dist2(vr, vg, vb), vr, vg, vb);
             if (key < bkey || (key == bkey && k < b)) {
                 bkey = key;
                 b = k;
@@ -1381,7 +1380,7 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
         }
         SearchOut o;
         o.ka = a;
-        finish_pair(win, RW, S, b, ir, ig, ib, dae, bkey, o);
+        finish_pair(win, RW, S, b, ir, ig, ib, sb.dae, bkey, o);
         F.rcode[off + jp] = (uint16_t)(o.ka * K + o.kb);
         F.rw[off + jp] = o.omega;
         F.rerr[off + jp] = o.err;
@@ -1531,10 +1530,15 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
         const int bv = RV0 + c / RW, bu = RU0 + c % RW;
         F.blocks[k] = c;
         F.pxoff[k] = o;
+        F.amap[c] = (short)(k + 1);
         ++k;
         o += min(I.s, I.H - bv * I.s) * min(I.s, I.W - bu * I.s);
     }
-    // the LR neighbourhood in 1/255 units (zero outside the image: masked by the search)
+    const int ncomp = en.x - st.x;
+    __syncthreads();
+    // one round of loads: the LR neighbourhood in 1/255 units (zero outside the image: masked by
+    // the search), every re-searched pixel's guide colour, error and pair (PAPER: its label),
+    // and the component's pixel list
     for (int t = tid; t < ncell; t += nthr) {
         const int v = RV0 + t / RW, u = RU0 + t % RW;
         float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1544,29 +1548,51 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
         }
         F.region[t] = c4;
     }
+    for (int w0 = warp; w0 < na; w0 += nwarps) {
+        const int c = F.blocks[w0], off = F.pxoff[w0];
+        const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+        const int ys = bv * I.s, xs = bu * I.s;
+        const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
+        for (int jp = (tid & 31); jp < ey * ex; jp += 32) {
+            const int y = ys + jp / ex, x = xs + jp % ex;
+            const int64_t lp = (int64_t)y * I.W + x;
+            const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
+            F.hrpx[off + jp] = (uint32_t)__ldg(ip) | ((uint32_t)__ldg(ip + 1) << 8) |
+                               ((uint32_t)__ldg(ip + 2) << 16);
+            F.eold[off + jp] = __ldcg(&I.err[lp]);
+            F.code0[off + jp] = __ldcg(&I.code[lp]);
+            F.rcode[off + jp] =
+                (B.strict || __ldcg(&W_.lab[I.p0 + lp]) == j) ? (uint16_t)0 : kNotSearched;
+        }
+    }
+    for (int t = tid; t < ncomp; t += nthr) F.full[t] = W_.comp_pix[st.x + t];
     for (int t = tid; t < nq; t += nthr) F.best[t] = 0ull;
     __syncthreads();
     // per q, the component's largest current error in the block (ties: lowest raster index)
-    for (int t = st.x + tid; t < en.x; t += nthr) {
-        const int64_t lp = (int64_t)W_.comp_pix[t] - I.p0;
+    for (int t = tid; t < ncomp; t += nthr) {
+        const int64_t lp = (int64_t)F.full[t] - I.p0;
         const int y = (int)(lp / I.W), x = (int)(lp % I.W);
-        const int qi = F.qmap[(y / I.s - RV0) * RW + (x / I.s - RU0)] - 1;
+        const int cell = (y / I.s - RV0) * RW + (x / I.s - RU0);
+        const int ai = F.amap[cell] - 1;
+        const int ex = min(I.s, I.W - (x / I.s) * I.s);
+        const int pix = F.pxoff[ai] + (y % I.s) * ex + (x % I.s);
         const unsigned long long key =
-            ((unsigned long long)__float_as_uint(__ldcg(&I.err[lp])) << 32) |
+            ((unsigned long long)__float_as_uint(F.eold[pix]) << 32) |
             (unsigned long long)(0xFFFFFFFFu - (uint32_t)lp);
-        atomicMax(&F.best[qi], key);
+        atomicMax(&F.best[F.qmap[cell] - 1], key);
     }
     __syncthreads();
-    // the replacement colours, applied to the staged neighbourhood only
+    // the replacement colours (guide colours of the argmax pixels), applied to the staged
+    // neighbourhood only
     for (int t = tid; t < nq; t += nthr) {
         const uint32_t lp = 0xFFFFFFFFu - (uint32_t)(F.best[t] & 0xFFFFFFFFull);
         const int y = (int)(lp / (uint32_t)I.W), x = (int)(lp % (uint32_t)I.W);
-        const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
-        const uint32_t c = (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16);
+        const int cell = (y / I.s - RV0) * RW + (x / I.s - RU0);
+        const int ex = min(I.s, I.W - (x / I.s) * I.s);
+        const uint32_t c = F.hrpx[F.pxoff[F.amap[cell] - 1] + (y % I.s) * ex + (x % I.s)];
         F.newc[t] = c;
-        const int q = F.qs[t];
-        F.region[(q / I.w - RV0) * RW + (q % I.w - RU0)] =
-            make_float4((float)ip[0], (float)ip[1], (float)ip[2], 0.f);
+        F.region[cell] = make_float4((float)(c & 255u), (float)((c >> 8) & 255u),
+                                     (float)(c >> 16), 0.f);
     }
     __syncthreads();
     GLU_TRACE(X.it, j, 5);
@@ -1602,15 +1628,37 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
     }
     __syncthreads();
     GLU_TRACE(X.it, j, 8);
-    for (int bi = warp; bi < na; bi += nwarps) {
-        float e0, e1;
-        int ns;
-        fast_block_sums(I, F, RW, RV0, RU0, bi, e0, e1, ns);
-        if ((threadIdx.x & 31) == 0 && ns > 0) {
-            atomicAdd(&sh.e0, (unsigned long long)to_fixed(e0));
-            atomicAdd(&sh.e1, (unsigned long long)to_fixed(e1));
-            atomicAdd(&sh.searched, ns);
+    {
+        long long a0 = 0, a1 = 0;
+        int an = 0;
+        for (int bi = warp; bi < na; bi += nwarps) {
+            float e0, e1;
+            int ns;
+            fast_block_sums(I, F, RW, RV0, RU0, bi, e0, e1, ns);
+            if (ns > 0) {
+                a0 += to_fixed(e0);
+                a1 += to_fixed(e1);
+                an += ns;
+            }
         }
+        if ((tid & 31) == 0) {
+            F.wsum[warp][0] = a0;
+            F.wsum[warp][1] = a1;
+            F.wcnt[warp] = an;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long a0 = 0, a1 = 0;
+        int an = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            a0 += F.wsum[w][0];
+            a1 += F.wsum[w][1];
+            an += F.wcnt[w];
+        }
+        sh.e0 = (unsigned long long)a0;
+        sh.e1 = (unsigned long long)a1;
+        sh.searched = an;
     }
     __syncthreads();
     GLU_TRACE(X.it, j, 6);
@@ -1943,32 +1991,69 @@ static int launch_trials(const JBatch& B, const TrialCtx& X, cudaStream_t st) {
 
 // ---------------------------------------------------------------- phase-timing instrumentation
 namespace prof {
-constexpr int kSlots = 64, kMaxEv = 4 + 3 * GLU_MAX_ITERS;
+// Slots 0 .. kSlots-1: calls issued directly; slot kSlots: the events inside the recorded graph
+// (external event nodes, recorded again at every replay; each replay's times are collected
+// before the next replay is launched).
+constexpr int kSlots = 64, kGraphSlot = kSlots, kMaxEv = 4 + 3 * GLU_MAX_ITERS;
 static bool enabled = false;
-static cudaEvent_t ev[kSlots][kMaxEv];
-static int nev[kSlots];
-static int used = 0;           // slots filled since the last read
+static cudaEvent_t ev[kSlots + 1][kMaxEv];
+static int nev[kSlots + 1];
+static int used = 0;           // direct slots filled since the last read
 static bool created = false;
+static bool graph_pending = false;
+static float gacc[5];
+static int gcalls = 0;
 
 static void mark(int slot, int i, cudaStream_t st) {
-    if (slot >= 0) cudaEventRecord(ev[slot][i], st);
+    if (slot < 0) return;
+    if (slot == kGraphSlot) cudaEventRecordWithFlags(ev[slot][i], st, cudaEventRecordExternal);
+    else cudaEventRecord(ev[slot][i], st);
+}
+
+// Phase times of one slot's events: [control init + grid downsample, search, components,
+// trials, residuals].
+static int phase_times(int sl, float ms[5]) {
+    for (int k = 0; k < 5; ++k) ms[k] = 0.f;
+    const int n = nev[sl];
+    if (n < 4) return GLU_ERR_INVALID_ARG;
+    if (cudaEventSynchronize(ev[sl][n - 1]) != cudaSuccess) return GLU_ERR_CUDA;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[sl][0], ev[sl][1]);
+    ms[0] += t;
+    cudaEventElapsedTime(&t, ev[sl][1], ev[sl][2]);
+    ms[1] += t;
+    cudaEventElapsedTime(&t, ev[sl][2], ev[sl][3]);
+    ms[4] += t;
+    // per iteration: [previous end .. components built] [.. trials] [.. residual]
+    for (int i = 3; i + 3 <= n - 1; i += 3) {
+        cudaEventElapsedTime(&t, ev[sl][i], ev[sl][i + 1]);
+        ms[2] += t;
+        cudaEventElapsedTime(&t, ev[sl][i + 1], ev[sl][i + 2]);
+        ms[3] += t;
+        cudaEventElapsedTime(&t, ev[sl][i + 2], ev[sl][i + 3]);
+        ms[4] += t;
+    }
+    return GLU_OK;
+}
+
+// Adds the last graph replay's phase times to the running sums (waits for that replay).
+static int collect_graph() {
+    if (!graph_pending) return GLU_OK;
+    graph_pending = false;
+    float t[5];
+    const int rc = phase_times(kGraphSlot, t);
+    if (rc) return rc;
+    for (int k = 0; k < 5; ++k) gacc[k] += t[k];
+    ++gcalls;
+    return GLU_OK;
 }
 }  // namespace prof
 
-int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, void* wsp,
-                       size_t ws_bytes, glu_joint_stats* stats, cudaStream_t st) {
-    if (n <= 0) return GLU_OK;
-    if (n > kMaxJointBatch) return GLU_ERR_UNSUPPORTED;
-    static std::mutex mu;  // the parameter staging block and the stats copy are shared
-    std::lock_guard<std::mutex> lock(mu);
-    int64_t np, nq, nch;
-    batch_sizes(items, n, &np, &nq, &nch);
-    if (np >= (int64_t)0x7fffffff) return GLU_ERR_UNSUPPORTED;  // 32-bit pixel ids
-    JointWs ws;
-    const size_t need = carve(wsp, np, nq, n, cm.N, nch, &ws);
-    if (ws_bytes < need) return GLU_ERR_WORKSPACE;
-    int slot = -1;
-    if (prof::enabled && prof::used < prof::kSlots) slot = prof::used++;
+// Every launch of one Algorithm 2 call on `st` (phase events into profiling slot `slot`, if
+// >= 0). The sequence depends only on the arguments: iterations after an image's convergence
+// still launch and return at once, so the sequence can be replayed as a CUDA graph.
+static int issue_joint(const JointItem* items, int n, const JointCommon& cm, const JointWs& ws,
+                       int64_t np, int64_t nq, int slot, cudaStream_t st) {
     int evi = 0;
 
     static JBatch B;   // host staging of the parameter block (copied at each launch)
@@ -2026,8 +2111,8 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
     int rc = launch_search_batch(sa, n, st);
     if (rc) return rc;
     prof::mark(slot, evi++, st);
-    k_resid_partial<<<B.nchunks, 256, 0, st>>>(B, ws.partial, ws.ctl);
-    k_resid_final<<<1, 256, 0, st>>>(B, ws.partial, ws.ctl, -1);
+    k_resid_partial<<<B.nchunks, 256, 0, st>>>(B, ws.ctl);
+    k_resid_final<<<1, 32, 0, st>>>(B, ws.ctl, -1);
     GLU_LAUNCH_CHECK();
     prof::mark(slot, evi++, st);
 
@@ -2064,12 +2149,108 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
         rc = launch_trials(B, X, st);
         if (rc) return rc;
         prof::mark(slot, evi++, st);
-        k_resid_partial<<<B.nchunks, 256, 0, st>>>(B, ws.partial, ws.ctl);
-        k_resid_final<<<1, 256, 0, st>>>(B, ws.partial, ws.ctl, it);
+        k_resid_partial<<<B.nchunks, 256, 0, st>>>(B, ws.ctl);
+        k_resid_final<<<1, 32, 0, st>>>(B, ws.ctl, it);
         GLU_LAUNCH_CHECK();
         prof::mark(slot, evi++, st);
     }
     if (slot >= 0) prof::nev[slot] = evi;
+    return GLU_OK;
+}
+
+// One recorded call: the arguments it was recorded for and its executable graph.
+struct JointGraph {
+    bool valid, profiled;
+    int device, n, seen;
+    JointItem items[kMaxJointBatch];
+    JointCommon cm;
+    void* ws;
+    size_t ws_bytes;
+    cudaGraphExec_t exec;
+};
+
+static bool same_call(const JointGraph& g, int device, const JointItem* items, int n,
+                      const JointCommon& cm, void* ws, size_t ws_bytes) {
+    return g.device == device && g.n == n && g.ws == ws && g.ws_bytes == ws_bytes &&
+           memcmp(&g.cm, &cm, sizeof(cm)) == 0 &&
+           memcmp(g.items, items, sizeof(JointItem) * (size_t)n) == 0;
+}
+
+int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, void* wsp,
+                       size_t ws_bytes, glu_joint_stats* stats, cudaStream_t st) {
+    if (n <= 0) return GLU_OK;
+    if (n > kMaxJointBatch) return GLU_ERR_UNSUPPORTED;
+    static std::mutex mu;  // the parameter staging block, the graph cache and the stats copy
+    std::lock_guard<std::mutex> lock(mu);
+    int64_t np, nq, nch;
+    batch_sizes(items, n, &np, &nq, &nch);
+    if (np >= (int64_t)0x7fffffff) return GLU_ERR_UNSUPPORTED;  // 32-bit pixel ids
+    JointWs ws;
+    const size_t need = carve(wsp, np, nq, n, cm.N, nch, &ws);
+    if (ws_bytes < need) return GLU_ERR_WORKSPACE;
+    // Launch gaps dominate the small kernels of late iterations: a call repeated with the same
+    // arguments is recorded as a CUDA graph on its second occurrence (the first runs directly,
+    // so the autotuner can time its kernels) and replayed from then on. Profiling runs directly.
+    JointItem key[kMaxJointBatch];
+    memset(key, 0, sizeof(key));
+    memcpy(key, items, sizeof(JointItem) * (size_t)n);
+    JointCommon ckey;
+    memset(&ckey, 0, sizeof(ckey));
+    ckey = cm;
+    int device = 0;
+    GLU_CUDA_TRY(cudaGetDevice(&device));
+    static JointGraph g = {};
+    int rc = GLU_OK;
+    const bool same = g.valid && g.profiled == prof::enabled &&
+                      same_call(g, device, key, n, ckey, wsp, ws_bytes);
+    if (prof::enabled && (same || g.valid)) {
+        rc = prof::collect_graph();   // the previous replay's phase times
+        if (rc) return rc;
+    }
+    if (same && g.exec) {
+        GLU_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+        if (prof::enabled) prof::graph_pending = true;
+    } else if (same && g.seen >= 1) {
+        static cudaStream_t cap = nullptr;
+        static int cap_device = -1;
+        if (!cap || cap_device != device) {
+            if (cap) cudaStreamDestroy(cap);
+            GLU_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cap_device = device;
+        }
+        cudaGraph_t graph = nullptr;
+        GLU_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+        rc = issue_joint(key, n, ckey, ws, np, nq, prof::enabled ? prof::kGraphSlot : -1, cap);
+        const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (rc == GLU_OK && ec == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+            g.exec = exec;
+            GLU_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+            if (prof::enabled) prof::graph_pending = true;
+        } else {
+            (void)cudaGetLastError();
+            if (rc == GLU_OK) {
+                const int slot = prof::enabled && prof::used < prof::kSlots ? prof::used++ : -1;
+                rc = issue_joint(key, n, ckey, ws, np, nq, slot, st);
+            }
+        }
+        if (graph) cudaGraphDestroy(graph);
+    } else {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = JointGraph{};
+        g.valid = true;
+        g.profiled = prof::enabled;
+        g.device = device;
+        g.n = n;
+        memcpy(g.items, key, sizeof(key));
+        g.cm = ckey;
+        g.ws = wsp;
+        g.ws_bytes = ws_bytes;
+        g.seen = 1;
+        const int slot = prof::enabled && prof::used < prof::kSlots ? prof::used++ : -1;
+        rc = issue_joint(key, n, ckey, ws, np, nq, slot, st);
+    }
+    if (rc) return rc;
     if (stats) {
         static JointCtl h;
         GLU_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -2158,10 +2339,14 @@ extern "C" int glu_dbg_trace(unsigned long long* host, int64_t n) {
 extern "C" int glu_joint_profile(int32_t enable) {
     using namespace glu;
     if (enable && !prof::created) {
-        for (int i = 0; i < prof::kSlots; ++i)
+        for (int i = 0; i <= prof::kSlots; ++i)
             for (int j = 0; j < prof::kMaxEv; ++j)
                 if (cudaEventCreate(&prof::ev[i][j]) != cudaSuccess) return GLU_ERR_CUDA;
         prof::created = true;
+    }
+    if (!enable && prof::enabled) {
+        const int rc = prof::collect_graph();
+        if (rc) return rc;
     }
     prof::enabled = enable != 0;
     return GLU_OK;
@@ -2170,30 +2355,20 @@ extern "C" int glu_joint_profile(int32_t enable) {
 extern "C" int glu_joint_profile_read(float* ms, int32_t* calls) {
     using namespace glu;
     if (!ms || !calls) return GLU_ERR_INVALID_ARG;
-    for (int k = 0; k < 5; ++k) ms[k] = 0.f;
-    *calls = 0;
+    int rc = prof::collect_graph();
+    if (rc) return rc;
+    for (int k = 0; k < 5; ++k) ms[k] = prof::gacc[k];
+    *calls = prof::gcalls;
     for (int sl = 0; sl < prof::used; ++sl) {
-        const int n = prof::nev[sl];
-        if (n < 4) continue;
-        if (cudaEventSynchronize(prof::ev[sl][n - 1]) != cudaSuccess) return GLU_ERR_CUDA;
-        float t = 0.f;
-        cudaEventElapsedTime(&t, prof::ev[sl][0], prof::ev[sl][1]);
-        ms[0] += t;  // control init + grid downsample
-        cudaEventElapsedTime(&t, prof::ev[sl][1], prof::ev[sl][2]);
-        ms[1] += t;  // Algorithm 1 search kernel
-        cudaEventElapsedTime(&t, prof::ev[sl][2], prof::ev[sl][3]);
-        ms[4] += t;  // R_0
-        // per iteration: [previous end .. components built] [.. trials] [.. residual]
-        for (int i = 3; i + 3 <= n - 1; i += 3) {
-            cudaEventElapsedTime(&t, prof::ev[sl][i], prof::ev[sl][i + 1]);
-            ms[2] += t;
-            cudaEventElapsedTime(&t, prof::ev[sl][i + 1], prof::ev[sl][i + 2]);
-            ms[3] += t;
-            cudaEventElapsedTime(&t, prof::ev[sl][i + 2], prof::ev[sl][i + 3]);
-            ms[4] += t;
-        }
+        float t[5];
+        rc = prof::phase_times(sl, t);
+        if (rc == GLU_ERR_INVALID_ARG) continue;
+        if (rc) return rc;
+        for (int k = 0; k < 5; ++k) ms[k] += t[k];
         ++*calls;
     }
     prof::used = 0;
+    prof::gcalls = 0;
+    for (int k = 0; k < 5; ++k) prof::gacc[k] = 0.f;
     return GLU_OK;
 }

@@ -41,16 +41,34 @@ __device__ __forceinline__ float dist2(float er, float eg, float eb) {
 
 // Step-2 key of candidate b for a fixed a: the squared Eq. 3 error in 1/255 units. With the Eq. 5
 // weight w = d_b / (d_a + d_b + eps) and u = L_a - I, v = L_b - I, the residual is
-// r = w u + (1 - w) v = (d_b u + (d_a + eps) v) / D with D = d_a + d_b + eps. One float per
-// candidate, compared exactly, so the candidate order is a total order (ties: lowest k) and a
-// re-search after some candidates change can be done exactly from the previous winner.
-__device__ __forceinline__ float b_key(float db, float dae, float ur, float ug, float ub, float vr,
-                                       float vg, float vb) {
-    const float xr = __fmaf_rn(db, ur, __fmul_rn(dae, vr));
-    const float xg = __fmaf_rn(db, ug, __fmul_rn(dae, vg));
-    const float xb = __fmaf_rn(db, ub, __fmul_rn(dae, vb));
+// r = w u + (1 - w) v = (d_b u + (d_a + eps) v) / D with D = d_a + d_b + eps. v is formed
+// exactly for uint8 colours, so an exactly representable pixel (I = L_a = L_b) gets error 0.
+// One float per candidate, compared exactly, so the candidate order is a total order (ties:
+// lowest k) and a re-search after some candidates change can be done exactly from the previous
+// winner.
+struct StepB {
+    float ur, ug, ub;   // u = L_a - I
+    float dae;          // d_a + eps
+};
+
+__device__ __forceinline__ StepB step_b_setup(float4 ca, float d2a, float ir, float ig, float ib,
+                                              float eps255) {
+    StepB t;
+    t.ur = ca.x - ir;
+    t.ug = ca.y - ig;
+    t.ub = ca.z - ib;
+    t.dae = sqrt_approx(d2a) + eps255;
+    return t;
+}
+
+// d2b = ||L_b - I||^2 (as dist2 computes it), (vr, vg, vb) = L_b - I.
+__device__ __forceinline__ float b_key(const StepB& t, float d2b, float vr, float vg, float vb) {
+    const float db = sqrt_approx(d2b);
+    const float xr = __fmaf_rn(db, t.ur, __fmul_rn(t.dae, vr));
+    const float xg = __fmaf_rn(db, t.ug, __fmul_rn(t.dae, vg));
+    const float xb = __fmaf_rn(db, t.ub, __fmul_rn(t.dae, vb));
     const float num = dist2(xr, xg, xb);
-    const float D = __fadd_rn(db, dae);
+    const float D = __fadd_rn(db, t.dae);
     return __fdividef(num, __fmul_rn(D, D));
 }
 
@@ -72,9 +90,7 @@ __device__ __forceinline__ SearchOut step_b(const float4* __restrict__ win, int 
                                             uint32_t rowmask, uint32_t colmask, int a, float d2a,
                                             float ir, float ig, float ib, float eps255) {
     constexpr int kRowUnroll = (kCompact || S > 5) ? 1 : S;
-    const float4 ca = lds_f4(&win[(a / S) * rs + (a % S)]);
-    const float ur = ca.x - ir, ug = ca.y - ig, ub = ca.z - ib;
-    const float dae = sqrt_approx(d2a) + eps255;
+    const StepB t = step_b_setup(lds_f4(&win[(a / S) * rs + (a % S)]), d2a, ir, ig, ib, eps255);
     float bkey = kInf;
     int b = a;
 #pragma unroll(kRowUnroll)
@@ -84,7 +100,7 @@ __device__ __forceinline__ SearchOut step_b(const float4* __restrict__ win, int 
             const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
             const float4 c = lds_f4(&win[dy * rs + dx]);
             const float vr = c.x - ir, vg = c.y - ig, vb = c.z - ib;
-            const float key = b_key(sqrt_approx(dist2(vr, vg, vb)), dae, ur, ug, ub, vr, vg, vb);
+            const float key = b_key(t, dist2(vr, vg, vb), vr, vg, vb);
             if (ok && key < bkey) {
                 bkey = key;
                 b = dy * S + dx;
@@ -93,7 +109,7 @@ __device__ __forceinline__ SearchOut step_b(const float4* __restrict__ win, int 
     }
     SearchOut o;
     o.ka = a;
-    finish_pair(win, rs, S, b, ir, ig, ib, dae, bkey, o);
+    finish_pair(win, rs, S, b, ir, ig, ib, t.dae, bkey, o);
     return o;
 }
 

@@ -12,13 +12,13 @@ struct SearchVariant {
     int tile_h, min_blocks, compact;
 };
 constexpr SearchVariant kSearchVariants[] = {
-    {16, 3, 0}, {16, 2, 0}, {8, 2, 0}, {32, 2, 0}, {16, 4, 1},
+    {32, 2, 0}, {16, 2, 0}, {8, 2, 0}, {16, 3, 0}, {16, 4, 1},
 };
 constexpr int kNumSearchVariants = (int)(sizeof(kSearchVariants) / sizeof(kSearchVariants[0]));
 
 // Eq. 1 apply, 3-channel float targets: rows of the 128-pixel-wide tiles.
 constexpr int kApplyTW = 128;
-constexpr int kApplyVariantRows[] = {8, 4, 16};
+constexpr int kApplyVariantRows[] = {16, 8, 32, 64};
 constexpr int kNumApplyVariants = (int)(sizeof(kApplyVariantRows) / sizeof(kApplyVariantRows[0]));
 
 }  // namespace glu

@@ -1387,10 +1387,26 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
     }
 }
 
-// One queued full search (entry from fast_block_pass).
+// One queued full search (entry from fast_block_pass), by a team of kTeam consecutive lanes: each
+// lane scans every kTeam-th window candidate and the team reduces (value, k) lexicographically,
+// which is exactly the first minimum the sequential scan finds (values compare exactly).
+constexpr int kTeam = 4;
+
+__device__ __forceinline__ void team_min(float& v, int& k, unsigned mask) {
+#pragma unroll
+    for (int o = 1; o < kTeam; o <<= 1) {
+        const float ov = __shfl_xor_sync(mask, v, o);
+        const int ok = __shfl_xor_sync(mask, k, o);
+        if (ov < v || (ov == v && ok < k)) {
+            v = ov;
+            k = ok;
+        }
+    }
+}
+
 template <int S>
 __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, FastSmem& F, int RW,
-                                              int RV0, int RU0, int e) {
+                                              int RV0, int RU0, int e, int tl, unsigned mask) {
     constexpr int r = (S - 1) / 2, K = S * S;
     const int pix = e & 0xFFF, bi = (e >> 12) & 0xFF, a_known = (e >> 20) - 1;
     const int c = F.blocks[bi];
@@ -1400,17 +1416,53 @@ __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, Fa
     const float4* win = &F.region[(bv - r - RV0) * RW + (bu - r - RU0)];
     const uint32_t rgb = F.hrpx[pix];
     const float ir = (float)(rgb & 255u), ig = (float)((rgb >> 8) & 255u), ib = (float)(rgb >> 16);
-    SearchOut o;
-    if (a_known >= 0) {
-        const float4 ca = lds_f4(&win[(a_known / S) * RW + (a_known % S)]);
-        o = step_b<S, true, false>(win, RW, rm, cm, a_known,
-                                   dist2(ca.x - ir, ca.y - ig, ca.z - ib), ir, ig, ib, B.eps255);
+    // step 1 (unless the entry carries a): the nearest colour, ties to the lowest k
+    int a = a_known;
+    float d2a;
+    if (a < 0) {
+        float bd = kInf;
+        int ba = K;
+        for (int k = tl; k < K; k += kTeam) {
+            const int dy = k / S, dx = k % S;
+            if (!((rm >> dy) & (cm >> dx) & 1u)) continue;
+            const float4 cc = lds_f4(&win[dy * RW + dx]);
+            const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
+            if (d2 < bd) {
+                bd = d2;
+                ba = k;
+            }
+        }
+        team_min(bd, ba, mask);
+        a = ba;
+        d2a = bd;
     } else {
-        o = search_pixel<S, true>(win, RW, rm, cm, ir, ig, ib, B.eps255, false);
+        const float4 ca = lds_f4(&win[(a / S) * RW + (a % S)]);
+        d2a = dist2(ca.x - ir, ca.y - ig, ca.z - ib);
     }
-    F.rcode[pix] = (uint16_t)(o.ka * K + o.kb);
-    F.rw[pix] = o.omega;
-    F.rerr[pix] = o.err;
+    // step 2: b minimising the key, ties to the lowest k
+    const StepB sb = step_b_setup(lds_f4(&win[(a / S) * RW + (a % S)]), d2a, ir, ig, ib, B.eps255);
+    float bkey = kInf;
+    int b = K;
+    for (int k = tl; k < K; k += kTeam) {
+        const int dy = k / S, dx = k % S;
+        if (!((rm >> dy) & (cm >> dx) & 1u)) continue;
+        const float4 cc = lds_f4(&win[dy * RW + dx]);
+        const float vr = cc.x - ir, vg = cc.y - ig, vb = cc.z - ib;
+        const float key = b_key(sb, dist2(vr, vg, vb), vr, vg, vb);
+        if (key < bkey) {
+            bkey = key;
+            b = k;
+        }
+    }
+    team_min(bkey, b, mask);
+    if (tl == 0) {
+        SearchOut o;
+        o.ka = a;
+        finish_pair(win, RW, S, b, ir, ig, ib, sb.dae, bkey, o);
+        F.rcode[pix] = (uint16_t)(o.ka * K + o.kb);
+        F.rw[pix] = o.omega;
+        F.rerr[pix] = o.err;
+    }
 }
 
 // Block bi's old and new error sums (fixed order) and the number of pixels re-searched.
@@ -1616,14 +1668,18 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
 #ifdef GLU_TRIAL_TRACE
     if (tid == 0 && j < kTraceMax) g_trace[X.it][j][9] = (unsigned long long)nfull;
 #endif
-    for (int t = tid; t < nfull; t += nthr) {
-        const int e = F.full[t];
-        switch (I.S) {
-            case 1: fast_full_search<1>(B, I, F, RW, RV0, RU0, e); break;
-            case 3: fast_full_search<3>(B, I, F, RW, RV0, RU0, e); break;
-            case 5: fast_full_search<5>(B, I, F, RW, RV0, RU0, e); break;
-            case 7: fast_full_search<7>(B, I, F, RW, RV0, RU0, e); break;
-            default: fast_full_search<9>(B, I, F, RW, RV0, RU0, e); break;
+    {
+        const int tl = tid % kTeam;
+        const unsigned mask = ((1u << kTeam) - 1u) << ((tid & 31) - tl);
+        for (int t = tid / kTeam; t < nfull; t += nthr / kTeam) {
+            const int e = F.full[t];
+            switch (I.S) {
+                case 1: fast_full_search<1>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
+                case 3: fast_full_search<3>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
+                case 5: fast_full_search<5>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
+                case 7: fast_full_search<7>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
+                default: fast_full_search<9>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
+            }
         }
     }
     __syncthreads();
@@ -1743,7 +1799,8 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
         store_rgb(I.lr, I.lr_pitch, qv, qu,
                   (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16));
     }
-    __threadfence();
+    // visible to this CTA after the barrier, and to helpers through the fence thread 0 issues
+    // before it publishes the task (cumulative over what the barrier ordered before it)
     __syncthreads();
     // trial: Algorithm 1 again on the affected pixels (STRICT: every block within r of Q; PAPER:
     // the component's own pixels), in place, summing e0 and e1
@@ -1778,7 +1835,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     FastSmem& F = *reinterpret_cast<FastSmem*>(dyn_smem);
     __shared__ float4 wins[kTrialThreads / 32][kSmax * kSmax];
-    __shared__ int s_j, s_idx, s_nu, s_accept, s_flag, s_npend, s_povf;
+    __shared__ int s_j, s_idx, s_nu, s_accept, s_flag, s_npend, s_povf, s_next;
     __shared__ int s_pend[kPend];
     __shared__ unsigned long long s_e0, s_e1;
     __shared__ FastShared sh;
@@ -1790,10 +1847,13 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
     const unsigned long long t0 = now_ns();
     const bool dag = *(volatile int*)&ctl->dag_bad[X.it] == 0;
     bool stop = false;
+    int next = -1;   // a successor this CTA made ready itself: tried next, without the queue
 
     while (!stop) {
         int j;
-        if (dag) {
+        if (dag && next >= 0) {
+            j = next;
+        } else if (dag) {
             if (tid == 0) {
                 s_idx = atomicAdd(&ctl->head[X.it], 1);
                 s_flag = 0;
@@ -1801,12 +1861,27 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
             __syncthreads();
             const int idx = s_idx;
             if (idx >= M) break;
-            // wait for the component published at this position, helping meanwhile
+            // wait for the component published at this position, helping meanwhile: thread 0
+            // polls closely while no large trial has items open, then the CTA helps a round
             int hint = -1;
             for (;;) {
-                if (tid == 0) s_j = ld_acquire(&W_.queue[idx]);
+                if (tid == 0) {
+                    int v = -1;
+                    for (int k = 0; k < 64; ++k) {
+                        v = ld_acquire(&W_.queue[idx]);
+                        if (v >= 0 || *(volatile const int*)&ctl->open_tasks > 0) break;
+                        // components taken by continuation never pass through the queue: a
+                        // position can stay empty, and every component may already be done
+                        if (*(volatile const int*)&ctl->finished[X.it] >= M) {
+                            v = -2;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    s_j = v;
+                }
                 __syncthreads();
-                if (s_j >= 0) break;
+                if (s_j >= 0 || s_j == -2) break;
                 if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
                 if (__syncthreads_or(warp_should_abort(ctl, t0) ? 1 : 0)) {
                     if (tid == 0) s_flag = 1;
@@ -1821,6 +1896,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                 }
                 break;
             }
+            if (s_j == -2) break;
             j = s_j;
         } else {
             if (tid == 0) {
@@ -1896,7 +1972,6 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                 continue;
             }
         }
-        __threadfence();
         GLU_TRACE(X.it, j, 1);
         const int2 st = W_.start[j], en = W_.start[j + 1];
         const int img = img_of_p(B, W_.roots[j]);
@@ -1909,10 +1984,11 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                            t0);
         if (tid == 0) s_accept = accept;
         GLU_TRACE(X.it, j, 2);
-        // the outcome is visible before any successor can start
-        __threadfence();
+        // the outcome is visible before any successor can start: every write precedes the
+        // barrier, and each thread that publishes (a successor, the done flag) fences after it
         __syncthreads();
         if (tid == 0) {
+            __threadfence();
             if (!ok) {
                 set_status(GLU_ERR_TIMEOUT);
                 atomicExch(&ctl->timeout, 1);
@@ -1922,14 +1998,21 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
             else atomicAdd(&ctl->rolled[img][X.it], 1);
         }
         if (dag) {
+            if (tid == 0) s_next = -1;
+            __syncthreads();
             const int s0 = W_.dag_start[j].x, s1 = W_.dag_start[j + 1].x;
             for (int k = s0 + tid; k < s1; k += kTrialThreads) {
                 const int sj = W_.succ[k];
+                __threadfence();   // release: this CTA's writes before the count drops
                 if (atomicSub(&W_.pend[sj], 1) == 1) {
                     GLU_TRACE_ANY(X.it, sj, 0);   // the time it became ready
-                    __threadfence();
-                    const int pos = atomicAdd(&ctl->tail[X.it], 1);
-                    st_release(&W_.queue[pos], sj);
+                    __threadfence();   // acquire: the other predecessors' writes
+                    // the first successor this CTA made ready is tried here next; the others
+                    // go to the queue
+                    if (atomicCAS(&s_next, -1, sj) != -1) {
+                        const int pos = atomicAdd(&ctl->tail[X.it], 1);
+                        st_release(&W_.queue[pos], sj);
+                    }
                 }
             }
         }
@@ -1940,6 +2023,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
         GLU_TRACE(X.it, j, 3);
         if (!ok) stop = true;
         __syncthreads();
+        next = dag ? s_next : -1;
     }
     // no component left to take: help the running ones until every component is done
     // (per warp; lane 0 decides)

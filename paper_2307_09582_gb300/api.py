@@ -379,9 +379,9 @@ def glu_joint_profile_read() -> dict:
 def joint_launches(N: int) -> int:
     """Kernel launches one glu_joint_optimize call makes (iterations after convergence still
     launch and return at once): control init, grid downsample, search, R_0 (2), then per
-    iteration threshold, merge, flatten, 3 root-compaction, count, 3 scan, fill, 5 for the
-    trials' dependency graph, trials and the residual (2)."""
-    return 5 + 19 * N
+    iteration threshold, the large-error list (scan, scatter), merge, flatten, 3 root-compaction,
+    count, 3 scan, fill, 5 for the trials' dependency graph, trials and the residual (2)."""
+    return 5 + 21 * N
 
 
 def tune_mode(on: bool) -> None:

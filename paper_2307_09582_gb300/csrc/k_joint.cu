@@ -75,6 +75,7 @@ struct JointCtl {
     int active_any;
     int timeout;
     int M_cur;
+    int nfg;          // large-error pixels of the current iteration (all active images)
     int open_tasks;
     int claim[GLU_MAX_ITERS];
     int finished[GLU_MAX_ITERS];
@@ -372,23 +373,71 @@ __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int
 
 // ----------------------------------------------------------------------- threshold and CCL
 
-// Large-error set of the active images and union-find init; clears the owner slots.
+// Large-error set of the active images and union-find init; clears the owner slots. A CTA per
+// tile of kScanTile pixels also counts the tile's large-error pixels for their ordered
+// compaction.
 __global__ void k_threshold(const __grid_constant__ JBatch B, int* lab, int* own, uint8_t* ovf,
-                            JointCtl* c, int it) {
+                            int* tile_cnt, JointCtl* c, int it) {
     if (!any_active(c)) return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < B.np; p += stride) {
+    __shared__ int wsum[8];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int local = 0, run_img = -1, run = 0;
+    for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+        const int64_t p = base + k;
+        if (p >= B.np) break;
         const int i = img_of_p(B, p);
         bool fg = false;
         if (c->active[i]) fg = B.im[i].err[p - B.im[i].p0] > B.tau;
         lab[p] = fg ? (int)p : -1;
-        if (fg) atomicAdd(&c->n_large[i][it], 1);
+        if (fg) {
+            if (i != run_img) {
+                if (run) atomicAdd(&c->n_large[run_img][it], run);
+                run_img = i;
+                run = 0;
+            }
+            ++run;
+            ++local;
+        }
     }
+    if (run) atomicAdd(&c->n_large[run_img][it], run);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < 8; ++w) t += wsum[w];
+        tile_cnt[blockIdx.x] = t;
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < B.nq; q += stride) {
 #pragma unroll
         for (int k = 0; k < kOwnSlots; ++k) own[q * kOwnSlots + k] = -1;
         ovf[q] = 0;
     }
+}
+
+// The large-error pixels in raster (global index) order: fgl[0 .. nfg). Later passes of the
+// iteration visit only them.
+__global__ void k_fg_scatter(const int* lab, int64_t np, const int* tile_off, int* fgl,
+                             const JointCtl* c) {
+    if (!any_active(c)) return;
+    __shared__ int wsm[8];
+    constexpr int per = kScanTile / kScanThreads;
+    const int64_t my = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * per;
+    int flags = 0, cntl = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        const bool f = my + k < np && lab[my + k] >= 0;
+        flags |= (int)f << k;
+        cntl += f;
+    }
+    int ex;
+    (void)block_excl_scan(cntl, &ex, wsm);
+    int o = tile_off[blockIdx.x] + ex;
+#pragma unroll
+    for (int k = 0; k < per; ++k)
+        if ((flags >> k) & 1) fgl[o++] = (int)(my + k);
 }
 
 // Root of x with path halving; parents only ever decrease (parent < child).
@@ -419,11 +468,12 @@ __device__ __forceinline__ void uf_union(int* par, int a, int b) {
     }
 }
 
-__global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const JointCtl* c) {
+__global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const int* fgl,
+                            const JointCtl* c) {
     if (!any_active(c)) return;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < B.np;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        if (__ldcg(&lab[p]) < 0) continue;
+    const int nfg = c->nfg;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nfg; e += gridDim.x * blockDim.x) {
+        const int64_t p = fgl[e];
         const JImg& I = B.im[img_of_p(B, p)];
         const int64_t lp = p - I.p0;
         const int y = (int)(lp / I.W), x = (int)(lp % I.W);
@@ -440,25 +490,32 @@ __global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const Jo
     }
 }
 
-__global__ void k_ccl_flatten(int* lab, int64_t n, const JointCtl* c) {
+__global__ void k_ccl_flatten(int* lab, const int* fgl, const JointCtl* c) {
     if (!any_active(c)) return;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        if (__ldcg(&lab[p]) >= 0) lab[p] = uf_find(lab, (int)p);
+    const int nfg = c->nfg;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nfg; e += gridDim.x * blockDim.x) {
+        const int p = fgl[e];
+        lab[p] = uf_find(lab, p);
     }
 }
 
 // -------------------------------------------------------------- roots: ordered compaction
 
-// per-tile root counts (a root is a labelled pixel that is its own parent)
-__global__ void k_root_count(const int* lab, int64_t n, int* tile_cnt, const JointCtl* c) {
+// per-tile root counts over the large-error list (a root is a pixel that is its own parent)
+__global__ void k_root_count(const int* lab, const int* fgl, int* tile_cnt, const JointCtl* c) {
     if (!any_active(c)) return;
     __shared__ int wsum[8];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    const int nfg = c->nfg;
+    const int base = blockIdx.x * kScanTile;
     int local = 0;
-    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
-        const int64_t p = base + i;
-        if (p < n && lab[p] == (int)p) ++local;
+    if (base < nfg) {
+        for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+            const int e = base + i;
+            if (e < nfg) {
+                const int p = fgl[e];
+                if (lab[p] == p) ++local;
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
@@ -471,8 +528,10 @@ __global__ void k_root_count(const int* lab, int64_t n, int* tile_cnt, const Joi
     }
 }
 
-// single-CTA exclusive scan of tile counts in place; the total becomes M
-__global__ void k_root_scan(int* tile_cnt, int ntiles, JointCtl* c) {
+// single-CTA exclusive scan of tile counts in place; the total becomes nfg (OUT = 0) or M
+// (OUT = 1); an empty large-error set stops every image
+template <int OUT>
+__global__ void k_tile_scan(int* tile_cnt, int ntiles, JointCtl* c) {
     if (!any_active(c)) return;
     __shared__ int wsm[8];
     int carry = 0;
@@ -485,28 +544,34 @@ __global__ void k_root_scan(int* tile_cnt, int ntiles, JointCtl* c) {
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        c->M_cur = carry;
+        if (OUT == 0) c->nfg = carry;
+        else c->M_cur = carry;
         if (carry == 0) c->active_any = 0;  // every large-error set is empty: all images stop
     }
 }
 
 // scatter roots in global order; component j's per-iteration state is cleared here
-__global__ void k_root_scatter(const __grid_constant__ JBatch B, const int* lab,
+__global__ void k_root_scatter(const __grid_constant__ JBatch B, const int* lab, const int* fgl,
                                const int* tile_off, int* roots, int2* cnt, int2* fill, int* done,
                                int2* dag_cnt, int* dag_fill, int* queue, JointCtl* c, int it) {
     if (!any_active(c)) return;
     __shared__ int wsm[8];
-    const int64_t n = B.np;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int off = tile_off[blockIdx.x];
+    const int nfg = c->nfg;
+    const int base = blockIdx.x * kScanTile;
+    if (base >= nfg) return;   // uniform across the CTA
+    const int off = tile_off[blockIdx.x];
     // 16 consecutive elements per thread keep the order inside the tile
-    const int per = kScanTile / kScanThreads;
-    const int64_t my = base + (int64_t)threadIdx.x * per;
+    constexpr int per = kScanTile / kScanThreads;
+    const int my = base + threadIdx.x * per;
     int flags = 0, cntl = 0;
 #pragma unroll
     for (int k = 0; k < per; ++k) {
-        const int64_t p = my + k;
-        const bool r = p < n && lab[p] == (int)p;
+        const int e = my + k;
+        bool r = false;
+        if (e < nfg) {
+            const int p = fgl[e];
+            r = lab[p] == p;
+        }
         flags |= (int)r << k;
         cntl += r;
     }
@@ -516,14 +581,15 @@ __global__ void k_root_scatter(const __grid_constant__ JBatch B, const int* lab,
 #pragma unroll
     for (int k = 0; k < per; ++k) {
         if ((flags >> k) & 1) {
-            roots[j] = (int)(my + k);
+            const int p = fgl[my + k];
+            roots[j] = p;
             cnt[j] = make_int2(0, 0);
             fill[j] = make_int2(0, 0);
             done[j] = 0;
             dag_cnt[j] = make_int2(0, 0);
             dag_fill[j] = 0;
             queue[j] = -1;
-            atomicAdd(&c->M[img_of_p(B, my + k)][it], 1);
+            atomicAdd(&c->M[img_of_p(B, p)][it], 1);
             ++j;
         }
     }
@@ -542,14 +608,14 @@ __device__ __forceinline__ int lower_bound_i(const int* a, int n, int key) {
 
 // pixel -> component id (lab rewritten in place); counts of pixels and of distinct LR blocks;
 // owner slots of each LR block list the components touching it.
-__global__ void k_comp_count(const __grid_constant__ JBatch B, int* lab, const int* roots,
-                             int2* cnt, int* own, uint8_t* ovf, uint8_t* qflag, const JointCtl* c) {
+__global__ void k_comp_count(const __grid_constant__ JBatch B, int* lab, const int* fgl,
+                             const int* roots, int2* cnt, int* own, uint8_t* ovf, uint8_t* qflag,
+                             const JointCtl* c) {
     if (!any_active(c)) return;
-    const int M = c->M_cur;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < B.np;
-         p += (int64_t)gridDim.x * blockDim.x) {
+    const int M = c->M_cur, nfg = c->nfg;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nfg; e += gridDim.x * blockDim.x) {
+        const int64_t p = fgl[e];
         const int root = lab[p];
-        if (root < 0) continue;
         const int j = lower_bound_i(roots, M, root);
         lab[p] = j;
         atomicAdd(&cnt[j].x, 1);
@@ -643,14 +709,14 @@ __global__ void k_comp_scan(const int2* cnt, const int2* tile_off, int2* start, 
     }
 }
 
-__global__ void k_comp_fill(const __grid_constant__ JBatch B, const int* lab,
+__global__ void k_comp_fill(const __grid_constant__ JBatch B, const int* lab, const int* fgl,
                             const uint8_t* qflag, const int2* start, int2* fill, int* comp_pix,
                             int* qlist, const JointCtl* c) {
     if (!any_active(c)) return;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < B.np;
-         p += (int64_t)gridDim.x * blockDim.x) {
+    const int nfg = c->nfg;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nfg; e += gridDim.x * blockDim.x) {
+        const int64_t p = fgl[e];
         const int j = lab[p];
-        if (j < 0) continue;
         const int pos = atomicAdd(&fill[j].x, 1);
         comp_pix[start[j].x + pos] = (int)p;
         if (qflag[p]) {
@@ -714,14 +780,20 @@ __device__ __forceinline__ void bitonic_sort_smem(int* a, int n2) {
 }
 
 // PASS 0: pend[j] and successor counts. PASS 1: successor lists, and the components without
-// predecessors enter the ready queue. Both passes enumerate the same set.
+// predecessors enter the ready queue. Both passes enumerate the same set. Distinct predecessors
+// come from a shared-memory bitmap over component indices (one atomicOr per candidate) when
+// M <= kDepsBits, else from a sorted candidate list.
+constexpr int kDepsBits = 1 << 16;
+
 template <int PASS>
 __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
     JointCtl* c = W.ctl;
     if (!any_active(c)) return;
     __shared__ int cand[kCandMax];
-    __shared__ int s_n, s_cnt, s_bad;
+    __shared__ unsigned bits[kDepsBits / 32];
+    __shared__ int s_n, s_bad;
     const int M = c->M_cur;
+    const bool use_bits = M <= kDepsBits;
     if (PASS == 1) {
         if (threadIdx.x == 0) {
             s_bad = *(volatile int*)&c->dag_bad[it];
@@ -733,11 +805,10 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
         __syncthreads();
         if (s_bad) return;
     }
+    if (use_bits)
+        for (int t = threadIdx.x; t < (M + 31) / 32; t += blockDim.x) bits[t] = 0u;
     for (int j = blockIdx.x; j < M; j += gridDim.x) {
-        if (threadIdx.x == 0) {
-            s_n = 0;
-            s_cnt = 0;
-        }
+        if (threadIdx.x == 0) s_n = 0;
         __syncthreads();
         const int2 st = W.start[j], en = W.start[j + 1];
         const JImg& I = B.im[img_of_p(B, W.roots[j])];
@@ -745,6 +816,24 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
         const int D = B.strict ? 2 * r : r;
         const int ND = (2 * D + 1) * (2 * D + 1);
         const int npairs = (en.y - st.y) * ND;
+        // one candidate predecessor i < j: with the bitmap, the first sighting emits it
+        auto offer = [&](int i) {
+            if (use_bits) {
+                const unsigned bit = 1u << (i & 31);
+                if (atomicOr(&bits[i >> 5], bit) & bit) return;
+                const int slot = atomicAdd(&s_n, 1);
+                if (slot < kCandMax) cand[slot] = i;
+                if (PASS == 0) {
+                    atomicAdd(&W.dag_cnt[i].x, 1);
+                } else {
+                    const int pos = atomicAdd(&W.dag_fill[i], 1);
+                    W.succ[W.dag_start[i].x + pos] = j;
+                }
+            } else {
+                const int slot = atomicAdd(&s_n, 1);
+                if (slot < kCandMax) cand[slot] = i;
+            }
+        };
         for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
             const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
             const int nb = t % ND;
@@ -760,8 +849,7 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 for (int k = 0; k < ey * ex; ++k) {
                     const int i = W.lab[I.p0 + (int64_t)(ys + k / ex) * I.W + xs + k % ex];
                     if (i >= 0 && i < j && i != last) {
-                        const int slot = atomicAdd(&s_n, 1);
-                        if (slot < kCandMax) cand[slot] = i;
+                        offer(i);
                         last = i;
                     }
                 }
@@ -769,46 +857,58 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 for (int k = 0; k < kOwnSlots; ++k) {
                     const int i = W.own[b * kOwnSlots + k];
                     if (i < 0) break;
-                    if (i < j) {
-                        const int slot = atomicAdd(&s_n, 1);
-                        if (slot < kCandMax) cand[slot] = i;
-                    }
+                    if (i < j) offer(i);
                 }
             }
         }
         __syncthreads();
         const int n = s_n;
-        if (n > kCandMax) {
-            if (threadIdx.x == 0) atomicExch(&c->dag_bad[it], 1);
-            __syncthreads();
-            continue;
-        }
-        int n2 = 1;
-        while (n2 < n) n2 <<= 1;
-        for (int t = n + threadIdx.x; t < n2; t += blockDim.x) cand[t] = 0x7fffffff;
-        __syncthreads();
-        if (n > 1) bitonic_sort_smem(cand, n2);
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            const int i = cand[t];
-            if (t > 0 && cand[t - 1] == i) continue;   // distinct predecessors only
-            if (PASS == 0) {
-                atomicAdd(&W.dag_cnt[i].x, 1);
-                atomicAdd(&s_cnt, 1);
+        int npred;
+        if (use_bits) {
+            npred = n;
+            // clear the bits this component set (every set bit is one of its predecessors)
+            if (n <= kCandMax) {
+                for (int t = threadIdx.x; t < n; t += blockDim.x) bits[cand[t] >> 5] = 0u;
             } else {
-                const int pos = atomicAdd(&W.dag_fill[i], 1);
-                W.succ[W.dag_start[i].x + pos] = j;
+                for (int t = threadIdx.x; t < (M + 31) / 32; t += blockDim.x) bits[t] = 0u;
             }
+        } else {
+            if (n > kCandMax) {
+                if (threadIdx.x == 0) atomicExch(&c->dag_bad[it], 1);
+                __syncthreads();
+                continue;
+            }
+            int n2 = 1;
+            while (n2 < n) n2 <<= 1;
+            for (int t = n + threadIdx.x; t < n2; t += blockDim.x) cand[t] = 0x7fffffff;
+            __syncthreads();
+            if (n > 1) bitonic_sort_smem(cand, n2);
+            if (threadIdx.x == 0) s_n = 0;
+            __syncthreads();
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                const int i = cand[t];
+                if (t > 0 && cand[t - 1] == i) continue;   // distinct predecessors only
+                atomicAdd(&s_n, 1);
+                if (PASS == 0) {
+                    atomicAdd(&W.dag_cnt[i].x, 1);
+                } else {
+                    const int pos = atomicAdd(&W.dag_fill[i], 1);
+                    W.succ[W.dag_start[i].x + pos] = j;
+                }
+            }
+            __syncthreads();
+            npred = s_n;
         }
-        __syncthreads();
         if (threadIdx.x == 0) {
             if (PASS == 0) {
-                W.pend[j] = s_cnt;
+                W.pend[j] = npred;
             } else if (W.pend[j] == 0) {
                 const int pos = atomicAdd(&c->tail[it], 1);
                 W.queue[pos] = j;
                 GLU_TRACE_ANY(it, j, 0);
             }
         }
+        __syncthreads();
     }
 }
 
@@ -862,6 +962,39 @@ __device__ __forceinline__ float load_weight_cg(const void* base, int fmt, int64
     if (fmt == GLU_W_F16) return __half2float(__ldcg((const __half*)base + i));
     return (float)__ldcg((const unsigned short*)base + i) * (1.0f / 65535.0f);
 }
+
+// Shared-memory limits of the one-CTA trial path (below) and its layout.
+constexpr int kFastQRaw = 512;    // LR block entries of the component (before removing repeats)
+constexpr int kFastQ = 64;        // distinct LR blocks of the component
+constexpr int kFastA = 256;       // blocks re-searched
+constexpr int kFastPx = 4096;     // pixels re-searched
+constexpr int kFastRegion = 2304; // LR pixels of the staged neighbourhood
+
+struct FastSmem {
+    float4 region[kFastRegion];
+    unsigned long long best[kFastQ];
+    int rawq[kFastQRaw];
+    int qs[kFastQ];
+    uint32_t newc[kFastQ];
+    int blocks[kFastA];
+    int pxoff[kFastA + 1];
+    int scan[32];
+    short qmap[kFastRegion];  // Q block: its index + 1
+    short amap[kFastRegion];  // block to re-search: its index + 1
+    uint16_t rcode[kFastPx];
+    float rw[kFastPx];
+    float rerr[kFastPx];
+    uint32_t hrpx[kFastPx];   // guide colour of every re-searched pixel
+    float eold[kFastPx];      // its error before the trial
+    uint16_t code0[kFastPx];  // its pair before the trial
+    int full[kFastPx];        // the component's pixels, then the pixels needing a full search
+    int nfull;
+    long long wsum[32][2];    // per-warp fixed-point error sums (old, new)
+    int wcnt[32];             // per-warp pixels re-searched
+};
+
+constexpr uint16_t kNotSearched = 0xFFFFu;
+constexpr int kMaxChg = 8;       // replaced LR pixels per window for the exact re-search
 
 // One warp re-runs Algorithm 1 on the HR pixels of LR block (bv, bu) of image I against the
 // current LR image (comp >= 0: only the pixels of that component), writing the results in place
@@ -964,7 +1097,7 @@ __device__ __forceinline__ unsigned long long trial_tag(int it, int j, int phase
 // One warp processes item t of component j of image img: claims its block (STRICT blocks reached
 // from several q are processed once), then runs the trial (kind 0, sums returned) or the
 // rollback (kind 1).
-__device__ __forceinline__ bool process_item(const JBatch& B, const TrialCtx& X, float4* win,
+__device__ __noinline__ bool process_item(const JBatch& B, const TrialCtx& X, float4* win,
                                              int j, int img, int stY, int kind, int t, float& e0,
                                              float& e1) {
     const int lane = threadIdx.x & 31;
@@ -1042,7 +1175,7 @@ __device__ __forceinline__ bool slot_has_items(const JointWs& W_, int k) {
 // Claiming is one fetch-and-add on the slot's (epoch << 32 | next) word. An increment that lands
 // on a closed slot is harmless (opening overwrites the word); one that lands on an open epoch
 // owns item `next` of that epoch, whose context cannot change before that item is finished.
-__device__ bool help_one(const JBatch& B, const TrialCtx& X, float4* win, int own, int G,
+__device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4* win, int own, int G,
                          int& hint) {
     const JointWs& W_ = X.ws;
     const int lane = threadIdx.x & 31;
@@ -1220,36 +1353,6 @@ __device__ __forceinline__ int block_excl_scan_any(int v, int* out_excl, int* sm
 // rolled-back trial writes nothing, so the global state never holds a rejected trial. The
 // arithmetic and the summation order (per block: Kahan per lane over the block's pixels in raster
 // order, then a butterfly; blocks summed in fixed point) are those of the general path below.
-constexpr int kFastQRaw = 512;    // LR block entries of the component (before removing repeats)
-constexpr int kFastQ = 64;        // distinct LR blocks of the component
-constexpr int kFastA = 256;       // blocks re-searched
-constexpr int kFastPx = 4096;     // pixels re-searched
-constexpr int kFastRegion = 2304; // LR pixels of the staged neighbourhood
-
-struct FastSmem {
-    float4 region[kFastRegion];
-    unsigned long long best[kFastQ];
-    int rawq[kFastQRaw];
-    int qs[kFastQ];
-    uint32_t newc[kFastQ];
-    int blocks[kFastA];
-    int pxoff[kFastA + 1];
-    int scan[32];
-    short qmap[kFastRegion];  // Q block: its index + 1
-    short amap[kFastRegion];  // block to re-search: its index + 1
-    uint16_t rcode[kFastPx];
-    float rw[kFastPx];
-    float rerr[kFastPx];
-    uint32_t hrpx[kFastPx];   // guide colour of every re-searched pixel
-    float eold[kFastPx];      // its error before the trial
-    uint16_t code0[kFastPx];  // its pair before the trial
-    int full[kFastPx];        // the component's pixels, then the pixels needing a full search
-    int nfull;
-    long long wsum[32][2];    // per-warp fixed-point error sums (old, new)
-    int wcnt[32];             // per-warp pixels re-searched
-};
-
-constexpr uint16_t kNotSearched = 0xFFFFu;
 
 // The re-search of a trial in three passes, so that the few pixels that need a full search do
 // not hold up whole warps:
@@ -1261,7 +1364,6 @@ constexpr uint16_t kNotSearched = 0xFFFFu;
 //   pass 2 (every thread of the CTA): the queued searches;
 //   pass 3 (a warp per block): the block's old and new error sums, Kahan per lane over the
 //     block's pixels in raster order, then a butterfly (the order of the general path).
-constexpr int kMaxChg = 8;
 
 __device__ __forceinline__ int full_entry(int pix, int bi, int a_known) {
     return pix | (bi << 12) | ((a_known + 1) << 20);
@@ -2206,21 +2308,28 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
     X.ws = ws;
 
     for (int it = 0; it < cm.N; ++it) {
-        k_threshold<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.own, ws.ovf, ws.ctl, it);
-        k_ccl_merge<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.ctl);
-        k_ccl_flatten<<<grid_cap(np, T), T, 0, st>>>(ws.lab, np, ws.ctl);
-        k_root_count<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, np, ws.tile_a, ws.ctl);
-        k_root_scan<<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
-        k_root_scatter<<<tiles_a, kScanThreads, 0, st>>>(B, ws.lab, ws.tile_a, ws.roots, ws.cnt,
-                                                         ws.fill, ws.done, ws.dag_cnt,
+        // large-error set, its ordered list, and its components (the list is the Q-list
+        // scratch of the trials, free until then)
+        int* fgl = ws.ulist;
+        const int lgrid = 2 * sm_count();   // list passes: a thread per large-error pixel or so
+        k_threshold<<<tiles_a, kScanThreads, 0, st>>>(B, ws.lab, ws.own, ws.ovf, ws.tile_a,
+                                                       ws.ctl, it);
+        k_tile_scan<0><<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
+        k_fg_scatter<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, np, ws.tile_a, fgl, ws.ctl);
+        k_ccl_merge<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.ctl);
+        k_ccl_flatten<<<lgrid, T, 0, st>>>(ws.lab, fgl, ws.ctl);
+        k_root_count<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, fgl, ws.tile_a, ws.ctl);
+        k_tile_scan<1><<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
+        k_root_scatter<<<tiles_a, kScanThreads, 0, st>>>(B, ws.lab, fgl, ws.tile_a, ws.roots,
+                                                         ws.cnt, ws.fill, ws.done, ws.dag_cnt,
                                                          ws.dag_fill, ws.queue, ws.ctl, it);
-        k_comp_count<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.roots, ws.cnt, ws.own, ws.ovf,
-                                                    ws.qflag, ws.ctl);
+        k_comp_count<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.roots, ws.cnt, ws.own,
+                                                         ws.ovf, ws.qflag, ws.ctl);
         k_comp_tile_reduce<<<tiles_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.ctl);
         k_comp_tile_scan<<<1, kScanThreads, 0, st>>>(ws.tile_b, ws.ctl);
         k_comp_scan<<<tiles_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.start, ws.ctl);
-        k_comp_fill<<<grid_cap(np, T), T, 0, st>>>(B, ws.lab, ws.qflag, ws.start, ws.fill,
-                                                   ws.comp_pix, ws.qlist, ws.ctl);
+        k_comp_fill<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.qflag, ws.start,
+                                                        ws.fill, ws.comp_pix, ws.qlist, ws.ctl);
         // the trials' dependency graph
         k_deps<0><<<grid_cap(ws.mcap, 1, 8), 256, 0, st>>>(B, ws, it);
         k_comp_tile_reduce<<<tiles_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.ctl);

@@ -145,7 +145,7 @@ int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* par
  * GLU_JOINT_STATIC_BYTES array in the library's own device memory (held by every GPU that loads
  * the library until the process exits). Arguments and results as glu_joint_optimize, minus the
  * workspace. Returns GLU_ERR_WORKSPACE, before any launch, when glu_joint_workspace_size() for
- * this image exceeds GLU_JOINT_STATIC_BYTES (about 1.3 megapixels at scale 8, 5x5 window, 5
+ * this image exceeds GLU_JOINT_STATIC_BYTES (about 0.9 megapixels at scale 8, 5x5 window, 5
  * iterations). The first call on each device looks up the array's device address with that
  * device current; make that first call before any stream capture. All calls on a device share
  * the array (each call initialises what it reads); calls that overlap on the GPU race, so issue

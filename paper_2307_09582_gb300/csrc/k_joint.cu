@@ -4,22 +4,28 @@
 // The images of a batch share one global HR pixel index space and one global LR index space
 // (image after image, raster order inside each). Per iteration n (all launched up front; every
 // kernel returns at once when device-side flags say every image has converged, so the host
-// never waits in the middle):
+// never waits in the middle, and a repeated call is replayed as a CUDA graph):
 //   threshold   E_p > tau marks the large-error set of every still-active image; union-find
 //               labels (parent pointers only ever decrease, so every component's root is its
-//               smallest global index, i.e. its smallest raster index inside its image)
+//               smallest global index, i.e. its smallest raster index inside its image); the
+//               set's pixels are compacted in raster order and later passes visit only them
 //   merge/flat  8- (or 4-) connected unions inside each image, then every pixel points at its root
 //   roots       ordered stream compaction of the roots: component j = the j-th smallest root
 //   buckets     pixels and distinct LR blocks per component (counts, exclusive scan, fill)
-//   trials      persistent kernel: CTAs claim components in ascending order; component j waits
-//               only for earlier components of its image whose LR blocks lie within D of its
-//               own (D = 2r for STRICT, r for PAPER) — exactly the components whose trials can
-//               read or write state j reads or writes — so the concurrent result equals the
-//               sequential one. Block items of a trial are shared with idle warps of the grid.
-//               Waits are bounded (GLU_ERR_TIMEOUT) and can never deadlock: a component only
-//               waits for lower indices, which were claimed earlier by running CTAs.
-//   residual    R_n = sum_p E_p per image in FP64 with a fixed reduction order; an image stops
-//               when its set is empty, when no trial was kept, or when R_n >= R_{n-1}.
+//   graph       trial j must follow trial i < j exactly when an LR block of i lies within D of
+//               one of j (D = 2r STRICT, r PAPER): those are the trials that read or write state
+//               j reads or writes. Per component: the number of such predecessors and, per
+//               component, the list of its successors
+//   trials      persistent kernel over a ready queue: a component whose predecessors have all
+//               finished is tried by one CTA (small components: entirely in shared memory; large
+//               ones: block items shared with idle warps of the grid); its commit releases its
+//               successors, continuing with the first it made ready. Trials that run at the same
+//               time touch disjoint state, so the result equals the sequential order. Waits are
+//               bounded (GLU_ERR_TIMEOUT) and cannot deadlock (edges only go from lower to
+//               higher indices)
+//   residual    R_n = sum_p E_p per image, exact in units of 2^-32 (64-bit integer sum); an
+//               image stops when its set is empty, when no trial was kept, or when
+//               R_n >= R_{n-1}.
 // Trial sums e0 / e1 are FP32 Kahan sums per LR block (fixed lane order), rounded to 2^-32 and
 // added as 64-bit integers: exact and independent of the order blocks finish in.
 #include <stddef.h>

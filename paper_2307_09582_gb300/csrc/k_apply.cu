@@ -450,14 +450,268 @@ int launch_apply(const ApplyArgs& a, cudaStream_t st) {
     return GLU_OK;
 }
 
+// The LR-gradient sums of k_apply_backward_lr with the HR pixels a tile of TxT LR pixels depends
+// on (its blocks within r, i.e. the pixels whose windows can reach it) staged in shared memory
+// once: decoded pair, weight and upstream gradient. Every input is read from HBM about
+// (1 + 2r/T)^2 times instead of (2r+1)^2 times, and the scan touches shared memory only. Same
+// loops, same order, same results.
+template <int C>
+__global__ void __launch_bounds__(256) k_apply_backward_lr_tile(const BackwardArgs P, int T) {
+    // RH x RW HR pixels of the region: pair (k_a | k_b << 8), weight, upstream gradient
+    extern __shared__ float rsm[];
+    const int r = (P.S - 1) >> 1, K = P.S * P.S;
+    const float invK = 1.0f / (float)K;
+    const int v0 = blockIdx.y * T, u0 = blockIdx.x * T;
+    const int bv0 = max(v0 - r, 0), bv1 = min(v0 + T + r, P.h);
+    const int bu0 = max(u0 - r, 0), bu1 = min(u0 + T + r, P.w);
+    const int y0 = bv0 * P.s, y1 = min(bv1 * P.s, P.H);
+    const int x0 = bu0 * P.s, x1 = min(bu1 * P.s, P.W);
+    const int RW = x1 - x0, RH = y1 - y0, NR = RH * RW;
+    float* rg = rsm;                                   // NR x C
+    float* rw = rsm + (size_t)NR * C;                  // NR
+    uint16_t* rpair = (uint16_t*)(rw + NR);            // NR
+    // staged four pixels per thread at a time, loads first (each code decoded once per CTA; a
+    // code outside the window range matches no LR pixel)
+    constexpr int kU = 4;
+    for (int i0 = threadIdx.x; i0 < NR; i0 += blockDim.x * kU) {
+        int code[kU];
+        float w[kU], g[kU][C];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int i = i0 + k * blockDim.x;
+            code[k] = 0;
+            if (i < NR) {
+                const int yy = i / RW, xx = i - yy * RW;
+                const int64_t p = (int64_t)(y0 + yy) * P.W + x0 + xx;
+                code[k] = P.code[p];
+                w[k] = load_weight(P.weight, P.wfmt, p);
+                const int64_t og = (int64_t)(y0 + yy) * P.G_pitch + (int64_t)(x0 + xx) * C;
+#pragma unroll
+                for (int c = 0; c < C; ++c) g[k][c] = __ldcs(&P.G[og + c]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int i = i0 + k * blockDim.x;
+            if (i < NR) {
+                const int ka = qdiv(code[k], invK), kb = code[k] - ka * K;
+                rpair[i] = code[k] < K * K ? (uint16_t)(ka | (kb << 8)) : (uint16_t)0xFFFFu;
+                rw[i] = w[k];
+#pragma unroll
+                for (int c = 0; c < C; ++c) rg[(size_t)i * C + c] = g[k][c];
+            }
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    // a full s x s block: lane j's pixels sit at fixed offsets from the block's corner (rows
+    // advance by 32 / s per step when s divides 32); blocks cut by the image edge take the
+    // general loop
+    const int s = P.s;
+    const bool pow2 = s <= 32 && (32 % s) == 0;
+    const int lane_dy = pow2 ? lane / s : 0, lane_dx = pow2 ? lane % s : 0;
+    const int step = pow2 ? (32 / s) * RW : 0;
+    const int nstep = pow2 ? (s * s + 31) / 32 : 0;
+    const int lane_off = lane_dy * RW + lane_dx;
+    for (int t = threadIdx.x >> 5; t < T * T; t += warps) {
+        const int v = v0 + t / T, u = u0 + t % T;
+        if (v >= P.h || u >= P.w) continue;   // warp-uniform
+        float acc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = 0.f;
+        for (int bv = max(0, v - r); bv <= min(P.h - 1, v + r); ++bv) {
+            const int ys = bv * s;
+            for (int bu = max(0, u - r); bu <= min(P.w - 1, u + r); ++bu) {
+                // window index of q as seen from pixels of block (bv, bu)
+                const int kq = (v - bv + r) * P.S + (u - bu + r);
+                const int xs = bu * s;
+                const bool full = pow2 && ys + s <= P.H && xs + s <= P.W;
+                if (full) {
+                    int i = (ys - y0) * RW + (xs - x0) + lane_off;
+                    for (int k = 0; k < nstep; ++k, i += step) {
+                        if (k * 32 + lane >= s * s) break;
+                        const int pr = rpair[i];
+                        const int ka = pr & 0xFF, kb = pr >> 8;
+                        if (ka != kq && kb != kq) continue;
+                        const float w = rw[i];
+                        const float f = (ka == kq ? w : 0.f) + (kb == kq ? 1.f - w : 0.f);
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            acc[c] = __fmaf_rn(f, rg[(size_t)i * C + c], acc[c]);
+                    }
+                } else {
+                    const int ey = min(s, P.H - ys), ex = min(s, P.W - xs);
+                    const float inv_ex = 1.0f / (float)ex;
+                    for (int j = lane; j < ey * ex; j += 32) {
+                        const int jy = qdiv(j, inv_ex), jx = j - jy * ex;
+                        const int i = (ys + jy - y0) * RW + (xs + jx - x0);
+                        const int pr = rpair[i];
+                        const int ka = pr & 0xFF, kb = pr >> 8;
+                        if (ka != kq && kb != kq) continue;
+                        const float w = rw[i];
+                        const float f = (ka == kq ? w : 0.f) + (kb == kq ? 1.f - w : 0.f);
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            acc[c] = __fmaf_rn(f, rg[(size_t)i * C + c], acc[c]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) P.gT[(int64_t)v * P.gT_pitch + (int64_t)u * C + c] = acc[c];
+        }
+    }
+}
+
+// grad_w of the adjoint for 3 channels, tiled like k_apply3_tile: the LR target region and the
+// code -> cell table in shared memory, the upstream gradient streamed in as three 16-byte loads
+// per 4 pixels, the 4 results stored as one 16-byte store. Same arithmetic and order as
+// k_apply_backward_w. Conditions: float32 target and gradient, W % 4 == 0, aligned rows.
+template <int TH>
+__global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_gw_tile(const BackwardArgs P) {
+    constexpr int NW = TH < 8 ? TH : 8;
+    constexpr int RPW = TH / NW;
+    extern __shared__ float4 reg4[];   // RH x RW region (RGB_), then K*K offset pairs
+    const int x0 = blockIdx.x * kApplyTW, y0 = blockIdx.y * TH;
+    const int s = P.s, S = P.S, r = (S - 1) >> 1, K = S * S, K2 = K * K;
+    const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + TH, P.H);
+    const int v0 = y0 / s - r, u0 = x0 / s - r;
+    const int RH = (ye - 1) / s + r - v0 + 1, RW = (xe - 1) / s + r - u0 + 1;
+    uint32_t* tab = (uint32_t*)(reg4 + apply_region_cells(TH, s, S));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int xs = x0 + lane * 4;
+    const bool col_ok = xs < P.W;
+    uint2 cc[RPW];
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int y = y0 + wid + k * NW;
+        cc[k] = make_uint2(0u, 0u);
+        if (col_ok && y < P.H) cc[k] = __ldcs((const uint2*)P.code + (((int64_t)y * P.W + xs) >> 2));
+    }
+    for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
+        const int rr = i / RW, c1 = i - rr * RW;
+        const int v = min(max(v0 + rr, 0), P.h - 1);
+        const int u = min(max(u0 + c1, 0), P.w - 1);
+        const float* t = P.T + (int64_t)v * P.T_pitch + (int64_t)u * 3;
+        reg4[i] = make_float4(__ldg(t), __ldg(t + 1), __ldg(t + 2), 0.f);
+    }
+    for (int c = threadIdx.x; c < K2; c += blockDim.x) {
+        const int ka = c / K, kb = c - ka * K;
+        tab[c] = (uint32_t)((ka / S) * RW + ka % S) | ((uint32_t)((kb / S) * RW + kb % S) << 16);
+    }
+    __syncthreads();
+    if (!col_ok) return;
+    const bool interior = v0 >= 0 && u0 >= 0 && (ye - 1) / s + r < P.h && (xe - 1) / s + r < P.w;
+    const int c0 = xs / s, rem = xs - c0 * s;
+    int wcol[4], pxj[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        pxj[j] = c0 + (rem + j >= s) + (rem + j >= 2 * s) + (rem + j >= 3 * s);
+        wcol[j] = pxj[j] - r - u0;
+    }
+    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int y = y0 + wid + k * NW;
+        if (y >= P.H) break;
+        const float4* g4 = (const float4*)(P.G + (int64_t)y * P.G_pitch + (int64_t)xs * 3);
+        const float4 ga = __ldcs(g4), gb = __ldcs(g4 + 1), gc = __ldcs(g4 + 2);
+        const float g[12] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x, gc.y, gc.z, gc.w};
+        const int py = y / s;
+        const int rowbase = (py - r - v0) * RW;
+        const int code[4] = {(int)(cc[k].x & 0xFFFFu), (int)(cc[k].x >> 16),
+                             (int)(cc[k].y & 0xFFFFu), (int)(cc[k].y >> 16)};
+        float res[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int base = rowbase + wcol[j];
+            const int c = code[j];
+            int ia, ib;
+            if (c < K2) {
+                const uint32_t t = tab[c];
+                ia = base + (int)(t & 0xFFFFu);
+                ib = base + (int)(t >> 16);
+            } else {
+                set_status(GLU_ERR_DEVICE_CHECK);
+                ia = ib = 0;
+            }
+            if (!interior) {
+                const int ka = qdiv(c, invK), kb = c - ka * K;
+                const int ra = qdiv(ka, invS), rb = qdiv(kb, invS);
+                const int va = py + ra - r, ua = pxj[j] + (ka - ra * S) - r;
+                const int vb = py + rb - r, ub = pxj[j] + (kb - rb * S) - r;
+                if ((unsigned)va >= (unsigned)P.h || (unsigned)ua >= (unsigned)P.w) {
+                    set_status(GLU_ERR_DEVICE_CHECK);
+                    ia = 0;
+                }
+                if ((unsigned)vb >= (unsigned)P.h || (unsigned)ub >= (unsigned)P.w) {
+                    set_status(GLU_ERR_DEVICE_CHECK);
+                    ib = 0;
+                }
+            }
+            const float4 ta = reg4[ia], tb = reg4[ib];
+            float acc = 0.f;
+            acc = __fmaf_rn(g[j * 3 + 0], ta.x - tb.x, acc);
+            acc = __fmaf_rn(g[j * 3 + 1], ta.y - tb.y, acc);
+            acc = __fmaf_rn(g[j * 3 + 2], ta.z - tb.z, acc);
+            res[j] = acc;
+        }
+        __stcs((float4*)(P.gw + (int64_t)y * P.W + xs), make_float4(res[0], res[1], res[2], res[3]));
+    }
+}
+
 template <int C>
 static int launch_bw_t(const BackwardArgs& a, cudaStream_t st) {
     const int threads = 256;
-    const int grid_q = grid_for((int64_t)a.h * a.w * 32, threads);
-    k_apply_backward_lr<C><<<grid_q, threads, 0, st>>>(a);
+    // the largest LR tile whose HR region's codes fit the shared-memory budget
+    const int r = (a.S - 1) / 2;
+    int T = 0;
+    size_t smem = 0;
+    for (int t : {8, 4, 2, 1}) {
+        const size_t side = (size_t)(t + 2 * r) * a.s;
+        const size_t bytes = side * side * (sizeof(float) * (C + 1) + sizeof(uint16_t));
+        if (bytes <= 110 * 1024 && a.s <= 64) {
+            T = t;
+            smem = bytes;
+            break;
+        }
+    }
+    if (T > 0) {
+        auto kern = k_apply_backward_lr_tile<C>;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+            return GLU_ERR_CUDA;
+        const dim3 grid((a.w + T - 1) / T, (a.h + T - 1) / T);
+        kern<<<grid, threads, smem, st>>>(a, T);
+    } else {
+        const int grid_q = grid_for((int64_t)a.h * a.w * 32, threads);
+        k_apply_backward_lr<C><<<grid_q, threads, 0, st>>>(a);
+    }
     GLU_LAUNCH_CHECK();
     if (a.gw) {
-        k_apply_backward_w<C><<<grid_for((int64_t)a.H * a.W, threads), threads, 0, st>>>(a);
+        const bool tiled = C == 3 && a.W % 4 == 0 && a.G_pitch == (int64_t)a.W * 3 &&
+                           ((uintptr_t)a.G & 15u) == 0 && ((uintptr_t)a.gw & 15u) == 0 &&
+                           ((uintptr_t)a.code & 7u) == 0;
+        if (tiled) {
+            constexpr int TH = 16;
+            const size_t sm = sizeof(float4) * (size_t)apply_region_cells(TH, a.s, a.S) +
+                              sizeof(uint32_t) * (size_t)(a.S * a.S) * (a.S * a.S);
+            if (sm > 48 * 1024 &&
+                cudaFuncSetAttribute(k_apply3_gw_tile<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm) != cudaSuccess)
+                return GLU_ERR_CUDA;
+            const dim3 grid((a.W + kApplyTW - 1) / kApplyTW, (a.H + TH - 1) / TH);
+            k_apply3_gw_tile<TH><<<grid, 32 * 8, sm, st>>>(a);
+        } else {
+            k_apply_backward_w<C><<<grid_for((int64_t)a.H * a.W, threads), threads, 0, st>>>(a);
+        }
         GLU_LAUNCH_CHECK();
     }
     return GLU_OK;

@@ -25,6 +25,7 @@ sys.path.insert(0, ROOT)
 
 H4K, W4K, SCALE, WIN, NITER = 2160, 3840, 8, 5, 5
 BATCH_NITER = 3
+EXACT_OPS_PER_PAIR = 21   # GLU*: d (3), v (3), v.d (3), |d|^2 + eps (4), w (1), e (3), |e|^2 (3), compare (1)
 VIDEO_FRAMES = 120
 METRIC = "HR Mpix/s for GLU optimise+apply at 4K x8; batched/bwd vs plain; % of roofline"
 WORKLOAD = "joint-optimise+LRop+apply 3840x2160 x8, 5x5 window, 5 Alg.2 iterations, STRICT"
@@ -390,6 +391,14 @@ def measure_extras(api, torch, img, dev, flush, stream):
     ms_b = timed(lambda: api.glu_apply_backward(theta, T, G, grad_lr=gT, grad_w=gw))
     res["backward_ms"] = ms_b
     res["backward_vs_apply"] = ms_b / ms_a
+    # GLU* (Eq. 4, every pair of window pixels) on the same guide and LR image
+    pe = api.glu_params(S=WIN, mode=api.GLU_MODE_EXACT)
+    th_e = api.Theta.empty(H, W, SCALE, WIN, api.GLU_W_F32, dev)
+    ms_e = timed(lambda: api.glu_optimize(hr, lr, pe, SCALE, theta=th_e), reps=5)
+    pairs = WIN * WIN * (WIN * WIN - 1) // 2
+    res["exact_ms"] = ms_e
+    res["exact_alu_frac"] = (H * W * pairs * EXACT_OPS_PER_PAIR / (ms_e / 1e3)) / (
+        torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2.07e9)
     res["batch16"] = measure_batch(api, torch, dev, timed)
     if VIDEO_FRAMES > 0:
         res["video"] = measure_video(api, torch, dev, VIDEO_FRAMES)

@@ -65,7 +65,10 @@ typedef struct {
     int32_t wfmt;       /* glu_wfmt; UNORM16 stores round(w * 65535) */
 } glu_theta;
 
-typedef enum { GLU_MODE_FAST = 0, GLU_MODE_GNU = 1 } glu_mode;
+/* FAST: Algorithm 1 (Eq. 5 weight). GNU: weight fixed to 1. EXACT: GLU* (Sec. 3.1) — every
+ * unordered pair k_a < k_b of window pixels with the Eq. 4 least-squares weight (not clamped, so
+ * weights may leave [0, 1]: float32 weight storage only); quadratic in the window size. */
+typedef enum { GLU_MODE_FAST = 0, GLU_MODE_GNU = 1, GLU_MODE_EXACT = 2 } glu_mode;
 typedef enum { GLU_JOINT_STRICT = 0, GLU_JOINT_PAPER = 1 } glu_joint_mode;
 typedef enum { GLU_DOWN_GRID = 0, GLU_DOWN_BOX = 1 } glu_down_mode;
 
@@ -74,7 +77,7 @@ typedef struct {
     float eps;            /* epsilon of Eq. 4 / Eq. 5 (paper: 1e-3, Sec. 3.1) */
     float tau;            /* large-error threshold of Algorithm 2 (paper: 30/255) */
     int32_t N;            /* maximum iterations of Algorithm 2 (paper: 3), <= GLU_MAX_ITERS */
-    int32_t mode;         /* glu_mode: Algorithm 1, or the weight-1 special case (GNU) */
+    int32_t mode;         /* glu_mode: Algorithm 1, the weight-1 special case (GNU), or GLU* */
     int32_t joint;        /* glu_joint_mode: STRICT (default) or PAPER reading of Algorithm 2 */
     int32_t connectivity; /* 8 (default) or 4: adjacency of large-error components */
 } glu_params;

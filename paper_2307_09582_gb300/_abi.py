@@ -21,7 +21,7 @@ GLU_ERR_TIMEOUT = -7
 
 GLU_U8, GLU_F16, GLU_F32 = 0, 1, 2
 GLU_W_F32, GLU_W_F16, GLU_W_UNORM16 = 0, 1, 2
-GLU_MODE_FAST, GLU_MODE_GNU = 0, 1
+GLU_MODE_FAST, GLU_MODE_GNU, GLU_MODE_EXACT = 0, 1, 2
 GLU_JOINT_STRICT, GLU_JOINT_PAPER = 0, 1
 GLU_DOWN_GRID, GLU_DOWN_BOX = 0, 1
 GLU_MAX_ITERS = 32

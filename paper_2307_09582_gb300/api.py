@@ -17,7 +17,7 @@ import torch
 
 from . import _abi as A
 from ._abi import (GLU_DOWN_BOX, GLU_DOWN_GRID, GLU_F16, GLU_F32, GLU_JOINT_PAPER,  # noqa: F401
-                   GLU_JOINT_STRICT, GLU_MODE_FAST, GLU_MODE_GNU, GLU_U8, GLU_W_F16, GLU_W_F32,
+                   GLU_JOINT_STRICT, GLU_MODE_EXACT, GLU_MODE_FAST, GLU_MODE_GNU, GLU_U8, GLU_W_F16, GLU_W_F32,
                    GLU_TUNE_APPLY, GLU_TUNE_SEARCH, GLU_W_UNORM16, GluError)
 
 _DT = {torch.uint8: A.GLU_U8, torch.float16: A.GLU_F16, torch.float32: A.GLU_F32}

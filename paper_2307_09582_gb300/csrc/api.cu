@@ -23,7 +23,8 @@ bool image_ok(const glu_image* im) {
 
 bool params_ok(const glu_params* p) {
     return p && p->S >= 1 && p->S <= 9 && (p->S & 1) && p->eps >= 0.f && p->tau >= 0.f &&
-           p->N >= 0 && p->N <= GLU_MAX_ITERS && (p->mode == GLU_MODE_FAST || p->mode == GLU_MODE_GNU) &&
+           p->N >= 0 && p->N <= GLU_MAX_ITERS &&
+           (p->mode == GLU_MODE_FAST || p->mode == GLU_MODE_GNU || p->mode == GLU_MODE_EXACT) &&
            (p->joint == GLU_JOINT_STRICT || p->joint == GLU_JOINT_PAPER) &&
            (p->connectivity == 4 || p->connectivity == 8);
 }
@@ -68,8 +69,9 @@ const char* glu_version(void) { return "glu-gb300 0.1 (sm_103a)"; }
 
 int glu_device_status(void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    int codes[4] = {read_and_clear_status_search(st), read_and_clear_status_apply(st),
-                    read_and_clear_status_down(st), read_and_clear_status_joint(st)};
+    int codes[5] = {read_and_clear_status_search(st), read_and_clear_status_apply(st),
+                    read_and_clear_status_down(st), read_and_clear_status_joint(st),
+                    read_and_clear_status_search_exact(st)};
     for (int c : codes)
         if (c != GLU_OK) return c;
     return GLU_OK;
@@ -96,6 +98,8 @@ int glu_optimize(const glu_image* hr, const glu_image* lr, const glu_params* par
     if (theta->H != hr->h || theta->W != hr->w || theta->S != params->S ||
         lr->h != lr_dim(hr->h, s) || lr->w != lr_dim(hr->w, s))
         return GLU_ERR_SHAPE;
+    // Eq. 4 weights are not clamped to [0, 1]: only the float32 format holds them
+    if (params->mode == GLU_MODE_EXACT && theta->wfmt != GLU_W_F32) return GLU_ERR_UNSUPPORTED;
     SearchArgs a;
     a.hr = hr->data;
     a.hr_pitch = hr->pitch;
@@ -115,6 +119,7 @@ int glu_optimize(const glu_image* hr, const glu_image* lr, const glu_params* par
     a.weight = theta->weight;
     a.wfmt = theta->wfmt;
     a.err = err_map;
+    if (params->mode == GLU_MODE_EXACT) return launch_search_exact(a, (cudaStream_t)stream);
     return launch_search(a, (cudaStream_t)stream);
 }
 
@@ -321,6 +326,14 @@ int glu_optimize_batched(const glu_batch_item* items, int32_t n, const glu_param
             if (rc) return rc;
             if (a[k].hr_dtype != items[0].hr.dtype || a[k].wfmt != items[0].theta.wfmt)
                 return GLU_ERR_UNSUPPORTED;
+        }
+        if (params->mode == GLU_MODE_EXACT) {
+            if (a[0].wfmt != GLU_W_F32) return GLU_ERR_UNSUPPORTED;
+            for (int k = 0; k < m; ++k) {
+                const int rc = launch_search_exact(a[k], (cudaStream_t)stream);
+                if (rc) return rc;
+            }
+            continue;
         }
         const int rc = launch_search_batch(a, m, (cudaStream_t)stream);
         if (rc) return rc;

@@ -26,6 +26,8 @@ struct SearchArgs {
 };
 
 int launch_search(const SearchArgs& a, cudaStream_t st);
+// GLU* (Eq. 4, every pair of window pixels); float32 weights only.
+int launch_search_exact(const SearchArgs& a, cudaStream_t st);
 constexpr int kMaxSearchBatch = 32;  // images per search launch (the kernel's parameter block)
 // Several images in one persistent launch; every item shares hr_dtype, wfmt, gnu and eps255.
 int launch_search_batch(const SearchArgs* items, int n, cudaStream_t st);
@@ -68,6 +70,7 @@ int read_and_clear_status_search(cudaStream_t st);
 int read_and_clear_status_apply(cudaStream_t st);
 int read_and_clear_status_down(cudaStream_t st);
 int read_and_clear_status_joint(cudaStream_t st);
+int read_and_clear_status_search_exact(cudaStream_t st);
 
 // Joint optimisation (Algorithm 2).
 struct JointArgs {

@@ -113,6 +113,11 @@ __device__ __forceinline__ SearchOut step_b(const float4* __restrict__ win, int 
     return o;
 }
 
+// Dot product with a fixed operation order.
+__device__ __forceinline__ float dot3(float ar, float ag, float ab, float br, float bg, float bb) {
+    return __fmaf_rn(ab, bb, __fmaf_rn(ag, bg, __fmul_rn(ar, br)));
+}
+
 // win: window candidate (dy, dx) at win[dy * rs + dx] (float4: r, g, b, unused), in shared
 // memory. rowmask / colmask: bit i set when window row / column i lies inside the LR image
 // (ignored when kInterior: the caller guarantees the whole window is inside).

@@ -65,6 +65,19 @@ def test_host_validation_codes(lib):
     lr = A.GluImage(fake, 16, 16, 3, A.GLU_U8, 16 * 3)
     assert lib.glu_optimize(ctypes.byref(hr), ctypes.byref(lr), ctypes.byref(p2),
                             ctypes.byref(th), None, None) == A.GLU_ERR_INVALID_ARG
+    # GLU* (Eq. 4) weights are unclamped: only float32 weights can hold them; unknown modes fail
+    p3 = A.GluParams.from_buffer_copy(p)
+    p3.mode = A.GLU_MODE_EXACT
+    th16 = A.GluTheta(fake, fake, 64, 64, 4, 3, A.GLU_W_UNORM16)
+    assert lib.glu_optimize(ctypes.byref(hr), ctypes.byref(lr), ctypes.byref(p3),
+                            ctypes.byref(th16), None, None) == A.GLU_ERR_UNSUPPORTED
+    p3.mode = 3
+    assert lib.glu_optimize(ctypes.byref(hr), ctypes.byref(lr), ctypes.byref(p3),
+                            ctypes.byref(th), None, None) == A.GLU_ERR_INVALID_ARG
+    p3.mode = A.GLU_MODE_EXACT   # the joint optimisation (Algorithm 2) runs Algorithm 1 only
+    assert lib.glu_joint_optimize(ctypes.byref(hr), 4, ctypes.byref(p3), ctypes.byref(lr),
+                                  ctypes.byref(th), None, None, fake, 1 << 30, None) == \
+        A.GLU_ERR_UNSUPPORTED
     bad_pitch = A.GluImage(fake, 64, 64, 3, A.GLU_U8, 100)
     assert lib.glu_downsample(ctypes.byref(bad_pitch), 4, 0, ctypes.byref(lr), None) == \
         A.GLU_ERR_INVALID_ARG

@@ -35,13 +35,20 @@ def pair_err64(Ic, Lc, s, S, y, x, ka, kb, eps, unit):
     return w, np.linalg.norm(w * d + Lb - I) / unit
 
 
-@pytest.mark.parametrize("H,W,s,S,lrmode", [(64, 80, 4, 3, "box"), (96, 72, 8, 5, "grid"),
-                                            (50, 70, 4, 7, "box"), (41, 33, 2, 5, "grid"),
-                                            (30, 30, 16, 3, "grid")])
-def test_exact_matches_oracle(api, H, W, s, S, lrmode):
+@pytest.mark.parametrize("H,W,s,S,lrmode,f16", [(64, 80, 4, 3, "box", False),
+                                                (96, 72, 8, 5, "grid", False),
+                                                (50, 70, 4, 7, "box", False),
+                                                (41, 33, 2, 5, "grid", False),
+                                                (30, 30, 16, 3, "grid", False),
+                                                (45, 61, 3, 5, "box", False),
+                                                (70, 90, 8, 5, "box", True)])
+def test_exact_matches_oracle(api, H, W, s, S, lrmode, f16):
     from paper_2307_09582_gb300.inputs import Scene, render_u8
     img = render_u8(Scene(width=W, height=H, n_cells=12, n_dots=15, n_lines=3, seed=H * W + S))
     hr = torch.from_numpy(img).cuda()
+    if f16:
+        hr = (hr.to(torch.float32) / 255).to(torch.float16)
+        img = hr.cpu().numpy().astype(np.float64)
     mode = api.GLU_DOWN_BOX if lrmode == "box" else api.GLU_DOWN_GRID
     lr = api.glu_downsample(hr, s, mode)
     p = api.glu_params(S=S, mode=api.GLU_MODE_EXACT)
@@ -69,7 +76,8 @@ def test_exact_matches_oracle(api, H, W, s, S, lrmode):
     # Eq. 1 with these (unclamped) weights reproduces the guide up to the reported error
     out = api.glu_apply(th, lr.to(torch.float32) if lr.dtype != torch.uint8
                         else lr.to(torch.float32) / 255.0)
-    rec_err = torch.linalg.norm(out - hr.to(torch.float32) / 255.0, dim=2)
+    g = hr.to(torch.float32) if f16 else hr.to(torch.float32) / 255.0
+    rec_err = torch.linalg.norm(out - g, dim=2)
     assert torch.allclose(rec_err, err, atol=2e-4)
 
 
@@ -83,3 +91,17 @@ def test_exact_requires_float32_weights(api):
     th, err = api.glu_optimize(hr, lr, p, 4, err_map=True, wfmt=api.GLU_W_F32)
     torch.cuda.synchronize()
     assert float(err.abs().max()) == 0.0     # exactly representable: zero error
+    # every pair has L_a = L_b: Eq. 4 gives 0 / eps = 0, and the first valid pair wins
+    ref = O.glu_exact(np.zeros((16, 16, 3), np.uint8), np.zeros((4, 4, 3), np.uint8), 4, 3)
+    assert float(th.weight_f32().abs().max()) == 0.0 and np.all(ref["omega"] == 0.0)
+    codes = th.codes_i32().cpu().numpy()
+    assert np.array_equal(codes // 9, ref["ka"]) and np.array_equal(codes % 9, ref["kb"])
+    # with eps = 0 the weight of L_a = L_b is taken as 1, like the oracle's
+    th0, _ = api.glu_optimize(hr, lr, api.glu_params(S=3, eps=0.0, mode=api.GLU_MODE_EXACT), 4,
+                              err_map=True, wfmt=api.GLU_W_F32)
+    ref = O.glu_exact(np.zeros((16, 16, 3), np.uint8), np.zeros((4, 4, 3), np.uint8), 4, 3,
+                      eps=0.0)
+    torch.cuda.synchronize()
+    assert np.array_equal(th0.weight_f32().cpu().numpy(), ref["omega"].astype(np.float32))
+    codes = th0.codes_i32().cpu().numpy()
+    assert np.array_equal(codes // 9, ref["ka"]) and np.array_equal(codes % 9, ref["kb"])

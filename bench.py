@@ -31,6 +31,9 @@ METRIC = "HR Mpix/s for GLU optimise+apply at 4K x8; batched/bwd vs plain; % of 
 WORKLOAD = "joint-optimise+LRop+apply 3840x2160 x8, 5x5 window, 5 Alg.2 iterations, STRICT"
 # canonical FP32 lane operations of Algorithm 1 per window candidate (a-step 7, b-step 20)
 OPS_PER_CANDIDATE = 27
+# DRAM bytes (read + write) of the trial kernel over one call (its 5 launches) on this workload,
+# from one ncu capture of the current kernel (profiles/k_trials_joint4k.md)
+TRIALS_DRAM_BYTES_PER_CALL = (89.1 + 38.2) * 1e6
 
 
 def peaks():
@@ -283,8 +286,10 @@ def run_glu(args):
     }
     dom_name, dom = max(cand.items(), key=lambda kv: kv[1]["ms"])
     achieved = dom["work"] / (dom["ms"] / 1e3)
+    traffic = TRIALS_DRAM_BYTES_PER_CALL if "k_trials" in dom_name else None
     roofline = dict(kernel=dom_name, bound=dom["bound"], achieved=achieved, peak=dom["peak"],
-                    unit=dom["unit"], frac=achieved / dom["peak"], traffic=None,
+                    unit=dom["unit"], frac=achieved / dom["peak"], traffic=traffic,
+                    traffic_unit="DRAM bytes per call (all trial launches of one call, ncu)",
                     peak_source=pk["src"], launch_ms=dom["ms"],
                     others={k: dict(ms=v["ms"], frac=(v["work"] / (v["ms"] / 1e3)) / v["peak"])
                             for k, v in cand.items()})
@@ -515,8 +520,8 @@ def measure_batch(api, torch, dev, timed):
 
 def run_kernel_case(args):
     """One kernel on an input larger than L2, a few launches (the target of an ncu capture):
-    search / apply / backward on a 7680x4320 guide at scale 8, window 5; trials = the joint 4K
-    workload (its first trial launch is iteration 1)."""
+    search / apply / backward / exact (GLU*, float32 weights) on a 7680x4320 guide at scale 8,
+    window 5; trials = the joint 4K workload (its first trial launch is iteration 1)."""
     import torch
     import __graft_entry__ as g
     g.build()
@@ -544,6 +549,13 @@ def run_kernel_case(args):
     T = torch.rand((h, w, 3), device=dev)
     out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
     api.glu_optimize(hr, lr, p, SCALE, theta=theta, err_map=err)
+    if args.kernel_case == "exact":
+        pe = api.glu_params(S=WIN, mode=api.GLU_MODE_EXACT)
+        th_e = api.Theta.empty(H, W, SCALE, WIN, api.GLU_W_F32, dev)
+        for _ in range(args.case_reps):
+            api.glu_optimize(hr, lr, pe, SCALE, theta=th_e, err_map=err)
+        torch.cuda.synchronize()
+        return 0
     for _ in range(args.case_reps):
         if args.kernel_case == "search":
             api.glu_optimize(hr, lr, p, SCALE, theta=theta, err_map=err)
@@ -564,7 +576,7 @@ def main():
     ap.add_argument("--impl", default="glu", choices=["glu", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
-    ap.add_argument("--kernel-case", choices=["search", "apply", "backward", "trials"],
+    ap.add_argument("--kernel-case", choices=["search", "apply", "backward", "trials", "exact"],
                     help="run one kernel on a profiling case and exit (no JSON line)")
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--video-frames", type=int, default=VIDEO_FRAMES)

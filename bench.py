@@ -568,6 +568,65 @@ def run_kernel_case(args):
     return 0
 
 
+def run_quality_sweep(args):
+    """Self-upsampling quality over scaling ratios and window sizes on the 3840x2160 guide, after
+    the paper's large-ratio experiment and its window-size table (Sec. 5): PSNR of Eq. 1 applied
+    to the LR image itself against the guide, for GLU- (Algorithm 1 on the grid-downsampled LR),
+    GLU (Algorithm 2, N = 3, STRICT), GLU* (all pairs, Eq. 4) and GNU (weight 1), with the time
+    of each call. One JSON line (not a throughput measurement)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_09582_gb300 import api
+    from paper_2307_09582_gb300.inputs import joint_4k_scene, render_u8
+    dev = torch.device("cuda", 0)
+    img = render_u8(joint_4k_scene())
+    hr = torch.from_numpy(img).to(dev)
+    ref = hr.to(torch.float32) / 255.0
+
+    def psnr(th, lr):
+        out = api.glu_apply(th, lr.to(torch.float32) / 255.0)
+        mse = ((out - ref).double() ** 2).mean()
+        return float(10 * torch.log10(1.0 / mse))
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    rows = []
+    for s_ in (8, 16, 32, 64, 128):
+        lr = api.glu_downsample(hr, s_, api.GLU_DOWN_GRID)
+        for S in (3, 5, 7, 9):
+            row = dict(scale=s_, window=S)
+            for name, mode, wfmt in (("glu_minus", api.GLU_MODE_FAST, api.GLU_W_F32),
+                                     ("glu_star", api.GLU_MODE_EXACT, api.GLU_W_F32),
+                                     ("gnu", api.GLU_MODE_GNU, api.GLU_W_F32)):
+                p = api.glu_params(S=S, mode=mode)
+                api.glu_optimize(hr, lr, p, s_, wfmt=wfmt)   # warm-up (and tuning)
+                (th, _), ms = timed(lambda: api.glu_optimize(hr, lr, p, s_, wfmt=wfmt))
+                row[name] = dict(psnr=psnr(th, lr), ms=ms)
+            # Algorithm 2 where a trial's re-searched area (S^2 blocks of s^2 pixels) stays
+            # moderate: its trials at the largest windows and ratios run for seconds
+            if s_ * S <= 384:
+                pj = api.glu_params(S=S, N=3)
+                try:
+                    (lj, tj, _, st), ms = timed(lambda: api.glu_joint_optimize(hr, s_, pj))
+                    row["glu"] = dict(psnr=psnr(tj, lj), ms=ms,
+                                      iterations=len(st["iters"]) if st else None)
+                except Exception as e:   # noqa: BLE001 - recorded, the sweep goes on
+                    row["glu"] = dict(error=str(e).splitlines()[0])
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps(dict(sweep="self-upsampling PSNR (dB) vs scale and window, 3840x2160 "
+                                "synthetic guide", rows=rows,
+                          status=api.glu_device_status())))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -579,6 +638,8 @@ def main():
     ap.add_argument("--kernel-case", choices=["search", "apply", "backward", "trials", "exact"],
                     help="run one kernel on a profiling case and exit (no JSON line)")
     ap.add_argument("--case-reps", type=int, default=3)
+    ap.add_argument("--quality-sweep", action="store_true",
+                    help="self-upsampling PSNR over scales 8-128 and windows 3-9, then exit")
     ap.add_argument("--video-frames", type=int, default=VIDEO_FRAMES)
     ap.add_argument("--variant", type=int, default=None,
                     help="with --kernel-case search/apply: the kernel variant to run")
@@ -586,6 +647,8 @@ def main():
     globals()["VIDEO_FRAMES"] = args.video_frames
     if args.kernel_case:
         return run_kernel_case(args)
+    if args.quality_sweep:
+        return run_quality_sweep(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -76,3 +76,41 @@ def lr_like_gpu(lr_tensor):
     """The LR image the GPU used, as a numpy array in its own dtype (uint8 or float)."""
     a = lr_tensor.cpu().numpy()
     return a if a.dtype == np.uint8 else a.astype(np.float64)
+
+
+def exact_pair_err(Ic, Lc, unit, s, S, y, x, ka, kb, eps=1e-3):
+    """Eq. 4 weight and Eq. 3 error (FP64, [0, 1] units) of window pair (ka, kb) at (y, x);
+    Ic, Lc as returned by oracle.colours()."""
+    r = (S - 1) // 2
+    py, px = y // s, x // s
+    La = Lc[py + ka // S - r, px + ka % S - r]
+    Lb = Lc[py + kb // S - r, px + kb % S - r]
+    I = Ic[y, x]
+    d = La - Lb
+    den = d @ d + eps * unit * unit
+    w = ((I - Lb) @ d) / den if den > 0 else 1.0
+    return w, np.linalg.norm(w * d + Lb - I) / unit
+
+
+def check_exact(I, L, s, S, theta, err_gpu, eps=1e-3, ref=None):
+    """GLU* parity: codes equal except where the GPU's pair is, in FP64, within NEAR_TIE of the
+    oracle's best error (under 1 % of the pixels); where codes match, weights within
+    1e-4 * max(1, |w|) (Eq. 4 weights are unclamped) and errors within 1e-5."""
+    K = S * S
+    if ref is None:
+        ref = O.glu_exact(I, L, s, S, eps=eps)
+    codes = theta.codes_i32().cpu().numpy()
+    ka, kb = codes // K, codes % K
+    same = (ka == ref["ka"]) & (kb == ref["kb"])
+    (Ic, Lc), unit = O.colours(I, L)
+    for (y, x) in np.argwhere(~same)[:2000]:
+        _, e = exact_pair_err(Ic, Lc, unit, s, S, y, x, int(ka[y, x]), int(kb[y, x]), eps)
+        assert e <= ref["err"][y, x] + NEAR_TIE, (y, x, e, ref["err"][y, x])
+    assert (~same).mean() < 0.01
+    wg = theta.weight_f32().cpu().numpy().astype(np.float64)
+    dw = np.abs(wg - ref["omega"]) / np.maximum(1.0, np.abs(ref["omega"]))
+    assert dw[same].max(initial=0.0) < 1e-4
+    de = np.abs(err_gpu.cpu().numpy().astype(np.float64) - ref["err"])
+    assert de[same].max(initial=0.0) < 1e-5
+    return dict(mismatches=int((~same).sum()), max_dw=float(dw[same].max(initial=0.0)),
+                max_derr=float(de[same].max(initial=0.0)))

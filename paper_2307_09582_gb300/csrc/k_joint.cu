@@ -117,6 +117,7 @@ struct JointWs {
     int* own;               // nq * kOwnSlots
     uint8_t* ovf;           // nq
     unsigned long long* stamp;  // nq
+    int* bown;              // nq: the item that re-searches an affected block (general path)
     unsigned long long* best;   // nq
     uint32_t* backup;       // nq
     int8_t* dlog;           // N * mcap: kept (1) / rolled back (0) per component and iteration
@@ -181,6 +182,7 @@ static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t
     t.own = (int*)take(sizeof(int) * nq * kOwnSlots);
     t.ovf = (uint8_t*)take(nq);
     t.stamp = (unsigned long long*)take(sizeof(unsigned long long) * nq);
+    t.bown = (int*)take(sizeof(int) * nq);
     t.best = (unsigned long long*)take(sizeof(unsigned long long) * nq);
     t.backup = (uint32_t*)take(sizeof(uint32_t) * nq);
     t.dlog = (int8_t*)take((size_t)(N > 0 ? N : 1) * (size_t)mcap);
@@ -1006,10 +1008,18 @@ constexpr int kMaxChg = 8;       // replaced LR pixels per window for the exact 
 // current LR image (comp >= 0: only the pixels of that component), writing the results in place
 // and the previous values to the backup planes. The previous errors (e0) and the new ones (e1)
 // are summed with Kahan compensation in a fixed lane order and reduced with a fixed butterfly.
+// The general path splits LR blocks of more than kChunkPx HR pixels (scales above 32) into chunks
+// of kChunkPx pixels in raster order, one item each, so that a large block is re-searched by
+// several warps.
+constexpr int kChunkPx = 1024;
+__device__ __forceinline__ int block_chunks(const JImg& I) {
+    return (I.s * I.s + kChunkPx - 1) / kChunkPx;
+}
+
 template <int S>
 __device__ __noinline__ void warp_block_trial(const JBatch& B, const TrialCtx& X, const JImg& I,
-                                              float4* win, int bv, int bu, int comp, int img,
-                                              float& e0, float& e1) {
+                                              float4* win, int bv, int bu, int chunk, int comp,
+                                              int img, float& e0, float& e1) {
     constexpr int r = (S - 1) / 2, K = S * S;
     const int lane = threadIdx.x & 31;
     for (int k = lane; k < K; k += 32) {
@@ -1028,7 +1038,8 @@ __device__ __noinline__ void warp_block_trial(const JBatch& B, const TrialCtx& X
     const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
     int nsearched = 0;
-    for (int j = lane; j < ey * ex; j += 32) {
+    const int jend = min(ey * ex, (chunk + 1) * kChunkPx);
+    for (int j = chunk * kChunkPx + lane; j < jend; j += 32) {
         const int y = ys + j / ex, x = xs + j % ex;
         const int64_t lp = (int64_t)y * I.W + x, p = I.p0 + lp;
         if (comp >= 0 && __ldcg(&X.ws.lab[p]) != comp) continue;
@@ -1062,13 +1073,15 @@ __device__ __noinline__ void warp_block_trial(const JBatch& B, const TrialCtx& X
     __syncwarp();
 }
 
-// Roll back a trial for LR block (bv, bu): restore Theta and E from the backup planes.
+// Roll back a trial for a chunk of LR block (bv, bu): restore Theta and E from the backup planes.
 __device__ __forceinline__ void warp_block_rollback(const JBatch& B, const TrialCtx& X,
-                                                    const JImg& I, int bv, int bu, int comp) {
+                                                    const JImg& I, int bv, int bu, int chunk,
+                                                    int comp) {
     const int lane = threadIdx.x & 31;
     const int ys = bv * I.s, xs = bu * I.s;
     const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
-    for (int j = lane; j < ey * ex; j += 32) {
+    const int jend = min(ey * ex, (chunk + 1) * kChunkPx);
+    for (int j = chunk * kChunkPx + lane; j < jend; j += 32) {
         const int y = ys + j / ex, x = xs + j % ex;
         const int64_t lp = (int64_t)y * I.W + x, p = I.p0 + lp;
         if (comp >= 0 && __ldcg(&X.ws.lab[p]) != comp) continue;
@@ -1100,35 +1113,30 @@ __device__ __forceinline__ unsigned long long trial_tag(int it, int j, int phase
     return ((unsigned long long)(it * 4 + phase) << 40) | (unsigned long long)(j + 1);
 }
 
-// One warp processes item t of component j of image img: claims its block (STRICT blocks reached
-// from several q are processed once), then runs the trial (kind 0, sums returned) or the
-// rollback (kind 1).
+// One warp processes item t of component j of image img: chunk t % nch of the block of block
+// item t / nch (STRICT: only if that block item owns the block, so a block reached from several
+// q is processed once), running the trial (kind 0, sums returned) or the rollback (kind 1).
 __device__ __noinline__ bool process_item(const JBatch& B, const TrialCtx& X, float4* win,
                                              int j, int img, int stY, int kind, int t, float& e0,
                                              float& e1) {
-    const int lane = threadIdx.x & 31;
     const JImg& I = B.im[img];
     e0 = 0.f;
     e1 = 0.f;
+    const int nch = block_chunks(I), t0 = t / nch, chunk = t % nch;
     int bv, bu;
-    if (!item_block(B, X, I, stY, t, bv, bu)) return false;
-    if (B.strict) {
-        const unsigned long long tag = trial_tag(X.it, j, kind + 1);
-        int claimed = 0;
-        if (lane == 0) claimed = atomicExch(&X.ws.stamp[I.q0 + (int64_t)bv * I.w + bu], tag) != tag;
-        if (!__shfl_sync(0xffffffffu, claimed, 0)) return false;
-    }
+    if (!item_block(B, X, I, stY, t0, bv, bu)) return false;
+    if (B.strict && __ldcg(&X.ws.bown[I.q0 + (int64_t)bv * I.w + bu]) != t0) return false;
     const int comp = B.strict ? -1 : j;
     if (kind == 0) {
         switch (I.S) {
-            case 1: warp_block_trial<1>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
-            case 3: warp_block_trial<3>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
-            case 5: warp_block_trial<5>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
-            case 7: warp_block_trial<7>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
-            default: warp_block_trial<9>(B, X, I, win, bv, bu, comp, img, e0, e1); break;
+            case 1: warp_block_trial<1>(B, X, I, win, bv, bu, chunk, comp, img, e0, e1); break;
+            case 3: warp_block_trial<3>(B, X, I, win, bv, bu, chunk, comp, img, e0, e1); break;
+            case 5: warp_block_trial<5>(B, X, I, win, bv, bu, chunk, comp, img, e0, e1); break;
+            case 7: warp_block_trial<7>(B, X, I, win, bv, bu, chunk, comp, img, e0, e1); break;
+            default: warp_block_trial<9>(B, X, I, win, bv, bu, chunk, comp, img, e0, e1); break;
         }
     } else {
-        warp_block_rollback(B, X, I, bv, bu, comp);
+        warp_block_rollback(B, X, I, bv, bu, chunk, comp);
     }
     return true;
 }
@@ -1144,15 +1152,24 @@ __device__ __forceinline__ unsigned long long now_ns() {
 }
 
 // Backstop for every wait of the trial kernel: a launch that has run this long has gone wrong
-// (the whole 4K workload takes milliseconds); give up, record GLU_ERR_TIMEOUT and return.
+// (the whole 4K workload takes milliseconds); give up, record GLU_ERR_TIMEOUT and return. The
+// allowance grows with the iteration's component count (a trial at scale 128 re-searches
+// 150 K pixels, and tens of thousands of them can depend on one another), up to a cap.
 constexpr unsigned long long kTrialDeadlineNs = 5000000000ull;
+constexpr unsigned long long kDeadlinePerComponentNs = 500000ull;
+constexpr unsigned long long kTrialDeadlineCapNs = 30000000000ull;
+__device__ __forceinline__ unsigned long long trial_deadline(int M) {
+    const unsigned long long d = kTrialDeadlineNs + (unsigned long long)M * kDeadlinePerComponentNs;
+    return d < kTrialDeadlineCapNs ? d : kTrialDeadlineCapNs;
+}
 
-// Warp-uniform: true when the launch must stop waiting (deadline passed or another wait
-// already timed out). Lane 0 decides, every lane gets the same answer.
-__device__ __forceinline__ bool warp_should_abort(const JointCtl* c, unsigned long long t0) {
+// Warp-uniform: true when the launch must stop waiting (its deadline, an absolute global-timer
+// value, has passed, or another wait already timed out). Lane 0 decides, every lane gets the
+// same answer.
+__device__ __forceinline__ bool warp_should_abort(const JointCtl* c, unsigned long long deadline) {
     int a = 0;
     if ((threadIdx.x & 31) == 0)
-        a = (*(volatile const int*)&c->timeout != 0) || (now_ns() - t0 > kTrialDeadlineNs);
+        a = (*(volatile const int*)&c->timeout != 0) || now_ns() > deadline;
     return __shfl_sync(0xffffffffu, a, 0) != 0;
 }
 
@@ -1263,7 +1280,7 @@ __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4
 // (fixed-point) sums of a trial in e0/e1. False on an exhausted wait.
 __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j, int img, int stY,
                          int kind, int nitems, int G, unsigned long long* s_e0,
-                         unsigned long long* s_e1, int* s_flag, unsigned long long t0) {
+                         unsigned long long* s_e1, int* s_flag, unsigned long long deadline) {
     const JointWs& W_ = X.ws;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int nwarps = kTrialThreads / 32;
@@ -1303,7 +1320,7 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
         if (lane == 0) fin = ld_acquire(&W_.slot_fin[own]) >= nitems;
         if (__shfl_sync(0xffffffffu, fin, 0)) break;
         if (!help_one(B, X, win, own, G, hint)) __nanosleep(100);
-        if (warp_should_abort(X.ws.ctl, t0)) {
+        if (warp_should_abort(X.ws.ctl, deadline)) {
             if (lane == 0) *s_flag = 1;
             break;
         }
@@ -1860,7 +1877,7 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
 __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int img, int j,
                           int2 st, int2 en, float4* win, int G, int* s_nu,
                           unsigned long long* s_e0, unsigned long long* s_e1, int* s_flag,
-                          int* accept, unsigned long long t0) {
+                          int* accept, unsigned long long deadline) {
     const JointWs& W_ = X.ws;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int r = (I.S - 1) / 2;
@@ -1907,20 +1924,32 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
         store_rgb(I.lr, I.lr_pitch, qv, qu,
                   (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16));
     }
+    // STRICT: every affected block (within r of Q) gets one owner among the block items that
+    // reach it
+    const int NB = (2 * r + 1) * (2 * r + 1);
+    if (B.strict) {
+        const unsigned long long tagA = trial_tag(X.it, j, 1);
+        for (int t = tid; t < nu * NB; t += nthr) {
+            int bv, bu;
+            if (!item_block(B, X, I, st.y, t, bv, bu)) continue;
+            const int64_t b = I.q0 + (int64_t)bv * I.w + bu;
+            if (atomicExch(&W_.stamp[b], tagA) != tagA) W_.bown[b] = t;
+        }
+    }
     // visible to this CTA after the barrier, and to helpers through the fence thread 0 issues
     // before it publishes the task (cumulative over what the barrier ordered before it)
     __syncthreads();
     // trial: Algorithm 1 again on the affected pixels (STRICT: every block within r of Q; PAPER:
-    // the component's own pixels), in place, summing e0 and e1
-    const int NB = (2 * r + 1) * (2 * r + 1);
-    const int nitems = B.strict ? nu * NB : nu;
-    bool ok = run_task(B, X, win, j, img, st.y, 0, nitems, G, s_e0, s_e1, s_flag, t0);
+    // the component's own pixels), in place, summing e0 and e1; blocks above kChunkPx pixels
+    // in several items
+    const int nitems = (B.strict ? nu * NB : nu) * block_chunks(I);
+    bool ok = run_task(B, X, win, j, img, st.y, 0, nitems, G, s_e0, s_e1, s_flag, deadline);
     const bool keep = !((long long)*s_e1 > (long long)*s_e0);
     __syncthreads();
     // keep (the results are in place) or roll back: Theta and E from the backup planes, the LR
     // colours from their backups
     if (!keep && ok) {
-        ok = run_task(B, X, win, j, img, st.y, 1, nitems, G, s_e0, s_e1, s_flag, t0);
+        ok = run_task(B, X, win, j, img, st.y, 1, nitems, G, s_e0, s_e1, s_flag, deadline);
         for (int t = tid; t < nu; t += nthr) {
             const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
             store_rgb(I.lr, I.lr_pitch, (int)(lq / I.w), (int)(lq % I.w), W_.backup[I.q0 + lq]);
@@ -1952,7 +1981,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
     const int M = ctl->M_cur;
     const JointWs& W_ = X.ws;
     float4* win = wins[warp];
-    const unsigned long long t0 = now_ns();
+    const unsigned long long deadline = now_ns() + trial_deadline(M);
     const bool dag = *(volatile int*)&ctl->dag_bad[X.it] == 0;
     bool stop = false;
     int next = -1;   // a successor this CTA made ready itself: tried next, without the queue
@@ -1991,7 +2020,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                 __syncthreads();
                 if (s_j >= 0 || s_j == -2) break;
                 if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
-                if (__syncthreads_or(warp_should_abort(ctl, t0) ? 1 : 0)) {
+                if (__syncthreads_or(warp_should_abort(ctl, deadline) ? 1 : 0)) {
                     if (tid == 0) s_flag = 1;
                     __syncthreads();
                     break;
@@ -2062,7 +2091,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                     }
                     if (__syncthreads_or(mine) == 0) break;
                     if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
-                    if (__syncthreads_or(warp_should_abort(ctl, t0) ? 1 : 0)) {
+                    if (__syncthreads_or(warp_should_abort(ctl, deadline) ? 1 : 0)) {
                         if (tid == 0) s_flag = 1;
                         break;
                     }
@@ -2089,7 +2118,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
         const bool fast = fast_trial(B, X, I, img, j, st, en, F, sh, &accept);
         if (!fast)
             ok = big_trial(B, X, I, img, j, st, en, win, G, &s_nu, &s_e0, &s_e1, &s_flag, &accept,
-                           t0);
+                           deadline);
         if (tid == 0) s_accept = accept;
         GLU_TRACE(X.it, j, 2);
         // the outcome is visible before any successor can start: every write precedes the
@@ -2142,7 +2171,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
         if (lane == 0) fin = *(volatile const int*)&ctl->finished[X.it] >= M;
         if (__shfl_sync(0xffffffffu, fin, 0)) break;
         if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
-        if (warp_should_abort(ctl, t0)) break;
+        if (warp_should_abort(ctl, deadline)) break;
     }
 }
 

@@ -61,7 +61,7 @@ typedef enum { GLU_W_F32 = 0, GLU_W_F16 = 1, GLU_W_UNORM16 = 2 } glu_wfmt;
 typedef struct {
     uint16_t* code;     /* H * W pair codes, k_a * S * S + k_b */
     void* weight;       /* H * W weights w in [0, 1] (Eq. 5) stored as `wfmt` */
-    int32_t H, W, scale, S;
+    int32_t H, W, scale, S;  /* 0 < H < 2^22 */
     int32_t wfmt;       /* glu_wfmt; UNORM16 stores round(w * 65535) */
 } glu_theta;
 

@@ -29,8 +29,10 @@ bool params_ok(const glu_params* p) {
            (p->connectivity == 4 || p->connectivity == 8);
 }
 
+// (fewer than 2^22 rows: the kernels divide row indices by the scale in float)
 bool theta_ok(const glu_theta* t) {
-    return t && t->code && t->weight && t->H > 0 && t->W > 0 && t->scale >= 1 && t->S >= 1 &&
+    return t && t->code && t->weight && t->H > 0 && t->H < (1 << 22) && t->W > 0 &&
+           t->scale >= 1 && t->S >= 1 &&
            t->S <= 9 && (t->S & 1) && t->wfmt >= GLU_W_F32 && t->wfmt <= GLU_W_UNORM16;
 }
 

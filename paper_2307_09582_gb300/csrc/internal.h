@@ -1,6 +1,7 @@
 // Host-side launcher interfaces between the C-ABI layer (api.cu) and the kernel files.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,6 +25,14 @@ struct SearchArgs {
     int wfmt;
     float* err;        // nullable
 };
+
+// 2D tiled TMA tensor map over a row-major array: `inner` elements of `esize` bytes per row,
+// `rows` rows `row_bytes` apart, box of box_inner x box_rows elements, out-of-bounds elements
+// zero-filled on loads and skipped on stores. False when TMA cannot describe the array (base
+// not 16-byte aligned, row_bytes or the box row not a multiple of 16 bytes, box side > 256).
+bool encode_map_2d(CUtensorMap* map, CUtensorMapDataType dt, size_t esize, const void* base,
+                   uint64_t inner, uint64_t rows, uint64_t row_bytes, uint32_t box_inner,
+                   uint32_t box_rows);
 
 int launch_search(const SearchArgs& a, cudaStream_t st);
 // GLU* (Eq. 4, every pair of window pixels); float32 weights only.

@@ -9,6 +9,8 @@
 // over each block's pixels), then reduces lanes with a fixed butterfly: no atomics, the result
 // is bit-reproducible. This is the segmented reduction over the inverse pixel-to-LR map with the
 // map left implicit (the window bounds it, so it is never materialised).
+#include <algorithm>
+
 #include "internal.h"
 #include "tune.h"
 #include "variants.h"
@@ -71,34 +73,51 @@ __global__ void k_apply(const ApplyArgs P) {
     }
 }
 
-// Exact integer quotient n / d for 0 <= n < 2^13 and d <= 81 (pair codes, window indices):
-// (n + 0.5) / d stays at least 0.5 / d away from an integer, far above the float error.
+// Exact integer quotient n / d for 0 <= n < 2^22 and d >= 1 (pair codes, window indices, rows):
+// (n + 0.5) / d stays at least 0.5 / d away from an integer, and the float error of
+// (n + 0.5) * fl(1 / d) is below (n + 0.5) / d * 2^-23 < 0.5 / d.
 __device__ __forceinline__ int qdiv(int n, float inv_d) {
     return __float2int_rd(((float)n + 0.5f) * inv_d);
 }
 
 template <int WF> struct W4;
+// load: 4 weights from global memory (streaming); shared: the same from shared memory.
 template <> struct W4<GLU_W_F32> {
-    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
-        const float4 v = __ldcs((const float4*)b + (p >> 2));
+    static __device__ __forceinline__ void decode(float4 v, float w[4]) {
         w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
+        decode(__ldcs((const float4*)b + (p >> 2)), w);
+    }
+    static __device__ __forceinline__ void shared(const void* b, int p, float w[4]) {
+        decode(*((const float4*)b + (p >> 2)), w);
     }
 };
 template <> struct W4<GLU_W_F16> {
-    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
-        const uint2 v = __ldcs((const uint2*)b + (p >> 2));
+    static __device__ __forceinline__ void decode(uint2 v, float w[4]) {
         const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
         const float2 c = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
         w[0] = a.x; w[1] = a.y; w[2] = c.x; w[3] = c.y;
     }
+    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
+        decode(__ldcs((const uint2*)b + (p >> 2)), w);
+    }
+    static __device__ __forceinline__ void shared(const void* b, int p, float w[4]) {
+        decode(*((const uint2*)b + (p >> 2)), w);
+    }
 };
 template <> struct W4<GLU_W_UNORM16> {
-    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
-        const uint2 v = __ldcs((const uint2*)b + (p >> 2));
+    static __device__ __forceinline__ void decode(uint2 v, float w[4]) {
         w[0] = (float)(v.x & 0xFFFFu) * (1.0f / 65535.0f);
         w[1] = (float)(v.x >> 16) * (1.0f / 65535.0f);
         w[2] = (float)(v.y & 0xFFFFu) * (1.0f / 65535.0f);
         w[3] = (float)(v.y >> 16) * (1.0f / 65535.0f);
+    }
+    static __device__ __forceinline__ void load(const void* b, int64_t p, float w[4]) {
+        decode(__ldcs((const uint2*)b + (p >> 2)), w);
+    }
+    static __device__ __forceinline__ void shared(const void* b, int p, float w[4]) {
+        decode(*((const uint2*)b + (p >> 2)), w);
     }
 };
 
@@ -108,6 +127,25 @@ __device__ __forceinline__ void store12(float* out, const float r[12]) {
     __stcs(o + 0, make_float4(r[0], r[1], r[2], r[3]));
     __stcs(o + 1, make_float4(r[4], r[5], r[6], r[7]));
     __stcs(o + 2, make_float4(r[8], r[9], r[10], r[11]));
+}
+// The same into shared memory (the output tile of the TMA kernel).
+__device__ __forceinline__ void store12_smem(float* out, const float r[12]) {
+    float4* o = (float4*)out;
+    o[0] = make_float4(r[0], r[1], r[2], r[3]);
+    o[1] = make_float4(r[4], r[5], r[6], r[7]);
+    o[2] = make_float4(r[8], r[9], r[10], r[11]);
+}
+__device__ __forceinline__ void store12_smem(__half* out, const float r[12]) {
+    uint2* o = (uint2*)out;
+    uint32_t u[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const __half2 h = __floats2half2_rn(r[2 * k], r[2 * k + 1]);
+        u[k] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    o[0] = make_uint2(u[0], u[1]);
+    o[1] = make_uint2(u[2], u[3]);
+    o[2] = make_uint2(u[4], u[5]);
 }
 __device__ __forceinline__ void store12(__half* out, const float r[12]) {
     uint2* o = (uint2*)out;
@@ -128,6 +166,109 @@ __host__ __device__ __forceinline__ int apply_region_cells(int th, int s, int S)
     return ((th - 1) / s + 2 + 2 * r) * ((kApplyTW - 1) / s + 2 + 2 * r);
 }
 
+// Geometry of one tile's windows in its LR region (shared by the tiled kernels below).
+struct TileGeom {
+    int s, S, r, K, K2, RW, v0;
+    bool interior;            // every window of the tile inside the LR image
+    int wcol[4], pxj[4];      // per pixel of the thread's group: window corner column, LR column
+    float invs, invK, invS;
+};
+
+// Eq. 1 for the thread's 4 consecutive pixels of HR row y: pair codes packed in cc, weights w.
+// Codes that would leave the LR image (not produced by the search) are recorded as
+// GLU_ERR_DEVICE_CHECK and redirected to the region's first cell.
+__device__ __forceinline__ void apply_row4(const ApplyArgs& P, const float4* reg4,
+                                           const uint32_t* tab, const TileGeom& g, int y,
+                                           uint2 cc, const float w[4], float res[12]) {
+    const int py = qdiv(y, g.invs);
+    const int rowbase = (py - g.r - g.v0) * g.RW;   // region row of the window's top row
+    const int code[4] = {(int)(cc.x & 0xFFFFu), (int)(cc.x >> 16), (int)(cc.y & 0xFFFFu),
+                         (int)(cc.y >> 16)};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int base = rowbase + g.wcol[j];
+        const int c = code[j];
+        int ia, ib;
+        if (c < g.K2) {
+            const uint32_t t = tab[c];
+            ia = base + (int)(t & 0xFFFFu);
+            ib = base + (int)(t >> 16);
+        } else {
+            set_status(GLU_ERR_DEVICE_CHECK);
+            ia = ib = 0;
+        }
+        if (!g.interior) {
+            const int ka = qdiv(c, g.invK), kb = c - ka * g.K;
+            const int ra = qdiv(ka, g.invS), rb = qdiv(kb, g.invS);
+            const int va = py + ra - g.r, ua = g.pxj[j] + (ka - ra * g.S) - g.r;
+            const int vb = py + rb - g.r, ub = g.pxj[j] + (kb - rb * g.S) - g.r;
+            if ((unsigned)va >= (unsigned)P.h || (unsigned)ua >= (unsigned)P.w) {
+                set_status(GLU_ERR_DEVICE_CHECK);
+                ia = 0;
+            }
+            if ((unsigned)vb >= (unsigned)P.h || (unsigned)ub >= (unsigned)P.w) {
+                set_status(GLU_ERR_DEVICE_CHECK);
+                ib = 0;
+            }
+        }
+        const float4 ta = reg4[ia], tb = reg4[ib];
+        res[j * 3 + 0] = __fmaf_rn(w[j], ta.x - tb.x, tb.x);
+        res[j * 3 + 1] = __fmaf_rn(w[j], ta.y - tb.y, tb.y);
+        res[j * 3 + 2] = __fmaf_rn(w[j], ta.z - tb.z, tb.z);
+    }
+}
+
+// The LR region of a tile (clamped to the image: entries outside it are never selected by a
+// valid code) and the pair-code table: code -> (cell of T_a, cell of T_b) relative to the
+// window corner, by float-reciprocal quotients (exact for these small operands).
+__device__ __forceinline__ void stage_region_table(const ApplyArgs& P, float4* reg4, uint32_t* tab,
+                                                   int RH, int RW, int v0, int u0,
+                                                   const TileGeom& g, bool table = true) {
+    const float* T = (const float*)P.T;
+    const float invRW = 1.0f / (float)RW;
+    for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
+        const int rr = qdiv(i, invRW), c1 = i - rr * RW;
+        const int v = min(max(v0 + rr, 0), P.h - 1);
+        const int u = min(max(u0 + c1, 0), P.w - 1);
+        const float* t = T + (int64_t)v * P.T_pitch + (int64_t)u * 3;
+        reg4[i] = make_float4(__ldg(t), __ldg(t + 1), __ldg(t + 2), 0.f);
+    }
+    if (!table) return;
+    for (int c = threadIdx.x; c < g.K2; c += blockDim.x) {
+        const int ka = qdiv(c, g.invK), kb = c - ka * g.K;
+        const int ra = qdiv(ka, g.invS), rb = qdiv(kb, g.invS);
+        const uint32_t oa = (uint32_t)(ra * RW + (ka - ra * g.S));
+        const uint32_t ob = (uint32_t)(rb * RW + (kb - rb * g.S));
+        tab[c] = oa | (ob << 16);
+    }
+}
+
+__device__ __forceinline__ TileGeom tile_geom(const ApplyArgs& P, int x0, int y0, int xe, int ye,
+                                              int xs, int RW, int v0, int u0) {
+    TileGeom g;
+    g.s = P.s;
+    g.S = P.S;
+    g.r = (P.S - 1) >> 1;
+    g.K = P.S * P.S;
+    g.K2 = g.K * g.K;
+    g.RW = RW;
+    g.v0 = v0;
+    g.invs = 1.0f / (float)g.s;
+    g.invK = 1.0f / (float)g.K;
+    g.invS = 1.0f / (float)g.S;
+    g.interior = v0 >= 0 && u0 >= 0 && qdiv(ye - 1, g.invs) + g.r < P.h &&
+                 qdiv(xe - 1, g.invs) + g.r < P.w;
+    // window corner columns of the 4 pixels in the region: xs / s once, then at most three
+    // block boundaries within the next 3 pixels
+    const int c0 = qdiv(xs, g.invs), rem = xs - c0 * g.s;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        g.pxj[j] = c0 + (rem + j >= g.s) + (rem + j >= 2 * g.s) + (rem + j >= 3 * g.s);
+        g.wcol[j] = g.pxj[j] - g.r - u0;
+    }
+    return g;
+}
+
 // Eq. 1 fast path, tiled: a CTA owns TH x kApplyTW HR pixels (a warp per row, 4 pixels per
 // lane). The LR region its windows reach is copied to shared memory with coalesced row loads,
 // so the 8 gathers per 4 pixels are shared-memory reads, and a per-CTA table turns a pair code
@@ -141,12 +282,12 @@ __global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_tile(const Ap
     constexpr int RPW = TH / NW;
     extern __shared__ float4 reg4[];   // RH x RW region (RGB_), then K*K offset pairs
     const int x0 = blockIdx.x * kApplyTW, y0 = blockIdx.y * TH;
-    const int s = P.s, S = P.S, r = (S - 1) >> 1, K = S * S, K2 = K * K;
+    const int s = P.s, S = P.S, r = (S - 1) >> 1;
     const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + TH, P.H);
-    const int v0 = y0 / s - r, u0 = x0 / s - r;
-    const int RH = (ye - 1) / s + r - v0 + 1, RW = (xe - 1) / s + r - u0 + 1;
+    const float inv_s = 1.0f / (float)s;   // exact quotients (qdiv)
+    const int v0 = qdiv(y0, inv_s) - r, u0 = qdiv(x0, inv_s) - r;
+    const int RH = qdiv(ye - 1, inv_s) + r - v0 + 1, RW = qdiv(xe - 1, inv_s) + r - u0 + 1;
     uint32_t* tab = (uint32_t*)(reg4 + apply_region_cells(TH, s, S));
-    const float* T = (const float*)P.T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int xs = x0 + lane * 4;
     const bool col_ok = xs < P.W;
@@ -163,78 +304,92 @@ __global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_tile(const Ap
             W4<WF>::load(P.weight, p0, w[k]);
         }
     }
-    // the LR region, clamped to the image (entries outside it are never selected by a valid code)
-    for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
-        const int rr = i / RW, c1 = i - rr * RW;
-        const int v = min(max(v0 + rr, 0), P.h - 1);
-        const int u = min(max(u0 + c1, 0), P.w - 1);
-        const float* t = T + (int64_t)v * P.T_pitch + (int64_t)u * 3;
-        reg4[i] = make_float4(__ldg(t), __ldg(t + 1), __ldg(t + 2), 0.f);
-    }
-    // pair code -> (cell of T_a, cell of T_b) in the region, relative to the window corner
-    for (int c = threadIdx.x; c < K2; c += blockDim.x) {
-        const int ka = c / K, kb = c - ka * K;
-        const uint32_t oa = (uint32_t)((ka / S) * RW + ka % S);
-        const uint32_t ob = (uint32_t)((kb / S) * RW + kb % S);
-        tab[c] = oa | (ob << 16);
-    }
+    const TileGeom g = tile_geom(P, x0, y0, xe, ye, xs, RW, v0, u0);
+    stage_region_table(P, reg4, tab, RH, RW, v0, u0, g);
     __syncthreads();
     if (!col_ok) return;
-    // every window of the tile inside the LR image: only the code range needs checking
-    const bool interior = v0 >= 0 && u0 >= 0 && (ye - 1) / s + r < P.h && (xe - 1) / s + r < P.w;
-    // window corner columns of the 4 pixels in the region: xs / s once, then at most three
-    // block boundaries within the next 3 pixels
-    const int c0 = xs / s, rem = xs - c0 * s;
-    int wcol[4], pxj[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        pxj[j] = c0 + (rem + j >= s) + (rem + j >= 2 * s) + (rem + j >= 3 * s);
-        wcol[j] = pxj[j] - r - u0;
-    }
-    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
         const int y = y0 + wid + k * NW;
         if (y >= P.H) break;
-        const int py = y / s;
-        const int rowbase = (py - r - v0) * RW;   // region row of the window's top row
-        const int code[4] = {(int)(cc[k].x & 0xFFFFu), (int)(cc[k].x >> 16),
-                             (int)(cc[k].y & 0xFFFFu), (int)(cc[k].y >> 16)};
         float res[12];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int base = rowbase + wcol[j];
-            const int c = code[j];
-            int ia, ib;
-            if (c < K2) {
-                const uint32_t t = tab[c];
-                ia = base + (int)(t & 0xFFFFu);
-                ib = base + (int)(t >> 16);
-            } else {
-                set_status(GLU_ERR_DEVICE_CHECK);
-                ia = ib = 0;
-            }
-            if (!interior) {
-                // codes from the search never leave the LR image; anything else is recorded
-                const int ka = qdiv(c, invK), kb = c - ka * K;
-                const int ra = qdiv(ka, invS), rb = qdiv(kb, invS);
-                const int va = py + ra - r, ua = pxj[j] + (ka - ra * S) - r;
-                const int vb = py + rb - r, ub = pxj[j] + (kb - rb * S) - r;
-                if ((unsigned)va >= (unsigned)P.h || (unsigned)ua >= (unsigned)P.w) {
-                    set_status(GLU_ERR_DEVICE_CHECK);
-                    ia = 0;
-                }
-                if ((unsigned)vb >= (unsigned)P.h || (unsigned)ub >= (unsigned)P.w) {
-                    set_status(GLU_ERR_DEVICE_CHECK);
-                    ib = 0;
-                }
-            }
-            const float4 ta = reg4[ia], tb = reg4[ib];
-            res[j * 3 + 0] = __fmaf_rn(w[k][j], ta.x - tb.x, tb.x);
-            res[j * 3 + 1] = __fmaf_rn(w[k][j], ta.y - tb.y, tb.y);
-            res[j * 3 + 2] = __fmaf_rn(w[k][j], ta.z - tb.z, tb.z);
-        }
+        apply_row4(P, reg4, tab, g, y, cc[k], w[k], res);
         store12((OT*)P.out + (int64_t)y * P.out_pitch + (int64_t)xs * 3, res);
+    }
+}
+
+// The same tile with the tensor memory accelerator: the tile's codes and weights arrive by two
+// 2D TMA loads (mbarrier completion, bounded wait) while the CTA stages the LR region; results
+// go to a shared-memory output tile, written back by TMA stores (two boxes of 64 pixels x 3
+// channels per row band: a box row holds at most 256 elements). Every global access of the
+// streaming data is then a full-line bulk copy. Same arithmetic as k_apply3_tile.
+template <int WF, typename OT, int TH>
+__global__ void __launch_bounds__(256) k_apply3_tma(const ApplyArgs P,
+                                                    const __grid_constant__ CUtensorMap mcode,
+                                                    const __grid_constant__ CUtensorMap mw,
+                                                    const __grid_constant__ CUtensorMap mout) {
+    constexpr int NW = 8, RPW = TH / NW;
+    constexpr int WB = WF == GLU_W_F32 ? 4 : 2;          // weight bytes
+    constexpr int HALF = kApplyTW / 2 * 3;               // output elements per box row
+    static_assert(TH % NW == 0, "whole rows per warp");
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    // TMA boxes start on 128-byte boundaries of the shared window (the launch adds 128 bytes)
+    unsigned char* sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
+    uint16_t* scode = (uint16_t*)sm;                                 // [TH][128]
+    unsigned char* sw = sm + TH * kApplyTW * 2;                      // [TH][128] weights
+    OT* sout = (OT*)(sw + TH * kApplyTW * WB);                       // [2][TH][HALF]
+    uint64_t* bar = (uint64_t*)((unsigned char*)sout + 2 * TH * HALF * sizeof(OT));
+    float4* reg4 = (float4*)(bar + 2);
+    const int x0 = blockIdx.x * kApplyTW, y0 = blockIdx.y * TH;
+    const int s = P.s, S = P.S, r = (S - 1) >> 1;
+    const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + TH, P.H);
+    const float inv_s = 1.0f / (float)s;   // exact quotients (qdiv)
+    const int v0 = qdiv(y0, inv_s) - r, u0 = qdiv(x0, inv_s) - r;
+    const int RH = qdiv(ye - 1, inv_s) + r - v0 + 1, RW = qdiv(xe - 1, inv_s) + r - u0 + 1;
+    uint32_t* tab = (uint32_t*)(reg4 + apply_region_cells(TH, s, S));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int xs = x0 + lane * 4;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(TH * kApplyTW * (2 + WB)));
+        tma_load_2d(scode, &mcode, bar, x0, y0);
+        tma_load_2d(sw, &mw, bar, x0, y0);
+    }
+    const TileGeom g = tile_geom(P, x0, y0, xe, ye, xs, RW, v0, u0);
+    stage_region_table(P, reg4, tab, RH, RW, v0, u0, g);
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(ok ? 0 : 1)) {
+        if (threadIdx.x == 0) set_status(GLU_ERR_TIMEOUT);
+        (void)mbar_wait_bounded(bar, 0);   // the copies may still land: wait before leaving
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int row = wid + k * NW, y = y0 + row;
+        float res[12];
+        if (y < P.H && xs < P.W) {
+            const uint2 cc = *(const uint2*)&scode[row * kApplyTW + lane * 4];
+            float w[4];
+            W4<WF>::shared(sw + (size_t)row * kApplyTW * WB, lane * 4, w);
+            apply_row4(P, reg4, tab, g, y, cc, w, res);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 12; ++j) res[j] = 0.f;   // outside the image: not stored
+        }
+        store12_smem(sout + ((lane >> 4) * TH + row) * HALF + (lane & 15) * 12, res);
+    }
+    // the output tile is complete in shared memory: make it visible to the async proxy
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tma_store_2d(&mout, sout, x0 * 3, y0);
+        if ((x0 + kApplyTW / 2) < P.W) tma_store_2d(&mout, sout + TH * HALF, x0 * 3 + HALF, y0);
+        tma_store_commit_wait_read();   // shared memory stays valid until the stores read it
     }
 }
 
@@ -362,28 +517,138 @@ static int grid_for(int64_t work, int threads) {
     return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
 }
 
-// k_apply3_tile for variant v (tile rows), weight format and output type.
-template <typename F>
-static int apply_tile_dispatch(int v, int wfmt, bool out_f16, F&& launch) {
-#define GLU_APPLY_CASE(k)                                                                         \
-    case k:                                                                                       \
-        if (out_f16) {                                                                            \
-            if (wfmt == GLU_W_F32) return launch(k_apply3_tile<GLU_W_F32, __half, kApplyVariantRows[k]>); \
-            if (wfmt == GLU_W_F16) return launch(k_apply3_tile<GLU_W_F16, __half, kApplyVariantRows[k]>); \
-            return launch(k_apply3_tile<GLU_W_UNORM16, __half, kApplyVariantRows[k]>);            \
-        }                                                                                         \
-        if (wfmt == GLU_W_F32) return launch(k_apply3_tile<GLU_W_F32, float, kApplyVariantRows[k]>); \
-        if (wfmt == GLU_W_F16) return launch(k_apply3_tile<GLU_W_F16, float, kApplyVariantRows[k]>); \
-        return launch(k_apply3_tile<GLU_W_UNORM16, float, kApplyVariantRows[k]>)
-    static_assert(kNumApplyVariants == 4, "one case per variant");
-    switch (v) {
-        GLU_APPLY_CASE(0);
-        GLU_APPLY_CASE(1);
-        GLU_APPLY_CASE(2);
-        GLU_APPLY_CASE(3);
+// Persistent form of k_apply3_tma: a CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x,
+// ... with the codes and weights of the next two tiles in flight (two TMA stages, one mbarrier
+// each) and the output of the previous tile still being written by its TMA store (two output
+// buffers) while it computes the current one; only the LR region is staged synchronously (it
+// comes from L2). Same arithmetic as k_apply3_tile.
+template <int WF, typename OT, int TH>
+__global__ void __launch_bounds__(256) k_apply3_pipe(const ApplyArgs P,
+                                                     const __grid_constant__ CUtensorMap mcode,
+                                                     const __grid_constant__ CUtensorMap mw,
+                                                     const __grid_constant__ CUtensorMap mout,
+                                                     int tiles_x, int ntiles) {
+    constexpr int NW = 8, RPW = TH / NW;
+    constexpr int WB = WF == GLU_W_F32 ? 4 : 2;
+    constexpr int HALF = kApplyTW / 2 * 3;
+    constexpr int IN_BYTES = TH * kApplyTW * (2 + WB);              // codes, then weights
+    constexpr int OUT_BYTES = 2 * TH * HALF * (int)sizeof(OT);      // two boxes of HALF columns
+    static_assert(TH % NW == 0 && IN_BYTES % 128 == 0 && OUT_BYTES % 128 == 0, "tile layout");
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char* sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
+    unsigned char* sin = sm;                                         // [2][IN_BYTES]
+    OT* sout = (OT*)(sm + 2 * IN_BYTES);                             // [2][OUT_BYTES]
+    uint64_t* bar = (uint64_t*)(sm + 2 * IN_BYTES + 2 * OUT_BYTES);  // [2]
+    float4* reg4 = (float4*)(bar + 2);
+    const int s = P.s, S = P.S, r = (S - 1) >> 1;
+    uint32_t* tab = (uint32_t*)(reg4 + apply_region_cells(TH, s, S));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    auto issue = [&](int stage, int t) {   // thread 0 only
+        const int x0 = (t % tiles_x) * kApplyTW, y0 = (t / tiles_x) * TH;
+        mbar_arrive_expect_tx(&bar[stage], (uint32_t)IN_BYTES);
+        tma_load_2d(sin + stage * IN_BYTES, &mcode, &bar[stage], x0, y0);
+        tma_load_2d(sin + stage * IN_BYTES + TH * kApplyTW * 2, &mw, &bar[stage], x0, y0);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        if (blockIdx.x < ntiles) issue(0, blockIdx.x);
+        if (blockIdx.x + gridDim.x < ntiles) issue(1, blockIdx.x + gridDim.x);
+    }
+    int i = 0, tab_rw = -1;   // the table holds offsets for region width tab_rw
+    bool failed = false;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int stage = i & 1;
+        const uint32_t phase = (uint32_t)(i >> 1) & 1u;
+        const int x0 = (t % tiles_x) * kApplyTW, y0 = (t / tiles_x) * TH;
+        const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + TH, P.H);
+        const float inv_s = 1.0f / (float)s;   // exact quotients (qdiv)
+        const int v0 = qdiv(y0, inv_s) - r, u0 = qdiv(x0, inv_s) - r;
+        const int RH = qdiv(ye - 1, inv_s) + r - v0 + 1, RW = qdiv(xe - 1, inv_s) + r - u0 + 1;
+        const int xs = x0 + lane * 4;
+        const TileGeom g = tile_geom(P, x0, y0, xe, ye, xs, RW, v0, u0);
+        // (the previous tile's readers of the region and table passed the last barrier)
+        stage_region_table(P, reg4, tab, RH, RW, v0, u0, g, RW != tab_rw);
+        tab_rw = RW;
+        // this stage's output buffer was last written out two tiles ago: its store must have
+        // read it (one younger store group may still be reading the other buffer)
+        if (threadIdx.x == 0 && i >= 2) tma_store_wait_read_1();
+        __syncthreads();
+        const bool ok = mbar_wait_bounded(&bar[stage], phase);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            failed = true;
+            break;
+        }
+        const unsigned char* cin = sin + stage * IN_BYTES;
+        OT* cout = sout + stage * (OUT_BYTES / (int)sizeof(OT));
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+            const int row = wid + k * NW, y = y0 + row;
+            float res[12];
+            if (y < P.H && xs < P.W) {
+                const uint2 cc = *(const uint2*)(cin + (row * kApplyTW + lane * 4) * 2);
+                float w[4];
+                W4<WF>::shared(cin + TH * kApplyTW * 2 + (size_t)row * kApplyTW * WB, lane * 4,
+                               w);
+                apply_row4(P, reg4, tab, g, y, cc, w, res);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 12; ++j) res[j] = 0.f;   // outside the image: not stored
+            }
+            store12_smem(cout + ((lane >> 4) * TH + row) * HALF + (lane & 15) * 12, res);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();   // the output tile is complete and this stage's inputs are consumed
+        if (threadIdx.x == 0) {
+            tma_store_2d(&mout, cout, x0 * 3, y0);
+            if (x0 + kApplyTW / 2 < P.W) tma_store_2d(&mout, cout + TH * HALF, x0 * 3 + HALF, y0);
+            tma_store_commit();
+            if (t + 2 * (int)gridDim.x < ntiles) issue(stage, t + 2 * gridDim.x);
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (failed) {
+            set_status(GLU_ERR_TIMEOUT);
+            // loads still in flight land before the CTA leaves (bounded waits)
+            (void)mbar_wait_bounded(&bar[i & 1], (uint32_t)(i >> 1) & 1u);
+            if (blockIdx.x + (i + 1) * (int)gridDim.x < ntiles)
+                (void)mbar_wait_bounded(&bar[(i + 1) & 1], (uint32_t)((i + 1) >> 1) & 1u);
+        }
+        tma_store_commit_wait_read();   // every store has read its shared-memory source
+    }
+}
+
+// k_apply3_tile / k_apply3_tma with TH rows for a weight format and output type.
+template <template <int, typename, int> class KT, int TH, typename F>
+static int apply_kernel_for(int wfmt, bool out_f16, F&& launch) {
+    if (out_f16) {
+        if (wfmt == GLU_W_F32) return launch(KT<GLU_W_F32, __half, TH>::fn());
+        if (wfmt == GLU_W_F16) return launch(KT<GLU_W_F16, __half, TH>::fn());
+        return launch(KT<GLU_W_UNORM16, __half, TH>::fn());
+    }
+    if (wfmt == GLU_W_F32) return launch(KT<GLU_W_F32, float, TH>::fn());
+    if (wfmt == GLU_W_F16) return launch(KT<GLU_W_F16, float, TH>::fn());
+    return launch(KT<GLU_W_UNORM16, float, TH>::fn());
+}
+template <int WF, typename OT, int TH> struct TileK {
+    static auto fn() { return k_apply3_tile<WF, OT, TH>; }
+};
+template <int WF, typename OT, int TH> struct TmaK {
+    static auto fn() { return k_apply3_tma<WF, OT, TH>; }
+};
+template <int WF, typename OT, int TH> struct PipeK {
+    static auto fn() { return k_apply3_pipe<WF, OT, TH>; }
+};
+template <template <int, typename, int> class KT, typename F>
+static int apply_rows_dispatch(int rows, int wfmt, bool out_f16, F&& launch) {
+    switch (rows) {
+        case 8: return apply_kernel_for<KT, 8>(wfmt, out_f16, launch);
+        case 16: return apply_kernel_for<KT, 16>(wfmt, out_f16, launch);
+        case 32: return apply_kernel_for<KT, 32>(wfmt, out_f16, launch);
+        case 64: return apply_kernel_for<KT, 64>(wfmt, out_f16, launch);
         default: return GLU_ERR_INVALID_ARG;
     }
-#undef GLU_APPLY_CASE
 }
 
 int launch_apply(const ApplyArgs& a, cudaStream_t st) {
@@ -398,22 +663,77 @@ int launch_apply(const ApplyArgs& a, cudaStream_t st) {
 #define GLU_APPLY_TILED 1
 #endif
     if ((vec && GLU_APPLY_TILED) || vec16) {
+        // TMA needs 16-byte rows of codes, weights and output and 16-byte aligned bases
+        const size_t wb = a.wfmt == GLU_W_F32 ? 4 : 2, ob = vec16 ? 2 : 4;
+        CUtensorMap mcode, mw, mout;
+        int tma_rows = -1;   // rows the three maps were encoded for
+        auto maps_for = [&](int th) -> bool {
+            if (tma_rows == th) return true;
+            const bool ok =
+                encode_map_2d(&mcode, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.code, a.W, a.H,
+                              (uint64_t)a.W * 2, kApplyTW, th) &&
+                encode_map_2d(&mw, wb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                              wb, a.weight, a.W, a.H, (uint64_t)a.W * wb, kApplyTW, th) &&
+                encode_map_2d(&mout, vec16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              ob, a.out, (uint64_t)a.W * 3, a.H, (uint64_t)a.out_pitch * ob,
+                              kApplyTW / 2 * 3, th);
+            tma_rows = ok ? th : -1;
+            return ok;
+        };
         auto run = [&](int v) -> int {
-            const int th = kApplyVariantRows[v];
-            const size_t smem = sizeof(float4) * (size_t)apply_region_cells(th, a.s, a.S) +
-                                sizeof(uint32_t) * (size_t)(a.S * a.S) * (a.S * a.S);
+            const int th = kApplyVariants[v].rows;
+            const size_t region = sizeof(float4) * (size_t)apply_region_cells(th, a.s, a.S) +
+                                  sizeof(uint32_t) * (size_t)(a.S * a.S) * (a.S * a.S);
             const dim3 grid((a.W + kApplyTW - 1) / kApplyTW, (a.H + th - 1) / th);
+            if (kApplyVariants[v].tma == 2 && maps_for(th)) {
+                const int tiles_x = (a.W + kApplyTW - 1) / kApplyTW;
+                const int ntiles = tiles_x * ((a.H + th - 1) / th);
+                const size_t smem = 128 + 2 * (size_t)th * kApplyTW * (2 + wb) +
+                                    4 * (size_t)th * (kApplyTW / 2 * 3) * ob + 16 + region;
+                auto launch = [&](auto kern) -> int {
+                    if (smem > 48 * 1024 &&
+                        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem) != cudaSuccess)
+                        return GLU_ERR_CUDA;
+                    int dev = 0, sms = 148, per_sm = 1;
+                    GLU_CUDA_TRY(cudaGetDevice(&dev));
+                    GLU_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                    GLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256,
+                                                                               smem));
+                    const int grid = std::max(1, std::min(ntiles, sms * std::max(per_sm, 1)));
+                    kern<<<grid, 256, smem, st>>>(a, mcode, mw, mout, tiles_x, ntiles);
+                    GLU_LAUNCH_CHECK();
+                    return GLU_OK;
+                };
+                return apply_rows_dispatch<PipeK>(th, a.wfmt, vec16, launch);
+            }
+            if (kApplyVariants[v].tma == 1 && maps_for(th)) {
+                const size_t smem = 128 + (size_t)th * kApplyTW * (2 + wb) +
+                                    2 * (size_t)th * (kApplyTW / 2 * 3) * ob + 16 + region;
+                auto launch = [&](auto kern) -> int {
+                    if (smem > 48 * 1024 &&
+                        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem) != cudaSuccess)
+                        return GLU_ERR_CUDA;
+                    kern<<<grid, 256, smem, st>>>(a, mcode, mw, mout);
+                    GLU_LAUNCH_CHECK();
+                    return GLU_OK;
+                };
+                return apply_rows_dispatch<TmaK>(th, a.wfmt, vec16, launch);
+            }
             const int nthr = 32 * (th < 8 ? th : 8);
             auto launch = [&](auto kern) -> int {
-                if (smem > 48 * 1024 &&
+                if (region > 48 * 1024 &&
                     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem) != cudaSuccess)
+                                         (int)region) != cudaSuccess)
                     return GLU_ERR_CUDA;
-                kern<<<grid, nthr, smem, st>>>(a);
+                kern<<<grid, nthr, region, st>>>(a);
                 GLU_LAUNCH_CHECK();
                 return GLU_OK;
             };
-            return apply_tile_dispatch(v, a.wfmt, vec16, launch);
+            return apply_rows_dispatch<TileK>(th, a.wfmt, vec16, launch);
         };
         const int key[5] = {a.out_dtype, a.wfmt, a.S, a.s, tune_size_class((long long)a.H * a.W)};
         int v = 0;

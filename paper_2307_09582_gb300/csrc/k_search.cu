@@ -32,6 +32,24 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
+bool encode_map_2d(CUtensorMap* map, CUtensorMapDataType dt, size_t esize, const void* base,
+                   uint64_t inner, uint64_t rows, uint64_t row_bytes, uint32_t box_inner,
+                   uint32_t box_rows) {
+    auto enc = get_encode();
+    if (!enc || ((uintptr_t)base & 15u) != 0 || row_bytes % 16 != 0 ||
+        (box_inner * esize) % 16 != 0 || box_inner > 256 || box_rows > 256 || inner == 0 ||
+        rows == 0)
+        return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 bool make_hr_map(const SearchArgs& a, CUtensorMap* map, int tile_h) {
     auto enc = get_encode();
     if (!enc) return false;

@@ -127,7 +127,10 @@ int glu_tune_variant_name(int32_t kernel, int32_t variant, char* buf, int32_t ca
         snprintf(buf, (size_t)cap, "tile %dx%d, %d CTAs/SM, %s candidate loops", kTileW, sv.tile_h,
                  sv.min_blocks, sv.compact ? "rolled" : "row-unrolled");
     } else {
-        snprintf(buf, (size_t)cap, "tile 128x%d", kApplyVariantRows[variant]);
+        snprintf(buf, (size_t)cap, "tile 128x%d%s", kApplyVariants[variant].rows,
+                 kApplyVariants[variant].tma == 2   ? ", TMA pipeline (persistent)"
+                 : kApplyVariants[variant].tma == 1 ? ", TMA loads and stores"
+                                                    : "");
     }
     return GLU_OK;
 }

@@ -16,9 +16,16 @@ constexpr SearchVariant kSearchVariants[] = {
 };
 constexpr int kNumSearchVariants = (int)(sizeof(kSearchVariants) / sizeof(kSearchVariants[0]));
 
-// Eq. 1 apply, 3-channel float targets: rows of the 128-pixel-wide tiles.
+// Eq. 1 apply, 3-channel float targets: rows of the 128-pixel-wide tiles, and how the tile's
+// codes, weights and output move: plain loads and stores (0), TMA per tile (1), or TMA in a
+// persistent two-stage pipeline (2). Where the arrays do not allow TMA, a variant runs the
+// plain tiled kernel with the same rows.
 constexpr int kApplyTW = 128;
-constexpr int kApplyVariantRows[] = {16, 8, 32, 64};
-constexpr int kNumApplyVariants = (int)(sizeof(kApplyVariantRows) / sizeof(kApplyVariantRows[0]));
+struct ApplyVariant {
+    int rows, tma;
+};
+constexpr ApplyVariant kApplyVariants[] = {{16, 0}, {8, 0}, {32, 0}, {64, 0}, {16, 1},
+                                           {8, 1},  {32, 1}, {16, 2}, {8, 2},  {32, 2}};
+constexpr int kNumApplyVariants = (int)(sizeof(kApplyVariants) / sizeof(kApplyVariants[0]));
 
 }  // namespace glu

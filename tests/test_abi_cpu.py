@@ -185,12 +185,16 @@ def test_missing_library_fails_loudly(tmp_path):
 def test_tuner_host_side(lib):
     from paper_2307_09582_gb300 import _abi as A
     assert lib.glu_tune_variants(A.GLU_TUNE_SEARCH) == 5
-    assert lib.glu_tune_variants(A.GLU_TUNE_APPLY) == 4
+    assert lib.glu_tune_variants(A.GLU_TUNE_APPLY) == 10
     assert lib.glu_tune_variants(7) == A.GLU_ERR_INVALID_ARG
     buf = ctypes.create_string_buffer(128)
     assert lib.glu_tune_variant_name(A.GLU_TUNE_SEARCH, 0, buf, 128) == A.GLU_OK
     assert buf.value.startswith(b"tile 64x32")
-    assert lib.glu_tune_variant_name(A.GLU_TUNE_APPLY, 4, buf, 128) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_tune_variant_name(A.GLU_TUNE_APPLY, 4, buf, 128) == A.GLU_OK
+    assert buf.value == b"tile 128x16, TMA loads and stores"
+    assert lib.glu_tune_variant_name(A.GLU_TUNE_APPLY, 7, buf, 128) == A.GLU_OK
+    assert buf.value == b"tile 128x16, TMA pipeline (persistent)"
+    assert lib.glu_tune_variant_name(A.GLU_TUNE_APPLY, 10, buf, 128) == A.GLU_ERR_INVALID_ARG
     assert lib.glu_tune_force(A.GLU_TUNE_SEARCH, 5) == A.GLU_ERR_INVALID_ARG
     assert lib.glu_tune_force(A.GLU_TUNE_SEARCH, -1) == A.GLU_OK
     # export / import round trip of the text form

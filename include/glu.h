@@ -224,6 +224,19 @@ int glu_apply(const glu_theta* theta, const glu_image* lr_target, glu_image* hr_
 int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
                        const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* stream);
 
+/* The same adjoint with a caller workspace (device memory, 16-byte aligned, at least
+ * glu_apply_backward_workspace_size(theta, c) bytes: 8 c S^2 bytes per LR pixel; contents
+ * scratch). A pixel of LR block B reaches exactly two LR pixels, one per window index, so every
+ * block sums its pixels' contributions per window index once (raster order) into the slot of the
+ * LR pixel it feeds, and each LR pixel then adds its S^2 slots (neighbour order, a before b):
+ * every input is read once. Fixed summation order, no atomics: bit-reproducible (the order
+ * differs from glu_apply_backward's, so the two agree to rounding). GLU_ERR_WORKSPACE if ws is
+ * missing, misaligned or too small. */
+size_t glu_apply_backward_workspace_size(const glu_theta* theta, int32_t c);
+int glu_apply_backward_ws(const glu_theta* theta, const glu_image* lr_target,
+                          const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* ws,
+                          size_t ws_bytes, void* stream);
+
 /* Autotuner (not part of the method: implementation choice only). The Algorithm 1 search
  * (GLU_TUNE_SEARCH: tile height x CTAs per SM x candidate loop schedule) and the tiled Eq. 1
  * apply (GLU_TUNE_APPLY: tile height) have several implementation variants that compute the same

@@ -92,6 +92,9 @@ PROTOTYPES = {
     "glu_apply": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _vp]),
     "glu_apply_backward": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _P(GluImage),
                                           _vp, _vp]),
+    "glu_apply_backward_workspace_size": (ctypes.c_size_t, [_P(GluTheta), _i32]),
+    "glu_apply_backward_ws": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage),
+                                             _P(GluImage), _vp, _vp, ctypes.c_size_t, _vp]),
     "glu_joint_decisions": (ctypes.c_int64, [_vp, ctypes.c_size_t, _i32, _i32, _i32, _P(GluParams),
                                              _vp, _i64, _vp]),
     "glu_joint_profile": (ctypes.c_int, [_i32]),

@@ -345,10 +345,16 @@ def glu_apply(theta: Theta, lr_target: torch.Tensor, out: torch.Tensor | None = 
     return out
 
 
+_BW_WS = {}   # device -> workspace of the adjoint (grown on demand, reused across calls)
+
+
 def glu_apply_backward(theta: Theta, lr_target: torch.Tensor, grad_hr: torch.Tensor,
                        grad_lr: torch.Tensor | None = None, grad_w: torch.Tensor | bool = True,
-                       weight: torch.Tensor | None = None, stream=None):
-    """Adjoint of Eq. 1: returns (grad_lr, grad_w or None)."""
+                       weight: torch.Tensor | None = None, stream=None,
+                       workspace: torch.Tensor | bool | None = True):
+    """Adjoint of Eq. 1: returns (grad_lr, grad_w or None). With `workspace` (True: a cached
+    per-device buffer; or a uint8 tensor) the bucketed form glu_apply_backward_ws runs, without
+    it (None / False) the tiled glu_apply_backward."""
     if grad_lr is None:
         grad_lr = torch.empty_like(lr_target, dtype=torch.float32)
     if grad_w is True:
@@ -357,9 +363,26 @@ def glu_apply_backward(theta: Theta, lr_target: torch.Tensor, grad_hr: torch.Ten
         grad_w = None
     td = theta.desc(weight, A.GLU_W_F32 if weight is not None else None)
     ti, gi, go = image(lr_target), image(grad_hr), image(grad_lr)
-    A.check("glu_apply_backward", lib().glu_apply_backward(
+    if workspace is None or workspace is False:
+        A.check("glu_apply_backward", lib().glu_apply_backward(
+            ctypes.byref(td), ctypes.byref(ti), ctypes.byref(gi), ctypes.byref(go),
+            _ptr(grad_w), _stream(stream)))
+        return grad_lr, grad_w
+    C = lr_target.shape[2] if lr_target.dim() == 3 else 1
+    need = int(lib().glu_apply_backward_workspace_size(ctypes.byref(td), C))
+    if workspace is True:
+        dev = grad_hr.device
+        ws = _BW_WS.get(dev)
+        if ws is None or ws.numel() < need + 16:
+            ws = torch.empty(need + 16, dtype=torch.uint8, device=dev)
+            _BW_WS[dev] = ws
+    else:
+        ws = workspace
+    base = ws.data_ptr()
+    aligned = (base + 15) & ~15
+    A.check("glu_apply_backward_ws", lib().glu_apply_backward_ws(
         ctypes.byref(td), ctypes.byref(ti), ctypes.byref(gi), ctypes.byref(go), _ptr(grad_w),
-        _stream(stream)))
+        ctypes.c_void_p(aligned), ws.numel() - (aligned - base), _stream(stream)))
     return grad_lr, grad_w
 
 

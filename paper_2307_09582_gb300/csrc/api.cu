@@ -152,8 +152,12 @@ int glu_apply(const glu_theta* theta, const glu_image* lr_target, glu_image* hr_
     return launch_apply(a, (cudaStream_t)stream);
 }
 
-int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
-                       const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* stream) {
+}  // extern "C"
+
+namespace {
+// Arguments of the adjoint (shared by both entry points).
+int backward_args(const glu_theta* theta, const glu_image* lr_target, const glu_image* grad_hr,
+                  glu_image* grad_lr, float* grad_w, BackwardArgs& a) {
     if (!theta_ok(theta) || !image_ok(lr_target) || !image_ok(grad_hr) || !image_ok(grad_lr))
         return GLU_ERR_INVALID_ARG;
     if (lr_target->dtype != GLU_F32 || grad_hr->dtype != GLU_F32 || grad_lr->dtype != GLU_F32)
@@ -164,7 +168,6 @@ int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
         lr_target->w != lr_dim(theta->W, s) || grad_lr->h != lr_target->h ||
         grad_lr->w != lr_target->w)
         return GLU_ERR_SHAPE;
-    BackwardArgs a;
     a.code = theta->code;
     a.weight = theta->weight;
     a.wfmt = theta->wfmt;
@@ -182,7 +185,35 @@ int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
     a.gT = (float*)grad_lr->data;
     a.gT_pitch = grad_lr->pitch;
     a.gw = grad_w;
-    return launch_apply_backward(a, (cudaStream_t)stream);
+    return GLU_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
+                       const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* stream) {
+    BackwardArgs a;
+    const int rc = backward_args(theta, lr_target, grad_hr, grad_lr, grad_w, a);
+    return rc ? rc : launch_apply_backward(a, (cudaStream_t)stream);
+}
+
+size_t glu_apply_backward_workspace_size(const glu_theta* theta, int32_t c) {
+    if (!theta_ok(theta) || c < 1 || c > 4) return 0;
+    return apply_backward_workspace_bytes(lr_dim(theta->H, theta->scale),
+                                          lr_dim(theta->W, theta->scale), theta->S, c);
+}
+
+int glu_apply_backward_ws(const glu_theta* theta, const glu_image* lr_target,
+                          const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* ws,
+                          size_t ws_bytes, void* stream) {
+    BackwardArgs a;
+    const int rc = backward_args(theta, lr_target, grad_hr, grad_lr, grad_w, a);
+    if (rc) return rc;
+    if (!ws || ((uintptr_t)ws & 15u) != 0 ||
+        ws_bytes < apply_backward_workspace_bytes(a.h, a.w, a.S, a.C))
+        return GLU_ERR_WORKSPACE;
+    return launch_apply_backward_ws(a, ws, (cudaStream_t)stream);
 }
 
 size_t glu_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params) {

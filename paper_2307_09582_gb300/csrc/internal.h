@@ -71,6 +71,10 @@ struct BackwardArgs {
 };
 
 int launch_apply_backward(const BackwardArgs& a, cudaStream_t st);
+// The same with a caller workspace of apply_backward_workspace_bytes(h, w, S, C) bytes
+// (16-byte aligned): per-block window-bucket sums, then one gather per LR pixel.
+size_t apply_backward_workspace_bytes(int h, int w, int S, int C);
+int launch_apply_backward_ws(const BackwardArgs& a, void* ws, cudaStream_t st);
 
 int launch_downsample(const glu_image& hr, int s, int mode, const glu_image& lr, cudaStream_t st);
 

@@ -986,6 +986,196 @@ __global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_gw_tile(const
     }
 }
 
+// ------------------------------------------------------------------ adjoint with a workspace
+//
+// A pixel p of LR block B contributes to exactly two LR pixels: q_a = the pixel at window index
+// k_a of B's window (w_p G_p) and q_b (of k_b, (1 - w_p) G_p). Grouping B's pixels by window
+// index therefore gives, per bucket k, B's whole contribution to one LR pixel q = B + (k / S - r,
+// k % S - r), of which B is neighbour K - 1 - k (the window is symmetric). Two passes, each input
+// read once:
+//   k_bw_block_sums: a warp per block stages its pixels in shared memory (and, with grad_w,
+//     writes grad_w_p = G_p . (T_a - T_b) on the way); lane k sums bucket k (lanes k, k + 32,
+//     k + 64 for windows above 32 pixels) over the block's pixels in raster order and stores the
+//     sums in q's slot slots[q][K - 1 - k][a or b][c] of the workspace;
+//   k_bw_gather: a thread per LR pixel adds its slots, neighbours in order, a before b.
+// Every sum has a fixed order (bit-reproducible); no atomics. (Measured alternative: one fixed
+// butterfly per distinct window index of each 64-pixel chunk was slower on textured guides,
+// where a block holds many distinct indices.)
+constexpr int kBsChunk = 128;   // pixels a warp stages at a time
+template <int C, int NQ>
+__global__ void __launch_bounds__(256) k_bw_block_sums(const BackwardArgs P, float* slots) {
+    constexpr int CG = C == 3 ? 4 : C;           // gradient row padded to 16 bytes for C = 3
+    __shared__ int2 s_pw[8][kBsChunk];           // pair (k_a | k_b << 8), weight bits
+    __shared__ __align__(16) float s_g[8][kBsChunk * CG];
+    __shared__ float s_t[8][32 * NQ * C];        // the block's window of T (grad_w)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = (P.S - 1) >> 1, S = P.S, K = S * S, s = P.s;
+    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
+    const int64_t nblocks = (int64_t)P.h * P.w;
+    for (int64_t blk = (int64_t)blockIdx.x * 8 + warp; blk < nblocks;
+         blk += (int64_t)gridDim.x * 8) {
+        const int bv = (int)(blk / P.w), bu = (int)(blk - (int64_t)bv * P.w);
+        if (P.gw) {
+            // window cells inside the image (codes never select the others)
+            for (int k = lane; k < K; k += 32) {
+                const int kr = qdiv(k, invS);
+                const int v = min(max(bv + kr - r, 0), P.h - 1);
+                const int u = min(max(bu + (k - kr * S) - r, 0), P.w - 1);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    s_t[warp][k * C + c] = __ldg(&P.T[(int64_t)v * P.T_pitch + (int64_t)u * C + c]);
+            }
+            __syncwarp();
+        }
+        float acc_a[NQ][C], acc_b[NQ][C];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc_a[q][c] = acc_b[q][c] = 0.f;
+        const int ys = bv * s, xs = bu * s;
+        const int ey = min(s, P.H - ys), ex = min(s, P.W - xs), n = ey * ex;
+        const float inv_ex = 1.0f / (float)ex;
+        for (int j0 = 0; j0 < n; j0 += kBsChunk) {
+            const int m = min(kBsChunk, n - j0);
+            for (int jj = lane; jj < m; jj += 32) {
+                const int j = j0 + jj, jy = qdiv(j, inv_ex);
+                const int y = ys + jy, x = xs + (j - jy * ex);
+                const int64_t p = (int64_t)y * P.W + x;
+                const int code = P.code[p];
+                const float w = load_weight(P.weight, P.wfmt, p);
+                const int64_t og = (int64_t)y * P.G_pitch + (int64_t)x * C;
+                float g[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) g[c] = __ldcs(&P.G[og + c]);
+                const bool valid = code < K * K;
+                const int ka = qdiv(code, invK), kb = code - ka * K;
+                s_pw[warp][jj] = make_int2(valid ? (ka | (kb << 8)) : 0xFFFF, __float_as_int(w));
+                if (C == 3) {
+                    *(float4*)&s_g[warp][jj * CG] = make_float4(g[0], g[1], g[C - 1], 0.f);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) s_g[warp][jj * CG + c] = g[c];
+                }
+                if (P.gw) {
+                    float gw = 0.f;
+                    if (valid) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            gw = __fmaf_rn(g[c], s_t[warp][ka * C + c] - s_t[warp][kb * C + c], gw);
+                    } else {
+                        set_status(GLU_ERR_DEVICE_CHECK);
+                    }
+                    P.gw[p] = gw;
+                }
+            }
+            __syncwarp();
+#pragma unroll 4
+            for (int jj = 0; jj < m; ++jj) {
+                const int2 pw = s_pw[warp][jj];
+                const int ka = pw.x & 0xFF, kb = pw.x >> 8;   // 255: no pair
+                const float w = __int_as_float(pw.y);
+                float g[C];
+                if (C == 3) {
+                    const float4 g4 = *(const float4*)&s_g[warp][jj * CG];
+                    g[0] = g4.x;
+                    g[1] = g4.y;
+                    g[C - 1] = g4.z;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) g[c] = s_g[warp][jj * CG + c];
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int kk = lane + 32 * q;
+                    if (ka == kk) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c) acc_a[q][c] = __fmaf_rn(w, g[c], acc_a[q][c]);
+                    }
+                    if (kb == kk) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            acc_b[q][c] = __fmaf_rn(1.f - w, g[c], acc_b[q][c]);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        // bucket k feeds q = B + (k / S - r, k % S - r) as its neighbour K - 1 - k
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int kk = lane + 32 * q;
+            if (kk >= K) continue;
+            const int kr = qdiv(kk, invS);
+            const int qv = bv + kr - r, qu = bu + (kk - kr * S) - r;
+            if (qv < 0 || qv >= P.h || qu < 0 || qu >= P.w) continue;
+            float* o = slots + (((int64_t)qv * P.w + qu) * K + (K - 1 - kk)) * 2 * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                o[c] = acc_a[q][c];
+                o[C + c] = acc_b[q][c];
+            }
+        }
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_bw_gather(const BackwardArgs P, const float* slots) {
+    const int r = (P.S - 1) >> 1, S = P.S, K = S * S;
+    const float invS = 1.0f / (float)S;
+    const int64_t nq = (int64_t)P.h * P.w;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(q / P.w), u = (int)(q - (int64_t)v * P.w);
+        float acc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = 0.f;
+        const float* sl = slots + q * K * 2 * C;
+        for (int n = 0; n < K; ++n) {
+            // neighbour n is block q + (n / S - r, n % S - r); outside the image: no slot
+            const int nr = qdiv(n, invS);
+            const int bv = v + nr - r, bu = u + (n - nr * S) - r;
+            if (bv < 0 || bv >= P.h || bu < 0 || bu >= P.w) continue;
+            // L1-cached loads: a thread reads its slots' sectors in full, one after the other
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] += __ldg(&sl[n * 2 * C + c]);
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] += __ldg(&sl[n * 2 * C + C + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) P.gT[(int64_t)v * P.gT_pitch + (int64_t)u * C + c] = acc[c];
+    }
+}
+
+size_t apply_backward_workspace_bytes(int h, int w, int S, int C) {
+    return (size_t)h * w * (size_t)S * S * 2 * (size_t)C * sizeof(float);
+}
+
+template <int C>
+static int launch_bw_ws_t(const BackwardArgs& a, float* slots, cudaStream_t st) {
+    const int K = a.S * a.S;
+    const int64_t nblocks = (int64_t)a.h * a.w;
+    const int grid1 = grid_for(nblocks * 32, 256);
+    if (K <= 32) k_bw_block_sums<C, 1><<<grid1, 256, 0, st>>>(a, slots);
+    else if (K <= 64) k_bw_block_sums<C, 2><<<grid1, 256, 0, st>>>(a, slots);
+    else k_bw_block_sums<C, 3><<<grid1, 256, 0, st>>>(a, slots);
+    GLU_LAUNCH_CHECK();
+    k_bw_gather<C><<<grid_for(nblocks, 256), 256, 0, st>>>(a, slots);
+    GLU_LAUNCH_CHECK();
+    return GLU_OK;
+}
+
+int launch_apply_backward_ws(const BackwardArgs& a, void* ws, cudaStream_t st) {
+    if (a.H <= 0 || a.W <= 0) return GLU_OK;
+    float* slots = (float*)ws;
+    switch (a.C) {
+        case 1: return launch_bw_ws_t<1>(a, slots, st);
+        case 2: return launch_bw_ws_t<2>(a, slots, st);
+        case 3: return launch_bw_ws_t<3>(a, slots, st);
+        case 4: return launch_bw_ws_t<4>(a, slots, st);
+        default: return GLU_ERR_UNSUPPORTED;
+    }
+}
+
 template <int C>
 static int launch_bw_t(const BackwardArgs& a, cudaStream_t st) {
     const int threads = 256;

@@ -182,6 +182,27 @@ def test_missing_library_fails_loudly(tmp_path):
         A.load(str(tmp_path / "libglu.so"))
 
 
+def test_backward_workspace_host_side(lib):
+    from paper_2307_09582_gb300 import _abi as A
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
+    th = A.GluTheta(fake, fake, 64, 80, 8, 5, A.GLU_W_F32)
+    # 8 c S^2 bytes per LR pixel (8 x 10 LR pixels)
+    assert lib.glu_apply_backward_workspace_size(ctypes.byref(th), 3) == 8 * 10 * 8 * 3 * 25
+    assert lib.glu_apply_backward_workspace_size(ctypes.byref(th), 5) == 0
+    T = A.GluImage(fake, 8, 10, 3, A.GLU_F32, 30)
+    G = A.GluImage(fake, 64, 80, 3, A.GLU_F32, 240)
+    gT = A.GluImage(fake, 8, 10, 3, A.GLU_F32, 30)
+    need = lib.glu_apply_backward_workspace_size(ctypes.byref(th), 3)
+    args = (ctypes.byref(th), ctypes.byref(T), ctypes.byref(G), ctypes.byref(gT), None)
+    assert lib.glu_apply_backward_ws(*args, fake, need - 1, None) == A.GLU_ERR_WORKSPACE
+    assert lib.glu_apply_backward_ws(*args, ctypes.c_void_p(0x1004), need, None) == \
+        A.GLU_ERR_WORKSPACE
+    assert lib.glu_apply_backward_ws(*args, None, need, None) == A.GLU_ERR_WORKSPACE
+    G_bad = A.GluImage(fake, 64, 81, 3, A.GLU_F32, 243)
+    assert lib.glu_apply_backward_ws(ctypes.byref(th), ctypes.byref(T), ctypes.byref(G_bad),
+                                     ctypes.byref(gT), None, fake, need, None) == A.GLU_ERR_SHAPE
+
+
 def test_tuner_host_side(lib):
     from paper_2307_09582_gb300 import _abi as A
     assert lib.glu_tune_variants(A.GLU_TUNE_SEARCH) == 5

@@ -29,15 +29,18 @@ def make_theta(api, H, W, s, S, seed=1):
     return img, hr, lr, theta
 
 
+@pytest.mark.parametrize("ws", [True, None])
 @pytest.mark.parametrize("H,W,s,S,C", [(250, 347, 8, 5, 3), (96, 96, 8, 3, 3), (97, 131, 3, 3, 1),
-                                       (64, 80, 16, 5, 4), (50, 70, 2, 9, 3)])
-def test_backward_matches_fp64_oracle(api, H, W, s, S, C):
+                                       (64, 80, 16, 5, 4), (50, 70, 2, 9, 3), (90, 100, 7, 7, 2),
+                                       (300, 200, 64, 3, 3), (130, 250, 128, 5, 1)])
+def test_backward_matches_fp64_oracle(api, H, W, s, S, C, ws):
+    """Both forms: the bucketed one with a workspace (ws=True) and the tiled one (ws=None)."""
     _, _, _, theta = make_theta(api, H, W, s, S)
     h, w = api.lr_dims(H, W, s)
     g = torch.Generator().manual_seed(3)
     T = torch.rand((h, w, C), generator=g).cuda()
     G = torch.randn((H, W, C), generator=g).cuda()
-    gT, gw = api.glu_apply_backward(theta, T, G)
+    gT, gw = api.glu_apply_backward(theta, T, G, workspace=ws)
     torch.cuda.synchronize()
     K = S * S
     codes = theta.codes_i32().cpu().numpy()
@@ -54,7 +57,7 @@ def test_backward_matches_fp64_oracle(api, H, W, s, S, C):
     assert np.all(np.abs(gT.cpu().numpy() - rT) <= tol)
     assert np.abs(gw.cpu().numpy() - rw).max() < 1e-5
     # deterministic: bitwise identical on a second call
-    gT2, gw2 = api.glu_apply_backward(theta, T, G)
+    gT2, gw2 = api.glu_apply_backward(theta, T, G, workspace=ws)
     torch.cuda.synchronize()
     assert torch.equal(gT, gT2) and torch.equal(gw, gw2)
 

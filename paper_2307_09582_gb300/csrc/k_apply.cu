@@ -1118,31 +1118,50 @@ __global__ void __launch_bounds__(256) k_bw_block_sums(const BackwardArgs P, flo
     }
 }
 
+// The slots of 32 consecutive LR pixels are one contiguous run of 32 K 2C floats: the CTA copies
+// it into shared memory with 16-byte coalesced loads, then thread i adds pixel i's slots in order.
+constexpr int kGatherQ = 32;
 template <int C>
-__global__ void __launch_bounds__(256) k_bw_gather(const BackwardArgs P, const float* slots) {
+__global__ void __launch_bounds__(128) k_bw_gather(const BackwardArgs P, const float* slots) {
+    extern __shared__ float4 gsm4[];
+    float* gsm = (float*)gsm4;
     const int r = (P.S - 1) >> 1, S = P.S, K = S * S;
     const float invS = 1.0f / (float)S;
+    const int per_q = K * 2 * C;                        // floats of one LR pixel's slots
     const int64_t nq = (int64_t)P.h * P.w;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int v = (int)(q / P.w), u = (int)(q - (int64_t)v * P.w);
-        float acc[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = 0.f;
-        const float* sl = slots + q * K * 2 * C;
-        for (int n = 0; n < K; ++n) {
-            // neighbour n is block q + (n / S - r, n % S - r); outside the image: no slot
-            const int nr = qdiv(n, invS);
-            const int bv = v + nr - r, bu = u + (n - nr * S) - r;
-            if (bv < 0 || bv >= P.h || bu < 0 || bu >= P.w) continue;
-            // L1-cached loads: a thread reads its slots' sectors in full, one after the other
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] += __ldg(&sl[n * 2 * C + c]);
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] += __ldg(&sl[n * 2 * C + C + c]);
+    for (int64_t q0 = (int64_t)blockIdx.x * kGatherQ; q0 < nq;
+         q0 += (int64_t)gridDim.x * kGatherQ) {
+        const int nqc = (int)min((int64_t)kGatherQ, nq - q0);
+        const int nf = nqc * per_q;                     // a multiple of 2; of 4 when nqc = 32
+        const float* src = slots + q0 * per_q;          // 16-byte aligned when q0 % 32 == 0
+        __syncthreads();                                // the previous chunk's readers are done
+        if (nqc == kGatherQ) {
+            const float4* s4 = (const float4*)src;
+            for (int i = threadIdx.x; i < nf / 4; i += blockDim.x) gsm4[i] = __ldcs(&s4[i]);
+        } else {
+            for (int i = threadIdx.x; i < nf; i += blockDim.x) gsm[i] = __ldcs(&src[i]);
         }
+        __syncthreads();
+        if (threadIdx.x < nqc) {
+            const int64_t q = q0 + threadIdx.x;
+            const int v = (int)(q / P.w), u = (int)(q - (int64_t)v * P.w);
+            const float* sl = gsm + threadIdx.x * per_q;
+            float acc[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) P.gT[(int64_t)v * P.gT_pitch + (int64_t)u * C + c] = acc[c];
+            for (int c = 0; c < C; ++c) acc[c] = 0.f;
+            for (int n = 0; n < K; ++n) {
+                // neighbour n is block q + (n / S - r, n % S - r); outside the image: no slot
+                const int nr = qdiv(n, invS);
+                const int bv = v + nr - r, bu = u + (n - nr * S) - r;
+                if (bv < 0 || bv >= P.h || bu < 0 || bu >= P.w) continue;
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] += sl[n * 2 * C + c];
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] += sl[n * 2 * C + C + c];
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) P.gT[(int64_t)v * P.gT_pitch + (int64_t)u * C + c] = acc[c];
+        }
     }
 }
 
@@ -1159,7 +1178,13 @@ static int launch_bw_ws_t(const BackwardArgs& a, float* slots, cudaStream_t st) 
     else if (K <= 64) k_bw_block_sums<C, 2><<<grid1, 256, 0, st>>>(a, slots);
     else k_bw_block_sums<C, 3><<<grid1, 256, 0, st>>>(a, slots);
     GLU_LAUNCH_CHECK();
-    k_bw_gather<C><<<grid_for(nblocks, 256), 256, 0, st>>>(a, slots);
+    const size_t gsm = sizeof(float) * (size_t)kGatherQ * K * 2 * C;   // <= 83 KB (9x9, c = 4)
+    if (gsm > 48 * 1024 &&
+        cudaFuncSetAttribute(k_bw_gather<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gsm) != cudaSuccess)
+        return GLU_ERR_CUDA;
+    k_bw_gather<C><<<grid_for((nblocks + kGatherQ - 1) / kGatherQ * 128, 128), 128, gsm, st>>>(
+        a, slots);
     GLU_LAUNCH_CHECK();
     return GLU_OK;
 }

@@ -366,6 +366,60 @@ int oracle_apply_adjoint(const int32_t* ka, const int32_t* kb, const double* ome
     return OR_OK;
 }
 
+/* ------------------------------------- least-squares LR colour update (non-paper, NEXT-F4) */
+
+/* One update of the LR colours L for a fixed Theta: every LR pixel q independently takes the
+ * value that minimises the reconstruction error sum_p || T_hat_p - I_p ||^2 of Eq. 1 (T = L)
+ * with every other LR pixel held at its current value (a Jacobi sweep of the normal equations).
+ * Pixel p reconstructs c_pa L_a + c_pb L_b with c_pa = omega_p, c_pb = 1 - omega_p, or L_a alone
+ * (c = 1) when a_p = b_p; so q collects, over the pixels that use it,
+ *     num_q += c_pq (I_p - c_pj L_j)   (j the other LR pixel of p, if any),   den_q += c_pq^2,
+ * and L'_q = num_q / den_q clamped to the colour range [0, unit]; an LR pixel no pixel uses keeps
+ * its value. Sums in raster order of p. */
+int oracle_ls_update(const double* I, int H, int W, const double* L, int s, int S,
+                     const int32_t* ka, const int32_t* kb, const double* omega, double unit,
+                     double* Lout) {
+    if (!I || !L || !ka || !kb || !omega || !Lout || H <= 0 || W <= 0 || s <= 0 || S <= 0 ||
+        !(S & 1) || !(unit > 0.0))
+        return OR_EINVAL;
+    int h, w;
+    oracle_lr_dims(H, W, s, &h, &w);
+    size_t nq = (size_t)h * w;
+    double* num = (double*)calloc(nq * 3, sizeof(double));
+    double* den = (double*)calloc(nq, sizeof(double));
+    if (!num || !den) {
+        free(num);
+        free(den);
+        return OR_ENOMEM;
+    }
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            size_t a = lr_index(y, x, s, S, ka[p], w), b = lr_index(y, x, s, S, kb[p], w);
+            const double* Ip = &I[p * 3];
+            if (a == b) {
+                for (int c = 0; c < 3; ++c) num[a * 3 + c] += Ip[c];
+                den[a] += 1.0;
+                continue;
+            }
+            double ca = omega[p], cb = 1.0 - omega[p];
+            for (int c = 0; c < 3; ++c) {
+                num[a * 3 + c] += ca * (Ip[c] - cb * L[b * 3 + c]);
+                num[b * 3 + c] += cb * (Ip[c] - ca * L[a * 3 + c]);
+            }
+            den[a] += ca * ca;
+            den[b] += cb * cb;
+        }
+    for (size_t q = 0; q < nq; ++q)
+        for (int c = 0; c < 3; ++c) {
+            double v = den[q] > 0.0 ? num[q * 3 + c] / den[q] : L[q * 3 + c];
+            Lout[q * 3 + c] = v < 0.0 ? 0.0 : (v > unit ? unit : v);
+        }
+    free(num);
+    free(den);
+    return OR_OK;
+}
+
 /* --------------------------------------------------- connected components (Algorithm 2, step 3) */
 
 /* Label the set pixels of mask; components numbered 0..M-1 in ascending order of their smallest

@@ -13,6 +13,9 @@ copies of guide pixels). Each C routine follows one equation or algorithm of the
   apply / apply_adjoint              Eq. 1 and its adjoint
   label_components                   connected components of Algorithm 2
   joint                              Algorithm 2 (PAPER and STRICT readings)
+  ls_update / ls_joint               a least-squares LR colour update alternated with Algorithm 1
+                                     (not the paper's method: the alternative joint scheme the
+                                     GPU path offers beside Algorithm 2)
 """
 from __future__ import annotations
 
@@ -45,6 +48,7 @@ def _lib():
             "oracle_label_components": [_p, _i, _i, _i, _p],
             "oracle_joint": [_p, _i, _i, _i, _i, _d, _d, _d, _i, _i, _i, _p, _p, _p, _p, _p, _p,
                              _p, ctypes.c_int64, _p, ctypes.c_int64, _d, _i],
+            "oracle_ls_update": [_p, _i, _i, _p, _i, _i, _p, _p, _p, _d, _p],
             "oracle_op_box3": [_p, _i, _i, _i, _p],
             "oracle_op_gauss3": [_p, _i, _i, _i, _p],
             "oracle_op_saturation": [_p, ctypes.c_size_t, _d, _p],
@@ -250,6 +254,45 @@ def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap
         L = L.astype(np.uint8)
     return dict(L=L, ka=ka, kb=kb, omega=om, err=er, R0=float(stats[0]), iters=iters,
                 accept_log=log[:min(nlog, log_cap)].copy())
+
+
+def ls_update(I, L, s, S, ka, kb, omega):
+    """One least-squares LR colour update for a fixed Theta (see glu_oracle.c). I: uint8 or
+    float guide; L: float LR colours in [0, 1]. Returns float64 LR colours in [0, 1]."""
+    (I,), unit = colours(I)
+    Lf = np.ascontiguousarray(np.asarray(L, np.float64) * unit)
+    H, W, _ = I.shape
+    out = np.empty_like(Lf)
+    _chk(_lib().oracle_ls_update(_ptr(I), H, W, _ptr(Lf), s, S,
+                                 _ptr(np.ascontiguousarray(ka, np.int32)),
+                                 _ptr(np.ascontiguousarray(kb, np.int32)),
+                                 _ptr(np.ascontiguousarray(omega, np.float64)), unit, _ptr(out)),
+         "ls_update")
+    return out / unit
+
+
+def ls_joint(I, s, S, N=3, eps=1e-3, L0=None):
+    """Alternate Algorithm 1 (reassignment) and ls_update (LR colour update), starting from the
+    grid-downsampled guide (or L0, colours in [0, 1]): an update is kept only if the residual
+    R = sum_p E_p of Algorithm 1 on the new LR image is below the current one; the first that is
+    not ends the loop. Returns dict(L (float64, [0, 1]), ka, kb, omega, err, R0, residuals)."""
+    I = np.asarray(I)
+    if L0 is None:
+        L0 = to_unit(downsample_grid(I, s))
+    L = np.asarray(L0, np.float64)
+    f = glu_fast(I, L, s, S, eps=eps)
+    R = float(f["err"].sum())
+    out = dict(R0=R, residuals=[])
+    for _ in range(N):
+        Ln = ls_update(I, L, s, S, f["ka"], f["kb"], f["omega"])
+        fn = glu_fast(I, Ln, s, S, eps=eps)
+        Rn = float(fn["err"].sum())
+        if not Rn < R:
+            break
+        L, f, R = Ln, fn, Rn
+        out["residuals"].append(R)
+    out.update(L=L, ka=f["ka"], kb=f["kb"], omega=f["omega"], err=f["err"])
+    return out
 
 
 def op_box3(X):

@@ -386,3 +386,87 @@ def test_lr_operators_closed_forms():
     gray = np.full((2, 2, 3), 0.4)
     assert np.allclose(O.op_saturation(gray, 1.3), 0.4)
     assert O.op_gamma(np.array([[[0.5]]]), 0.8)[0, 0, 0] == pytest.approx(math.exp(0.8 * math.log(0.5)))
+
+
+# ------------------------------------------------ least-squares LR colour update (non-paper)
+
+def _random_pairs(rng, H, W, s, S, equal_frac=0.2):
+    """Random valid window pairs (some with k_a = k_b) and weights in [0, 1]."""
+    h, w = O.lr_dims(H, W, s)
+    r = (S - 1) // 2
+    ka = np.empty((H, W), np.int32)
+    kb = np.empty((H, W), np.int32)
+    for y in range(H):
+        for x in range(W):
+            valid = [k for k in range(S * S)
+                     if 0 <= y // s + k // S - r < h and 0 <= x // s + k % S - r < w]
+            ka[y, x] = rng.choice(valid)
+            kb[y, x] = ka[y, x] if rng.random() < equal_frac else rng.choice(valid)
+    return ka, kb, rng.random((H, W))
+
+
+@pytest.mark.parametrize("seed,s,S", [(0, 4, 3), (1, 3, 5), (2, 5, 3)])
+def test_ls_update_is_coordinatewise_least_squares(seed, s, S):
+    """Each new LR colour is the least-squares solution (numpy lstsq, one unknown per channel)
+    of the reconstruction errors of the pixels that use it, the other LR colours held fixed;
+    clamped to [0, 1]."""
+    rng = np.random.default_rng(seed)
+    H, W = 13, 11
+    h, w = O.lr_dims(H, W, s)
+    I = rng.random((H, W, 3))
+    L = rng.random((h, w, 3))
+    ka, kb, om = _random_pairs(rng, H, W, s, S)
+    out = O.ls_update(I, L, s, S, ka, kb, om)
+    r = (S - 1) // 2
+    rows = {}
+    for y in range(H):
+        for x in range(W):
+            def lr(k):
+                return (y // s + k // S - r) * w + (x // s + k % S - r)
+            a, b = lr(ka[y, x]), lr(kb[y, x])
+            if a == b:
+                rows.setdefault(a, []).append((1.0, I[y, x]))
+                continue
+            wa = om[y, x]
+            La, Lb = L.reshape(-1, 3)[a], L.reshape(-1, 3)[b]
+            rows.setdefault(a, []).append((wa, I[y, x] - (1 - wa) * Lb))
+            rows.setdefault(b, []).append((1 - wa, I[y, x] - wa * La))
+    for q in range(h * w):
+        got = out.reshape(-1, 3)[q]
+        if q not in rows:
+            assert np.array_equal(got, L.reshape(-1, 3)[q])
+            continue
+        A = np.array([[c] for c, _ in rows[q]])
+        t = np.array([tt for _, tt in rows[q]])
+        if not np.any(A):
+            continue
+        x = np.linalg.lstsq(A, t, rcond=None)[0][0]
+        assert np.allclose(got, np.clip(x, 0.0, 1.0), atol=1e-12)
+
+
+@pytest.mark.parametrize("S", [3, 5])
+def test_ls_update_keeps_an_exactly_representable_lr_image(S):
+    """A guide that is the nearest-neighbour upsampling of an LR image is reconstructed exactly
+    (E = 0) from its grid downsampling, so that LR image is a fixed point of the update."""
+    rng = np.random.default_rng(S)
+    s = 4
+    Lu8 = rand_img(rng, 5, 6)
+    I = np.repeat(np.repeat(Lu8, s, axis=0), s, axis=1)
+    L0 = O.to_unit(O.downsample_grid(I, s))
+    f = O.glu_fast(I, L0, s, S)
+    assert np.all(f["err"] == 0.0)
+    out = O.ls_update(I, L0, s, S, f["ka"], f["kb"], f["omega"])
+    assert np.allclose(out, L0, atol=1e-12)
+    r = O.ls_joint(I, s, S, N=3)
+    assert r["R0"] == 0.0 and r["residuals"] == []
+
+
+def test_ls_joint_residuals_decrease_and_state_is_consistent():
+    from paper_2307_09582_gb300.inputs import Scene, render_u8
+    img = render_u8(Scene(width=96, height=80, n_cells=10, n_dots=12, n_lines=2, seed=4))
+    r = O.ls_joint(img, 8, 3, N=4)
+    R = [r["R0"]] + r["residuals"]
+    assert len(R) > 1 and all(b < a for a, b in zip(R, R[1:]))
+    f = O.glu_fast(img, r["L"], 8, 3)
+    assert np.array_equal(f["ka"], r["ka"]) and np.allclose(f["err"], r["err"])
+    assert abs(float(f["err"].sum()) - R[-1]) < 1e-9

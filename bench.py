@@ -404,6 +404,23 @@ def measure_extras(api, torch, img, dev, flush, stream):
     res["exact_ms"] = ms_e
     res["exact_alu_frac"] = (H * W * pairs * EXACT_OPS_PER_PAIR / (ms_e / 1e3)) / (
         torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2.07e9)
+    # the least-squares LR update alternated with Algorithm 1 (not the paper's method) beside
+    # Algorithm 2 on the same guide, window and iteration count: time and final residual
+    pl = api.glu_params(S=WIN, N=NITER)
+    wl = torch.empty(api.glu_ls_joint_workspace_size(H, W, SCALE, pl) + 256, dtype=torch.uint8,
+                     device=dev)
+    lr_l = torch.empty((h, w, 3), dtype=torch.float32, device=dev)
+    th_l = api.Theta.empty(H, W, SCALE, WIN, api.GLU_W_F32, dev)
+    ms_l = timed(lambda: api.glu_ls_joint_optimize(hr, SCALE, pl, lr_out=lr_l, theta=th_l,
+                                                   err_map=False, stats=False, workspace=wl),
+                 reps=5)
+    _, _, _, st_l = api.glu_ls_joint_optimize(hr, SCALE, pl, lr_out=lr_l, theta=th_l,
+                                              err_map=False, workspace=wl)
+    _, _, _, st_j = api.glu_joint_optimize(hr, SCALE, pl, err_map=False)
+    res["ls_joint"] = dict(ms=ms_l, R0=st_l["R0"], kept=st_l["kept"],
+                           residual=([st_l["R0"]] + st_l["residuals"])[st_l["kept"]],
+                           alg2_residual=st_j["iters"][-1]["residual"] if st_j["iters"]
+                           else st_j["R0"])
     res["batch16"] = measure_batch(api, torch, dev, timed)
     if VIDEO_FRAMES > 0:
         res["video"] = measure_video(api, torch, dev, VIDEO_FRAMES)

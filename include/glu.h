@@ -237,6 +237,39 @@ int glu_apply_backward_ws(const glu_theta* theta, const glu_image* lr_target,
                           const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* ws,
                           size_t ws_bytes, void* stream);
 
+/* Least-squares LR colour update (an alternative joint scheme beside Algorithm 2; not the
+ * paper's method). For a fixed Theta every LR pixel q takes, independently, the colour that
+ * minimises the Eq. 1 reconstruction error sum_p || T_hat_p - I_p ||^2 (T = the LR image) with
+ * the other LR pixels held at their current values: with c_pa = w_p, c_pb = 1 - w_p (or the single
+ * coefficient 1 when a_p = b_p), num_q = sum_p c_pq (I_p - c_pj L_j), den_q = sum_p c_pq^2 over the
+ * pixels that use q, L'_q = num_q / den_q clamped to [0, 1]; an LR pixel no pixel uses keeps its
+ * colour. Per-LR-pixel sums in FP32 with Kahan compensation in a fixed order (bit-reproducible).
+ *  hr: U8 or F16 guide (3 channels); theta: F32 weights; lr_in / lr_out: F32, 3 channels, LR size
+ *  (distinct buffers); ws: glu_ls_update_workspace_size(theta) bytes (32 S^2 per LR pixel),
+ *  16-byte aligned. */
+size_t glu_ls_update_workspace_size(const glu_theta* theta);
+int glu_ls_update(const glu_image* hr, const glu_theta* theta, const glu_image* lr_in,
+                  glu_image* lr_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Alternation of Algorithm 1 (reassignment) and glu_ls_update (LR colour update), starting from
+ * grid downsampling: after each update Algorithm 1 runs on the new LR image, and the new state
+ * (LR image, Theta, E) is kept only if its residual R = sum_p E_p is below the current one; the
+ * first update that is not kept ends the loop (the remaining iterations change nothing). At most
+ * params->N iterations; params->mode must be GLU_MODE_FAST. lr_out: F32, 3 channels; theta: F32
+ * weights; err_map nullable; stats (nullable, host) synchronises the stream once at the end.
+ * ws: glu_ls_joint_workspace_size bytes, 256-byte aligned. */
+typedef struct {
+    double R0;                          /* residual of the grid-downsampled start */
+    double residual[GLU_MAX_ITERS];     /* residual of each iteration's candidate state (0 for
+                                           iterations after the loop stopped) */
+    int32_t iterations;                 /* candidate states computed (N) */
+    int32_t kept;                       /* the last kept iteration (0: none) */
+} glu_ls_stats;
+size_t glu_ls_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params);
+int glu_ls_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
+                          glu_image* lr_out, glu_theta* theta, float* err_map,
+                          glu_ls_stats* stats, void* ws, size_t ws_bytes, void* stream);
+
 /* Autotuner (not part of the method: implementation choice only). The Algorithm 1 search
  * (GLU_TUNE_SEARCH: tile height x CTAs per SM x candidate loop schedule) and the tiled Eq. 1
  * apply (GLU_TUNE_APPLY: tile height) have several implementation variants that compute the same

@@ -54,6 +54,13 @@ class GluJointStats(ctypes.Structure):
                 ("searched", ctypes.c_int64 * GLU_MAX_ITERS)]
 
 
+class GluLsStats(ctypes.Structure):
+    _fields_ = [("R0", ctypes.c_double),
+                ("residual", ctypes.c_double * GLU_MAX_ITERS),
+                ("iterations", ctypes.c_int32),
+                ("kept", ctypes.c_int32)]
+
+
 class GluBatchItem(ctypes.Structure):
     _fields_ = [("hr", GluImage), ("lr", GluImage), ("theta", GluTheta),
                 ("err_map", ctypes.c_void_p)]
@@ -93,6 +100,13 @@ PROTOTYPES = {
     "glu_apply_backward": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _P(GluImage),
                                           _vp, _vp]),
     "glu_apply_backward_workspace_size": (ctypes.c_size_t, [_P(GluTheta), _i32]),
+    "glu_ls_update_workspace_size": (ctypes.c_size_t, [_P(GluTheta)]),
+    "glu_ls_update": (ctypes.c_int, [_P(GluImage), _P(GluTheta), _P(GluImage), _P(GluImage), _vp,
+                                     ctypes.c_size_t, _vp]),
+    "glu_ls_joint_workspace_size": (ctypes.c_size_t, [_i32, _i32, _i32, _P(GluParams)]),
+    "glu_ls_joint_optimize": (ctypes.c_int, [_P(GluImage), _i32, _P(GluParams), _P(GluImage),
+                                             _P(GluTheta), _vp, _P(GluLsStats), _vp,
+                                             ctypes.c_size_t, _vp]),
     "glu_apply_backward_ws": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage),
                                              _P(GluImage), _vp, _vp, ctypes.c_size_t, _vp]),
     "glu_joint_decisions": (ctypes.c_int64, [_vp, ctypes.c_size_t, _i32, _i32, _i32, _P(GluParams),

@@ -386,6 +386,64 @@ def glu_apply_backward(theta: Theta, lr_target: torch.Tensor, grad_hr: torch.Ten
     return grad_lr, grad_w
 
 
+def glu_ls_update(hr: torch.Tensor, theta: Theta, lr_in: torch.Tensor,
+                  lr_out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """One least-squares LR colour update for a fixed Theta (float32 weights); lr_in / lr_out
+    float32 h x w x 3 in [0, 1]. Not the paper's method (see glu.h)."""
+    if lr_out is None:
+        lr_out = torch.empty_like(lr_in)
+    td = theta.desc()
+    need = int(lib().glu_ls_update_workspace_size(ctypes.byref(td)))
+    if workspace is None:
+        workspace = torch.empty(need + 16, dtype=torch.uint8, device=hr.device)
+    base = workspace.data_ptr()
+    aligned = (base + 15) & ~15
+    hi, li, lo = image(hr), image(lr_in), image(lr_out)
+    A.check("glu_ls_update", lib().glu_ls_update(
+        ctypes.byref(hi), ctypes.byref(td), ctypes.byref(li), ctypes.byref(lo),
+        ctypes.c_void_p(aligned), workspace.numel() - (aligned - base), _stream(stream)))
+    return lr_out
+
+
+def glu_ls_joint_workspace_size(H: int, W: int, scale: int, params: A.GluParams) -> int:
+    return int(lib().glu_ls_joint_workspace_size(H, W, scale, ctypes.byref(params)))
+
+
+def glu_ls_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
+                          lr_out: torch.Tensor | None = None, theta: Theta | None = None,
+                          err_map: torch.Tensor | bool | None = True, stats: bool = True,
+                          workspace: torch.Tensor | None = None, stream=None):
+    """Algorithm 1 alternated with the least-squares LR colour update. Returns (lr (float32),
+    theta, err_map or None, stats dict or None)."""
+    H, W = hr.shape[:2]
+    h, w = lr_dims(H, W, scale)
+    if lr_out is None:
+        lr_out = torch.empty((h, w, 3), dtype=torch.float32, device=hr.device)
+    if theta is None:
+        theta = Theta.empty(H, W, scale, params.S, A.GLU_W_F32, hr.device)
+    if err_map is True:
+        err_map = torch.empty((H, W), dtype=torch.float32, device=hr.device)
+    elif err_map is False:
+        err_map = None
+    need = glu_ls_joint_workspace_size(H, W, scale, params)
+    if workspace is None or workspace.numel() < need + 256:
+        workspace = torch.empty(need + 256, dtype=torch.uint8, device=hr.device)
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    st = A.GluLsStats() if stats else None
+    hi, li, td = image(hr), image(lr_out), theta.desc()
+    A.check("glu_ls_joint_optimize", lib().glu_ls_joint_optimize(
+        ctypes.byref(hi), scale, ctypes.byref(params), ctypes.byref(li), ctypes.byref(td),
+        _ptr(err_map), ctypes.byref(st) if st is not None else None, ctypes.c_void_p(aligned),
+        workspace.numel() - (aligned - base), _stream(stream)))
+    sd = None
+    if st is not None:
+        sd = dict(R0=st.R0, residuals=[st.residual[i] for i in range(st.iterations)],
+                  kept=st.kept)
+    return lr_out, theta, err_map, sd
+
+
 def glu_joint_profile(enable: bool) -> None:
     A.check("glu_joint_profile", lib().glu_joint_profile(1 if enable else 0))
 

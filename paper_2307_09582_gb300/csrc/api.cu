@@ -71,9 +71,9 @@ const char* glu_version(void) { return "glu-gb300 0.1 (sm_103a)"; }
 
 int glu_device_status(void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    int codes[5] = {read_and_clear_status_search(st), read_and_clear_status_apply(st),
+    int codes[6] = {read_and_clear_status_search(st), read_and_clear_status_apply(st),
                     read_and_clear_status_down(st), read_and_clear_status_joint(st),
-                    read_and_clear_status_search_exact(st)};
+                    read_and_clear_status_search_exact(st), read_and_clear_status_ls(st)};
     for (int c : codes)
         if (c != GLU_OK) return c;
     return GLU_OK;
@@ -196,6 +196,95 @@ int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
     BackwardArgs a;
     const int rc = backward_args(theta, lr_target, grad_hr, grad_lr, grad_w, a);
     return rc ? rc : launch_apply_backward(a, (cudaStream_t)stream);
+}
+
+size_t glu_ls_update_workspace_size(const glu_theta* theta) {
+    if (!theta_ok(theta)) return 0;
+    return ls_update_workspace_bytes(lr_dim(theta->H, theta->scale),
+                                     lr_dim(theta->W, theta->scale), theta->S);
+}
+
+int glu_ls_update(const glu_image* hr, const glu_theta* theta, const glu_image* lr_in,
+                  glu_image* lr_out, void* ws, size_t ws_bytes, void* stream) {
+    if (!image_ok(hr) || !theta_ok(theta) || !image_ok(lr_in) || !image_ok(lr_out))
+        return GLU_ERR_INVALID_ARG;
+    if ((hr->dtype != GLU_U8 && hr->dtype != GLU_F16) || hr->c != 3 || lr_in->c != 3 ||
+        lr_out->c != 3 || lr_in->dtype != GLU_F32 || lr_out->dtype != GLU_F32 ||
+        theta->wfmt != GLU_W_F32 || lr_in->data == lr_out->data)
+        return GLU_ERR_UNSUPPORTED;
+    const int s = theta->scale, h = lr_dim(theta->H, s), w = lr_dim(theta->W, s);
+    if (hr->h != theta->H || hr->w != theta->W || lr_in->h != h || lr_in->w != w ||
+        lr_out->h != h || lr_out->w != w)
+        return GLU_ERR_SHAPE;
+    if (!ws || ((uintptr_t)ws & 15u) != 0 || ws_bytes < ls_update_workspace_bytes(h, w, theta->S))
+        return GLU_ERR_WORKSPACE;
+    LsUpdate u;
+    u.hr = hr->data;
+    u.hr_pitch = hr->pitch;
+    u.hr_dtype = hr->dtype;
+    u.code = theta->code;
+    u.weight = (const float*)theta->weight;
+    u.L = (const float*)lr_in->data;
+    u.L_pitch = lr_in->pitch;
+    u.Lout = (float*)lr_out->data;
+    u.Lout_pitch = lr_out->pitch;
+    u.H = theta->H;
+    u.W = theta->W;
+    u.h = h;
+    u.w = w;
+    u.s = s;
+    u.S = theta->S;
+    u.slots = (float*)ws;
+    u.active = nullptr;
+    return ls_update(u, (cudaStream_t)stream);
+}
+
+size_t glu_ls_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params) {
+    if (H <= 0 || W <= 0 || H >= (1 << 22) || scale < 1 || !params_ok(params)) return 0;
+    return ls_joint_workspace_bytes(H, W, scale, params->S);
+}
+
+int glu_ls_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
+                          glu_image* lr_out, glu_theta* theta, float* err_map,
+                          glu_ls_stats* stats, void* ws, size_t ws_bytes, void* stream) {
+    if (!image_ok(hr) || !image_ok(lr_out) || !params_ok(params) || !theta_ok(theta) || scale < 1)
+        return GLU_ERR_INVALID_ARG;
+    if ((hr->dtype != GLU_U8 && hr->dtype != GLU_F16) || hr->c != 3 || lr_out->c != 3 ||
+        lr_out->dtype != GLU_F32 || theta->wfmt != GLU_W_F32 || params->mode != GLU_MODE_FAST)
+        return GLU_ERR_UNSUPPORTED;
+    if (theta->H != hr->h || theta->W != hr->w || theta->S != params->S || theta->scale != scale ||
+        lr_out->h != lr_dim(hr->h, scale) || lr_out->w != lr_dim(hr->w, scale))
+        return GLU_ERR_SHAPE;
+    const size_t need = ls_joint_workspace_bytes(hr->h, hr->w, scale, params->S);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return GLU_ERR_WORKSPACE;
+    LsJoint j;
+    j.hr_image = *hr;
+    j.lr_image = *lr_out;
+    j.L = (float*)lr_out->data;
+    j.L_pitch = lr_out->pitch;
+    j.code = theta->code;
+    j.weight = (float*)theta->weight;
+    j.err = err_map;
+    j.H = hr->h;
+    j.W = hr->w;
+    j.s = scale;
+    j.S = params->S;
+    j.N = params->N;
+    j.eps255 = fmaxf(params->eps * 255.0f, 1e-12f);
+    j.ws = ws;
+    unsigned long long R[GLU_MAX_ITERS + 1];
+    int kept = 0;
+    const int rc = ls_joint(j, (cudaStream_t)stream, stats ? R : nullptr, stats ? &kept : nullptr);
+    if (rc) return rc;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->R0 = (double)R[0] * (1.0 / 4294967296.0);
+        for (int i = 1; i <= params->N; ++i)
+            stats->residual[i - 1] = (double)R[i] * (1.0 / 4294967296.0);
+        stats->iterations = params->N;
+        stats->kept = kept;
+    }
+    return GLU_OK;
 }
 
 size_t glu_apply_backward_workspace_size(const glu_theta* theta, int32_t c) {

@@ -78,11 +78,44 @@ int launch_apply_backward_ws(const BackwardArgs& a, void* ws, cudaStream_t st);
 
 int launch_downsample(const glu_image& hr, int s, int mode, const glu_image& lr, cudaStream_t st);
 
+// Least-squares LR colour update for a fixed Theta (k_ls.cu; float32 weights, float32 LR colours
+// in [0, 1]) and its alternation with Algorithm 1.
+struct LsUpdate {
+    const void* hr;
+    int64_t hr_pitch;
+    int hr_dtype;
+    const uint16_t* code;
+    const float* weight;
+    const float* L;
+    int64_t L_pitch;
+    float* Lout;
+    int64_t Lout_pitch;
+    int H, W, h, w, s, S;
+    float* slots;         // ls_update_workspace_bytes(h, w, S), 16-byte aligned
+    const int* active;    // nullable (device flag)
+};
+size_t ls_update_workspace_bytes(int h, int w, int S);
+int ls_update(const LsUpdate& u, cudaStream_t st);
+struct LsJoint {
+    glu_image hr_image, lr_image;   // guide (U8 / F16) and the float32 LR image (L below)
+    float* L;
+    int64_t L_pitch;
+    uint16_t* code;
+    float* weight;
+    float* err;                     // nullable
+    int H, W, s, S, N;
+    float eps255;
+    void* ws;                       // ls_joint_workspace_bytes, 256-byte aligned
+};
+size_t ls_joint_workspace_bytes(int H, int W, int s, int S);
+int ls_joint(const LsJoint& j, cudaStream_t st, unsigned long long* R_host, int* kept_host);
+
 // Status words of each translation unit (read and cleared; synchronous on st).
 int read_and_clear_status_search(cudaStream_t st);
 int read_and_clear_status_apply(cudaStream_t st);
 int read_and_clear_status_down(cudaStream_t st);
 int read_and_clear_status_joint(cudaStream_t st);
+int read_and_clear_status_ls(cudaStream_t st);
 int read_and_clear_status_search_exact(cudaStream_t st);
 
 // Joint optimisation (Algorithm 2).

@@ -1,9 +1,12 @@
 // Eq. 1 (apply) and its adjoint.
 //
-// apply: one thread per group of 4 consecutive HR pixels of a row: the pair codes and weights
-// stream from HBM, the two LR gathers hit L2 (the LR target is small), the result streams out.
+// apply, 3-channel float32 targets with aligned rows: the tiled forms below (LR region and a
+// pair-code table in shared memory; plain, per-tile TMA and persistent TMA-pipeline variants,
+// chosen by the autotuner). Other targets: one thread per group of 4 consecutive HR pixels of a
+// row, codes and weights streaming from HBM, the two LR gathers hitting L2.
 //
-// backward: grad_lr_q = sum_{p: a_p = q} w_p G_p + sum_{p: b_p = q} (1 - w_p) G_p. The pixels that
+// backward (without a workspace; the workspace form is further down):
+// grad_lr_q = sum_{p: a_p = q} w_p G_p + sum_{p: b_p = q} (1 - w_p) G_p. The pixels that
 // can map to q are bounded by the window: p's block must lie within r of q. One warp owns one
 // LR pixel and walks those source blocks in a fixed order (blocks in raster order, lanes strided
 // over each block's pixels), then reduces lanes with a fixed butterfly: no atomics, the result
@@ -393,59 +396,6 @@ __global__ void __launch_bounds__(256) k_apply3_tma(const ApplyArgs P,
     }
 }
 
-// Eq. 1 fast path for 3-channel float32 targets and outputs with W % 4 == 0 and 16-byte
-// aligned rows: one thread per 4 consecutive pixels; codes and weights arrive as one 8- or
-// 16-byte streaming load each, the 8 LR gathers go through the read-only path (the LR target
-// is small and stays in L1/L2), the 12 results leave as three 16-byte streaming stores.
-template <int WF>
-__global__ void __launch_bounds__(256) k_apply3_vec(const ApplyArgs P) {
-    const int G4 = P.W >> 2;
-    const int64_t total = (int64_t)G4 * P.H;
-    const int S = P.S, r = (P.S - 1) >> 1, K = P.S * P.S;
-    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
-    const float* T = (const float*)P.T;
-    float* out = (float*)P.out;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(g / G4), x0 = (int)(g - (int64_t)y * G4) * 4;
-        const int64_t p0 = (int64_t)y * P.W + x0;
-        const uint2 cc = __ldcs((const uint2*)P.code + (p0 >> 2));
-        const int code[4] = {(int)(cc.x & 0xFFFFu), (int)(cc.x >> 16), (int)(cc.y & 0xFFFFu),
-                             (int)(cc.y >> 16)};
-        float w[4];
-        W4<WF>::load(P.weight, p0, w);
-        const int py = y / P.s;
-        float res[12];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int px = (x0 + j) / P.s;
-            const int ka = qdiv(code[j], invK), kb = code[j] - ka * K;
-            const int ra = qdiv(ka, invS), rb = qdiv(kb, invS);
-            const int va = py + ra - r, ua = px + (ka - ra * S) - r;
-            const int vb = py + rb - r, ub = px + (kb - rb * S) - r;
-            int64_t oa = (int64_t)va * P.T_pitch + (int64_t)ua * 3;
-            int64_t ob = (int64_t)vb * P.T_pitch + (int64_t)ub * 3;
-            if ((unsigned)va >= (unsigned)P.h || (unsigned)ua >= (unsigned)P.w || ka >= K) {
-                set_status(GLU_ERR_DEVICE_CHECK);
-                oa = 0;
-            }
-            if ((unsigned)vb >= (unsigned)P.h || (unsigned)ub >= (unsigned)P.w || kb >= K) {
-                set_status(GLU_ERR_DEVICE_CHECK);
-                ob = 0;
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float ta = __ldg(T + oa + c), tb = __ldg(T + ob + c);
-                res[j * 3 + c] = __fmaf_rn(w[j], ta - tb, tb);
-            }
-        }
-        float4* o = (float4*)(out + (int64_t)y * P.out_pitch + (int64_t)x0 * 3);
-        __stcs(o + 0, make_float4(res[0], res[1], res[2], res[3]));
-        __stcs(o + 1, make_float4(res[4], res[5], res[6], res[7]));
-        __stcs(o + 2, make_float4(res[8], res[9], res[10], res[11]));
-    }
-}
-
 template <int C>
 __global__ void k_apply_backward_lr(const BackwardArgs P) {
     const int lane = threadIdx.x & 31;
@@ -659,10 +609,7 @@ int launch_apply(const ApplyArgs& a, cudaStream_t st) {
                        ((uintptr_t)a.code & 7u) == 0 && ((uintptr_t)a.weight & (wsz - 1)) == 0;
     const bool vec = in_ok && a.out_dtype == GLU_F32 && ((uintptr_t)a.out & 15u) == 0;
     const bool vec16 = in_ok && a.out_dtype == GLU_F16 && ((uintptr_t)a.out & 7u) == 0;
-#ifndef GLU_APPLY_TILED
-#define GLU_APPLY_TILED 1
-#endif
-    if ((vec && GLU_APPLY_TILED) || vec16) {
+    if (vec || vec16) {
         // TMA needs 16-byte rows of codes, weights and output and 16-byte aligned bases
         const size_t wb = a.wfmt == GLU_W_F32 ? 4 : 2, ob = vec16 ? 2 : 4;
         CUtensorMap mcode, mw, mout;
@@ -740,22 +687,6 @@ int launch_apply(const ApplyArgs& a, cudaStream_t st) {
         const int rc = tune_choose(kTuneApply, key, kNumApplyVariants, run, st, &v);
         if (rc) return rc;
         return run(v);
-    }
-    if (vec) {
-        const int64_t work = (int64_t)(a.W / 4) * a.H;
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int64_t blocks = (work + threads - 1) / threads;
-        const int64_t cap = (int64_t)sms * 32;
-        const int grid = (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
-        switch (a.wfmt) {
-            case GLU_W_F32: k_apply3_vec<GLU_W_F32><<<grid, threads, 0, st>>>(a); break;
-            case GLU_W_F16: k_apply3_vec<GLU_W_F16><<<grid, threads, 0, st>>>(a); break;
-            default: k_apply3_vec<GLU_W_UNORM16><<<grid, threads, 0, st>>>(a); break;
-        }
-        GLU_LAUNCH_CHECK();
-        return GLU_OK;
     }
     const int64_t work = (int64_t)((a.W + 3) / 4) * a.H;
     const int grid = grid_for(work, threads);

@@ -182,7 +182,8 @@ def test_plain_256_pipeline_against_oracle_theta(api):
 
 @pytest.mark.parametrize("wfmt", [0, 1, 2])
 def test_apply_vector_path_parity(api, wfmt):
-    # W % 4 == 0, float32 3-channel target/output: the 4-pixel vector path of Eq. 1
+    # W % 4 == 0, float32 3-channel target/output: the tiled paths of Eq. 1 (the autotuner's
+    # default variant; every variant is checked bit-identical in test_gpu_tune.py)
     H, W, s, S = 200, 320, 8, 5
     img = scene_img(21, H, W)
     hr = dev(img)

@@ -932,13 +932,60 @@ __global__ void __launch_bounds__(32 * (TH < 8 ? TH : 8)) k_apply3_gw_tile(const
 // Every sum has a fixed order (bit-reproducible); no atomics. (Measured alternative: one fixed
 // butterfly per distinct window index of each 64-pixel chunk was slower on textured guides,
 // where a block holds many distinct indices.)
-constexpr int kBsChunk = 128;   // pixels a warp stages at a time
+constexpr int kBsChunk = 64;    // pixels a warp stages at a time (two per lane)
+
+// Stable counting sort of one 64-pixel chunk by key (key 255: not listed): pixel jj = lane +
+// 32 h has key key[h]; writes the chunk indices in key order, raster order inside a key, to
+// list[] and the key starts to start[0..K] (start[K] = listed pixels). cnt: per-warp scratch of
+// K + 1 ints. Warp-uniform.
+__device__ __forceinline__ void chunk_sort(const int (&key)[2], int K, int* cnt, int* start,
+                                           uint8_t* list) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int k = lane; k <= K; k += 32) cnt[k] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const unsigned m = __match_any_sync(0xffffffffu, key[h]);
+        if (key[h] < K && (m & lt) == 0) cnt[key[h]] += __popc(m);
+        __syncwarp();
+    }
+    int carry = 0;
+    for (int k0 = 0; k0 <= K; k0 += 32) {
+        const int k = k0 + lane;
+        const int v = k < K ? cnt[k] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (k <= K) start[k] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    for (int k = lane; k < K; k += 32) cnt[k] = start[k];   // running positions
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const unsigned m = __match_any_sync(0xffffffffu, key[h]);
+        if (key[h] < K) list[cnt[key[h]] + __popc(m & lt)] = (uint8_t)(lane + 32 * h);
+        __syncwarp();
+        if (key[h] < K && (m & lt) == 0) cnt[key[h]] += __popc(m);
+        __syncwarp();
+    }
+}
+
 template <int C, int NQ>
 __global__ void __launch_bounds__(256) k_bw_block_sums(const BackwardArgs P, float* slots) {
     constexpr int CG = C == 3 ? 4 : C;           // gradient row padded to 16 bytes for C = 3
-    __shared__ int2 s_pw[8][kBsChunk];           // pair (k_a | k_b << 8), weight bits
+    constexpr int KM = 32 * NQ;                   // buckets covered by the warp's lanes
+    __shared__ float s_w[8][kBsChunk];
     __shared__ __align__(16) float s_g[8][kBsChunk * CG];
-    __shared__ float s_t[8][32 * NQ * C];        // the block's window of T (grad_w)
+    __shared__ float s_t[8][KM * C];              // the block's window of T (grad_w)
+    __shared__ int s_cnt[8][KM + 1];
+    __shared__ int s_sa[8][KM + 1], s_sb[8][KM + 1];
+    __shared__ uint8_t s_la[8][kBsChunk], s_lb[8][kBsChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = (P.S - 1) >> 1, S = P.S, K = S * S, s = P.s;
     const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
@@ -967,9 +1014,13 @@ __global__ void __launch_bounds__(256) k_bw_block_sums(const BackwardArgs P, flo
         const int ey = min(s, P.H - ys), ex = min(s, P.W - xs), n = ey * ex;
         const float inv_ex = 1.0f / (float)ex;
         for (int j0 = 0; j0 < n; j0 += kBsChunk) {
-            const int m = min(kBsChunk, n - j0);
-            for (int jj = lane; jj < m; jj += 32) {
-                const int j = j0 + jj, jy = qdiv(j, inv_ex);
+            int ka[2], kb[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int jj = lane + 32 * h, j = j0 + jj;
+                ka[h] = kb[h] = 255;
+                if (j >= n) continue;
+                const int jy = qdiv(j, inv_ex);
                 const int y = ys + jy, x = xs + (j - jy * ex);
                 const int64_t p = (int64_t)y * P.W + x;
                 const int code = P.code[p];
@@ -979,8 +1030,12 @@ __global__ void __launch_bounds__(256) k_bw_block_sums(const BackwardArgs P, flo
 #pragma unroll
                 for (int c = 0; c < C; ++c) g[c] = __ldcs(&P.G[og + c]);
                 const bool valid = code < K * K;
-                const int ka = qdiv(code, invK), kb = code - ka * K;
-                s_pw[warp][jj] = make_int2(valid ? (ka | (kb << 8)) : 0xFFFF, __float_as_int(w));
+                const int qa = qdiv(code, invK), qb = code - qa * K;
+                if (valid) {
+                    ka[h] = qa;
+                    kb[h] = qb;
+                }
+                s_w[warp][jj] = w;
                 if (C == 3) {
                     *(float4*)&s_g[warp][jj * CG] = make_float4(g[0], g[1], g[C - 1], 0.f);
                 } else {
@@ -992,41 +1047,34 @@ __global__ void __launch_bounds__(256) k_bw_block_sums(const BackwardArgs P, flo
                     if (valid) {
 #pragma unroll
                         for (int c = 0; c < C; ++c)
-                            gw = __fmaf_rn(g[c], s_t[warp][ka * C + c] - s_t[warp][kb * C + c], gw);
+                            gw = __fmaf_rn(g[c], s_t[warp][qa * C + c] - s_t[warp][qb * C + c], gw);
                     } else {
                         set_status(GLU_ERR_DEVICE_CHECK);
                     }
                     P.gw[p] = gw;
                 }
             }
-            __syncwarp();
-#pragma unroll 4
-            for (int jj = 0; jj < m; ++jj) {
-                const int2 pw = s_pw[warp][jj];
-                const int ka = pw.x & 0xFF, kb = pw.x >> 8;   // 255: no pair
-                const float w = __int_as_float(pw.y);
-                float g[C];
-                if (C == 3) {
-                    const float4 g4 = *(const float4*)&s_g[warp][jj * CG];
-                    g[0] = g4.x;
-                    g[1] = g4.y;
-                    g[C - 1] = g4.z;
-                } else {
+            chunk_sort(ka, K, s_cnt[warp], s_sa[warp], s_la[warp]);
+            chunk_sort(kb, K, s_cnt[warp], s_sb[warp], s_lb[warp]);
+            // lane k walks bucket k of each list: the chunk's pixels with that window index,
+            // in raster order
 #pragma unroll
-                    for (int c = 0; c < C; ++c) g[c] = s_g[warp][jj * CG + c];
+            for (int q = 0; q < NQ; ++q) {
+                const int kk = lane + 32 * q;
+                if (kk >= K) continue;
+                for (int e = s_sa[warp][kk]; e < s_sa[warp][kk + 1]; ++e) {
+                    const int jj = s_la[warp][e];
+                    const float w = s_w[warp][jj];
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        acc_a[q][c] = __fmaf_rn(w, s_g[warp][jj * CG + c], acc_a[q][c]);
                 }
+                for (int e = s_sb[warp][kk]; e < s_sb[warp][kk + 1]; ++e) {
+                    const int jj = s_lb[warp][e];
+                    const float w = 1.f - s_w[warp][jj];
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    const int kk = lane + 32 * q;
-                    if (ka == kk) {
-#pragma unroll
-                        for (int c = 0; c < C; ++c) acc_a[q][c] = __fmaf_rn(w, g[c], acc_a[q][c]);
-                    }
-                    if (kb == kk) {
-#pragma unroll
-                        for (int c = 0; c < C; ++c)
-                            acc_b[q][c] = __fmaf_rn(1.f - w, g[c], acc_b[q][c]);
-                    }
+                    for (int c = 0; c < C; ++c)
+                        acc_b[q][c] = __fmaf_rn(w, s_g[warp][jj * CG + c], acc_b[q][c]);
                 }
             }
             __syncwarp();

@@ -393,9 +393,16 @@ def measure_extras(api, torch, img, dev, flush, stream):
     G = torch.randn((H, W, 3), device=dev)
     gT = torch.empty((h, w, 3), device=dev)
     gw = torch.empty((H, W), device=dev)
-    ms_b = timed(lambda: api.glu_apply_backward(theta, T, G, grad_lr=gT, grad_w=gw))
+    # the adjoint for one Theta and many calls (a fit through the upsampler): the plan (inverse
+    # pixel-to-LR map) is built once; also the workspace form without a plan
+    ms_plan = timed(lambda: api.glu_apply_backward_plan(theta), reps=3)
+    plan = api.glu_apply_backward_plan(theta)
+    ms_b = timed(lambda: api.glu_apply_backward(theta, T, G, grad_lr=gT, grad_w=gw, plan=plan))
+    ms_bw = timed(lambda: api.glu_apply_backward(theta, T, G, grad_lr=gT, grad_w=gw))
     res["backward_ms"] = ms_b
     res["backward_vs_apply"] = ms_b / ms_a
+    res["backward_plan_build_ms"] = ms_plan
+    res["backward_workspace_form_ms"] = ms_bw
     # GLU* (Eq. 4, every pair of window pixels) on the same guide and LR image
     pe = api.glu_params(S=WIN, mode=api.GLU_MODE_EXACT)
     th_e = api.Theta.empty(H, W, SCALE, WIN, api.GLU_W_F32, dev)

@@ -233,6 +233,20 @@ int glu_apply_backward(const glu_theta* theta, const glu_image* lr_target,
  * differs from glu_apply_backward's, so the two agree to rounding). GLU_ERR_WORKSPACE if ws is
  * missing, misaligned or too small. */
 size_t glu_apply_backward_workspace_size(const glu_theta* theta, int32_t c);
+
+/* The adjoint for a Theta used by many calls (an LR operator fitted through the upsampler): a
+ * plan, the inverse pixel-to-LR map of Theta's codes (every LR pixel's contributing HR pixels
+ * and sides, neighbour blocks in order, a then b, raster order inside), is built once
+ * (glu_apply_backward_plan: device memory of glu_apply_backward_plan_size bytes, 4-byte
+ * aligned; valid while the codes do not change: the weights may), and each
+ * glu_apply_backward_planned call reads every LR pixel's list once (a warp per LR pixel, lanes
+ * strided over its entries, a fixed butterfly: bit-reproducible). Same results contract as
+ * glu_apply_backward (its summation order differs). */
+size_t glu_apply_backward_plan_size(const glu_theta* theta);
+int glu_apply_backward_plan(const glu_theta* theta, void* plan, size_t plan_bytes, void* stream);
+int glu_apply_backward_planned(const glu_theta* theta, const void* plan,
+                               const glu_image* lr_target, const glu_image* grad_hr,
+                               glu_image* grad_lr, float* grad_w, void* stream);
 int glu_apply_backward_ws(const glu_theta* theta, const glu_image* lr_target,
                           const glu_image* grad_hr, glu_image* grad_lr, float* grad_w, void* ws,
                           size_t ws_bytes, void* stream);

@@ -348,13 +348,26 @@ def glu_apply(theta: Theta, lr_target: torch.Tensor, out: torch.Tensor | None = 
 _BW_WS = {}   # device -> workspace of the adjoint (grown on demand, reused across calls)
 
 
+def glu_apply_backward_plan(theta: Theta, stream=None) -> torch.Tensor:
+    """The inverse pixel-to-LR map of theta's codes for glu_apply_backward(plan=...): valid while
+    the codes do not change (the weights may)."""
+    td = theta.desc()
+    need = int(lib().glu_apply_backward_plan_size(ctypes.byref(td)))
+    plan = torch.empty(need // 4 + 1, dtype=torch.int32, device=theta.code.device)
+    A.check("glu_apply_backward_plan", lib().glu_apply_backward_plan(
+        ctypes.byref(td), ctypes.c_void_p(plan.data_ptr()), plan.numel() * 4, _stream(stream)))
+    return plan
+
+
 def glu_apply_backward(theta: Theta, lr_target: torch.Tensor, grad_hr: torch.Tensor,
                        grad_lr: torch.Tensor | None = None, grad_w: torch.Tensor | bool = True,
                        weight: torch.Tensor | None = None, stream=None,
-                       workspace: torch.Tensor | bool | None = True):
-    """Adjoint of Eq. 1: returns (grad_lr, grad_w or None). With `workspace` (True: a cached
-    per-device buffer; or a uint8 tensor) the bucketed form glu_apply_backward_ws runs, without
-    it (None / False) the tiled glu_apply_backward."""
+                       workspace: torch.Tensor | bool | None = True,
+                       plan: torch.Tensor | None = None):
+    """Adjoint of Eq. 1: returns (grad_lr, grad_w or None). With `plan` (from
+    glu_apply_backward_plan) glu_apply_backward_planned runs; otherwise with `workspace` (True: a
+    cached per-device buffer; or a uint8 tensor) the bucketed glu_apply_backward_ws, without it
+    (None / False) the tiled glu_apply_backward."""
     if grad_lr is None:
         grad_lr = torch.empty_like(lr_target, dtype=torch.float32)
     if grad_w is True:
@@ -363,6 +376,11 @@ def glu_apply_backward(theta: Theta, lr_target: torch.Tensor, grad_hr: torch.Ten
         grad_w = None
     td = theta.desc(weight, A.GLU_W_F32 if weight is not None else None)
     ti, gi, go = image(lr_target), image(grad_hr), image(grad_lr)
+    if plan is not None:
+        A.check("glu_apply_backward_planned", lib().glu_apply_backward_planned(
+            ctypes.byref(td), ctypes.c_void_p(plan.data_ptr()), ctypes.byref(ti),
+            ctypes.byref(gi), ctypes.byref(go), _ptr(grad_w), _stream(stream)))
+        return grad_lr, grad_w
     if workspace is None or workspace is False:
         A.check("glu_apply_backward", lib().glu_apply_backward(
             ctypes.byref(td), ctypes.byref(ti), ctypes.byref(gi), ctypes.byref(go),
@@ -531,10 +549,11 @@ class GluApplyFn(torch.autograd.Function):
     (a fixed-order reduction, bit-reproducible)."""
 
     @staticmethod
-    def forward(ctx, lr_target, weight, theta):
+    def forward(ctx, lr_target, weight, theta, plan=None):
         lr_target = lr_target.contiguous()
         weight = weight.contiguous()
         ctx.theta = theta
+        ctx.plan = plan
         ctx.save_for_backward(lr_target, weight)
         return glu_apply(theta, lr_target, weight=weight)
 
@@ -543,12 +562,16 @@ class GluApplyFn(torch.autograd.Function):
         lr_target, weight = ctx.saved_tensors
         g = grad_out.contiguous().to(torch.float32)
         grad_lr, grad_w = glu_apply_backward(ctx.theta, lr_target, g,
-                                             grad_w=ctx.needs_input_grad[1], weight=weight)
+                                             grad_w=ctx.needs_input_grad[1], weight=weight,
+                                             plan=ctx.plan)
         return (grad_lr if ctx.needs_input_grad[0] else None,
-                grad_w if ctx.needs_input_grad[1] else None, None)
+                grad_w if ctx.needs_input_grad[1] else None, None, None)
 
 
-def apply_autograd(theta: Theta, lr_target: torch.Tensor, weight: torch.Tensor | None = None):
-    """Differentiable Eq. 1 (w.r.t. the LR target and, if it requires grad, the weights)."""
+def apply_autograd(theta: Theta, lr_target: torch.Tensor, weight: torch.Tensor | None = None,
+                   plan: torch.Tensor | None = None):
+    """Differentiable Eq. 1 (w.r.t. the LR target and, if it requires grad, the weights). With
+    `plan` (glu_apply_backward_plan(theta)) the backward pass reads the precomputed inverse map,
+    the fast form for many passes over one Theta."""
     w = theta.weight_f32() if weight is None else weight
-    return GluApplyFn.apply(lr_target, w, theta)
+    return GluApplyFn.apply(lr_target, w, theta, plan)

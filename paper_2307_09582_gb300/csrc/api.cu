@@ -287,6 +287,31 @@ int glu_ls_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* 
     return GLU_OK;
 }
 
+size_t glu_apply_backward_plan_size(const glu_theta* theta) {
+    if (!theta_ok(theta) || (int64_t)theta->H * theta->W >= ((int64_t)1 << 30)) return 0;
+    const int s = theta->scale;
+    return apply_backward_plan_bytes((int64_t)theta->H * theta->W,
+                                     (int64_t)lr_dim(theta->H, s) * lr_dim(theta->W, s), theta->S);
+}
+
+int glu_apply_backward_plan(const glu_theta* theta, void* plan, size_t plan_bytes, void* stream) {
+    const size_t need = glu_apply_backward_plan_size(theta);
+    if (need == 0) return GLU_ERR_INVALID_ARG;
+    if (!plan || ((uintptr_t)plan & 3u) != 0 || plan_bytes < need) return GLU_ERR_WORKSPACE;
+    return apply_backward_plan(theta->code, theta->H, theta->W, theta->scale, theta->S, plan,
+                               (cudaStream_t)stream);
+}
+
+int glu_apply_backward_planned(const glu_theta* theta, const void* plan,
+                               const glu_image* lr_target, const glu_image* grad_hr,
+                               glu_image* grad_lr, float* grad_w, void* stream) {
+    BackwardArgs a;
+    const int rc = backward_args(theta, lr_target, grad_hr, grad_lr, grad_w, a);
+    if (rc) return rc;
+    if (!plan || ((uintptr_t)plan & 3u) != 0) return GLU_ERR_WORKSPACE;
+    return launch_apply_backward_planned(a, plan, (cudaStream_t)stream);
+}
+
 size_t glu_apply_backward_workspace_size(const glu_theta* theta, int32_t c) {
     if (!theta_ok(theta) || c < 1 || c > 4) return 0;
     return apply_backward_workspace_bytes(lr_dim(theta->H, theta->scale),

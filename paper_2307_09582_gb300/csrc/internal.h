@@ -75,6 +75,12 @@ int launch_apply_backward(const BackwardArgs& a, cudaStream_t st);
 // (16-byte aligned): per-block window-bucket sums, then one gather per LR pixel.
 size_t apply_backward_workspace_bytes(int h, int w, int S, int C);
 int launch_apply_backward_ws(const BackwardArgs& a, void* ws, cudaStream_t st);
+// The inverse pixel-to-LR map of a Theta (built once, apply_backward_plan_bytes, 4-byte aligned)
+// and the adjoint that reads it.
+size_t apply_backward_plan_bytes(int64_t np, int64_t nq, int S);
+int apply_backward_plan(const uint16_t* code, int H, int W, int s, int S, void* plan,
+                        cudaStream_t st);
+int launch_apply_backward_planned(const BackwardArgs& a, const void* plan, cudaStream_t st);
 
 int launch_downsample(const glu_image& hr, int s, int mode, const glu_image& lr, cudaStream_t st);
 

@@ -1180,6 +1180,32 @@ int launch_apply_backward_ws(const BackwardArgs& a, void* ws, cudaStream_t st) {
     }
 }
 
+// grad_w_p = G_p . (T_a - T_b) for every HR pixel (the tiled kernel where the layout allows).
+template <int C>
+static int launch_gw(const BackwardArgs& a, cudaStream_t st) {
+    const int threads = 256;
+    {
+        const bool tiled = C == 3 && a.W % 4 == 0 && a.G_pitch == (int64_t)a.W * 3 &&
+                           ((uintptr_t)a.G & 15u) == 0 && ((uintptr_t)a.gw & 15u) == 0 &&
+                           ((uintptr_t)a.code & 7u) == 0;
+        if (tiled) {
+            constexpr int TH = 16;
+            const size_t sm = sizeof(float4) * (size_t)apply_region_cells(TH, a.s, a.S) +
+                              sizeof(uint32_t) * (size_t)(a.S * a.S) * (a.S * a.S);
+            if (sm > 48 * 1024 &&
+                cudaFuncSetAttribute(k_apply3_gw_tile<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm) != cudaSuccess)
+                return GLU_ERR_CUDA;
+            const dim3 grid((a.W + kApplyTW - 1) / kApplyTW, (a.H + TH - 1) / TH);
+            k_apply3_gw_tile<TH><<<grid, 32 * 8, sm, st>>>(a);
+        } else {
+            k_apply_backward_w<C><<<grid_for((int64_t)a.H * a.W, threads), threads, 0, st>>>(a);
+        }
+        GLU_LAUNCH_CHECK();
+    }
+    return GLU_OK;
+}
+
 template <int C>
 static int launch_bw_t(const BackwardArgs& a, cudaStream_t st) {
     const int threads = 256;
@@ -1209,26 +1235,261 @@ static int launch_bw_t(const BackwardArgs& a, cudaStream_t st) {
         k_apply_backward_lr<C><<<grid_q, threads, 0, st>>>(a);
     }
     GLU_LAUNCH_CHECK();
-    if (a.gw) {
-        const bool tiled = C == 3 && a.W % 4 == 0 && a.G_pitch == (int64_t)a.W * 3 &&
-                           ((uintptr_t)a.G & 15u) == 0 && ((uintptr_t)a.gw & 15u) == 0 &&
-                           ((uintptr_t)a.code & 7u) == 0;
-        if (tiled) {
-            constexpr int TH = 16;
-            const size_t sm = sizeof(float4) * (size_t)apply_region_cells(TH, a.s, a.S) +
-                              sizeof(uint32_t) * (size_t)(a.S * a.S) * (a.S * a.S);
-            if (sm > 48 * 1024 &&
-                cudaFuncSetAttribute(k_apply3_gw_tile<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sm) != cudaSuccess)
-                return GLU_ERR_CUDA;
-            const dim3 grid((a.W + kApplyTW - 1) / kApplyTW, (a.H + TH - 1) / TH);
-            k_apply3_gw_tile<TH><<<grid, 32 * 8, sm, st>>>(a);
-        } else {
-            k_apply_backward_w<C><<<grid_for((int64_t)a.H * a.W, threads), threads, 0, st>>>(a);
-        }
-        GLU_LAUNCH_CHECK();
-    }
+    if (a.gw) return launch_gw<C>(a, st);
     return GLU_OK;
+}
+
+// ------------------------------------------------------- adjoint with a precomputed plan
+//
+// For a Theta used by many adjoint calls (an LR operator fitted through the upsampler), the
+// inverse pixel-to-LR map is built once: for every LR pixel q, the list of its contributions
+// (HR pixel p, side a or b) in a fixed order: neighbour blocks B = q + (n / S - r, n % S - r) for
+// n = 0 .. K - 1, inside B first the pixels with a_p = q then those with b_p = q, each in raster
+// order. Layout (int32): off[nq + 1], the entries p << 1 | side (2 per HR pixel at most), and
+// the per-(q, n, side) counts / starts used while building. A call then reads each LR pixel's
+// list once: a warp per LR pixel, lanes strided over the entries, a fixed butterfly.
+size_t apply_backward_plan_bytes(int64_t np, int64_t nq, int S) {
+    return sizeof(int) * (size_t)((nq + 1) + 2 * np + nq * (int64_t)S * S * 2);
+}
+
+struct PlanArgs {
+    const uint16_t* code;
+    int H, W, h, w, s, S;
+    int* off;    // nq + 1
+    int* ent;    // 2 np
+    int* cnt;    // nq K 2: counts, then starts
+};
+
+// Counts (pass 0) or entries (pass 1) of one block per warp; chunk ranks by warp match, so the
+// entries of one (q, n, side) are in raster order.
+template <int PASS, int NQ>
+__global__ void __launch_bounds__(256) k_plan_block(const PlanArgs A) {
+    __shared__ int s_run[8][2][32 * NQ];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int r = (A.S - 1) >> 1, S = A.S, K = S * S, s = A.s;
+    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
+    const int64_t nblocks = (int64_t)A.h * A.w;
+    for (int64_t blk = (int64_t)blockIdx.x * 8 + warp; blk < nblocks;
+         blk += (int64_t)gridDim.x * 8) {
+        const int bv = (int)(blk / A.w), bu = (int)(blk - (int64_t)bv * A.w);
+        for (int k = lane; k < 32 * NQ; k += 32) s_run[warp][0][k] = s_run[warp][1][k] = 0;
+        __syncwarp();
+        const int ys = bv * s, xs = bu * s;
+        const int ey = min(s, A.H - ys), ex = min(s, A.W - xs), n = ey * ex;
+        const float inv_ex = 1.0f / (float)ex;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            const int j = j0 + lane;
+            int key[2] = {255, 255};
+            int64_t p = 0;
+            if (j < n) {
+                const int jy = qdiv(j, inv_ex);
+                p = (int64_t)(ys + jy) * A.W + xs + (j - jy * ex);
+                const int code = A.code[p];
+                if (code < K * K) {
+                    key[0] = qdiv(code, invK);
+                    key[1] = code - key[0] * K;
+                } else {
+                    set_status(GLU_ERR_DEVICE_CHECK);
+                }
+            }
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int k = key[side];
+                const unsigned m = __match_any_sync(0xffffffffu, k);
+                if (PASS == 1 && k < K) {
+                    const int kr = qdiv(k, invS);
+                    const int qv = bv + kr - r, qu = bu + (k - kr * S) - r;
+                    if (qv < 0 || qv >= A.h || qu < 0 || qu >= A.w) {
+                        set_status(GLU_ERR_DEVICE_CHECK);   // not a code the search produces
+                    } else {
+                        const int64_t q = (int64_t)qv * A.w + qu;
+                        const int pos = A.cnt[(q * K + (K - 1 - k)) * 2 + side] +
+                                        s_run[warp][side][k] + __popc(m & lt);
+                        A.ent[pos] = (int)((p << 1) | side);
+                    }
+                }
+                __syncwarp();
+                if (k < K && (m & lt) == 0) s_run[warp][side][k] += __popc(m);
+                __syncwarp();
+            }
+        }
+        if (PASS == 0) {
+            for (int k = lane; k < K; k += 32) {
+                const int kr = qdiv(k, invS);
+                const int qv = bv + kr - r, qu = bu + (k - kr * S) - r;
+                if (qv < 0 || qv >= A.h || qu < 0 || qu >= A.w) continue;
+                const int64_t q = (int64_t)qv * A.w + qu;
+                A.cnt[(q * K + (K - 1 - k)) * 2 + 0] = s_run[warp][0][k];
+                A.cnt[(q * K + (K - 1 - k)) * 2 + 1] = s_run[warp][1][k];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Per LR pixel: its total (neighbours inside the image) -> off[q] (before the scan).
+__global__ void k_plan_totals(const PlanArgs A) {
+    const int r = (A.S - 1) >> 1, S = A.S, K = S * S;
+    const float invS = 1.0f / (float)S;
+    const int64_t nq = (int64_t)A.h * A.w;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(q / A.w), u = (int)(q - (int64_t)v * A.w);
+        int t = 0;
+        for (int nn = 0; nn < K; ++nn) {
+            const int nr = qdiv(nn, invS);
+            const int bv = v + nr - r, bu = u + (nn - nr * S) - r;
+            if (bv < 0 || bv >= A.h || bu < 0 || bu >= A.w) continue;
+            t += A.cnt[(q * K + nn) * 2] + A.cnt[(q * K + nn) * 2 + 1];
+        }
+        A.off[q] = t;
+    }
+}
+
+// Exclusive scan of off[0 .. nq) in place (off[nq] = total): one CTA, 1024 threads, in order.
+__global__ void __launch_bounds__(1024) k_plan_scan(int* off, int64_t nq) {
+    __shared__ int wsum[32];
+    __shared__ int carry_s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nq; b0 += 1024) {
+        const int64_t i = b0 + threadIdx.x;
+        const int v = i < nq ? off[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int t = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        const int excl = carry_s + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+        if (i < nq) off[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s += wsum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[nq] = carry_s;
+}
+
+// counts -> starts: off[q] + the counts of the earlier (n, side) of q (n ascending, a then b).
+__global__ void k_plan_starts(const PlanArgs A) {
+    const int r = (A.S - 1) >> 1, S = A.S, K = S * S;
+    const float invS = 1.0f / (float)S;
+    const int64_t nq = (int64_t)A.h * A.w;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(q / A.w), u = (int)(q - (int64_t)v * A.w);
+        int pos = A.off[q];
+        for (int nn = 0; nn < K; ++nn) {
+            const int nr = qdiv(nn, invS);
+            const int bv = v + nr - r, bu = u + (nn - nr * S) - r;
+            if (bv < 0 || bv >= A.h || bu < 0 || bu >= A.w) continue;
+            const int ca = A.cnt[(q * K + nn) * 2], cb = A.cnt[(q * K + nn) * 2 + 1];
+            A.cnt[(q * K + nn) * 2] = pos;
+            A.cnt[(q * K + nn) * 2 + 1] = pos + ca;
+            pos += ca + cb;
+        }
+    }
+}
+
+int apply_backward_plan(const uint16_t* code, int H, int W, int s, int S, void* plan,
+                        cudaStream_t st) {
+    PlanArgs A;
+    A.code = code;
+    A.H = H;
+    A.W = W;
+    A.s = s;
+    A.S = S;
+    A.h = (H + s - 1) / s;
+    A.w = (W + s - 1) / s;
+    const int64_t np = (int64_t)H * W, nq = (int64_t)A.h * A.w;
+    A.off = (int*)plan;
+    A.ent = A.off + (nq + 1);
+    A.cnt = A.ent + 2 * np;
+    const int K = S * S;
+    const int g = grid_for(nq * 32, 256);
+    auto both = [&](auto k0, auto k1) {
+        k0<<<g, 256, 0, st>>>(A);
+        k_plan_totals<<<grid_for(nq, 256), 256, 0, st>>>(A);
+        k_plan_scan<<<1, 1024, 0, st>>>(A.off, nq);
+        k_plan_starts<<<grid_for(nq, 256), 256, 0, st>>>(A);
+        k1<<<g, 256, 0, st>>>(A);
+    };
+    if (K <= 32) both(k_plan_block<0, 1>, k_plan_block<1, 1>);
+    else if (K <= 64) both(k_plan_block<0, 2>, k_plan_block<1, 2>);
+    else both(k_plan_block<0, 3>, k_plan_block<1, 3>);
+    GLU_LAUNCH_CHECK();
+    return GLU_OK;
+}
+
+// A warp per LR pixel over its plan entries (lane-strided), then a fixed butterfly.
+template <int C>
+__global__ void __launch_bounds__(256) k_bw_planned(const BackwardArgs P, const int* off,
+                                                   const int* ent, int dense) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nq = (int64_t)P.h * P.w;
+    for (int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < nq;
+         q += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const int e0 = off[q], e1 = off[q + 1];
+        float acc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = 0.f;
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const int x = __ldcs(&ent[e]);
+            const int64_t p = (int64_t)(x >> 1);
+            const float w = load_weight(P.weight, P.wfmt, p);
+            const float f = (x & 1) ? 1.f - w : w;
+            const int64_t og = dense ? p * C : (p / P.W) * P.G_pitch + (p % P.W) * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = __fmaf_rn(f, __ldg(&P.G[og + c]), acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        }
+        if (lane == 0) {
+            const int v = (int)(q / P.w), u = (int)(q - (int64_t)v * P.w);
+#pragma unroll
+            for (int c = 0; c < C; ++c) P.gT[(int64_t)v * P.gT_pitch + (int64_t)u * C + c] = acc[c];
+        }
+    }
+}
+
+template <int C>
+static int launch_bw_planned_t(const BackwardArgs& a, const void* plan, cudaStream_t st) {
+    const int64_t nq = (int64_t)a.h * a.w;
+    const int* off = (const int*)plan;
+    const int* ent = off + (nq + 1);
+    k_bw_planned<C><<<grid_for(nq * 32, 256), 256, 0, st>>>(a, off, ent,
+                                                            a.G_pitch == (int64_t)a.W * C);
+    GLU_LAUNCH_CHECK();
+    if (a.gw) return launch_gw<C>(a, st);
+    return GLU_OK;
+}
+
+int launch_apply_backward_planned(const BackwardArgs& a, const void* plan, cudaStream_t st) {
+    if (a.H <= 0 || a.W <= 0) return GLU_OK;
+    switch (a.C) {
+        case 1: return launch_bw_planned_t<1>(a, plan, st);
+        case 2: return launch_bw_planned_t<2>(a, plan, st);
+        case 3: return launch_bw_planned_t<3>(a, plan, st);
+        case 4: return launch_bw_planned_t<4>(a, plan, st);
+        default: return GLU_ERR_UNSUPPORTED;
+    }
 }
 
 int launch_apply_backward(const BackwardArgs& a, cudaStream_t st) {

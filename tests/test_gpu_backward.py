@@ -29,18 +29,22 @@ def make_theta(api, H, W, s, S, seed=1):
     return img, hr, lr, theta
 
 
-@pytest.mark.parametrize("ws", [True, None])
+@pytest.mark.parametrize("ws", [True, None, "plan"])
 @pytest.mark.parametrize("H,W,s,S,C", [(250, 347, 8, 5, 3), (96, 96, 8, 3, 3), (97, 131, 3, 3, 1),
                                        (64, 80, 16, 5, 4), (50, 70, 2, 9, 3), (90, 100, 7, 7, 2),
                                        (300, 200, 64, 3, 3), (130, 250, 128, 5, 1)])
 def test_backward_matches_fp64_oracle(api, H, W, s, S, C, ws):
-    """Both forms: the bucketed one with a workspace (ws=True) and the tiled one (ws=None)."""
+    """All three forms: the bucketed one with a workspace (ws=True), the tiled one (ws=None) and
+    the one reading a precomputed plan (ws="plan")."""
     _, _, _, theta = make_theta(api, H, W, s, S)
     h, w = api.lr_dims(H, W, s)
     g = torch.Generator().manual_seed(3)
     T = torch.rand((h, w, C), generator=g).cuda()
     G = torch.randn((H, W, C), generator=g).cuda()
-    gT, gw = api.glu_apply_backward(theta, T, G, workspace=ws)
+    plan = api.glu_apply_backward_plan(theta) if ws == "plan" else None
+    if plan is not None:
+        ws = None
+    gT, gw = api.glu_apply_backward(theta, T, G, workspace=ws, plan=plan)
     torch.cuda.synchronize()
     K = S * S
     codes = theta.codes_i32().cpu().numpy()
@@ -57,7 +61,7 @@ def test_backward_matches_fp64_oracle(api, H, W, s, S, C, ws):
     assert np.all(np.abs(gT.cpu().numpy() - rT) <= tol)
     assert np.abs(gw.cpu().numpy() - rw).max() < 1e-5
     # deterministic: bitwise identical on a second call
-    gT2, gw2 = api.glu_apply_backward(theta, T, G, workspace=ws)
+    gT2, gw2 = api.glu_apply_backward(theta, T, G, workspace=ws, plan=plan)
     torch.cuda.synchronize()
     assert torch.equal(gT, gT2) and torch.equal(gw, gw2)
 
@@ -117,10 +121,11 @@ def test_fit_colour_matrix_through_upsampler(api):
     Am = torch.eye(3, device="cuda", requires_grad=True)
     cv = torch.zeros(3, device="cuda", requires_grad=True)
     opt = torch.optim.Adam([Am, cv], lr=1e-2)
+    plan = api.glu_apply_backward_plan(theta)   # one Theta, 200 backward passes
     for _ in range(200):
         opt.zero_grad()
         T = Lf @ Am.T + cv
-        out = api.apply_autograd(theta, T)
+        out = api.apply_autograd(theta, T, plan=plan)
         loss = ((out - target) ** 2).mean()
         loss.backward()
         opt.step()

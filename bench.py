@@ -580,14 +580,20 @@ def run_kernel_case(args):
             api.glu_optimize(hr, lr, pe, SCALE, theta=th_e, err_map=err)
         torch.cuda.synchronize()
         return 0
+    if args.kernel_case == "backward":
+        # the plan is built once; each rep runs the planned adjoint, then the workspace form
+        plan = api.glu_apply_backward_plan(theta)
+        G = torch.randn((H, W, 3), device=dev)
+        for _ in range(args.case_reps):
+            api.glu_apply_backward(theta, T, G, plan=plan)
+            api.glu_apply_backward(theta, T, G)
+        torch.cuda.synchronize()
+        return 0
     for _ in range(args.case_reps):
         if args.kernel_case == "search":
             api.glu_optimize(hr, lr, p, SCALE, theta=theta, err_map=err)
         elif args.kernel_case == "apply":
             api.glu_apply(theta, T, out=out)
-        elif args.kernel_case == "backward":
-            G = torch.randn((H, W, 3), device=dev)
-            api.glu_apply_backward(theta, T, G)
     torch.cuda.synchronize()
     return 0
 

@@ -1447,14 +1447,32 @@ __global__ void __launch_bounds__(256) k_bw_planned(const BackwardArgs P, const 
         float acc[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] = 0.f;
-        for (int e = e0 + lane; e < e1; e += 32) {
-            const int x = __ldcs(&ent[e]);
-            const int64_t p = (int64_t)(x >> 1);
-            const float w = load_weight(P.weight, P.wfmt, p);
-            const float f = (x & 1) ? 1.f - w : w;
-            const int64_t og = dense ? p * C : (p / P.W) * P.G_pitch + (p % P.W) * C;
+        // four entries per lane at a time: their loads are issued together (the sums still
+        // run over the lane's entries in ascending order)
+        for (int e = e0 + lane; e < e1; e += 128) {
+            int x[4];
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = __fmaf_rn(f, __ldg(&P.G[og + c]), acc[c]);
+            for (int u = 0; u < 4; ++u) x[u] = e + 32 * u < e1 ? __ldcs(&ent[e + 32 * u]) : -1;
+            float f[4], g[4][C];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                f[u] = 0.f;
+#pragma unroll
+                for (int c = 0; c < C; ++c) g[u][c] = 0.f;
+                if (x[u] < 0) continue;
+                const int64_t p = (int64_t)(x[u] >> 1);
+                const float w = load_weight(P.weight, P.wfmt, p);
+                f[u] = (x[u] & 1) ? 1.f - w : w;
+                const int64_t og = dense ? p * C : (p / P.W) * P.G_pitch + (p % P.W) * C;
+#pragma unroll
+                for (int c = 0; c < C; ++c) g[u][c] = __ldg(&P.G[og + c]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (x[u] < 0) break;
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] = __fmaf_rn(f[u], g[u][c], acc[c]);
+            }
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {

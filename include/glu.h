@@ -284,6 +284,14 @@ int glu_ls_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* 
                           glu_image* lr_out, glu_theta* theta, float* err_map,
                           glu_ls_stats* stats, void* ws, size_t ws_bytes, void* stream);
 
+/* Test hook (failure detection): the deadline, in nanoseconds, of the waits of Algorithm 2's
+ * trial kernel (the ready queue, the general path's items, the in-order fallback); 0 restores
+ * the default (5 s plus 0.5 ms per component, at most 30 s). With a limit that runs out, the
+ * waits give up, the kernel records GLU_ERR_TIMEOUT in its status word and returns, the call
+ * with stats returns GLU_ERR_TIMEOUT and glu_device_status() reports it; the context stays
+ * usable. Process-wide; not thread-safe. */
+int glu_test_set_wait_limit(uint64_t ns);
+
 /* Autotuner (not part of the method: implementation choice only). The Algorithm 1 search
  * (GLU_TUNE_SEARCH: tile height x CTAs per SM x candidate loop schedule) and the tiled Eq. 1
  * apply (GLU_TUNE_APPLY: tile height) have several implementation variants that compute the same

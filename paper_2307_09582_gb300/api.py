@@ -348,6 +348,11 @@ def glu_apply(theta: Theta, lr_target: torch.Tensor, out: torch.Tensor | None = 
 _BW_WS = {}   # device -> workspace of the adjoint (grown on demand, reused across calls)
 
 
+def test_set_wait_limit(ns: int) -> None:
+    """Test hook: deadline of the trial kernel's waits in ns (0: the default)."""
+    A.check("glu_test_set_wait_limit", lib().glu_test_set_wait_limit(int(ns)))
+
+
 def glu_apply_backward_plan(theta: Theta, stream=None) -> torch.Tensor:
     """The inverse pixel-to-LR map of theta's codes for glu_apply_backward(plan=...): valid while
     the codes do not change (the weights may)."""

@@ -287,6 +287,11 @@ int glu_ls_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* 
     return GLU_OK;
 }
 
+int glu_test_set_wait_limit(uint64_t ns) {
+    set_trial_wait_limit((unsigned long long)ns);
+    return GLU_OK;
+}
+
 size_t glu_apply_backward_plan_size(const glu_theta* theta) {
     if (!theta_ok(theta) || (int64_t)theta->H * theta->W >= ((int64_t)1 << 30)) return 0;
     const int s = theta->scale;
@@ -518,6 +523,7 @@ int glu_joint_optimize_batched(const glu_batch_item* items, int32_t n, const glu
     cm.strict = params->joint == GLU_JOINT_STRICT;
     cm.conn = params->connectivity;
     cm.wfmt = items[0].theta.wfmt;
+    cm.wait_limit_ns = 0;
     return launch_joint_batch(it, n, cm, ws, ws_bytes, stats, (cudaStream_t)stream);
 }
 

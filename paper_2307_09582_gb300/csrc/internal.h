@@ -160,7 +160,10 @@ struct JointItem {
 struct JointCommon {
     float eps255, tau;
     int N, strict, conn, wfmt;
+    unsigned long long wait_limit_ns;   // set by launch_joint_batch (0: the default deadline)
 };
+// Test hook: the deadline of the trial kernel's waits (0 restores the default).
+void set_trial_wait_limit(unsigned long long ns);
 size_t joint_batch_workspace_bytes(const JointItem* items, int n, int N);
 // stats: null or an array of n records
 int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, void* ws,

@@ -926,7 +926,11 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
 struct TrialCtx {
     JointWs ws;
     int it;
+    unsigned long long wait_limit_ns;   // 0: trial_deadline(M)
 };
+
+static unsigned long long g_wait_limit_ns = 0;   // test hook (glu_test_set_wait_limit)
+void set_trial_wait_limit(unsigned long long ns) { g_wait_limit_ns = ns; }
 
 __device__ __forceinline__ long long to_fixed(float x) {
     // x * 2^32 is exact in float; conversion rounds the part below 2^-32 to nearest
@@ -1981,7 +1985,8 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
     const int M = ctl->M_cur;
     const JointWs& W_ = X.ws;
     float4* win = wins[warp];
-    const unsigned long long deadline = now_ns() + trial_deadline(M);
+    const unsigned long long deadline =
+        now_ns() + (X.wait_limit_ns ? X.wait_limit_ns : trial_deadline(M));
     const bool dag = *(volatile int*)&ctl->dag_bad[X.it] == 0;
     bool stop = false;
     int next = -1;   // a successor this CTA made ready itself: tried next, without the queue
@@ -2341,6 +2346,7 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
     const int tiles_b = (int)((ws.mcap + kScanTile - 1) / kScanTile);
     TrialCtx X;
     X.ws = ws;
+    X.wait_limit_ns = cm.wait_limit_ns;
 
     for (int it = 0; it < cm.N; ++it) {
         // large-error set, its ordered list, and its components (the list is the Q-list
@@ -2425,6 +2431,7 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
     JointCommon ckey;
     memset(&ckey, 0, sizeof(ckey));
     ckey = cm;
+    ckey.wait_limit_ns = g_wait_limit_ns;   // part of the graph key: a changed limit re-records
     int device = 0;
     GLU_CUDA_TRY(cudaGetDevice(&device));
     static JointGraph g = {};
@@ -2523,6 +2530,7 @@ int launch_joint(const JointArgs& a, void* ws, size_t ws_bytes, glu_joint_stats*
     cm.strict = a.strict;
     cm.conn = a.conn;
     cm.wfmt = a.wfmt;
+    cm.wait_limit_ns = 0;
     return launch_joint_batch(&it, 1, cm, ws, ws_bytes, stats, st);
 }
 

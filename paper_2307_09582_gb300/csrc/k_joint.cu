@@ -47,6 +47,11 @@ constexpr int kScanThreads = 256;   // 16 elements per thread
 constexpr int kTrialThreads = 1024;
 constexpr int kResidChunk = 8192;
 constexpr int kMaxSlots = 4096;
+// The general path's affected blocks, listed per task slot for the first kListSlots slots (up to
+// kSlotA blocks each); other tasks enumerate (block, neighbour) items and skip the ones they do
+// not own.
+constexpr int kListSlots = 256;
+constexpr int kSlotA = 2048;
 constexpr int kSmax = 9;            // largest window
 
 // One image of a batch.
@@ -131,10 +136,11 @@ struct JointWs {
     int* slot_j;
     int* slot_n;            // items
     int* slot_img;          // image of the component
-    int* slot_kind;         // 0 trial, 1 rollback
+    int* slot_kind;         // bit 0: rollback (else trial); bit 1: items from the slot's A list
     unsigned long long* slot_e0;
     unsigned long long* slot_e1;
     int* slot_fin;          // items finished
+    int* alist;             // kListSlots * kSlotA: per slot, the owned block items of its task
     // dependency graph of the iteration's trials: succ lists (CSR) and pending-predecessor counts
     int2* dag_cnt;          // mcap: (successors, unused)
     int2* dag_start;        // mcap + 1
@@ -198,6 +204,7 @@ static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t
     t.slot_e0 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
     t.slot_e1 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
     t.slot_fin = (int*)take(sizeof(int) * kMaxSlots);
+    t.alist = (int*)take(sizeof(int) * kListSlots * kSlotA);
     t.ecap = std::min<int64_t>(2 * mcap + (1 << 20), (int64_t)1 << 30);
     t.dag_cnt = (int2*)take(sizeof(int2) * mcap);
     t.dag_start = (int2*)take(sizeof(int2) * (mcap + 1));
@@ -1119,19 +1126,23 @@ __device__ __forceinline__ unsigned long long trial_tag(int it, int j, int phase
 
 // One warp processes item t of component j of image img: chunk t % nch of the block of block
 // item t / nch (STRICT: only if that block item owns the block, so a block reached from several
-// q is processed once), running the trial (kind 0, sums returned) or the rollback (kind 1).
+// q is processed once), running the trial (kind bit 0 clear, sums returned) or the rollback.
+// With kind bit 1 the block items are the owned ones listed in task slot `slot`'s A list.
 __device__ __noinline__ bool process_item(const JBatch& B, const TrialCtx& X, float4* win,
-                                             int j, int img, int stY, int kind, int t, float& e0,
-                                             float& e1) {
+                                             int j, int img, int stY, int kind, int t, int slot,
+                                             float& e0, float& e1) {
     const JImg& I = B.im[img];
     e0 = 0.f;
     e1 = 0.f;
-    const int nch = block_chunks(I), t0 = t / nch, chunk = t % nch;
+    const int nch = block_chunks(I), chunk = t % nch;
+    int t0 = t / nch;
+    if (kind & 2) t0 = __ldcg(&X.ws.alist[(int64_t)slot * kSlotA + t0]);
     int bv, bu;
     if (!item_block(B, X, I, stY, t0, bv, bu)) return false;
-    if (B.strict && __ldcg(&X.ws.bown[I.q0 + (int64_t)bv * I.w + bu]) != t0) return false;
+    if (B.strict && !(kind & 2) && __ldcg(&X.ws.bown[I.q0 + (int64_t)bv * I.w + bu]) != t0)
+        return false;
     const int comp = B.strict ? -1 : j;
-    if (kind == 0) {
+    if ((kind & 1) == 0) {
         switch (I.S) {
             case 1: warp_block_trial<1>(B, X, I, win, bv, bu, chunk, comp, img, e0, e1); break;
             case 3: warp_block_trial<3>(B, X, I, win, bv, bu, chunk, comp, img, e0, e1); break;
@@ -1264,10 +1275,10 @@ __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4
     img = __shfl_sync(0xffffffffu, img, 0);
     stY = __shfl_sync(0xffffffffu, stY, 0);
     float e0, e1;
-    const bool did = process_item(B, X, win, j, img, stY, kind, item, e0, e1);
+    const bool did = process_item(B, X, win, j, img, stY, kind, item, s_sel, e0, e1);
     __syncwarp();
     if (lane == 0) {
-        if (did && kind == 0) {
+        if (did && (kind & 1) == 0) {
             atomicAdd(&W_.slot_e0[s_sel], (unsigned long long)to_fixed(e0));
             atomicAdd(&W_.slot_e1[s_sel], (unsigned long long)to_fixed(e1));
         }
@@ -1292,8 +1303,8 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
     if (nitems <= nwarps) {
         for (int t = warp; t < nitems; t += nwarps) {
             float e0, e1;
-            const bool did = process_item(B, X, win, j, img, stY, kind, t, e0, e1);
-            if (did && kind == 0 && lane == 0) {
+            const bool did = process_item(B, X, win, j, img, stY, kind, t, own, e0, e1);
+            if (did && (kind & 1) == 0 && lane == 0) {
                 atomicAdd(s_e0, (unsigned long long)to_fixed(e0));
                 atomicAdd(s_e1, (unsigned long long)to_fixed(e1));
             }
@@ -1332,7 +1343,7 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
     __syncthreads();
     if (tid == 0) {
         __threadfence();
-        if (kind == 0) {
+        if ((kind & 1) == 0) {
             *s_e0 = ld_volatile_u64(&W_.slot_e0[own]);
             *s_e1 = ld_volatile_u64(&W_.slot_e1[own]);
         }
@@ -1879,7 +1890,7 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
 // General path (components too large for fast_trial): in place with backup planes, block items
 // shared with every idle warp of the grid, explicit rollback. Returns false on an exhausted wait.
 __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int img, int j,
-                          int2 st, int2 en, float4* win, int G, int* s_nu,
+                          int2 st, int2 en, float4* win, int G, int* s_nu, int* s_na,
                           unsigned long long* s_e0, unsigned long long* s_e1, int* s_flag,
                           int* accept, unsigned long long deadline) {
     const JointWs& W_ = X.ws;
@@ -1887,6 +1898,7 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
     const int r = (I.S - 1) / 2;
     if (tid == 0) {
         *s_nu = 0;
+        *s_na = 0;
         *s_e0 = 0ull;
         *s_e1 = 0ull;
         *s_flag = 0;
@@ -1929,15 +1941,24 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
                   (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16));
     }
     // STRICT: every affected block (within r of Q) gets one owner among the block items that
-    // reach it
+    // reach it; the owners also go to this slot's A list, so that the tasks claim only items
+    // with work (without the list, most (block, neighbour) items find another owner)
     const int NB = (2 * r + 1) * (2 * r + 1);
+    const bool listed = B.strict && blockIdx.x < kListSlots;
     if (B.strict) {
         const unsigned long long tagA = trial_tag(X.it, j, 1);
+        int* al = W_.alist + (int64_t)blockIdx.x * kSlotA;
         for (int t = tid; t < nu * NB; t += nthr) {
             int bv, bu;
             if (!item_block(B, X, I, st.y, t, bv, bu)) continue;
             const int64_t b = I.q0 + (int64_t)bv * I.w + bu;
-            if (atomicExch(&W_.stamp[b], tagA) != tagA) W_.bown[b] = t;
+            if (atomicExch(&W_.stamp[b], tagA) != tagA) {
+                W_.bown[b] = t;
+                if (listed) {
+                    const int k = atomicAdd(s_na, 1);
+                    if (k < kSlotA) al[k] = t;
+                }
+            }
         }
     }
     // visible to this CTA after the barrier, and to helpers through the fence thread 0 issues
@@ -1946,14 +1967,16 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
     // trial: Algorithm 1 again on the affected pixels (STRICT: every block within r of Q; PAPER:
     // the component's own pixels), in place, summing e0 and e1; blocks above kChunkPx pixels
     // in several items
-    const int nitems = (B.strict ? nu * NB : nu) * block_chunks(I);
-    bool ok = run_task(B, X, win, j, img, st.y, 0, nitems, G, s_e0, s_e1, s_flag, deadline);
+    const bool use_list = listed && *s_na <= kSlotA;
+    const int nitems = (use_list ? *s_na : B.strict ? nu * NB : nu) * block_chunks(I);
+    const int lk = use_list ? 2 : 0;
+    bool ok = run_task(B, X, win, j, img, st.y, lk, nitems, G, s_e0, s_e1, s_flag, deadline);
     const bool keep = !((long long)*s_e1 > (long long)*s_e0);
     __syncthreads();
     // keep (the results are in place) or roll back: Theta and E from the backup planes, the LR
     // colours from their backups
     if (!keep && ok) {
-        ok = run_task(B, X, win, j, img, st.y, 1, nitems, G, s_e0, s_e1, s_flag, deadline);
+        ok = run_task(B, X, win, j, img, st.y, 1 | lk, nitems, G, s_e0, s_e1, s_flag, deadline);
         for (int t = tid; t < nu; t += nthr) {
             const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
             store_rgb(I.lr, I.lr_pitch, (int)(lq / I.w), (int)(lq % I.w), W_.backup[I.q0 + lq]);
@@ -1976,7 +1999,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     FastSmem& F = *reinterpret_cast<FastSmem*>(dyn_smem);
     __shared__ float4 wins[kTrialThreads / 32][kSmax * kSmax];
-    __shared__ int s_j, s_idx, s_nu, s_accept, s_flag, s_npend, s_povf, s_next;
+    __shared__ int s_j, s_idx, s_nu, s_na, s_accept, s_flag, s_npend, s_povf, s_next;
     __shared__ int s_pend[kPend];
     __shared__ unsigned long long s_e0, s_e1;
     __shared__ FastShared sh;
@@ -2122,8 +2145,8 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
         bool ok = true;
         const bool fast = fast_trial(B, X, I, img, j, st, en, F, sh, &accept);
         if (!fast)
-            ok = big_trial(B, X, I, img, j, st, en, win, G, &s_nu, &s_e0, &s_e1, &s_flag, &accept,
-                           deadline);
+            ok = big_trial(B, X, I, img, j, st, en, win, G, &s_nu, &s_na, &s_e0, &s_e1, &s_flag,
+                           &accept, deadline);
         if (tid == 0) s_accept = accept;
         GLU_TRACE(X.it, j, 2);
         // the outcome is visible before any successor can start: every write precedes the

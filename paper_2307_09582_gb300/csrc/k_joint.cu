@@ -133,14 +133,13 @@ struct JointWs {
     // one task slot per persistent CTA: the block items of its component's trial or rollback,
     // open to every warp of the grid
     unsigned long long* slot_word;  // (epoch << 32) | next item; odd epoch = open
-    int* slot_j;
-    int* slot_n;            // items
-    int* slot_img;          // image of the component
-    int* slot_kind;         // bit 0: rollback (else trial); bit 1: items from the slot's A list
+    // (component j, items, image * 4 + kind, j's LR list offset); kind bit 0: rollback (else
+    // trial), bit 1: items from the slot's A list
+    int4* slot_info;
     unsigned long long* slot_e0;
     unsigned long long* slot_e1;
     int* slot_fin;          // items finished
-    int* alist;             // kListSlots * kSlotA: per slot, the owned block items of its task
+    int* alist;             // kListSlots * kSlotA: per slot, the LR blocks its task re-searches
     // dependency graph of the iteration's trials: succ lists (CSR) and pending-predecessor counts
     int2* dag_cnt;          // mcap: (successors, unused)
     int2* dag_start;        // mcap + 1
@@ -197,10 +196,7 @@ static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t
     t.sh_w = (float*)take(sizeof(float) * np);
     t.sh_err = (float*)take(sizeof(float) * np);
     t.slot_word = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
-    t.slot_j = (int*)take(sizeof(int) * kMaxSlots);
-    t.slot_n = (int*)take(sizeof(int) * kMaxSlots);
-    t.slot_img = (int*)take(sizeof(int) * kMaxSlots);
-    t.slot_kind = (int*)take(sizeof(int) * kMaxSlots);
+    t.slot_info = (int4*)take(sizeof(int4) * kMaxSlots);
     t.slot_e0 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
     t.slot_e1 = (unsigned long long*)take(sizeof(unsigned long long) * kMaxSlots);
     t.slot_fin = (int*)take(sizeof(int) * kMaxSlots);
@@ -1127,20 +1123,23 @@ __device__ __forceinline__ unsigned long long trial_tag(int it, int j, int phase
 // One warp processes item t of component j of image img: chunk t % nch of the block of block
 // item t / nch (STRICT: only if that block item owns the block, so a block reached from several
 // q is processed once), running the trial (kind bit 0 clear, sums returned) or the rollback.
-// With kind bit 1 the block items are the owned ones listed in task slot `slot`'s A list.
+// With kind bit 1 the block items are the blocks listed in task slot `slot`'s A list.
 __device__ __noinline__ bool process_item(const JBatch& B, const TrialCtx& X, float4* win,
                                              int j, int img, int stY, int kind, int t, int slot,
                                              float& e0, float& e1) {
     const JImg& I = B.im[img];
     e0 = 0.f;
     e1 = 0.f;
-    const int nch = block_chunks(I), chunk = t % nch;
-    int t0 = t / nch;
-    if (kind & 2) t0 = __ldcg(&X.ws.alist[(int64_t)slot * kSlotA + t0]);
+    const int nch = block_chunks(I), t0 = t / nch, chunk = t % nch;
     int bv, bu;
-    if (!item_block(B, X, I, stY, t0, bv, bu)) return false;
-    if (B.strict && !(kind & 2) && __ldcg(&X.ws.bown[I.q0 + (int64_t)bv * I.w + bu]) != t0)
-        return false;
+    if (kind & 2) {   // a listed block: owned by this task, inside the image
+        const int lq = __ldcg(&X.ws.alist[(int64_t)slot * kSlotA + t0]);
+        bv = lq / I.w;
+        bu = lq % I.w;
+    } else {
+        if (!item_block(B, X, I, stY, t0, bv, bu)) return false;
+        if (B.strict && __ldcg(&X.ws.bown[I.q0 + (int64_t)bv * I.w + bu]) != t0) return false;
+    }
     const int comp = B.strict ? -1 : j;
     if ((kind & 1) == 0) {
         switch (I.S) {
@@ -1203,77 +1202,96 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
 // True when slot k holds an open task with unclaimed items (a relaxed snapshot).
 __device__ __forceinline__ bool slot_has_items(const JointWs& W_, int k) {
     const unsigned long long w = ld_volatile_u64(&W_.slot_word[k]);
-    return ((w >> 32) & 1ull) && (int)(w & 0xFFFFFFFFull) < *(volatile const int*)&W_.slot_n[k];
+    return ((w >> 32) & 1ull) &&
+           (int)(w & 0xFFFFFFFFull) < *(volatile const int*)&W_.slot_info[k].y;
+}
+
+__device__ __forceinline__ int4 ld_volatile_i4(const int4* p) {
+    int4 v;
+    asm volatile("ld.volatile.global.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// Lane 0: claim the next item of slot k (item -1 if the slot is closed or has none left).
+__device__ __forceinline__ int claim_item(const JointWs& W_, int k, int4& info) {
+    const unsigned long long old = atom_add_acquire_u64(&W_.slot_word[k], 1ull);
+    if (!((old >> 32) & 1ull)) return -1;
+    const int nx = (int)(old & 0xFFFFFFFFull);
+    info = ld_volatile_i4(&W_.slot_info[k]);
+    if (nx >= info.y) return -1;
+    // the claimer of the last item takes the task off the open count
+    if (nx + 1 == info.y) atomicSub(&W_.ctl->open_tasks, 1);
+    return nx;
 }
 
 // One warp: take one unclaimed item of an open task — its own CTA's slot first, then the slot it
 // helped last (`hint`), otherwise the open task of the smallest component — and process it.
-// Returns false if no item was available.
+// Returns false if no item was available. own_left: the caller's own slot is open and may still
+// have items; it is claimed from directly (no snapshot first), and own_left cleared once it has
+// none.
 //
 // Claiming is one fetch-and-add on the slot's (epoch << 32 | next) word. An increment that lands
 // on a closed slot is harmless (opening overwrites the word); one that lands on an open epoch
 // owns item `next` of that epoch, whose context cannot change before that item is finished.
 __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4* win, int own, int G,
-                         int& hint) {
+                         int& hint, bool& own_left) {
     const JointWs& W_ = X.ws;
     const int lane = threadIdx.x & 31;
-    int s_sel = -1;
-    if (lane == 0) {
-        if (slot_has_items(W_, own)) s_sel = own;
-        else if (hint >= 0 && slot_has_items(W_, hint)) s_sel = hint;
-        else if (*(volatile const int*)&W_.ctl->open_tasks <= 0) s_sel = -2;  // nothing open
+    int s_sel = -1, item = -1;
+    int4 info = make_int4(0, 0, 0, 0);
+    if (own_left) {
+        if (lane == 0) {
+            item = claim_item(W_, own, info);
+            if (item >= 0) s_sel = own;
+        }
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item < 0) own_left = false;
+    }
+    if (item < 0) {
+        if (lane == 0) {
+            if (slot_has_items(W_, own)) s_sel = own;
+            else if (hint >= 0 && slot_has_items(W_, hint)) s_sel = hint;
+            else if (*(volatile const int*)&W_.ctl->open_tasks <= 0) s_sel = -2;  // nothing open
+        }
+        s_sel = __shfl_sync(0xffffffffu, s_sel, 0);
+        if (s_sel == -2) {
+            hint = -1;
+            return false;
+        }
+        if (s_sel < 0) {
+            int bj = 0x7fffffff, bs = -1;
+            for (int k = lane; k < G; k += 32) {
+                if (!slot_has_items(W_, k)) continue;
+                const int jj = *(volatile const int*)&W_.slot_info[k].x;
+                if (jj < bj) { bj = jj; bs = k; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+                if (oj < bj || (oj == bj && os < bs)) { bj = oj; bs = os; }
+            }
+            s_sel = bs;
+        }
+        if (s_sel < 0) {
+            hint = -1;
+            return false;
+        }
+        if (lane == 0) item = claim_item(W_, s_sel, info);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item < 0) {
+            hint = -1;
+            return false;
+        }
     }
     s_sel = __shfl_sync(0xffffffffu, s_sel, 0);
-    if (s_sel == -2) {
-        hint = -1;
-        return false;
-    }
-    if (s_sel < 0) {
-        int bj = 0x7fffffff, bs = -1;
-        for (int k = lane; k < G; k += 32) {
-            if (!slot_has_items(W_, k)) continue;
-            const int jj = *(volatile const int*)&W_.slot_j[k];
-            if (jj < bj) { bj = jj; bs = k; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-            const int os = __shfl_xor_sync(0xffffffffu, bs, o);
-            if (oj < bj || (oj == bj && os < bs)) { bj = oj; bs = os; }
-        }
-        s_sel = bs;
-    }
-    if (s_sel < 0) {
-        hint = -1;
-        return false;
-    }
-    int item = -1, j = 0, kind = 0, stY = 0, img = 0;
-    if (lane == 0) {
-        const unsigned long long old = atom_add_acquire_u64(&W_.slot_word[s_sel], 1ull);
-        if ((old >> 32) & 1ull) {
-            const int nx = (int)(old & 0xFFFFFFFFull);
-            const int n = *(volatile const int*)&W_.slot_n[s_sel];
-            if (nx < n) {
-                item = nx;
-                j = *(volatile const int*)&W_.slot_j[s_sel];
-                kind = *(volatile const int*)&W_.slot_kind[s_sel];
-                img = *(volatile const int*)&W_.slot_img[s_sel];
-                stY = W_.start[j].y;
-                // the claimer of the last item takes the task off the open count
-                if (nx + 1 == n) atomicSub(&W_.ctl->open_tasks, 1);
-            }
-        }
-    }
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item < 0) {
-        hint = -1;
-        return false;
-    }
     hint = s_sel;
-    j = __shfl_sync(0xffffffffu, j, 0);
-    kind = __shfl_sync(0xffffffffu, kind, 0);
-    img = __shfl_sync(0xffffffffu, img, 0);
-    stY = __shfl_sync(0xffffffffu, stY, 0);
+    const int j = __shfl_sync(0xffffffffu, info.x, 0);
+    const int ik = __shfl_sync(0xffffffffu, info.z, 0);
+    const int stY = __shfl_sync(0xffffffffu, info.w, 0);
+    const int img = ik >> 2, kind = ik & 3;
     float e0, e1;
     const bool did = process_item(B, X, win, j, img, stY, kind, item, s_sel, e0, e1);
     __syncwarp();
@@ -1314,10 +1332,7 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
     }
     if (tid == 0) {
         const unsigned long long e = W_.slot_word[own] >> 32;  // even: closed
-        W_.slot_j[own] = j;
-        W_.slot_n[own] = nitems;
-        W_.slot_img[own] = img;
-        W_.slot_kind[own] = kind;
+        W_.slot_info[own] = make_int4(j, nitems, img * 4 + kind, stY);
         W_.slot_e0[own] = 0ull;
         W_.slot_e1[own] = 0ull;
         W_.slot_fin[own] = 0;
@@ -1330,11 +1345,12 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
     // every decision below is warp-uniform (lane 0 reads, all lanes follow), so the warp-wide
     // shuffles inside help_one always run with the full warp
     int hint = -1;
+    bool own_left = true;
     for (;;) {
         int fin = 0;
         if (lane == 0) fin = ld_acquire(&W_.slot_fin[own]) >= nitems;
         if (__shfl_sync(0xffffffffu, fin, 0)) break;
-        if (!help_one(B, X, win, own, G, hint)) __nanosleep(100);
+        if (!help_one(B, X, win, own, G, hint, own_left)) __nanosleep(100);
         if (warp_should_abort(X.ws.ctl, deadline)) {
             if (lane == 0) *s_flag = 1;
             break;
@@ -1956,7 +1972,7 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
                 W_.bown[b] = t;
                 if (listed) {
                     const int k = atomicAdd(s_na, 1);
-                    if (k < kSlotA) al[k] = t;
+                    if (k < kSlotA) al[k] = bv * I.w + bu;
                 }
             }
         }
@@ -2004,6 +2020,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
     __shared__ unsigned long long s_e0, s_e1;
     __shared__ FastShared sh;
     const int tid = threadIdx.x, warp = tid >> 5;
+    bool no_own = false;   // help_one: this CTA has no task of its own open here
     const int G = gridDim.x;
     const int M = ctl->M_cur;
     const JointWs& W_ = X.ws;
@@ -2047,7 +2064,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                 }
                 __syncthreads();
                 if (s_j >= 0 || s_j == -2) break;
-                if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
+                if (!help_one(B, X, win, blockIdx.x, G, hint, no_own)) __nanosleep(200);
                 if (__syncthreads_or(warp_should_abort(ctl, deadline) ? 1 : 0)) {
                     if (tid == 0) s_flag = 1;
                     __syncthreads();
@@ -2118,7 +2135,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                         }
                     }
                     if (__syncthreads_or(mine) == 0) break;
-                    if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
+                    if (!help_one(B, X, win, blockIdx.x, G, hint, no_own)) __nanosleep(200);
                     if (__syncthreads_or(warp_should_abort(ctl, deadline) ? 1 : 0)) {
                         if (tid == 0) s_flag = 1;
                         break;
@@ -2198,7 +2215,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
         int fin = 0;
         if (lane == 0) fin = *(volatile const int*)&ctl->finished[X.it] >= M;
         if (__shfl_sync(0xffffffffu, fin, 0)) break;
-        if (!help_one(B, X, win, blockIdx.x, G, hint)) __nanosleep(200);
+        if (!help_one(B, X, win, blockIdx.x, G, hint, no_own)) __nanosleep(200);
         if (warp_should_abort(ctl, deadline)) break;
     }
 }

@@ -845,30 +845,62 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 if (slot < kCandMax) cand[slot] = i;
             }
         };
-        for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
-            const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
-            const int nb = t % ND;
-            const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
-            const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
-            if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
-            const int64_t b = I.q0 + (int64_t)bv * I.w + bu;
-            if (W.ovf[b]) {
-                // more components than owner slots: read the block's pixel labels
-                const int ys = bv * I.s, xs = bu * I.s;
-                const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
-                int last = -1;
-                for (int k = 0; k < ey * ex; ++k) {
-                    const int i = W.lab[I.p0 + (int64_t)(ys + k / ex) * I.W + xs + k % ex];
-                    if (i >= 0 && i < j && i != last) {
-                        offer(i);
-                        last = i;
+        // kDepsBatch (block, neighbour) pairs per thread and round, their loads issued together
+        // (a block's overflow flag and its owner slots as two 16-byte loads): the largest
+        // components span hundreds of LR blocks, and their CTA sets the kernel's duration
+        constexpr int kDepsBatch = 4;
+        static_assert(kOwnSlots == 8, "owner slots are read as two int4");
+        for (int t0 = threadIdx.x * kDepsBatch; t0 < npairs; t0 += blockDim.x * kDepsBatch) {
+            int64_t bb[kDepsBatch];
+            int bvv[kDepsBatch], buu[kDepsBatch];
+#pragma unroll
+            for (int k = 0; k < kDepsBatch; ++k) {
+                bb[k] = -1;
+                const int t = t0 + k;
+                if (t >= npairs) continue;
+                const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+                const int nb = t % ND;
+                bvv[k] = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+                buu[k] = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+                if (bvv[k] < 0 || bvv[k] >= I.h || buu[k] < 0 || buu[k] >= I.w) continue;
+                bb[k] = I.q0 + (int64_t)bvv[k] * I.w + buu[k];
+            }
+            uint8_t ov[kDepsBatch];
+            int4 o0[kDepsBatch], o1[kDepsBatch];
+#pragma unroll
+            for (int k = 0; k < kDepsBatch; ++k) {
+                ov[k] = 0;
+                o0[k] = o1[k] = make_int4(-1, -1, -1, -1);
+                if (bb[k] < 0) continue;
+                ov[k] = W.ovf[bb[k]];
+                const int4* op = reinterpret_cast<const int4*>(W.own + bb[k] * kOwnSlots);
+                o0[k] = op[0];
+                o1[k] = op[1];
+            }
+#pragma unroll
+            for (int k = 0; k < kDepsBatch; ++k) {
+                if (bb[k] < 0) continue;
+                if (ov[k]) {
+                    // more components than owner slots: read the block's pixel labels
+                    const int ys = bvv[k] * I.s, xs = buu[k] * I.s;
+                    const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
+                    int last = -1;
+                    for (int e = 0; e < ey * ex; ++e) {
+                        const int i = W.lab[I.p0 + (int64_t)(ys + e / ex) * I.W + xs + e % ex];
+                        if (i >= 0 && i < j && i != last) {
+                            offer(i);
+                            last = i;
+                        }
                     }
-                }
-            } else {
-                for (int k = 0; k < kOwnSlots; ++k) {
-                    const int i = W.own[b * kOwnSlots + k];
-                    if (i < 0) break;
-                    if (i < j) offer(i);
+                } else {
+                    // slots fill in order: the first -1 ends the list
+                    const int sl[kOwnSlots] = {o0[k].x, o0[k].y, o0[k].z, o0[k].w,
+                                               o1[k].x, o1[k].y, o1[k].z, o1[k].w};
+#pragma unroll
+                    for (int e = 0; e < kOwnSlots; ++e) {
+                        if (sl[e] < 0) break;
+                        if (sl[e] < j) offer(sl[e]);
+                    }
                 }
             }
         }
@@ -1292,6 +1324,10 @@ __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4
     const int ik = __shfl_sync(0xffffffffu, info.z, 0);
     const int stY = __shfl_sync(0xffffffffu, info.w, 0);
     const int img = ik >> 2, kind = ik & 3;
+#ifdef GLU_TRIAL_TRACE
+    if (lane == 0 && s_sel != (int)blockIdx.x && j < kTraceMax && (kind & 1) == 0)
+        atomicAdd(&g_trace[X.it][j][8], 1ull);
+#endif
     float e0, e1;
     const bool did = process_item(B, X, win, j, img, stY, kind, item, s_sel, e0, e1);
     __syncwarp();
@@ -1986,13 +2022,19 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
     const bool use_list = listed && *s_na <= kSlotA;
     const int nitems = (use_list ? *s_na : B.strict ? nu * NB : nu) * block_chunks(I);
     const int lk = use_list ? 2 : 0;
+    GLU_TRACE(X.it, j, 4);
+#ifdef GLU_TRIAL_TRACE
+    if (tid == 0 && j < kTraceMax) g_trace[X.it][j][9] = (unsigned long long)nitems;
+#endif
     bool ok = run_task(B, X, win, j, img, st.y, lk, nitems, G, s_e0, s_e1, s_flag, deadline);
+    GLU_TRACE(X.it, j, 5);
     const bool keep = !((long long)*s_e1 > (long long)*s_e0);
     __syncthreads();
     // keep (the results are in place) or roll back: Theta and E from the backup planes, the LR
     // colours from their backups
     if (!keep && ok) {
         ok = run_task(B, X, win, j, img, st.y, 1 | lk, nitems, G, s_e0, s_e1, s_flag, deadline);
+        GLU_TRACE(X.it, j, 7);
         for (int t = tid; t < nu; t += nthr) {
             const int64_t lq = (int64_t)W_.ulist[st.y + t] - I.q0;
             store_rgb(I.lr, I.lr_pitch, (int)(lq / I.w), (int)(lq % I.w), W_.backup[I.q0 + lq]);

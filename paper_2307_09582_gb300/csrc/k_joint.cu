@@ -743,7 +743,7 @@ __global__ void k_comp_fill(const __grid_constant__ JBatch B, const int* lab, co
 #ifdef GLU_TRIAL_TRACE
 // Debug builds only: per-component timestamps (claim, dependencies met, trial summed, done).
 constexpr int kTraceMax = 1 << 15;
-static __device__ unsigned long long g_trace[GLU_MAX_ITERS][kTraceMax][10];
+static __device__ unsigned long long g_trace[GLU_MAX_ITERS][kTraceMax][16];
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -1262,13 +1262,13 @@ __device__ __forceinline__ int claim_item(const JointWs& W_, int k, int4& info) 
 // helped last (`hint`), otherwise the open task of the smallest component — and process it.
 // Returns false if no item was available. own_left: the caller's own slot is open and may still
 // have items; it is claimed from directly (no snapshot first), and own_left cleared once it has
-// none.
+// none. own_only: take no item of another slot.
 //
 // Claiming is one fetch-and-add on the slot's (epoch << 32 | next) word. An increment that lands
 // on a closed slot is harmless (opening overwrites the word); one that lands on an open epoch
 // owns item `next` of that epoch, whose context cannot change before that item is finished.
 __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4* win, int own, int G,
-                         int& hint, bool& own_left) {
+                         int& hint, bool& own_left, bool own_only = false) {
     const JointWs& W_ = X.ws;
     const int lane = threadIdx.x & 31;
     int s_sel = -1, item = -1;
@@ -1281,6 +1281,7 @@ __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item < 0) own_left = false;
     }
+    if (item < 0 && own_only) return false;
     if (item < 0) {
         if (lane == 0) {
             if (slot_has_items(W_, own)) s_sel = own;
@@ -1325,11 +1326,20 @@ __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4
     const int stY = __shfl_sync(0xffffffffu, info.w, 0);
     const int img = ik >> 2, kind = ik & 3;
 #ifdef GLU_TRIAL_TRACE
+    const unsigned long long tr0 = gtimer();
     if (lane == 0 && s_sel != (int)blockIdx.x && j < kTraceMax && (kind & 1) == 0)
         atomicAdd(&g_trace[X.it][j][8], 1ull);
 #endif
     float e0, e1;
     const bool did = process_item(B, X, win, j, img, stY, kind, item, s_sel, e0, e1);
+#ifdef GLU_TRIAL_TRACE
+    if (lane == 0 && j < kTraceMax && (kind & 1) == 0) {
+        const unsigned long long tr1 = gtimer();
+        atomicMax(&g_trace[X.it][j][11], tr1);
+        atomicAdd(&g_trace[X.it][j][13], tr1 - tr0);
+        if (item + 1 == info.y) g_trace[X.it][j][10] = tr0;   // the last item claimed
+    }
+#endif
     __syncwarp();
     if (lane == 0) {
         if (did && (kind & 1) == 0) {
@@ -1380,13 +1390,15 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
     __syncthreads();
     // every decision below is warp-uniform (lane 0 reads, all lanes follow), so the warp-wide
     // shuffles inside help_one always run with the full warp
+    // the owner's warps take only this task's items, then wait for its last ones: a warp busy
+    // with another task's item would hold the CTA back after this task is done
     int hint = -1;
     bool own_left = true;
     for (;;) {
         int fin = 0;
         if (lane == 0) fin = ld_acquire(&W_.slot_fin[own]) >= nitems;
         if (__shfl_sync(0xffffffffu, fin, 0)) break;
-        if (!help_one(B, X, win, own, G, hint, own_left)) __nanosleep(100);
+        if (!help_one(B, X, win, own, G, hint, own_left, true)) __nanosleep(64);
         if (warp_should_abort(X.ws.ctl, deadline)) {
             if (lane == 0) *s_flag = 1;
             break;

@@ -203,9 +203,8 @@ def run_glu(args):
     err = torch.empty((H, W), dtype=torch.float32, device=dev)
     wsz = api.glu_joint_workspace_size(H, W, SCALE, params)
     wsbuf = torch.empty(wsz + 256, dtype=torch.uint8, device=dev)
-    Lf = torch.empty((h, w, 3), dtype=torch.float32, device=dev)
-    T1 = torch.empty_like(Lf)
-    T2 = torch.empty_like(Lf)
+    T1 = torch.empty((h, w, 3), dtype=torch.float32, device=dev)
+    T2 = torch.empty_like(T1)
     out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device=dev)
@@ -221,9 +220,8 @@ def run_glu(args):
                                stats=False, workspace=wsbuf)
         if record:
             e[1].record(stream)
-        # LR operator on the optimised LR image (uint8 -> [0,1] float is torch plumbing)
-        torch.div(lr, 255.0, out=Lf)
-        api.glu_fx_filter3(Lf, 0, out=T1)
+        # LR operator on the optimised LR image (the filter reads the uint8 image as x / 255)
+        api.glu_fx_filter3_u8(lr, 0, out=T1)
         api.glu_fx_point(T1, sat=1.3, gamma=1.0, out=T2)
         if record:
             e[2].record(stream)
@@ -294,22 +292,27 @@ def run_glu(args):
                     others={k: dict(ms=v["ms"], frac=(v["work"] / (v["ms"] / 1e3)) / v["peak"])
                             for k, v in cand.items()})
 
-    # end to end through the public API with host buffers: H2D guide, pipeline, D2H result
+    # end to end through the C ABI with host buffers: one glu_pipeline_host call per step copies
+    # the guide in, runs the same pipeline and copies the result out (pinned host memory)
     hr_host = torch.from_numpy(img).pin_memory()
     out_host = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    pws = torch.empty(api.glu_pipeline_host_workspace_size(H, W, SCALE, params) + 256,
+                      dtype=torch.uint8, device=dev)
+    def host_step():
+        api.glu_pipeline_host(hr_host, SCALE, params, 0, 1.3, 1.0, out_host, pws)
+    for _ in range(3):   # the library records the call's CUDA graph on its second sighting
+        host_step()
     e2e_ms = []
-    for i in range(args.steps + 1):
+    for i in range(args.steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        hr.copy_(hr_host, non_blocking=True)
-        step(False)
-        out_host.copy_(out, non_blocking=True)
+        host_step()
         b.record(stream)
         b.synchronize()
-        if i > 0:
-            e2e_ms.append(a.elapsed_time(b))
+        e2e_ms.append(a.elapsed_time(b))
+    del pws
     e2e_tot = max_over_ranks(sum(e2e_ms), ws, dev)
     e2e_val = ws * npx * len(e2e_ms) / (e2e_tot / 1e3) / 1e6
 

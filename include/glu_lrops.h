@@ -14,7 +14,10 @@
 #ifndef GLU_LROPS_H
 #define GLU_LROPS_H
 
+#include <stddef.h>
 #include <stdint.h>
+
+#include "glu.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -25,10 +28,37 @@ extern "C" {
 int glu_fx_filter3(const float* X, int32_t h, int32_t w, int32_t C, int64_t pitch, float* Y,
                    int64_t ypitch, int32_t op, void* stream);
 
+/* The same filter on a uint8 image (colour * 255, e.g. an optimised LR image of
+ * glu_joint_optimize), each value read as x / 255 (correctly rounded). */
+int glu_fx_filter3_u8(const uint8_t* X, int32_t h, int32_t w, int32_t C, int64_t pitch, float* Y,
+                      int64_t ypitch, int32_t op, void* stream);
+
 /* Per-pixel RGB (C = 3): saturation about the Rec. 601 luma, Y = l + sat * (c - l) clamped
  * to [0, 1] (sat = 1 disables), then per-channel c^gamma (gamma = 1 disables). X may equal Y. */
 int glu_fx_point(const float* X, int32_t h, int32_t w, int64_t pitch, float* Y, int64_t ypitch,
                  float sat, float gamma, void* stream);
+
+/* ------------------------------------------------ the benchmark pipeline on host buffers
+ *
+ * One call runs the whole optimise-then-upsample flow of the method (Sec. 3: Theta from the
+ * guide, the operator on the LR image, Eq. 1 back to full resolution) with the guide and the
+ * result in HOST memory: the guide hr_host (H x W x 3 uint8, rows W * 3 bytes apart) is copied
+ * to the device; Algorithm 2 (params: FAST mode, window S, N iterations) optimises the LR image
+ * and Theta (unorm16 weights) at scale `scale`; the LR operator glu_fx_filter3_u8 (op) then
+ * glu_fx_point (sat, gamma) turns the optimised LR image into T; Eq. 1 (glu_apply) upsamples T;
+ * the H x W x 3 float32 result is copied to out_host (rows W * 3 floats apart). Host buffers in
+ * pinned (page-locked) memory give the copies full bandwidth; pageable memory works, slower.
+ *
+ * ws: device workspace of glu_pipeline_host_workspace_size() bytes, 256-byte aligned, owned by
+ * the caller; it holds the device copies of the guide, the LR images, Theta, the result and
+ * Algorithm 2's workspace. Repeated calls with the same buffers replay Algorithm 2 as a CUDA
+ * graph. The call returns after out_host holds the result (it synchronises `stream`); argument
+ * errors return before any copy. 0 if the sizes are invalid. */
+size_t glu_pipeline_host_workspace_size(int32_t H, int32_t W, int32_t scale,
+                                        const glu_params* params);
+int glu_pipeline_host(const uint8_t* hr_host, int32_t H, int32_t W, int32_t scale,
+                      const glu_params* params, int32_t op, float sat, float gamma,
+                      float* out_host, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

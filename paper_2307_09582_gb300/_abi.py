@@ -137,6 +137,10 @@ PROTOTYPES = {
     "glu_version": (ctypes.c_char_p, []),
     "glu_fx_filter3": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _i64, _i32, _vp]),
     "glu_fx_point": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp, _i64, _f, _f, _vp]),
+    "glu_fx_filter3_u8": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _i64, _i32, _vp]),
+    "glu_pipeline_host_workspace_size": (ctypes.c_size_t, [_i32, _i32, _i32, _P(GluParams)]),
+    "glu_pipeline_host": (ctypes.c_int, [_vp, _i32, _i32, _i32, _P(GluParams), _i32, _f, _f,
+                                         _vp, _vp, ctypes.c_size_t, _vp]),
 }
 
 _LIB = None

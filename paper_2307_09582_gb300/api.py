@@ -537,6 +537,44 @@ def glu_fx_filter3(x: torch.Tensor, op: int, out: torch.Tensor | None = None, st
     return out
 
 
+def glu_fx_filter3_u8(x: torch.Tensor, op: int, out: torch.Tensor | None = None, stream=None):
+    """glu_fx_filter3 on a uint8 (h, w, C) image read as x / 255; float32 result."""
+    if x.dtype != torch.uint8:
+        raise TypeError("glu_fx_filter3_u8: uint8 input")
+    h, w, C = x.shape
+    out = torch.empty((h, w, C), dtype=torch.float32, device=x.device) if out is None else out
+    A.check("glu_fx_filter3_u8", lib().glu_fx_filter3_u8(_ptr(x), h, w, C, x.stride(0),
+                                                         _ptr(out), out.stride(0), op,
+                                                         _stream(stream)))
+    return out
+
+
+def glu_pipeline_host_workspace_size(H: int, W: int, scale: int, params: A.GluParams) -> int:
+    return int(lib().glu_pipeline_host_workspace_size(H, W, scale, ctypes.byref(params)))
+
+
+def glu_pipeline_host(hr_host: torch.Tensor, scale: int, params: A.GluParams, op: int,
+                      sat: float, gamma: float, out_host: torch.Tensor,
+                      workspace: torch.Tensor, stream=None) -> torch.Tensor:
+    """The whole pipeline on host buffers (guide in, Algorithm 2, LR operator, Eq. 1, result
+    out) in one library call. hr_host: (H, W, 3) uint8 CPU tensor (pinned for full copy speed);
+    out_host: (H, W, 3) float32 CPU tensor; workspace: a CUDA uint8 tensor of at least
+    glu_pipeline_host_workspace_size() + 256 bytes. Returns out_host once it holds the result."""
+    H, W = hr_host.shape[:2]
+    if (hr_host.device.type != "cpu" or out_host.device.type != "cpu"
+            or hr_host.dtype != torch.uint8 or out_host.dtype != torch.float32
+            or not hr_host.is_contiguous() or not out_host.is_contiguous()
+            or tuple(out_host.shape) != (H, W, 3) or tuple(hr_host.shape) != (H, W, 3)):
+        raise ValueError("glu_pipeline_host: contiguous (H, W, 3) uint8 / float32 host tensors")
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    avail = workspace.numel() - (aligned - base)
+    A.check("glu_pipeline_host", lib().glu_pipeline_host(
+        _ptr(hr_host), H, W, scale, ctypes.byref(params), op, sat, gamma, _ptr(out_host),
+        ctypes.c_void_p(aligned), avail, _stream(stream)))
+    return out_host
+
+
 def glu_fx_point(x: torch.Tensor, sat: float = 1.0, gamma: float = 1.0,
                  out: torch.Tensor | None = None, stream=None):
     """LR operator fixture: saturation about Rec. 601 luma (clamped), then per-channel gamma."""

@@ -87,8 +87,13 @@ int launch_downsample(const glu_image& hr, int s, int mode, const glu_image& lr,
 }
 
 // ------------------------------------------------------------------------------ LR operators
-// op codes: 0 box3, 1 gauss3 (both with clamped edges, float32 in [0,1] units, C channels)
-__global__ void k_op_filter3(const float* X, int h, int w, int C, int64_t pitch, float* Y,
+// op codes: 0 box3, 1 gauss3 (both with clamped edges, [0,1] units, C channels). Input float32,
+// or uint8 read as x / 255 (correctly rounded, as a separate float division would give).
+__device__ __forceinline__ float op_in(float x) { return x; }
+__device__ __forceinline__ float op_in(uint8_t x) { return __fdiv_rn((float)x, 255.0f); }
+
+template <typename TX>
+__global__ void k_op_filter3(const TX* X, int h, int w, int C, int64_t pitch, float* Y,
                              int64_t ypitch, int op) {
     const int64_t n = (int64_t)h * w;
     const float kg[3] = {0.25f, 0.5f, 0.25f};
@@ -101,7 +106,7 @@ __global__ void k_op_filter3(const float* X, int h, int w, int C, int64_t pitch,
                 for (int du = -1; du <= 1; ++du) {
                     const int vv = min(max(v + dv, 0), h - 1), uu = min(max(u + du, 0), w - 1);
                     const float wgt = op == 0 ? (1.0f / 9.0f) : kg[dv + 1] * kg[du + 1];
-                    acc = __fmaf_rn(wgt, X[(int64_t)vv * pitch + (int64_t)uu * C + c], acc);
+                    acc = __fmaf_rn(wgt, op_in(X[(int64_t)vv * pitch + (int64_t)uu * C + c]), acc);
                 }
             Y[(int64_t)v * ypitch + (int64_t)u * C + c] = acc;
         }
@@ -137,6 +142,18 @@ int glu_fx_filter3(const float* X, int32_t h, int32_t w, int32_t C, int64_t pitc
                    int64_t ypitch, int32_t op, void* stream) {
     if (!X || !Y || h <= 0 || w <= 0 || C < 1 || C > 4 || (op != 0 && op != 1) ||
         pitch < (int64_t)w * C || ypitch < (int64_t)w * C || X == Y)
+        return GLU_ERR_INVALID_ARG;
+    const int threads = 256;
+    glu::k_op_filter3<<<glu::grid_for((int64_t)h * w, threads), threads, 0, (cudaStream_t)stream>>>(
+        X, h, w, C, pitch, Y, ypitch, op);
+    GLU_LAUNCH_CHECK();
+    return GLU_OK;
+}
+
+int glu_fx_filter3_u8(const uint8_t* X, int32_t h, int32_t w, int32_t C, int64_t pitch, float* Y,
+                      int64_t ypitch, int32_t op, void* stream) {
+    if (!X || !Y || h <= 0 || w <= 0 || C < 1 || C > 4 || (op != 0 && op != 1) ||
+        pitch < (int64_t)w * C || ypitch < (int64_t)w * C)
         return GLU_ERR_INVALID_ARG;
     const int threads = 256;
     glu::k_op_filter3<<<glu::grid_for((int64_t)h * w, threads), threads, 0, (cudaStream_t)stream>>>(

@@ -230,3 +230,43 @@ def test_tuner_host_side(lib):
     assert lib.glu_tune_import(b"0 0 0 5 8 23 9 0.1\n") == A.GLU_ERR_INVALID_ARG  # no variant 9
     assert lib.glu_tune_import(b"garbage") == A.GLU_ERR_INVALID_ARG
     assert lib.glu_tune_clear() == A.GLU_OK
+
+
+def test_pipeline_host_side(lib):
+    """glu_pipeline_host: workspace size and every argument error, all before any copy."""
+    from paper_2307_09582_gb300 import _abi as A
+    p = A.GluParams()
+    lib.glu_params_default(ctypes.byref(p))
+    H, W, s = 64, 80, 8
+    need = lib.glu_pipeline_host_workspace_size(H, W, s, ctypes.byref(p))
+    # Algorithm 2's workspace plus the device copies: guide (3 B/px), Theta (4 B/px), result
+    # (12 B/px) and three LR images (3 + 12 + 12 B per LR pixel), each 256-byte aligned
+    jws = lib.glu_joint_workspace_size(H, W, s, ctypes.byref(p))
+    assert need >= jws + H * W * (3 + 4 + 12) + 8 * 10 * 27
+    assert need <= jws + H * W * (3 + 4 + 12) + 8 * 10 * 27 + 8 * 256
+    assert lib.glu_pipeline_host_workspace_size(0, W, s, ctypes.byref(p)) == 0
+    assert lib.glu_pipeline_host_workspace_size(H, W, s, None) == 0
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
+    args = lambda **k: (k.get("hr", fake), k.get("H", H), W, s, ctypes.byref(k.get("p", p)),
+                        k.get("op", 1), k.get("sat", 1.3), k.get("gamma", 1.0),
+                        k.get("out", fake), k.get("ws", fake), k.get("wsb", need), None)
+    assert lib.glu_pipeline_host(*args(hr=None)) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_pipeline_host(*args(out=None)) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_pipeline_host(*args(H=0)) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_pipeline_host(*args(op=2)) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_pipeline_host(*args(sat=-1.0)) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_pipeline_host(*args(gamma=0.0)) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_pipeline_host(*args(wsb=need - 1)) == A.GLU_ERR_WORKSPACE
+    assert lib.glu_pipeline_host(*args(ws=ctypes.c_void_p(0x1010))) == A.GLU_ERR_WORKSPACE
+    assert lib.glu_pipeline_host(*args(ws=None)) == A.GLU_ERR_WORKSPACE
+    q = A.GluParams()
+    lib.glu_params_default(ctypes.byref(q))
+    q.mode = A.GLU_MODE_EXACT
+    assert lib.glu_pipeline_host(*args(p=q)) == A.GLU_ERR_UNSUPPORTED
+    q.mode = A.GLU_MODE_FAST
+    q.S = 4
+    assert lib.glu_pipeline_host(*args(p=q)) == A.GLU_ERR_INVALID_ARG
+    # the uint8 filter's own checks
+    assert lib.glu_fx_filter3_u8(None, 8, 10, 3, 30, fake, 30, 0, None) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_fx_filter3_u8(fake, 8, 10, 3, 29, fake, 30, 0, None) == A.GLU_ERR_INVALID_ARG
+    assert lib.glu_fx_filter3_u8(fake, 8, 10, 3, 30, fake, 30, 3, None) == A.GLU_ERR_INVALID_ARG

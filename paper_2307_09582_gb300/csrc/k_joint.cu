@@ -795,6 +795,10 @@ __device__ __forceinline__ void bitonic_sort_smem(int* a, int n2) {
 // come from a shared-memory bitmap over component indices (one atomicOr per candidate) when
 // M <= kDepsBits, else from a sorted candidate list.
 constexpr int kDepsBits = 1 << 16;
+// Neighbourhood bitmap of one component (dilated bounding box of its blocks), used above this
+// many (block, neighbour) pairs.
+constexpr int kNbBits = 1 << 15;
+constexpr int kNbMinPairs = 4096;
 
 template <int PASS>
 __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
@@ -802,7 +806,8 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
     if (!any_active(c)) return;
     __shared__ int cand[kCandMax];
     __shared__ unsigned bits[kDepsBits / 32];
-    __shared__ int s_n, s_bad;
+    __shared__ unsigned nbits[kNbBits / 32];
+    __shared__ int s_n, s_bad, s_vmin, s_vmax, s_umin, s_umax;
     const int M = c->M_cur;
     const bool use_bits = M <= kDepsBits;
     if (PASS == 1) {
@@ -819,7 +824,11 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
     if (use_bits)
         for (int t = threadIdx.x; t < (M + 31) / 32; t += blockDim.x) bits[t] = 0u;
     for (int j = blockIdx.x; j < M; j += gridDim.x) {
-        if (threadIdx.x == 0) s_n = 0;
+        if (threadIdx.x == 0) {
+            s_n = 0;
+            s_vmin = s_umin = 0x7fffffff;
+            s_vmax = s_umax = -1;
+        }
         __syncthreads();
         const int2 st = W.start[j], en = W.start[j + 1];
         const JImg& I = B.im[img_of_p(B, W.roots[j])];
@@ -827,6 +836,42 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
         const int D = B.strict ? 2 * r : r;
         const int ND = (2 * D + 1) * (2 * D + 1);
         const int npairs = (en.y - st.y) * ND;
+        // a large component's (block, neighbour) pairs name each block of its neighbourhood many
+        // times: mark them in a bitmap over the bounding box of its blocks dilated by D, then
+        // look up every marked block once
+        int nitems = npairs, BV0 = 0, BU0 = 0, BW = 1;
+        bool nbmap = false;
+        if (npairs > kNbMinPairs) {
+            for (int t = st.y + (int)threadIdx.x; t < en.y; t += blockDim.x) {
+                const int64_t lq = (int64_t)W.qlist[t] - I.q0;
+                const int v = (int)(lq / I.w), u = (int)(lq % I.w);
+                atomicMin(&s_vmin, v);
+                atomicMax(&s_vmax, v);
+                atomicMin(&s_umin, u);
+                atomicMax(&s_umax, u);
+            }
+            __syncthreads();
+            BV0 = s_vmin - D;
+            BU0 = s_umin - D;
+            BW = s_umax - s_umin + 1 + 2 * D;
+            const int BH = s_vmax - s_vmin + 1 + 2 * D;
+            nbmap = (int64_t)BH * BW <= kNbBits;
+            if (nbmap) {
+                nitems = BH * BW;
+                for (int t = threadIdx.x; t < (nitems + 31) / 32; t += blockDim.x) nbits[t] = 0u;
+                __syncthreads();
+                for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+                    const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+                    const int nb = t % ND;
+                    const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+                    const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+                    if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
+                    const int idx = (bv - BV0) * BW + (bu - BU0);
+                    atomicOr(&nbits[idx >> 5], 1u << (idx & 31));
+                }
+                __syncthreads();
+            }
+        }
         // one candidate predecessor i < j: with the bitmap, the first sighting emits it
         auto offer = [&](int i) {
             if (use_bits) {
@@ -845,24 +890,30 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 if (slot < kCandMax) cand[slot] = i;
             }
         };
-        // kDepsBatch (block, neighbour) pairs per thread and round, their loads issued together
-        // (a block's overflow flag and its owner slots as two 16-byte loads): the largest
-        // components span hundreds of LR blocks, and their CTA sets the kernel's duration
+        // kDepsBatch items (pairs, or bitmap positions) per thread and round, their loads issued
+        // together (a block's overflow flag and its owner slots as two 16-byte loads): the
+        // largest components span hundreds of LR blocks, and their CTA sets the kernel's duration
         constexpr int kDepsBatch = 4;
         static_assert(kOwnSlots == 8, "owner slots are read as two int4");
-        for (int t0 = threadIdx.x * kDepsBatch; t0 < npairs; t0 += blockDim.x * kDepsBatch) {
+        for (int t0 = threadIdx.x * kDepsBatch; t0 < nitems; t0 += blockDim.x * kDepsBatch) {
             int64_t bb[kDepsBatch];
             int bvv[kDepsBatch], buu[kDepsBatch];
 #pragma unroll
             for (int k = 0; k < kDepsBatch; ++k) {
                 bb[k] = -1;
                 const int t = t0 + k;
-                if (t >= npairs) continue;
-                const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
-                const int nb = t % ND;
-                bvv[k] = (int)(lq / I.w) + nb / (2 * D + 1) - D;
-                buu[k] = (int)(lq % I.w) + nb % (2 * D + 1) - D;
-                if (bvv[k] < 0 || bvv[k] >= I.h || buu[k] < 0 || buu[k] >= I.w) continue;
+                if (t >= nitems) continue;
+                if (nbmap) {
+                    if (!((nbits[t >> 5] >> (t & 31)) & 1u)) continue;
+                    bvv[k] = BV0 + t / BW;
+                    buu[k] = BU0 + t % BW;
+                } else {
+                    const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+                    const int nb = t % ND;
+                    bvv[k] = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+                    buu[k] = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+                    if (bvv[k] < 0 || bvv[k] >= I.h || buu[k] < 0 || buu[k] >= I.w) continue;
+                }
                 bb[k] = I.q0 + (int64_t)bvv[k] * I.w + buu[k];
             }
             uint8_t ov[kDepsBatch];

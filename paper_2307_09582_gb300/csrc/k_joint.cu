@@ -1747,21 +1747,30 @@ __device__ __forceinline__ void fast_block_sums(const JImg& I, FastSmem& F, int 
     ns = n;
 }
 
+constexpr int kSuccCache = 32;   // successors of a one-CTA trial's component staged for its commit
+
 struct FastShared {
     int nq, vmin, vmax, umin, umax, na, npx, ok;
     unsigned long long e0, e1;
     int searched;
+    int s0, s1;            // the component's successor range (s1 < 0: not staged)
+    int sc[kSuccCache];    // its first successors
 };
 
 // Tries component j in this CTA if it fits (returns false, having changed nothing, if it does
 // not). On return *accept holds the decision and the global state holds its outcome.
+//
+// stage: the iteration's dependency graph exists; the last warp then stages j's successor list
+// in sh while the others write the kept trial out, so the commit does not wait for it.
 __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int img, int j,
-                          int2 st, int2 en, FastSmem& F, FastShared& sh, int* accept) {
+                          int2 st, int2 en, FastSmem& F, FastShared& sh, int* accept,
+                          bool stage) {
     const JointWs& W_ = X.ws;
     const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x, nwarps = nthr >> 5;
     const int r = (I.S - 1) / 2;
     const int Rm = B.strict ? 2 * r : r, Am = B.strict ? r : 0;
     const int nraw = en.y - st.y;
+    if (tid == 0) sh.s1 = -1;   // read by the commit after later barriers
     if (nraw > kFastQRaw) return false;   // uniform: from global values every thread read
     if (tid == 0) {
         sh.nq = 0;
@@ -1974,6 +1983,15 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
     __syncthreads();
     GLU_TRACE(X.it, j, 6);
     const bool keep = !((long long)sh.e1 > (long long)sh.e0);
+    if (stage && warp == nwarps - 1) {
+        const int lane = tid & 31;
+        const int s0 = W_.dag_start[j].x, s1 = W_.dag_start[j + 1].x;
+        for (int t = lane; t < min(s1 - s0, kSuccCache); t += 32) sh.sc[t] = W_.succ[s0 + t];
+        if (lane == 0) {
+            sh.s0 = s0;
+            sh.s1 = s1;
+        }
+    }
     if (keep) {
         // write the kept trial: Theta / E of every re-searched pixel, then the LR colours
         for (int bi = warp; bi < na; bi += nwarps) {
@@ -2265,7 +2283,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
         const JImg& I = B.im[img];
         int accept = 0;
         bool ok = true;
-        const bool fast = fast_trial(B, X, I, img, j, st, en, F, sh, &accept);
+        const bool fast = fast_trial(B, X, I, img, j, st, en, F, sh, &accept, dag);
         if (!fast)
             ok = big_trial(B, X, I, img, j, st, en, win, G, &s_nu, &s_na, &s_e0, &s_e1, &s_flag,
                            &accept, deadline);
@@ -2287,9 +2305,11 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
         if (dag) {
             if (tid == 0) s_next = -1;
             __syncthreads();
-            const int s0 = W_.dag_start[j].x, s1 = W_.dag_start[j + 1].x;
+            const bool staged = sh.s1 >= 0;   // by the one-CTA trial (written before a barrier)
+            const int s0 = staged ? sh.s0 : W_.dag_start[j].x;
+            const int s1 = staged ? sh.s1 : W_.dag_start[j + 1].x;
             for (int k = s0 + tid; k < s1; k += kTrialThreads) {
-                const int sj = W_.succ[k];
+                const int sj = (staged && k - s0 < kSuccCache) ? sh.sc[k - s0] : W_.succ[k];
                 __threadfence();   // release: this CTA's writes before the count drops
                 if (atomicSub(&W_.pend[sj], 1) == 1) {
                     GLU_TRACE_ANY(X.it, sj, 0);   // the time it became ready

@@ -254,6 +254,16 @@ __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Fetch-and-add with release and acquire semantics at GPU scope: the writes ordered before it
+// (including other threads' writes ordered by a barrier) are visible to whoever observes the
+// result, and the writes released by earlier updates of *p are visible after it.
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+
 __device__ __forceinline__ bool any_active(const JointCtl* c) {
     return *(volatile const int*)&c->active_any != 0;
 }
@@ -2290,10 +2300,10 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
         if (tid == 0) s_accept = accept;
         GLU_TRACE(X.it, j, 2);
         // the outcome is visible before any successor can start: every write precedes the
-        // barrier, and each thread that publishes (a successor, the done flag) fences after it
+        // barrier, and each thread that publishes (a successor, the done flag) does so with
+        // release semantics after it
         __syncthreads();
         if (tid == 0) {
-            __threadfence();
             if (!ok) {
                 set_status(GLU_ERR_TIMEOUT);
                 atomicExch(&ctl->timeout, 1);
@@ -2310,10 +2320,10 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
             const int s1 = staged ? sh.s1 : W_.dag_start[j + 1].x;
             for (int k = s0 + tid; k < s1; k += kTrialThreads) {
                 const int sj = (staged && k - s0 < kSuccCache) ? sh.sc[k - s0] : W_.succ[k];
-                __threadfence();   // release: this CTA's writes before the count drops
-                if (atomicSub(&W_.pend[sj], 1) == 1) {
+                // release: this CTA's writes before the count drops; acquire: the other
+                // predecessors' writes
+                if (atom_add_acq_rel(&W_.pend[sj], -1) == 1) {
                     GLU_TRACE_ANY(X.it, sj, 0);   // the time it became ready
-                    __threadfence();   // acquire: the other predecessors' writes
                     // the first successor this CTA made ready is tried here next; the others
                     // go to the queue
                     if (atomicCAS(&s_next, -1, sj) != -1) {

@@ -33,7 +33,7 @@ WORKLOAD = "joint-optimise+LRop+apply 3840x2160 x8, 5x5 window, 5 Alg.2 iteratio
 OPS_PER_CANDIDATE = 27
 # DRAM bytes (read + write) of the trial kernel over one call (its 5 launches) on this workload,
 # from one ncu capture of the current kernel (profiles/k_trials_joint4k.md)
-TRIALS_DRAM_BYTES_PER_CALL = (90.8 + 39.4) * 1e6
+TRIALS_DRAM_BYTES_PER_CALL = (91.5 + 40.2) * 1e6
 
 
 def peaks():

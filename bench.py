@@ -165,7 +165,8 @@ def run_reference(args):
     line = dict(metric=METRIC, value=value, unit="HR Mpix/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * tot / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD, sample=sample),
+                config=dict(workload=WORKLOAD, H=2160, W=3840, scale=SCALE, window=WIN,
+                            iterations=NITER, joint="STRICT", sample=sample),
                 cpu_baseline=dict(value=value, unit="HR Mpix/s", cores=os.cpu_count(),
                                   kind="oracle", sample=sample),
                 e2e=dict(value=value, unit="HR Mpix/s", h2d_bytes_per_step=0,

@@ -470,3 +470,236 @@ def test_ls_joint_residuals_decrease_and_state_is_consistent():
     f = O.glu_fast(img, r["L"], 8, 3)
     assert np.array_equal(f["ka"], r["ka"]) and np.allclose(f["err"], r["err"])
     assert abs(float(f["err"].sum()) - R[-1]) < 1e-9
+
+
+# ------------------------------------------ Algorithm 1 step 2 and Eq. 4 by independent brute force
+
+def _np_window(L01, s, S, y, x):
+    """(k, colour) of the valid window pixels of HR pixel (y, x), window index ascending."""
+    h, w, _ = L01.shape
+    r = (S - 1) // 2
+    ks, cols = [], []
+    for k in range(S * S):
+        v, u = y // s + k // S - r, x // s + k % S - r
+        if 0 <= v < h and 0 <= u < w:
+            ks.append(k)
+            cols.append(L01[v, u])
+    return ks, np.array(cols)
+
+
+def _first_argmin(vals):
+    """Index of the first minimum (the lowest window index wins exact ties) and the gap to the
+    runner-up (inf if there is none)."""
+    vals = np.asarray(vals)
+    i = int(np.argmin(vals))
+    rest = np.delete(vals, i)
+    return i, (float(rest.min() - vals[i]) if rest.size else math.inf)
+
+
+def np_alg1(I01, L01, s, S, eps):
+    """Algorithm 1 in numpy, everything in [0, 1] colour units: a = nearest window colour
+    (Eq. 3 norm); then every b of the window, b = a included, with the Eq. 5 weight
+    w = d_b / (d_a + d_b + eps) (w = 1 on a zero denominator) and the Eq. 3 error of
+    w L_a + (1 - w) L_b; the smallest error wins, the lowest k_b on exact ties.
+    Returns per-pixel ka, kb, w, err and the margins of both argmins."""
+    H, W, _ = I01.shape
+    res = {k: np.zeros((H, W), np.int64) for k in ("ka", "kb")}
+    for k in ("w", "err", "margin_a", "margin_b"):
+        res[k] = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            ks, cols = _np_window(L01, s, S, y, x)
+            Ip = I01[y, x]
+            d = np.sqrt(((cols - Ip) ** 2).sum(axis=1))
+            ia, ma = _first_argmin(d)
+            ws, errs = [], []
+            for j in range(len(ks)):
+                den = d[ia] + d[j] + eps
+                wj = d[j] / den if den > 0 else 1.0
+                rec = wj * cols[ia] + (1.0 - wj) * cols[j]
+                ws.append(wj)
+                errs.append(math.sqrt(float(((rec - Ip) ** 2).sum())))
+            ib, mb = _first_argmin(errs)
+            res["ka"][y, x], res["kb"][y, x] = ks[ia], ks[ib]
+            res["w"][y, x], res["err"][y, x] = ws[ib], errs[ib]
+            res["margin_a"][y, x], res["margin_b"][y, x] = ma, mb
+    return res
+
+
+def np_glu_exact(I01, L01, s, S, eps):
+    """GLU* (Sec. 3.1) in numpy, [0, 1] units: every unordered pair k_a < k_b of the window with
+    the Eq. 4 weight w = (I - L_b).(L_a - L_b) / (|L_a - L_b|^2 + eps), unclamped; the smallest
+    Eq. 3 error wins, the first pair in (k_a, k_b) order on exact ties; a one-pixel window gives
+    a = b, w = 1."""
+    H, W, _ = I01.shape
+    res = {k: np.zeros((H, W), np.int64) for k in ("ka", "kb")}
+    for k in ("w", "err", "margin"):
+        res[k] = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            ks, cols = _np_window(L01, s, S, y, x)
+            Ip = I01[y, x]
+            if len(ks) == 1:
+                res["ka"][y, x] = res["kb"][y, x] = ks[0]
+                res["w"][y, x] = 1.0
+                res["err"][y, x] = float(np.sqrt(((cols[0] - Ip) ** 2).sum()))
+                res["margin"][y, x] = math.inf
+                continue
+            pairs, ws, errs = [], [], []
+            for i in range(len(ks)):
+                for j in range(i + 1, len(ks)):
+                    dv = cols[i] - cols[j]
+                    den = float(dv @ dv) + eps
+                    wij = float((Ip - cols[j]) @ dv) / den if den > 0 else 1.0
+                    rec = wij * cols[i] + (1.0 - wij) * cols[j]
+                    pairs.append((ks[i], ks[j]))
+                    ws.append(wij)
+                    errs.append(math.sqrt(float(((rec - Ip) ** 2).sum())))
+            t, m = _first_argmin(errs)
+            res["ka"][y, x], res["kb"][y, x] = pairs[t]
+            res["w"][y, x], res["err"][y, x], res["margin"][y, x] = ws[t], errs[t], m
+    return res
+
+
+def _general_position_guide(rng, L_u8, s, H, W, kind):
+    """A guide over LR image L_u8: a third random colours, a third LR colours plus small noise
+    (b = a tends to win there), a third exact copies of a window colour (d_a = 0). `kind` is
+    'u8' or 'f' (floats in [0, 1] with non-integer values)."""
+    h, w, _ = L_u8.shape
+    I = rng.integers(0, 256, size=(H, W, 3)).astype(np.float64)
+    sel = rng.integers(0, 3, size=(H, W))
+    for y in range(H):
+        for x in range(W):
+            v = min(h - 1, max(0, y // s + int(rng.integers(-1, 2))))
+            u = min(w - 1, max(0, x // s + int(rng.integers(-1, 2))))
+            if sel[y, x] == 1:
+                I[y, x] = np.clip(L_u8[v, u] + rng.integers(-4, 5, size=3), 0, 255)
+            elif sel[y, x] == 2:
+                I[y, x] = L_u8[v, u]
+    if kind == "u8":
+        return I.astype(np.uint8), L_u8
+    jitter = rng.uniform(-0.3, 0.3, size=I.shape) * (sel[..., None] == 0)
+    return np.clip(I + jitter, 0, 255) / 255.0, L_u8.astype(np.float64) / 255.0
+
+
+@pytest.mark.parametrize("kind", ["u8", "f"])
+@pytest.mark.parametrize("S", [3, 5])
+@pytest.mark.parametrize("eps", [1e-3, 0.0])
+def test_fast_step2_equals_numpy_brute_force(kind, S, eps):
+    """Algorithm 1 (a, then b over the whole window including b = a, Eq. 5 weight, Eq. 3 error)
+    recomputed by brute force in numpy in [0, 1] units, on guides in general position plus
+    pixels that sit on (or next to) an LR colour. Fixes the b choice (not the runner-up), that
+    b = a stays a candidate, the eps term of Eq. 5 in both unit paths (raw 0..255 and [0, 1]),
+    the tie rule (lowest k_b: with eps = 0 and d_a = 0 every b reconstructs L_a exactly), and
+    the near-tie gaps the parity tests rely on."""
+    rng = np.random.Generator(np.random.PCG64(100 + 10 * S + (1 if kind == "f" else 0)))
+    s, H, W = 3, 14, 13
+    h, w = O.lr_dims(H, W, s)
+    L_u8 = rand_img(rng, h, w)
+    I, L = _general_position_guide(rng, L_u8, s, H, W, kind)
+    got = O.glu_fast(I, L, s, S, eps=eps, gaps=True)
+    ref = np_alg1(O.to_unit(I), O.to_unit(L), s, S, eps)
+    decided = (ref["margin_a"] > 1e-9) & ((ref["margin_b"] > 1e-9) | (ref["margin_b"] == 0.0))
+    assert decided.mean() > 0.6
+    exact_tie = ref["margin_b"] == 0.0
+    for key in ("ka", "kb"):
+        assert np.array_equal(got[key][decided], ref[key][decided]), key
+    assert np.allclose(got["omega"][decided], ref["w"][decided], rtol=0, atol=1e-12)
+    assert np.allclose(got["err"], ref["err"], rtol=0, atol=1e-12)
+    # b = a wins at some pixels with a nonzero error, so dropping that candidate would fail here
+    bwins = decided & (ref["ka"] == ref["kb"]) & (ref["err"] > 1e-6)
+    assert bwins.sum() >= 3
+    # and a proper pair b != a wins at others (the runner-up rule would fail there)
+    assert (decided & (ref["ka"] != ref["kb"])).sum() >= 20
+    if eps == 0.0:
+        # d_a = 0 with eps = 0: every b gives the same (zero) error, the lowest valid k_b wins
+        zero = ref["err"] == 0.0
+        assert zero.sum() > 10 and np.all(exact_tie[zero])
+        for (y, x) in np.argwhere(zero):
+            ks, _ = _np_window(O.to_unit(L), s, S, y, x)
+            assert got["kb"][y, x] == ks[0]
+    # the near-tie gaps: distance to the runner-up of a different colour (equal colours never
+    # appear twice in these windows, so that is the plain runner-up)
+    fin = np.isfinite(ref["margin_a"])
+    assert np.allclose(got["gap_a"][fin], ref["margin_a"][fin], rtol=0, atol=1e-12)
+    fin_b = np.isfinite(ref["margin_b"]) & decided & ~exact_tie
+    assert np.allclose(got["gap_b"][fin_b], ref["margin_b"][fin_b], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["u8", "f"])
+@pytest.mark.parametrize("S", [3, 5])
+def test_exact_eps_term_equals_numpy_brute_force(kind, S):
+    """GLU* with eps = 1e-3 against a numpy brute force written from Eq. 4 in [0, 1] units: the
+    eps of Eq. 4 adds to a squared colour distance, so on raw 0..255 values it must scale by
+    255^2 (by 255 it would give other weights). Both unit paths, ragged borders."""
+    rng = np.random.Generator(np.random.PCG64(200 + S + (7 if kind == "f" else 0)))
+    s, H, W = 3, 10, 11
+    h, w = O.lr_dims(H, W, s)
+    L_u8 = rand_img(rng, h, w)
+    # near-duplicate LR colours make |L_a - L_b|^2 comparable to eps, where eps matters most
+    L_u8[1, 1] = np.clip(L_u8[1, 2].astype(int) + [1, 0, 0], 0, 255)
+    I, L = _general_position_guide(rng, L_u8, s, H, W, kind)
+    eps = 1e-3
+    got = O.glu_exact(I, L, s, S, eps=eps)
+    ref = np_glu_exact(O.to_unit(I), O.to_unit(L), s, S, eps)
+    # exact ties (margin 0: a pixel copying a window colour gives error 0 with every pair that
+    # has that colour as L_b) are decided by the first-pair rule and compared as well
+    decided = (ref["margin"] > 1e-9) | (ref["margin"] == 0.0)
+    assert decided.mean() > 0.9 and (ref["margin"] == 0.0).sum() > 5
+    assert np.array_equal(got["ka"][decided], ref["ka"][decided])
+    assert np.array_equal(got["kb"][decided], ref["kb"][decided])
+    scale = np.maximum(1.0, np.abs(ref["w"]))
+    assert np.all(np.abs(got["omega"] - ref["w"])[decided] <= 1e-12 * scale[decided])
+    assert np.allclose(got["err"], ref["err"], rtol=0, atol=1e-12)
+    # the eps term is visible: eps = 0 changes some weights by far more than the tolerance
+    z = O.glu_exact(I, L, s, S, eps=0.0)
+    same = (z["ka"] == got["ka"]) & (z["kb"] == got["kb"])
+    assert np.abs(z["omega"] - got["omega"])[same].max() > 1e-6
+
+
+# ----------------------------------------------- Algorithm 2: equality and the two stop rules
+
+def _equal_trial_guide():
+    """A 2x2 guide, one LR pixel (s = 2), window 1x1, eps = 0, colours differing only in the red
+    channel so every distance and sum is an exact integer. The grid sample (1, 1) is 0; the
+    other pixels are 102, 51, 51 (all above tau = 30 in raw units) and form one 8-connected
+    component whose largest error is (0, 0). With eps = 0 and a = b the Eq. 5 weight is 1/2 and
+    the reconstruction is L exactly. Replacing L by 102 gives
+        e0 = 102 + 51 + 51 + 0 = 204 = 0 + 51 + 51 + 102 = e1,
+    a trial with equal errors, which Algorithm 2 keeps (it rolls back only on e1 > e0). The
+    new state repeats the pattern (the sample pixel is now the largest error), so without the
+    rule that stops when R_n does not decrease the loop would keep swapping."""
+    I = np.zeros((2, 2, 3), np.uint8)
+    I[0, 0, 0], I[0, 1, 0], I[1, 0, 0] = 102, 51, 51
+    return I
+
+
+def test_joint_accepts_equal_error_trial_and_stops_on_flat_residual():
+    I = _equal_trial_guide()
+    j = O.joint(I, 2, 1, N=3, eps=0.0, strict=True)
+    assert len(j["iters"]) == 1                      # R_1 == R_0: the loop ends after one
+    it = j["iters"][0]
+    assert (it["n_large"], it["M"], it["accepted"], it["rolled_back"]) == (3, 1, 1, 0)
+    assert list(j["accept_log"]) == [1]              # e1 == e0 is kept
+    assert list(j["L"][0, 0]) == [102, 0, 0]
+    assert j["R0"] == pytest.approx(204 / 255, abs=1e-15)
+    assert it["residual"] == pytest.approx(204 / 255, abs=1e-15)
+    assert it["min_decision_margin"] == math.inf     # |e1 - e0| is exactly 0 (never nonzero)
+    assert np.allclose(j["err"][:, :, None].ravel(), np.array([0, 51, 51, 102]) / 255, atol=1e-15)
+
+
+def test_joint_stops_after_an_iteration_that_keeps_nothing():
+    """Window 1x1, one outlier in a flat block: STRICT rolls the only trial back, the state is
+    unchanged, and the loop ends after that iteration instead of repeating it N times."""
+    s, S = 4, 1
+    I = np.full((8, 8, 3), 0.2)
+    I[0, 0] = [0.8, 0.8, 0.8]
+    j = O.joint(I, s, S, N=3, strict=True)
+    assert len(j["iters"]) == 1
+    assert j["iters"][0]["accepted"] == 0 and j["iters"][0]["rolled_back"] == 1
+    # with something to gain the loop runs on: a planted dot is fixed in iteration 1, so a
+    # second iteration starts and finds nothing above tau
+    I2 = np.full((32, 32, 3), 0.25)
+    I2[9:11, 12:14] = [0.9, 0.1, 0.5]
+    j2 = O.joint(I2, 4, 3, N=3, strict=True)
+    assert len(j2["iters"]) == 2 and j2["iters"][1]["n_large"] == 0

@@ -10,6 +10,10 @@
  * Conventions shared by every call
  *  - All image / parameter buffers are DEVICE memory owned by the caller, unless a comment says
  *    "host". The library never allocates on these calls and keeps no pointer after returning.
+ *  - Host threads: every entry point may be called from several host threads at once (each on
+ *    its own stream); host-side parameter blocks are per call. The joint calls share one graph
+ *    cache and are serialised by a library-wide lock while they issue their launches. The
+ *    profiling switch (glu_joint_profile) and the test hooks are process-wide settings.
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
  *    default stream) unless stated otherwise. Errors in the arguments are reported
  *    synchronously by the return value; no exception crosses the ABI.
@@ -148,11 +152,15 @@ int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* par
  * GLU_JOINT_STATIC_BYTES array in the library's own device memory (held by every GPU that loads
  * the library until the process exits). Arguments and results as glu_joint_optimize, minus the
  * workspace. Returns GLU_ERR_WORKSPACE, before any launch, when glu_joint_workspace_size() for
- * this image exceeds GLU_JOINT_STATIC_BYTES (about 0.9 megapixels at scale 8, 5x5 window, 5
- * iterations). The first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture. All calls on a device share
- * the array (each call initialises what it reads); calls that overlap on the GPU race, so issue
- * them one after another. Allocates nothing. */
+ * this image exceeds GLU_JOINT_STATIC_BYTES: at scale 8, 5x5 window, 5 iterations that is about
+ * 0.88 megapixels (1248 x 702 is the largest 16:9 image that fits, 1024 x 768 fits, 1280 x 720
+ * does not). The first call in each device context looks up the array's device address with
+ * that device current (and loads the library's device code there); make that first call before
+ * any stream capture. All calls on a device share the array (each call initialises what it
+ * reads); calls that overlap on the GPU race, so issue them one after another. Allocates
+ * nothing and creates no stream, event or graph: every launch goes directly onto `stream`
+ * (repeated calls are not recorded as a graph, unlike glu_joint_optimize) and the autotuner does
+ * not time variants during the call. */
 #define GLU_JOINT_STATIC_BYTES (64u << 20)
 int glu_joint_optimize_static(const glu_image* hr, int32_t scale, const glu_params* params,
                               glu_image* lr_out, glu_theta* theta, float* err_map,
@@ -283,6 +291,10 @@ size_t glu_ls_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const gl
 int glu_ls_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
                           glu_image* lr_out, glu_theta* theta, float* err_map,
                           glu_ls_stats* stats, void* ws, size_t ws_bytes, void* stream);
+
+/* Test hook: the number of CUDA graphs glu_joint_optimize / glu_joint_optimize_batched have
+ * recorded in this process so far (a repeated call is recorded once, then replayed). */
+int64_t glu_test_joint_graph_count(void);
 
 /* Test hook (failure detection): the deadline, in nanoseconds, of the waits of Algorithm 2's
  * trial kernel (the ready queue, the general path's items, the in-order fallback); 0 restores

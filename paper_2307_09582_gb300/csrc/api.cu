@@ -40,6 +40,46 @@ int lr_dim(int n, int s) { return (n + s - 1) / s; }
 
 }  // namespace
 
+namespace glu {
+
+int joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
+                   glu_image* lr_out, glu_theta* theta, float* err_map, glu_joint_stats* stats,
+                   void* ws, size_t ws_bytes, void* stream, int direct) {
+    if (!image_ok(hr) || !image_ok(lr_out) || !params_ok(params) || !theta_ok(theta) || scale < 1)
+        return GLU_ERR_INVALID_ARG;
+    if (hr->dtype != GLU_U8 || lr_out->dtype != GLU_U8 || hr->c != 3 || lr_out->c != 3)
+        return GLU_ERR_UNSUPPORTED;
+    if (params->mode != GLU_MODE_FAST) return GLU_ERR_UNSUPPORTED;
+    if (theta->H != hr->h || theta->W != hr->w || theta->S != params->S || theta->scale != scale ||
+        lr_out->h != lr_dim(hr->h, scale) || lr_out->w != lr_dim(hr->w, scale))
+        return GLU_ERR_SHAPE;
+    const size_t need = joint_workspace_bytes(hr->h, hr->w, scale, params->S, params->N);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return GLU_ERR_WORKSPACE;
+    JointArgs a;
+    a.hr = (const uint8_t*)hr->data;
+    a.hr_pitch = hr->pitch;
+    a.lr = (uint8_t*)lr_out->data;
+    a.lr_pitch = lr_out->pitch;
+    a.H = hr->h;
+    a.W = hr->w;
+    a.h = lr_out->h;
+    a.w = lr_out->w;
+    a.s = scale;
+    a.S = params->S;
+    a.eps255 = fmaxf(params->eps * 255.0f, 1e-12f);  // > 0: see search.cuh
+    a.tau = params->tau;
+    a.N = params->N;
+    a.strict = params->joint == GLU_JOINT_STRICT;
+    a.conn = params->connectivity;
+    a.code = theta->code;
+    a.weight = theta->weight;
+    a.wfmt = theta->wfmt;
+    a.err = err_map;
+    return launch_joint(a, ws, ws_bytes, stats, (cudaStream_t)stream, direct);
+}
+
+}  // namespace glu
+
 extern "C" {
 
 void glu_params_default(glu_params* p) {
@@ -353,38 +393,11 @@ int64_t glu_joint_decisions(const void* ws, size_t ws_bytes, int32_t H, int32_t 
 int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
                        glu_image* lr_out, glu_theta* theta, float* err_map,
                        glu_joint_stats* stats, void* ws, size_t ws_bytes, void* stream) {
-    if (!image_ok(hr) || !image_ok(lr_out) || !params_ok(params) || !theta_ok(theta) || scale < 1)
-        return GLU_ERR_INVALID_ARG;
-    if (hr->dtype != GLU_U8 || lr_out->dtype != GLU_U8 || hr->c != 3 || lr_out->c != 3)
-        return GLU_ERR_UNSUPPORTED;
-    if (params->mode != GLU_MODE_FAST) return GLU_ERR_UNSUPPORTED;
-    if (theta->H != hr->h || theta->W != hr->w || theta->S != params->S || theta->scale != scale ||
-        lr_out->h != lr_dim(hr->h, scale) || lr_out->w != lr_dim(hr->w, scale))
-        return GLU_ERR_SHAPE;
-    const size_t need = joint_workspace_bytes(hr->h, hr->w, scale, params->S, params->N);
-    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return GLU_ERR_WORKSPACE;
-    JointArgs a;
-    a.hr = (const uint8_t*)hr->data;
-    a.hr_pitch = hr->pitch;
-    a.lr = (uint8_t*)lr_out->data;
-    a.lr_pitch = lr_out->pitch;
-    a.H = hr->h;
-    a.W = hr->w;
-    a.h = lr_out->h;
-    a.w = lr_out->w;
-    a.s = scale;
-    a.S = params->S;
-    a.eps255 = fmaxf(params->eps * 255.0f, 1e-12f);  // > 0: see search.cuh
-    a.tau = params->tau;
-    a.N = params->N;
-    a.strict = params->joint == GLU_JOINT_STRICT;
-    a.conn = params->connectivity;
-    a.code = theta->code;
-    a.weight = theta->weight;
-    a.wfmt = theta->wfmt;
-    a.err = err_map;
-    return launch_joint(a, ws, ws_bytes, stats, (cudaStream_t)stream);
+    return joint_optimize(hr, scale, params, lr_out, theta, err_map, stats, ws, ws_bytes, stream,
+                          0);
 }
+
+int64_t glu_test_joint_graph_count(void) { return joint_graphs_recorded(); }
 
 }  // extern "C"
 

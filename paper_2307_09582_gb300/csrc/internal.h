@@ -143,7 +143,13 @@ size_t joint_workspace_bytes(int H, int W, int s, int S, int N);
 int joint_decisions(const void* ws, size_t ws_bytes, int H, int W, int s, int N, int8_t* out,
                     int64_t cap, cudaStream_t st, int64_t* written);
 int launch_joint(const JointArgs& a, void* ws, size_t ws_bytes, glu_joint_stats* stats,
-                 cudaStream_t st);
+                 cudaStream_t st, int direct = 0);
+// Argument checks and launch of glu_joint_optimize; direct as in JointCommon.
+int joint_optimize(const glu_image* hr, int32_t scale, const glu_params* params,
+                   glu_image* lr_out, glu_theta* theta, float* err_map, glu_joint_stats* stats,
+                   void* ws, size_t ws_bytes, void* stream, int direct);
+// CUDA graphs recorded by the joint calls so far (test hook).
+long long joint_graphs_recorded();
 
 // Algorithm 2 over a batch of images in one set of launches.
 constexpr int kMaxJointBatch = 32;
@@ -160,7 +166,10 @@ struct JointItem {
 struct JointCommon {
     float eps255, tau;
     int N, strict, conn, wfmt;
-    unsigned long long wait_limit_ns;   // set by launch_joint_batch (0: the default deadline)
+    unsigned long long wait_limit_ns = 0;  // set by launch_joint_batch (0: the default deadline)
+    // 1: every launch issued directly on the caller's stream: never recorded as a CUDA graph
+    // (no stream creation, capture or instantiation) and no autotuner timing
+    int direct = 0;
 };
 // Test hook: the deadline of the trial kernel's waits (0 restores the default).
 void set_trial_wait_limit(unsigned long long ns);

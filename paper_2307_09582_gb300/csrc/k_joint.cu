@@ -32,10 +32,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <memory>
 #include <mutex>
 
 #include "internal.h"
 #include "search.cuh"
+#include "tune.h"
 
 namespace glu {
 
@@ -2371,9 +2374,10 @@ static int grid_cap(int64_t work, int threads, int per_sm = 16) {
 }
 
 static int launch_trials(const JBatch& B, const TrialCtx& X, cudaStream_t st) {
-    static int blocks_per_sm = -1;
+    static std::atomic<int> blocks_per_sm{-1};   // the same on every device of one kind
     const size_t smem = sizeof(FastSmem);
-    if (blocks_per_sm < 0) {
+    int bps = blocks_per_sm.load();
+    if (bps < 0) {
         if (cudaFuncSetAttribute(k_trials, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return GLU_ERR_CUDA;
@@ -2381,9 +2385,10 @@ static int launch_trials(const JBatch& B, const TrialCtx& X, cudaStream_t st) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trials, kTrialThreads, smem) !=
             cudaSuccess)
             return GLU_ERR_CUDA;
-        blocks_per_sm = nb > 0 ? nb : 1;
+        bps = nb > 0 ? nb : 1;
+        blocks_per_sm.store(bps);
     }
-    int grid = sm_count() * blocks_per_sm;
+    int grid = sm_count() * bps;
     if (grid > kMaxSlots) grid = kMaxSlots;
     k_trials<<<grid, kTrialThreads, smem, st>>>(B, X);
     GLU_LAUNCH_CHECK();
@@ -2457,7 +2462,7 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
                        int64_t np, int64_t nq, int slot, cudaStream_t st) {
     int evi = 0;
 
-    static JBatch B;   // host staging of the parameter block (copied at each launch)
+    JBatch B;   // host staging of the parameter block (copied into each launch)
     memset(&B, 0, sizeof(B));
     int64_t p0 = 0, q0 = 0;
     int c0 = 0;
@@ -2585,11 +2590,37 @@ static bool same_call(const JointGraph& g, int device, const JointItem* items, i
            memcmp(g.items, items, sizeof(JointItem) * (size_t)n) == 0;
 }
 
+static std::atomic<long long> g_graphs_recorded{0};
+long long joint_graphs_recorded() { return g_graphs_recorded.load(); }
+
+// Copies the control block's statistics to the host records (synchronises st).
+static int read_stats(const JointWs& ws, int n, glu_joint_stats* stats, cudaStream_t st) {
+    std::unique_ptr<JointCtl> h(new JointCtl);
+    GLU_CUDA_TRY(cudaMemcpyAsync(h.get(), ws.ctl, sizeof(JointCtl), cudaMemcpyDeviceToHost, st));
+    GLU_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) {
+        glu_joint_stats& o = stats[i];
+        memset(&o, 0, sizeof(o));
+        o.iterations = h->iterations[i];
+        for (int k = 0; k < GLU_MAX_ITERS; ++k) {
+            o.n_large[k] = h->n_large[i][k];
+            o.components[k] = h->M[i][k];
+            o.accepted[k] = h->accepted[i][k];
+            o.rolled_back[k] = h->rolled[i][k];
+            o.searched[k] = (int64_t)h->searched[i][k];
+        }
+        for (int k = 0; k <= h->iterations[i] && k <= GLU_MAX_ITERS; ++k)
+            o.residual[k] = h->residual[i][k];
+    }
+    return h->timeout ? GLU_ERR_TIMEOUT : GLU_OK;
+}
+
 int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, void* wsp,
                        size_t ws_bytes, glu_joint_stats* stats, cudaStream_t st) {
     if (n <= 0) return GLU_OK;
     if (n > kMaxJointBatch) return GLU_ERR_UNSUPPORTED;
-    static std::mutex mu;  // the parameter staging block, the graph cache and the stats copy
+    // the graph cache, the capture stream and the profiling slots are shared by every call
+    static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
     int64_t np, nq, nch;
     batch_sizes(items, n, &np, &nq, &nch);
@@ -2607,6 +2638,14 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
     memset(&ckey, 0, sizeof(ckey));
     ckey = cm;
     ckey.wait_limit_ns = g_wait_limit_ns;   // part of the graph key: a changed limit re-records
+    if (cm.direct) {
+        // every launch straight onto the caller's stream; the graph cache is left alone
+        TuneTimingOff no_timing;
+        const int slot = prof::enabled && prof::used < prof::kSlots ? prof::used++ : -1;
+        const int rc = issue_joint(key, n, ckey, ws, np, nq, slot, st);
+        if (rc) return rc;
+        return stats ? read_stats(ws, n, stats, st) : GLU_OK;
+    }
     int device = 0;
     GLU_CUDA_TRY(cudaGetDevice(&device));
     static JointGraph g = {};
@@ -2635,6 +2674,7 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
         cudaGraphExec_t exec = nullptr;
         if (rc == GLU_OK && ec == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
             g.exec = exec;
+            ++g_graphs_recorded;
             GLU_CUDA_TRY(cudaGraphLaunch(g.exec, st));
             if (prof::enabled) prof::graph_pending = true;
         } else {
@@ -2661,31 +2701,11 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
         rc = issue_joint(key, n, ckey, ws, np, nq, slot, st);
     }
     if (rc) return rc;
-    if (stats) {
-        static JointCtl h;
-        GLU_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
-        GLU_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int i = 0; i < n; ++i) {
-            glu_joint_stats& o = stats[i];
-            memset(&o, 0, sizeof(o));
-            o.iterations = h.iterations[i];
-            for (int k = 0; k < GLU_MAX_ITERS; ++k) {
-                o.n_large[k] = h.n_large[i][k];
-                o.components[k] = h.M[i][k];
-                o.accepted[k] = h.accepted[i][k];
-                o.rolled_back[k] = h.rolled[i][k];
-                o.searched[k] = (int64_t)h.searched[i][k];
-            }
-            for (int k = 0; k <= h.iterations[i] && k <= GLU_MAX_ITERS; ++k)
-                o.residual[k] = h.residual[i][k];
-        }
-        if (h.timeout) return GLU_ERR_TIMEOUT;
-    }
-    return GLU_OK;
+    return stats ? read_stats(ws, n, stats, st) : GLU_OK;
 }
 
 int launch_joint(const JointArgs& a, void* ws, size_t ws_bytes, glu_joint_stats* stats,
-                 cudaStream_t st) {
+                 cudaStream_t st, int direct) {
     JointItem it;
     it.hr = a.hr;
     it.hr_pitch = a.hr_pitch;
@@ -2706,6 +2726,7 @@ int launch_joint(const JointArgs& a, void* ws, size_t ws_bytes, glu_joint_stats*
     cm.conn = a.conn;
     cm.wfmt = a.wfmt;
     cm.wait_limit_ns = 0;
+    cm.direct = direct;
     return launch_joint_batch(&it, 1, cm, ws, ws_bytes, stats, st);
 }
 
@@ -2720,12 +2741,12 @@ int joint_decisions(const void* wsp, size_t ws_bytes, int H, int W, int s, int N
     JointWs ws;
     const size_t need = carve(const_cast<void*>(wsp), np, nq, 1, N, nch, &ws);
     if (ws_bytes < need) return GLU_ERR_WORKSPACE;
-    static JointCtl c;
-    GLU_CUDA_TRY(cudaMemcpyAsync(&c, ws.ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
+    std::unique_ptr<JointCtl> c(new JointCtl);
+    GLU_CUDA_TRY(cudaMemcpyAsync(c.get(), ws.ctl, sizeof(JointCtl), cudaMemcpyDeviceToHost, st));
     GLU_CUDA_TRY(cudaStreamSynchronize(st));
     int64_t off = 0;
-    for (int k = 0; k < c.iterations[0] && k < N; ++k) {
-        const int64_t m = c.M[0][k];
+    for (int k = 0; k < c->iterations[0] && k < N; ++k) {
+        const int64_t m = c->M[0][k];
         if (off + m > cap) return GLU_ERR_INVALID_ARG;
         if (m > 0)
             GLU_CUDA_TRY(cudaMemcpyAsync(out + off, ws.dlog + (int64_t)k * ws.mcap, (size_t)m,

@@ -179,7 +179,7 @@ bool make_hr_map(const SearchArgs& a, CUtensorMap* map, int tile_h);
 
 template <typename HT, int TH, int MINB, bool CP>
 int launch_search_chunk(const SearchArgs* items, int n, cudaStream_t st) {
-    static SBatch B;  // host staging of the parameter block (copied at launch; callers serialise)
+    SBatch B;  // host staging of the parameter block (copied into the launch)
     memset(&B, 0, sizeof(B));
     size_t smem = 0;
     int tiles = 0;

@@ -28,6 +28,7 @@ std::mutex g_mu;
 std::map<Key, Entry> g_cache;
 bool g_on = false;
 int g_forced[kTuneKernels] = {-1, -1};
+thread_local bool t_timing_off = false;
 
 int nvariants(int kernel) {
     if (kernel == kTuneSearch) return kNumSearchVariants;
@@ -38,6 +39,9 @@ int nvariants(int kernel) {
 Key make_key(int kernel, const int k[5]) { return Key(kernel, k[0], k[1], k[2], k[3], k[4]); }
 
 }  // namespace
+
+TuneTimingOff::TuneTimingOff() : prev(t_timing_off) { t_timing_off = true; }
+TuneTimingOff::~TuneTimingOff() { t_timing_off = prev; }
 
 int tune_size_class(long long n) {
     int c = 0;
@@ -60,7 +64,7 @@ int tune_choose(int kernel, const int key[5], int n, const std::function<int(int
             *chosen = it->second.variant;
             return GLU_OK;
         }
-        if (!g_on) return GLU_OK;
+        if (!g_on || t_timing_off) return GLU_OK;
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)

@@ -20,4 +20,14 @@ int tune_choose(int kernel, const int key[5], int nvariants, const std::function
 // ceil(log2(n)) for n >= 1: the size part of a shape class.
 int tune_size_class(long long n);
 
+// While an object of this type lives, tune_choose on this host thread never times variants (it
+// takes a forced or cached choice, else variant 0): no events are created, nothing synchronises.
+struct TuneTimingOff {
+    TuneTimingOff();
+    ~TuneTimingOff();
+    TuneTimingOff(const TuneTimingOff&) = delete;
+    TuneTimingOff& operator=(const TuneTimingOff&) = delete;
+    bool prev;
+};
+
 }  // namespace glu

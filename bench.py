@@ -12,6 +12,8 @@ host cores (the reference arm of this comparison).
 from __future__ import annotations
 
 import argparse
+import datetime
+import hashlib
 import json
 import os
 import statistics
@@ -32,8 +34,19 @@ WORKLOAD = "joint-optimise+LRop+apply 3840x2160 x8, 5x5 window, 5 Alg.2 iteratio
 # canonical FP32 lane operations of Algorithm 1 per window candidate (a-step 7, b-step 20)
 OPS_PER_CANDIDATE = 27
 # DRAM bytes (read + write) of the trial kernel over one call (its 5 launches) on this workload,
-# from one ncu capture of the current kernel (profiles/k_trials_joint4k.md)
-TRIALS_DRAM_BYTES_PER_CALL = (91.5 + 40.2) * 1e6
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of every k_trials launch of
+# `bench.py --kernel-case trials --case-reps 1`), and the digest of the kernel sources it was
+# taken on: once the sources differ, the figure no longer describes the kernel and is not reported
+TRIALS_DRAM = dict(bytes_per_call=(91.5 + 40.2) * 1e6, sources_sha256="unset")
+TRIALS_SOURCES = ("k_joint.cu", "search.cuh", "common.cuh")
+
+
+def trials_sources_digest() -> str:
+    h = hashlib.sha256()
+    for name in TRIALS_SOURCES:
+        with open(os.path.join(ROOT, "paper_2307_09582_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def peaks():
@@ -46,10 +59,13 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms while the timed region runs."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms (with nvidia-smi's own
+    timestamps) from before an untimed pre-roll of the workload until after the timed region,
+    so that the load window holds many samples even when the timed region is short."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, index: int):
         self.index = index
@@ -60,7 +76,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -80,25 +96,46 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    @staticmethod
+    def _when(ts: str):
+        try:
+            return datetime.datetime.strptime(ts.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def summary(self, t0=None, t1=None, timed=None):
+        """Samples taken in [t0, t1] (host wall-clock seconds; the load window): median SM clock,
+        max clock, the throttle reasons seen; `timed` = (start, end) of the timed region, whose
+        own samples are counted and summarised beside."""
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                rows.append((self._when(f[0]), float(f[1]), float(f[2]),
+                             {n for n, v in zip(names, f[5:9]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+
+        def within(a, b):
+            return [r for r in rows if r[0] is None or (a is None or r[0] >= a - 0.05)
+                    and (b is None or r[0] <= b + 0.05)]
+        sel = within(t0, t1)
+        if not sel:
             return None
-        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
-                    samples=len(sm))
+        out = dict(sm_mhz=statistics.median(r[1] for r in sel), sm_max_mhz=max(r[2] for r in sel),
+                   reasons=sorted(set().union(*(r[3] for r in sel))), samples=len(sel),
+                   period_ms=self.PERIOD_MS,
+                   window="untimed pre-roll of the same step, the timed region, the e2e leg")
+        if timed is not None:
+            tr = within(*timed)
+            out["samples_timed_region"] = len(tr)
+            if tr:
+                out["sm_mhz_timed_region"] = statistics.median(r[1] for r in tr)
+                out["reasons_timed_region"] = sorted(set().union(*(r[3] for r in tr)))
+        return out
 
 
 def dist_env():
@@ -138,11 +175,14 @@ def oracle_pipeline_sample(img, rows: int):
     return crop.shape[0] * crop.shape[1], time.perf_counter() - t0
 
 
-def cpu_baseline(img, rows=720):
-    px, sec = oracle_pipeline_sample(img, rows)
+def cpu_baseline(img):
+    """The oracle's whole pipeline on the whole 3840x2160 guide, once (no crop: Algorithm 2's
+    cost follows the components, not the area, so a crop would not give the image's rate)."""
+    px, sec = oracle_pipeline_sample(img, img.shape[0])
     return dict(value=px / sec / 1e6, unit="HR Mpix/s", cores=os.cpu_count(), kind="oracle",
-                sample=f"FP64 oracle pipeline (Alg.2 N={NITER} STRICT, LR op, Eq.1) on the top "
-                       f"{rows} rows of the 3840x2160 guide ({px} px, {sec:.2f} s)")
+                seconds=sec,
+                sample=f"FP64 oracle pipeline (Alg.2 N={NITER} STRICT, LR op, Eq.1) on the whole "
+                       f"3840x2160 guide ({px} px, {sec:.2f} s, one run)")
 
 
 def run_reference(args):
@@ -151,8 +191,13 @@ def run_reference(args):
         return 0
     from paper_2307_09582_gb300.inputs import joint_4k_scene, render_u8
     img = render_u8(joint_4k_scene())
-    rows = 270
-    for _ in range(args.warmup):
+    # a step is the whole guide when K steps of it take at most ~150 s, else the top rows
+    # (a multiple of the scale) that fit that
+    _, t_full = oracle_pipeline_sample(img, img.shape[0])   # the first warm-up step
+    rows = img.shape[0]
+    if args.steps * t_full > 150.0:
+        rows = max(SCALE * 8, int(img.shape[0] * 150.0 / (args.steps * t_full)) // SCALE * SCALE)
+    for _ in range(args.warmup - 1):
         oracle_pipeline_sample(img, rows)
     times, px = [], 0
     for _ in range(args.steps):
@@ -160,8 +205,10 @@ def run_reference(args):
         times.append(sec)
     tot = sum(times)
     value = px * args.steps / tot / 1e6
-    sample = (f"FP64 oracle pipeline on the top {rows} rows of the 3840x2160 guide per step "
-              f"({px} px)")
+    sample = (f"FP64 oracle pipeline on the whole 3840x2160 guide per step ({px} px)"
+              if rows == img.shape[0] else
+              f"FP64 oracle pipeline on the top {rows} rows of the 3840x2160 guide per step "
+              f"({px} px; the whole guide takes {t_full:.1f} s)")
     line = dict(metric=METRIC, value=value, unit="HR Mpix/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * tot / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
@@ -249,14 +296,23 @@ def run_glu(args):
     if status != 0:
         raise RuntimeError(f"device status {status} after the warm-up run")
 
-    api.glu_joint_profile_read()   # forget the warm-up calls
+    clk = ClockSampler(local).__enter__()
+    t_load0 = time.time()
+    # untimed pre-roll of the same step (about a second) so that the clock record under load has
+    # many samples however short the timed region is
+    while time.time() - t_load0 < 1.0:
+        flush.zero_()
+        step(False)
+        torch.cuda.synchronize()
+    api.glu_joint_profile_read()   # forget the warm-up and pre-roll calls
     barrier(ws)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            step(True)
-        torch.cuda.synchronize()
+    t_timed0 = time.time()
+    for _ in range(args.steps):
+        flush.zero_()
+        step(True)
+    torch.cuda.synchronize()
+    t_timed1 = time.time()
     barrier(ws)
     api.glu_joint_profile(False)
     prof = api.glu_joint_profile_read()
@@ -285,10 +341,17 @@ def run_glu(args):
     }
     dom_name, dom = max(cand.items(), key=lambda kv: kv[1]["ms"])
     achieved = dom["work"] / (dom["ms"] / 1e3)
-    traffic = TRIALS_DRAM_BYTES_PER_CALL if "k_trials" in dom_name else None
+    traffic, traffic_note = None, None
+    if "k_trials" in dom_name:
+        if trials_sources_digest() == TRIALS_DRAM["sources_sha256"]:
+            traffic = TRIALS_DRAM["bytes_per_call"]
+            traffic_note = ("DRAM bytes per call (all trial launches of one call) from an ncu "
+                            "capture of these kernel sources")
+        else:
+            traffic_note = "no ncu capture of the current kernel sources"
     roofline = dict(kernel=dom_name, bound=dom["bound"], achieved=achieved, peak=dom["peak"],
                     unit=dom["unit"], frac=achieved / dom["peak"], traffic=traffic,
-                    traffic_unit="DRAM bytes per call (all trial launches of one call, ncu)",
+                    traffic_note=traffic_note,
                     peak_source=pk["src"], launch_ms=dom["ms"],
                     others={k: dict(ms=v["ms"], frac=(v["work"] / (v["ms"] / 1e3)) / v["peak"])
                             for k, v in cand.items()})
@@ -314,6 +377,8 @@ def run_glu(args):
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     del pws
+    t_load1 = time.time()
+    clk.__exit__(None, None, None)
     e2e_tot = max_over_ranks(sum(e2e_ms), ws, dev)
     e2e_val = ws * npx * len(e2e_ms) / (e2e_tot / 1e3) / 1e6
 
@@ -338,7 +403,7 @@ def run_glu(args):
                     e2e=dict(value=e2e_val, unit="HR Mpix/s", h2d_bytes_per_step=img.nbytes,
                              d2h_bytes_per_step=out_host.numel() * 4),
                     gpu_launches=args.steps * (api.joint_launches(NITER) + 3),
-                    clocks=clk.summary(),
+                    clocks=clk.summary(t_load0, t_load1, timed=(t_timed0, t_timed1)),
                     autotune=tuned,
                     breakdown=dict(joint_ms=statistics.mean(joint_ms),
                                    apply_ms=statistics.mean(apply_ms),

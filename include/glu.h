@@ -292,6 +292,20 @@ int glu_ls_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* 
                           glu_image* lr_out, glu_theta* theta, float* err_map,
                           glu_ls_stats* stats, void* ws, size_t ws_bytes, void* stream);
 
+/* Verification aid (not part of the method): log the decisions of Algorithm 2 that FP32 takes
+ * on real-valued comparisons, so that an FP64 reference can follow them where its own values are
+ * closer than FP32 resolution. While set, glu_joint_optimize / glu_joint_optimize_batched append
+ * records of four int32 to the DEVICE buffer buf (16-byte aligned): buf[0] counts the records
+ * written so far (the caller zeroes it before a call), the records follow from byte 16, at most
+ * cap of them (further ones are counted, not stored), in no fixed order:
+ *   (iteration, component, LR pixel, HR pixel): for each LR pixel a trial replaces, the HR pixel
+ *       whose colour replaces it (the component's largest-error pixel in that block);
+ *   (256 + iteration, HR pixel, 1 if in the large-error set else 0, 0): every pixel whose error
+ *       is within 1e-5 of tau at that iteration's threshold pass.
+ * Pixel indices are inside the pixel's own image. buf = NULL turns the log off. Process-wide;
+ * not thread-safe. */
+int glu_test_joint_argmax_log(void* buf, int64_t cap);
+
 /* Test hook: the number of CUDA graphs glu_joint_optimize / glu_joint_optimize_batched have
  * recorded in this process so far (a repeated call is recorded once, then replayed). */
 int64_t glu_test_joint_graph_count(void);

@@ -460,9 +460,9 @@ int oracle_label_components(const uint8_t* mask, int H, int W, int conn, int32_t
 
 /* --------------------------------------------------------------- joint optimisation (Alg. 2) */
 
-/* Per-iteration statistics, 10 doubles each, after a leading R_0:
+/* Per-iteration statistics, 11 doubles each, after a leading R_0:
  *   [n_large, M, accepted, rolled_back, residual, min nonzero |e1 - e0|, min |E_p - tau|,
- *    pixels searched, decisions replayed, argmax near-ties]
+ *    pixels searched, decisions replayed, argmax near-ties, argmax choices replayed]
  * An argmax near-tie is a block [q_up] of a component where the largest error and the error of
  * another pixel of a different colour are within 1e-6: a lower-precision implementation may
  * then pick the other pixel, which is as correct to its precision.
@@ -471,13 +471,38 @@ int oracle_label_components(const uint8_t* mask, int H, int W, int conn, int32_t
  * whose FP64 margin |e1 - e0| is at most force_tol (in [0, 1] units) takes the decision
  * force[t] (t counts trials across iterations in order) instead of its own; such a margin is
  * below the resolution of the other implementation's sums, so either decision is correct.
- * Every other trial decides by the rule e1 > e0 as usual. */
-#define JSTAT 10
+ * Every other trial decides by the rule e1 > e0 as usual.
+ *
+ * Argmax replay (same purpose): `amax` holds amax_n records of four int32 (iteration from 0,
+ * component, LR pixel, HR pixel), sorted by (iteration, component, LR pixel): the other
+ * implementation's choice of the pixel whose colour replaces that LR pixel. Where that pixel
+ * differs from the oracle's own argmax, belongs to the component and to the block, and its FP64
+ * error is within amax_tol (in [0, 1] units) of the block's largest, the oracle takes it: the
+ * two errors are then closer than the other implementation's resolution, so either choice is
+ * correct. Any other record is ignored (a different choice then shows up as a difference).
+ * Records (256 + iteration, HR pixel, membership, 0) in the same array give the other
+ * implementation's large-error membership of pixels near tau; where the oracle's own error is
+ * within thr_tol of tau (FP64), it takes that membership. */
+#define JSTAT 12
+
+/* Index of record (it, j, q) in the sorted array, or -1. */
+static int64_t find_amax(const int32_t* a, int64_t n, int32_t it, int32_t j, int32_t q) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        const int32_t* r = &a[mid * 4];
+        const int less = r[0] < it || (r[0] == it && (r[1] < j || (r[1] == j && r[2] < q)));
+        if (less) lo = mid + 1; else hi = mid;
+    }
+    if (lo < n && a[lo * 4] == it && a[lo * 4 + 1] == j && a[lo * 4 + 2] == q) return lo;
+    return -1;
+}
 
 int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double tau,
                  double unit, int N, int strict, int conn, double* L, int32_t* ka, int32_t* kb,
                  double* omega, double* err, double* stats, int8_t* accept_log, int64_t log_cap,
-                 const int8_t* force, int64_t force_n, double force_tol, int threads) {
+                 const int8_t* force, int64_t force_n, double force_tol, const int32_t* amax,
+                 int64_t amax_n, double amax_tol, double thr_tol, int threads) {
     if (!I || !L || !ka || !kb || !omega || !err || H <= 0 || W <= 0 || s <= 0 || S < 1 ||
         S > 9 || (S % 2) == 0 || N < 0 || (conn != 4 && conn != 8) || !(unit > 0.0))
         return OR_EINVAL;
@@ -535,16 +560,27 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
         /* the set of pixels with large error */
         size_t nlarge = 0;
         double thr_margin = INFINITY;
+        int thr_replayed = 0;
         for (size_t p = 0; p < n; ++p) {
             mask[p] = err[p] > tau;
-            nlarge += mask[p];
             double m = fabs(err[p] - tau);
             if (m < thr_margin) thr_margin = m;
+            if (amax && m <= thr_tol * unit) {
+                /* the record's third field is the membership: look for either value */
+                int64_t k = find_amax(amax, amax_n, 256 + it - 1, (int32_t)p, 0);
+                if (k < 0) k = find_amax(amax, amax_n, 256 + it - 1, (int32_t)p, 1);
+                if (k >= 0 && (uint8_t)(amax[k * 4 + 2] != 0) != mask[p]) {
+                    mask[p] = amax[k * 4 + 2] != 0;
+                    ++thr_replayed;
+                }
+            }
+            nlarge += mask[p];
         }
         if (st) {
             for (int j = 0; j < JSTAT; ++j) st[j] = 0.0;
             st[0] = (double)nlarge;
             st[6] = thr_margin / unit;
+            st[11] = thr_replayed;
         }
         if (nlarge == 0) break;
         int M = oracle_label_components(mask, H, W, conn, lab);
@@ -560,7 +596,7 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
             for (size_t p = 0; p < n; ++p)
                 if (lab[p] >= 0) order[fillp[lab[p]]++] = (int32_t)p;
         }
-        int accepted = 0, rolled = 0, replayed = 0, argmax_ties = 0;
+        int accepted = 0, rolled = 0, replayed = 0, argmax_ties = 0, amax_replayed = 0;
         double min_dec = INFINITY, searched = 0.0;
 
         for (int ci = 0; ci < M; ++ci) {
@@ -589,6 +625,20 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
                 if (p != qpix[q] && !same3(&I[(size_t)p * 3], &I[(size_t)qpix[q] * 3]) &&
                     qbest[q] - err[p] <= 1e-6 * unit)
                     ++argmax_ties;
+            }
+            if (amax) {
+                for (int t = 0; t < nq; ++t) {
+                    int q = lr_list[t];
+                    int64_t k = find_amax(amax, amax_n, it - 1, ci, q);
+                    if (k < 0) continue;
+                    int pg = amax[k * 4 + 3];
+                    if (pg == qpix[q] || pg < 0 || (size_t)pg >= n || lab[pg] != ci) continue;
+                    if ((pg / W) / s * w + (pg % W) / s != q) continue;
+                    if (!(err[pg] >= qbest[q] - amax_tol * unit)) continue;
+                    qpix[q] = pg;
+                    for (int c = 0; c < 3; ++c) qval[(size_t)q * 3 + c] = I[(size_t)pg * 3 + c];
+                    ++amax_replayed;
+                }
             }
             /* the pixels whose Theta and E are re-optimised and summed */
             int na = 0;
@@ -668,7 +718,8 @@ int oracle_joint(const double* I, int H, int W, int s, int S, double eps, double
         for (size_t p = 0; p < n; ++p) R += err[p];
         if (st) {
             st[1] = M; st[2] = accepted; st[3] = rolled; st[4] = R / unit; st[5] = min_dec / unit;
-            st[7] = searched; st[8] = replayed; st[9] = argmax_ties;
+            st[7] = searched; st[8] = replayed; st[9] = argmax_ties; st[10] = amax_replayed;
+            st[11] = thr_replayed;
         }
         if (accepted == 0 || !(R < R_prev)) break;
         R_prev = R;

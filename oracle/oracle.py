@@ -47,7 +47,8 @@ def _lib():
             "oracle_apply_adjoint": [_p, _p, _p, _i, _i, _i, _i, _p, _i, _p, _p, _p],
             "oracle_label_components": [_p, _i, _i, _i, _p],
             "oracle_joint": [_p, _i, _i, _i, _i, _d, _d, _d, _i, _i, _i, _p, _p, _p, _p, _p, _p,
-                             _p, ctypes.c_int64, _p, ctypes.c_int64, _d, _i],
+                             _p, ctypes.c_int64, _p, ctypes.c_int64, _d, _p, ctypes.c_int64, _d,
+                             _d, _i],
             "oracle_ls_update": [_p, _i, _i, _p, _i, _i, _p, _p, _p, _d, _p],
             "oracle_op_box3": [_p, _i, _i, _i, _p],
             "oracle_op_gauss3": [_p, _i, _i, _i, _p],
@@ -212,14 +213,18 @@ def label_components(mask, conn=8):
     return labels, M
 
 
-JSTAT = 10
+JSTAT = 12
 
 
 def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap=1 << 20,
-          force=None, force_tol=0.0, threads=0):
+          force=None, force_tol=0.0, argmax=None, argmax_tol=0.0, thr_tol=0.0, threads=0):
     """Algorithm 2. Returns dict(L, ka, kb, omega, err, R0, iters=[...], accept_log); L is
     uint8 for a uint8 guide. `force` (int8 keep/rollback per trial, in order) is followed only
-    where the oracle's own margin |e1 - e0| <= force_tol (see glu_oracle.c)."""
+    where the oracle's own margin |e1 - e0| <= force_tol; `argmax` (int32 records of another
+    implementation's decisions, the log of glu_test_joint_argmax_log) holds replacement choices,
+    followed only where the logged pixel's FP64 error is within argmax_tol of the block's
+    largest, and large-error memberships, followed only where the oracle's error is within
+    thr_tol of tau (see glu_oracle.c)."""
     is_u8 = np.asarray(I).dtype == np.uint8
     (I,), unit = colours(I)
     H, W, _ = I.shape
@@ -232,10 +237,15 @@ def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap
     stats = np.full(1 + JSTAT * max(N, 1), np.nan)
     log = np.full(log_cap, -1, np.int8)
     fz = None if force is None else np.ascontiguousarray(force, np.int8)
+    am = None
+    if argmax is not None:
+        am = np.asarray(argmax, np.int32).reshape(-1, 4)
+        am = np.ascontiguousarray(am[np.lexsort((am[:, 2], am[:, 1], am[:, 0]))])
     _chk(_lib().oracle_joint(_ptr(I), H, W, s, S, eps, tau, unit, N, int(bool(strict)), conn,
                              _ptr(L),
                              _ptr(ka), _ptr(kb), _ptr(om), _ptr(er), _ptr(stats), _ptr(log),
                              log_cap, _ptr(fz), 0 if fz is None else fz.size, force_tol,
+                             _ptr(am), 0 if am is None else am.shape[0], argmax_tol, thr_tol,
                              threads), "joint")
     iters = []
     for it in range(N):
@@ -246,7 +256,8 @@ def joint(I, s, S, N=3, tau=30.0 / 255.0, eps=1e-3, strict=True, conn=8, log_cap
                           rolled_back=int(st[3]), residual=float(st[4]),
                           min_decision_margin=float(st[5]), min_threshold_margin=float(st[6]),
                           searched=int(st[7]), replayed=int(st[8]),
-                          argmax_near_ties=int(st[9])))
+                          argmax_near_ties=int(st[9]), argmax_replayed=int(st[10]),
+                          threshold_replayed=int(st[11])))
         if st[0] == 0:
             break
     nlog = sum(it["M"] for it in iters)

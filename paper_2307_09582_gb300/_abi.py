@@ -102,6 +102,7 @@ PROTOTYPES = {
     "glu_apply_backward_workspace_size": (ctypes.c_size_t, [_P(GluTheta), _i32]),
     "glu_test_set_wait_limit": (ctypes.c_int, [ctypes.c_uint64]),
     "glu_test_joint_graph_count": (_i64, []),
+    "glu_test_joint_argmax_log": (ctypes.c_int, [_vp, _i64]),
     "glu_apply_backward_plan_size": (ctypes.c_size_t, [_P(GluTheta)]),
     "glu_apply_backward_plan": (ctypes.c_int, [_P(GluTheta), _vp, ctypes.c_size_t, _vp]),
     "glu_apply_backward_planned": (ctypes.c_int, [_P(GluTheta), _vp, _P(GluImage), _P(GluImage),

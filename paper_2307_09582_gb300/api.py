@@ -133,9 +133,11 @@ def glu_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
                        lr_out: torch.Tensor | None = None, theta: Theta | None = None,
                        err_map: torch.Tensor | bool | None = True, stats: bool = True,
                        workspace: torch.Tensor | None = None, wfmt: int = A.GLU_W_F32,
-                       decisions: bool = False, stream=None):
+                       decisions: bool = False, argmax_log: bool = False, stream=None):
     """Algorithm 2. Returns (lr, theta, err_map or None, stats dict or None); with
-    decisions=True the stats hold the per-component keep/rollback log."""
+    decisions=True the stats hold the per-component keep/rollback log, with argmax_log=True
+    (verification aid) also every trial's replacement choices as an (n, 4) int32 array of
+    (iteration, component, LR pixel, HR pixel) records."""
     H, W = hr.shape[:2]
     h, w = lr_dims(H, W, scale)
     if lr_out is None:
@@ -154,10 +156,20 @@ def glu_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
     avail = workspace.numel() - (aligned - base)
     st = A.GluJointStats() if stats else None
     hi, li, td = image(hr), image(lr_out), theta.desc()
-    A.check("glu_joint_optimize", lib().glu_joint_optimize(
-        ctypes.byref(hi), scale, ctypes.byref(params), ctypes.byref(li), ctypes.byref(td),
-        _ptr(err_map), ctypes.byref(st) if st is not None else None, ctypes.c_void_p(aligned),
-        avail, _stream(stream)))
+    alog = None
+    if argmax_log:
+        cap = 4 * h * w * max(params.N, 1) + 65536
+        alog = torch.zeros((cap + 1, 4), dtype=torch.int32, device=hr.device)
+        A.check("glu_test_joint_argmax_log",
+                lib().glu_test_joint_argmax_log(ctypes.c_void_p(alog.data_ptr()), cap))
+    try:
+        A.check("glu_joint_optimize", lib().glu_joint_optimize(
+            ctypes.byref(hi), scale, ctypes.byref(params), ctypes.byref(li), ctypes.byref(td),
+            _ptr(err_map), ctypes.byref(st) if st is not None else None,
+            ctypes.c_void_p(aligned), avail, _stream(stream)))
+    finally:
+        if alog is not None:
+            lib().glu_test_joint_argmax_log(None, 0)
     sd = None
     if st is not None and decisions:
         import numpy as np
@@ -172,6 +184,12 @@ def glu_joint_optimize(hr: torch.Tensor, scale: int, params: A.GluParams,
         decisions = None
     if st is not None:
         sd = _stats_dict(st, decisions)
+        if alog is not None:
+            a = alog.cpu().numpy()
+            n = int(a[0, 0])
+            if n > a.shape[0] - 1:
+                raise RuntimeError(f"argmax log overflow: {n} records")
+            sd["argmax"] = a[1:1 + n].copy()
     return lr_out, theta, err_map, sd
 
 

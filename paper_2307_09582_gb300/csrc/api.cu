@@ -399,6 +399,12 @@ int glu_joint_optimize(const glu_image* hr, int32_t scale, const glu_params* par
 
 int64_t glu_test_joint_graph_count(void) { return joint_graphs_recorded(); }
 
+int glu_test_joint_argmax_log(void* buf, int64_t cap) {
+    if (buf && (cap < 0 || ((uintptr_t)buf & 15u) != 0)) return GLU_ERR_INVALID_ARG;
+    set_argmax_log(buf, buf ? cap : 0);
+    return GLU_OK;
+}
+
 }  // extern "C"
 
 namespace {

@@ -167,12 +167,18 @@ struct JointCommon {
     float eps255, tau;
     int N, strict, conn, wfmt;
     unsigned long long wait_limit_ns = 0;  // set by launch_joint_batch (0: the default deadline)
+    int4* argmax_log = nullptr;            // set by launch_joint_batch (test hook; null: off)
+    long long argmax_cap = 0;
     // 1: every launch issued directly on the caller's stream: never recorded as a CUDA graph
     // (no stream creation, capture or instantiation) and no autotuner timing
     int direct = 0;
+    int pad_ = 0;   // no implicit padding: the graph cache compares these bytes
 };
+static_assert(sizeof(JointCommon) == 56, "JointCommon has no implicit padding");
 // Test hook: the deadline of the trial kernel's waits (0 restores the default).
 void set_trial_wait_limit(unsigned long long ns);
+// Test hook: log every trial's replacement choice (see glu_test_joint_argmax_log); null: off.
+void set_argmax_log(void* buf, long long cap);
 size_t joint_batch_workspace_bytes(const JointItem* items, int n, int N);
 // stats: null or an array of n records
 int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, void* ws,

@@ -299,6 +299,17 @@ __device__ __forceinline__ int block_excl_scan(int v, int* out_excl, int* smem_w
     return total;
 }
 
+// Verification log (test hook, null: off): log[0].x counts records, records from log[1], at most
+// cap of them. Kinds: (iteration, component, LR pixel, HR pixel) for a trial's replacement
+// choice; (256 + iteration, HR pixel, membership, 0) for a pixel whose FP32 error is within
+// kThrLogBand of tau at the threshold pass (indices inside the pixel's image).
+constexpr float kThrLogBand = 1e-5f;
+__device__ __forceinline__ void log_record(int4* log, long long cap, int4 rec) {
+    if (!log) return;
+    const int pos = atomicAdd(&log[0].x, 1);
+    if (pos < cap) log[1 + pos] = rec;
+}
+
 // ---------------------------------------------------------------- control and init kernels
 
 // Every counter of the control block starts at zero, except the active flags of the nimg
@@ -401,7 +412,7 @@ __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int
 // tile of kScanTile pixels also counts the tile's large-error pixels for their ordered
 // compaction.
 __global__ void k_threshold(const __grid_constant__ JBatch B, int* lab, int* own, uint8_t* ovf,
-                            int* tile_cnt, JointCtl* c, int it) {
+                            int* tile_cnt, JointCtl* c, int it, int4* vlog, long long vcap) {
     if (!any_active(c)) return;
     __shared__ int wsum[8];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -411,7 +422,12 @@ __global__ void k_threshold(const __grid_constant__ JBatch B, int* lab, int* own
         if (p >= B.np) break;
         const int i = img_of_p(B, p);
         bool fg = false;
-        if (c->active[i]) fg = B.im[i].err[p - B.im[i].p0] > B.tau;
+        if (c->active[i]) {
+            const float e = B.im[i].err[p - B.im[i].p0];
+            fg = e > B.tau;
+            if (vlog && fabsf(e - B.tau) < kThrLogBand)
+                log_record(vlog, vcap, make_int4(256 + it, (int)(p - B.im[i].p0), fg ? 1 : 0, 0));
+        }
         lab[p] = fg ? (int)p : -1;
         if (fg) {
             if (i != run_img) {
@@ -1026,10 +1042,24 @@ struct TrialCtx {
     JointWs ws;
     int it;
     unsigned long long wait_limit_ns;   // 0: trial_deadline(M)
+    // verification log (null: off; see log_record)
+    int4* alog;
+    long long alog_cap;
 };
 
 static unsigned long long g_wait_limit_ns = 0;   // test hook (glu_test_set_wait_limit)
 void set_trial_wait_limit(unsigned long long ns) { g_wait_limit_ns = ns; }
+static int4* g_argmax_log = nullptr;              // test hook (glu_test_joint_argmax_log)
+static long long g_argmax_cap = 0;
+void set_argmax_log(void* buf, long long cap) {
+    g_argmax_log = (int4*)buf;
+    g_argmax_cap = buf ? cap : 0;
+}
+
+// Appends one replacement choice to the verification log (one thread).
+__device__ __forceinline__ void log_argmax(const TrialCtx& X, int j, int q, int lp) {
+    log_record(X.alog, X.alog_cap, make_int4(X.it, j, q, lp));
+}
 
 __device__ __forceinline__ long long to_fixed(float x) {
     // x * 2^32 is exact in float; conversion rounds the part below 2^-32 to nearest
@@ -1920,6 +1950,7 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
         const int ex = min(I.s, I.W - (x / I.s) * I.s);
         const uint32_t c = F.hrpx[F.pxoff[F.amap[cell] - 1] + (y % I.s) * ex + (x % I.s)];
         F.newc[t] = c;
+        log_argmax(X, j, F.qs[t], (int)lp);
         F.region[cell] = make_float4((float)(c & 255u), (float)((c >> 8) & 255u),
                                      (float)(c >> 16), 0.f);
     }
@@ -2082,6 +2113,7 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
         const uint32_t lp = 0xFFFFFFFFu - (uint32_t)(__ldcg(&W_.best[I.q0 + lq]) & 0xFFFFFFFFull);
         const int y = (int)(lp / (uint32_t)I.W), x = (int)(lp % (uint32_t)I.W);
         W_.backup[I.q0 + lq] = load_rgb(I.lr, I.lr_pitch, qv, qu);
+        log_argmax(X, j, (int)lq, (int)lp);
         const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
         store_rgb(I.lr, I.lr_pitch, qv, qu,
                   (uint32_t)ip[0] | ((uint32_t)ip[1] << 8) | ((uint32_t)ip[2] << 16));
@@ -2527,6 +2559,8 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
     TrialCtx X;
     X.ws = ws;
     X.wait_limit_ns = cm.wait_limit_ns;
+    X.alog = cm.argmax_log;
+    X.alog_cap = cm.argmax_cap;
 
     for (int it = 0; it < cm.N; ++it) {
         // large-error set, its ordered list, and its components (the list is the Q-list
@@ -2534,7 +2568,8 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
         int* fgl = ws.ulist;
         const int lgrid = 2 * sm_count();   // list passes: a thread per large-error pixel or so
         k_threshold<<<tiles_a, kScanThreads, 0, st>>>(B, ws.lab, ws.own, ws.ovf, ws.tile_a,
-                                                       ws.ctl, it);
+                                                       ws.ctl, it, cm.argmax_log,
+                                                       cm.argmax_cap);
         k_tile_scan<0><<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
         k_fg_scatter<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, np, ws.tile_a, fgl, ws.ctl);
         k_ccl_merge<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.ctl);
@@ -2638,6 +2673,8 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
     memset(&ckey, 0, sizeof(ckey));
     ckey = cm;
     ckey.wait_limit_ns = g_wait_limit_ns;   // part of the graph key: a changed limit re-records
+    ckey.argmax_log = g_argmax_log;
+    ckey.argmax_cap = g_argmax_cap;
     if (cm.direct) {
         // every launch straight onto the caller's stream; the graph cache is left alone
         TuneTimingOff no_timing;

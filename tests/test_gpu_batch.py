@@ -98,7 +98,7 @@ def test_optimize_batched_more_than_one_launch(api):
 def joint_single(api, img, s, S, N, strict, wfmt=0):
     hr = torch.from_numpy(img).cuda()
     p = api.glu_params(S=S, N=N, joint=api.GLU_JOINT_STRICT if strict else api.GLU_JOINT_PAPER)
-    return api.glu_joint_optimize(hr, s, p, wfmt=wfmt, decisions=True)
+    return api.glu_joint_optimize(hr, s, p, wfmt=wfmt, decisions=True, argmax_log=True)
 
 
 @pytest.mark.parametrize("strict", [True, False])
@@ -119,12 +119,15 @@ def test_joint_batched_equals_single_and_oracle(api, strict):
         assert sb["iterations"] == ss["iterations"] and sb["R0"] == ss["R0"]
         assert sb["iters"] == ss["iters"]
     # the first item against the oracle, through its single-image twin's decision log
-    from tests.test_gpu_joint import compare, REPLAY_TOL
+    from tests.test_gpu_joint import ARGMAX_TOL, REPLAY_TOL, THR_TOL, compare
     img, s, S = items[0]
     ls, ts, es, ss = joint_single(api, img, s, S, N, strict)
     ss["strict"] = strict
-    ref = O.joint(img, s, S, N=N, strict=strict, force=ss["decisions"], force_tol=REPLAY_TOL)
-    compare(api, img, s, S, N, strict, ls, ts, es, ss, ref)
+    ref = O.joint(img, s, S, N=N, strict=strict, force=ss["decisions"], force_tol=REPLAY_TOL,
+                  argmax=ss["argmax"], argmax_tol=ARGMAX_TOL, thr_tol=THR_TOL)
+    ref["replayed_logs"] = True
+    rep = compare(api, img, s, S, N, strict, ls, ts, es, ss, ref)
+    assert rep["mode"] == "exact", rep
 
 
 def test_joint_batched_sixteen_image_workload(api):

@@ -23,33 +23,50 @@ def api():
 # trials whose FP64 margin |e1 - e0| is below this follow the GPU's logged decision in the
 # oracle (ten times the FP32 resolution of a sum of ~1e3 errors of ~0.1); all others must agree
 REPLAY_TOL = 1e-4
+# replacement choices (the largest-error pixel of a component in an LR block) where the FP64
+# errors of the GPU's pixel and the oracle's are within the error-map tolerance follow the GPU's
+# logged choice in the oracle; all others must agree
+ARGMAX_TOL = 1e-5
+# large-error memberships of pixels whose FP64 error is within this of tau follow the GPU's
+# (FP32 errors agree with FP64 to well below it, and the GPU logs every pixel within 1e-5)
+THR_TOL = 2e-6
 
 
 def run_both(api, img, s, S, N, strict, conn=8):
     hr = torch.from_numpy(img).cuda()
     p = api.glu_params(S=S, N=N, joint=api.GLU_JOINT_STRICT if strict else api.GLU_JOINT_PAPER,
                        connectivity=conn)
-    lr, theta, err, st = api.glu_joint_optimize(hr, s, p, decisions=True)
+    lr, theta, err, st = api.glu_joint_optimize(hr, s, p, decisions=True, argmax_log=True)
     st["strict"] = strict
     torch.cuda.synchronize()
     assert api.glu_device_status() == 0
     ref = O.joint(img, s, S, N=N, strict=strict, conn=conn, force=st["decisions"],
-                  force_tol=REPLAY_TOL)
+                  force_tol=REPLAY_TOL, argmax=st["argmax"], argmax_tol=ARGMAX_TOL,
+                  thr_tol=THR_TOL)
+    ref["replayed_logs"] = True
     return hr, lr, theta, err, st, ref
 
 
 def compare(api, img, s, S, N, strict, lr, theta, err, st, ref):
     """Decisions and final state equal the oracle's. Trials within REPLAY_TOL of a tie follow
-    the GPU's decision in the oracle (counted); every other decision must agree."""
-    thr_ok = all(it["min_threshold_margin"] > 1e-6 for it in ref["iters"])
+    the GPU's decision in the oracle, replacement choices within ARGMAX_TOL the GPU's choice
+    (both counted); every other decision must agree. The report's "mode" says which comparison
+    ran: "exact" (element-wise) or "properties" (a reference computed without the GPU's logs
+    where some E_p is within 1e-6 of tau or an argmax is a near-tie, decisions only the logs
+    let the oracle follow)."""
+    thr_ok = ref.get("replayed_logs", False) or (
+        all(it["min_threshold_margin"] > 1e-6 for it in ref["iters"]) and
+        not any(it["argmax_near_ties"] for it in ref["iters"]))
     gi = st["iters"]
     ri = [it for it in ref["iters"] if it["n_large"] > 0]
     msg = f"\ngpu {gi}\nref {ri}"
     assert st["R0"] == pytest.approx(ref["R0"], rel=1e-6), msg
-    if not thr_ok or any(it["argmax_near_ties"] for it in ri):
-        # a decision within FP32 resolution that replay does not cover (E_p within 1e-6 of tau,
-        # or an argmax near-tie): check what holds for any correct run instead
-        return compare_properties(api, img, s, S, lr, theta, err, st, ref, msg)
+    if not thr_ok:
+        # without the logs, a decision within FP32 resolution may legitimately differ: check
+        # what holds for any correct run instead
+        rep = compare_properties(api, img, s, S, lr, theta, err, st, ref, msg)
+        rep["mode"] = "properties"
+        return rep
     assert len(gi) == len(ri), msg
     for g, r in zip(gi, ri):
         assert (g["n_large"], g["M"], g["accepted"], g["rolled_back"]) == \
@@ -78,6 +95,10 @@ def compare(api, img, s, S, N, strict, lr, theta, err, st, ref):
         assert np.abs(e - ref["err"])[same].max() < 1e-5
         rep = dict(mismatches=int((~same).sum()))
     rep["replayed_decisions"] = replayed
+    rep["replayed_argmax"] = sum(it["argmax_replayed"] for it in ri)
+    rep["argmax_near_ties"] = sum(it["argmax_near_ties"] for it in ri)
+    rep["replayed_threshold"] = sum(it["threshold_replayed"] for it in ri)
+    rep["mode"] = "exact"
     return rep
 
 
@@ -123,6 +144,7 @@ def test_joint_matches_oracle(api, H, W, s, S, strict):
     hr, lr, theta, err, st, ref = run_both(api, img, s, S, N=4, strict=strict)
     rep = compare(api, img, s, S, 4, strict, lr, theta, err, st, ref)
     print(f"\njoint {H}x{W} s={s} S={S} strict={strict}: {st['iters']} {rep}")
+    assert rep["mode"] == "exact", rep
 
 
 def test_joint_4connectivity(api):
@@ -174,3 +196,7 @@ def test_joint_4k_workload_full_parity(api):
     hr, lr, theta, err, st, ref = run_both(api, img, 8, 5, N=5, strict=True)
     rep = compare(api, img, 8, 5, 5, True, lr, theta, err, st, ref)
     print(f"\njoint 4K: {st['iters']} {rep}")
+    # the workload's errors stay clear of tau, so the comparison is element-wise: the final LR
+    # image bit-identical, every decision equal (or replayed within its tolerance), Theta / E as
+    # for Algorithm 1
+    assert rep["mode"] == "exact", rep

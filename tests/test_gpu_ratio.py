@@ -60,6 +60,7 @@ def test_large_ratio_joint_parity(api, H, W, s, S):
     hr, lr, theta, err, st, ref = run_both(api, img, s, S, N=3, strict=True)
     rep = compare(api, img, s, S, 3, True, lr, theta, err, st, ref)
     print(f"\njoint {H}x{W} s={s} S={S}: {st['iters']} {rep}")
+    assert rep["mode"] == "exact", rep
 
 
 def test_window_size_nesting(api):

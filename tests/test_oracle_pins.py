@@ -703,3 +703,41 @@ def test_joint_stops_after_an_iteration_that_keeps_nothing():
     I2[9:11, 12:14] = [0.9, 0.1, 0.5]
     j2 = O.joint(I2, 4, 3, N=3, strict=True)
     assert len(j2["iters"]) == 2 and j2["iters"][1]["n_large"] == 0
+
+
+# ------------------------------------------- replay of another implementation's logged decisions
+
+def test_joint_argmax_replay_follows_only_near_ties():
+    """The verification replay (glu_oracle.c, oracle_joint): a logged replacement pixel is taken
+    only where its FP64 error is within the tolerance of the block's largest. Two pixels of one
+    block with exactly equal errors of different colour: by itself the oracle takes the lowest
+    raster index; with a record naming the other one it takes that; a record naming a pixel far
+    from the largest error is ignored."""
+    I = np.zeros((2, 2, 3), np.uint8)
+    I[0, 0] = (40, 0, 0)
+    I[0, 1] = (0, 40, 0)          # same error (40) as (0, 0), other colour; 8-connected to it
+    own = O.joint(I, 2, 1, N=1, eps=0.0, strict=False)
+    assert list(own["L"][0, 0]) == [40, 0, 0]
+    assert own["iters"][0]["argmax_near_ties"] == 1
+    rec = np.array([[0, 0, 0, 1]], np.int32)      # iteration 0, component 0, LR pixel 0, HR 1
+    rp = O.joint(I, 2, 1, N=1, eps=0.0, strict=False, argmax=rec, argmax_tol=1e-5)
+    assert list(rp["L"][0, 0]) == [0, 40, 0] and rp["iters"][0]["argmax_replayed"] == 1
+    far = np.array([[0, 0, 0, 2]], np.int32)      # pixel (1, 0): error 0, not in the component
+    rf = O.joint(I, 2, 1, N=1, eps=0.0, strict=False, argmax=far, argmax_tol=1e-5)
+    assert list(rf["L"][0, 0]) == [40, 0, 0] and rf["iters"][0]["argmax_replayed"] == 0
+
+
+def test_joint_threshold_replay_follows_only_pixels_at_tau():
+    """A pixel whose error is exactly tau (distance 30 in raw units) is not in the large-error set
+    (E_p > tau is strict); a logged membership of 1 is followed there, but not for a pixel whose
+    error is far from tau."""
+    I = np.zeros((2, 4, 3), np.uint8)
+    I[0, 0] = (30, 0, 0)          # E = 30/255 = tau
+    I[0, 3] = (90, 0, 0)          # E far above tau
+    own = O.joint(I, 2, 1, N=1, eps=0.0, strict=False)
+    assert own["iters"][0]["n_large"] == 1 and own["iters"][0]["min_threshold_margin"] < 1e-12
+    rec = np.array([[256, 0, 1, 0], [256, 3, 0, 0]], np.int32)
+    rp = O.joint(I, 2, 1, N=1, eps=0.0, strict=False, argmax=rec, argmax_tol=1e-5, thr_tol=2e-6)
+    it = rp["iters"][0]
+    assert it["threshold_replayed"] == 1 and it["n_large"] == 2 and it["M"] == 2
+    assert list(rp["L"][0, 0]) == [30, 0, 0] and list(rp["L"][0, 1]) == [90, 0, 0]

@@ -23,11 +23,13 @@
 //               time touch disjoint state, so the result equals the sequential order. Waits are
 //               bounded (GLU_ERR_TIMEOUT) and cannot deadlock (edges only go from lower to
 //               higher indices)
-//   residual    R_n = sum_p E_p per image, exact in units of 2^-32 (64-bit integer sum); an
-//               image stops when its set is empty, when no trial was kept, or when
-//               R_n >= R_{n-1}.
-// Trial sums e0 / e1 are FP32 Kahan sums per LR block (fixed lane order), rounded to 2^-32 and
-// added as 64-bit integers: exact and independent of the order blocks finish in.
+//   residual    R_n = sum_p E_p per image, exact in units of 2^-32 (64-bit integer sum of every
+//               E_p rounded to a multiple of 2^-32); an image stops when its set is empty, when
+//               no trial was kept, or when R_n >= R_{n-1}.
+// Trial sums e0 / e1 use the same arithmetic: every pixel's error rounded to a multiple of 2^-32,
+// added as 64-bit integers, so they are exact and independent of the order blocks finish in, and
+// R_n = R_{n-1} + sum over the kept trials of (e1 - e0) holds exactly: only R_0 needs a pass over
+// the image; the kept trials add their differences to the running residual.
 #include <stddef.h>
 #include <string.h>
 
@@ -379,16 +381,16 @@ __global__ void k_resid_partial(const __grid_constant__ JBatch B, JointCtl* c) {
     }
 }
 
-// it < 0: initial residuals R_0. Otherwise finish iteration it for every active image: record
-// R, decide whether it stops. An image whose large-error set was empty stops without counting
-// the iteration (Algorithm 2 breaks before any trial). The accumulators are cleared for the next
-// residual.
+// it < 0: initial residuals R_0 (the accumulators hold k_resid_partial's sums). Otherwise finish
+// iteration it for every active image: the accumulator holds R_{it} + the kept trials' (e1 - e0),
+// i.e. R_{it+1} exactly; record it and decide whether the image stops. An image whose
+// large-error set was empty stops without counting the iteration (Algorithm 2 breaks before any
+// trial).
 __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int it) {
     if (!any_active(c) || threadIdx.x != 0) return;
     for (int i = 0; i < B.n; ++i) {
         if (!c->active[i]) continue;
         const double R = (double)c->racc[i] * (1.0 / 4294967296.0);
-        c->racc[i] = 0ull;
         if (it < 0) {
             c->residual[i][0] = R;
         } else if (c->M[i][it] == 0) {
@@ -1066,11 +1068,11 @@ __device__ __forceinline__ long long to_fixed(float x) {
     return __float2ll_rn(x * 4294967296.0f);
 }
 
-__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
-    const float y = v - comp;
-    const float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
+// Warp-wide sum of a 64-bit integer (fixed butterfly; integer addition is exact).
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 __device__ __forceinline__ uint32_t load_rgb(const uint8_t* L, int64_t pitch, int v, int u) {
@@ -1140,7 +1142,7 @@ constexpr int kMaxChg = 8;       // replaced LR pixels per window for the exact 
 // One warp re-runs Algorithm 1 on the HR pixels of LR block (bv, bu) of image I against the
 // current LR image (comp >= 0: only the pixels of that component), writing the results in place
 // and the previous values to the backup planes. The previous errors (e0) and the new ones (e1)
-// are summed with Kahan compensation in a fixed lane order and reduced with a fixed butterfly.
+// are summed exactly in 2^-32 units.
 // The general path splits LR blocks of more than kChunkPx HR pixels (scales above 32) into chunks
 // of kChunkPx pixels in raster order, one item each, so that a large block is re-searched by
 // several warps.
@@ -1152,7 +1154,7 @@ __device__ __forceinline__ int block_chunks(const JImg& I) {
 template <int S>
 __device__ __noinline__ void warp_block_trial(const JBatch& B, const TrialCtx& X, const JImg& I,
                                               float4* win, int bv, int bu, int chunk, int comp,
-                                              int img, float& e0, float& e1) {
+                                              int img, long long& e0, long long& e1) {
     constexpr int r = (S - 1) / 2, K = S * S;
     const int lane = threadIdx.x & 31;
     for (int k = lane; k < K; k += 32) {
@@ -1169,7 +1171,7 @@ __device__ __noinline__ void warp_block_trial(const JBatch& B, const TrialCtx& X
     window_masks(bv, bu, I.h, I.w, S, rm, cm);
     const int ys = bv * I.s, xs = bu * I.s;
     const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
-    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+    long long s0 = 0, s1 = 0;
     int nsearched = 0;
     const int jend = min(ey * ex, (chunk + 1) * kChunkPx);
     for (int j = chunk * kChunkPx + lane; j < jend; j += 32) {
@@ -1189,20 +1191,15 @@ __device__ __noinline__ void warp_block_trial(const JBatch& B, const TrialCtx& X
         I.code[lp] = (uint16_t)(o.ka * K + o.kb);
         store_weight(I.weight, B.wfmt, lp, o.omega);
         I.err[lp] = o.err;
-        kahan_add(s0, c0, eold);
-        kahan_add(s1, c1, o.err);
+        s0 += to_fixed(eold);
+        s1 += to_fixed(o.err);
     }
-    float t0 = s0 - c0, t1 = s1 - c1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-        nsearched += __shfl_xor_sync(0xffffffffu, nsearched, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) nsearched += __shfl_xor_sync(0xffffffffu, nsearched, o);
     if (lane == 0 && nsearched)
         atomicAdd(&X.ws.ctl->searched[img][X.it], (unsigned long long)nsearched);
-    e0 = t0;
-    e1 = t1;
+    e0 = warp_sum_ll(s0);
+    e1 = warp_sum_ll(s1);
     __syncwarp();
 }
 
@@ -1252,10 +1249,10 @@ __device__ __forceinline__ unsigned long long trial_tag(int it, int j, int phase
 // With kind bit 1 the block items are the blocks listed in task slot `slot`'s A list.
 __device__ __noinline__ bool process_item(const JBatch& B, const TrialCtx& X, float4* win,
                                              int j, int img, int stY, int kind, int t, int slot,
-                                             float& e0, float& e1) {
+                                             long long& e0, long long& e1) {
     const JImg& I = B.im[img];
-    e0 = 0.f;
-    e1 = 0.f;
+    e0 = 0;
+    e1 = 0;
     const int nch = block_chunks(I), t0 = t / nch, chunk = t % nch;
     int bv, bu;
     if (kind & 2) {   // a listed block: owned by this task, inside the image
@@ -1424,7 +1421,7 @@ __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4
     if (lane == 0 && s_sel != (int)blockIdx.x && j < kTraceMax && (kind & 1) == 0)
         atomicAdd(&g_trace[X.it][j][8], 1ull);
 #endif
-    float e0, e1;
+    long long e0, e1;
     const bool did = process_item(B, X, win, j, img, stY, kind, item, s_sel, e0, e1);
 #ifdef GLU_TRIAL_TRACE
     if (lane == 0 && j < kTraceMax && (kind & 1) == 0) {
@@ -1437,8 +1434,8 @@ __device__ __noinline__ bool help_one(const JBatch& B, const TrialCtx& X, float4
     __syncwarp();
     if (lane == 0) {
         if (did && (kind & 1) == 0) {
-            atomicAdd(&W_.slot_e0[s_sel], (unsigned long long)to_fixed(e0));
-            atomicAdd(&W_.slot_e1[s_sel], (unsigned long long)to_fixed(e1));
+            atomicAdd(&W_.slot_e0[s_sel], (unsigned long long)e0);
+            atomicAdd(&W_.slot_e1[s_sel], (unsigned long long)e1);
         }
         // release: this warp's writes (backup planes, Theta, E, sums) are visible to whoever
         // observes the count
@@ -1460,11 +1457,11 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
     const int own = blockIdx.x;
     if (nitems <= nwarps) {
         for (int t = warp; t < nitems; t += nwarps) {
-            float e0, e1;
+            long long e0, e1;
             const bool did = process_item(B, X, win, j, img, stY, kind, t, own, e0, e1);
             if (did && (kind & 1) == 0 && lane == 0) {
-                atomicAdd(s_e0, (unsigned long long)to_fixed(e0));
-                atomicAdd(s_e1, (unsigned long long)to_fixed(e1));
+                atomicAdd(s_e0, (unsigned long long)e0);
+                atomicAdd(s_e1, (unsigned long long)e1);
             }
         }
         __syncthreads();
@@ -1765,28 +1762,24 @@ __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, Fa
 
 // Block bi's old and new error sums (fixed order) and the number of pixels re-searched.
 __device__ __forceinline__ void fast_block_sums(const JImg& I, FastSmem& F, int RW, int RV0,
-                                                int RU0, int bi, float& e0, float& e1, int& ns) {
+                                                int RU0, int bi, long long& e0, long long& e1,
+                                                int& ns) {
     const int lane = threadIdx.x & 31;
     const int c = F.blocks[bi], off = F.pxoff[bi];
     const int bv = RV0 + c / RW, bu = RU0 + c % RW;
     const int ey = min(I.s, I.H - bv * I.s), ex = min(I.s, I.W - bu * I.s);
-    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+    long long s0 = 0, s1 = 0;
     int n = 0;
     for (int jp = lane; jp < ey * ex; jp += 32) {
         if (F.rcode[off + jp] == kNotSearched) continue;
-        kahan_add(s0, c0, F.eold[off + jp]);
-        kahan_add(s1, c1, F.rerr[off + jp]);
+        s0 += to_fixed(F.eold[off + jp]);
+        s1 += to_fixed(F.rerr[off + jp]);
         ++n;
     }
-    float t0 = s0 - c0, t1 = s1 - c1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-        n += __shfl_xor_sync(0xffffffffu, n, o);
-    }
-    e0 = t0;
-    e1 = t1;
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    e0 = warp_sum_ll(s0);
+    e1 = warp_sum_ll(s1);
     ns = n;
 }
 
@@ -1996,14 +1989,12 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
         long long a0 = 0, a1 = 0;
         int an = 0;
         for (int bi = warp; bi < na; bi += nwarps) {
-            float e0, e1;
+            long long e0, e1;
             int ns;
             fast_block_sums(I, F, RW, RV0, RU0, bi, e0, e1, ns);
-            if (ns > 0) {
-                a0 += to_fixed(e0);
-                a1 += to_fixed(e1);
-                an += ns;
-            }
+            a0 += e0;
+            a1 += e1;
+            an += ns;
         }
         if ((tid & 31) == 0) {
             F.wsum[warp][0] = a0;
@@ -2334,6 +2325,12 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                            &accept, deadline);
         if (tid == 0) s_accept = accept;
         GLU_TRACE(X.it, j, 2);
+#ifdef GLU_TRIAL_TRACE
+        if (tid == 0 && j < kTraceMax) {
+            g_trace[X.it][j][14] = fast ? 1ull : 2ull;
+            g_trace[X.it][j][15] = (unsigned long long)blockIdx.x;
+        }
+#endif
         // the outcome is visible before any successor can start: every write precedes the
         // barrier, and each thread that publishes (a successor, the done flag) does so with
         // release semantics after it
@@ -2344,8 +2341,14 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                 atomicExch(&ctl->timeout, 1);
             }
             W_.dlog[(int64_t)X.it * W_.mcap + j] = (int8_t)(s_accept ? 1 : 0);
-            if (s_accept) atomicAdd(&ctl->accepted[img][X.it], 1);
-            else atomicAdd(&ctl->rolled[img][X.it], 1);
+            if (s_accept) {
+                atomicAdd(&ctl->accepted[img][X.it], 1);
+                // the running residual: exact, since e0 / e1 and R sum the same rounded errors
+                const unsigned long long d = fast ? sh.e1 - sh.e0 : s_e1 - s_e0;
+                if (d) atomicAdd(&ctl->racc[img], d);
+            } else {
+                atomicAdd(&ctl->rolled[img][X.it], 1);
+            }
         }
         if (dag) {
             if (tid == 0) s_next = -1;
@@ -2359,6 +2362,9 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
                 // predecessors' writes
                 if (atom_add_acq_rel(&W_.pend[sj], -1) == 1) {
                     GLU_TRACE_ANY(X.it, sj, 0);   // the time it became ready
+#ifdef GLU_TRIAL_TRACE
+                    if (sj < kTraceMax) g_trace[X.it][sj][12] = (unsigned long long)(j + 1);
+#endif
                     // the first successor this CTA made ready is tried here next; the others
                     // go to the queue
                     if (atomicCAS(&s_next, -1, sj) != -1) {
@@ -2598,7 +2604,7 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
         rc = launch_trials(B, X, st);
         if (rc) return rc;
         prof::mark(slot, evi++, st);
-        k_resid_partial<<<B.nchunks, 256, 0, st>>>(B, ws.ctl);
+        // R_{it+1} = R_it + the kept trials' differences (added by the trials themselves)
         k_resid_final<<<1, 32, 0, st>>>(B, ws.ctl, it);
         GLU_LAUNCH_CHECK();
         prof::mark(slot, evi++, st);
@@ -2802,6 +2808,12 @@ extern "C" int glu_dbg_trace(unsigned long long* host, int64_t n) {
     const size_t bytes = sizeof(unsigned long long) * (size_t)n;
     if (bytes > sizeof(glu::g_trace)) return GLU_ERR_INVALID_ARG;
     return cudaMemcpyFromSymbol(host, glu::g_trace, bytes) == cudaSuccess ? GLU_OK : GLU_ERR_CUDA;
+}
+
+extern "C" int glu_dbg_trace_clear(void) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, glu::g_trace) != cudaSuccess) return GLU_ERR_CUDA;
+    return cudaMemset(p, 0, sizeof(glu::g_trace)) == cudaSuccess ? GLU_OK : GLU_ERR_CUDA;
 }
 #endif
 

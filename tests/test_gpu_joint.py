@@ -172,6 +172,10 @@ def test_joint_strict_invariants_and_determinism(api):
     R = [st1["R0"]] + [it["residual"] for it in st1["iters"]]
     assert all(b <= a for a, b in zip(R, R[1:]))
     assert e1.double().sum().item() == pytest.approx(R[-1], rel=1e-9)
+    # the running residual (R_0 plus every kept trial's e1 - e0, all in 2^-32 units) equals the
+    # integer sum of the final error map rounded to 2^-32, exactly
+    fixed = np.rint(e1.cpu().numpy().astype(np.float64) * 2.0 ** 32).astype(np.int64).sum()
+    assert R[-1] == float(int(fixed)) * 2.0 ** -32
     # every LR pixel is one HR pixel of its own block
     L = lr1.cpu().numpy()
     for v in range(L.shape[0]):

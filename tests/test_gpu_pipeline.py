@@ -97,7 +97,9 @@ def test_joint_4k_pipeline_rows_match_oracle_pipeline(api):
     same = (codes // K == ref["ka"]) & (codes % K == ref["kb"])
     o = out.cpu().numpy().astype(np.float64)
     assert np.abs(o - outr)[same].max() <= 1e-3
-    assert (~same).mean() < 1e-3
+    # pairs differ only at near-ties of Algorithm 1 (compare() checked that each is a valid
+    # optimum there)
+    assert rep["mismatches"] <= rep["near_ties"], rep
     mine = O.apply(codes // K, codes % K, th.weight_f32().cpu().numpy().astype(np.float64), s, S,
                    Tr)
     assert np.abs(o - mine).max() <= 1e-3

@@ -502,9 +502,10 @@ def joint_launches(N: int) -> int:
     """Kernel launches one glu_joint_optimize call makes (iterations after convergence still
     launch and return at once): control init, grid downsample, search, R_0 (2), then per
     iteration threshold, the large-error list (scan, scatter), merge, flatten, 3 root-compaction,
-    count, 3 scan, fill, 5 for the trials' dependency graph, trials and the residual update
-    (the kept trials add their differences; one launch records R_n and the stop rule)."""
-    return 5 + 20 * N
+    count, 3 scan, fill, 5 for the trials' dependency graph (all of which return at once when
+    the one-CTA list kernel, also launched, did their work), trials and the residual update (the
+    kept trials add their differences; one launch records R_n and the stop rule)."""
+    return 5 + 21 * N
 
 
 def tune_mode(on: bool) -> None:

@@ -93,6 +93,7 @@ struct JointCtl {
     int M_cur;
     int nfg;          // large-error pixels of the current iteration (all active images)
     int open_tasks;
+    int small_cur;    // 1: the one-CTA list kernel built this iteration's components and graph
     int claim[GLU_MAX_ITERS];
     int finished[GLU_MAX_ITERS];
     int head[GLU_MAX_ITERS];      // ready queue: positions taken
@@ -273,6 +274,12 @@ __device__ __forceinline__ bool any_active(const JointCtl* c) {
     return *(volatile const int*)&c->active_any != 0;
 }
 
+// The list passes of the multi-kernel path run only when the one-CTA kernel (k_small_comp) did
+// not already build this iteration's components and dependency graph.
+__device__ __forceinline__ bool skip_lists(const JointCtl* c) {
+    return !any_active(c) || *(volatile const int*)&c->small_cur != 0;
+}
+
 // Block-wide exclusive scan of one int per thread (blockDim.x == 256). Returns the total.
 __device__ __forceinline__ int block_excl_scan(int v, int* out_excl, int* smem_warp) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -297,6 +304,34 @@ __device__ __forceinline__ int block_excl_scan(int v, int* out_excl, int* smem_w
     const int warp_base = wid > 0 ? smem_warp[wid - 1] : 0;
     const int total = smem_warp[7];
     *out_excl = warp_base + x - v;
+    __syncthreads();
+    return total;
+}
+
+// Block-wide exclusive scan of one int per thread for any blockDim.x <= 1024 (a multiple of 32).
+// Returns the total; smem_warp holds 32 ints.
+__device__ __forceinline__ int block_excl_scan_any(int v, int* out_excl, int* smem_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < nw ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        smem_warp[lane] = t;
+    }
+    __syncthreads();
+    *out_excl = (wid > 0 ? smem_warp[wid - 1] : 0) + x - v;
+    const int total = smem_warp[nw - 1];
     __syncthreads();
     return total;
 }
@@ -416,6 +451,7 @@ __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int
 __global__ void k_threshold(const __grid_constant__ JBatch B, int* lab, int* own, uint8_t* ovf,
                             int* tile_cnt, JointCtl* c, int it, int4* vlog, long long vcap) {
     if (!any_active(c)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->small_cur = 0;   // a new iteration's lists
     __shared__ int wsum[8];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int local = 0, run_img = -1, run = 0;
@@ -512,7 +548,7 @@ __device__ __forceinline__ void uf_union(int* par, int a, int b) {
 
 __global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const int* fgl,
                             const JointCtl* c) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     const int nfg = c->nfg;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nfg; e += gridDim.x * blockDim.x) {
         const int64_t p = fgl[e];
@@ -533,7 +569,7 @@ __global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const in
 }
 
 __global__ void k_ccl_flatten(int* lab, const int* fgl, const JointCtl* c) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     const int nfg = c->nfg;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nfg; e += gridDim.x * blockDim.x) {
         const int p = fgl[e];
@@ -545,12 +581,13 @@ __global__ void k_ccl_flatten(int* lab, const int* fgl, const JointCtl* c) {
 
 // per-tile root counts over the large-error list (a root is a pixel that is its own parent)
 __global__ void k_root_count(const int* lab, const int* fgl, int* tile_cnt, const JointCtl* c) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     __shared__ int wsum[8];
     const int nfg = c->nfg;
-    const int base = blockIdx.x * kScanTile;
-    int local = 0;
-    if (base < nfg) {
+    // grid-stride over the list's tiles (a small grid: the list is short after iteration 1)
+    for (int tile = blockIdx.x; tile * kScanTile < nfg; tile += gridDim.x) {
+        const int base = tile * kScanTile;
+        int local = 0;
         for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
             const int e = base + i;
             if (e < nfg) {
@@ -558,15 +595,16 @@ __global__ void k_root_count(const int* lab, const int* fgl, int* tile_cnt, cons
                 if (lab[p] == p) ++local;
             }
         }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = local;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int i = 0; i < 8; ++i) t += wsum[i];
-        tile_cnt[blockIdx.x] = t;
+        for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = local;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int i = 0; i < 8; ++i) t += wsum[i];
+            tile_cnt[tile] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -574,8 +612,10 @@ __global__ void k_root_count(const int* lab, const int* fgl, int* tile_cnt, cons
 // (OUT = 1); an empty large-error set stops every image
 template <int OUT>
 __global__ void k_tile_scan(int* tile_cnt, int ntiles, JointCtl* c) {
-    if (!any_active(c)) return;
+    if (OUT == 0 ? !any_active(c) : skip_lists(c)) return;
     __shared__ int wsm[8];
+    // the root counts cover only the list's tiles
+    if (OUT == 1) ntiles = (c->nfg + kScanTile - 1) / kScanTile;
     int carry = 0;
     for (int base = 0; base < ntiles; base += kScanThreads) {
         const int i = base + threadIdx.x;
@@ -596,12 +636,12 @@ __global__ void k_tile_scan(int* tile_cnt, int ntiles, JointCtl* c) {
 __global__ void k_root_scatter(const __grid_constant__ JBatch B, const int* lab, const int* fgl,
                                const int* tile_off, int* roots, int2* cnt, int2* fill, int* done,
                                int2* dag_cnt, int* dag_fill, int* queue, JointCtl* c, int it) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     __shared__ int wsm[8];
     const int nfg = c->nfg;
-    const int base = blockIdx.x * kScanTile;
-    if (base >= nfg) return;   // uniform across the CTA
-    const int off = tile_off[blockIdx.x];
+    for (int tile = blockIdx.x; tile * kScanTile < nfg; tile += gridDim.x) {   // uniform
+    const int base = tile * kScanTile;
+    const int off = tile_off[tile];
     // 16 consecutive elements per thread keep the order inside the tile
     constexpr int per = kScanTile / kScanThreads;
     const int my = base + threadIdx.x * per;
@@ -635,9 +675,20 @@ __global__ void k_root_scatter(const __grid_constant__ JBatch B, const int* lab,
             ++j;
         }
     }
+    }
 }
 
 // ------------------------------------------------------------------- per-component buckets
+
+// First index whose value exceeds key (a ascending), n if none.
+__device__ __forceinline__ int upper_bound_i(const int* a, int n, int key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ int lower_bound_i(const int* a, int n, int key) {
     int lo = 0, hi = n;
@@ -653,7 +704,7 @@ __device__ __forceinline__ int lower_bound_i(const int* a, int n, int key) {
 __global__ void k_comp_count(const __grid_constant__ JBatch B, int* lab, const int* fgl,
                              const int* roots, int2* cnt, int* own, uint8_t* ovf, uint8_t* qflag,
                              const JointCtl* c) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     const int M = c->M_cur, nfg = c->nfg;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nfg; e += gridDim.x * blockDim.x) {
         const int64_t p = fgl[e];
@@ -680,32 +731,34 @@ __global__ void k_comp_count(const __grid_constant__ JBatch B, int* lab, const i
 
 // multi-CTA exclusive scan of int2 counts over M (read from the control block)
 __global__ void k_comp_tile_reduce(const int2* cnt, int2* tile_sum, const JointCtl* c) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     const int M = c->M_cur;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    if (base >= M) return;
     __shared__ int wx[8], wy[8];
-    int sx = 0, sy = 0;
-    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
-        const int64_t j = base + i;
-        if (j < M) { sx += cnt[j].x; sy += cnt[j].y; }
-    }
+    for (int tile = blockIdx.x; (int64_t)tile * kScanTile < M; tile += gridDim.x) {   // uniform
+        const int64_t base = (int64_t)tile * kScanTile;
+        int sx = 0, sy = 0;
+        for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+            const int64_t j = base + i;
+            if (j < M) { sx += cnt[j].x; sy += cnt[j].y; }
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-    }
-    if ((threadIdx.x & 31) == 0) { wx[threadIdx.x >> 5] = sx; wy[threadIdx.x >> 5] = sy; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tx = 0, ty = 0;
-        for (int i = 0; i < 8; ++i) { tx += wx[i]; ty += wy[i]; }
-        tile_sum[blockIdx.x] = make_int2(tx, ty);
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if ((threadIdx.x & 31) == 0) { wx[threadIdx.x >> 5] = sx; wy[threadIdx.x >> 5] = sy; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tx = 0, ty = 0;
+            for (int i = 0; i < 8; ++i) { tx += wx[i]; ty += wy[i]; }
+            tile_sum[tile] = make_int2(tx, ty);
+        }
+        __syncthreads();
     }
 }
 
 __global__ void k_comp_tile_scan(int2* tile_sum, const JointCtl* c) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     const int M = c->M_cur;
     const int ntiles = (M + kScanTile - 1) / kScanTile;
     __shared__ int wsm[8];
@@ -723,11 +776,11 @@ __global__ void k_comp_tile_scan(int2* tile_sum, const JointCtl* c) {
 }
 
 __global__ void k_comp_scan(const int2* cnt, const int2* tile_off, int2* start, const JointCtl* c) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     const int M = c->M_cur;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    if (base >= M) return;
     __shared__ int wsm[8];
+    for (int tile = blockIdx.x; (int64_t)tile * kScanTile < M; tile += gridDim.x) {   // uniform
+    const int64_t base = (int64_t)tile * kScanTile;
     const int per = kScanTile / kScanThreads;
     const int64_t my = base + (int64_t)threadIdx.x * per;
     int sx = 0, sy = 0;
@@ -741,7 +794,7 @@ __global__ void k_comp_scan(const int2* cnt, const int2* tile_off, int2* start, 
     int ex, ey;
     (void)block_excl_scan(sx, &ex, wsm);
     (void)block_excl_scan(sy, &ey, wsm);
-    int ox = tile_off[blockIdx.x].x + ex, oy = tile_off[blockIdx.x].y + ey;
+    int ox = tile_off[tile].x + ex, oy = tile_off[tile].y + ey;
 #pragma unroll
     for (int k = 0; k < per; ++k) {
         if (my + k < M) start[my + k] = make_int2(ox, oy);
@@ -749,12 +802,13 @@ __global__ void k_comp_scan(const int2* cnt, const int2* tile_off, int2* start, 
         oy += v[k].y;
         if (my + k == M - 1) start[M] = make_int2(ox, oy);
     }
+    }
 }
 
 __global__ void k_comp_fill(const __grid_constant__ JBatch B, const int* lab, const int* fgl,
                             const uint8_t* qflag, const int2* start, int2* fill, int* comp_pix,
                             int* qlist, const JointCtl* c) {
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     const int nfg = c->nfg;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nfg; e += gridDim.x * blockDim.x) {
         const int64_t p = fgl[e];
@@ -787,6 +841,14 @@ __device__ __forceinline__ unsigned long long gtimer() {
 #else
 #define GLU_TRACE(it, j, k) do { } while (0)
 #define GLU_TRACE_ANY(it, j, k) do { } while (0)
+#endif
+#ifdef GLU_TRIAL_TRACE
+// Debug builds only: phase stamps of the one-CTA list kernel per iteration.
+static __device__ unsigned long long g_small_t[GLU_MAX_ITERS][16];
+#define GLU_SMALL_STAMP(it, k) \
+    do { if (threadIdx.x == 0) g_small_t[it][k] = gtimer(); } while (0)
+#else
+#define GLU_SMALL_STAMP(it, k) do { } while (0)
 #endif
 
 // ------------------------------------------------------------ dependency graph of the trials
@@ -834,7 +896,7 @@ constexpr int kNbMinPairs = 4096;
 template <int PASS>
 __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
     JointCtl* c = W.ctl;
-    if (!any_active(c)) return;
+    if (skip_lists(c)) return;
     __shared__ int cand[kCandMax];
     __shared__ unsigned bits[kDepsBits / 32];
     __shared__ unsigned nbits[kNbBits / 32];
@@ -1037,6 +1099,338 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
     }
 }
 
+// ------------------------------------------- small large-error lists: the whole phase in one CTA
+//
+// After the first iteration the large-error list is short (a few thousand pixels or fewer), and
+// the multi-kernel path above spends its time in launch gaps and near-empty grids. k_small_comp
+// does the same work in one 1024-thread CTA with the list in shared memory:
+//   components  min-label hooking over the list's adjacencies (neighbours found by binary search
+//               in the sorted list) alternated with pointer jumping until nothing changes: every
+//               pass is a barrier-separated sweep of logarithmic depth, and the final root of a
+//               component is its smallest index, i.e. its smallest raster index
+//   buckets     components numbered in order of their roots; pixel and distinct-LR-block buckets
+//               (owner slots claimed as in k_comp_count, so every later reader sees the same state)
+//   graph       one flat pass over every (component block, neighbouring cell) pair: the blocks of
+//               all components are hashed into cells of D + 1 LR pixels, so every block within D
+//               of a block lies in the 3 x 3 cells around it; each distinct (predecessor,
+//               component) edge enters a shared hash set once, which gives the predecessor counts
+//               and, after a scan, the successor lists
+// The kernels of the multi-kernel path then return at once (small_cur). If the hooking does not
+// settle within kSmallRounds passes (it always has on the workloads), the kernel returns before
+// writing anything and the multi-kernel path runs instead.
+constexpr int kSmallFg = 4096;      // large-error pixels handled by the one-CTA path
+constexpr int kSmallHash = 8192;    // cell hash slots (power of two, more than kSmallFg)
+constexpr int kSmallEdges = 2 * kSmallFg;   // edge hash-set slots (power of two)
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallPer = kSmallFg / kSmallThreads;   // list pixels per thread
+constexpr int kSmallRounds = 64;
+
+struct SmallSmem {
+    union {
+        struct {
+            int p[kSmallFg];        // the list: global pixel ids, ascending
+            int a[kSmallFg];        // component forest, then component ids
+        } l;
+        int eset[kSmallEdges];      // graph: edge keys i * kSmallFg + j (-1: empty)
+    } u;
+    int b[2 * kSmallFg];            // root ranks; then per component (pixels, blocks) counters
+    int q[kSmallFg];                // the distinct (component, block) pairs' blocks, qlist order
+    int2 tab[kSmallHash];           // (cell key, first entry); key -1: empty
+    int ecid[kSmallFg];             // entry: component
+    int eq[kSmallFg];               // entry: LR block
+    int enext[kSmallFg];            // next entry of the same cell
+    int scan[32];
+    int nent, nedge, bad;
+};
+
+__device__ __forceinline__ int img_of_q(const JBatch& B, int64_t q) {
+    int i = 0;
+    while (i + 1 < B.n && B.im[i + 1].q0 <= q) ++i;
+    return i;
+}
+
+__device__ __forceinline__ int hash_slot(int key, int mask) {
+    return (int)(((unsigned)key * 2654435761u) >> 13) & mask;
+}
+
+// Chunked exclusive scan of n values in place (each thread a contiguous chunk); returns the total.
+__device__ __forceinline__ int small_scan(int* v, int n, int* scan_smem) {
+    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int e0 = (int)threadIdx.x * per, e1 = min(e0 + per, n);
+    int s = 0;
+    for (int e = e0; e < e1; ++e) s += v[e];
+    int ex;
+    const int tot = block_excl_scan_any(s, &ex, scan_smem);
+    for (int e = e0; e < e1; ++e) {
+        const int t = v[e];
+        v[e] = ex;
+        ex += t;
+    }
+    __syncthreads();
+    return tot;
+}
+
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    k_small_comp(const __grid_constant__ JBatch B, JointWs W, int it) {
+    JointCtl* c = W.ctl;
+    if (!any_active(c)) return;
+    const int nfg = c->nfg;
+    if (nfg <= 0 || nfg > kSmallFg) return;   // the multi-kernel path does it (small_cur is 0)
+    extern __shared__ __align__(16) unsigned char small_dyn[];
+    SmallSmem& S = *reinterpret_cast<SmallSmem*>(small_dyn);
+    int* P = S.u.l.p;
+    volatile int* A = S.u.l.a;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int e = tid; e < nfg; e += nthr) {
+        P[e] = __ldcg(&W.ulist[e]);
+        A[e] = e;
+    }
+    for (int t = tid; t < kSmallHash; t += nthr) S.tab[t] = make_int2(-1, -1);
+    if (tid == 0) {
+        S.nent = 0;
+        S.nedge = 0;
+        S.bad = 0;
+    }
+    __syncthreads();
+    GLU_SMALL_STAMP(it, 0);
+    // the backward neighbours (W, N, and NW, NE with 8-connectivity) of this thread's pixels e =
+    // tid + k * nthr, as local indices (-1: not in the list)
+    int nbr[kSmallPer][4];
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k) {
+        const int e = tid + k * nthr;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) nbr[k][d] = -1;
+        if (e >= nfg) continue;
+        const int p = P[e];
+        const JImg& I = B.im[img_of_p(B, p)];
+        const int64_t lp = p - I.p0;
+        const int y = (int)(lp / I.W), x = (int)(lp % I.W);
+        int cand[4] = {x > 0 ? p - 1 : -1, y > 0 ? p - I.W : -1,
+                       (y > 0 && x > 0 && B.conn == 8) ? p - I.W - 1 : -1,
+                       (y > 0 && x + 1 < I.W && B.conn == 8) ? p - I.W + 1 : -1};
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            if (cand[d] < 0) continue;
+            const int f = lower_bound_i(P, e, cand[d]);
+            if (f < e && P[f] == cand[d]) nbr[k][d] = f;
+        }
+    }
+    // hook every edge's two roots (the larger under the smaller), then jump pointers until every
+    // tree is a star; repeat until no edge joins two trees
+    bool settled = false;
+    for (int round = 0; round < kSmallRounds; ++round) {
+        int changed = 0;
+#pragma unroll
+        for (int k = 0; k < kSmallPer; ++k) {
+            const int e = tid + k * nthr;
+            if (e >= nfg) continue;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const int f = nbr[k][d];
+                if (f < 0) continue;
+                const int ra = A[e], rb = A[f];
+                if (ra == rb) continue;
+                atomicMin((int*)&A[max(ra, rb)], min(ra, rb));
+                changed = 1;
+            }
+        }
+        if (!__syncthreads_or(changed)) {
+            settled = true;
+            break;
+        }
+        for (int jr = 0; jr < 32; ++jr) {   // pointer jumping: at most log2(kSmallFg) + 1 rounds
+            int moved = 0;
+#pragma unroll
+            for (int k = 0; k < kSmallPer; ++k) {
+                const int e = tid + k * nthr;
+                if (e >= nfg) continue;
+                const int pe = A[e], g = A[pe];
+                if (g != pe) {
+                    A[e] = g;
+                    moved = 1;
+                }
+            }
+            if (!__syncthreads_or(moved)) break;
+        }
+    }
+    if (!settled) return;   // nothing global written yet: the multi-kernel path runs
+    GLU_SMALL_STAMP(it, 1);
+    GLU_SMALL_STAMP(it, 2);
+    // components in order of their roots; per-component state cleared as in k_root_scatter
+    int M;
+    {
+        const int per = (nfg + nthr - 1) / nthr;
+        const int e0 = tid * per, e1 = min(e0 + per, nfg);
+        int nr = 0;
+        for (int e = e0; e < e1; ++e) nr += A[e] == e;
+        int ex;
+        M = block_excl_scan_any(nr, &ex, S.scan);
+        for (int e = e0; e < e1; ++e) {
+            if (A[e] != e) continue;
+            const int j = ex++;
+            S.b[e] = j;
+            const int p = P[e];
+            W.roots[j] = p;
+            W.done[j] = 0;
+            W.queue[j] = -1;
+            atomicAdd(&c->M[img_of_p(B, p)][it], 1);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nfg; e += nthr) A[e] = S.b[A[e]];   // component id (root's rank)
+    __syncthreads();
+    for (int j = tid; j < 2 * M; j += nthr) S.b[j] = 0;
+    if (tid == 0) c->M_cur = M;
+    __syncthreads();
+    GLU_SMALL_STAMP(it, 3);
+    // buckets: label, owner slots (as k_comp_count), pixel and distinct-block counts
+    int* cntp = S.b;        // pixels per component
+    int* cntq = S.b + M;    // distinct LR blocks per component (owner-slot representatives)
+    for (int e = tid; e < nfg; e += nthr) {
+        const int p = P[e], j = A[e];
+        W.lab[p] = j;
+        const JImg& I = B.im[img_of_p(B, p)];
+        const int64_t lp = p - I.p0;
+        const int y = (int)(lp / I.W), x = (int)(lp % I.W);
+        const int64_t q = I.q0 + (int64_t)(y / I.s) * I.w + (x / I.s);
+        int ins = -1;
+        for (int k = 0; k < kOwnSlots; ++k) {
+            const int old = atomicCAS(&W.own[q * kOwnSlots + k], -1, j);
+            if (old == -1) { ins = 1; break; }
+            if (old == j) { ins = 0; break; }
+        }
+        if (ins == -1) W.ovf[q] = 1;
+        const bool rep = ins != 0;
+        atomicAdd(&cntp[j], 1);
+        S.q[e] = rep ? (int)q : -1;   // temporarily per pixel
+        if (rep) atomicAdd(&cntq[j], 1);
+    }
+    __syncthreads();
+    GLU_SMALL_STAMP(it, 4);
+    const int totp = small_scan(cntp, M, S.scan);
+    const int totq = small_scan(cntq, M, S.scan);
+    for (int j = tid; j < M; j += nthr) W.start[j] = make_int2(cntp[j], cntq[j]);
+    if (tid == 0) W.start[M] = make_int2(totp, totq);
+    __syncthreads();
+    // fill comp_pix and qlist (the counters become the end of each component's range), and hash
+    // every (component, block) pair into its cell
+    for (int e = tid; e < nfg; e += nthr) {
+        const int p = P[e], j = A[e];
+        const int pos = atomicAdd(&cntp[j], 1);
+        W.comp_pix[pos] = p;
+        const int q = S.q[e];
+        if (q < 0) continue;
+        const int qp = atomicAdd(&cntq[j], 1);
+        W.qlist[qp] = q;
+        const JImg& I = B.im[img_of_q(B, q)];
+        const int D = B.strict ? I.S - 1 : (I.S - 1) / 2;
+        const int C = D + 1, cw = (I.w + C - 1) / C;
+        const int lq = q - (int)I.q0;
+        const int key = (int)(I.q0 + (int64_t)((lq / I.w) / C) * cw + (lq % I.w) / C);
+        int h = hash_slot(key, kSmallHash - 1);
+        for (int k = 0; k < kSmallHash; ++k) {
+            const int old = atomicCAS(&S.tab[h].x, -1, key);
+            if (old == -1 || old == key) break;
+            h = (h + 1) & (kSmallHash - 1);
+        }
+        const int ent = atomicAdd(&S.nent, 1);
+        S.ecid[ent] = j;
+        S.eq[ent] = q;
+        S.enext[ent] = atomicExch(&S.tab[h].y, ent);
+    }
+    __syncthreads();
+    GLU_SMALL_STAMP(it, 5);
+    // from here the list and the forest are no longer needed: their space holds the edge set
+    for (int t = tid; t < totq; t += nthr) S.q[t] = __ldcg(&W.qlist[t]);
+    for (int t = tid; t < kSmallEdges; t += nthr) S.u.eset[t] = -1;
+    __syncthreads();
+    GLU_SMALL_STAMP(it, 6);
+    // graph: items (block t of the qlist, neighbouring cell) over the whole CTA; the component of
+    // qlist position t is the j with start.y[j] <= t < start.y[j + 1] (cntq holds the ends)
+    int* npred = cntp;   // per component: distinct predecessors
+    for (int j = tid; j < M; j += nthr) npred[j] = 0;
+    __syncthreads();
+    for (int t9 = tid; t9 < totq * 9; t9 += nthr) {
+        const int t = t9 / 9;
+        const int j = upper_bound_i(cntq, M, t);   // first j whose range ends after t
+        const JImg& I = B.im[img_of_p(B, W.roots[j])];
+        const int D = B.strict ? I.S - 1 : (I.S - 1) / 2;
+        const int C = D + 1, cw = (I.w + C - 1) / C, ch = (I.h + C - 1) / C;
+        const int lq = S.q[t] - (int)I.q0;
+        const int v = lq / I.w, u = lq % I.w;
+        const int cv = v / C + (t9 % 9) / 3 - 1, cu = u / C + (t9 % 9) % 3 - 1;
+        if (cv < 0 || cv >= ch || cu < 0 || cu >= cw) continue;
+        const int key = (int)(I.q0 + (int64_t)cv * cw + cu);
+        int h = hash_slot(key, kSmallHash - 1);
+        int ent = -1;
+        for (int k = 0; k < kSmallHash; ++k) {
+            const int kk = S.tab[h].x;
+            if (kk == key) { ent = S.tab[h].y; break; }
+            if (kk == -1) break;
+            h = (h + 1) & (kSmallHash - 1);
+        }
+        for (int g = 0; ent >= 0 && g < kSmallFg; ++g, ent = S.enext[ent]) {
+            const int i = S.ecid[ent];
+            if (i >= j) continue;
+            const int lq2 = S.eq[ent] - (int)I.q0;
+            const int dv = lq2 / I.w - v, du = lq2 % I.w - u;
+            if (dv < -D || dv > D || du < -D || du > D) continue;
+            const int ekey = i * kSmallFg + j;
+            int eh = hash_slot(ekey, kSmallEdges - 1);
+            bool inserted = false;
+            int k = 0;
+            for (; k < kSmallEdges; ++k) {
+                const int old = atomicCAS(&S.u.eset[eh], -1, ekey);
+                if (old == -1) { inserted = true; break; }
+                if (old == ekey) break;
+                eh = (eh + 1) & (kSmallEdges - 1);
+            }
+            if (k == kSmallEdges) S.bad = 1;   // the set is full
+            if (inserted) {
+                atomicAdd(&npred[j], 1);
+                atomicAdd(&S.nedge, 1);
+            }
+        }
+    }
+    __syncthreads();
+    GLU_SMALL_STAMP(it, 7);
+    GLU_SMALL_STAMP(it, 8);
+    const int nedge = S.nedge;
+    if (S.bad || nedge > W.ecap) {
+        if (tid == 0) atomicExch(&c->dag_bad[it], 1);   // the trials claim in index order
+    } else {
+        for (int j = tid; j < M; j += nthr) W.pend[j] = npred[j];
+        int* scnt = cntq;   // successors per predecessor (the ranges are no longer needed)
+        __syncthreads();
+        for (int j = tid; j < M; j += nthr) scnt[j] = 0;
+        __syncthreads();
+        for (int t = tid; t < kSmallEdges; t += nthr) {
+            const int ek = S.u.eset[t];
+            if (ek >= 0) atomicAdd(&scnt[ek / kSmallFg], 1);
+        }
+        __syncthreads();
+        const int tot = small_scan(scnt, M, S.scan);
+        for (int j = tid; j < M; j += nthr) W.dag_start[j] = make_int2(scnt[j], 0);
+        if (tid == 0) W.dag_start[M] = make_int2(tot, 0);
+        __syncthreads();
+        for (int t = tid; t < kSmallEdges; t += nthr) {
+            const int ek = S.u.eset[t];
+            if (ek >= 0) W.succ[atomicAdd(&scnt[ek / kSmallFg], 1)] = ek % kSmallFg;
+        }
+        // components without predecessors enter the ready queue
+        for (int j = tid; j < M; j += nthr) {
+            if (npred[j] != 0) continue;
+            const int pos = atomicAdd(&c->tail[it], 1);
+            W.queue[pos] = j;
+            GLU_TRACE_ANY(it, j, 0);
+        }
+    }
+    __syncthreads();
+    GLU_SMALL_STAMP(it, 9);
+    if (tid == 0) c->small_cur = 1;
+}
+
 // ---------------------------------------------------------------------------- the trials
 
 
@@ -1132,8 +1526,6 @@ struct FastSmem {
     uint16_t code0[kFastPx];  // its pair before the trial
     int full[kFastPx];        // the component's pixels, then the pixels needing a full search
     int nfull;
-    long long wsum[32][2];    // per-warp fixed-point error sums (old, new)
-    int wcnt[32];             // per-warp pixels re-searched
 };
 
 constexpr uint16_t kNotSearched = 0xFFFFu;
@@ -1143,12 +1535,13 @@ constexpr int kMaxChg = 8;       // replaced LR pixels per window for the exact 
 // current LR image (comp >= 0: only the pixels of that component), writing the results in place
 // and the previous values to the backup planes. The previous errors (e0) and the new ones (e1)
 // are summed exactly in 2^-32 units.
-// The general path splits LR blocks of more than kChunkPx HR pixels (scales above 32) into chunks
-// of kChunkPx pixels in raster order, one item each, so that a large block is re-searched by
-// several warps.
-constexpr int kChunkPx = 1024;
+// The general path splits every LR block into chunks of HR pixels in raster order, one item each,
+// so that a block is re-searched by several warps: 32 pixels (one per lane) for blocks of up to
+// 1024 pixels, 1024 pixels above that (scales above 32). The sums are exact integers, so the
+// grouping does not change them.
+__device__ __forceinline__ int chunk_px(const JImg& I) { return I.s * I.s <= 1024 ? 32 : 1024; }
 __device__ __forceinline__ int block_chunks(const JImg& I) {
-    return (I.s * I.s + kChunkPx - 1) / kChunkPx;
+    return (I.s * I.s + chunk_px(I) - 1) / chunk_px(I);
 }
 
 template <int S>
@@ -1173,8 +1566,9 @@ __device__ __noinline__ void warp_block_trial(const JBatch& B, const TrialCtx& X
     const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
     long long s0 = 0, s1 = 0;
     int nsearched = 0;
-    const int jend = min(ey * ex, (chunk + 1) * kChunkPx);
-    for (int j = chunk * kChunkPx + lane; j < jend; j += 32) {
+    const int cpx = chunk_px(I);
+    const int jend = min(ey * ex, (chunk + 1) * cpx);
+    for (int j = chunk * cpx + lane; j < jend; j += 32) {
         const int y = ys + j / ex, x = xs + j % ex;
         const int64_t lp = (int64_t)y * I.W + x, p = I.p0 + lp;
         if (comp >= 0 && __ldcg(&X.ws.lab[p]) != comp) continue;
@@ -1210,8 +1604,9 @@ __device__ __forceinline__ void warp_block_rollback(const JBatch& B, const Trial
     const int lane = threadIdx.x & 31;
     const int ys = bv * I.s, xs = bu * I.s;
     const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
-    const int jend = min(ey * ex, (chunk + 1) * kChunkPx);
-    for (int j = chunk * kChunkPx + lane; j < jend; j += 32) {
+    const int cpx = chunk_px(I);
+    const int jend = min(ey * ex, (chunk + 1) * cpx);
+    for (int j = chunk * cpx + lane; j < jend; j += 32) {
         const int y = ys + j / ex, x = xs + j % ex;
         const int64_t lp = (int64_t)y * I.W + x, p = I.p0 + lp;
         if (comp >= 0 && __ldcg(&X.ws.lab[p]) != comp) continue;
@@ -1509,34 +1904,6 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
     return *s_flag == 0;
 }
 
-// Block-wide exclusive scan of one int per thread for any blockDim.x <= 1024 (a multiple of 32).
-// Returns the total; smem_warp holds 32 ints.
-__device__ __forceinline__ int block_excl_scan_any(int v, int* out_excl, int* smem_warp) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) smem_warp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int t = lane < nw ? smem_warp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        smem_warp[lane] = t;
-    }
-    __syncthreads();
-    *out_excl = (wid > 0 ? smem_warp[wid - 1] : 0) + x - v;
-    const int total = smem_warp[nw - 1];
-    __syncthreads();
-    return total;
-}
-
 // ------------------------------------------------------ trials of small components in one CTA
 //
 // A component whose blocks, re-searched pixels and LR neighbourhood fit in shared memory is tried
@@ -1565,7 +1932,7 @@ __device__ __forceinline__ int full_entry(int pix, int bi, int a_known) {
 template <int S>
 __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_, const JImg& I,
                                              FastSmem& F, int RW, int RV0, int RU0, int bi,
-                                             int comp, bool incr) {
+                                             int comp, bool incr, long long& e1) {
     constexpr int r = (S - 1) / 2, K = S * S;
     const int lane = threadIdx.x & 31;
     const int c = F.blocks[bi], off = F.pxoff[bi];
@@ -1679,6 +2046,7 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
         F.rcode[off + jp] = (uint16_t)(o.ka * K + o.kb);
         F.rw[off + jp] = o.omega;
         F.rerr[off + jp] = o.err;
+        e1 += to_fixed(o.err);
     }
 }
 
@@ -1701,7 +2069,8 @@ __device__ __forceinline__ void team_min(float& v, int& k, unsigned mask) {
 
 template <int S>
 __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, FastSmem& F, int RW,
-                                              int RV0, int RU0, int e, int tl, unsigned mask) {
+                                              int RV0, int RU0, int e, int tl, unsigned mask,
+                                              long long& e1) {
     constexpr int r = (S - 1) / 2, K = S * S;
     const int pix = e & 0xFFF, bi = (e >> 12) & 0xFF, a_known = (e >> 20) - 1;
     const int c = F.blocks[bi];
@@ -1757,30 +2126,8 @@ __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, Fa
         F.rcode[pix] = (uint16_t)(o.ka * K + o.kb);
         F.rw[pix] = o.omega;
         F.rerr[pix] = o.err;
+        e1 += to_fixed(o.err);
     }
-}
-
-// Block bi's old and new error sums (fixed order) and the number of pixels re-searched.
-__device__ __forceinline__ void fast_block_sums(const JImg& I, FastSmem& F, int RW, int RV0,
-                                                int RU0, int bi, long long& e0, long long& e1,
-                                                int& ns) {
-    const int lane = threadIdx.x & 31;
-    const int c = F.blocks[bi], off = F.pxoff[bi];
-    const int bv = RV0 + c / RW, bu = RU0 + c % RW;
-    const int ey = min(I.s, I.H - bv * I.s), ex = min(I.s, I.W - bu * I.s);
-    long long s0 = 0, s1 = 0;
-    int n = 0;
-    for (int jp = lane; jp < ey * ex; jp += 32) {
-        if (F.rcode[off + jp] == kNotSearched) continue;
-        s0 += to_fixed(F.eold[off + jp]);
-        s1 += to_fixed(F.rerr[off + jp]);
-        ++n;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    e0 = warp_sum_ll(s0);
-    e1 = warp_sum_ll(s1);
-    ns = n;
 }
 
 constexpr int kSuccCache = 32;   // successors of a one-CTA trial's component staged for its commit
@@ -1900,6 +2247,10 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
         }
         F.region[t] = c4;
     }
+    // e0 (the searched pixels' previous errors, exact in 2^-32 units) and the number searched
+    // are summed here; e1 as the searches finish
+    long long acc0 = 0;
+    int nsr = 0;
     for (int w0 = warp; w0 < na; w0 += nwarps) {
         const int c = F.blocks[w0], off = F.pxoff[w0];
         const int bv = RV0 + c / RW, bu = RU0 + c % RW;
@@ -1911,10 +2262,25 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
             const uint8_t* ip = I.hr + (int64_t)y * I.hr_pitch + (int64_t)x * 3;
             F.hrpx[off + jp] = (uint32_t)__ldg(ip) | ((uint32_t)__ldg(ip + 1) << 8) |
                                ((uint32_t)__ldg(ip + 2) << 16);
-            F.eold[off + jp] = __ldcg(&I.err[lp]);
+            const float eo = __ldcg(&I.err[lp]);
+            F.eold[off + jp] = eo;
             F.code0[off + jp] = __ldcg(&I.code[lp]);
-            F.rcode[off + jp] =
-                (B.strict || __ldcg(&W_.lab[I.p0 + lp]) == j) ? (uint16_t)0 : kNotSearched;
+            const bool sr = B.strict || __ldcg(&W_.lab[I.p0 + lp]) == j;
+            F.rcode[off + jp] = sr ? (uint16_t)0 : kNotSearched;
+            if (sr) {
+                acc0 += to_fixed(eo);
+                ++nsr;
+            }
+        }
+    }
+    {
+        const long long w0s = warp_sum_ll(acc0);
+        int wn = nsr;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
+        if ((tid & 31) == 0 && wn) {
+            atomicAdd(&sh.e0, (unsigned long long)w0s);
+            atomicAdd(&sh.searched, wn);
         }
     }
     for (int t = tid; t < ncomp; t += nthr) F.full[t] = W_.comp_pix[st.x + t];
@@ -1954,13 +2320,14 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
     const bool incr = B.strict != 0;   // PAPER leaves Theta stale outside components: no re-search
     if (tid == 0) F.nfull = 0;
     __syncthreads();
+    long long acc1 = 0;
     for (int bi = warp; bi < na; bi += nwarps) {
         switch (I.S) {
-            case 1: fast_block_pass<1>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
-            case 3: fast_block_pass<3>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
-            case 5: fast_block_pass<5>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
-            case 7: fast_block_pass<7>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
-            default: fast_block_pass<9>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr); break;
+            case 1: fast_block_pass<1>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr, acc1); break;
+            case 3: fast_block_pass<3>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr, acc1); break;
+            case 5: fast_block_pass<5>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr, acc1); break;
+            case 7: fast_block_pass<7>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr, acc1); break;
+            default: fast_block_pass<9>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr, acc1); break;
         }
     }
     __syncthreads();
@@ -1975,47 +2342,20 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
         for (int t = tid / kTeam; t < nfull; t += nthr / kTeam) {
             const int e = F.full[t];
             switch (I.S) {
-                case 1: fast_full_search<1>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
-                case 3: fast_full_search<3>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
-                case 5: fast_full_search<5>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
-                case 7: fast_full_search<7>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
-                default: fast_full_search<9>(B, I, F, RW, RV0, RU0, e, tl, mask); break;
+                case 1: fast_full_search<1>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                case 3: fast_full_search<3>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                case 5: fast_full_search<5>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                case 7: fast_full_search<7>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                default: fast_full_search<9>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
             }
         }
     }
+    {
+        const long long w1 = warp_sum_ll(acc1);
+        if ((tid & 31) == 0 && w1) atomicAdd(&sh.e1, (unsigned long long)w1);
+    }
     __syncthreads();
     GLU_TRACE(X.it, j, 8);
-    {
-        long long a0 = 0, a1 = 0;
-        int an = 0;
-        for (int bi = warp; bi < na; bi += nwarps) {
-            long long e0, e1;
-            int ns;
-            fast_block_sums(I, F, RW, RV0, RU0, bi, e0, e1, ns);
-            a0 += e0;
-            a1 += e1;
-            an += ns;
-        }
-        if ((tid & 31) == 0) {
-            F.wsum[warp][0] = a0;
-            F.wsum[warp][1] = a1;
-            F.wcnt[warp] = an;
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        long long a0 = 0, a1 = 0;
-        int an = 0;
-        for (int w = 0; w < nwarps; ++w) {
-            a0 += F.wsum[w][0];
-            a1 += F.wsum[w][1];
-            an += F.wcnt[w];
-        }
-        sh.e0 = (unsigned long long)a0;
-        sh.e1 = (unsigned long long)a1;
-        sh.searched = an;
-    }
-    __syncthreads();
     GLU_TRACE(X.it, j, 6);
     const bool keep = !((long long)sh.e1 > (long long)sh.e0);
     if (stage && warp == nwarps - 1) {
@@ -2134,8 +2474,7 @@ __device__ bool big_trial(const JBatch& B, const TrialCtx& X, const JImg& I, int
     // before it publishes the task (cumulative over what the barrier ordered before it)
     __syncthreads();
     // trial: Algorithm 1 again on the affected pixels (STRICT: every block within r of Q; PAPER:
-    // the component's own pixels), in place, summing e0 and e1; blocks above kChunkPx pixels
-    // in several items
+    // the component's own pixels), in place, summing e0 and e1; every block in several items
     const bool use_list = listed && *s_na <= kSlotA;
     const int nitems = (use_list ? *s_na : B.strict ? nu * NB : nu) * block_chunks(I);
     const int lk = use_list ? 2 : 0;
@@ -2375,7 +2714,8 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
             }
         }
         if (tid == 0) {
-            st_release(&W_.done[j], 1);
+            // done[] is read only by the in-order fallback (no dependency graph)
+            if (!dag) st_release(&W_.done[j], 1);
             atomicAdd(&ctl->finished[X.it], 1);
         }
         GLU_TRACE(X.it, j, 3);
@@ -2409,6 +2749,18 @@ static int grid_cap(int64_t work, int threads, int per_sm = 16) {
     const int64_t blocks = (work + threads - 1) / threads;
     const int64_t cap = (int64_t)sm_count() * per_sm;
     return (int)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
+}
+
+// Opt-in shared memory of the one-CTA list kernel (once per process).
+static int small_comp_setup() {
+    static std::once_flag once;
+    static int rc = GLU_OK;
+    std::call_once(once, [] {
+        if (cudaFuncSetAttribute(k_small_comp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(SmallSmem)) != cudaSuccess)
+            rc = GLU_ERR_CUDA;
+    });
+    return rc;
 }
 
 static int launch_trials(const JBatch& B, const TrialCtx& X, cudaStream_t st) {
@@ -2535,6 +2887,10 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
     B.nchunks = c0;
     const int T = 256;
 
+    {
+        const int rc0 = small_comp_setup();
+        if (rc0) return rc0;
+    }
     prof::mark(slot, evi++, st);
     k_ctl_init<<<grid_cap(nq > kMaxSlots ? nq : kMaxSlots, T), T, 0, st>>>(ws.ctl, ws.stamp, nq,
                                                                           ws.slot_word, n);
@@ -2562,6 +2918,10 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
 
     const int tiles_a = (int)((np + kScanTile - 1) / kScanTile);
     const int tiles_b = (int)((ws.mcap + kScanTile - 1) / kScanTile);
+    // the list passes over tiles of the large-error list or of the components: grid-stride
+    // over a small grid (the lists are short after the first iteration)
+    const int list_grid_a = std::min(tiles_a, 2 * sm_count());
+    const int list_grid_b = std::min(tiles_b, 2 * sm_count());
     TrialCtx X;
     X.ws = ws;
     X.wait_limit_ns = cm.wait_limit_ns;
@@ -2578,26 +2938,28 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
                                                        cm.argmax_cap);
         k_tile_scan<0><<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
         k_fg_scatter<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, np, ws.tile_a, fgl, ws.ctl);
+        // a short list: the whole phase in one CTA; the launches below then return at once
+        k_small_comp<<<1, kSmallThreads, sizeof(SmallSmem), st>>>(B, ws, it);
         k_ccl_merge<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.ctl);
         k_ccl_flatten<<<lgrid, T, 0, st>>>(ws.lab, fgl, ws.ctl);
-        k_root_count<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, fgl, ws.tile_a, ws.ctl);
+        k_root_count<<<list_grid_a, kScanThreads, 0, st>>>(ws.lab, fgl, ws.tile_a, ws.ctl);
         k_tile_scan<1><<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
-        k_root_scatter<<<tiles_a, kScanThreads, 0, st>>>(B, ws.lab, fgl, ws.tile_a, ws.roots,
+        k_root_scatter<<<list_grid_a, kScanThreads, 0, st>>>(B, ws.lab, fgl, ws.tile_a, ws.roots,
                                                          ws.cnt, ws.fill, ws.done, ws.dag_cnt,
                                                          ws.dag_fill, ws.queue, ws.ctl, it);
         k_comp_count<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.roots, ws.cnt, ws.own,
                                                          ws.ovf, ws.qflag, ws.ctl);
-        k_comp_tile_reduce<<<tiles_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.ctl);
+        k_comp_tile_reduce<<<list_grid_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.ctl);
         k_comp_tile_scan<<<1, kScanThreads, 0, st>>>(ws.tile_b, ws.ctl);
-        k_comp_scan<<<tiles_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.start, ws.ctl);
+        k_comp_scan<<<list_grid_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.start, ws.ctl);
         k_comp_fill<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.qflag, ws.start,
                                                         ws.fill, ws.comp_pix, ws.qlist, ws.ctl);
         // the trials' dependency graph
-        k_deps<0><<<grid_cap(ws.mcap, 1, 8), 256, 0, st>>>(B, ws, it);
-        k_comp_tile_reduce<<<tiles_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.ctl);
+        k_deps<0><<<grid_cap(ws.mcap, 1, 4), 256, 0, st>>>(B, ws, it);
+        k_comp_tile_reduce<<<list_grid_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.ctl);
         k_comp_tile_scan<<<1, kScanThreads, 0, st>>>(ws.tile_b, ws.ctl);
-        k_comp_scan<<<tiles_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.dag_start, ws.ctl);
-        k_deps<1><<<grid_cap(ws.mcap, 1, 8), 256, 0, st>>>(B, ws, it);
+        k_comp_scan<<<list_grid_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.dag_start, ws.ctl);
+        k_deps<1><<<grid_cap(ws.mcap, 1, 4), 256, 0, st>>>(B, ws, it);
         GLU_LAUNCH_CHECK();
         prof::mark(slot, evi++, st);
         X.it = it;
@@ -2808,6 +3170,11 @@ extern "C" int glu_dbg_trace(unsigned long long* host, int64_t n) {
     const size_t bytes = sizeof(unsigned long long) * (size_t)n;
     if (bytes > sizeof(glu::g_trace)) return GLU_ERR_INVALID_ARG;
     return cudaMemcpyFromSymbol(host, glu::g_trace, bytes) == cudaSuccess ? GLU_OK : GLU_ERR_CUDA;
+}
+
+extern "C" int glu_dbg_small_times(unsigned long long* host) {
+    return cudaMemcpyFromSymbol(host, glu::g_small_t, sizeof(glu::g_small_t)) == cudaSuccess
+               ? GLU_OK : GLU_ERR_CUDA;
 }
 
 extern "C" int glu_dbg_trace_clear(void) {

@@ -555,6 +555,28 @@ def measure_video(api, torch, dev, n_frames):
         vs.bind(f, frames[f], outs[f])
     res["graph_no_fork"] = timeline(lambda f: vs.launch(f))
     vs.close()
+    # Theta reused by two operators (Gaussian + gamma 0.8; box + saturation 1.3): one pipeline
+    # with both operators (one Algorithm 1 per frame, each operator's branch forked beside it)
+    # against two single-operator pipelines per frame
+    ops2 = [(1, 1.0, 0.8), (0, 1.3, 1.0)]
+    outs2 = torch.empty((n_frames, H, W, 3), dtype=torch.float16, device=dev)
+    vm = api.Video(H, W, s, p, out_dtype=torch.float16, overlap=True, ops=ops2)
+    for f in range(n_frames):
+        vm.bind(f, frames[f], [outs[f], outs2[f]])
+    va = api.Video(H, W, s, p, out_dtype=torch.float16, overlap=True, ops=ops2[:1])
+    vb = api.Video(H, W, s, p, out_dtype=torch.float16, overlap=True, ops=ops2[1:])
+    for f in range(n_frames):
+        va.bind(f, frames[f], outs[f])
+        vb.bind(f, frames[f], outs2[f])
+    res["two_operators"] = dict(
+        shared_theta_graph=timeline(lambda f: vm.launch(f)),
+        two_pipelines=timeline(lambda f: (va.launch(f), vb.launch(f))))
+    res["two_operators"]["speedup"] = (res["two_operators"]["shared_theta_graph"]["fps"] /
+                                       res["two_operators"]["two_pipelines"]["fps"])
+    vm.close()
+    va.close()
+    vb.close()
+    del outs2
     h, w = api.lr_dims(H, W, s)
     lr = torch.empty((h, w, 3), dtype=torch.float32, device=dev)
     t1, T = torch.empty_like(lr), torch.empty_like(lr)

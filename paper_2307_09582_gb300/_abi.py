@@ -66,15 +66,20 @@ class GluBatchItem(ctypes.Structure):
                 ("err_map", ctypes.c_void_p)]
 
 
+GLU_VIDEO_MAX_SLOTS = 256
+GLU_VIDEO_MAX_OPS = 4
+
+
+class GluLrOp(ctypes.Structure):
+    _fields_ = [("filter", ctypes.c_int32), ("saturation", ctypes.c_float),
+                ("gamma", ctypes.c_float)]
+
+
 class GluVideoDesc(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("hr_dtype", ctypes.c_int32),
                 ("out_dtype", ctypes.c_int32), ("scale", ctypes.c_int32), ("params", GluParams),
-                ("wfmt", ctypes.c_int32), ("filter", ctypes.c_int32),
-                ("saturation", ctypes.c_float), ("gamma", ctypes.c_float),
-                ("overlap", ctypes.c_int32)]
-
-
-GLU_VIDEO_MAX_SLOTS = 256
+                ("wfmt", ctypes.c_int32), ("n_ops", ctypes.c_int32),
+                ("ops", GluLrOp * GLU_VIDEO_MAX_OPS), ("overlap", ctypes.c_int32)]
 GLU_TUNE_SEARCH, GLU_TUNE_APPLY = 0, 1
 
 _P = ctypes.POINTER
@@ -122,9 +127,9 @@ PROTOTYPES = {
     "glu_joint_profile_read": (ctypes.c_int, [_P(ctypes.c_float), _P(_i32)]),
     "glu_video_workspace_size": (ctypes.c_size_t, [_P(GluVideoDesc)]),
     "glu_video_create": (ctypes.c_int, [_P(GluVideoDesc), _vp, ctypes.c_size_t, _P(_vp)]),
-    "glu_video_bind": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    "glu_video_bind": (ctypes.c_int, [_vp, _i32, _vp, _P(_vp)]),
     "glu_video_launch": (ctypes.c_int, [_vp, _i32, _vp]),
-    "glu_video_run": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "glu_video_run": (ctypes.c_int, [_vp, _vp, _P(_vp), _vp]),
     "glu_video_views": (ctypes.c_int, [_vp, _P(GluImage), _P(GluImage), _P(GluTheta)]),
     "glu_video_destroy": (ctypes.c_int, [_vp]),
     "glu_tune_mode": (ctypes.c_int, [_i32]),

@@ -277,21 +277,30 @@ def glu_joint_optimize_batched(hrs, scales, params: A.GluParams, Ss=None, lrs=No
 
 
 class Video:
-    """Per-frame pipeline (BOX downsample -> 3x3 filter + saturation + gamma on the LR image ->
-    Algorithm 1 -> Eq. 1) with one CUDA graph per bound (frame, output) slot. The workspace
-    (LR images and Theta) is a torch tensor owned here."""
+    """Per-frame pipeline (BOX downsample -> LR operators (3x3 filter + saturation + gamma) on the
+    LR image -> Algorithm 1 once -> Eq. 1 per operator) with one CUDA graph per bound (frame,
+    outputs) slot. `ops`: list of (filter, saturation, gamma), one output per operator (default:
+    the single operator given by filter / saturation / gamma). The workspace (LR images, targets,
+    Theta) is a torch tensor owned here."""
 
     def __init__(self, H, W, scale, params: A.GluParams, hr_dtype=torch.float16,
                  out_dtype=torch.float16, wfmt=A.GLU_W_UNORM16, filter=1, saturation=1.0,
-                 gamma=0.8, overlap=True, device="cuda"):
+                 gamma=0.8, overlap=True, device="cuda", ops=None):
+        if ops is None:
+            ops = [(filter, saturation, gamma)]
+        if not 1 <= len(ops) <= A.GLU_VIDEO_MAX_OPS:
+            raise ValueError(f"1 to {A.GLU_VIDEO_MAX_OPS} operators")
         d = A.GluVideoDesc()
         d.H, d.W, d.scale = H, W, scale
         d.hr_dtype, d.out_dtype = _DT[hr_dtype], _DT[out_dtype]
         d.params = params
-        d.wfmt, d.filter, d.saturation, d.gamma = wfmt, filter, saturation, gamma
+        d.wfmt = wfmt
+        d.n_ops = len(ops)
+        for k, (f, sat, g) in enumerate(ops):
+            d.ops[k] = A.GluLrOp(int(f), float(sat), float(g))
         d.overlap = 1 if overlap else 0
         self.desc, self.H, self.W, self.scale, self.S = d, H, W, scale, params.S
-        self.out_dtype, self.wfmt = out_dtype, wfmt
+        self.out_dtype, self.wfmt, self.n_ops = out_dtype, wfmt, len(ops)
         need = int(lib().glu_video_workspace_size(ctypes.byref(d)))
         if need == 0:
             A.check("glu_video_workspace_size", A.GLU_ERR_INVALID_ARG)
@@ -303,27 +312,37 @@ class Video:
         self.h = h
         self._bound = {}
 
-    def bind(self, slot: int, hr: torch.Tensor, out: torch.Tensor) -> None:
-        assert hr.is_contiguous() and out.is_contiguous()
-        assert hr.shape == (self.H, self.W, 3) and out.shape == (self.H, self.W, 3)
+    def _outs(self, outs):
+        outs = [outs] if isinstance(outs, torch.Tensor) else list(outs)
+        if len(outs) != self.n_ops:
+            raise ValueError(f"{self.n_ops} output tensors expected")
+        for o in outs:
+            assert o.is_contiguous() and o.shape == (self.H, self.W, 3)
+        return outs, (ctypes.c_void_p * self.n_ops)(*[o.data_ptr() for o in outs])
+
+    def bind(self, slot: int, hr: torch.Tensor, outs) -> None:
+        """Record slot `slot`: the frame `hr` into `outs` (a tensor, or one per operator)."""
+        assert hr.is_contiguous() and hr.shape == (self.H, self.W, 3)
+        outs, arr = self._outs(outs)
         A.check("glu_video_bind", lib().glu_video_bind(self.h, slot, ctypes.c_void_p(hr.data_ptr()),
-                                                       ctypes.c_void_p(out.data_ptr())))
-        self._bound[slot] = (hr, out)   # keep the buffers alive while the graph refers to them
+                                                       arr))
+        self._bound[slot] = (hr, outs)   # keep the buffers alive while the graph refers to them
 
     def launch(self, slot: int, stream=None) -> None:
         A.check("glu_video_launch", lib().glu_video_launch(self.h, slot, _stream(stream)))
 
-    def run(self, hr: torch.Tensor, out: torch.Tensor, stream=None) -> None:
-        assert hr.is_contiguous() and out.is_contiguous()
-        A.check("glu_video_run", lib().glu_video_run(self.h, ctypes.c_void_p(hr.data_ptr()),
-                                                     ctypes.c_void_p(out.data_ptr()),
+    def run(self, hr: torch.Tensor, outs, stream=None) -> None:
+        assert hr.is_contiguous()
+        outs, arr = self._outs(outs)
+        A.check("glu_video_run", lib().glu_video_run(self.h, ctypes.c_void_p(hr.data_ptr()), arr,
                                                      _stream(stream)))
 
     def views(self):
-        """(lr, target, Theta) views into the workspace, as torch tensors."""
-        li, ti, th = A.GluImage(), A.GluImage(), A.GluTheta()
-        A.check("glu_video_views", lib().glu_video_views(self.h, ctypes.byref(li),
-                                                         ctypes.byref(ti), ctypes.byref(th)))
+        """(lr, [target of each operator], Theta) views into the workspace, as torch tensors."""
+        li, th = A.GluImage(), A.GluTheta()
+        ti = (A.GluImage * self.n_ops)()
+        A.check("glu_video_views", lib().glu_video_views(self.h, ctypes.byref(li), ti,
+                                                         ctypes.byref(th)))
         base = self.ws.data_ptr()
 
         def view(ptr, n, dtype, shape):
@@ -332,7 +351,7 @@ class Video:
             return self.ws[off:off + n * esz].view(dtype).view(shape)
 
         lr = view(li.data, li.h * li.w * 3, torch.float32, (li.h, li.w, 3))
-        T = view(ti.data, ti.h * ti.w * 3, torch.float32, (ti.h, ti.w, 3))
+        T = [view(t.data, t.h * t.w * 3, torch.float32, (t.h, t.w, 3)) for t in ti]
         code = view(th.code, self.H * self.W, torch.int16, (self.H, self.W))
         weight = view(th.weight, self.H * self.W, _WT[self.wfmt], (self.H, self.W))
         return lr, T, Theta(code, weight, self.H, self.W, self.scale, self.S, self.wfmt)

@@ -1,6 +1,8 @@
-// Per-frame pipeline (downsample -> LR operator -> Algorithm 1 -> Eq. 1) replayed as CUDA
-// graphs. The LR operator branch and the Algorithm 1 branch are independent (Theta is computed
-// from the guide alone, Sec. 3), so they fork onto two streams and join before the apply.
+// Per-frame pipeline (downsample -> LR operators -> Algorithm 1 once -> Eq. 1 per operator)
+// replayed as CUDA graphs. Theta is computed from the guide alone (Sec. 3), so one optimisation
+// serves every operator of the frame; each operator's branch forks onto a stream of its own
+// beside Algorithm 1 and applies Theta to its target once Theta is ready; the branches join at
+// the end of the frame.
 #include <new>
 
 #include "common.cuh"
@@ -13,15 +15,16 @@ using namespace glu;
 struct glu_video {
     glu_video_desc d;
     int h, w;
-    float* lr;           // h x w x 3: BOX downsample of the frame
-    float* t1;           // h x w x 3: filtered
-    float* T;            // h x w x 3: processed target
-    uint16_t* code;      // H x W
-    void* weight;        // H x W
+    float* lr;                       // h x w x 3: BOX downsample of the frame
+    float* t1[GLU_VIDEO_MAX_OPS];    // h x w x 3: filtered, per operator
+    float* T[GLU_VIDEO_MAX_OPS];     // h x w x 3: processed target, per operator
+    uint16_t* code;                  // H x W
+    void* weight;                    // H x W
     int device;
-    cudaStream_t side;   // forked branch
-    cudaStream_t rec;    // recording stream for graph capture
-    cudaEvent_t fork, join;
+    cudaStream_t side[GLU_VIDEO_MAX_OPS];   // forked branches, one per operator
+    cudaStream_t rec;                // recording stream for graph capture
+    cudaEvent_t fork, theta_ready;
+    cudaEvent_t join[GLU_VIDEO_MAX_OPS];
     cudaGraphExec_t exec[GLU_VIDEO_MAX_SLOTS];
 };
 
@@ -39,8 +42,12 @@ bool desc_ok(const glu_video_desc* d) {
     if (p.S < 1 || p.S > 9 || !(p.S & 1) || !(p.eps >= 0.f)) return false;
     if (p.mode != GLU_MODE_FAST && p.mode != GLU_MODE_GNU) return false;
     if (d->wfmt < GLU_W_F32 || d->wfmt > GLU_W_UNORM16) return false;
-    if (d->filter < -1 || d->filter > 1) return false;
-    if (!(d->saturation >= 0.f) || !(d->gamma > 0.f)) return false;
+    if (d->n_ops < 1 || d->n_ops > GLU_VIDEO_MAX_OPS) return false;
+    for (int k = 0; k < d->n_ops; ++k) {
+        const glu_lr_op& o = d->ops[k];
+        if (o.filter < -1 || o.filter > 1) return false;
+        if (!(o.saturation >= 0.f) || !(o.gamma > 0.f)) return false;
+    }
     return true;
 }
 
@@ -55,50 +62,91 @@ size_t layout(const glu_video_desc* d, char* base, glu_video* v) {
         return p;
     };
     char* lr = take(lrb);
-    char* t1 = take(lrb);
-    char* T = take(lrb);
+    char* t1[GLU_VIDEO_MAX_OPS];
+    char* T[GLU_VIDEO_MAX_OPS];
+    for (int k = 0; k < d->n_ops; ++k) {
+        t1[k] = take(lrb);
+        T[k] = take(lrb);
+    }
     char* code = take(sizeof(uint16_t) * np);
     char* weight = take((size_t)wbytes(d->wfmt) * np);
     if (v) {
         v->h = h;
         v->w = w;
         v->lr = (float*)lr;
-        v->t1 = (float*)t1;
-        v->T = (float*)T;
+        for (int k = 0; k < d->n_ops; ++k) {
+            v->t1[k] = (float*)t1[k];
+            v->T[k] = (float*)T[k];
+        }
         v->code = (uint16_t*)code;
         v->weight = weight;
     }
     return off;
 }
 
-// One frame's launches on `st` (the fork / join events make `side` part of the same work).
-int issue(glu_video* v, const void* hr, void* out, cudaStream_t st) {
+// Operator k on the LR image (on stream st).
+int issue_op(glu_video* v, int k, cudaStream_t st) {
+    const glu_lr_op& o = v->d.ops[k];
+    const int64_t pitch = (int64_t)v->w * 3;
+    const float* src = v->lr;
+    if (o.filter >= 0) {
+        const int rc = glu_fx_filter3(v->lr, v->h, v->w, 3, pitch, v->t1[k], pitch, o.filter, st);
+        if (rc) return rc;
+        src = v->t1[k];
+    }
+    return glu_fx_point(src, v->h, v->w, pitch, v->T[k], pitch, o.saturation, o.gamma, st);
+}
+
+// Eq. 1 of the frame's Theta on target k into out (on stream st).
+int issue_apply(glu_video* v, int k, void* out, cudaStream_t st) {
+    const glu_video_desc& d = v->d;
+    ApplyArgs p;
+    p.code = v->code;
+    p.weight = v->weight;
+    p.wfmt = d.wfmt;
+    p.H = d.H;
+    p.W = d.W;
+    p.s = d.scale;
+    p.S = d.params.S;
+    p.h = v->h;
+    p.w = v->w;
+    p.C = 3;
+    p.T = v->T[k];
+    p.T_pitch = (int64_t)v->w * 3;
+    p.T_dtype = GLU_F32;
+    p.out = out;
+    p.out_pitch = (int64_t)d.W * 3;
+    p.out_dtype = d.out_dtype;
+    return launch_apply(p, st);
+}
+
+// One frame's launches on `st` (the fork / join events make the side streams part of the same
+// work).
+int issue(glu_video* v, const void* hr, void* const* outs, cudaStream_t st) {
     const glu_video_desc& d = v->d;
     glu_image hi{const_cast<void*>(hr), d.H, d.W, 3, d.hr_dtype, (int64_t)d.W * 3};
     glu_image li{v->lr, v->h, v->w, 3, GLU_F32, (int64_t)v->w * 3};
     int rc = launch_downsample(hi, d.scale, GLU_DOWN_BOX, li, st);
     if (rc) return rc;
-    cudaStream_t ops = st;
     if (d.overlap) {
         GLU_CUDA_TRY(cudaEventRecord(v->fork, st));
-        GLU_CUDA_TRY(cudaStreamWaitEvent(v->side, v->fork, 0));
-        ops = v->side;
+        for (int k = 0; k < d.n_ops; ++k) {
+            GLU_CUDA_TRY(cudaStreamWaitEvent(v->side[k], v->fork, 0));
+            rc = issue_op(v, k, v->side[k]);
+            if (rc) return rc;
+        }
+    } else {
+        for (int k = 0; k < d.n_ops; ++k) {
+            rc = issue_op(v, k, st);
+            if (rc) return rc;
+        }
     }
-    const int64_t pitch = (int64_t)v->w * 3;
-    const float* src = v->lr;
-    if (d.filter >= 0) {
-        rc = glu_fx_filter3(v->lr, v->h, v->w, 3, pitch, v->t1, pitch, d.filter, ops);
-        if (rc) return rc;
-        src = v->t1;
-    }
-    rc = glu_fx_point(src, v->h, v->w, pitch, v->T, pitch, d.saturation, d.gamma, ops);
-    if (rc) return rc;
     SearchArgs a;
     a.hr = hr;
     a.hr_pitch = (int64_t)d.W * 3;
     a.hr_dtype = d.hr_dtype;
     a.lr = v->lr;
-    a.lr_pitch = pitch;
+    a.lr_pitch = (int64_t)v->w * 3;
     a.lr_dtype = GLU_F32;
     a.H = d.H;
     a.W = d.W;
@@ -114,38 +162,42 @@ int issue(glu_video* v, const void* hr, void* out, cudaStream_t st) {
     a.err = nullptr;
     rc = launch_search(a, st);
     if (rc) return rc;
-    if (d.overlap) {
-        GLU_CUDA_TRY(cudaEventRecord(v->join, v->side));
-        GLU_CUDA_TRY(cudaStreamWaitEvent(st, v->join, 0));
+    if (!d.overlap) {
+        for (int k = 0; k < d.n_ops; ++k) {
+            rc = issue_apply(v, k, outs[k], st);
+            if (rc) return rc;
+        }
+        return GLU_OK;
     }
-    ApplyArgs p;
-    p.code = v->code;
-    p.weight = v->weight;
-    p.wfmt = d.wfmt;
-    p.H = d.H;
-    p.W = d.W;
-    p.s = d.scale;
-    p.S = d.params.S;
-    p.h = v->h;
-    p.w = v->w;
-    p.C = 3;
-    p.T = v->T;
-    p.T_pitch = pitch;
-    p.T_dtype = GLU_F32;
-    p.out = out;
-    p.out_pitch = (int64_t)d.W * 3;
-    p.out_dtype = d.out_dtype;
-    return launch_apply(p, st);
+    GLU_CUDA_TRY(cudaEventRecord(v->theta_ready, st));
+    for (int k = 0; k < d.n_ops; ++k) {
+        GLU_CUDA_TRY(cudaStreamWaitEvent(v->side[k], v->theta_ready, 0));
+        rc = issue_apply(v, k, outs[k], v->side[k]);
+        if (rc) return rc;
+        GLU_CUDA_TRY(cudaEventRecord(v->join[k], v->side[k]));
+    }
+    for (int k = 0; k < d.n_ops; ++k) GLU_CUDA_TRY(cudaStreamWaitEvent(st, v->join[k], 0));
+    return GLU_OK;
 }
 
 void release(glu_video* v) {
     for (auto& e : v->exec)
         if (e) cudaGraphExecDestroy(e);
     if (v->fork) cudaEventDestroy(v->fork);
-    if (v->join) cudaEventDestroy(v->join);
-    if (v->side) cudaStreamDestroy(v->side);
+    if (v->theta_ready) cudaEventDestroy(v->theta_ready);
+    for (int k = 0; k < GLU_VIDEO_MAX_OPS; ++k) {
+        if (v->join[k]) cudaEventDestroy(v->join[k]);
+        if (v->side[k]) cudaStreamDestroy(v->side[k]);
+    }
     if (v->rec) cudaStreamDestroy(v->rec);
     delete v;
+}
+
+bool outs_ok(const glu_video* v, void* const* outs) {
+    if (!outs) return false;
+    for (int k = 0; k < v->d.n_ops; ++k)
+        if (!outs[k]) return false;
+    return true;
 }
 
 }  // namespace
@@ -166,11 +218,14 @@ int glu_video_create(const glu_video_desc* desc, void* ws, size_t ws_bytes, glu_
     if (!v) return GLU_ERR_CUDA;
     v->d = *desc;
     layout(desc, (char*)ws, v);
-    if (cudaGetDevice(&v->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&v->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&v->rec, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&v->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&v->join, cudaEventDisableTiming) != cudaSuccess) {
+    bool ok = cudaGetDevice(&v->device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&v->rec, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&v->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&v->theta_ready, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < desc->n_ops; ++k)
+        ok = cudaStreamCreateWithFlags(&v->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&v->join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         release(v);
         return GLU_ERR_CUDA;
     }
@@ -178,11 +233,12 @@ int glu_video_create(const glu_video_desc* desc, void* ws, size_t ws_bytes, glu_
     return GLU_OK;
 }
 
-int glu_video_bind(glu_video* v, int32_t slot, const void* hr, void* out) {
-    if (!v || !hr || !out || slot < 0 || slot >= GLU_VIDEO_MAX_SLOTS) return GLU_ERR_INVALID_ARG;
+int glu_video_bind(glu_video* v, int32_t slot, const void* hr, void* const* outs) {
+    if (!v || !hr || !outs_ok(v, outs) || slot < 0 || slot >= GLU_VIDEO_MAX_SLOTS)
+        return GLU_ERR_INVALID_ARG;
     cudaGraph_t g = nullptr;
     GLU_CUDA_TRY(cudaStreamBeginCapture(v->rec, cudaStreamCaptureModeRelaxed));
-    const int rc = issue(v, hr, out, v->rec);
+    const int rc = issue(v, hr, outs, v->rec);
     const cudaError_t ec = cudaStreamEndCapture(v->rec, &g);
     if (rc != GLU_OK || ec != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -204,15 +260,17 @@ int glu_video_launch(glu_video* v, int32_t slot, void* stream) {
     return GLU_OK;
 }
 
-int glu_video_run(glu_video* v, const void* hr, void* out, void* stream) {
-    if (!v || !hr || !out) return GLU_ERR_INVALID_ARG;
-    return issue(v, hr, out, (cudaStream_t)stream);
+int glu_video_run(glu_video* v, const void* hr, void* const* outs, void* stream) {
+    if (!v || !hr || !outs_ok(v, outs)) return GLU_ERR_INVALID_ARG;
+    return issue(v, hr, outs, (cudaStream_t)stream);
 }
 
-int glu_video_views(const glu_video* v, glu_image* lr, glu_image* target, glu_theta* theta) {
+int glu_video_views(const glu_video* v, glu_image* lr, glu_image* targets, glu_theta* theta) {
     if (!v) return GLU_ERR_INVALID_ARG;
     if (lr) *lr = glu_image{v->lr, v->h, v->w, 3, GLU_F32, (int64_t)v->w * 3};
-    if (target) *target = glu_image{v->T, v->h, v->w, 3, GLU_F32, (int64_t)v->w * 3};
+    if (targets)
+        for (int k = 0; k < v->d.n_ops; ++k)
+            targets[k] = glu_image{v->T[k], v->h, v->w, 3, GLU_F32, (int64_t)v->w * 3};
     if (theta)
         *theta = glu_theta{v->code, v->weight, v->d.H, v->d.W, v->d.scale, v->d.params.S,
                            v->d.wfmt};

@@ -153,25 +153,33 @@ def test_video_host_validation(lib):
     d.hr_dtype, d.out_dtype = A.GLU_F16, A.GLU_F16
     lib.glu_params_default(ctypes.byref(d.params))
     d.params.S = 5
-    d.wfmt, d.filter, d.saturation, d.gamma, d.overlap = A.GLU_W_UNORM16, 1, 1.0, 0.8, 1
+    d.wfmt, d.n_ops, d.overlap = A.GLU_W_UNORM16, 1, 1
+    d.ops[0] = A.GluLrOp(1, 1.0, 0.8)
     need = lib.glu_video_workspace_size(ctypes.byref(d))
     h, w = 270, 480
-    # three LR float images, the codes and the weights, each 256-byte aligned
+    # the LR float image, two per operator (filtered, target), the codes and the weights, each
+    # 256-byte aligned
     lr = -(-(h * w * 3 * 4) // 256) * 256
     assert need == 3 * lr + 2 * (-(-(2160 * 3840 * 2) // 256) * 256)
+    d.n_ops = 3
+    d.ops[1] = A.GluLrOp(0, 1.3, 1.0)
+    d.ops[2] = A.GluLrOp(-1, 1.0, 1.2)
+    assert lib.glu_video_workspace_size(ctypes.byref(d)) == need + 4 * lr
+    d.n_ops = 1
     out = ctypes.c_void_p()
     assert lib.glu_video_create(ctypes.byref(d), None, need, ctypes.byref(out)) == \
         A.GLU_ERR_WORKSPACE
     assert lib.glu_video_create(ctypes.byref(d), ctypes.c_void_p(0x1100), need - 1,
                                 ctypes.byref(out)) == A.GLU_ERR_WORKSPACE
-    for field, bad in (("hr_dtype", A.GLU_F32), ("out_dtype", A.GLU_U8), ("filter", 2),
-                       ("gamma", 0.0), ("scale", 0)):
-        old = getattr(d, field)
-        setattr(d, field, bad)
+    for obj, field, bad in ((d, "hr_dtype", A.GLU_F32), (d, "out_dtype", A.GLU_U8),
+                            (d.ops[0], "filter", 2), (d.ops[0], "gamma", 0.0), (d, "scale", 0),
+                            (d, "n_ops", 0), (d, "n_ops", A.GLU_VIDEO_MAX_OPS + 1)):
+        old = getattr(obj, field)
+        setattr(obj, field, bad)
         assert lib.glu_video_workspace_size(ctypes.byref(d)) == 0, field
         assert lib.glu_video_create(ctypes.byref(d), ctypes.c_void_p(0x1100), need,
                                     ctypes.byref(out)) == A.GLU_ERR_INVALID_ARG
-        setattr(d, field, old)
+        setattr(obj, field, old)
     assert lib.glu_video_launch(None, 0, None) == A.GLU_ERR_INVALID_ARG
     assert lib.glu_video_destroy(None) == A.GLU_OK
 

@@ -78,7 +78,7 @@ def test_video_last_frame_matches_oracle(api):
         v.bind(k, fr[k], out[k])
         v.launch(k)
     torch.cuda.synchronize()
-    lr, T, theta = v.views()      # the working images of the last frame
+    lr, (T,), theta = v.views()   # the working images of the last frame
     I = fr[n - 1].cpu().numpy()
     lr_ref = O.downsample_box(I, s)
     assert np.abs(lr.cpu().numpy() - lr_ref).max() < 1e-6
@@ -111,4 +111,74 @@ def test_video_rebind_and_argument_errors(api):
         v.launch(4)              # never bound
     with pytest.raises(A.GluError):
         v.launch(A.GLU_VIDEO_MAX_SLOTS)
+    v.close()
+
+
+# two and three LR operators sharing the frame's Theta: (filter, saturation, gamma)
+OPS2 = [(1, 1.0, 0.8), (0, 1.3, 1.0)]
+OPS3 = [(1, 1.0, 0.8), (0, 1.3, 1.0), (-1, 0.7, 1.2)]
+
+
+def separate_op(api, hr, s, S, wfmt, out_dtype, op):
+    lr = api.glu_downsample(hr, s, api.GLU_DOWN_BOX, dtype=torch.float32)
+    f, sat, g = op
+    t = api.glu_fx_filter3(lr, f) if f >= 0 else lr
+    T = api.glu_fx_point(t, sat, g)
+    theta, _ = api.glu_optimize(hr, lr, api.glu_params(S=S), s, wfmt=wfmt)
+    return api.glu_apply(theta, T, out_dtype=out_dtype)
+
+
+@pytest.mark.parametrize("ops,overlap", [(OPS2, True), (OPS3, True), (OPS2, False)])
+def test_video_theta_shared_by_several_operators(api, ops, overlap):
+    """One Algorithm 1 per frame serves every operator (Theta is target-free): the graph replay,
+    the direct launches and, per operator, the separate single-operator calls give identical
+    frames."""
+    s, S, n, W, H = 8, 5, 4, 264, 200
+    fr = frames_f16(W, H, n)
+    k = len(ops)
+    v = api.Video(H, W, s, api.glu_params(S=S), out_dtype=torch.float16, overlap=overlap, ops=ops)
+    outs = torch.zeros((n, k, H, W, 3), dtype=torch.float16, device="cuda")
+    eager = torch.zeros_like(outs)
+    for f in range(n):
+        v.bind(f, fr[f], [outs[f, i] for i in range(k)])
+    for f in range(n):
+        v.launch(f)
+    torch.cuda.synchronize()
+    assert api.glu_device_status() == 0
+    for f in range(n):
+        v.run(fr[f], [eager[f, i] for i in range(k)])
+    torch.cuda.synchronize()
+    assert torch.equal(outs, eager)
+    for f in (0, n - 1):
+        for i, op in enumerate(ops):
+            ref = separate_op(api, fr[f], s, S, api.GLU_W_UNORM16, torch.float16, op)
+            torch.cuda.synchronize()
+            assert torch.equal(outs[f, i], ref), (f, i)
+    v.close()
+
+
+def test_video_several_operators_frame_matches_oracle(api):
+    """The last frame of a two-operator pipeline: the LR image, both targets (Gaussian + gamma 0.8;
+    box + saturation 1.3) against the oracle's operators, Theta against Algorithm 1, and both
+    outputs against Eq. 1 of the oracle's Theta on the GPU's targets."""
+    s, S, n, W, H = 8, 5, 3, 200, 136
+    fr = frames_f16(W, H, n)
+    v = api.Video(H, W, s, api.glu_params(S=S), out_dtype=torch.float32, wfmt=api.GLU_W_F32,
+                  ops=OPS2)
+    out = torch.empty((n, 2, H, W, 3), dtype=torch.float32, device="cuda")
+    for f in range(n):
+        v.bind(f, fr[f], [out[f, 0], out[f, 1]])
+        v.launch(f)
+    torch.cuda.synchronize()
+    lr, (T0, T1), theta = v.views()
+    I = fr[n - 1].cpu().numpy()
+    assert np.abs(lr.cpu().numpy() - O.downsample_box(I, s)).max() < 1e-6
+    L = lr.cpu().numpy().astype(np.float64)
+    assert np.abs(T0.cpu().numpy() - O.op_gamma(O.op_gauss3(L), 0.8)).max() < 1e-5
+    assert np.abs(T1.cpu().numpy() - O.op_saturation(O.op_box3(L), 1.3)).max() < 1e-5
+    check_search(I, L, s, S, theta, wfmt=api.GLU_W_F32)
+    ref = O.glu_fast(I, L, s, S)
+    for i, T in enumerate((T0, T1)):
+        hr_ref = O.apply(ref["ka"], ref["kb"], ref["omega"], s, S, T.cpu().numpy())
+        assert np.abs(out[n - 1, i].cpu().numpy() - hr_ref).max() < 1e-3, i
     v.close()

@@ -159,6 +159,152 @@ __device__ __forceinline__ SearchOut search_pixel(const float4* __restrict__ win
     return step_b<S, kCompact, kInterior>(win, rs, rowmask, colmask, a, bd, ir, ig, ib, eps255);
 }
 
+// ------------------------------------------------------------------ two pixels, packed FP32
+//
+// Two HR pixels of one LR block share the window, so every candidate is evaluated for both at
+// once with the packed two-lane FP32 instructions (add / sub / mul / fma .rn.f32x2): each lane
+// is an ordinary IEEE single-precision operation with round-to-nearest, so lane 0 computes
+// exactly what the scalar search_pixel computes for pixel 0 and lane 1 for pixel 1, in the same
+// order; the square roots and the divisions stay per lane (the same calls as above), and the
+// comparisons and tie-breaks are per pixel. The window is read from a second shared-memory copy
+// that holds each colour channel twice, (r, r, g, g) and (b, b), so a candidate arrives as three
+// packed operands.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// dist2 of both lanes (the same operation order as dist2)
+__device__ __forceinline__ f32x2 dist2x2(f32x2 er, f32x2 eg, f32x2 eb) {
+    return fma2(eb, eb, fma2(eg, eg, mul2(er, er)));
+}
+
+// The duplicated window copy: candidate k's (r, r, g, g) at rg[k] and (b, b) at bb[k].
+__device__ __forceinline__ void lds_dup(const float4* rg, const float2* bb, f32x2& r2, f32x2& g2,
+                                        f32x2& b2) {
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                 : "=l"(r2), "=l"(g2)
+                 : "r"((uint32_t)__cvta_generic_to_shared(rg)));
+    asm volatile("ld.shared.b64 %0, [%1];"
+                 : "=l"(b2)
+                 : "r"((uint32_t)__cvta_generic_to_shared(bb)));
+}
+
+// Algorithm 1 for two pixels (colours (ir0, ig0, ib0) and (ir1, ig1, ib1)) with the same window:
+// win (float4 copy, used for the chosen pairs), rg / bb (duplicated copy) indexed alike. Results
+// equal search_pixel's for each pixel, bit for bit.
+template <int S, bool kCompact = false, bool kInterior = false>
+__device__ __forceinline__ void search_pair(const float4* __restrict__ win,
+                                            const float4* __restrict__ rg,
+                                            const float2* __restrict__ bb, int rs,
+                                            uint32_t rowmask, uint32_t colmask, float ir0,
+                                            float ig0, float ib0, float ir1, float ig1,
+                                            float ib1, float eps255, bool gnu, SearchOut& o0,
+                                            SearchOut& o1) {
+    constexpr int kRowUnroll = (kCompact || S > 5) ? 1 : S;
+    const f32x2 ir = pack2(ir0, ir1), ig = pack2(ig0, ig1), ib = pack2(ib0, ib1);
+    // step 1: the nearest colour of each pixel (exact for uint8 colours), ties to the lowest k
+    float bd0 = kInf, bd1 = kInf;
+    int a0 = 0, a1 = 0;
+#pragma unroll(kRowUnroll)
+    for (int dy = 0; dy < S; ++dy) {
+#pragma unroll
+        for (int dx = 0; dx < S; ++dx) {
+            const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
+            f32x2 cr, cg, cb;
+            lds_dup(&rg[dy * rs + dx], &bb[dy * rs + dx], cr, cg, cb);
+            float d0, d1;
+            unpack2(dist2x2(sub2(cr, ir), sub2(cg, ig), sub2(cb, ib)), d0, d1);
+            const int k = dy * S + dx;
+            if (ok && d0 < bd0) {
+                bd0 = d0;
+                a0 = k;
+            }
+            if (ok && d1 < bd1) {
+                bd1 = d1;
+                a1 = k;
+            }
+        }
+    }
+    if (gnu) {
+        o0.ka = o0.kb = a0;
+        o1.ka = o1.kb = a1;
+        o0.omega = o1.omega = 1.0f;
+        o0.err = sqrt_approx(bd0) * (1.0f / 255.0f);
+        o1.err = sqrt_approx(bd1) * (1.0f / 255.0f);
+        return;
+    }
+    // step 2: for each pixel's a, b over the window minimising the key, ties to the lowest k
+    const float4 ca0 = lds_f4(&win[(a0 / S) * rs + (a0 % S)]);
+    const float4 ca1 = lds_f4(&win[(a1 / S) * rs + (a1 % S)]);
+    const f32x2 ur = sub2(pack2(ca0.x, ca1.x), ir);
+    const f32x2 ug = sub2(pack2(ca0.y, ca1.y), ig);
+    const f32x2 ub = sub2(pack2(ca0.z, ca1.z), ib);
+    const float dae0 = sqrt_approx(bd0) + eps255, dae1 = sqrt_approx(bd1) + eps255;
+    const f32x2 dae = pack2(dae0, dae1);
+    float bkey0 = kInf, bkey1 = kInf;
+    int b0 = a0, b1 = a1;
+#pragma unroll(kRowUnroll)
+    for (int dy = 0; dy < S; ++dy) {
+#pragma unroll
+        for (int dx = 0; dx < S; ++dx) {
+            const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
+            f32x2 cr, cg, cb;
+            lds_dup(&rg[dy * rs + dx], &bb[dy * rs + dx], cr, cg, cb);
+            const f32x2 vr = sub2(cr, ir), vg = sub2(cg, ig), vb = sub2(cb, ib);
+            float q0, q1;
+            unpack2(dist2x2(vr, vg, vb), q0, q1);
+            const f32x2 db = pack2(sqrt_approx(q0), sqrt_approx(q1));
+            const f32x2 xr = fma2(db, ur, mul2(dae, vr));
+            const f32x2 xg = fma2(db, ug, mul2(dae, vg));
+            const f32x2 xb = fma2(db, ub, mul2(dae, vb));
+            const f32x2 D = add2(db, dae);
+            float n0, n1, e0, e1;
+            unpack2(dist2x2(xr, xg, xb), n0, n1);
+            unpack2(mul2(D, D), e0, e1);
+            const float key0 = __fdividef(n0, e0), key1 = __fdividef(n1, e1);
+            const int k = dy * S + dx;
+            if (ok && key0 < bkey0) {
+                bkey0 = key0;
+                b0 = k;
+            }
+            if (ok && key1 < bkey1) {
+                bkey1 = key1;
+                b1 = k;
+            }
+        }
+    }
+    o0.ka = a0;
+    o1.ka = a1;
+    finish_pair(win, rs, S, b0, ir0, ig0, ib0, dae0, bkey0, o0);
+    finish_pair(win, rs, S, b1, ir1, ig1, ib1, dae1, bkey1, o1);
+}
+
 // Row/column validity masks of the window centred on LR block (py, px) of an h x w LR image.
 __device__ __forceinline__ void window_masks(int py, int px, int h, int w, int S,
                                              uint32_t& rowmask, uint32_t& colmask) {

@@ -9,11 +9,13 @@
 // Per tile, the HR tile is staged into shared memory by a 2D TMA load (cp.async.bulk.tensor)
 // completing on an mbarrier (one tensor map per image, kept in the kernel's parameter block);
 // while it is in flight the CTA's threads copy the LR halo (the LR rows and columns the tile's
-// windows reach) into shared memory as float4 colours in 1/255 units. Each thread then owns
-// whole pixels: both candidate loops of Algorithm 1 run in registers against the shared-memory
-// window, so no cross-lane reduction is needed and the tie-break is the deterministic lowest
-// window index. Every variant computes the same arithmetic in the same order: results are
-// bit-identical across variants.
+// windows reach) into shared memory as float4 colours in 1/255 units, plus a copy with every
+// channel duplicated for the packed two-pixel search. Each thread then owns whole pixels, two
+// vertically adjacent ones of one LR block at a time: both candidate loops of Algorithm 1 run in
+// registers against the shared-memory window with packed two-lane FP32 arithmetic (one lane per
+// pixel; search_pair), so no cross-lane reduction is needed and the tie-break is the
+// deterministic lowest window index. Every variant computes the same arithmetic in the same
+// order: results are bit-identical across variants and to the one-pixel search_pixel.
 #pragma once
 
 #include <cudaTypedefs.h>
@@ -50,7 +52,14 @@ struct SBatch {
     int n, total_tiles;
     int wfmt, gnu;
     float eps255;
+    int region_cap;   // LR halo cells of the largest tile: the shared copies' stride
 };
+
+// Shared-memory bytes of the LR halo copies for region_cap cells: float4 colours, then the
+// duplicated (r, r, g, g) float4 and (b, b) float2 copies.
+__host__ __device__ constexpr size_t region_bytes(int cells) {
+    return (size_t)cells * (sizeof(float4) * 2 + sizeof(float2));
+}
 
 template <typename HT, int TH>
 struct HrTile {
@@ -62,6 +71,8 @@ template <int S, typename HT, int TH, bool CP>
 __device__ __forceinline__ bool search_tile(const SBatch& B, int i, int x0, int y0,
                                             HrTile<HT, TH>& tile, uint64_t* bar, uint32_t phase,
                                             float4* region) {
+    float4* const rg = region + B.region_cap;
+    float2* const bbuf = reinterpret_cast<float2*>(rg + B.region_cap);
     const SImg& I = B.im[i];
     constexpr int r = (S - 1) / 2;
     const int tid = threadIdx.x;
@@ -103,6 +114,8 @@ __device__ __forceinline__ bool search_tile(const SBatch& B, int i, int x0, int 
             }
         }
         region[k] = c;
+        rg[k] = make_float4(c.x, c.x, c.y, c.y);
+        bbuf[k] = make_float2(c.z, c.z);
     }
     __syncthreads();
     if (I.use_tma && !mbar_wait_bounded(bar, phase)) {
@@ -114,16 +127,23 @@ __device__ __forceinline__ bool search_tile(const SBatch& B, int i, int x0, int 
 
     // interior tiles (every window inside the LR image) skip the validity masks
     const bool interior = v0 >= 0 && u0 >= 0 && (ye - 1) / s + r < I.h && (xe - 1) / s + r < I.w;
-    // a thread keeps one column of the tile (kThreads is a multiple of kTileW) and walks rows
+    // a thread keeps one column of the tile (kThreads is a multiple of kTileW) and walks pairs
+    // of rows (ty, ty + 1); the warps of one row pair decide alike whether both rows lie in one
+    // LR block (then they share the window and are searched together) or not
+    static_assert(TH % (2 * (kThreads / kTileW)) == 0, "row pairs tile the tile");
     const int tx = tid % kTileW, x = x0 + tx, px = x / s;
     const int col = px - r - u0;
-    for (int ty = tid / kTileW; ty < TH; ty += kThreads / kTileW) {
-        const int y = y0 + ty;
-        if (y >= I.H || x >= I.W) continue;
+    auto store = [&](int y, const SearchOut& o) {
+        const int64_t p = (int64_t)y * I.W + x;
+        I.code[p] = (uint16_t)(o.ka * S * S + o.kb);
+        store_weight(I.weight, B.wfmt, p, o.omega);
+        if (I.err) I.err[p] = o.err;
+    };
+    auto one = [&](int ty) {
+        const int y = y0 + ty, py = y / s;
         const float ir = Px<HT>::to255(tile.px[ty][tx * 3 + 0]);
         const float ig = Px<HT>::to255(tile.px[ty][tx * 3 + 1]);
         const float ib = Px<HT>::to255(tile.px[ty][tx * 3 + 2]);
-        const int py = y / s;
         const float4* win = &region[(py - r - v0) * RW + col];
         SearchOut o;
         if (interior) {
@@ -133,10 +153,37 @@ __device__ __forceinline__ bool search_tile(const SBatch& B, int i, int x0, int 
             window_masks(py, px, I.h, I.w, S, rm, cm);
             o = search_pixel<S, CP>(win, RW, rm, cm, ir, ig, ib, B.eps255, B.gnu != 0);
         }
-        const int64_t p = (int64_t)y * I.W + x;
-        I.code[p] = (uint16_t)(o.ka * S * S + o.kb);
-        store_weight(I.weight, B.wfmt, p, o.omega);
-        if (I.err) I.err[p] = o.err;
+        store(y, o);
+    };
+    for (int ty = 2 * (tid / kTileW); ty < TH; ty += 2 * (kThreads / kTileW)) {
+        const int y = y0 + ty;
+        if (y >= I.H || x >= I.W) continue;
+        const bool two = y + 1 < I.H && y / s == (y + 1) / s;
+        if (!two) {
+            one(ty);
+            if (y + 1 < I.H) one(ty + 1);
+            continue;
+        }
+        const int py = y / s;
+        const int wo = (py - r - v0) * RW + col;
+        SearchOut o0, o1;
+        const float ir0 = Px<HT>::to255(tile.px[ty][tx * 3 + 0]);
+        const float ig0 = Px<HT>::to255(tile.px[ty][tx * 3 + 1]);
+        const float ib0 = Px<HT>::to255(tile.px[ty][tx * 3 + 2]);
+        const float ir1 = Px<HT>::to255(tile.px[ty + 1][tx * 3 + 0]);
+        const float ig1 = Px<HT>::to255(tile.px[ty + 1][tx * 3 + 1]);
+        const float ib1 = Px<HT>::to255(tile.px[ty + 1][tx * 3 + 2]);
+        if (interior) {
+            search_pair<S, CP, true>(&region[wo], &rg[wo], &bbuf[wo], RW, 0u, 0u, ir0, ig0, ib0,
+                                     ir1, ig1, ib1, B.eps255, B.gnu != 0, o0, o1);
+        } else {
+            uint32_t rm, cm;
+            window_masks(py, px, I.h, I.w, S, rm, cm);
+            search_pair<S, CP>(&region[wo], &rg[wo], &bbuf[wo], RW, rm, cm, ir0, ig0, ib0, ir1,
+                               ig1, ib1, B.eps255, B.gnu != 0, o0, o1);
+        }
+        store(y, o0);
+        store(y + 1, o1);
     }
     __syncthreads();  // the tile buffers are reused by the next tile
     return true;
@@ -181,7 +228,7 @@ template <typename HT, int TH, int MINB, bool CP>
 int launch_search_chunk(const SearchArgs* items, int n, cudaStream_t st) {
     SBatch B;  // host staging of the parameter block (copied into the launch)
     memset(&B, 0, sizeof(B));
-    size_t smem = 0;
+    int cap = 0;
     int tiles = 0;
     for (int k = 0; k < n; ++k) {
         const SearchArgs& a = items[k];
@@ -201,9 +248,10 @@ int launch_search_chunk(const SearchArgs* items, int n, cudaStream_t st) {
         tiles += I.tiles_x * ((a.H + TH - 1) / TH);
         const int r = (a.S - 1) / 2;
         const int rh = (TH - 1) / a.s + 2 + 2 * r, rw = (kTileW - 1) / a.s + 2 + 2 * r;
-        const size_t need = sizeof(float4) * (size_t)rh * rw;
-        if (need > smem) smem = need;
+        if (rh * rw > cap) cap = rh * rw;
     }
+    const size_t smem = region_bytes(cap);
+    B.region_cap = cap;
     B.n = n;
     B.total_tiles = tiles;
     B.wfmt = items[0].wfmt;

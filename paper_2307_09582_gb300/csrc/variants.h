@@ -12,7 +12,7 @@ struct SearchVariant {
     int tile_h, min_blocks, compact;
 };
 constexpr SearchVariant kSearchVariants[] = {
-    {32, 2, 0}, {16, 2, 0}, {8, 2, 0}, {16, 3, 0}, {16, 4, 1},
+    {32, 2, 0}, {16, 2, 0}, {8, 2, 0}, {16, 3, 1}, {16, 4, 1},
 };
 constexpr int kNumSearchVariants = (int)(sizeof(kSearchVariants) / sizeof(kSearchVariants[0]));
 

@@ -94,6 +94,8 @@ struct JointCtl {
     int nfg;          // large-error pixels of the current iteration (all active images)
     int open_tasks;
     int small_cur;    // 1: the one-CTA list kernel built this iteration's components and graph
+    int nedge;        // dependency edges listed by k_deps in the current iteration
+    int ticket[GLU_MAX_ITERS];    // tiles taken by the threshold pass (decoupled look-back order)
     int claim[GLU_MAX_ITERS];
     int finished[GLU_MAX_ITERS];
     int head[GLU_MAX_ITERS];      // ready queue: positions taken
@@ -124,6 +126,7 @@ struct JointWs {
     int2* start;            // mcap + 1
     int* done;              // mcap
     int* tile_a;            // tiles over np
+    unsigned long long* tstat;  // tiles over np: look-back status of the threshold pass
     int2* tile_b;           // tiles over mcap
     int* own;               // nq * kOwnSlots
     uint8_t* ovf;           // nq
@@ -189,6 +192,7 @@ static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t
     t.start = (int2*)take(sizeof(int2) * (mcap + 1));
     t.done = (int*)take(sizeof(int) * mcap);
     t.tile_a = (int*)take(sizeof(int) * tiles_a);
+    t.tstat = (unsigned long long*)take(sizeof(unsigned long long) * tiles_a);
     t.tile_b = (int2*)take(sizeof(int2) * tiles_b);
     t.own = (int*)take(sizeof(int) * nq * kOwnSlots);
     t.ovf = (uint8_t*)take(nq);
@@ -336,6 +340,13 @@ __device__ __forceinline__ int block_excl_scan_any(int v, int* out_excl, int* sm
     return total;
 }
 
+// Warp-wide sum of a 64-bit integer (fixed butterfly; integer addition is exact).
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Verification log (test hook, null: off): log[0].x counts records, records from log[1], at most
 // cap of them. Kinds: (iteration, component, LR pixel, HR pixel) for a trial's replacement
 // choice; (256 + iteration, HR pixel, membership, 0) for a pixel whose FP32 error is within
@@ -352,10 +363,12 @@ __device__ __forceinline__ void log_record(int4* log, long long cap, int4 rec) {
 // Every counter of the control block starts at zero, except the active flags of the nimg
 // images and active_any; stamps and task slots are cleared.
 __global__ void k_ctl_init(JointCtl* c, unsigned long long* stamp, int64_t nq,
-                           unsigned long long* slot_word, int nimg) {
+                           unsigned long long* slot_word, int nimg, unsigned long long* tstat,
+                           int64_t ntstat) {
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = i0; i < kMaxSlots; i += stride) slot_word[i] = 0ull;
+    for (int64_t i = i0; i < ntstat; i += stride) tstat[i] = 0ull;
     for (int64_t i = i0; i < nq; i += stride) stamp[i] = 0ull;
     int* ci = (int*)c;
     constexpr int nwords = (int)(sizeof(JointCtl) / sizeof(int));
@@ -445,77 +458,172 @@ __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int
 
 // ----------------------------------------------------------------------- threshold and CCL
 
-// Large-error set of the active images and union-find init; clears the owner slots. A CTA per
-// tile of kScanTile pixels also counts the tile's large-error pixels for their ordered
-// compaction.
-__global__ void k_threshold(const __grid_constant__ JBatch B, int* lab, int* own, uint8_t* ovf,
-                            int* tile_cnt, JointCtl* c, int it, int4* vlog, long long vcap) {
+// Large-error set of the active images, its ordered list and the union-find init, in one pass
+// over the image: a CTA per tile of kScanTile pixels (16 consecutive pixels per thread) marks
+// E_p > tau, starts every large-error pixel as its own union-find root (lab[p] = p) and writes
+// the tile's large-error pixels to the list fgl in raster order at the tile's offset, found by
+// decoupled look-back: tiles are taken in order by an atomic ticket, each publishes its count,
+// then its inclusive prefix once it has read its predecessors' (a tile waits only on tiles that
+// were taken before it, so every wait ends; the waits are bounded all the same). Iteration 0
+// (full_clear) also sets every other pixel's label to -1 and clears the owner slots; later
+// iterations find them cleared by k_lists_clear, which resets only the previous lists' pixels
+// and blocks.
+constexpr uint32_t kLookbackSpin = 1u << 22;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Status word of a tile: [63:58] tag (iteration + 1), [57:56] 1 = count, 2 = inclusive prefix,
+// [55:0] the value.
+__device__ __forceinline__ unsigned long long tstat_word(int tag, int kind, long long v) {
+    return ((unsigned long long)tag << 58) | ((unsigned long long)kind << 56) |
+           ((unsigned long long)v & ((1ull << 56) - 1));
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_threshold_list(const __grid_constant__ JBatch B, JointWs W, int it, int full_clear,
+                     int4* vlog, long long vcap) {
+    JointCtl* c = W.ctl;
     if (!any_active(c)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->small_cur = 0;   // a new iteration's lists
-    __shared__ int wsum[8];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int local = 0, run_img = -1, run = 0;
-    for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
-        const int64_t p = base + k;
-        if (p >= B.np) break;
-        const int i = img_of_p(B, p);
+    constexpr int kRounds = kScanTile / kScanThreads;   // 256 consecutive pixels per round
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_cnt[kRounds * kWarps];   // per (round, warp): large-error pixels, raster order
+    __shared__ int wsm[8];
+    __shared__ int s_tile;
+    __shared__ long long s_excl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_tile = atomicAdd(&c->ticket[it], 1);
+        if (s_tile == 0) {   // a new iteration's lists
+            c->small_cur = 0;
+            c->nedge = 0;
+        }
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t base = (int64_t)tile * kScanTile;
+    unsigned bal[kRounds];
+    int run_img = -1, run = 0;
+#pragma unroll
+    for (int k = 0; k < kRounds; ++k) {
+        const int64_t p = base + k * kScanThreads + tid;
         bool fg = false;
-        if (c->active[i]) {
-            const float e = B.im[i].err[p - B.im[i].p0];
-            fg = e > B.tau;
-            if (vlog && fabsf(e - B.tau) < kThrLogBand)
-                log_record(vlog, vcap, make_int4(256 + it, (int)(p - B.im[i].p0), fg ? 1 : 0, 0));
-        }
-        lab[p] = fg ? (int)p : -1;
-        if (fg) {
-            if (i != run_img) {
-                if (run) atomicAdd(&c->n_large[run_img][it], run);
-                run_img = i;
-                run = 0;
+        if (p < B.np) {
+            const int i = img_of_p(B, p);
+            if (c->active[i]) {
+                const float e = B.im[i].err[p - B.im[i].p0];
+                fg = e > B.tau;
+                if (vlog && fabsf(e - B.tau) < kThrLogBand)
+                    log_record(vlog, vcap,
+                               make_int4(256 + it, (int)(p - B.im[i].p0), fg ? 1 : 0, 0));
             }
-            ++run;
-            ++local;
+            if (full_clear) W.lab[p] = fg ? (int)p : -1;
+            else if (fg) W.lab[p] = (int)p;
+            if (fg) {
+                if (i != run_img) {
+                    if (run) atomicAdd(&c->n_large[run_img][it], run);
+                    run_img = i;
+                    run = 0;
+                }
+                ++run;
+            }
         }
+        bal[k] = __ballot_sync(0xffffffffu, fg);
+        if (lane == 0) s_cnt[k * kWarps + warp] = __popc(bal[k]);
     }
     if (run) atomicAdd(&c->n_large[run_img][it], run);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = local;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < 8; ++w) t += wsum[w];
-        tile_cnt[blockIdx.x] = t;
+    // exclusive offsets of the (round, warp) groups in raster order, and the tile's count
+    const int v = tid < kRounds * kWarps ? s_cnt[tid] : 0;
+    int ex;
+    const int agg = block_excl_scan(v, &ex, wsm);
+    if (tid < kRounds * kWarps) s_cnt[tid] = ex;
+    // the tile's offset: warp 0 looks back over 32 predecessor tiles at a time
+    if (warp == 0) {
+        const int tag = it + 1;
+        if (lane == 0)
+            st_release_u64(&W.tstat[tile], tstat_word(tag, tile == 0 ? 2 : 1, agg));
+        long long excl = 0;
+        bool ok = true;
+        for (int k0 = tile - 1; k0 >= 0; k0 -= 32) {
+            const int k = k0 - lane;
+            unsigned long long w = tstat_word(tag, 2, 0);   // before tile 0: a zero prefix
+            if (k >= 0) {
+                uint32_t spins = 0;
+                for (;;) {
+                    w = ld_acquire_u64(&W.tstat[k]);
+                    if ((int)(w >> 58) == tag && ((w >> 56) & 3ull) != 0) break;
+                    if (++spins > kLookbackSpin || *(volatile const int*)&c->timeout) {
+                        ok = false;
+                        w = tstat_word(tag, 2, 0);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            const unsigned pm = __ballot_sync(0xffffffffu, ((w >> 56) & 3ull) == 2);
+            const int stop = pm ? __ffs(pm) - 1 : 31;   // the nearest inclusive prefix
+            excl += warp_sum_ll(lane <= stop ? (long long)(w & ((1ull << 56) - 1)) : 0);
+            if (pm) break;
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) {
+            if (!ok) {
+                set_status(GLU_ERR_TIMEOUT);
+                atomicExch(&c->timeout, 1);
+                excl = 0;
+            }
+            if (tile > 0) st_release_u64(&W.tstat[tile], tstat_word(tag, 2, excl + agg));
+            s_excl = excl;
+            if (tile == (int)gridDim.x - 1) {   // the last tile knows the list's length
+                c->nfg = (int)(excl + agg);
+                if (excl + agg == 0) c->active_any = 0;   // every large-error set is empty
+            }
+        }
     }
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < B.nq; q += stride) {
+    __syncthreads();
+    const long long e0 = s_excl;
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-        for (int k = 0; k < kOwnSlots; ++k) own[q * kOwnSlots + k] = -1;
-        ovf[q] = 0;
+    for (int k = 0; k < kRounds; ++k)
+        if ((bal[k] >> lane) & 1u)
+            W.ulist[e0 + s_cnt[k * kWarps + warp] + __popc(bal[k] & lt)] =
+                (int)(base + k * kScanThreads + tid);
+    if (full_clear) {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + tid; q < B.nq; q += stride) {
+#pragma unroll
+            for (int k = 0; k < kOwnSlots; ++k) W.own[q * kOwnSlots + k] = -1;
+            W.ovf[q] = 0;
+        }
     }
 }
 
-// The large-error pixels in raster (global index) order: fgl[0 .. nfg). Later passes of the
-// iteration visit only them.
-__global__ void k_fg_scatter(const int* lab, int64_t np, const int* tile_off, int* fgl,
-                             const JointCtl* c) {
+// After an iteration's trials: the labels of its large-error pixels back to -1 and the owner
+// slots of the LR blocks its components touched cleared (everything else is still clear), so
+// the next threshold pass writes only its own pixels.
+__global__ void k_lists_clear(JointWs W) {
+    JointCtl* c = W.ctl;
     if (!any_active(c)) return;
-    __shared__ int wsm[8];
-    constexpr int per = kScanTile / kScanThreads;
-    const int64_t my = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * per;
-    int flags = 0, cntl = 0;
+    const int M = c->M_cur;
+    if (c->nfg <= 0 || M <= 0) return;
+    const int2 tot = W.start[M];
+    const int stride = gridDim.x * blockDim.x;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot.x; e += stride)
+        W.lab[__ldcg(&W.comp_pix[e])] = -1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot.y; e += stride) {
+        const int64_t q = __ldcg(&W.qlist[e]);
 #pragma unroll
-    for (int k = 0; k < per; ++k) {
-        const bool f = my + k < np && lab[my + k] >= 0;
-        flags |= (int)f << k;
-        cntl += f;
+        for (int k = 0; k < kOwnSlots; ++k) W.own[q * kOwnSlots + k] = -1;
+        W.ovf[q] = 0;
     }
-    int ex;
-    (void)block_excl_scan(cntl, &ex, wsm);
-    int o = tile_off[blockIdx.x] + ex;
-#pragma unroll
-    for (int k = 0; k < per; ++k)
-        if ((flags >> k) & 1) fgl[o++] = (int)(my + k);
 }
 
 // Root of x with path halving; parents only ever decrease (parent < child).
@@ -612,7 +720,7 @@ __global__ void k_root_count(const int* lab, const int* fgl, int* tile_cnt, cons
 // (OUT = 1); an empty large-error set stops every image
 template <int OUT>
 __global__ void k_tile_scan(int* tile_cnt, int ntiles, JointCtl* c) {
-    if (OUT == 0 ? !any_active(c) : skip_lists(c)) return;
+    if (skip_lists(c)) return;
     __shared__ int wsm[8];
     // the root counts cover only the list's tiles
     if (OUT == 1) ntiles = (c->nfg + kScanTile - 1) / kScanTile;
@@ -883,17 +991,31 @@ __device__ __forceinline__ void bitonic_sort_smem(int* a, int n2) {
     }
 }
 
-// PASS 0: pend[j] and successor counts. PASS 1: successor lists, and the components without
-// predecessors enter the ready queue. Both passes enumerate the same set. Distinct predecessors
-// come from a shared-memory bitmap over component indices (one atomicOr per candidate) when
-// M <= kDepsBits, else from a sorted candidate list.
+// k_deps: per component j, pend[j] = the number of its distinct predecessors, every predecessor's
+// successor count, and every (predecessor, j) edge appended to a scratch list; k_edge_scatter then
+// writes the successor lists (CSR, after a scan of the counts) from that list and puts the
+// components without predecessors in the ready queue. Distinct predecessors come from a
+// shared-memory bitmap over component indices (one atomicOr per candidate) when M <= kDepsBits,
+// else from a sorted candidate list.
 constexpr int kDepsBits = 1 << 16;
 // Neighbourhood bitmap of one component (dilated bounding box of its blocks), used above this
 // many (block, neighbour) pairs.
 constexpr int kNbBits = 1 << 15;
 constexpr int kNbMinPairs = 4096;
 
-template <int PASS>
+// The scratch list of dependency edges (i, j): the backup weight plane, free outside the trials.
+__device__ __forceinline__ int2* edge_list(const JointWs& W) { return reinterpret_cast<int2*>(W.sh_w); }
+__device__ __forceinline__ int edge_cap(const JBatch& B) {
+    return (int)(B.np / 2 < ((int64_t)1 << 30) ? B.np / 2 : ((int64_t)1 << 30));
+}
+
+__device__ __forceinline__ void add_edge(const JBatch& B, const JointWs& W, JointCtl* c, int i,
+                                         int j) {
+    atomicAdd(&W.dag_cnt[i].x, 1);
+    const int k = atomicAdd(&c->nedge, 1);
+    if (k < edge_cap(B)) edge_list(W)[k] = make_int2(i, j);
+}
+
 __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
     JointCtl* c = W.ctl;
     if (skip_lists(c)) return;
@@ -903,17 +1025,6 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
     __shared__ int s_n, s_bad, s_vmin, s_vmax, s_umin, s_umax;
     const int M = c->M_cur;
     const bool use_bits = M <= kDepsBits;
-    if (PASS == 1) {
-        if (threadIdx.x == 0) {
-            s_bad = *(volatile int*)&c->dag_bad[it];
-            if (!s_bad && (int64_t)W.dag_start[M].x > W.ecap) {
-                s_bad = 1;
-                atomicExch(&c->dag_bad[it], 1);
-            }
-        }
-        __syncthreads();
-        if (s_bad) return;
-    }
     if (use_bits)
         for (int t = threadIdx.x; t < (M + 31) / 32; t += blockDim.x) bits[t] = 0u;
     for (int j = blockIdx.x; j < M; j += gridDim.x) {
@@ -972,12 +1083,7 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 if (atomicOr(&bits[i >> 5], bit) & bit) return;
                 const int slot = atomicAdd(&s_n, 1);
                 if (slot < kCandMax) cand[slot] = i;
-                if (PASS == 0) {
-                    atomicAdd(&W.dag_cnt[i].x, 1);
-                } else {
-                    const int pos = atomicAdd(&W.dag_fill[i], 1);
-                    W.succ[W.dag_start[i].x + pos] = j;
-                }
+                add_edge(B, W, c, i, j);
             } else {
                 const int slot = atomicAdd(&s_n, 1);
                 if (slot < kCandMax) cand[slot] = i;
@@ -1076,26 +1182,38 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 const int i = cand[t];
                 if (t > 0 && cand[t - 1] == i) continue;   // distinct predecessors only
                 atomicAdd(&s_n, 1);
-                if (PASS == 0) {
-                    atomicAdd(&W.dag_cnt[i].x, 1);
-                } else {
-                    const int pos = atomicAdd(&W.dag_fill[i], 1);
-                    W.succ[W.dag_start[i].x + pos] = j;
-                }
+                add_edge(B, W, c, i, j);
             }
             __syncthreads();
             npred = s_n;
         }
-        if (threadIdx.x == 0) {
-            if (PASS == 0) {
-                W.pend[j] = npred;
-            } else if (W.pend[j] == 0) {
-                const int pos = atomicAdd(&c->tail[it], 1);
-                W.queue[pos] = j;
-                GLU_TRACE_ANY(it, j, 0);
-            }
-        }
+        if (threadIdx.x == 0) W.pend[j] = npred;
         __syncthreads();
+    }
+}
+
+// Successor lists from the edge list (dag_start: the scanned successor counts) and the ready
+// queue's first entries. The graph is dropped (the trials then claim in index order) when the
+// edges did not fit the scratch list or the successor array.
+__global__ void k_edge_scatter(const __grid_constant__ JBatch B, JointWs W, int it) {
+    JointCtl* c = W.ctl;
+    if (skip_lists(c)) return;
+    const int M = c->M_cur, ne = c->nedge;
+    if (*(volatile int*)&c->dag_bad[it] || ne > edge_cap(B) || (int64_t)W.dag_start[M].x > W.ecap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&c->dag_bad[it], 1);
+        return;
+    }
+    const int2* E = edge_list(W);
+    const int stride = gridDim.x * blockDim.x;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += stride) {
+        const int2 e = __ldcg(&E[k]);
+        W.succ[W.dag_start[e.x].x + atomicAdd(&W.dag_fill[e.x], 1)] = e.y;
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
+        if (W.pend[j] != 0) continue;
+        const int pos = atomicAdd(&c->tail[it], 1);
+        W.queue[pos] = j;
+        GLU_TRACE_ANY(it, j, 0);
     }
 }
 
@@ -1170,8 +1288,11 @@ __device__ __forceinline__ int small_scan(int* v, int n, int* scan_smem) {
     return tot;
 }
 
+// cond / has_cond: inside a recorded graph, the condition of the conditional node that holds the
+// multi-kernel path; set to 0 (skip it) when this kernel built the lists (its default, 1, runs it).
 __global__ void __launch_bounds__(kSmallThreads, 1)
-    k_small_comp(const __grid_constant__ JBatch B, JointWs W, int it) {
+    k_small_comp(const __grid_constant__ JBatch B, JointWs W, int it,
+                 cudaGraphConditionalHandle cond, int has_cond) {
     JointCtl* c = W.ctl;
     if (!any_active(c)) return;
     const int nfg = c->nfg;
@@ -1428,7 +1549,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     }
     __syncthreads();
     GLU_SMALL_STAMP(it, 9);
-    if (tid == 0) c->small_cur = 1;
+    if (tid == 0) {
+        c->small_cur = 1;
+        if (has_cond) cudaGraphSetConditional(cond, 0u);
+    }
 }
 
 // ---------------------------------------------------------------------------- the trials
@@ -1462,12 +1586,6 @@ __device__ __forceinline__ long long to_fixed(float x) {
     return __float2ll_rn(x * 4294967296.0f);
 }
 
-// Warp-wide sum of a 64-bit integer (fixed butterfly; integer addition is exact).
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 __device__ __forceinline__ uint32_t load_rgb(const uint8_t* L, int64_t pitch, int v, int u) {
     const uint8_t* p = L + (int64_t)v * pitch + (int64_t)u * 3;
@@ -2848,8 +2966,11 @@ static int collect_graph() {
 // Every launch of one Algorithm 2 call on `st` (phase events into profiling slot `slot`, if
 // >= 0). The sequence depends only on the arguments: iterations after an image's convergence
 // still launch and return at once, so the sequence can be replayed as a CUDA graph.
+// body: a second stream when `st` is recording a graph (the multi-kernel list path of every
+// iteration then goes into a conditional node that the one-CTA kernel switches off), else null.
 static int issue_joint(const JointItem* items, int n, const JointCommon& cm, const JointWs& ws,
-                       int64_t np, int64_t nq, int slot, cudaStream_t st) {
+                       int64_t np, int64_t nq, int slot, cudaStream_t st,
+                       cudaStream_t body = nullptr) {
     int evi = 0;
 
     JBatch B;   // host staging of the parameter block (copied into each launch)
@@ -2892,8 +3013,8 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
         if (rc0) return rc0;
     }
     prof::mark(slot, evi++, st);
-    k_ctl_init<<<grid_cap(nq > kMaxSlots ? nq : kMaxSlots, T), T, 0, st>>>(ws.ctl, ws.stamp, nq,
-                                                                          ws.slot_word, n);
+    k_ctl_init<<<grid_cap(nq > kMaxSlots ? nq : kMaxSlots, T), T, 0, st>>>(
+        ws.ctl, ws.stamp, nq, ws.slot_word, n, ws.tstat, (np + kScanTile - 1) / kScanTile + 1);
     // initialise every LR image by regular grid downsampling, Theta and E by Algorithm 1
     k_grid_batch<<<grid_cap(nq, T), T, 0, st>>>(B);
     GLU_LAUNCH_CHECK();
@@ -2933,38 +3054,70 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
         // scratch of the trials, free until then)
         int* fgl = ws.ulist;
         const int lgrid = 2 * sm_count();   // list passes: a thread per large-error pixel or so
-        k_threshold<<<tiles_a, kScanThreads, 0, st>>>(B, ws.lab, ws.own, ws.ovf, ws.tile_a,
-                                                       ws.ctl, it, cm.argmax_log,
-                                                       cm.argmax_cap);
-        k_tile_scan<0><<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
-        k_fg_scatter<<<tiles_a, kScanThreads, 0, st>>>(ws.lab, np, ws.tile_a, fgl, ws.ctl);
-        // a short list: the whole phase in one CTA; the launches below then return at once
-        k_small_comp<<<1, kSmallThreads, sizeof(SmallSmem), st>>>(B, ws, it);
-        k_ccl_merge<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.ctl);
-        k_ccl_flatten<<<lgrid, T, 0, st>>>(ws.lab, fgl, ws.ctl);
-        k_root_count<<<list_grid_a, kScanThreads, 0, st>>>(ws.lab, fgl, ws.tile_a, ws.ctl);
-        k_tile_scan<1><<<1, kScanThreads, 0, st>>>(ws.tile_a, tiles_a, ws.ctl);
-        k_root_scatter<<<list_grid_a, kScanThreads, 0, st>>>(B, ws.lab, fgl, ws.tile_a, ws.roots,
+        k_threshold_list<<<tiles_a, kScanThreads, 0, st>>>(B, ws, it, it == 0 ? 1 : 0,
+                                                            cm.argmax_log, cm.argmax_cap);
+        // a short list: the whole phase in one CTA, and the multi-kernel path below is skipped:
+        // inside a recorded graph by a conditional node, otherwise its kernels return at once
+        cudaGraphConditionalHandle cond = 0;
+        cudaStream_t ls = st;   // the stream of the multi-kernel path
+        if (body) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            GLU_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g));
+            if (cs != cudaStreamCaptureStatusActive || !g) return GLU_ERR_CUDA;
+            GLU_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+        }
+        k_small_comp<<<1, kSmallThreads, sizeof(SmallSmem), st>>>(B, ws, it, cond, body ? 1 : 0);
+        if (body) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            const cudaGraphEdgeData* edata = nullptr;
+            size_t nd = 0;
+            GLU_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edata, &nd));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = cond;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node = nullptr;
+            GLU_CUDA_TRY(cudaGraphAddNode(&node, g, deps, edata, nd, &cp));
+            GLU_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                                             cudaStreamSetCaptureDependencies));
+            GLU_CUDA_TRY(cudaStreamBeginCaptureToGraph(body, cp.conditional.phGraph_out[0], nullptr,
+                                                       nullptr, 0, cudaStreamCaptureModeRelaxed));
+            ls = body;
+        }
+        k_ccl_merge<<<lgrid, T, 0, ls>>>(B, ws.lab, fgl, ws.ctl);
+        k_ccl_flatten<<<lgrid, T, 0, ls>>>(ws.lab, fgl, ws.ctl);
+        k_root_count<<<list_grid_a, kScanThreads, 0, ls>>>(ws.lab, fgl, ws.tile_a, ws.ctl);
+        k_tile_scan<1><<<1, kScanThreads, 0, ls>>>(ws.tile_a, tiles_a, ws.ctl);
+        k_root_scatter<<<list_grid_a, kScanThreads, 0, ls>>>(B, ws.lab, fgl, ws.tile_a, ws.roots,
                                                          ws.cnt, ws.fill, ws.done, ws.dag_cnt,
                                                          ws.dag_fill, ws.queue, ws.ctl, it);
-        k_comp_count<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.roots, ws.cnt, ws.own,
+        k_comp_count<<<lgrid, T, 0, ls>>>(B, ws.lab, fgl, ws.roots, ws.cnt, ws.own,
                                                          ws.ovf, ws.qflag, ws.ctl);
-        k_comp_tile_reduce<<<list_grid_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.ctl);
-        k_comp_tile_scan<<<1, kScanThreads, 0, st>>>(ws.tile_b, ws.ctl);
-        k_comp_scan<<<list_grid_b, kScanThreads, 0, st>>>(ws.cnt, ws.tile_b, ws.start, ws.ctl);
-        k_comp_fill<<<lgrid, T, 0, st>>>(B, ws.lab, fgl, ws.qflag, ws.start,
+        k_comp_tile_reduce<<<list_grid_b, kScanThreads, 0, ls>>>(ws.cnt, ws.tile_b, ws.ctl);
+        k_comp_tile_scan<<<1, kScanThreads, 0, ls>>>(ws.tile_b, ws.ctl);
+        k_comp_scan<<<list_grid_b, kScanThreads, 0, ls>>>(ws.cnt, ws.tile_b, ws.start, ws.ctl);
+        k_comp_fill<<<lgrid, T, 0, ls>>>(B, ws.lab, fgl, ws.qflag, ws.start,
                                                         ws.fill, ws.comp_pix, ws.qlist, ws.ctl);
         // the trials' dependency graph
-        k_deps<0><<<grid_cap(ws.mcap, 1, 4), 256, 0, st>>>(B, ws, it);
-        k_comp_tile_reduce<<<list_grid_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.ctl);
-        k_comp_tile_scan<<<1, kScanThreads, 0, st>>>(ws.tile_b, ws.ctl);
-        k_comp_scan<<<list_grid_b, kScanThreads, 0, st>>>(ws.dag_cnt, ws.tile_b, ws.dag_start, ws.ctl);
-        k_deps<1><<<grid_cap(ws.mcap, 1, 4), 256, 0, st>>>(B, ws, it);
+        k_deps<<<grid_cap(ws.mcap, 1, 4), 256, 0, ls>>>(B, ws, it);
+        k_comp_tile_reduce<<<list_grid_b, kScanThreads, 0, ls>>>(ws.dag_cnt, ws.tile_b, ws.ctl);
+        k_comp_tile_scan<<<1, kScanThreads, 0, ls>>>(ws.tile_b, ws.ctl);
+        k_comp_scan<<<list_grid_b, kScanThreads, 0, ls>>>(ws.dag_cnt, ws.tile_b, ws.dag_start, ws.ctl);
+        k_edge_scatter<<<list_grid_b, 256, 0, ls>>>(B, ws, it);
         GLU_LAUNCH_CHECK();
+        if (body) {
+            cudaGraph_t done = nullptr;
+            GLU_CUDA_TRY(cudaStreamEndCapture(body, &done));
+        }
         prof::mark(slot, evi++, st);
         X.it = it;
         rc = launch_trials(B, X, st);
         if (rc) return rc;
+        k_lists_clear<<<list_grid_a, kScanThreads, 0, st>>>(ws);
         prof::mark(slot, evi++, st);
         // R_{it+1} = R_it + the kept trials' differences (added by the trials themselves)
         k_resid_final<<<1, 32, 0, st>>>(B, ws.ctl, it);
@@ -3065,16 +3218,29 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
         GLU_CUDA_TRY(cudaGraphLaunch(g.exec, st));
         if (prof::enabled) prof::graph_pending = true;
     } else if (same && g.seen >= 1) {
-        static cudaStream_t cap = nullptr;
+        static cudaStream_t cap = nullptr, cap_body = nullptr;
         static int cap_device = -1;
         if (!cap || cap_device != device) {
             if (cap) cudaStreamDestroy(cap);
+            if (cap_body) cudaStreamDestroy(cap_body);
+            cap = cap_body = nullptr;
             GLU_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            GLU_CUDA_TRY(cudaStreamCreateWithFlags(&cap_body, cudaStreamNonBlocking));
             cap_device = device;
         }
         cudaGraph_t graph = nullptr;
         GLU_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
-        rc = issue_joint(key, n, ckey, ws, np, nq, prof::enabled ? prof::kGraphSlot : -1, cap);
+        rc = issue_joint(key, n, ckey, ws, np, nq, prof::enabled ? prof::kGraphSlot : -1, cap,
+                         cap_body);
+        {   // a failure in the middle of a conditional body leaves that capture open: close it
+            cudaStreamCaptureStatus bs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(cap_body, &bs) == cudaSuccess &&
+                bs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t bg = nullptr;
+                (void)cudaStreamEndCapture(cap_body, &bg);
+                if (rc == GLU_OK) rc = GLU_ERR_CUDA;
+            }
+        }
         const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
         cudaGraphExec_t exec = nullptr;
         if (rc == GLU_OK && ec == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
@@ -3083,8 +3249,9 @@ int launch_joint_batch(const JointItem* items, int n, const JointCommon& cm, voi
             GLU_CUDA_TRY(cudaGraphLaunch(g.exec, st));
             if (prof::enabled) prof::graph_pending = true;
         } else {
+            // recording failed (a CUDA call refused inside the capture): issue directly
             (void)cudaGetLastError();
-            if (rc == GLU_OK) {
+            if (rc == GLU_OK || rc == GLU_ERR_CUDA) {
                 const int slot = prof::enabled && prof::used < prof::kSlots ? prof::used++ : -1;
                 rc = issue_joint(key, n, ckey, ws, np, nq, slot, st);
             }

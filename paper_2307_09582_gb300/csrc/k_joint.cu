@@ -951,6 +951,21 @@ __device__ __forceinline__ unsigned long long gtimer() {
 #define GLU_TRACE_ANY(it, j, k) do { } while (0)
 #endif
 #ifdef GLU_TRIAL_TRACE
+// Debug builds only: per-warp stamps inside the one-CTA trials of iteration 0 (component,
+// warp, [pass start, pass end, full-search start, full-search end, blocks, pixels queued]).
+constexpr int kWTraceMax = 4096;
+static __device__ unsigned long long g_wtrace[kWTraceMax][32][6];
+#define GLU_WSTAMP(it, j, k) \
+    do { if ((it) == 0 && (j) < kWTraceMax && (threadIdx.x & 31) == 0) \
+        g_wtrace[j][threadIdx.x >> 5][k] = gtimer(); } while (0)
+#define GLU_WVAL(it, j, k, v) \
+    do { if ((it) == 0 && (j) < kWTraceMax && (threadIdx.x & 31) == 0) \
+        g_wtrace[j][threadIdx.x >> 5][k] = (unsigned long long)(v); } while (0)
+#else
+#define GLU_WSTAMP(it, j, k) do { } while (0)
+#define GLU_WVAL(it, j, k, v) do { } while (0)
+#endif
+#ifdef GLU_TRIAL_TRACE
 // Debug builds only: phase stamps of the one-CTA list kernel per iteration.
 static __device__ unsigned long long g_small_t[GLU_MAX_ITERS][16];
 #define GLU_SMALL_STAMP(it, k) \
@@ -2058,28 +2073,30 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
     uint32_t rm, cm;
     window_masks(bv, bu, I.h, I.w, S, rm, cm);
     const float4* win = &F.region[(bv - r - RV0) * RW + (bu - r - RU0)];
-    // the replaced LR pixels in this block's window, ascending window index
-    int chg[kMaxChg];
+    // the replaced LR pixels in this block's window as a bit set over window indices (the same
+    // in every lane of the warp, so the loops over it below run in step)
+    constexpr int NW = (K + 31) / 32;
+    uint32_t chg[NW];
     int nchg = 0;
 #pragma unroll
-    for (int t = 0; t < kMaxChg; ++t) chg[t] = 0;
-    if (incr) {
-        for (int k0 = 0; k0 < K; k0 += 32) {
-            const int k = k0 + lane;
+    for (int w = 0; w < NW; ++w) {
+        chg[w] = 0u;
+        if (incr) {
+            const int k = w * 32 + lane;
             bool is = false;
             if (k < K)
                 is = F.qmap[(bv - r + k / S - RV0) * RW + (bu - r + k % S - RU0)] != 0;
-            unsigned m = __ballot_sync(0xffffffffu, is);
-            while (m) {
-                const int kk = k0 + __ffs(m) - 1;
-                m &= m - 1;
-#pragma unroll
-                for (int t = 0; t < kMaxChg; ++t)
-                    if (t == nchg) chg[t] = kk;
-                ++nchg;
-            }
+            chg[w] = __ballot_sync(0xffffffffu, is);
+            nchg += __popc(chg[w]);
         }
     }
+    auto changed = [&](int k) -> bool {
+        uint32_t m = chg[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w)
+            if ((k >> 5) == w) m = chg[w];
+        return (m >> (k & 31)) & 1u;
+    };
     const bool use_incr = incr && nchg <= kMaxChg;
     const int ys = bv * I.s, xs = bu * I.s;
     const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
@@ -2101,12 +2118,7 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
             } else {
                 const int code0 = (int)F.code0[off + jp];
                 const int a0 = code0 / K, b0 = code0 % K;
-                bool redo_a = false, redo_b = false;
-#pragma unroll
-                for (int t = 0; t < kMaxChg; ++t) {
-                    redo_a |= t < nchg && chg[t] == a0;
-                    redo_b |= t < nchg && chg[t] == b0;
-                }
+                const bool redo_a = changed(a0), redo_b = changed(b0);
                 if (redo_a) {
                     want = -1;
                 } else {
@@ -2116,14 +2128,15 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
                     bd = dist2(ca0.x - ir, ca0.y - ig, ca0.z - ib);
                     a = a0;
 #pragma unroll
-                    for (int t = 0; t < kMaxChg; ++t) {
-                        if (t >= nchg) break;
-                        const int k = chg[t];
-                        const float4 cc = lds_f4(&win[(k / S) * RW + (k % S)]);
-                        const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
-                        if (d2 < bd || (d2 == bd && k < a)) {
-                            bd = d2;
-                            a = k;
+                    for (int w = 0; w < NW; ++w) {
+                        for (uint32_t m = chg[w]; m; m &= m - 1u) {   // ascending window index
+                            const int k = w * 32 + __ffs(m) - 1;
+                            const float4 cc = lds_f4(&win[(k / S) * RW + (k % S)]);
+                            const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
+                            if (d2 < bd || (d2 == bd && k < a)) {
+                                bd = d2;
+                                a = k;
+                            }
                         }
                     }
                     if (a != a0 || redo_b) want = a;
@@ -2145,17 +2158,18 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
         float vr = cb0.x - ir, vg = cb0.y - ig, vb = cb0.z - ib;
         float bkey = b_key(sb, dist2(vr, vg, vb), vr, vg, vb);
 #pragma unroll
-        for (int t = 0; t < kMaxChg; ++t) {
-            if (t >= nchg) break;
-            const int k = chg[t];
-            const float4 cc = lds_f4(&win[(k / S) * RW + (k % S)]);
-            vr = cc.x - ir;
-            vg = cc.y - ig;
-            vb = cc.z - ib;
-            const float key = b_key(sb, dist2(vr, vg, vb), vr, vg, vb);
-            if (key < bkey || (key == bkey && k < b)) {
-                bkey = key;
-                b = k;
+        for (int w = 0; w < NW; ++w) {
+            for (uint32_t m = chg[w]; m; m &= m - 1u) {   // ascending window index
+                const int k = w * 32 + __ffs(m) - 1;
+                const float4 cc = lds_f4(&win[(k / S) * RW + (k % S)]);
+                vr = cc.x - ir;
+                vg = cc.y - ig;
+                vb = cc.z - ib;
+                const float key = b_key(sb, dist2(vr, vg, vb), vr, vg, vb);
+                if (key < bkey || (key == bkey && k < b)) {
+                    bkey = key;
+                    b = k;
+                }
             }
         }
         SearchOut o;
@@ -2168,10 +2182,16 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
     }
 }
 
-// One queued full search (entry from fast_block_pass), by a team of kTeam consecutive lanes: each
-// lane scans every kTeam-th window candidate and the team reduces (value, k) lexicographically,
-// which is exactly the first minimum the sequential scan finds (values compare exactly).
+// Queued full searches (entries from fast_block_pass). Up to kTeamMax entries (one round of the
+// CTA): a team of kTeam consecutive lanes per entry, each lane scanning every kTeam-th window
+// candidate; the team reduces (value, k) lexicographically, which is exactly the first minimum the
+// sequential scan finds (values compare exactly). More entries: one thread per two entries, which
+// run as one packed two-pixel search (search_pair_f4) when they lie in one block (they share the
+// window), else one after the other (search_pixel). An entry whose a is known is searched in full
+// as well: step 1 finds the same a (it was determined exactly), so the results are those of the
+// scalar search either way.
 constexpr int kTeam = 4;
+constexpr int kTeamMax = kTrialThreads / kTeam;
 
 __device__ __forceinline__ void team_min(float& v, int& k, unsigned mask) {
 #pragma unroll
@@ -2185,44 +2205,58 @@ __device__ __forceinline__ void team_min(float& v, int& k, unsigned mask) {
     }
 }
 
+__device__ __forceinline__ void full_put(FastSmem& F, int K, int pix, const SearchOut& o,
+                                         long long& acc) {
+    F.rcode[pix] = (uint16_t)(o.ka * K + o.kb);
+    F.rw[pix] = o.omega;
+    F.rerr[pix] = o.err;
+    acc += to_fixed(o.err);
+}
+
+__device__ __forceinline__ void full_colour(const FastSmem& F, int pix, float& ir, float& ig,
+                                            float& ib) {
+    const uint32_t rgb = F.hrpx[pix];
+    ir = (float)(rgb & 255u);
+    ig = (float)((rgb >> 8) & 255u);
+    ib = (float)(rgb >> 16);
+}
+
+template <int S>
+__device__ __forceinline__ const float4* full_window(const JImg& I, const FastSmem& F, int RW,
+                                                     int RV0, int RU0, int bi, uint32_t& rm,
+                                                     uint32_t& cm) {
+    constexpr int r = (S - 1) / 2;
+    const int c = F.blocks[bi];
+    const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+    window_masks(bv, bu, I.h, I.w, S, rm, cm);
+    return &F.region[(bv - r - RV0) * RW + (bu - r - RU0)];
+}
+
+// One entry by a team (scalar arithmetic).
 template <int S>
 __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, FastSmem& F, int RW,
                                               int RV0, int RU0, int e, int tl, unsigned mask,
-                                              long long& e1) {
-    constexpr int r = (S - 1) / 2, K = S * S;
-    const int pix = e & 0xFFF, bi = (e >> 12) & 0xFF, a_known = (e >> 20) - 1;
-    const int c = F.blocks[bi];
-    const int bv = RV0 + c / RW, bu = RU0 + c % RW;
+                                              long long& acc) {
+    constexpr int K = S * S;
+    const int pix = e & 0xFFF, bi = (e >> 12) & 0xFF;
     uint32_t rm, cm;
-    window_masks(bv, bu, I.h, I.w, S, rm, cm);
-    const float4* win = &F.region[(bv - r - RV0) * RW + (bu - r - RU0)];
-    const uint32_t rgb = F.hrpx[pix];
-    const float ir = (float)(rgb & 255u), ig = (float)((rgb >> 8) & 255u), ib = (float)(rgb >> 16);
-    // step 1 (unless the entry carries a): the nearest colour, ties to the lowest k
-    int a = a_known;
-    float d2a;
-    if (a < 0) {
-        float bd = kInf;
-        int ba = K;
-        for (int k = tl; k < K; k += kTeam) {
-            const int dy = k / S, dx = k % S;
-            if (!((rm >> dy) & (cm >> dx) & 1u)) continue;
-            const float4 cc = lds_f4(&win[dy * RW + dx]);
-            const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
-            if (d2 < bd) {
-                bd = d2;
-                ba = k;
-            }
+    const float4* win = full_window<S>(I, F, RW, RV0, RU0, bi, rm, cm);
+    float ir, ig, ib;
+    full_colour(F, pix, ir, ig, ib);
+    float bd = kInf;
+    int a = K;
+    for (int k = tl; k < K; k += kTeam) {
+        const int dy = k / S, dx = k % S;
+        if (!((rm >> dy) & (cm >> dx) & 1u)) continue;
+        const float4 cc = lds_f4(&win[dy * RW + dx]);
+        const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
+        if (d2 < bd) {
+            bd = d2;
+            a = k;
         }
-        team_min(bd, ba, mask);
-        a = ba;
-        d2a = bd;
-    } else {
-        const float4 ca = lds_f4(&win[(a / S) * RW + (a % S)]);
-        d2a = dist2(ca.x - ir, ca.y - ig, ca.z - ib);
     }
-    // step 2: b minimising the key, ties to the lowest k
-    const StepB sb = step_b_setup(lds_f4(&win[(a / S) * RW + (a % S)]), d2a, ir, ig, ib, B.eps255);
+    team_min(bd, a, mask);
+    const StepB sb = step_b_setup(lds_f4(&win[(a / S) * RW + (a % S)]), bd, ir, ig, ib, B.eps255);
     float bkey = kInf;
     int b = K;
     for (int k = tl; k < K; k += kTeam) {
@@ -2241,11 +2275,38 @@ __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, Fa
         SearchOut o;
         o.ka = a;
         finish_pair(win, RW, S, b, ir, ig, ib, sb.dae, bkey, o);
-        F.rcode[pix] = (uint16_t)(o.ka * K + o.kb);
-        F.rw[pix] = o.omega;
-        F.rerr[pix] = o.err;
-        e1 += to_fixed(o.err);
+        full_put(F, K, pix, o, acc);
     }
+}
+
+// Two entries by one thread (packed when they share the block).
+template <int S>
+__device__ __noinline__ void fast_full_pair(const JBatch& B, const JImg& I, FastSmem& F, int RW,
+                                            int RV0, int RU0, int e0, int e1, long long& acc) {
+    constexpr int K = S * S;
+    const int pix0 = e0 & 0xFFF, bi0 = (e0 >> 12) & 0xFF;
+    const int pix1 = e1 & 0xFFF, bi1 = e1 >= 0 ? (e1 >> 12) & 0xFF : -1;
+    uint32_t rm, cm;
+    const float4* win = full_window<S>(I, F, RW, RV0, RU0, bi0, rm, cm);
+    float ir0, ig0, ib0;
+    full_colour(F, pix0, ir0, ig0, ib0);
+    if (bi1 == bi0) {
+        float ir1, ig1, ib1;
+        full_colour(F, pix1, ir1, ig1, ib1);
+        SearchOut o0, o1;
+        search_pair_f4<S>(win, RW, rm, cm, ir0, ig0, ib0, ir1, ig1, ib1, B.eps255, o0, o1);
+        full_put(F, K, pix0, o0, acc);
+        full_put(F, K, pix1, o1, acc);
+        return;
+    }
+    full_put(F, K, pix0, search_pixel<S, true>(win, RW, rm, cm, ir0, ig0, ib0, B.eps255, false),
+             acc);
+    if (e1 < 0) return;
+    win = full_window<S>(I, F, RW, RV0, RU0, bi1, rm, cm);
+    float ir1, ig1, ib1;
+    full_colour(F, pix1, ir1, ig1, ib1);
+    full_put(F, K, pix1, search_pixel<S, true>(win, RW, rm, cm, ir1, ig1, ib1, B.eps255, false),
+             acc);
 }
 
 constexpr int kSuccCache = 32;   // successors of a one-CTA trial's component staged for its commit
@@ -2439,6 +2500,7 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
     if (tid == 0) F.nfull = 0;
     __syncthreads();
     long long acc1 = 0;
+    GLU_WSTAMP(X.it, j, 0);
     for (int bi = warp; bi < na; bi += nwarps) {
         switch (I.S) {
             case 1: fast_block_pass<1>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr, acc1); break;
@@ -2448,13 +2510,15 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
             default: fast_block_pass<9>(B, W_, I, F, RW, RV0, RU0, bi, comp, incr, acc1); break;
         }
     }
+    GLU_WSTAMP(X.it, j, 1);
     __syncthreads();
     const int nfull = F.nfull;
     GLU_TRACE(X.it, j, 7);
 #ifdef GLU_TRIAL_TRACE
     if (tid == 0 && j < kTraceMax) g_trace[X.it][j][9] = (unsigned long long)nfull;
 #endif
-    {
+    GLU_WSTAMP(X.it, j, 2);
+    if (nfull <= kTeamMax) {   // CTA-uniform choice (see fast_full_search)
         const int tl = tid % kTeam;
         const unsigned mask = ((1u << kTeam) - 1u) << ((tid & 31) - tl);
         for (int t = tid / kTeam; t < nfull; t += nthr / kTeam) {
@@ -2467,7 +2531,21 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
                 default: fast_full_search<9>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
             }
         }
+    } else {
+        for (int t = tid; 2 * t < nfull; t += nthr) {
+            const int e0 = F.full[2 * t], e1 = 2 * t + 1 < nfull ? F.full[2 * t + 1] : -1;
+            switch (I.S) {
+                case 1: fast_full_pair<1>(B, I, F, RW, RV0, RU0, e0, e1, acc1); break;
+                case 3: fast_full_pair<3>(B, I, F, RW, RV0, RU0, e0, e1, acc1); break;
+                case 5: fast_full_pair<5>(B, I, F, RW, RV0, RU0, e0, e1, acc1); break;
+                case 7: fast_full_pair<7>(B, I, F, RW, RV0, RU0, e0, e1, acc1); break;
+                default: fast_full_pair<9>(B, I, F, RW, RV0, RU0, e0, e1, acc1); break;
+            }
+        }
     }
+    GLU_WSTAMP(X.it, j, 3);
+    GLU_WVAL(X.it, j, 4, na);
+    GLU_WVAL(X.it, j, 5, nfull);
     {
         const long long w1 = warp_sum_ll(acc1);
         if ((tid & 31) == 0 && w1) atomicAdd(&sh.e1, (unsigned long long)w1);
@@ -3337,6 +3415,11 @@ extern "C" int glu_dbg_trace(unsigned long long* host, int64_t n) {
     const size_t bytes = sizeof(unsigned long long) * (size_t)n;
     if (bytes > sizeof(glu::g_trace)) return GLU_ERR_INVALID_ARG;
     return cudaMemcpyFromSymbol(host, glu::g_trace, bytes) == cudaSuccess ? GLU_OK : GLU_ERR_CUDA;
+}
+
+extern "C" int glu_dbg_wtrace(unsigned long long* host) {
+    return cudaMemcpyFromSymbol(host, glu::g_wtrace, sizeof(glu::g_wtrace)) == cudaSuccess
+               ? GLU_OK : GLU_ERR_CUDA;
 }
 
 extern "C" int glu_dbg_small_times(unsigned long long* host) {

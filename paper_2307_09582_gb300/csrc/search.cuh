@@ -215,17 +215,16 @@ __device__ __forceinline__ void lds_dup(const float4* rg, const float2* bb, f32x
                  : "r"((uint32_t)__cvta_generic_to_shared(bb)));
 }
 
-// Algorithm 1 for two pixels (colours (ir0, ig0, ib0) and (ir1, ig1, ib1)) with the same window:
-// win (float4 copy, used for the chosen pairs), rg / bb (duplicated copy) indexed alike. Results
-// equal search_pixel's for each pixel, bit for bit.
-template <int S, bool kCompact = false, bool kInterior = false>
-__device__ __forceinline__ void search_pair(const float4* __restrict__ win,
-                                            const float4* __restrict__ rg,
-                                            const float2* __restrict__ bb, int rs,
-                                            uint32_t rowmask, uint32_t colmask, float ir0,
-                                            float ig0, float ib0, float ir1, float ig1,
-                                            float ib1, float eps255, bool gnu, SearchOut& o0,
-                                            SearchOut& o1) {
+// Algorithm 1 for two pixels (colours (ir0, ig0, ib0) and (ir1, ig1, ib1)) with the same window.
+// win: the float4 copy (used for the chosen pairs); cand(idx, r2, g2, b2) delivers window cell
+// idx (= dy * rs + dx) as three packed (c, c) operands. Results equal search_pixel's for each
+// pixel, bit for bit.
+template <int S, bool kCompact, bool kInterior, typename Cand>
+__device__ __forceinline__ void search_pair_impl(const float4* __restrict__ win, Cand cand,
+                                                 int rs, uint32_t rowmask, uint32_t colmask,
+                                                 float ir0, float ig0, float ib0, float ir1,
+                                                 float ig1, float ib1, float eps255, bool gnu,
+                                                 SearchOut& o0, SearchOut& o1) {
     constexpr int kRowUnroll = (kCompact || S > 5) ? 1 : S;
     const f32x2 ir = pack2(ir0, ir1), ig = pack2(ig0, ig1), ib = pack2(ib0, ib1);
     // step 1: the nearest colour of each pixel (exact for uint8 colours), ties to the lowest k
@@ -237,7 +236,7 @@ __device__ __forceinline__ void search_pair(const float4* __restrict__ win,
         for (int dx = 0; dx < S; ++dx) {
             const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
             f32x2 cr, cg, cb;
-            lds_dup(&rg[dy * rs + dx], &bb[dy * rs + dx], cr, cg, cb);
+            cand(dy * rs + dx, cr, cg, cb);
             float d0, d1;
             unpack2(dist2x2(sub2(cr, ir), sub2(cg, ig), sub2(cb, ib)), d0, d1);
             const int k = dy * S + dx;
@@ -275,7 +274,7 @@ __device__ __forceinline__ void search_pair(const float4* __restrict__ win,
         for (int dx = 0; dx < S; ++dx) {
             const bool ok = kInterior || ((rowmask >> dy) & (colmask >> dx) & 1u) != 0u;
             f32x2 cr, cg, cb;
-            lds_dup(&rg[dy * rs + dx], &bb[dy * rs + dx], cr, cg, cb);
+            cand(dy * rs + dx, cr, cg, cb);
             const f32x2 vr = sub2(cr, ir), vg = sub2(cg, ig), vb = sub2(cb, ib);
             float q0, q1;
             unpack2(dist2x2(vr, vg, vb), q0, q1);
@@ -303,6 +302,39 @@ __device__ __forceinline__ void search_pair(const float4* __restrict__ win,
     o1.ka = a1;
     finish_pair(win, rs, S, b0, ir0, ig0, ib0, dae0, bkey0, o0);
     finish_pair(win, rs, S, b1, ir1, ig1, ib1, dae1, bkey1, o1);
+}
+
+// With the duplicated window copy: rg / bb indexed like win.
+template <int S, bool kCompact = false, bool kInterior = false>
+__device__ __forceinline__ void search_pair(const float4* __restrict__ win,
+                                            const float4* __restrict__ rg,
+                                            const float2* __restrict__ bb, int rs,
+                                            uint32_t rowmask, uint32_t colmask, float ir0,
+                                            float ig0, float ib0, float ir1, float ig1,
+                                            float ib1, float eps255, bool gnu, SearchOut& o0,
+                                            SearchOut& o1) {
+    auto cand = [&](int idx, f32x2& r2, f32x2& g2, f32x2& b2) {
+        lds_dup(&rg[idx], &bb[idx], r2, g2, b2);
+    };
+    search_pair_impl<S, kCompact, kInterior>(win, cand, rs, rowmask, colmask, ir0, ig0, ib0, ir1,
+                                             ig1, ib1, eps255, gnu, o0, o1);
+}
+
+// With the float4 window only: each candidate's channels are broadcast into packed pairs.
+template <int S>
+__device__ __forceinline__ void search_pair_f4(const float4* __restrict__ win, int rs,
+                                               uint32_t rowmask, uint32_t colmask, float ir0,
+                                               float ig0, float ib0, float ir1, float ig1,
+                                               float ib1, float eps255, SearchOut& o0,
+                                               SearchOut& o1) {
+    auto cand = [&](int idx, f32x2& r2, f32x2& g2, f32x2& b2) {
+        const float4 c = lds_f4(&win[idx]);
+        r2 = pack2(c.x, c.x);
+        g2 = pack2(c.y, c.y);
+        b2 = pack2(c.z, c.z);
+    };
+    search_pair_impl<S, true, false>(win, cand, rs, rowmask, colmask, ir0, ig0, ib0, ir1, ig1,
+                                     ib1, eps255, false, o0, o1);
 }
 
 // Row/column validity masks of the window centred on LR block (py, px) of an h x w LR image.

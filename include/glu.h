@@ -97,6 +97,12 @@ typedef struct {
     int32_t rolled_back[GLU_MAX_ITERS];  /* trials undone (e1 > e0) */
     double residual[GLU_MAX_ITERS + 1];  /* R_0 .. R_n = sum_p E_p, FP64, fixed-order reduction */
     int64_t searched[GLU_MAX_ITERS];     /* HR pixels re-run through Algorithm 1 by the trials */
+    uint32_t multi_kernel_lists;         /* bit n: iteration n's components and trial dependency
+                                            graph were built by the multi-kernel path (a large-
+                                            error list of more than 4096 pixels or one the single
+                                            CTA could not finish); clear: by one CTA (or nothing
+                                            to build) and, inside a recorded graph, the path's 15
+                                            kernels did not launch (the whole batch; per call) */
 } glu_joint_stats;
 
 /* Fill *p with the paper's parameters: S = 3, eps = 1e-3, tau = 30/255, N = 3, FAST, STRICT,
@@ -206,6 +212,21 @@ int glu_joint_optimize_batched(const glu_batch_item* items, int32_t n, const glu
 size_t glu_joint_batched_workspace_size(const glu_batch_item* items, int32_t n,
                                         const glu_params* params);
 
+/* Workspace bytes of one call of operation `op` for an H x W guide at `scale` with params (S, N):
+ * the same number as that operation's own *_workspace_size query (the adjoint forms for c = 3
+ * channels). 0 for an operation that takes no workspace (downsample, optimize, apply, theta
+ * decode) and for invalid arguments, which the operation itself then reports. */
+typedef enum {
+    GLU_OP_DOWNSAMPLE = 0, GLU_OP_OPTIMIZE = 1, GLU_OP_APPLY = 2, GLU_OP_THETA_DECODE = 3,
+    GLU_OP_JOINT = 4,               /* glu_joint_optimize */
+    GLU_OP_LS_JOINT = 5,            /* glu_ls_joint_optimize */
+    GLU_OP_LS_UPDATE = 6,           /* glu_ls_update */
+    GLU_OP_APPLY_BACKWARD = 7,      /* glu_apply_backward_ws */
+    GLU_OP_APPLY_BACKWARD_PLAN = 8  /* glu_apply_backward_plan's plan buffer */
+} glu_op;
+size_t glu_workspace_size(int32_t op, int32_t H, int32_t W, int32_t scale,
+                          const glu_params* params);
+
 /* Benchmark instrumentation (not part of the method). glu_joint_profile(1) makes later
  * glu_joint_optimize calls record CUDA events on their stream around their phases (calls replayed
  * as a CUDA graph record them as event nodes of the graph; each replay's times are collected
@@ -222,6 +243,15 @@ int glu_joint_profile_read(float* ms, int32_t* calls);
  *  H x W. */
 int glu_apply(const glu_theta* theta, const glu_image* lr_target, glu_image* hr_out,
               void* stream);
+
+/* Theta decoded (Eq. 1's pair of LR pixels and weight, per HR pixel): for HR pixel p = y * W + x
+ * with pair code k_a * S * S + k_b, a[p] = v_a * w + u_a where (v_a, u_a) = (y / s + k_a / S - r,
+ * x / s + k_a % S - r), r = (S - 1) / 2 and w = ceil(W / s), likewise b[p] from k_b, and
+ * w_out[p] the weight as float32. a, b, w_out: DEVICE buffers of H * W elements (row-major),
+ * caller-owned; any of them may be null (not all three). A code that points outside its pixel's
+ * (image-clipped) window writes -1 to a[p] and b[p] and records GLU_ERR_DEVICE_CHECK for
+ * glu_device_status(). Asynchronous on `stream`. */
+int glu_theta_decode(const glu_theta* theta, int32_t* a, int32_t* b, float* w_out, void* stream);
 
 /* Adjoint of Eq. 1 with the pair choice held fixed. For an upstream gradient G (grad_hr,
  * F32, H x W x c):

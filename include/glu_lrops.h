@@ -23,6 +23,13 @@
 extern "C" {
 #endif
 
+/* One LR operator: the 3x3 filter, then saturation, then gamma (each optional). */
+typedef struct {
+    int32_t filter;        /* -1: none, 0: 3x3 box, 1: 3x3 Gaussian [1 2 1]/4 */
+    float saturation;      /* 1 = unchanged */
+    float gamma;           /* 1 = unchanged */
+} glu_lr_op;
+
 /* 3x3 filter with clamped (replicated) edges: op 0 = box (1/9 each), op 1 = Gaussian
  * [1 2 1]/4 x [1 2 1]/4. C = 1..4 channels. X and Y must not alias. */
 int glu_fx_filter3(const float* X, int32_t h, int32_t w, int32_t C, int64_t pitch, float* Y,
@@ -38,14 +45,25 @@ int glu_fx_filter3_u8(const uint8_t* X, int32_t h, int32_t w, int32_t C, int64_t
 int glu_fx_point(const float* X, int32_t h, int32_t w, int64_t pitch, float* Y, int64_t ypitch,
                  float sat, float gamma, void* stream);
 
+/* The operator, then Eq. 1, as one issue: lr_target = f(lr) (lr: U8, read as x / 255, or F32;
+ * 3 channels, ceil(H/s) x ceil(W/s); lr_target: F32, 3 channels, the same size, caller-owned;
+ * it holds f(lr) afterwards), then hr_out = glu_apply(theta, lr_target). One kernel computes the
+ * whole operator per LR pixel (the values glu_fx_filter3(_u8) followed by glu_fx_point give); the
+ * apply is launched as its programmatic dependent, so on the persistent TMA path the codes and
+ * weights of its first tiles load while the operator runs, and it reads lr_target only once the
+ * operator has finished. hr_out is bit-identical to the three separate calls. lr, lr_target and
+ * hr_out must not overlap. */
+int glu_apply_lrop(const glu_theta* theta, const glu_image* lr, const glu_lr_op* op,
+                   glu_image* lr_target, glu_image* hr_out, void* stream);
+
 /* ------------------------------------------------ the benchmark pipeline on host buffers
  *
  * One call runs the whole optimise-then-upsample flow of the method (Sec. 3: Theta from the
  * guide, the operator on the LR image, Eq. 1 back to full resolution) with the guide and the
  * result in HOST memory: the guide hr_host (H x W x 3 uint8, rows W * 3 bytes apart) is copied
  * to the device; Algorithm 2 (params: FAST mode, window S, N iterations) optimises the LR image
- * and Theta (unorm16 weights) at scale `scale`; the LR operator glu_fx_filter3_u8 (op) then
- * glu_fx_point (sat, gamma) turns the optimised LR image into T; Eq. 1 (glu_apply) upsamples T;
+ * and Theta (unorm16 weights) at scale `scale`; the LR operator (3x3 filter op, then sat and
+ * gamma) turns the optimised LR image into T and Eq. 1 upsamples T (glu_apply_lrop);
  * the H x W x 3 float32 result is copied to out_host (rows W * 3 floats apart). Host buffers in
  * pinned (page-locked) memory give the copies full bandwidth; pageable memory works, slower.
  *

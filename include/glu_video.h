@@ -34,6 +34,7 @@
 #include <stdint.h>
 
 #include "glu.h"
+#include "glu_lrops.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -41,13 +42,6 @@ extern "C" {
 
 #define GLU_VIDEO_MAX_SLOTS 256
 #define GLU_VIDEO_MAX_OPS 4
-
-/* One LR operator of the pipeline (a stand-in for the image operator f, see glu_lrops.h). */
-typedef struct {
-    int32_t filter;        /* -1: none, 0: 3x3 box, 1: 3x3 Gaussian [1 2 1]/4 */
-    float saturation;      /* 1 = unchanged */
-    float gamma;           /* 1 = unchanged */
-} glu_lr_op;
 
 typedef struct {
     int32_t H, W;          /* frame size */
@@ -57,7 +51,7 @@ typedef struct {
     glu_params params;     /* S, eps, mode (FAST or GNU) for Algorithm 1 */
     int32_t wfmt;          /* weight storage of Theta */
     int32_t n_ops;         /* 1 .. GLU_VIDEO_MAX_OPS operators sharing the frame's Theta */
-    glu_lr_op ops[GLU_VIDEO_MAX_OPS];   /* operator k: target T_k, output k */
+    glu_lr_op ops[GLU_VIDEO_MAX_OPS];   /* operator k (glu_lrops.h): target T_k, output k */
     int32_t overlap;       /* 1: each operator runs on a forked stream beside Algorithm 1 */
 } glu_video_desc;
 

@@ -25,6 +25,8 @@ GLU_MODE_FAST, GLU_MODE_GNU, GLU_MODE_EXACT = 0, 1, 2
 GLU_JOINT_STRICT, GLU_JOINT_PAPER = 0, 1
 GLU_DOWN_GRID, GLU_DOWN_BOX = 0, 1
 GLU_MAX_ITERS = 32
+(GLU_OP_DOWNSAMPLE, GLU_OP_OPTIMIZE, GLU_OP_APPLY, GLU_OP_THETA_DECODE, GLU_OP_JOINT,
+ GLU_OP_LS_JOINT, GLU_OP_LS_UPDATE, GLU_OP_APPLY_BACKWARD, GLU_OP_APPLY_BACKWARD_PLAN) = range(9)
 
 
 class GluImage(ctypes.Structure):
@@ -51,7 +53,8 @@ class GluJointStats(ctypes.Structure):
                 ("accepted", ctypes.c_int32 * GLU_MAX_ITERS),
                 ("rolled_back", ctypes.c_int32 * GLU_MAX_ITERS),
                 ("residual", ctypes.c_double * (GLU_MAX_ITERS + 1)),
-                ("searched", ctypes.c_int64 * GLU_MAX_ITERS)]
+                ("searched", ctypes.c_int64 * GLU_MAX_ITERS),
+                ("multi_kernel_lists", ctypes.c_uint32)]
 
 
 class GluLsStats(ctypes.Structure):
@@ -102,6 +105,8 @@ PROTOTYPES = {
     "glu_joint_batched_workspace_size": (ctypes.c_size_t, [_P(GluBatchItem), _i32,
                                                            _P(GluParams)]),
     "glu_apply": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _vp]),
+    "glu_theta_decode": (ctypes.c_int, [_P(GluTheta), _vp, _vp, _vp, _vp]),
+    "glu_workspace_size": (ctypes.c_size_t, [_i32, _i32, _i32, _i32, _P(GluParams)]),
     "glu_apply_backward": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluImage), _P(GluImage),
                                           _vp, _vp]),
     "glu_apply_backward_workspace_size": (ctypes.c_size_t, [_P(GluTheta), _i32]),
@@ -144,6 +149,8 @@ PROTOTYPES = {
     "glu_version": (ctypes.c_char_p, []),
     "glu_fx_filter3": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _i64, _i32, _vp]),
     "glu_fx_point": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp, _i64, _f, _f, _vp]),
+    "glu_apply_lrop": (ctypes.c_int, [_P(GluTheta), _P(GluImage), _P(GluLrOp), _P(GluImage),
+                                      _P(GluImage), _vp]),
     "glu_fx_filter3_u8": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _i64, _i32, _vp]),
     "glu_pipeline_host_workspace_size": (ctypes.c_size_t, [_i32, _i32, _i32, _P(GluParams)]),
     "glu_pipeline_host": (ctypes.c_int, [_vp, _i32, _i32, _i32, _P(GluParams), _i32, _f, _f,

@@ -201,6 +201,7 @@ def _stats_dict(st: A.GluJointStats, decisions=None) -> dict:
                             residual=st.residual[k + 1], searched=st.searched[k])
                        for k in range(n)],
                 n_large_next=st.n_large[n] if n < A.GLU_MAX_ITERS else 0,
+                multi_kernel_lists=int(st.multi_kernel_lists),
                 decisions=decisions)
 
 
@@ -382,6 +383,25 @@ def glu_apply(theta: Theta, lr_target: torch.Tensor, out: torch.Tensor | None = 
     return out
 
 
+def glu_theta_decode(theta: Theta, stream=None):
+    """Theta as absolute LR pixel indices (a, b: int32 H x W, row-major v * w + u) and float32
+    weights (H x W), decoded on the device."""
+    dev = theta.code.device
+    a = torch.empty((theta.H, theta.W), dtype=torch.int32, device=dev)
+    b = torch.empty_like(a)
+    w = torch.empty((theta.H, theta.W), dtype=torch.float32, device=dev)
+    td = theta.desc()
+    A.check("glu_theta_decode", lib().glu_theta_decode(ctypes.byref(td), a.data_ptr(),
+                                                       b.data_ptr(), w.data_ptr(),
+                                                       _stream(stream)))
+    return a, b, w
+
+
+def glu_workspace_size(op: int, H: int, W: int, scale: int, params: A.GluParams) -> int:
+    """Workspace bytes of operation `op` (A.GLU_OP_*); 0 when it takes none."""
+    return int(lib().glu_workspace_size(op, H, W, scale, ctypes.byref(params)))
+
+
 _BW_WS = {}   # device -> workspace of the adjoint (grown on demand, reused across calls)
 
 
@@ -517,14 +537,19 @@ def glu_joint_profile_read() -> dict:
                 trials_ms=ms[3], residual_ms=ms[4])
 
 
-def joint_launches(N: int) -> int:
-    """Kernel launches one glu_joint_optimize call makes (iterations after convergence still
-    launch and return at once): control init, grid downsample, search, R_0 (2), then per
-    iteration threshold, the large-error list (scan, scatter), merge, flatten, 3 root-compaction,
-    count, 3 scan, fill, 5 for the trials' dependency graph (all of which return at once when
-    the one-CTA list kernel, also launched, did their work), trials and the residual update (the
-    kept trials add their differences; one launch records R_n and the stop rule)."""
-    return 5 + 21 * N
+def joint_launches(N: int, graph: bool = False, multi_kernel_lists: int = 0) -> int:
+    """Kernel launches one glu_joint_optimize call makes: control init, grid downsample, search
+    and R_0 (2), then per iteration the threshold pass with its ordered list, the one-CTA list
+    kernel, the multi-kernel list path (merge, flatten, root count, scan, root scatter, component
+    count, 3 scan, fill, dependency graph 5: 15 kernels), the trials, the list clear and the
+    residual update. Issued directly, every kernel launches (those with nothing to do return at
+    once). Replayed as a recorded graph (a repeated call), the 15 kernels of the multi-kernel
+    path sit in a conditional node and launch only in the iterations whose bit is set in the
+    stats' multi_kernel_lists."""
+    if not graph:
+        return 5 + 20 * N
+    multi = bin(multi_kernel_lists & ((1 << N) - 1)).count("1")
+    return 5 + 5 * N + 15 * multi
 
 
 def tune_mode(on: bool) -> None:
@@ -622,6 +647,24 @@ def glu_fx_point(x: torch.Tensor, sat: float = 1.0, gamma: float = 1.0,
     A.check("glu_fx_point", lib().glu_fx_point(_ptr(x), h, w, x.stride(0), _ptr(out),
                                                out.stride(0), sat, gamma, _stream(stream)))
     return out
+
+
+def glu_apply_lrop(theta: Theta, lr: torch.Tensor, filter: int = 0, sat: float = 1.0,
+                   gamma: float = 1.0, target: torch.Tensor | None = None,
+                   out: torch.Tensor | None = None, out_dtype=torch.float32, stream=None):
+    """The LR operator (3x3 filter -1/0/1, then saturation and gamma) on lr (uint8 or float32),
+    then Eq. 1, as one issue. Returns (out, target); target holds f(lr)."""
+    h, w, _ = lr.shape
+    if target is None:
+        target = torch.empty((h, w, 3), dtype=torch.float32, device=lr.device)
+    if out is None:
+        out = torch.empty((theta.H, theta.W, 3), dtype=out_dtype, device=lr.device)
+    td, li, ti, oi = theta.desc(), image(lr), image(target), image(out)
+    op = A.GluLrOp(filter, sat, gamma)
+    A.check("glu_apply_lrop", lib().glu_apply_lrop(ctypes.byref(td), ctypes.byref(li),
+                                                   ctypes.byref(op), ctypes.byref(ti),
+                                                   ctypes.byref(oi), _stream(stream)))
+    return out, target
 
 
 class GluApplyFn(torch.autograd.Function):

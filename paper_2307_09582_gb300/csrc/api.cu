@@ -2,6 +2,7 @@
 #include <string.h>
 
 #include "internal.h"
+#include "glu_lrops.h"
 
 using namespace glu;
 
@@ -192,6 +193,45 @@ int glu_apply(const glu_theta* theta, const glu_image* lr_target, glu_image* hr_
     return launch_apply(a, (cudaStream_t)stream);
 }
 
+int glu_apply_lrop(const glu_theta* theta, const glu_image* lr, const glu_lr_op* op,
+                   glu_image* lr_target, glu_image* hr_out, void* stream) {
+    if (!theta_ok(theta) || !image_ok(lr) || !image_ok(lr_target) || !image_ok(hr_out) || !op)
+        return GLU_ERR_INVALID_ARG;
+    if ((lr->dtype != GLU_U8 && lr->dtype != GLU_F32) || lr_target->dtype != GLU_F32 ||
+        hr_out->dtype == GLU_U8 || lr->c != 3 || lr_target->c != 3 || hr_out->c != 3)
+        return GLU_ERR_UNSUPPORTED;
+    if (op->filter < -1 || op->filter > 1 || !(op->saturation >= 0.f) || !(op->gamma > 0.f))
+        return GLU_ERR_INVALID_ARG;
+    const int s = theta->scale, h = lr_dim(theta->H, s), w = lr_dim(theta->W, s);
+    if (hr_out->h != theta->H || hr_out->w != theta->W || lr->h != h || lr->w != w ||
+        lr_target->h != h || lr_target->w != w)
+        return GLU_ERR_SHAPE;
+    if (lr->data == lr_target->data) return GLU_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = launch_lr_op(lr->data, lr->dtype, h, w, lr->pitch, (float*)lr_target->data,
+                          lr_target->pitch, op->filter, op->saturation, op->gamma, st);
+    if (rc) return rc;
+    ApplyArgs a;
+    a.code = theta->code;
+    a.weight = theta->weight;
+    a.wfmt = theta->wfmt;
+    a.H = theta->H;
+    a.W = theta->W;
+    a.s = s;
+    a.S = theta->S;
+    a.h = h;
+    a.w = w;
+    a.C = 3;
+    a.T = lr_target->data;
+    a.T_pitch = lr_target->pitch;
+    a.T_dtype = GLU_F32;
+    a.out = hr_out->data;
+    a.out_pitch = hr_out->pitch;
+    a.out_dtype = hr_out->dtype;
+    a.pdl = 1;
+    return launch_apply(a, st);
+}
+
 }  // extern "C"
 
 namespace {
@@ -373,6 +413,31 @@ int glu_apply_backward_ws(const glu_theta* theta, const glu_image* lr_target,
         ws_bytes < apply_backward_workspace_bytes(a.h, a.w, a.S, a.C))
         return GLU_ERR_WORKSPACE;
     return launch_apply_backward_ws(a, ws, (cudaStream_t)stream);
+}
+
+int glu_theta_decode(const glu_theta* theta, int32_t* a, int32_t* b, float* w, void* stream) {
+    if (!theta_ok(theta) || (!a && !b && !w)) return GLU_ERR_INVALID_ARG;
+    if ((int64_t)lr_dim(theta->H, theta->scale) * lr_dim(theta->W, theta->scale) >
+        (int64_t)INT32_MAX)
+        return GLU_ERR_SHAPE;
+    return launch_theta_decode(theta->code, theta->weight, theta->wfmt, theta->H, theta->W,
+                               theta->scale, theta->S, a, b, w, (cudaStream_t)stream);
+}
+
+size_t glu_workspace_size(int32_t op, int32_t H, int32_t W, int32_t scale,
+                          const glu_params* params) {
+    if (H <= 0 || W <= 0 || H >= (1 << 22) || scale < 1 || !params_ok(params)) return 0;
+    const int h = lr_dim(H, scale), w = lr_dim(W, scale);
+    switch (op) {
+        case GLU_OP_JOINT: return joint_workspace_bytes(H, W, scale, params->S, params->N);
+        case GLU_OP_LS_JOINT: return ls_joint_workspace_bytes(H, W, scale, params->S);
+        case GLU_OP_LS_UPDATE: return ls_update_workspace_bytes(h, w, params->S);
+        case GLU_OP_APPLY_BACKWARD: return apply_backward_workspace_bytes(h, w, params->S, 3);
+        case GLU_OP_APPLY_BACKWARD_PLAN:
+            if ((int64_t)H * W >= ((int64_t)1 << 30)) return 0;
+            return apply_backward_plan_bytes((int64_t)H * W, (int64_t)h * w, params->S);
+        default: return 0;
+    }
 }
 
 size_t glu_joint_workspace_size(int32_t H, int32_t W, int32_t scale, const glu_params* params) {

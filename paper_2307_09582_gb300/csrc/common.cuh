@@ -160,6 +160,29 @@ __device__ __forceinline__ void tma_store_commit_wait_read() {
     asm volatile("cp.async.bulk.commit_group;\n\tcp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+// 4-byte asynchronous global -> shared copy (LDGSTS), completed by cp_async_wait_all().
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream serialisation may
+// start before the preceding kernel of its stream has finished; griddep_wait() blocks until that
+// kernel has completed and its writes are visible (a no-op in a kernel launched without the
+// attribute). griddep_launch_dependents() lets the dependent kernel start early.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace glu
 
 // ------------------------------------------------------------------------ host helpers

@@ -52,9 +52,18 @@ struct ApplyArgs {
     void* out;
     int64_t out_pitch;
     int out_dtype;
+    int pdl = 0;   // 1: the preceding kernel of the stream writes T and triggers its dependents
+                   // (the persistent pipeline starts loading codes and weights before it ends)
 };
 
 int launch_apply(const ApplyArgs& a, cudaStream_t st);
+// The LR operator f (3x3 filter, then saturation and gamma) of a uint8 or float32 3-channel LR
+// image into a float32 image T, one thread per LR pixel; the kernel lets a programmatic
+// dependent launch start at once (its dependent waits for it before reading T).
+int launch_lr_op(const void* X, int x_dtype, int h, int w, int64_t pitch, float* Y, int64_t ypitch,
+                 int filter, float sat, float gamma, cudaStream_t st);
+int launch_theta_decode(const uint16_t* code, const void* weight, int wfmt, int H, int W, int s,
+                        int S, int32_t* a, int32_t* b, float* wt, cudaStream_t st);
 
 struct BackwardArgs {
     const uint16_t* code;

@@ -48,6 +48,30 @@ __device__ __forceinline__ int64_t lr_off(int y, int x, int k, int s, int S, int
     return (int64_t)v * pitch + (int64_t)u * C;
 }
 
+// Theta decoded into absolute LR pixel indices (row-major, v * w + u) of a and b and float32
+// weights, one thread per HR pixel. A code outside the window of its pixel writes -1 for both
+// indices and records GLU_ERR_DEVICE_CHECK.
+__global__ void k_theta_decode(const uint16_t* __restrict__ code, const void* weight, int wfmt,
+                               int H, int W, int s, int S, int h, int w, int32_t* a, int32_t* b,
+                               float* wt) {
+    const int64_t np = (int64_t)H * W;
+    const int K = S * S, r = (S - 1) >> 1;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(p / W), x = (int)(p % W);
+        const int c = code[p];
+        const int ka = c / K, kb = c % K;
+        const int va = y / s + ka / S - r, ua = x / s + ka % S - r;
+        const int vb = y / s + kb / S - r, ub = x / s + kb % S - r;
+        const bool ok = ka < K && va >= 0 && va < h && ua >= 0 && ua < w && vb >= 0 && vb < h &&
+                        ub >= 0 && ub < w;
+        if (!ok) set_status(GLU_ERR_DEVICE_CHECK);
+        if (a) a[p] = ok ? va * w + ua : -1;
+        if (b) b[p] = ok ? vb * w + ub : -1;
+        if (wt) wt[p] = load_weight(weight, wfmt, p);
+    }
+}
+
 template <int C>
 __global__ void k_apply(const ApplyArgs P) {
     const int64_t groups_per_row = (P.W + 3) / 4;
@@ -467,17 +491,65 @@ static int grid_for(int64_t work, int threads) {
     return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
 }
 
+int launch_theta_decode(const uint16_t* code, const void* weight, int wfmt, int H, int W, int s,
+                        int S, int32_t* a, int32_t* b, float* wt, cudaStream_t st) {
+    const int64_t np = (int64_t)H * W;
+    if (np == 0) return GLU_OK;
+    const int threads = 256;
+    k_theta_decode<<<grid_for(np, threads), threads, 0, st>>>(
+        code, weight, wfmt, H, W, s, S, (H + s - 1) / s, (W + s - 1) / s, a, b, wt);
+    GLU_LAUNCH_CHECK();
+    return GLU_OK;
+}
+
+// The LR region of a tile copied into float4 cells (RGB_) by 4-byte asynchronous copies, one
+// commit group per call (clamped to the image: cells outside it are never selected by a valid
+// code); completed by cp_async_wait_all() and a barrier.
+__device__ __forceinline__ void prefetch_region(const ApplyArgs& P, float4* reg4, int RH, int RW,
+                                                int v0, int u0) {
+    const float* T = (const float*)P.T;
+    const float invRW = 1.0f / (float)RW;
+    for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
+        const int rr = qdiv(i, invRW), c1 = i - rr * RW;
+        const int v = min(max(v0 + rr, 0), P.h - 1);
+        const int u = min(max(u0 + c1, 0), P.w - 1);
+        const float* t = T + (int64_t)v * P.T_pitch + (int64_t)u * 3;
+        float* d = reinterpret_cast<float*>(reg4 + i);
+        cp_async4(d, t);
+        cp_async4(d + 1, t + 1);
+        cp_async4(d + 2, t + 2);
+    }
+    cp_async_commit();
+}
+
+// The pair-code table of a region of width RW (see stage_region_table).
+__device__ __forceinline__ void build_pair_table(uint32_t* tab, int RW, int S) {
+    const int K = S * S, K2 = K * K;
+    const float invK = 1.0f / (float)K, invS = 1.0f / (float)S;
+    for (int c = threadIdx.x; c < K2; c += blockDim.x) {
+        const int ka = qdiv(c, invK), kb = c - ka * K;
+        const int ra = qdiv(ka, invS), rb = qdiv(kb, invS);
+        const uint32_t oa = (uint32_t)(ra * RW + (ka - ra * S));
+        const uint32_t ob = (uint32_t)(rb * RW + (kb - rb * S));
+        tab[c] = oa | (ob << 16);
+    }
+}
+
 // Persistent form of k_apply3_tma: a CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x,
 // ... with the codes and weights of the next two tiles in flight (two TMA stages, one mbarrier
-// each) and the output of the previous tile still being written by its TMA store (two output
-// buffers) while it computes the current one; only the LR region is staged synchronously (it
-// comes from L2). Same arithmetic as k_apply3_tile.
+// each), the output of the previous tile still being written by its TMA store (two output
+// buffers) while it computes the current one, and (nreg = 2) the next tile's LR region arriving
+// by asynchronous copies into a second region buffer (each with its own pair-code table) while
+// the current one is computed; with nreg = 1 (a region too large for two buffers) the region is
+// refilled between tiles. The LR target is first read after griddep_wait(), so the kernel may be
+// launched as the programmatic dependent of the kernel that writes the target: the codes and
+// weights of its first tiles are then already loading. Same arithmetic as k_apply3_tile.
 template <int WF, typename OT, int TH>
 __global__ void __launch_bounds__(256) k_apply3_pipe(const ApplyArgs P,
                                                      const __grid_constant__ CUtensorMap mcode,
                                                      const __grid_constant__ CUtensorMap mw,
                                                      const __grid_constant__ CUtensorMap mout,
-                                                     int tiles_x, int ntiles) {
+                                                     int tiles_x, int ntiles, int nreg) {
     constexpr int NW = 8, RPW = TH / NW;
     constexpr int WB = WF == GLU_W_F32 ? 4 : 2;
     constexpr int HALF = kApplyTW / 2 * 3;
@@ -489,15 +561,31 @@ __global__ void __launch_bounds__(256) k_apply3_pipe(const ApplyArgs P,
     unsigned char* sin = sm;                                         // [2][IN_BYTES]
     OT* sout = (OT*)(sm + 2 * IN_BYTES);                             // [2][OUT_BYTES]
     uint64_t* bar = (uint64_t*)(sm + 2 * IN_BYTES + 2 * OUT_BYTES);  // [2]
-    float4* reg4 = (float4*)(bar + 2);
     const int s = P.s, S = P.S, r = (S - 1) >> 1;
-    uint32_t* tab = (uint32_t*)(reg4 + apply_region_cells(TH, s, S));
+    const int cells = apply_region_cells(TH, s, S), K2 = S * S * S * S;
+    float4* regb = (float4*)(bar + 2);                               // [nreg][cells]
+    uint32_t* tabb = (uint32_t*)(regb + nreg * cells);               // [nreg][K2]
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float inv_s = 1.0f / (float)s;   // exact quotients (qdiv)
     auto issue = [&](int stage, int t) {   // thread 0 only
         const int x0 = (t % tiles_x) * kApplyTW, y0 = (t / tiles_x) * TH;
         mbar_arrive_expect_tx(&bar[stage], (uint32_t)IN_BYTES);
         tma_load_2d(sin + stage * IN_BYTES, &mcode, &bar[stage], x0, y0);
         tma_load_2d(sin + stage * IN_BYTES + TH * kApplyTW * 2, &mw, &bar[stage], x0, y0);
+    };
+    int tab_rw0 = -1, tab_rw1 = -1;   // region width each buffer's table holds offsets for
+    // start the region copy of tile t into buffer b (and its table if the width changed)
+    auto fill = [&](int b, int t) {
+        const int x0 = (t % tiles_x) * kApplyTW, y0 = (t / tiles_x) * TH;
+        const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + TH, P.H);
+        const int v0 = qdiv(y0, inv_s) - r, u0 = qdiv(x0, inv_s) - r;
+        const int RH = qdiv(ye - 1, inv_s) + r - v0 + 1, RW = qdiv(xe - 1, inv_s) + r - u0 + 1;
+        prefetch_region(P, regb + b * cells, RH, RW, v0, u0);
+        int& trw = b ? tab_rw1 : tab_rw0;
+        if (RW != trw) {
+            build_pair_table(tabb + b * K2, RW, S);
+            trw = RW;
+        }
     };
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -506,25 +594,27 @@ __global__ void __launch_bounds__(256) k_apply3_pipe(const ApplyArgs P,
         if (blockIdx.x < ntiles) issue(0, blockIdx.x);
         if (blockIdx.x + gridDim.x < ntiles) issue(1, blockIdx.x + gridDim.x);
     }
-    int i = 0, tab_rw = -1;   // the table holds offsets for region width tab_rw
+    griddep_wait();   // the LR target is complete from here on
+    if (blockIdx.x < ntiles) fill(0, blockIdx.x);
+    int i = 0;
     bool failed = false;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
         const int stage = i & 1;
         const uint32_t phase = (uint32_t)(i >> 1) & 1u;
+        const int rb = nreg == 2 ? stage : 0;
         const int x0 = (t % tiles_x) * kApplyTW, y0 = (t / tiles_x) * TH;
         const int xe = min(x0 + kApplyTW, P.W), ye = min(y0 + TH, P.H);
-        const float inv_s = 1.0f / (float)s;   // exact quotients (qdiv)
         const int v0 = qdiv(y0, inv_s) - r, u0 = qdiv(x0, inv_s) - r;
-        const int RH = qdiv(ye - 1, inv_s) + r - v0 + 1, RW = qdiv(xe - 1, inv_s) + r - u0 + 1;
+        const int RW = qdiv(xe - 1, inv_s) + r - u0 + 1;
         const int xs = x0 + lane * 4;
         const TileGeom g = tile_geom(P, x0, y0, xe, ye, xs, RW, v0, u0);
-        // (the previous tile's readers of the region and table passed the last barrier)
-        stage_region_table(P, reg4, tab, RH, RW, v0, u0, g, RW != tab_rw);
-        tab_rw = RW;
+        cp_async_wait_all();   // this thread's copies of this tile's region have landed
         // this stage's output buffer was last written out two tiles ago: its store must have
         // read it (one younger store group may still be reading the other buffer)
         if (threadIdx.x == 0 && i >= 2) tma_store_wait_read_1();
-        __syncthreads();
+        __syncthreads();   // the region and its table are complete; tile i-1 is finished
+        const int tn = t + gridDim.x;
+        if (nreg == 2 && tn < ntiles) fill(rb ^ 1, tn);   // the next region, while computing
         const bool ok = mbar_wait_bounded(&bar[stage], phase);
         if (__syncthreads_or(ok ? 0 : 1)) {
             failed = true;
@@ -532,6 +622,8 @@ __global__ void __launch_bounds__(256) k_apply3_pipe(const ApplyArgs P,
         }
         const unsigned char* cin = sin + stage * IN_BYTES;
         OT* cout = sout + stage * (OUT_BYTES / (int)sizeof(OT));
+        const float4* reg4 = regb + rb * cells;
+        const uint32_t* tab = tabb + rb * K2;
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
             const int row = wid + k * NW, y = y0 + row;
@@ -556,7 +648,9 @@ __global__ void __launch_bounds__(256) k_apply3_pipe(const ApplyArgs P,
             tma_store_commit();
             if (t + 2 * (int)gridDim.x < ntiles) issue(stage, t + 2 * gridDim.x);
         }
+        if (nreg == 1 && tn < ntiles) fill(0, tn);   // the single buffer is free again
     }
+    cp_async_wait_all();   // no copy of this thread is left in flight
     if (threadIdx.x == 0) {
         if (failed) {
             set_status(GLU_ERR_TIMEOUT);
@@ -637,21 +731,36 @@ int launch_apply(const ApplyArgs& a, cudaStream_t st) {
             if (kApplyVariants[v].tma == 2 && maps_for(th)) {
                 const int tiles_x = (a.W + kApplyTW - 1) / kApplyTW;
                 const int ntiles = tiles_x * ((a.H + th - 1) / th);
-                const size_t smem = 128 + 2 * (size_t)th * kApplyTW * (2 + wb) +
-                                    4 * (size_t)th * (kApplyTW / 2 * 3) * ob + 16 + region;
+                const size_t fixed = 128 + 2 * (size_t)th * kApplyTW * (2 + wb) +
+                                     4 * (size_t)th * (kApplyTW / 2 * 3) * ob + 16;
                 auto launch = [&](auto kern) -> int {
+                    int dev = 0, sms = 148, per_sm = 1, optin = 48 * 1024;
+                    GLU_CUDA_TRY(cudaGetDevice(&dev));
+                    GLU_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                    GLU_CUDA_TRY(cudaDeviceGetAttribute(
+                        &optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+                    // two region buffers when they fit (the next region loads during a tile)
+                    const int nreg = fixed + 2 * region <= (size_t)optin ? 2 : 1;
+                    const size_t smem = fixed + nreg * region;
                     if (smem > 48 * 1024 &&
                         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem) != cudaSuccess)
                         return GLU_ERR_CUDA;
-                    int dev = 0, sms = 148, per_sm = 1;
-                    GLU_CUDA_TRY(cudaGetDevice(&dev));
-                    GLU_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
                     GLU_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256,
                                                                                smem));
                     const int grid = std::max(1, std::min(ntiles, sms * std::max(per_sm, 1)));
-                    kern<<<grid, 256, smem, st>>>(a, mcode, mw, mout, tiles_x, ntiles);
-                    GLU_LAUNCH_CHECK();
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = dim3(grid);
+                    cfg.blockDim = dim3(256);
+                    cfg.dynamicSmemBytes = smem;
+                    cfg.stream = st;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                    attr[0].val.programmaticStreamSerializationAllowed = 1;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = a.pdl ? 1 : 0;
+                    GLU_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a, mcode, mw, mout, tiles_x,
+                                                    ntiles, nreg));
                     return GLU_OK;
                 };
                 return apply_rows_dispatch<PipeK>(th, a.wfmt, vec16, launch);

@@ -92,29 +92,45 @@ int launch_downsample(const glu_image& hr, int s, int mode, const glu_image& lr,
 __device__ __forceinline__ float op_in(float x) { return x; }
 __device__ __forceinline__ float op_in(uint8_t x) { return __fdiv_rn((float)x, 255.0f); }
 
+// Channel c of the 3x3 filter at (v, u): the nine taps in raster order, one FMA each.
+template <typename TX>
+__device__ __forceinline__ float filter3_at(const TX* X, int h, int w, int C, int64_t pitch, int v,
+                                            int u, int c, int op) {
+    const float kg[3] = {0.25f, 0.5f, 0.25f};
+    float acc = 0.f;
+    for (int dv = -1; dv <= 1; ++dv)
+        for (int du = -1; du <= 1; ++du) {
+            const int vv = min(max(v + dv, 0), h - 1), uu = min(max(u + du, 0), w - 1);
+            const float wgt = op == 0 ? (1.0f / 9.0f) : kg[dv + 1] * kg[du + 1];
+            acc = __fmaf_rn(wgt, op_in(X[(int64_t)vv * pitch + (int64_t)uu * C + c]), acc);
+        }
+    return acc;
+}
+
+// Saturation about the Rec. 601 luma (clamped to [0, 1]), then per-channel gamma; either is
+// skipped at 1.
+__device__ __forceinline__ void point_op(float c3[3], float sat, float gamma) {
+    if (sat != 1.0f) {
+        const float l = __fmaf_rn(0.114f, c3[2], __fmaf_rn(0.587f, c3[1], __fmul_rn(0.299f, c3[0])));
+        for (int c = 0; c < 3; ++c) c3[c] = __saturatef(__fmaf_rn(sat, __fsub_rn(c3[c], l), l));
+    }
+    if (gamma != 1.0f)
+        for (int c = 0; c < 3; ++c) c3[c] = c3[c] > 0.f ? powf(c3[c], gamma) : 0.f;
+}
+
 template <typename TX>
 __global__ void k_op_filter3(const TX* X, int h, int w, int C, int64_t pitch, float* Y,
                              int64_t ypitch, int op) {
     const int64_t n = (int64_t)h * w;
-    const float kg[3] = {0.25f, 0.5f, 0.25f};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int v = (int)(i / w), u = (int)(i % w);
-        for (int c = 0; c < C; ++c) {
-            float acc = 0.f;
-            for (int dv = -1; dv <= 1; ++dv)
-                for (int du = -1; du <= 1; ++du) {
-                    const int vv = min(max(v + dv, 0), h - 1), uu = min(max(u + du, 0), w - 1);
-                    const float wgt = op == 0 ? (1.0f / 9.0f) : kg[dv + 1] * kg[du + 1];
-                    acc = __fmaf_rn(wgt, op_in(X[(int64_t)vv * pitch + (int64_t)uu * C + c]), acc);
-                }
-            Y[(int64_t)v * ypitch + (int64_t)u * C + c] = acc;
-        }
+        for (int c = 0; c < C; ++c)
+            Y[(int64_t)v * ypitch + (int64_t)u * C + c] = filter3_at(X, h, w, C, pitch, v, u, c, op);
     }
 }
 
-// pointwise: saturation about Rec. 601 luma (clamped to [0,1]) then per-channel gamma; either
-// can be disabled (sat = 1, gamma = 1). In place allowed.
+// pointwise: saturation then gamma (point_op). In place allowed.
 __global__ void k_op_point(const float* X, int h, int w, int64_t pitch, float* Y, int64_t ypitch,
                            float sat, float gamma) {
     const int64_t n = (int64_t)h * w;
@@ -123,15 +139,44 @@ __global__ void k_op_point(const float* X, int h, int w, int64_t pitch, float* Y
         const int v = (int)(i / w), u = (int)(i % w);
         const float* x = X + (int64_t)v * pitch + (int64_t)u * 3;
         float c3[3] = {x[0], x[1], x[2]};
-        if (sat != 1.0f) {
-            const float l = 0.299f * c3[0] + 0.587f * c3[1] + 0.114f * c3[2];
-            for (int c = 0; c < 3; ++c) c3[c] = __saturatef(l + sat * (c3[c] - l));
-        }
-        if (gamma != 1.0f)
-            for (int c = 0; c < 3; ++c) c3[c] = c3[c] > 0.f ? powf(c3[c], gamma) : 0.f;
+        point_op(c3, sat, gamma);
         float* y = Y + (int64_t)v * ypitch + (int64_t)u * 3;
         for (int c = 0; c < 3; ++c) y[c] = c3[c];
     }
+}
+
+// The whole operator (filter -1: none, else k_op_filter3's op) per 3-channel LR pixel: the same
+// values as k_op_filter3 followed by k_op_point (the intermediate is a float either way).
+template <typename TX>
+__global__ void k_op_lr(const TX* X, int h, int w, int64_t pitch, float* Y, int64_t ypitch,
+                        int filter, float sat, float gamma) {
+    griddep_launch_dependents();   // a dependent apply may start loading codes and weights
+    const int64_t n = (int64_t)h * w;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(i / w), u = (int)(i % w);
+        float c3[3];
+        for (int c = 0; c < 3; ++c)
+            c3[c] = filter < 0 ? op_in(X[(int64_t)v * pitch + (int64_t)u * 3 + c])
+                               : filter3_at(X, h, w, 3, pitch, v, u, c, filter);
+        point_op(c3, sat, gamma);
+        float* y = Y + (int64_t)v * ypitch + (int64_t)u * 3;
+        for (int c = 0; c < 3; ++c) y[c] = c3[c];
+    }
+}
+
+int launch_lr_op(const void* X, int x_dtype, int h, int w, int64_t pitch, float* Y, int64_t ypitch,
+                 int filter, float sat, float gamma, cudaStream_t st) {
+    const int threads = 256;
+    const int grid = grid_for((int64_t)h * w, threads);
+    if (x_dtype == GLU_U8)
+        k_op_lr<<<grid, threads, 0, st>>>((const uint8_t*)X, h, w, pitch, Y, ypitch, filter, sat,
+                                          gamma);
+    else
+        k_op_lr<<<grid, threads, 0, st>>>((const float*)X, h, w, pitch, Y, ypitch, filter, sat,
+                                          gamma);
+    GLU_LAUNCH_CHECK();
+    return GLU_OK;
 }
 
 }  // namespace glu

@@ -95,6 +95,7 @@ struct JointCtl {
     int open_tasks;
     int small_cur;    // 1: the one-CTA list kernel built this iteration's components and graph
     int nedge;        // dependency edges listed by k_deps in the current iteration
+    int multi_lists;  // bit n: iteration n's lists were built by the multi-kernel path
     int ticket[GLU_MAX_ITERS];    // tiles taken by the threshold pass (decoupled look-back order)
     int claim[GLU_MAX_ITERS];
     int finished[GLU_MAX_ITERS];
@@ -436,6 +437,7 @@ __global__ void k_resid_partial(const __grid_constant__ JBatch B, JointCtl* c) {
 // trial).
 __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int it) {
     if (!any_active(c) || threadIdx.x != 0) return;
+    if (it >= 0 && !c->small_cur) c->multi_lists |= 1 << it;
     for (int i = 0; i < B.n; ++i) {
         if (!c->active[i]) continue;
         const double R = (double)c->racc[i] * (1.0 / 4294967296.0);
@@ -1309,7 +1311,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     k_small_comp(const __grid_constant__ JBatch B, JointWs W, int it,
                  cudaGraphConditionalHandle cond, int has_cond) {
     JointCtl* c = W.ctl;
-    if (!any_active(c)) return;
+    if (!any_active(c)) {   // converged: the multi-kernel path would return at once
+        if (has_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
     const int nfg = c->nfg;
     if (nfg <= 0 || nfg > kSmallFg) return;   // the multi-kernel path does it (small_cur is 0)
     extern __shared__ __align__(16) unsigned char small_dyn[];
@@ -3243,6 +3248,7 @@ static int read_stats(const JointWs& ws, int n, glu_joint_stats* stats, cudaStre
             o.rolled_back[k] = h->rolled[i][k];
             o.searched[k] = (int64_t)h->searched[i][k];
         }
+        o.multi_kernel_lists = (uint32_t)h->multi_lists;
         for (int k = 0; k <= h->iterations[i] && k <= GLU_MAX_ITERS; ++k)
             o.residual[k] = h->residual[i][k];
     }

@@ -13,7 +13,6 @@ struct PipeBufs {
     uint8_t* lr;        // h x w x 3, the optimised LR image
     uint16_t* code;     // H x W pair codes
     uint16_t* weight;   // H x W unorm16 weights
-    float* t1;          // h x w x 3, the filtered LR image
     float* t2;          // h x w x 3, T
     float* out;         // H x W x 3, Eq. 1
     void* jws;          // Algorithm 2's workspace
@@ -42,7 +41,6 @@ size_t carve_pipe(int H, int W, int s, const glu_params* p, void* base, PipeBufs
     t.lr = (uint8_t*)take(h * w * 3);
     t.code = (uint16_t*)take(np * sizeof(uint16_t));
     t.weight = (uint16_t*)take(np * sizeof(uint16_t));
-    t.t1 = (float*)take(h * w * 3 * sizeof(float));
     t.t2 = (float*)take(h * w * 3 * sizeof(float));
     t.out = (float*)take(np * 3 * sizeof(float));
     if (o) *o = t;
@@ -80,13 +78,11 @@ int glu_pipeline_host(const uint8_t* hr_host, int32_t H, int32_t W, int32_t scal
     int rc = glu_joint_optimize(&hr, scale, params, &lr, &th, nullptr, nullptr, b.jws,
                                 b.jws_bytes, stream);
     if (rc) return rc;
-    rc = glu_fx_filter3_u8(b.lr, h, w, 3, (int64_t)w * 3, b.t1, (int64_t)w * 3, op, stream);
-    if (rc) return rc;
-    rc = glu_fx_point(b.t1, h, w, (int64_t)w * 3, b.t2, (int64_t)w * 3, sat, gamma, stream);
-    if (rc) return rc;
+    // the operator and Eq. 1 as one issue (the apply starts while the operator runs)
+    const glu_lr_op f{op, sat, gamma};
     glu_image t{b.t2, h, w, 3, GLU_F32, (int64_t)w * 3};
     glu_image out{b.out, H, W, 3, GLU_F32, (int64_t)W * 3};
-    rc = glu_apply(&th, &t, &out, stream);
+    rc = glu_apply_lrop(&th, &lr, &f, &t, &out, stream);
     if (rc) return rc;
     GLU_CUDA_TRY(cudaMemcpyAsync(out_host, b.out, (size_t)H * W * 3 * sizeof(float),
                                  cudaMemcpyDeviceToHost, st));

@@ -248,10 +248,10 @@ def test_pipeline_host_side(lib):
     H, W, s = 64, 80, 8
     need = lib.glu_pipeline_host_workspace_size(H, W, s, ctypes.byref(p))
     # Algorithm 2's workspace plus the device copies: guide (3 B/px), Theta (4 B/px), result
-    # (12 B/px) and three LR images (3 + 12 + 12 B per LR pixel), each 256-byte aligned
+    # (12 B/px) and two LR images (3 + 12 B per LR pixel), each 256-byte aligned
     jws = lib.glu_joint_workspace_size(H, W, s, ctypes.byref(p))
-    assert need >= jws + H * W * (3 + 4 + 12) + 8 * 10 * 27
-    assert need <= jws + H * W * (3 + 4 + 12) + 8 * 10 * 27 + 8 * 256
+    assert need >= jws + H * W * (3 + 4 + 12) + 8 * 10 * 15
+    assert need <= jws + H * W * (3 + 4 + 12) + 8 * 10 * 15 + 8 * 256
     assert lib.glu_pipeline_host_workspace_size(0, W, s, ctypes.byref(p)) == 0
     assert lib.glu_pipeline_host_workspace_size(H, W, s, None) == 0
     fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
@@ -278,3 +278,37 @@ def test_pipeline_host_side(lib):
     assert lib.glu_fx_filter3_u8(None, 8, 10, 3, 30, fake, 30, 0, None) == A.GLU_ERR_INVALID_ARG
     assert lib.glu_fx_filter3_u8(fake, 8, 10, 3, 29, fake, 30, 0, None) == A.GLU_ERR_INVALID_ARG
     assert lib.glu_fx_filter3_u8(fake, 8, 10, 3, 30, fake, 30, 3, None) == A.GLU_ERR_INVALID_ARG
+
+
+def test_generic_workspace_size_matches_per_op_queries(lib):
+    from paper_2307_09582_gb300 import _abi as A
+    p = A.GluParams()
+    lib.glu_params_default(ctypes.byref(p))
+    p.S, p.N = 5, 3
+    H, W, s = 96, 136, 8
+    fake = ctypes.c_void_p(0x1000)
+    th = A.GluTheta(fake, fake, H, W, s, p.S, A.GLU_W_F32)
+    ws = lambda op: lib.glu_workspace_size(op, H, W, s, ctypes.byref(p))
+    assert ws(A.GLU_OP_JOINT) == lib.glu_joint_workspace_size(H, W, s, ctypes.byref(p)) > 0
+    assert ws(A.GLU_OP_LS_JOINT) == lib.glu_ls_joint_workspace_size(H, W, s, ctypes.byref(p)) > 0
+    assert ws(A.GLU_OP_LS_UPDATE) == lib.glu_ls_update_workspace_size(ctypes.byref(th)) > 0
+    assert ws(A.GLU_OP_APPLY_BACKWARD) == \
+        lib.glu_apply_backward_workspace_size(ctypes.byref(th), 3) > 0
+    assert ws(A.GLU_OP_APPLY_BACKWARD_PLAN) == \
+        lib.glu_apply_backward_plan_size(ctypes.byref(th)) > 0
+    for op in (A.GLU_OP_DOWNSAMPLE, A.GLU_OP_OPTIMIZE, A.GLU_OP_APPLY, A.GLU_OP_THETA_DECODE, 99):
+        assert ws(op) == 0
+    assert lib.glu_workspace_size(A.GLU_OP_JOINT, 0, W, s, ctypes.byref(p)) == 0
+    assert lib.glu_workspace_size(A.GLU_OP_JOINT, H, W, s, None) == 0
+
+
+def test_theta_decode_validates_before_launch(lib):
+    from paper_2307_09582_gb300 import _abi as A
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
+    th = A.GluTheta(fake, fake, 64, 80, 8, 4, A.GLU_W_F32)     # even S
+    assert lib.glu_theta_decode(ctypes.byref(th), fake, fake, fake, None) == \
+        A.GLU_ERR_INVALID_ARG
+    th.S = 3
+    assert lib.glu_theta_decode(ctypes.byref(th), None, None, None, None) == \
+        A.GLU_ERR_INVALID_ARG
+    assert lib.glu_theta_decode(None, fake, fake, fake, None) == A.GLU_ERR_INVALID_ARG

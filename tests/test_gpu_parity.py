@@ -199,3 +199,60 @@ def test_apply_vector_path_parity(api, wfmt):
     ref = O.apply(codes // K, codes % K, theta.weight_f32().cpu().numpy().astype(np.float64),
                   s, S, T.cpu().numpy().astype(np.float64))
     assert np.abs(out.cpu().numpy() - ref).max() < 1e-6
+
+
+# ------------------------------------------------------------------------- Theta decode
+
+@pytest.mark.parametrize("H,W,s,S,wfmt", [(97, 131, 3, 5, 1), (250, 347, 8, 3, 0),
+                                          (64, 80, 16, 7, 2)])
+def test_theta_decode_against_oracle_pairs(api, H, W, s, S, wfmt):
+    # absolute LR indices of (a, b) decoded on the device equal the oracle's window indices
+    # decoded here by the window definition (clipped windows included), the weights equal the
+    # stored ones, and gathering T through them reproduces Eq. 1 as glu_apply computes it
+    img = scene_img(40 + S, H, W)
+    hr = dev(img)
+    lr = api.glu_downsample(hr, s, api.GLU_DOWN_GRID)
+    theta, _ = api.glu_optimize(hr, lr, api.glu_params(S=S), s, wfmt=wfmt)
+    a, b, w = api.glu_theta_decode(theta)
+    torch.cuda.synchronize()
+    assert api.glu_device_status() == 0
+    h, wl = api.lr_dims(H, W, s)
+    r = (S - 1) // 2
+    codes = theta.codes_i32().cpu().numpy()
+    ka, kb = codes // (S * S), codes % (S * S)
+    yy, xx = np.mgrid[0:H, 0:W]
+    exp_a = (yy // s + ka // S - r) * wl + (xx // s + ka % S - r)
+    exp_b = (yy // s + kb // S - r) * wl + (xx // s + kb % S - r)
+    a, b, w = a.cpu().numpy(), b.cpu().numpy(), w.cpu().numpy()
+    assert np.array_equal(a, exp_a) and np.array_equal(b, exp_b)
+    assert a.min() >= 0 and a.max() < h * wl and b.min() >= 0 and b.max() < h * wl
+    assert np.array_equal(w, theta.weight_f32().cpu().numpy())
+    # the pairs are the oracle's Algorithm 1 pairs wherever its choice is not a near tie
+    L = lr_like_gpu(lr)
+    ref = O.glu_fast(img, L, s, S)
+    same = (ka == ref["ka"]) & (kb == ref["kb"])
+    assert same.mean() > 0.99
+    T = torch.rand((h, wl, 3), generator=torch.Generator().manual_seed(S)).cuda()
+    out = api.glu_apply(theta, T).cpu().numpy().astype(np.float64)
+    Tf = T.cpu().numpy().reshape(-1, 3).astype(np.float64)
+    g = w[..., None] * Tf[a] + (1.0 - w[..., None]) * Tf[b]
+    assert np.abs(out - g).max() < 1e-6
+
+
+def test_theta_decode_flags_codes_outside_the_window(api):
+    # a code naming a window position outside the image: the decode writes -1 for both indices
+    # of that pixel, leaves the others intact and reports GLU_ERR_DEVICE_CHECK
+    H, W, s, S = 32, 48, 4, 3
+    hr = dev(scene_img(7, H, W))
+    lr = api.glu_downsample(hr, s, api.GLU_DOWN_GRID)
+    theta, _ = api.glu_optimize(hr, lr, api.glu_params(S=S), s)
+    torch.cuda.synchronize()
+    assert api.glu_device_status() == 0
+    theta.code[0, 0] = 0          # (dy, dx) = (-1, -1) at the top-left corner: outside
+    a, b, _ = api.glu_theta_decode(theta)
+    torch.cuda.synchronize()
+    assert api.glu_device_status() == api.A.GLU_ERR_DEVICE_CHECK
+    assert api.glu_device_status() == 0
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert a[0, 0] == -1 and b[0, 0] == -1
+    assert a.ravel()[1:].min() >= 0 and b.ravel()[1:].min() >= 0

@@ -539,7 +539,7 @@ def glu_joint_profile_read() -> dict:
 
 def joint_launches(N: int, graph: bool = False, multi_kernel_lists: int = 0) -> int:
     """Kernel launches one glu_joint_optimize call makes: control init, grid downsample, search
-    and R_0 (2), then per iteration the threshold pass with its ordered list, the one-CTA list
+    and R_0 (2), then per iteration the threshold count and list-write passes, the one-CTA list
     kernel, the multi-kernel list path (merge, flatten, root count, scan, root scatter, component
     count, 3 scan, fill, dependency graph 5: 15 kernels), the trials, the list clear and the
     residual update. Issued directly, every kernel launches (those with nothing to do return at
@@ -547,9 +547,9 @@ def joint_launches(N: int, graph: bool = False, multi_kernel_lists: int = 0) -> 
     path sit in a conditional node and launch only in the iterations whose bit is set in the
     stats' multi_kernel_lists."""
     if not graph:
-        return 5 + 20 * N
+        return 5 + 21 * N
     multi = bin(multi_kernel_lists & ((1 << N) - 1)).count("1")
-    return 5 + 5 * N + 15 * multi
+    return 5 + 6 * N + 15 * multi
 
 
 def tune_mode(on: bool) -> None:

@@ -146,35 +146,49 @@ __global__ void k_op_point(const float* X, int h, int w, int64_t pitch, float* Y
 }
 
 // The whole operator (filter -1: none, else k_op_filter3's op) per 3-channel LR pixel: the same
-// values as k_op_filter3 followed by k_op_point (the intermediate is a float either way).
+// values as k_op_filter3 followed by k_op_point (the intermediate is a float either way). A CTA
+// owns a kLrTile x kLrTile tile: it stages the tile and a one-pixel ring (coordinates clamped to
+// the image, so the ring repeats the edge as the filter's clamped taps do) in shared memory with
+// coalesced row loads, then every thread filters its pixel from there, taps in the same order.
+constexpr int kLrTile = 16;
+
 template <typename TX>
-__global__ void k_op_lr(const TX* X, int h, int w, int64_t pitch, float* Y, int64_t ypitch,
-                        int filter, float sat, float gamma) {
+__global__ void __launch_bounds__(kLrTile * kLrTile)
+    k_op_lr(const TX* X, int h, int w, int64_t pitch, float* Y, int64_t ypitch, int filter,
+            float sat, float gamma) {
     griddep_launch_dependents();   // a dependent apply may start loading codes and weights
-    const int64_t n = (int64_t)h * w;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int v = (int)(i / w), u = (int)(i % w);
-        float c3[3];
-        for (int c = 0; c < 3; ++c)
-            c3[c] = filter < 0 ? op_in(X[(int64_t)v * pitch + (int64_t)u * 3 + c])
-                               : filter3_at(X, h, w, 3, pitch, v, u, c, filter);
-        point_op(c3, sat, gamma);
-        float* y = Y + (int64_t)v * ypitch + (int64_t)u * 3;
-        for (int c = 0; c < 3; ++c) y[c] = c3[c];
+    constexpr int RW = kLrTile + 2;
+    __shared__ TX tile[RW * RW * 3];
+    const int v0 = blockIdx.y * kLrTile, u0 = blockIdx.x * kLrTile;
+    for (int i = threadIdx.x; i < RW * RW * 3; i += blockDim.x) {
+        const int rr = i / (RW * 3), rem = i - rr * (RW * 3), cc = rem / 3, c = rem - cc * 3;
+        const int v = min(max(v0 - 1 + rr, 0), h - 1), u = min(max(u0 - 1 + cc, 0), w - 1);
+        tile[i] = X[(int64_t)v * pitch + (int64_t)u * 3 + c];
     }
+    __syncthreads();
+    const int tv = threadIdx.x / kLrTile, tu = threadIdx.x % kLrTile;
+    const int v = v0 + tv, u = u0 + tu;
+    if (v >= h || u >= w) return;
+    float c3[3];
+    for (int c = 0; c < 3; ++c)
+        c3[c] = filter < 0 ? op_in(tile[((tv + 1) * RW + tu + 1) * 3 + c])
+                           : filter3_at(tile + (tv * RW + tu) * 3 + c, 3, 3, 3, RW * 3, 1, 1, 0,
+                                        filter);
+    point_op(c3, sat, gamma);
+    float* y = Y + (int64_t)v * ypitch + (int64_t)u * 3;
+    for (int c = 0; c < 3; ++c) y[c] = c3[c];
 }
 
 int launch_lr_op(const void* X, int x_dtype, int h, int w, int64_t pitch, float* Y, int64_t ypitch,
                  int filter, float sat, float gamma, cudaStream_t st) {
-    const int threads = 256;
-    const int grid = grid_for((int64_t)h * w, threads);
+    const dim3 grid((w + kLrTile - 1) / kLrTile, (h + kLrTile - 1) / kLrTile);
+    if (grid.y > 65535u) return GLU_ERR_UNSUPPORTED;
     if (x_dtype == GLU_U8)
-        k_op_lr<<<grid, threads, 0, st>>>((const uint8_t*)X, h, w, pitch, Y, ypitch, filter, sat,
-                                          gamma);
+        k_op_lr<<<grid, kLrTile * kLrTile, 0, st>>>((const uint8_t*)X, h, w, pitch, Y, ypitch,
+                                                    filter, sat, gamma);
     else
-        k_op_lr<<<grid, threads, 0, st>>>((const float*)X, h, w, pitch, Y, ypitch, filter, sat,
-                                          gamma);
+        k_op_lr<<<grid, kLrTile * kLrTile, 0, st>>>((const float*)X, h, w, pitch, Y, ypitch,
+                                                    filter, sat, gamma);
     GLU_LAUNCH_CHECK();
     return GLU_OK;
 }

@@ -96,7 +96,6 @@ struct JointCtl {
     int small_cur;    // 1: the one-CTA list kernel built this iteration's components and graph
     int nedge;        // dependency edges listed by k_deps in the current iteration
     int multi_lists;  // bit n: iteration n's lists were built by the multi-kernel path
-    int ticket[GLU_MAX_ITERS];    // tiles taken by the threshold pass (decoupled look-back order)
     int claim[GLU_MAX_ITERS];
     int finished[GLU_MAX_ITERS];
     int head[GLU_MAX_ITERS];      // ready queue: positions taken
@@ -127,7 +126,8 @@ struct JointWs {
     int2* start;            // mcap + 1
     int* done;              // mcap
     int* tile_a;            // tiles over np
-    unsigned long long* tstat;  // tiles over np: look-back status of the threshold pass
+    unsigned long long* tstat;  // tiles over np: large-error pixels per threshold tile
+    uint32_t* tbits;            // tiles over np x kScanTile / 32: the threshold tiles' ballots
     int2* tile_b;           // tiles over mcap
     int* own;               // nq * kOwnSlots
     uint8_t* ovf;           // nq
@@ -194,6 +194,7 @@ static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t
     t.done = (int*)take(sizeof(int) * mcap);
     t.tile_a = (int*)take(sizeof(int) * tiles_a);
     t.tstat = (unsigned long long*)take(sizeof(unsigned long long) * tiles_a);
+    t.tbits = (uint32_t*)take(sizeof(uint32_t) * (size_t)tiles_a * (kScanTile / 32));
     t.tile_b = (int2*)take(sizeof(int2) * tiles_b);
     t.own = (int*)take(sizeof(int) * nq * kOwnSlots);
     t.ovf = (uint8_t*)take(nq);
@@ -348,6 +349,30 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
     return v;
 }
 
+// Block sums (blockDim.x a multiple of 32, at most 8 warps): every thread gets the total, added
+// in a fixed order, so the result does not depend on timing.
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* smem_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_ll(v);
+    if (lane == 0) smem_warp[wid] = v;
+    __syncthreads();
+    long long t = 0;
+    for (int k = 0; k < nw; ++k) t += smem_warp[k];
+    __syncthreads();
+    return t;
+}
+__device__ __forceinline__ int block_sum_int(int v, int* smem_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) smem_warp[wid] = v;
+    __syncthreads();
+    int t = 0;
+    for (int k = 0; k < nw; ++k) t += smem_warp[k];
+    __syncthreads();
+    return t;
+}
+
 // Verification log (test hook, null: off): log[0].x counts records, records from log[1], at most
 // cap of them. Kinds: (iteration, component, LR pixel, HR pixel) for a trial's replacement
 // choice; (256 + iteration, HR pixel, membership, 0) for a pixel whose FP32 error is within
@@ -460,67 +485,57 @@ __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int
 
 // ----------------------------------------------------------------------- threshold and CCL
 
-// Large-error set of the active images, its ordered list and the union-find init, in one pass
-// over the image: a CTA per tile of kScanTile pixels (16 consecutive pixels per thread) marks
-// E_p > tau, starts every large-error pixel as its own union-find root (lab[p] = p) and writes
-// the tile's large-error pixels to the list fgl in raster order at the tile's offset, found by
-// decoupled look-back: tiles are taken in order by an atomic ticket, each publishes its count,
-// then its inclusive prefix once it has read its predecessors' (a tile waits only on tiles that
-// were taken before it, so every wait ends; the waits are bounded all the same). Iteration 0
-// (full_clear) also sets every other pixel's label to -1 and clears the owner slots; later
-// iterations find them cleared by k_lists_clear, which resets only the previous lists' pixels
-// and blocks.
-constexpr uint32_t kLookbackSpin = 1u << 22;
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Status word of a tile: [63:58] tag (iteration + 1), [57:56] 1 = count, 2 = inclusive prefix,
-// [55:0] the value.
-__device__ __forceinline__ unsigned long long tstat_word(int tag, int kind, long long v) {
-    return ((unsigned long long)tag << 58) | ((unsigned long long)kind << 56) |
-           ((unsigned long long)v & ((1ull << 56) - 1));
-}
-
+// Large-error set of the active images, its ordered list and the union-find init, in two passes
+// over tiles of kScanTile pixels (16 per thread, in rounds of 256 consecutive pixels) with no
+// waits between CTAs:
+//   k_threshold_count  marks E_p > tau, starts every large-error pixel as its own union-find root
+//                      (lab[p] = p), stores the tile's ballots (one 32-bit word per warp and
+//                      round) and its count; iteration 0 (full_clear) also sets every other
+//                      pixel's label to -1 and clears the owner slots (later iterations find them
+//                      cleared by k_lists_clear, which resets only the previous lists' pixels and
+//                      blocks)
+//   k_threshold_write  adds up the counts of the tiles before its own (a fixed-order block sum
+//                      over at most a few thousand L2-resident integers) and writes the tile's
+//                      large-error pixels to the list in raster order from the stored ballots
+// The counts end in the last tile, which records the list's length.
 __global__ void __launch_bounds__(kScanThreads)
-    k_threshold_list(const __grid_constant__ JBatch B, JointWs W, int it, int full_clear,
-                     int4* vlog, long long vcap) {
+    k_threshold_count(const __grid_constant__ JBatch B, JointWs W, int it, int full_clear,
+                      int4* vlog, long long vcap) {
     JointCtl* c = W.ctl;
     if (!any_active(c)) return;
     constexpr int kRounds = kScanTile / kScanThreads;   // 256 consecutive pixels per round
     constexpr int kWarps = kScanThreads / 32;
-    __shared__ int s_cnt[kRounds * kWarps];   // per (round, warp): large-error pixels, raster order
     __shared__ int wsm[8];
-    __shared__ int s_tile;
-    __shared__ long long s_excl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_tile = atomicAdd(&c->ticket[it], 1);
-        if (s_tile == 0) {   // a new iteration's lists
-            c->small_cur = 0;
-            c->nedge = 0;
+    const int tile = blockIdx.x;
+    if (tile == 0 && tid == 0) {   // a new iteration's lists
+        c->small_cur = 0;
+        c->nedge = 0;
+    }
+    const int64_t base = (int64_t)tile * kScanTile;
+    // a tile inside one image (the usual case): all sixteen error loads issue together, with no
+    // per-pixel image lookup in front of them
+    const int i0 = img_of_p(B, base);
+    const bool one = i0 + 1 >= B.n || B.im[i0 + 1].p0 >= base + kScanTile;
+    const bool act0 = c->active[i0] != 0;
+    float e1[kRounds];
+    if (one) {
+        const float* err = B.im[i0].err - B.im[i0].p0;
+#pragma unroll
+        for (int k = 0; k < kRounds; ++k) {
+            const int64_t p = base + k * kScanThreads + tid;
+            e1[k] = act0 && p < B.np ? err[p] : 0.f;
         }
     }
-    __syncthreads();
-    const int tile = s_tile;
-    const int64_t base = (int64_t)tile * kScanTile;
-    unsigned bal[kRounds];
-    int run_img = -1, run = 0;
+    int run_img = -1, run = 0, cnt = 0;
 #pragma unroll
     for (int k = 0; k < kRounds; ++k) {
         const int64_t p = base + k * kScanThreads + tid;
         bool fg = false;
         if (p < B.np) {
-            const int i = img_of_p(B, p);
-            if (c->active[i]) {
-                const float e = B.im[i].err[p - B.im[i].p0];
+            const int i = one ? i0 : img_of_p(B, p);
+            if (one ? act0 : c->active[i] != 0) {
+                const float e = one ? e1[k] : B.im[i].err[p - B.im[i].p0];
                 fg = e > B.tau;
                 if (vlog && fabsf(e - B.tau) < kThrLogBand)
                     log_record(vlog, vcap,
@@ -530,74 +545,29 @@ __global__ void __launch_bounds__(kScanThreads)
             else if (fg) W.lab[p] = (int)p;
             if (fg) {
                 if (i != run_img) {
-                    if (run) atomicAdd(&c->n_large[run_img][it], run);
+                    if (run && !one) atomicAdd(&c->n_large[run_img][it], run);
                     run_img = i;
                     run = 0;
                 }
                 ++run;
             }
         }
-        bal[k] = __ballot_sync(0xffffffffu, fg);
-        if (lane == 0) s_cnt[k * kWarps + warp] = __popc(bal[k]);
+        const unsigned bal = __ballot_sync(0xffffffffu, fg);
+        if (lane == 0) W.tbits[(int64_t)tile * (kRounds * kWarps) + k * kWarps + warp] = bal;
+        cnt += fg ? 1 : 0;
     }
-    if (run) atomicAdd(&c->n_large[run_img][it], run);
-    __syncthreads();
-    // exclusive offsets of the (round, warp) groups in raster order, and the tile's count
-    const int v = tid < kRounds * kWarps ? s_cnt[tid] : 0;
-    int ex;
-    const int agg = block_excl_scan(v, &ex, wsm);
-    if (tid < kRounds * kWarps) s_cnt[tid] = ex;
-    // the tile's offset: warp 0 looks back over 32 predecessor tiles at a time
-    if (warp == 0) {
-        const int tag = it + 1;
-        if (lane == 0)
-            st_release_u64(&W.tstat[tile], tstat_word(tag, tile == 0 ? 2 : 1, agg));
-        long long excl = 0;
-        bool ok = true;
-        for (int k0 = tile - 1; k0 >= 0; k0 -= 32) {
-            const int k = k0 - lane;
-            unsigned long long w = tstat_word(tag, 2, 0);   // before tile 0: a zero prefix
-            if (k >= 0) {
-                uint32_t spins = 0;
-                for (;;) {
-                    w = ld_acquire_u64(&W.tstat[k]);
-                    if ((int)(w >> 58) == tag && ((w >> 56) & 3ull) != 0) break;
-                    if (++spins > kLookbackSpin || *(volatile const int*)&c->timeout) {
-                        ok = false;
-                        w = tstat_word(tag, 2, 0);
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-            const unsigned pm = __ballot_sync(0xffffffffu, ((w >> 56) & 3ull) == 2);
-            const int stop = pm ? __ffs(pm) - 1 : 31;   // the nearest inclusive prefix
-            excl += warp_sum_ll(lane <= stop ? (long long)(w & ((1ull << 56) - 1)) : 0);
-            if (pm) break;
+    // |E| per image (one atomic per CTA for a tile inside one image) and the tile's count
+    if (one) {
+        const int tot = block_sum_int(run, wsm);
+        if (tid == 0) {
+            if (tot) atomicAdd(&c->n_large[i0][it], tot);
+            W.tstat[tile] = (unsigned long long)tot;
         }
-        ok = __all_sync(0xffffffffu, ok);
-        if (lane == 0) {
-            if (!ok) {
-                set_status(GLU_ERR_TIMEOUT);
-                atomicExch(&c->timeout, 1);
-                excl = 0;
-            }
-            if (tile > 0) st_release_u64(&W.tstat[tile], tstat_word(tag, 2, excl + agg));
-            s_excl = excl;
-            if (tile == (int)gridDim.x - 1) {   // the last tile knows the list's length
-                c->nfg = (int)(excl + agg);
-                if (excl + agg == 0) c->active_any = 0;   // every large-error set is empty
-            }
-        }
+    } else {
+        if (run) atomicAdd(&c->n_large[run_img][it], run);
+        const int tot = block_sum_int(cnt, wsm);
+        if (tid == 0) W.tstat[tile] = (unsigned long long)tot;
     }
-    __syncthreads();
-    const long long e0 = s_excl;
-    const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int k = 0; k < kRounds; ++k)
-        if ((bal[k] >> lane) & 1u)
-            W.ulist[e0 + s_cnt[k * kWarps + warp] + __popc(bal[k] & lt)] =
-                (int)(base + k * kScanThreads + tid);
     if (full_clear) {
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         for (int64_t q = blockIdx.x * (int64_t)blockDim.x + tid; q < B.nq; q += stride) {
@@ -605,6 +575,41 @@ __global__ void __launch_bounds__(kScanThreads)
             for (int k = 0; k < kOwnSlots; ++k) W.own[q * kOwnSlots + k] = -1;
             W.ovf[q] = 0;
         }
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_threshold_write(JointWs W) {
+    JointCtl* c = W.ctl;
+    if (!any_active(c)) return;
+    constexpr int kRounds = kScanTile / kScanThreads;
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_cnt[kRounds * kWarps];   // per (round, warp): offset within the tile
+    __shared__ int wsm[8];
+    __shared__ long long s_ll[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    // the list offset of this tile: counts of the tiles before it, summed in a fixed order
+    long long part = 0;
+    for (int k = tid; k < tile; k += kScanThreads) part += (long long)__ldcg(&W.tstat[k]);
+    const long long excl = block_sum_ll(part, s_ll);
+    const uint32_t* bits = W.tbits + (int64_t)tile * (kRounds * kWarps);
+    const int v = tid < kRounds * kWarps ? __popc(__ldcg(&bits[tid])) : 0;
+    int ex;
+    const int agg = block_excl_scan(v, &ex, wsm);
+    if (tid < kRounds * kWarps) s_cnt[tid] = ex;
+    __syncthreads();
+    if (tid == 0 && tile == (int)gridDim.x - 1) {   // the last tile knows the list's length
+        c->nfg = (int)(excl + agg);
+        if (excl + agg == 0) c->active_any = 0;   // every large-error set is empty
+    }
+    const int64_t base = (int64_t)tile * kScanTile;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kRounds; ++k) {
+        const unsigned bal = __ldcg(&bits[k * kWarps + warp]);
+        if ((bal >> lane) & 1u)
+            W.ulist[excl + s_cnt[k * kWarps + warp] + __popc(bal & lt)] =
+                (int)(base + k * kScanThreads + tid);
     }
 }
 
@@ -1360,7 +1365,13 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     // hook every edge's two roots (the larger under the smaller), then jump pointers until every
     // tree is a star; repeat until no edge joins two trees
     bool settled = false;
+#ifdef GLU_TRIAL_TRACE
+    int n_jumps = 0;
+#endif
     for (int round = 0; round < kSmallRounds; ++round) {
+#ifdef GLU_TRIAL_TRACE
+        if (threadIdx.x == 0) g_small_t[it][10] = (unsigned long long)(round + 1);
+#endif
         int changed = 0;
 #pragma unroll
         for (int k = 0; k < kSmallPer; ++k) {
@@ -1392,6 +1403,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
                     moved = 1;
                 }
             }
+#ifdef GLU_TRIAL_TRACE
+            if (threadIdx.x == 0) g_small_t[it][11] = (unsigned long long)(++n_jumps);
+#endif
             if (!__syncthreads_or(moved)) break;
         }
     }
@@ -3046,6 +3060,29 @@ static int collect_graph() {
 }
 }  // namespace prof
 
+#ifdef GLU_TRIAL_TRACE
+// Trace build: an event after every launch of a directly issued call (glu_dbg_marks reads them).
+namespace dbgm {
+constexpr int kMax = 1024;
+static cudaEvent_t ev[kMax];
+static int tag[kMax];
+static int n = 0;
+static bool on = false;
+static void mark(cudaStream_t st, int t) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!on || n >= kMax || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
+        return;
+    if (!ev[n]) cudaEventCreate(&ev[n]);
+    tag[n] = t;
+    cudaEventRecord(ev[n++], st);
+}
+}  // namespace dbgm
+#define GLU_DBG_MARK(st, t) dbgm::mark(st, t)
+#else
+#define GLU_DBG_MARK(st, t)
+#endif
+
 // Every launch of one Algorithm 2 call on `st` (phase events into profiling slot `slot`, if
 // >= 0). The sequence depends only on the arguments: iterations after an image's convergence
 // still launch and return at once, so the sequence can be replayed as a CUDA graph.
@@ -3098,8 +3135,10 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
     prof::mark(slot, evi++, st);
     k_ctl_init<<<grid_cap(nq > kMaxSlots ? nq : kMaxSlots, T), T, 0, st>>>(
         ws.ctl, ws.stamp, nq, ws.slot_word, n, ws.tstat, (np + kScanTile - 1) / kScanTile + 1);
+    GLU_DBG_MARK(st, 1);
     // initialise every LR image by regular grid downsampling, Theta and E by Algorithm 1
     k_grid_batch<<<grid_cap(nq, T), T, 0, st>>>(B);
+    GLU_DBG_MARK(st, 2);
     GLU_LAUNCH_CHECK();
     SearchArgs sa[kMaxJointBatch];
     for (int k = 0; k < n; ++k) {
@@ -3113,10 +3152,13 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
     }
     prof::mark(slot, evi++, st);
     int rc = launch_search_batch(sa, n, st);
+    GLU_DBG_MARK(st, 3);
     if (rc) return rc;
     prof::mark(slot, evi++, st);
     k_resid_partial<<<B.nchunks, 256, 0, st>>>(B, ws.ctl);
+    GLU_DBG_MARK(st, 4);
     k_resid_final<<<1, 32, 0, st>>>(B, ws.ctl, -1);
+    GLU_DBG_MARK(st, 5);
     GLU_LAUNCH_CHECK();
     prof::mark(slot, evi++, st);
 
@@ -3137,8 +3179,11 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
         // scratch of the trials, free until then)
         int* fgl = ws.ulist;
         const int lgrid = 2 * sm_count();   // list passes: a thread per large-error pixel or so
-        k_threshold_list<<<tiles_a, kScanThreads, 0, st>>>(B, ws, it, it == 0 ? 1 : 0,
-                                                            cm.argmax_log, cm.argmax_cap);
+        k_threshold_count<<<tiles_a, kScanThreads, 0, st>>>(B, ws, it, it == 0 ? 1 : 0,
+                                                             cm.argmax_log, cm.argmax_cap);
+        GLU_DBG_MARK(st, 6);
+        k_threshold_write<<<tiles_a, kScanThreads, 0, st>>>(ws);
+        GLU_DBG_MARK(st, 7);
         // a short list: the whole phase in one CTA, and the multi-kernel path below is skipped:
         // inside a recorded graph by a conditional node, otherwise its kernels return at once
         cudaGraphConditionalHandle cond = 0;
@@ -3151,6 +3196,7 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
             GLU_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
         }
         k_small_comp<<<1, kSmallThreads, sizeof(SmallSmem), st>>>(B, ws, it, cond, body ? 1 : 0);
+        GLU_DBG_MARK(st, 8);
         if (body) {
             cudaStreamCaptureStatus cs;
             cudaGraph_t g = nullptr;
@@ -3172,25 +3218,40 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
             ls = body;
         }
         k_ccl_merge<<<lgrid, T, 0, ls>>>(B, ws.lab, fgl, ws.ctl);
+        GLU_DBG_MARK(ls, 9);
         k_ccl_flatten<<<lgrid, T, 0, ls>>>(ws.lab, fgl, ws.ctl);
+        GLU_DBG_MARK(ls, 10);
         k_root_count<<<list_grid_a, kScanThreads, 0, ls>>>(ws.lab, fgl, ws.tile_a, ws.ctl);
+        GLU_DBG_MARK(ls, 11);
         k_tile_scan<1><<<1, kScanThreads, 0, ls>>>(ws.tile_a, tiles_a, ws.ctl);
+        GLU_DBG_MARK(ls, 12);
         k_root_scatter<<<list_grid_a, kScanThreads, 0, ls>>>(B, ws.lab, fgl, ws.tile_a, ws.roots,
                                                          ws.cnt, ws.fill, ws.done, ws.dag_cnt,
                                                          ws.dag_fill, ws.queue, ws.ctl, it);
+        GLU_DBG_MARK(ls, 13);
         k_comp_count<<<lgrid, T, 0, ls>>>(B, ws.lab, fgl, ws.roots, ws.cnt, ws.own,
                                                          ws.ovf, ws.qflag, ws.ctl);
+        GLU_DBG_MARK(ls, 14);
         k_comp_tile_reduce<<<list_grid_b, kScanThreads, 0, ls>>>(ws.cnt, ws.tile_b, ws.ctl);
+        GLU_DBG_MARK(ls, 15);
         k_comp_tile_scan<<<1, kScanThreads, 0, ls>>>(ws.tile_b, ws.ctl);
+        GLU_DBG_MARK(ls, 16);
         k_comp_scan<<<list_grid_b, kScanThreads, 0, ls>>>(ws.cnt, ws.tile_b, ws.start, ws.ctl);
+        GLU_DBG_MARK(ls, 17);
         k_comp_fill<<<lgrid, T, 0, ls>>>(B, ws.lab, fgl, ws.qflag, ws.start,
                                                         ws.fill, ws.comp_pix, ws.qlist, ws.ctl);
+        GLU_DBG_MARK(ls, 18);
         // the trials' dependency graph
         k_deps<<<grid_cap(ws.mcap, 1, 4), 256, 0, ls>>>(B, ws, it);
+        GLU_DBG_MARK(ls, 19);
         k_comp_tile_reduce<<<list_grid_b, kScanThreads, 0, ls>>>(ws.dag_cnt, ws.tile_b, ws.ctl);
+        GLU_DBG_MARK(ls, 20);
         k_comp_tile_scan<<<1, kScanThreads, 0, ls>>>(ws.tile_b, ws.ctl);
+        GLU_DBG_MARK(ls, 21);
         k_comp_scan<<<list_grid_b, kScanThreads, 0, ls>>>(ws.dag_cnt, ws.tile_b, ws.dag_start, ws.ctl);
+        GLU_DBG_MARK(ls, 22);
         k_edge_scatter<<<list_grid_b, 256, 0, ls>>>(B, ws, it);
+        GLU_DBG_MARK(ls, 23);
         GLU_LAUNCH_CHECK();
         if (body) {
             cudaGraph_t done = nullptr;
@@ -3199,11 +3260,14 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
         prof::mark(slot, evi++, st);
         X.it = it;
         rc = launch_trials(B, X, st);
+        GLU_DBG_MARK(st, 24);
         if (rc) return rc;
         k_lists_clear<<<list_grid_a, kScanThreads, 0, st>>>(ws);
+        GLU_DBG_MARK(st, 25);
         prof::mark(slot, evi++, st);
         // R_{it+1} = R_it + the kept trials' differences (added by the trials themselves)
         k_resid_final<<<1, 32, 0, st>>>(B, ws.ctl, it);
+        GLU_DBG_MARK(st, 26);
         GLU_LAUNCH_CHECK();
         prof::mark(slot, evi++, st);
     }
@@ -3431,6 +3495,21 @@ extern "C" int glu_dbg_wtrace(unsigned long long* host) {
 extern "C" int glu_dbg_small_times(unsigned long long* host) {
     return cudaMemcpyFromSymbol(host, glu::g_small_t, sizeof(glu::g_small_t)) == cudaSuccess
                ? GLU_OK : GLU_ERR_CUDA;
+}
+
+extern "C" int glu_dbg_marks(int enable, float* ms, int* tags, int cap) {
+    using namespace glu;
+    int k = 0;
+    if (dbgm::n > 0 && ms && tags) {
+        if (cudaEventSynchronize(dbgm::ev[dbgm::n - 1]) != cudaSuccess) return -1;
+        for (int i = 1; i < dbgm::n && k < cap; ++i, ++k) {
+            cudaEventElapsedTime(&ms[k], dbgm::ev[i - 1], dbgm::ev[i]);
+            tags[k] = dbgm::tag[i];
+        }
+    }
+    dbgm::n = 0;
+    dbgm::on = enable != 0;
+    return k;
 }
 
 extern "C" int glu_dbg_trace_clear(void) {

@@ -527,7 +527,9 @@ __global__ void __launch_bounds__(kScanThreads)
             e1[k] = act0 && p < B.np ? err[p] : 0.f;
         }
     }
+    __shared__ unsigned s_bits[kRounds * kWarps];   // the tile's ballots in raster order
     int run_img = -1, run = 0, cnt = 0;
+    unsigned fgm = 0u;   // bit k: this thread's pixel of round k is a large-error pixel
 #pragma unroll
     for (int k = 0; k < kRounds; ++k) {
         const int64_t p = base + k * kScanThreads + tid;
@@ -541,8 +543,7 @@ __global__ void __launch_bounds__(kScanThreads)
                     log_record(vlog, vcap,
                                make_int4(256 + it, (int)(p - B.im[i].p0), fg ? 1 : 0, 0));
             }
-            if (full_clear) W.lab[p] = fg ? (int)p : -1;
-            else if (fg) W.lab[p] = (int)p;
+            if (full_clear && !fg) W.lab[p] = -1;
             if (fg) {
                 if (i != run_img) {
                     if (run && !one) atomicAdd(&c->n_large[run_img][it], run);
@@ -553,8 +554,29 @@ __global__ void __launch_bounds__(kScanThreads)
             }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, fg);
-        if (lane == 0) W.tbits[(int64_t)tile * (kRounds * kWarps) + k * kWarps + warp] = bal;
+        if (lane == 0) {
+            W.tbits[(int64_t)tile * (kRounds * kWarps) + k * kWarps + warp] = bal;
+            s_bits[k * kWarps + warp] = bal;
+        }
+        fgm |= fg ? 1u << k : 0u;
         cnt += fg ? 1 : 0;
+    }
+    __syncthreads();
+    // union-find init: every large-error pixel's parent is the first pixel of its horizontal run
+    // (within the row and the tile; a run that continues from the previous tile is joined to it
+    // by the merge), so the trees start one level deep and the merge's finds stay short; the
+    // root of every component is still its smallest pixel
+    for (unsigned m = fgm; m; m &= m - 1) {
+        const int k = __ffs(m) - 1;
+        const int pos = k * kScanThreads + tid;   // position in the tile, raster order
+        const int64_t p = base + pos;
+        const int i = one ? i0 : img_of_p(B, p);
+        const int64_t rowstart = p - (p - B.im[i].p0) % B.im[i].W;
+        int wi = pos >> 5;
+        unsigned zeros = ~s_bits[wi] & ((1u << (pos & 31)) - 1u);
+        while (!zeros && wi > 0) zeros = ~s_bits[--wi];
+        const int64_t start = zeros ? base + wi * 32 + (32 - __clz(zeros)) : base;
+        W.lab[p] = (int)(start > rowstart ? start : rowstart);
     }
     // |E| per image (one atomic per CTA for a tile inside one image) and the tile's count
     if (one) {
@@ -670,15 +692,26 @@ __global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const in
         const JImg& I = B.im[img_of_p(B, p)];
         const int64_t lp = p - I.p0;
         const int y = (int)(lp / I.W), x = (int)(lp % I.W);
-        // backward neighbours inside the image: W, N (and NW, NE for 8-connectivity)
-        if (x > 0 && __ldcg(&lab[p - 1]) >= 0) uf_union(lab, (int)p, (int)p - 1);
-        if (y > 0) {
-            const int64_t up = p - I.W;
-            if (__ldcg(&lab[up]) >= 0) uf_union(lab, (int)p, (int)up);
-            if (B.conn == 8) {
-                if (x > 0 && __ldcg(&lab[up - 1]) >= 0) uf_union(lab, (int)p, (int)up - 1);
-                if (x + 1 < I.W && __ldcg(&lab[up + 1]) >= 0) uf_union(lab, (int)p, (int)up + 1);
+        // backward neighbours inside the image: W, N (and NW, NE for 8-connectivity). With
+        // 8-connectivity a large-error N makes the other three redundant (W is joined to N as
+        // its NE neighbour, NW and NE as N's W and E neighbours, each when that pixel is
+        // merged), and a large-error W makes NW redundant (W's N): at most two unions per pixel.
+        const bool fw = x > 0 && __ldcg(&lab[p - 1]) >= 0;
+        const int64_t up = p - I.W;
+        const bool fn = y > 0 && __ldcg(&lab[up]) >= 0;
+        if (B.conn == 8) {
+            if (fn) {
+                uf_union(lab, (int)p, (int)up);
+            } else {
+                if (fw) uf_union(lab, (int)p, (int)p - 1);
+                else if (y > 0 && x > 0 && __ldcg(&lab[up - 1]) >= 0)
+                    uf_union(lab, (int)p, (int)up - 1);
+                if (y > 0 && x + 1 < I.W && __ldcg(&lab[up + 1]) >= 0)
+                    uf_union(lab, (int)p, (int)up + 1);
             }
+        } else {
+            if (fw) uf_union(lab, (int)p, (int)p - 1);
+            if (fn) uf_union(lab, (int)p, (int)up);
         }
     }
 }
@@ -973,6 +1006,10 @@ static __device__ unsigned long long g_wtrace[kWTraceMax][32][6];
 #define GLU_WVAL(it, j, k, v) do { } while (0)
 #endif
 #ifdef GLU_TRIAL_TRACE
+// Debug builds only: per component of iteration 0, k_deps' [start, end, items, bitmap, CTA].
+static __device__ unsigned long long g_deps_t[kTraceMax][5];
+#endif
+#ifdef GLU_TRIAL_TRACE
 // Debug builds only: phase stamps of the one-CTA list kernel per iteration.
 static __device__ unsigned long long g_small_t[GLU_MAX_ITERS][16];
 #define GLU_SMALL_STAMP(it, k) \
@@ -1023,7 +1060,9 @@ constexpr int kDepsBits = 1 << 16;
 // Neighbourhood bitmap of one component (dilated bounding box of its blocks), used above this
 // many (block, neighbour) pairs.
 constexpr int kNbBits = 1 << 15;
-constexpr int kNbMinPairs = 4096;
+constexpr int kNbMinPairs = 256;
+constexpr int kDepsWords = 256;   // bitmap words compacted per round (positions < 2^15: short)
+static_assert(kNbBits <= 32768, "bitmap positions are stored as short");
 
 // The scratch list of dependency edges (i, j): the backup weight plane, free outside the trials.
 __device__ __forceinline__ int2* edge_list(const JointWs& W) { return reinterpret_cast<int2*>(W.sh_w); }
@@ -1044,6 +1083,8 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
     __shared__ int cand[kCandMax];
     __shared__ unsigned bits[kDepsBits / 32];
     __shared__ unsigned nbits[kNbBits / 32];
+    __shared__ short plist[kDepsWords * 32];   // marked bitmap positions of one round
+    __shared__ int s_scan[32];
     __shared__ int s_n, s_bad, s_vmin, s_vmax, s_umin, s_umax;
     const int M = c->M_cur;
     const bool use_bits = M <= kDepsBits;
@@ -1062,15 +1103,22 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
         const int D = B.strict ? 2 * r : r;
         const int ND = (2 * D + 1) * (2 * D + 1);
         const int npairs = (en.y - st.y) * ND;
+#ifdef GLU_TRIAL_TRACE
+        if (it == 0 && threadIdx.x == 0 && j < kTraceMax) g_deps_t[j][0] = gtimer();
+#endif
         // a large component's (block, neighbour) pairs name each block of its neighbourhood many
         // times: mark them in a bitmap over the bounding box of its blocks dilated by D, then
         // look up every marked block once
         int nitems = npairs, BV0 = 0, BU0 = 0, BW = 1;
         bool nbmap = false;
         if (npairs > kNbMinPairs) {
-            for (int t = st.y + (int)threadIdx.x; t < en.y; t += blockDim.x) {
-                const int64_t lq = (int64_t)W.qlist[t] - I.q0;
-                const int v = (int)(lq / I.w), u = (int)(lq % I.w);
+            // the component's blocks, staged in cand (free until the lookups) when they fit
+            const int nbq = en.y - st.y;
+            const bool staged = nbq <= kCandMax;
+            for (int t = (int)threadIdx.x; t < nbq; t += blockDim.x) {
+                const int lq = (int)((int64_t)W.qlist[st.y + t] - I.q0);
+                if (staged) cand[t] = lq;
+                const int v = lq / I.w, u = lq % I.w;
                 atomicMin(&s_vmin, v);
                 atomicMax(&s_vmax, v);
                 atomicMin(&s_umin, u);
@@ -1086,14 +1134,36 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 nitems = BH * BW;
                 for (int t = threadIdx.x; t < (nitems + 31) / 32; t += blockDim.x) nbits[t] = 0u;
                 __syncthreads();
-                for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
-                    const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
-                    const int nb = t % ND;
-                    const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
-                    const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
-                    if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
-                    const int idx = (bv - BV0) * BW + (bu - BU0);
-                    atomicOr(&nbits[idx >> 5], 1u << (idx & 31));
+                if (staged) {
+                    // per (block, row of its neighbourhood): one run of 2D + 1 positions, at
+                    // most two bitmap words (D <= 8)
+                    const int NR = 2 * D + 1;
+                    for (int t = threadIdx.x; t < nbq * NR; t += blockDim.x) {
+                        const int lq = cand[t / NR];
+                        const int bv = lq / I.w + t % NR - D, qu = lq % I.w;
+                        if (bv < 0 || bv >= I.h) continue;
+                        const int row = (bv - BV0) * BW - BU0;
+                        const int b0 = row + max(qu - D, 0), b1 = row + min(qu + D, I.w - 1);
+                        const int w0 = b0 >> 5, w1 = b1 >> 5;
+                        if (w0 == w1) {
+                            atomicOr(&nbits[w0], (0xFFFFFFFFu >> (31 - (b1 & 31))) &
+                                                     (0xFFFFFFFFu << (b0 & 31)));
+                        } else {
+                            atomicOr(&nbits[w0], 0xFFFFFFFFu << (b0 & 31));
+                            for (int w = w0 + 1; w < w1; ++w) atomicOr(&nbits[w], 0xFFFFFFFFu);
+                            atomicOr(&nbits[w1], 0xFFFFFFFFu >> (31 - (b1 & 31)));
+                        }
+                    }
+                } else {
+                    for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+                        const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+                        const int nb = t % ND;
+                        const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+                        const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+                        if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
+                        const int idx = (bv - BV0) * BW + (bu - BU0);
+                        atomicOr(&nbits[idx >> 5], 1u << (idx & 31));
+                    }
                 }
                 __syncthreads();
             }
@@ -1111,70 +1181,89 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 if (slot < kCandMax) cand[slot] = i;
             }
         };
-        // kDepsBatch items (pairs, or bitmap positions) per thread and round, their loads issued
-        // together (a block's overflow flag and its owner slots as two 16-byte loads): the
+        // kDepsBatch items (pairs, or marked bitmap positions) per thread and round, their loads
+        // issued together (a block's overflow flag and its owner slots as two 16-byte loads): the
         // largest components span hundreds of LR blocks, and their CTA sets the kernel's duration
         constexpr int kDepsBatch = 4;
         static_assert(kOwnSlots == 8, "owner slots are read as two int4");
-        for (int t0 = threadIdx.x * kDepsBatch; t0 < nitems; t0 += blockDim.x * kDepsBatch) {
-            int64_t bb[kDepsBatch];
-            int bvv[kDepsBatch], buu[kDepsBatch];
+        auto run_items = [&](const short* plist, int n_items) {
+            for (int t0 = threadIdx.x * kDepsBatch; t0 < n_items; t0 += blockDim.x * kDepsBatch) {
+                int64_t bb[kDepsBatch];
+                int bvv[kDepsBatch], buu[kDepsBatch];
 #pragma unroll
-            for (int k = 0; k < kDepsBatch; ++k) {
-                bb[k] = -1;
-                const int t = t0 + k;
-                if (t >= nitems) continue;
-                if (nbmap) {
-                    if (!((nbits[t >> 5] >> (t & 31)) & 1u)) continue;
-                    bvv[k] = BV0 + t / BW;
-                    buu[k] = BU0 + t % BW;
-                } else {
-                    const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
-                    const int nb = t % ND;
-                    bvv[k] = (int)(lq / I.w) + nb / (2 * D + 1) - D;
-                    buu[k] = (int)(lq % I.w) + nb % (2 * D + 1) - D;
-                    if (bvv[k] < 0 || bvv[k] >= I.h || buu[k] < 0 || buu[k] >= I.w) continue;
+                for (int k = 0; k < kDepsBatch; ++k) {
+                    bb[k] = -1;
+                    const int t = t0 + k;
+                    if (t >= n_items) continue;
+                    if (plist) {
+                        const int pos = plist[t];
+                        bvv[k] = BV0 + pos / BW;
+                        buu[k] = BU0 + pos % BW;
+                    } else {
+                        const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+                        const int nb = t % ND;
+                        bvv[k] = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+                        buu[k] = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+                        if (bvv[k] < 0 || bvv[k] >= I.h || buu[k] < 0 || buu[k] >= I.w) continue;
+                    }
+                    bb[k] = I.q0 + (int64_t)bvv[k] * I.w + buu[k];
                 }
-                bb[k] = I.q0 + (int64_t)bvv[k] * I.w + buu[k];
-            }
-            uint8_t ov[kDepsBatch];
-            int4 o0[kDepsBatch], o1[kDepsBatch];
+                uint8_t ov[kDepsBatch];
+                int4 o0[kDepsBatch], o1[kDepsBatch];
 #pragma unroll
-            for (int k = 0; k < kDepsBatch; ++k) {
-                ov[k] = 0;
-                o0[k] = o1[k] = make_int4(-1, -1, -1, -1);
-                if (bb[k] < 0) continue;
-                ov[k] = W.ovf[bb[k]];
-                const int4* op = reinterpret_cast<const int4*>(W.own + bb[k] * kOwnSlots);
-                o0[k] = op[0];
-                o1[k] = op[1];
-            }
+                for (int k = 0; k < kDepsBatch; ++k) {
+                    ov[k] = 0;
+                    o0[k] = o1[k] = make_int4(-1, -1, -1, -1);
+                    if (bb[k] < 0) continue;
+                    ov[k] = W.ovf[bb[k]];
+                    const int4* op = reinterpret_cast<const int4*>(W.own + bb[k] * kOwnSlots);
+                    o0[k] = op[0];
+                    o1[k] = op[1];
+                }
 #pragma unroll
-            for (int k = 0; k < kDepsBatch; ++k) {
-                if (bb[k] < 0) continue;
-                if (ov[k]) {
-                    // more components than owner slots: read the block's pixel labels
-                    const int ys = bvv[k] * I.s, xs = buu[k] * I.s;
-                    const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
-                    int last = -1;
-                    for (int e = 0; e < ey * ex; ++e) {
-                        const int i = W.lab[I.p0 + (int64_t)(ys + e / ex) * I.W + xs + e % ex];
-                        if (i >= 0 && i < j && i != last) {
-                            offer(i);
-                            last = i;
+                for (int k = 0; k < kDepsBatch; ++k) {
+                    if (bb[k] < 0) continue;
+                    if (ov[k]) {
+                        // more components than owner slots: read the block's pixel labels
+                        const int ys = bvv[k] * I.s, xs = buu[k] * I.s;
+                        const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
+                        int last = -1;
+                        for (int e = 0; e < ey * ex; ++e) {
+                            const int i = W.lab[I.p0 + (int64_t)(ys + e / ex) * I.W + xs + e % ex];
+                            if (i >= 0 && i < j && i != last) {
+                                offer(i);
+                                last = i;
+                            }
+                        }
+                    } else {
+                        // slots fill in order: the first -1 ends the list
+                        const int sl[kOwnSlots] = {o0[k].x, o0[k].y, o0[k].z, o0[k].w,
+                                                   o1[k].x, o1[k].y, o1[k].z, o1[k].w};
+#pragma unroll
+                        for (int e = 0; e < kOwnSlots; ++e) {
+                            if (sl[e] < 0) break;
+                            if (sl[e] < j) offer(sl[e]);
                         }
                     }
-                } else {
-                    // slots fill in order: the first -1 ends the list
-                    const int sl[kOwnSlots] = {o0[k].x, o0[k].y, o0[k].z, o0[k].w,
-                                               o1[k].x, o1[k].y, o1[k].z, o1[k].w};
-#pragma unroll
-                    for (int e = 0; e < kOwnSlots; ++e) {
-                        if (sl[e] < 0) break;
-                        if (sl[e] < j) offer(sl[e]);
-                    }
                 }
             }
+        };
+        if (nbmap) {
+            // the marked positions only (the bounding box of a long component is mostly empty):
+            // each round compacts kDepsWords bitmap words into a list, then looks it up
+            const int nwords = (nitems + 31) / 32;
+            for (int w0 = 0; w0 < nwords; w0 += kDepsWords) {
+                const int w = w0 + (int)threadIdx.x;
+                const unsigned word = (threadIdx.x < kDepsWords && w < nwords) ? nbits[w] : 0u;
+                int ex;
+                const int tot = block_excl_scan_any(__popc(word), &ex, s_scan);
+                for (unsigned m = word; m; m &= m - 1) plist[ex++] = (short)(w * 32 + __ffs(m) - 1);
+                __syncthreads();
+                run_items(plist, tot);
+                __syncthreads();
+            }
+        } else {
+            run_items(nullptr, nitems);
         }
         __syncthreads();
         const int n = s_n;
@@ -1210,6 +1299,14 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
             npred = s_n;
         }
         if (threadIdx.x == 0) W.pend[j] = npred;
+#ifdef GLU_TRIAL_TRACE
+        if (it == 0 && threadIdx.x == 0 && j < kTraceMax) {
+            g_deps_t[j][1] = gtimer();
+            g_deps_t[j][2] = (unsigned long long)nitems;
+            g_deps_t[j][3] = (unsigned long long)(nbmap ? 1 : 0) | ((unsigned long long)npairs << 8);
+            g_deps_t[j][4] = (unsigned long long)blockIdx.x;
+        }
+#endif
         __syncthreads();
     }
 }
@@ -3489,6 +3586,11 @@ extern "C" int glu_dbg_trace(unsigned long long* host, int64_t n) {
 
 extern "C" int glu_dbg_wtrace(unsigned long long* host) {
     return cudaMemcpyFromSymbol(host, glu::g_wtrace, sizeof(glu::g_wtrace)) == cudaSuccess
+               ? GLU_OK : GLU_ERR_CUDA;
+}
+
+extern "C" int glu_dbg_deps_times(unsigned long long* host) {
+    return cudaMemcpyFromSymbol(host, glu::g_deps_t, sizeof(glu::g_deps_t)) == cudaSuccess
                ? GLU_OK : GLU_ERR_CUDA;
 }
 

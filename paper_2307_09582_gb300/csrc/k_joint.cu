@@ -126,7 +126,7 @@ struct JointWs {
     int2* start;            // mcap + 1
     int* done;              // mcap
     int* tile_a;            // tiles over np
-    unsigned long long* tstat;  // tiles over np: large-error pixels per threshold tile
+    uint32_t* tcnt;             // tiles over np (padded to 4): large-error pixels per threshold tile
     uint32_t* tbits;            // tiles over np x kScanTile / 32: the threshold tiles' ballots
     int2* tile_b;           // tiles over mcap
     int* own;               // nq * kOwnSlots
@@ -193,7 +193,7 @@ static size_t carve(void* base, int64_t np, int64_t nq, int nimg, int N, int64_t
     t.start = (int2*)take(sizeof(int2) * (mcap + 1));
     t.done = (int*)take(sizeof(int) * mcap);
     t.tile_a = (int*)take(sizeof(int) * tiles_a);
-    t.tstat = (unsigned long long*)take(sizeof(unsigned long long) * tiles_a);
+    t.tcnt = (uint32_t*)take(sizeof(uint32_t) * (size_t)((tiles_a + 3) & ~(int64_t)3));
     t.tbits = (uint32_t*)take(sizeof(uint32_t) * (size_t)tiles_a * (kScanTile / 32));
     t.tile_b = (int2*)take(sizeof(int2) * tiles_b);
     t.own = (int*)take(sizeof(int) * nq * kOwnSlots);
@@ -389,12 +389,12 @@ __device__ __forceinline__ void log_record(int4* log, long long cap, int4 rec) {
 // Every counter of the control block starts at zero, except the active flags of the nimg
 // images and active_any; stamps and task slots are cleared.
 __global__ void k_ctl_init(JointCtl* c, unsigned long long* stamp, int64_t nq,
-                           unsigned long long* slot_word, int nimg, unsigned long long* tstat,
-                           int64_t ntstat) {
+                           unsigned long long* slot_word, int nimg, uint32_t* tcnt,
+                           int64_t ntcnt) {
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = i0; i < kMaxSlots; i += stride) slot_word[i] = 0ull;
-    for (int64_t i = i0; i < ntstat; i += stride) tstat[i] = 0ull;
+    for (int64_t i = i0; i < ntcnt; i += stride) tcnt[i] = 0u;
     for (int64_t i = i0; i < nq; i += stride) stamp[i] = 0ull;
     int* ci = (int*)c;
     constexpr int nwords = (int)(sizeof(JointCtl) / sizeof(int));
@@ -530,36 +530,56 @@ __global__ void __launch_bounds__(kScanThreads)
     __shared__ unsigned s_bits[kRounds * kWarps];   // the tile's ballots in raster order
     int run_img = -1, run = 0, cnt = 0;
     unsigned fgm = 0u;   // bit k: this thread's pixel of round k is a large-error pixel
+    uint32_t* tb = W.tbits + (int64_t)tile * (kRounds * kWarps);
+    if (one && !vlog) {
+        // the usual case: one image, no verification log
+        const int pl = (int)base + tid;   // pixel ids fit in 31 bits
+        const int np = (int)B.np;
 #pragma unroll
-    for (int k = 0; k < kRounds; ++k) {
-        const int64_t p = base + k * kScanThreads + tid;
-        bool fg = false;
-        if (p < B.np) {
-            const int i = one ? i0 : img_of_p(B, p);
-            if (one ? act0 : c->active[i] != 0) {
-                const float e = one ? e1[k] : B.im[i].err[p - B.im[i].p0];
-                fg = e > B.tau;
-                if (vlog && fabsf(e - B.tau) < kThrLogBand)
-                    log_record(vlog, vcap,
-                               make_int4(256 + it, (int)(p - B.im[i].p0), fg ? 1 : 0, 0));
+        for (int k = 0; k < kRounds; ++k) {
+            const bool in = pl + k * kScanThreads < np;
+            const bool fg = act0 && in && e1[k] > B.tau;
+            if (full_clear && in && !fg) W.lab[pl + k * kScanThreads] = -1;
+            const unsigned bal = __ballot_sync(0xffffffffu, fg);
+            if (lane == 0) {
+                tb[k * kWarps + warp] = bal;
+                s_bits[k * kWarps + warp] = bal;
             }
-            if (full_clear && !fg) W.lab[p] = -1;
-            if (fg) {
-                if (i != run_img) {
-                    if (run && !one) atomicAdd(&c->n_large[run_img][it], run);
-                    run_img = i;
-                    run = 0;
+            fgm |= fg ? 1u << k : 0u;
+        }
+        run = cnt = __popc(fgm);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRounds; ++k) {
+            const int64_t p = base + k * kScanThreads + tid;
+            bool fg = false;
+            if (p < B.np) {
+                const int i = one ? i0 : img_of_p(B, p);
+                if (one ? act0 : c->active[i] != 0) {
+                    const float e = one ? e1[k] : B.im[i].err[p - B.im[i].p0];
+                    fg = e > B.tau;
+                    if (vlog && fabsf(e - B.tau) < kThrLogBand)
+                        log_record(vlog, vcap,
+                                   make_int4(256 + it, (int)(p - B.im[i].p0), fg ? 1 : 0, 0));
                 }
-                ++run;
+                if (full_clear && !fg) W.lab[p] = -1;
+                if (fg) {
+                    if (i != run_img) {
+                        if (run && !one) atomicAdd(&c->n_large[run_img][it], run);
+                        run_img = i;
+                        run = 0;
+                    }
+                    ++run;
+                }
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, fg);
+            if (lane == 0) {
+                tb[k * kWarps + warp] = bal;
+                s_bits[k * kWarps + warp] = bal;
+            }
+            fgm |= fg ? 1u << k : 0u;
+            cnt += fg ? 1 : 0;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, fg);
-        if (lane == 0) {
-            W.tbits[(int64_t)tile * (kRounds * kWarps) + k * kWarps + warp] = bal;
-            s_bits[k * kWarps + warp] = bal;
-        }
-        fgm |= fg ? 1u << k : 0u;
-        cnt += fg ? 1 : 0;
     }
     __syncthreads();
     // union-find init: every large-error pixel's parent is the first pixel of its horizontal run
@@ -583,12 +603,12 @@ __global__ void __launch_bounds__(kScanThreads)
         const int tot = block_sum_int(run, wsm);
         if (tid == 0) {
             if (tot) atomicAdd(&c->n_large[i0][it], tot);
-            W.tstat[tile] = (unsigned long long)tot;
+            W.tcnt[tile] = (uint32_t)tot;
         }
     } else {
         if (run) atomicAdd(&c->n_large[run_img][it], run);
         const int tot = block_sum_int(cnt, wsm);
-        if (tid == 0) W.tstat[tile] = (unsigned long long)tot;
+        if (tid == 0) W.tcnt[tile] = (uint32_t)tot;
     }
     if (full_clear) {
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -607,13 +627,28 @@ __global__ void __launch_bounds__(kScanThreads) k_threshold_write(JointWs W) {
     constexpr int kWarps = kScanThreads / 32;
     __shared__ int s_cnt[kRounds * kWarps];   // per (round, warp): offset within the tile
     __shared__ int wsm[8];
-    __shared__ long long s_ll[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
-    // the list offset of this tile: counts of the tiles before it, summed in a fixed order
-    long long part = 0;
-    for (int k = tid; k < tile; k += kScanThreads) part += (long long)__ldcg(&W.tstat[k]);
-    const long long excl = block_sum_ll(part, s_ll);
+    // a tile without large-error pixels writes nothing (the last one still records the length)
+    if (tile != (int)gridDim.x - 1 && __ldcg(&W.tcnt[tile]) == 0u) return;
+    // the list offset of this tile: counts of the tiles before it (four per 16-byte load, the
+    // loads of a thread issued together), summed in a fixed order
+    constexpr int kCntPer = 4;   // 16-byte loads per thread and round
+    int part = 0;
+    const uint4* c4 = reinterpret_cast<const uint4*>(W.tcnt);
+    for (int g0 = tid * kCntPer; g0 * 4 < tile; g0 += kScanThreads * kCntPer) {
+        uint4 v[kCntPer];
+#pragma unroll
+        for (int k = 0; k < kCntPer; ++k)
+            v[k] = (g0 + k) * 4 < tile ? __ldcg(&c4[g0 + k]) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int k = 0; k < kCntPer; ++k) {
+            const int t = (g0 + k) * 4;
+            part += (t < tile ? (int)v[k].x : 0) + (t + 1 < tile ? (int)v[k].y : 0) +
+                    (t + 2 < tile ? (int)v[k].z : 0) + (t + 3 < tile ? (int)v[k].w : 0);
+        }
+    }
+    const long long excl = block_sum_int(part, wsm);
     const uint32_t* bits = W.tbits + (int64_t)tile * (kRounds * kWarps);
     const int v = tid < kRounds * kWarps ? __popc(__ldcg(&bits[tid])) : 0;
     int ex;
@@ -3231,7 +3266,8 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
     }
     prof::mark(slot, evi++, st);
     k_ctl_init<<<grid_cap(nq > kMaxSlots ? nq : kMaxSlots, T), T, 0, st>>>(
-        ws.ctl, ws.stamp, nq, ws.slot_word, n, ws.tstat, (np + kScanTile - 1) / kScanTile + 1);
+        ws.ctl, ws.stamp, nq, ws.slot_word, n, ws.tcnt,
+        (((np + kScanTile - 1) / kScanTile + 1) + 3) & ~(int64_t)3);
     GLU_DBG_MARK(st, 1);
     // initialise every LR image by regular grid downsampling, Theta and E by Algorithm 1
     k_grid_batch<<<grid_cap(nq, T), T, 0, st>>>(B);

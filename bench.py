@@ -635,14 +635,15 @@ def measure_batch(api, torch, dev, timed):
 def run_kernel_case(args):
     """One kernel on an input larger than L2, a few launches (the target of an ncu capture):
     search / apply / backward / exact (GLU*, float32 weights) on a 7680x4320 guide at scale 8,
-    window 5; trials = the joint 4K workload (its first trial launch is iteration 1)."""
+    window 5; trials = the joint 4K workload (its first trial launch is iteration 1); tail = the
+    bench step's LR operator + Eq. 1 after the 4K joint call."""
     import torch
     import __graft_entry__ as g
     g.build()
     from paper_2307_09582_gb300 import api
     from paper_2307_09582_gb300.inputs import Scene, joint_4k_scene, render_u8
     dev = torch.device("cuda", 0)
-    if args.variant is not None and args.kernel_case in ("search", "apply"):
+    if args.variant is not None and args.kernel_case in ("search", "apply", "tail"):
         api.tune_force(api.GLU_TUNE_SEARCH if args.kernel_case == "search" else api.GLU_TUNE_APPLY,
                        args.variant)
     if args.kernel_case == "trials":
@@ -650,6 +651,25 @@ def run_kernel_case(args):
         hr = torch.from_numpy(img).to(dev)
         for _ in range(args.case_reps):
             api.glu_joint_optimize(hr, SCALE, api.glu_params(S=WIN, N=NITER), stats=False)
+        torch.cuda.synchronize()
+        return 0
+    if args.kernel_case == "tail":
+        # the bench step's tail on its own inputs: the 4K joint result, then per rep an L2 flush
+        # (a 256 MB write) and the LR operator + Eq. 1 (glu_apply_lrop)
+        img = render_u8(joint_4k_scene())
+        hr = torch.from_numpy(img).to(dev)
+        H, W = img.shape[:2]
+        h, w = api.lr_dims(H, W, SCALE)
+        lr = torch.empty((h, w, 3), dtype=torch.uint8, device=dev)
+        theta = api.Theta.empty(H, W, SCALE, WIN, api.GLU_W_UNORM16, dev)
+        api.glu_joint_optimize(hr, SCALE, api.glu_params(S=WIN, N=NITER), lr_out=lr,
+                               theta=theta, stats=False)
+        T = torch.empty((h, w, 3), dtype=torch.float32, device=dev)
+        out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        for _ in range(args.case_reps):
+            flush.zero_()
+            api.glu_apply_lrop(theta, lr, filter=0, sat=1.3, gamma=1.0, target=T, out=out)
         torch.cuda.synchronize()
         return 0
     H, W = 4320, 7680
@@ -755,7 +775,8 @@ def main():
     ap.add_argument("--impl", default="glu", choices=["glu", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
-    ap.add_argument("--kernel-case", choices=["search", "apply", "backward", "trials", "exact"],
+    ap.add_argument("--kernel-case",
+                    choices=["search", "apply", "backward", "trials", "exact", "tail"],
                     help="run one kernel on a profiling case and exit (no JSON line)")
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--quality-sweep", action="store_true",

@@ -2338,9 +2338,9 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
 // candidate; the team reduces (value, k) lexicographically, which is exactly the first minimum the
 // sequential scan finds (values compare exactly). More entries: one thread per two entries, which
 // run as one packed two-pixel search (search_pair_f4) when they lie in one block (they share the
-// window), else one after the other (search_pixel). An entry whose a is known is searched in full
-// as well: step 1 finds the same a (it was determined exactly), so the results are those of the
-// scalar search either way.
+// window), else one after the other (search_pixel). An entry whose a is known (step 1 decided it
+// exactly: integer distances) skips step 1 in the team form and is searched in full in the
+// packed form, which finds the same a: the results are those of the scalar search either way.
 constexpr int kTeam = 4;
 constexpr int kTeamMax = kTrialThreads / kTeam;
 
@@ -2395,18 +2395,24 @@ __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, Fa
     float ir, ig, ib;
     full_colour(F, pix, ir, ig, ib);
     float bd = kInf;
-    int a = K;
-    for (int k = tl; k < K; k += kTeam) {
-        const int dy = k / S, dx = k % S;
-        if (!((rm >> dy) & (cm >> dx) & 1u)) continue;
-        const float4 cc = lds_f4(&win[dy * RW + dx]);
-        const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
-        if (d2 < bd) {
-            bd = d2;
-            a = k;
+    int a = ((e >> 20) & 0xFF) - 1;   // >= 0: step 1 already decided a (exactly: integer distances)
+    if (a >= 0) {
+        const float4 ca = lds_f4(&win[(a / S) * RW + (a % S)]);
+        bd = dist2(ca.x - ir, ca.y - ig, ca.z - ib);
+    } else {
+        a = K;
+        for (int k = tl; k < K; k += kTeam) {
+            const int dy = k / S, dx = k % S;
+            if (!((rm >> dy) & (cm >> dx) & 1u)) continue;
+            const float4 cc = lds_f4(&win[dy * RW + dx]);
+            const float d2 = dist2(cc.x - ir, cc.y - ig, cc.z - ib);
+            if (d2 < bd) {
+                bd = d2;
+                a = k;
+            }
         }
+        team_min(bd, a, mask);
     }
-    team_min(bd, a, mask);
     const StepB sb = step_b_setup(lds_f4(&win[(a / S) * RW + (a % S)]), bd, ir, ig, ib, B.eps255);
     float bkey = kInf;
     int b = K;

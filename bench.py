@@ -37,7 +37,8 @@ OPS_PER_CANDIDATE = 27
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of every k_trials launch of
 # `bench.py --kernel-case trials --case-reps 1`), and the digest of the kernel sources it was
 # taken on: once the sources differ, the figure no longer describes the kernel and is not reported
-TRIALS_DRAM = dict(bytes_per_call=(91.5 + 40.2) * 1e6, sources_sha256="unset")
+TRIALS_DRAM = dict(bytes_per_call=(94.016 + 43.740) * 1e6,
+                   sources_sha256="3337969d2390b8178166874fd53f861a283ffe1c56aaec4c58f578d9716cab0d")
 TRIALS_SOURCES = ("k_joint.cu", "search.cuh", "common.cuh")
 
 

@@ -149,7 +149,8 @@ __global__ void k_op_point(const float* X, int h, int w, int64_t pitch, float* Y
 // values as k_op_filter3 followed by k_op_point (the intermediate is a float either way). A CTA
 // owns a kLrTile x kLrTile tile: it stages the tile and a one-pixel ring (coordinates clamped to
 // the image, so the ring repeats the edge as the filter's clamped taps do) in shared memory with
-// coalesced row loads, then every thread filters its pixel from there, taps in the same order.
+// coalesced row loads, converted to [0, 1] once there (x / 255 for uint8: the same value every
+// tap would compute), then every thread filters its pixel from there, taps in the same order.
 constexpr int kLrTile = 16;
 
 template <typename TX>
@@ -158,12 +159,12 @@ __global__ void __launch_bounds__(kLrTile * kLrTile)
             float sat, float gamma) {
     griddep_launch_dependents();   // a dependent apply may start loading codes and weights
     constexpr int RW = kLrTile + 2;
-    __shared__ TX tile[RW * RW * 3];
+    __shared__ float tile[RW * RW * 3];
     const int v0 = blockIdx.y * kLrTile, u0 = blockIdx.x * kLrTile;
     for (int i = threadIdx.x; i < RW * RW * 3; i += blockDim.x) {
         const int rr = i / (RW * 3), rem = i - rr * (RW * 3), cc = rem / 3, c = rem - cc * 3;
         const int v = min(max(v0 - 1 + rr, 0), h - 1), u = min(max(u0 - 1 + cc, 0), w - 1);
-        tile[i] = X[(int64_t)v * pitch + (int64_t)u * 3 + c];
+        tile[i] = op_in(X[(int64_t)v * pitch + (int64_t)u * 3 + c]);
     }
     __syncthreads();
     const int tv = threadIdx.x / kLrTile, tu = threadIdx.x % kLrTile;
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kLrTile * kLrTile)
     if (v >= h || u >= w) return;
     float c3[3];
     for (int c = 0; c < 3; ++c)
-        c3[c] = filter < 0 ? op_in(tile[((tv + 1) * RW + tu + 1) * 3 + c])
+        c3[c] = filter < 0 ? tile[((tv + 1) * RW + tu + 1) * 3 + c]
                            : filter3_at(tile + (tv * RW + tu) * 3 + c, 3, 3, 3, RW * 3, 1, 1, 0,
                                         filter);
     point_op(c3, sat, gamma);

@@ -2195,19 +2195,18 @@ __device__ bool run_task(const JBatch& B, const TrialCtx& X, float4* win, int j,
 // memory, every affected block is re-searched by one warp against it, and the new Theta / E stay
 // in shared memory until the decision. A kept trial writes them (and the new LR colours) out; a
 // rolled-back trial writes nothing, so the global state never holds a rejected trial. The
-// arithmetic and the summation order (per block: Kahan per lane over the block's pixels in raster
-// order, then a butterfly; blocks summed in fixed point) are those of the general path below.
+// arithmetic is that of the general path below, and so are the sums: every pixel's error rounded
+// to 2^-32 units and added as 64-bit integers, exact in any order.
 
-// The re-search of a trial in three passes, so that the few pixels that need a full search do
-// not hold up whole warps:
-//   pass 1 (a warp per block): load each pixel's guide colour, previous error and pair; with
-//     `incr` (STRICT: Theta is Algorithm 1 on the LR image before the trial) re-search it exactly
-//     from its previous pair when the replaced LR pixels in its window (at most kMaxChg) are
-//     neither its a nor its b and do not become its a; otherwise queue it for a full search
-//     (entry: pixel index, block, and the new a when only step 2 must be redone);
-//   pass 2 (every thread of the CTA): the queued searches;
-//   pass 3 (a warp per block): the block's old and new error sums, Kahan per lane over the
-//     block's pixels in raster order, then a butterfly (the order of the general path).
+// The re-search of a trial in two passes, so that the few pixels that need a full search do not
+// hold up whole warps:
+//   pass 1 (a warp per block): with `incr` (STRICT: Theta is Algorithm 1 on the LR image before
+//     the trial) re-search each pixel exactly from its previous pair when the replaced LR pixels
+//     in its window (at most kMaxChg) are neither its a nor its b and do not become its a;
+//     otherwise queue it for a full search (entry: pixel index, block, and the new a when only
+//     step 2 must be redone);
+//   pass 2 (every thread of the CTA): the queued searches.
+// e1 is summed as the pixels finish in either pass; e0 was summed while the pixels were staged.
 
 __device__ __forceinline__ int full_entry(int pix, int bi, int a_known) {
     return pix | (bi << 12) | ((a_known + 1) << 20);

@@ -34,6 +34,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <atomic>
 #include <memory>
 #include <mutex>
@@ -2332,20 +2333,19 @@ __device__ __noinline__ void fast_block_pass(const JBatch& B, const JointWs& W_,
     }
 }
 
-// Queued full searches (entries from fast_block_pass). Up to kTeamMax entries (one round of the
-// CTA): a team of kTeam consecutive lanes per entry, each lane scanning every kTeam-th window
-// candidate; the team reduces (value, k) lexicographically, which is exactly the first minimum the
-// sequential scan finds (values compare exactly). More entries: one thread per two entries, which
+// Queued full searches (entries from fast_block_pass). While one round of the CTA covers them: a
+// team of TEAM consecutive lanes per entry (4, 2 or 1: the widest that fits), each lane scanning
+// every TEAM-th window candidate; the team reduces (value, k) lexicographically, which is exactly
+// the first minimum the sequential scan finds (values compare exactly). More entries than
+// threads: one thread per two entries, which
 // run as one packed two-pixel search (search_pair_f4) when they lie in one block (they share the
 // window), else one after the other (search_pixel). An entry whose a is known (step 1 decided it
 // exactly: integer distances) skips step 1 in the team form and is searched in full in the
 // packed form, which finds the same a: the results are those of the scalar search either way.
-constexpr int kTeam = 4;
-constexpr int kTeamMax = kTrialThreads / kTeam;
-
+template <int TEAM>
 __device__ __forceinline__ void team_min(float& v, int& k, unsigned mask) {
 #pragma unroll
-    for (int o = 1; o < kTeam; o <<= 1) {
+    for (int o = 1; o < TEAM; o <<= 1) {
         const float ov = __shfl_xor_sync(mask, v, o);
         const int ok = __shfl_xor_sync(mask, k, o);
         if (ov < v || (ov == v && ok < k)) {
@@ -2382,8 +2382,8 @@ __device__ __forceinline__ const float4* full_window(const JImg& I, const FastSm
     return &F.region[(bv - r - RV0) * RW + (bu - r - RU0)];
 }
 
-// One entry by a team (scalar arithmetic).
-template <int S>
+// One entry by a team of TEAM lanes (scalar arithmetic).
+template <int S, int TEAM>
 __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, FastSmem& F, int RW,
                                               int RV0, int RU0, int e, int tl, unsigned mask,
                                               long long& acc) {
@@ -2400,7 +2400,7 @@ __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, Fa
         bd = dist2(ca.x - ir, ca.y - ig, ca.z - ib);
     } else {
         a = K;
-        for (int k = tl; k < K; k += kTeam) {
+        for (int k = tl; k < K; k += TEAM) {
             const int dy = k / S, dx = k % S;
             if (!((rm >> dy) & (cm >> dx) & 1u)) continue;
             const float4 cc = lds_f4(&win[dy * RW + dx]);
@@ -2410,12 +2410,12 @@ __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, Fa
                 a = k;
             }
         }
-        team_min(bd, a, mask);
+        team_min<TEAM>(bd, a, mask);
     }
     const StepB sb = step_b_setup(lds_f4(&win[(a / S) * RW + (a % S)]), bd, ir, ig, ib, B.eps255);
     float bkey = kInf;
     int b = K;
-    for (int k = tl; k < K; k += kTeam) {
+    for (int k = tl; k < K; k += TEAM) {
         const int dy = k / S, dx = k % S;
         if (!((rm >> dy) & (cm >> dx) & 1u)) continue;
         const float4 cc = lds_f4(&win[dy * RW + dx]);
@@ -2426,7 +2426,7 @@ __device__ __noinline__ void fast_full_search(const JBatch& B, const JImg& I, Fa
             b = k;
         }
     }
-    team_min(bkey, b, mask);
+    team_min<TEAM>(bkey, b, mask);
     if (tl == 0) {
         SearchOut o;
         o.ka = a;
@@ -2674,19 +2674,30 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
     if (tid == 0 && j < kTraceMax) g_trace[X.it][j][9] = (unsigned long long)nfull;
 #endif
     GLU_WSTAMP(X.it, j, 2);
-    if (nfull <= kTeamMax) {   // CTA-uniform choice (see fast_full_search)
-        const int tl = tid % kTeam;
-        const unsigned mask = ((1u << kTeam) - 1u) << ((tid & 31) - tl);
-        for (int t = tid / kTeam; t < nfull; t += nthr / kTeam) {
+    // one round of the CTA: teams of 4, 2 or 1 lanes per queued pixel (a CTA-uniform choice, see
+    // fast_full_search); longer queues: one thread per two pixels (packed when they share a block)
+    const int team = nfull <= nthr / 4 ? 4 : nfull <= nthr / 2 ? 2 : nfull <= nthr ? 1 : 0;
+    auto teams = [&](auto tw) {
+        constexpr int TW = decltype(tw)::value;
+        const int tl = tid % TW;
+        const unsigned mask = ((TW == 32 ? 0xFFFFFFFFu : (1u << TW) - 1u)) << ((tid & 31) - tl);
+        for (int t = tid / TW; t < nfull; t += nthr / TW) {
             const int e = F.full[t];
             switch (I.S) {
-                case 1: fast_full_search<1>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
-                case 3: fast_full_search<3>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
-                case 5: fast_full_search<5>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
-                case 7: fast_full_search<7>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
-                default: fast_full_search<9>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                case 1: fast_full_search<1, TW>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                case 3: fast_full_search<3, TW>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                case 5: fast_full_search<5, TW>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                case 7: fast_full_search<7, TW>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
+                default: fast_full_search<9, TW>(B, I, F, RW, RV0, RU0, e, tl, mask, acc1); break;
             }
         }
+    };
+    if (team == 4) {
+        teams(std::integral_constant<int, 4>());
+    } else if (team == 2) {
+        teams(std::integral_constant<int, 2>());
+    } else if (team == 1) {
+        teams(std::integral_constant<int, 1>());
     } else {
         for (int t = tid; 2 * t < nfull; t += nthr) {
             const int e0 = F.full[2 * t], e1 = 2 * t + 1 < nfull ? F.full[2 * t + 1] : -1;

@@ -2501,20 +2501,12 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
         sh.searched = 0;
         sh.ok = 1;
     }
-    for (int t = tid; t < nraw; t += nthr) F.rawq[t] = (int)((int64_t)W_.qlist[st.y + t] - I.q0);
     __syncthreads();
-    // distinct blocks Q (first occurrences) and their bounding box
+    // the component's LR blocks (repeats are possible where owner slots overflowed) and their
+    // bounding box
     for (int t = tid; t < nraw; t += nthr) {
-        const int q = F.rawq[t];
-        bool first = true;
-        for (int k = 0; k < t; ++k)
-            if (F.rawq[k] == q) {
-                first = false;
-                break;
-            }
-        if (!first) continue;
-        const int idx = atomicAdd(&sh.nq, 1);
-        if (idx < kFastQ) F.qs[idx] = q;
+        const int q = (int)((int64_t)W_.qlist[st.y + t] - I.q0);
+        F.rawq[t] = q;
         const int v = q / I.w, u = q % I.w;
         atomicMin(&sh.vmin, v);
         atomicMax(&sh.vmax, v);
@@ -2522,24 +2514,35 @@ __device__ bool fast_trial(const JBatch& B, const TrialCtx& X, const JImg& I, in
         atomicMax(&sh.umax, u);
     }
     __syncthreads();
-    const int nq = sh.nq;
     const int RV0 = sh.vmin - Rm, RU0 = sh.umin - Rm;
     const int RH = sh.vmax - sh.vmin + 1 + 2 * Rm, RW = sh.umax - sh.umin + 1 + 2 * Rm;
-    if (nq > kFastQ || RH * RW > kFastRegion) return false;
+    if (RH * RW > kFastRegion) return false;
     // region maps: Q blocks (index + 1) and the blocks to re-search
     for (int t = tid; t < RH * RW; t += nthr) {
         F.qmap[t] = 0;
         F.amap[t] = 0;
     }
     __syncthreads();
+    // distinct blocks Q: the first entry to claim a block's cell in the map numbers it (the
+    // numbering order does not matter: only the block <-> index pairing is used)
+    for (int t = tid; t < nraw; t += nthr) {
+        const int q = F.rawq[t];
+        const int cell = (q / I.w - RV0) * RW + (q % I.w - RU0);
+        unsigned short* qm = reinterpret_cast<unsigned short*>(&F.qmap[cell]);
+        if (atomicCAS(qm, (unsigned short)0, (unsigned short)0xFFFFu) != 0) continue;
+        const int idx = atomicAdd(&sh.nq, 1);
+        if (idx < kFastQ) {
+            F.qs[idx] = q;
+            F.qmap[cell] = (short)(idx + 1);
+        }
+    }
+    __syncthreads();
+    const int nq = sh.nq;
+    if (nq > kFastQ) return false;
     const int NA = (2 * Am + 1) * (2 * Am + 1);
     for (int t = tid; t < nq * NA; t += nthr) {
         const int q = F.qs[t / NA], nb = t % NA;
         const int v = q / I.w + nb / (2 * Am + 1) - Am, u = q % I.w + nb % (2 * Am + 1) - Am;
-        if (nb == 0) {
-            const int qv = q / I.w, qu = q % I.w;
-            F.qmap[(qv - RV0) * RW + (qu - RU0)] = (short)(t / NA + 1);
-        }
         if (v >= 0 && v < I.h && u >= 0 && u < I.w) F.amap[(v - RV0) * RW + (u - RU0)] = 1;
     }
     __syncthreads();

@@ -1121,7 +1121,7 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
     __shared__ unsigned nbits[kNbBits / 32];
     __shared__ short plist[kDepsWords * 32];   // marked bitmap positions of one round
     __shared__ int s_scan[32];
-    __shared__ int s_n, s_bad, s_vmin, s_vmax, s_umin, s_umax;
+    __shared__ int s_n, s_vmin, s_vmax, s_umin, s_umax;
     const int M = c->M_cur;
     const bool use_bits = M <= kDepsBits;
     if (use_bits)
@@ -1407,7 +1407,7 @@ struct SmallSmem {
         int eset[kSmallEdges];      // graph: edge keys i * kSmallFg + j (-1: empty)
     } u;
     int b[2 * kSmallFg];            // root ranks; then per component (pixels, blocks) counters
-    int q[kSmallFg];                // the distinct (component, block) pairs' blocks, qlist order
+    int q[kSmallFg];                // per list pixel: its (component, block) representative
     int2 tab[kSmallHash];           // (cell key, first entry); key -1: empty
     int ecid[kSmallFg];             // entry: component
     int eq[kSmallFg];               // entry: LR block
@@ -1630,22 +1630,22 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     __syncthreads();
     GLU_SMALL_STAMP(it, 5);
     // from here the list and the forest are no longer needed: their space holds the edge set
-    for (int t = tid; t < totq; t += nthr) S.q[t] = __ldcg(&W.qlist[t]);
     for (int t = tid; t < kSmallEdges; t += nthr) S.u.eset[t] = -1;
     __syncthreads();
     GLU_SMALL_STAMP(it, 6);
-    // graph: items (block t of the qlist, neighbouring cell) over the whole CTA; the component of
-    // qlist position t is the j with start.y[j] <= t < start.y[j + 1] (cntq holds the ends)
+    // graph: items (entry e = one (component, block) pair of the cell hash, neighbouring cell)
+    // over the whole CTA; the entry holds its component and block (no lookup in global memory)
     int* npred = cntp;   // per component: distinct predecessors
     for (int j = tid; j < M; j += nthr) npred[j] = 0;
     __syncthreads();
-    for (int t9 = tid; t9 < totq * 9; t9 += nthr) {
-        const int t = t9 / 9;
-        const int j = upper_bound_i(cntq, M, t);   // first j whose range ends after t
-        const JImg& I = B.im[img_of_p(B, W.roots[j])];
+    const int nent = S.nent;
+    for (int t9 = tid; t9 < nent * 9; t9 += nthr) {
+        const int e = t9 / 9;
+        const int j = S.ecid[e], q = S.eq[e];
+        const JImg& I = B.im[img_of_q(B, q)];
         const int D = B.strict ? I.S - 1 : (I.S - 1) / 2;
         const int C = D + 1, cw = (I.w + C - 1) / C, ch = (I.h + C - 1) / C;
-        const int lq = S.q[t] - (int)I.q0;
+        const int lq = q - (int)I.q0;
         const int v = lq / I.w, u = lq % I.w;
         const int cv = v / C + (t9 % 9) / 3 - 1, cu = u / C + (t9 % 9) % 3 - 1;
         if (cv < 0 || cv >= ch || cu < 0 || cu >= cw) continue;

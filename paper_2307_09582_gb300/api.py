@@ -540,16 +540,16 @@ def glu_joint_profile_read() -> dict:
 def joint_launches(N: int, graph: bool = False, multi_kernel_lists: int = 0) -> int:
     """Kernel launches one glu_joint_optimize call makes: control init, grid downsample, search
     and R_0 (2), then per iteration the threshold count and list-write passes, the one-CTA list
-    kernel, the multi-kernel list path (merge, flatten, root count, scan, root scatter, component
-    count, 3 scan, fill, dependency graph 5: 15 kernels), the trials, the list clear and the
-    residual update. Issued directly, every kernel launches (those with nothing to do return at
-    once). Replayed as a recorded graph (a repeated call), the 15 kernels of the multi-kernel
-    path sit in a conditional node and launch only in the iterations whose bit is set in the
-    stats' multi_kernel_lists."""
+    kernel, the multi-kernel list path (tile components, border merge, flatten, root count,
+    scan, root scatter, component count, 3 scan, fill, dependency graph 5: 16 kernels), the
+    trials, the list clear and the residual update. Issued directly, every kernel launches (those
+    with nothing to do return at once). Replayed as a recorded graph (a repeated call), the 16
+    kernels of the multi-kernel path sit in a conditional node and launch only in the iterations
+    whose bit is set in the stats' multi_kernel_lists."""
     if not graph:
-        return 5 + 21 * N
+        return 5 + 22 * N
     multi = bin(multi_kernel_lists & ((1 << N) - 1)).count("1")
-    return 5 + 6 * N + 15 * multi
+    return 5 + 6 * N + 16 * multi
 
 
 def tune_mode(on: bool) -> None:

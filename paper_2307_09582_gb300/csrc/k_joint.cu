@@ -489,12 +489,13 @@ __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int
 // Large-error set of the active images, its ordered list and the union-find init, in two passes
 // over tiles of kScanTile pixels (16 per thread, in rounds of 256 consecutive pixels) with no
 // waits between CTAs:
-//   k_threshold_count  marks E_p > tau, starts every large-error pixel as its own union-find root
-//                      (lab[p] = p), stores the tile's ballots (one 32-bit word per warp and
-//                      round) and its count; iteration 0 (full_clear) also sets every other
-//                      pixel's label to -1 and clears the owner slots (later iterations find them
-//                      cleared by k_lists_clear, which resets only the previous lists' pixels and
-//                      blocks)
+//   k_threshold_count  marks E_p > tau and stores the tile's ballots (one 32-bit word per warp
+//                      and round: together a raster bitmap of the large-error set, bit p of word
+//                      p / 32) and its count; iteration 0 (full_clear) also sets the label of
+//                      every pixel outside the set to -1 and clears the owner slots (later
+//                      iterations find them cleared by k_lists_clear, which resets only the
+//                      previous lists' pixels and blocks); the large-error pixels' labels are
+//                      written by the component kernels
 //   k_threshold_write  adds up the counts of the tiles before its own (a fixed-order block sum
 //                      over at most a few thousand L2-resident integers) and writes the tile's
 //                      large-error pixels to the list in raster order from the stored ballots
@@ -528,7 +529,6 @@ __global__ void __launch_bounds__(kScanThreads)
             e1[k] = act0 && p < B.np ? err[p] : 0.f;
         }
     }
-    __shared__ unsigned s_bits[kRounds * kWarps];   // the tile's ballots in raster order
     int run_img = -1, run = 0, cnt = 0;
     unsigned fgm = 0u;   // bit k: this thread's pixel of round k is a large-error pixel
     uint32_t* tb = W.tbits + (int64_t)tile * (kRounds * kWarps);
@@ -542,10 +542,7 @@ __global__ void __launch_bounds__(kScanThreads)
             const bool fg = act0 && in && e1[k] > B.tau;
             if (full_clear && in && !fg) W.lab[pl + k * kScanThreads] = -1;
             const unsigned bal = __ballot_sync(0xffffffffu, fg);
-            if (lane == 0) {
-                tb[k * kWarps + warp] = bal;
-                s_bits[k * kWarps + warp] = bal;
-            }
+            if (lane == 0) tb[k * kWarps + warp] = bal;
             fgm |= fg ? 1u << k : 0u;
         }
         run = cnt = __popc(fgm);
@@ -574,30 +571,9 @@ __global__ void __launch_bounds__(kScanThreads)
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, fg);
-            if (lane == 0) {
-                tb[k * kWarps + warp] = bal;
-                s_bits[k * kWarps + warp] = bal;
-            }
-            fgm |= fg ? 1u << k : 0u;
+            if (lane == 0) tb[k * kWarps + warp] = bal;
             cnt += fg ? 1 : 0;
         }
-    }
-    __syncthreads();
-    // union-find init: every large-error pixel's parent is the first pixel of its horizontal run
-    // (within the row and the tile; a run that continues from the previous tile is joined to it
-    // by the merge), so the trees start one level deep and the merge's finds stay short; the
-    // root of every component is still its smallest pixel
-    for (unsigned m = fgm; m; m &= m - 1) {
-        const int k = __ffs(m) - 1;
-        const int pos = k * kScanThreads + tid;   // position in the tile, raster order
-        const int64_t p = base + pos;
-        const int i = one ? i0 : img_of_p(B, p);
-        const int64_t rowstart = p - (p - B.im[i].p0) % B.im[i].W;
-        int wi = pos >> 5;
-        unsigned zeros = ~s_bits[wi] & ((1u << (pos & 31)) - 1u);
-        while (!zeros && wi > 0) zeros = ~s_bits[--wi];
-        const int64_t start = zeros ? base + wi * 32 + (32 - __clz(zeros)) : base;
-        W.lab[p] = (int)(start > rowstart ? start : rowstart);
     }
     // |E| per image (one atomic per CTA for a tile inside one image) and the tile's count
     if (one) {
@@ -719,6 +695,143 @@ __device__ __forceinline__ void uf_union(int* par, int a, int b) {
     }
 }
 
+// The same union-find on a CTA's shared-memory array.
+__device__ __forceinline__ int suf_find(int* par, int x) {
+    volatile int* vp = par;
+    for (;;) {
+        const int p = vp[x];
+        if (p == x) return x;
+        const int gp = vp[p];
+        if (gp != p) atomicMin(&par[x], gp);
+        x = p;
+    }
+}
+
+__device__ __forceinline__ void suf_union(int* par, int a, int b) {
+    for (;;) {
+        a = suf_find(par, a);
+        b = suf_find(par, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(&par[a], b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+// Components of the large-error set in two stages. Stage one (k_ccl_local): one warp per
+// kCclTile x kCclTile tile of an image finds the components of the tile's own large-error
+// pixels in shared memory, from the threshold pass's ballots (bit p of the raster bitmap is
+// E_p > tau), and labels every large-error pixel with the smallest pixel of its tile component.
+// Stage two (k_ccl_merge): the global union-find joins those labels across tile borders only.
+// Rows and columns are read in raster order, so the smallest pixel of a tile component is its
+// smallest global index and, after the merge, every component's root is its smallest pixel.
+constexpr int kCclTile = 32;
+
+// Neighbour rule of the border merge, for a large-error pixel with backward neighbours W, N
+// (and NW, NE with 8-connectivity), each flag meaning "inside the image and large-error".
+// With 8-connectivity a large-error N makes the other three redundant (W is joined to N as its
+// NE neighbour, NW and NE as N's W and E neighbours, each when that pixel is handled), and a
+// large-error W makes NW redundant (W's N): at most two unions per pixel. Bit 0: W, 1: N,
+// 2: NW, 3: NE.
+__device__ __forceinline__ unsigned ccl_edges(int conn, bool fw, bool fn, bool fnw, bool fne) {
+    if (conn != 8) return (fw ? 1u : 0u) | (fn ? 2u : 0u);
+    if (fn) return 2u;
+    return (fw ? 1u : (fnw ? 4u : 0u)) | (fne ? 8u : 0u);
+}
+
+// One warp per tile, lane r holding row r's bits: the tile's runs (maximal horizontal
+// segments, at most 16 per row) are the union-find's elements, numbered r * 16 + their order in
+// the row, which is raster order of their first pixels; a run is joined to every run of the row
+// above that touches it (8-connectivity: within one column to either side). With union by the
+// smaller number, every tile component's root is its first run, whose first pixel is the
+// component's smallest. Eight tiles side by side per CTA, no block-wide barrier: all tiles of a
+// 4K image are resident at once.
+constexpr int kCclRuns = kCclTile / 2;
+
+__device__ __forceinline__ int ccl_run(unsigned starts, int r, int cl) {
+    // the run holding column cl of a row whose run starts are `starts` (cl = 31: all bits)
+    return r * kCclRuns + __popc(starts & ((2u << cl) - 1u)) - 1;
+}
+
+__global__ void __launch_bounds__(256) k_ccl_local(const __grid_constant__ JBatch B, JointWs W) {
+    const JointCtl* c = W.ctl;
+    const int i = blockIdx.z;
+    const int iw = B.im[i].W, ih = B.im[i].H;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 8 + warp) * kCclTile, y0 = blockIdx.y * kCclTile;
+    if (x0 >= iw || y0 >= ih) return;
+    const int64_t rowp = B.im[i].p0 + (int64_t)y0 * iw + x0;
+    // the control words and the row's bitmap words in one round trip (the bitmap is read even
+    // when the pass is skipped: it is always allocated)
+    const int act_any = __ldcg(&c->active_any), small = __ldcg(&c->small_cur);
+    const int act = __ldcg(&c->active[i]);
+    unsigned m = 0u;
+    if (y0 + lane < ih) {
+        const int64_t p = rowp + (int64_t)lane * iw;
+        const int64_t wd = p >> 5;
+        const int sh = (int)(p & 31);
+        const unsigned lo = __ldcg(&W.tbits[wd]);
+        // the bits past the end of the batch are zero: the next word is needed only below it
+        const unsigned hi = sh && (wd + 1) * 32 < B.np ? __ldcg(&W.tbits[wd + 1]) : 0u;
+        m = __funnelshift_r(lo, hi, sh);
+        const int wv = iw - x0;
+        if (wv < kCclTile) m &= (1u << wv) - 1u;
+    }
+    if (!act_any || small || !act) return;
+    if (!__any_sync(0xffffffffu, m != 0u)) return;
+    __shared__ int par_s[8][kCclTile * kCclRuns];
+    __shared__ uint8_t rstart_s[8][kCclTile * kCclRuns];   // first column of each run
+    int* par = par_s[warp];
+    uint8_t* rstart = rstart_s[warp];
+    const unsigned st = m & ~(m << 1);   // first pixels of this row's runs
+    {
+        int j = 0;
+        for (unsigned b = st; b; b &= b - 1, ++j) {
+            par[lane * kCclRuns + j] = lane * kCclRuns + j;
+            rstart[lane * kCclRuns + j] = (uint8_t)(__ffs(b) - 1);
+        }
+    }
+    const unsigned up = __shfl_up_sync(0xffffffffu, m, 1);
+    __syncwarp();
+    if (lane > 0 && m && up) {
+        const unsigned ust = up & ~(up << 1);
+        int j = 0;
+        for (unsigned b = st; b; b &= b - 1, ++j) {
+            const int a = __ffs(b) - 1;
+            const unsigned rest = m >> a;
+            const int len = __ffs(~rest) ? __ffs(~rest) - 1 : 32 - a;   // run [a, a + len)
+            const int lo = B.conn == 8 && a > 0 ? a - 1 : a;
+            const int hi = B.conn == 8 ? min(a + len, kCclTile - 1) : a + len - 1;
+            const unsigned span = (hi - lo == 31 ? 0xffffffffu : ((2u << (hi - lo)) - 1u)) << lo;
+            const unsigned ov = up & span;
+            // one union per run of the row above that touches this one
+            for (unsigned t = ov & ~(ov << 1); t; t &= t - 1)
+                suf_union(par, lane * kCclRuns + j, ccl_run(ust, lane - 1, __ffs(t) - 1));
+        }
+    }
+    __syncwarp();
+    // labels: each lane its own row's runs, every pixel of a run the root run's first pixel (the
+    // finds of the lanes run together; a parent only decreases, so the forest stays valid)
+    int j = 0;
+    int* dst = W.lab + rowp + (int64_t)lane * iw;
+    for (unsigned b = st; b; b &= b - 1, ++j) {
+        const int a = __ffs(b) - 1;
+        const unsigned rest = m >> a;
+        const int len = __ffs(~rest) ? __ffs(~rest) - 1 : 32 - a;
+        const int root = suf_find(par, lane * kCclRuns + j);
+        const int g = (int)(rowp + (int64_t)(root / kCclRuns) * iw + rstart[root]);
+        for (int k = 0; k < len; ++k) dst[a + k] = g;
+    }
+}
+
+// Stage two: the edges of the neighbour rule that cross a tile border, through the global
+// union-find (every large-error pixel's label is its tile component's root). Only pixels in a
+// tile's first row or first or last column have such edges.
 __global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const int* fgl,
                             const JointCtl* c) {
     if (skip_lists(c)) return;
@@ -728,27 +841,18 @@ __global__ void k_ccl_merge(const __grid_constant__ JBatch B, int* lab, const in
         const JImg& I = B.im[img_of_p(B, p)];
         const int64_t lp = p - I.p0;
         const int y = (int)(lp / I.W), x = (int)(lp % I.W);
-        // backward neighbours inside the image: W, N (and NW, NE for 8-connectivity). With
-        // 8-connectivity a large-error N makes the other three redundant (W is joined to N as
-        // its NE neighbour, NW and NE as N's W and E neighbours, each when that pixel is
-        // merged), and a large-error W makes NW redundant (W's N): at most two unions per pixel.
-        const bool fw = x > 0 && __ldcg(&lab[p - 1]) >= 0;
+        const int r = y % kCclTile, cl = x % kCclTile;
+        if (r != 0 && cl != 0 && cl != kCclTile - 1) continue;
         const int64_t up = p - I.W;
+        const bool fw = x > 0 && __ldcg(&lab[p - 1]) >= 0;
         const bool fn = y > 0 && __ldcg(&lab[up]) >= 0;
-        if (B.conn == 8) {
-            if (fn) {
-                uf_union(lab, (int)p, (int)up);
-            } else {
-                if (fw) uf_union(lab, (int)p, (int)p - 1);
-                else if (y > 0 && x > 0 && __ldcg(&lab[up - 1]) >= 0)
-                    uf_union(lab, (int)p, (int)up - 1);
-                if (y > 0 && x + 1 < I.W && __ldcg(&lab[up + 1]) >= 0)
-                    uf_union(lab, (int)p, (int)up + 1);
-            }
-        } else {
-            if (fw) uf_union(lab, (int)p, (int)p - 1);
-            if (fn) uf_union(lab, (int)p, (int)up);
-        }
+        const bool fnw = B.conn == 8 && y > 0 && x > 0 && __ldcg(&lab[up - 1]) >= 0;
+        const bool fne = B.conn == 8 && y > 0 && x + 1 < I.W && __ldcg(&lab[up + 1]) >= 0;
+        const unsigned ed = ccl_edges(B.conn, fw, fn, fnw, fne);
+        if ((ed & 1u) && cl == 0) uf_union(lab, (int)p, (int)p - 1);
+        if ((ed & 2u) && r == 0) uf_union(lab, (int)p, (int)up);
+        if ((ed & 4u) && (r == 0 || cl == 0)) uf_union(lab, (int)p, (int)up - 1);
+        if ((ed & 8u) && (r == 0 || cl == kCclTile - 1)) uf_union(lab, (int)p, (int)up + 1);
     }
 }
 
@@ -3315,6 +3419,13 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
     prof::mark(slot, evi++, st);
 
     const int tiles_a = (int)((np + kScanTile - 1) / kScanTile);
+    int wmax = 1, hmax = 1;
+    for (int k = 0; k < n; ++k) {
+        wmax = std::max(wmax, B.im[k].W);
+        hmax = std::max(hmax, B.im[k].H);
+    }
+    const dim3 ccl_grid((wmax + 8 * kCclTile - 1) / (8 * kCclTile), (hmax + kCclTile - 1) / kCclTile,
+                        n);
     const int tiles_b = (int)((ws.mcap + kScanTile - 1) / kScanTile);
     // the list passes over tiles of the large-error list or of the components: grid-stride
     // over a small grid (the lists are short after the first iteration)
@@ -3369,6 +3480,8 @@ static int issue_joint(const JointItem* items, int n, const JointCommon& cm, con
                                                        nullptr, 0, cudaStreamCaptureModeRelaxed));
             ls = body;
         }
+        k_ccl_local<<<ccl_grid, 256, 0, ls>>>(B, ws);
+        GLU_DBG_MARK(ls, 27);
         k_ccl_merge<<<lgrid, T, 0, ls>>>(B, ws.lab, fgl, ws.ctl);
         GLU_DBG_MARK(ls, 9);
         k_ccl_flatten<<<lgrid, T, 0, ls>>>(ws.lab, fgl, ws.ctl);

@@ -1217,7 +1217,7 @@ __device__ __forceinline__ void add_edge(const JBatch& B, const JointWs& W, Join
     if (k < edge_cap(B)) edge_list(W)[k] = make_int2(i, j);
 }
 
-__global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
+__global__ void __launch_bounds__(256, 4) k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
     JointCtl* c = W.ctl;
     if (skip_lists(c)) return;
     __shared__ int cand[kCandMax];
@@ -1308,14 +1308,16 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
                 __syncthreads();
             }
         }
-        // one candidate predecessor i < j: with the bitmap, the first sighting emits it
+        // one candidate predecessor i < j: with the bitmap, the first sighting records it (its
+        // edge is appended with the component's others, one slot reservation for all of them;
+        // past kCandMax records, at once)
         auto offer = [&](int i) {
             if (use_bits) {
                 const unsigned bit = 1u << (i & 31);
                 if (atomicOr(&bits[i >> 5], bit) & bit) return;
                 const int slot = atomicAdd(&s_n, 1);
                 if (slot < kCandMax) cand[slot] = i;
-                add_edge(B, W, c, i, j);
+                else add_edge(B, W, c, i, j);
             } else {
                 const int slot = atomicAdd(&s_n, 1);
                 if (slot < kCandMax) cand[slot] = i;
@@ -1410,6 +1412,15 @@ __global__ void __launch_bounds__(256) k_deps(const __grid_constant__ JBatch B, 
         int npred;
         if (use_bits) {
             npred = n;
+            const int nrec = min(n, kCandMax);
+            if (threadIdx.x == 0) s_vmin = nrec ? atomicAdd(&c->nedge, nrec) : 0;
+            __syncthreads();
+            const int e0 = s_vmin, ecap = edge_cap(B);
+            for (int t = threadIdx.x; t < nrec; t += blockDim.x) {
+                const int i = cand[t];
+                atomicAdd(&W.dag_cnt[i].x, 1);
+                if (e0 + t < ecap) edge_list(W)[e0 + t] = make_int2(i, j);
+            }
             // clear the bits this component set (every set bit is one of its predecessors)
             if (n <= kCandMax) {
                 for (int t = threadIdx.x; t < n; t += blockDim.x) bits[cand[t] >> 5] = 0u;
@@ -1737,51 +1748,65 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     for (int t = tid; t < kSmallEdges; t += nthr) S.u.eset[t] = -1;
     __syncthreads();
     GLU_SMALL_STAMP(it, 6);
-    // graph: items (entry e = one (component, block) pair of the cell hash, neighbouring cell)
-    // over the whole CTA; the entry holds its component and block (no lookup in global memory)
+    // graph: tpe threads per entry (one (component, block) pair of the cell hash, which holds its
+    // component and block: no lookup in global memory), each working out the entry's block, cell
+    // and image constants once and scanning 9 / tpe of the nine cells around it (its own and the
+    // eight neighbours). tpe (1, 3 or 9) minimises rounds x (set-up + cells per thread), the
+    // set-up costing about three cell scans: 9 for short lists, fewer for long ones.
     int* npred = cntp;   // per component: distinct predecessors
     for (int j = tid; j < M; j += nthr) npred[j] = 0;
     __syncthreads();
     const int nent = S.nent;
-    for (int t9 = tid; t9 < nent * 9; t9 += nthr) {
-        const int e = t9 / 9;
+    int tpe = 9;
+    {
+        int best = 0x7fffffff;
+        for (int t = 9; t >= 1; t /= 3) {
+            const int cost = (nent * t + nthr - 1) / nthr * (3 + 9 / t);
+            if (cost < best) { best = cost; tpe = t; }
+        }
+    }
+    for (int et = tid; et < nent * tpe; et += nthr) {
+        const int e = et / tpe, sub = et - e * tpe;
         const int j = S.ecid[e], q = S.eq[e];
         const JImg& I = B.im[img_of_q(B, q)];
         const int D = B.strict ? I.S - 1 : (I.S - 1) / 2;
         const int C = D + 1, cw = (I.w + C - 1) / C, ch = (I.h + C - 1) / C;
         const int lq = q - (int)I.q0;
         const int v = lq / I.w, u = lq % I.w;
-        const int cv = v / C + (t9 % 9) / 3 - 1, cu = u / C + (t9 % 9) % 3 - 1;
-        if (cv < 0 || cv >= ch || cu < 0 || cu >= cw) continue;
-        const int key = (int)(I.q0 + (int64_t)cv * cw + cu);
-        int h = hash_slot(key, kSmallHash - 1);
-        int ent = -1;
-        for (int k = 0; k < kSmallHash; ++k) {
-            const int kk = S.tab[h].x;
-            if (kk == key) { ent = S.tab[h].y; break; }
-            if (kk == -1) break;
-            h = (h + 1) & (kSmallHash - 1);
-        }
-        for (int g = 0; ent >= 0 && g < kSmallFg; ++g, ent = S.enext[ent]) {
-            const int i = S.ecid[ent];
-            if (i >= j) continue;
-            const int lq2 = S.eq[ent] - (int)I.q0;
-            const int dv = lq2 / I.w - v, du = lq2 % I.w - u;
-            if (dv < -D || dv > D || du < -D || du > D) continue;
-            const int ekey = i * kSmallFg + j;
-            int eh = hash_slot(ekey, kSmallEdges - 1);
-            bool inserted = false;
-            int k = 0;
-            for (; k < kSmallEdges; ++k) {
-                const int old = atomicCAS(&S.u.eset[eh], -1, ekey);
-                if (old == -1) { inserted = true; break; }
-                if (old == ekey) break;
-                eh = (eh + 1) & (kSmallEdges - 1);
+        const int cv0 = v / C, cu0 = u / C;
+        for (int nc = sub; nc < 9; nc += tpe) {
+            const int cv = cv0 + nc / 3 - 1, cu = cu0 + nc % 3 - 1;
+            if (cv < 0 || cv >= ch || cu < 0 || cu >= cw) continue;
+            const int key = (int)(I.q0 + (int64_t)cv * cw + cu);
+            int h = hash_slot(key, kSmallHash - 1);
+            int ent = -1;
+            for (int k = 0; k < kSmallHash; ++k) {
+                const int kk = S.tab[h].x;
+                if (kk == key) { ent = S.tab[h].y; break; }
+                if (kk == -1) break;
+                h = (h + 1) & (kSmallHash - 1);
             }
-            if (k == kSmallEdges) S.bad = 1;   // the set is full
-            if (inserted) {
-                atomicAdd(&npred[j], 1);
-                atomicAdd(&S.nedge, 1);
+            for (int g = 0; ent >= 0 && g < kSmallFg; ++g, ent = S.enext[ent]) {
+                const int i = S.ecid[ent];
+                if (i >= j) continue;
+                const int lq2 = S.eq[ent] - (int)I.q0;
+                const int dv = lq2 / I.w - v, du = lq2 % I.w - u;
+                if (dv < -D || dv > D || du < -D || du > D) continue;
+                const int ekey = i * kSmallFg + j;
+                int eh = hash_slot(ekey, kSmallEdges - 1);
+                bool inserted = false;
+                int k = 0;
+                for (; k < kSmallEdges; ++k) {
+                    const int old = atomicCAS(&S.u.eset[eh], -1, ekey);
+                    if (old == -1) { inserted = true; break; }
+                    if (old == ekey) break;
+                    eh = (eh + 1) & (kSmallEdges - 1);
+                }
+                if (k == kSmallEdges) S.bad = 1;   // the set is full
+                if (inserted) {
+                    atomicAdd(&npred[j], 1);
+                    atomicAdd(&S.nedge, 1);
+                }
             }
         }
     }
@@ -3228,6 +3253,10 @@ static int small_comp_setup() {
     std::call_once(once, [] {
         if (cudaFuncSetAttribute(k_small_comp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(SmallSmem)) != cudaSuccess)
+            rc = GLU_ERR_CUDA;
+        // k_deps: four CTAs per SM (its whole grid resident) need the largest shared-memory split
+        if (cudaFuncSetAttribute(k_deps, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             rc = GLU_ERR_CUDA;
     });
     return rc;

@@ -1639,23 +1639,30 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
             settled = true;
             break;
         }
-        for (int jr = 0; jr < 32; ++jr) {   // pointer jumping: at most log2(kSmallFg) + 1 rounds
-            int moved = 0;
+        // every tree a star again, in one round: each thread walks from its pixels to the root,
+        // halving the path on the way. A parent is always a smaller index than its child and
+        // the root the smallest of its tree, so the writes (atomicMin) only ever move a pixel
+        // closer to its root, whichever threads walk through it, and leave each of this
+        // thread's pixels under the root itself
 #pragma unroll
-            for (int k = 0; k < kSmallPer; ++k) {
-                const int e = tid + k * nthr;
-                if (e >= nfg) continue;
-                const int pe = A[e], g = A[pe];
-                if (g != pe) {
-                    A[e] = g;
-                    moved = 1;
+        for (int k = 0; k < kSmallPer; ++k) {
+            const int e = tid + k * nthr;
+            if (e >= nfg) continue;
+            int x = e;
+            for (;;) {
+                const int px = A[x], g = A[px];
+                if (g == px) {
+                    if (x != e) atomicMin((int*)&A[e], px);
+                    break;
                 }
+                atomicMin((int*)&A[x], g);
+                x = g;
             }
-#ifdef GLU_TRIAL_TRACE
-            if (threadIdx.x == 0) g_small_t[it][11] = (unsigned long long)(++n_jumps);
-#endif
-            if (!__syncthreads_or(moved)) break;
         }
+#ifdef GLU_TRIAL_TRACE
+        if (threadIdx.x == 0) g_small_t[it][11] = (unsigned long long)(++n_jumps);
+#endif
+        __syncthreads();
     }
     if (!settled) return;   // nothing global written yet: the multi-kernel path runs
     GLU_SMALL_STAMP(it, 1);

@@ -486,7 +486,7 @@ __global__ void k_resid_final(const __grid_constant__ JBatch B, JointCtl* c, int
 
 // ----------------------------------------------------------------------- threshold and CCL
 
-// Large-error set of the active images, its ordered list and the union-find init, in two passes
+// Large-error set of the active images, its bitmap and its ordered list, in two passes
 // over tiles of kScanTile pixels (16 per thread, in rounds of 256 consecutive pixels) with no
 // waits between CTAs:
 //   k_threshold_count  marks E_p > tau and stores the tile's ballots (one 32-bit word per warp

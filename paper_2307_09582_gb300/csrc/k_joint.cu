@@ -1204,6 +1204,11 @@ constexpr int kNbMinPairs = 256;
 constexpr int kDepsWords = 256;   // bitmap words compacted per round (positions < 2^15: short)
 static_assert(kNbBits <= 32768, "bitmap positions are stored as short");
 
+// Multiplicative hash of a key into mask + 1 (a power of two) slots.
+__device__ __forceinline__ int hash_slot(int key, int mask) {
+    return (int)(((unsigned)key * 2654435761u) >> 13) & mask;
+}
+
 // The scratch list of dependency edges (i, j): the backup weight plane, free outside the trials.
 __device__ __forceinline__ int2* edge_list(const JointWs& W) { return reinterpret_cast<int2*>(W.sh_w); }
 __device__ __forceinline__ int edge_cap(const JBatch& B) {
@@ -1217,7 +1222,8 @@ __device__ __forceinline__ void add_edge(const JBatch& B, const JointWs& W, Join
     if (k < edge_cap(B)) edge_list(W)[k] = make_int2(i, j);
 }
 
-__global__ void __launch_bounds__(256, 4) k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
+__global__ void __launch_bounds__(256, 4)
+    k_deps(const __grid_constant__ JBatch B, JointWs W, int it) {
     JointCtl* c = W.ctl;
     if (skip_lists(c)) return;
     __shared__ int cand[kCandMax];
@@ -1226,239 +1232,348 @@ __global__ void __launch_bounds__(256, 4) k_deps(const __grid_constant__ JBatch 
     __shared__ short plist[kDepsWords * 32];   // marked bitmap positions of one round
     __shared__ int s_scan[32];
     __shared__ int s_n, s_vmin, s_vmax, s_umin, s_umax;
+    // components in batches of kDepsWarps (those this CTA's grid-stride loop would visit one
+    // after another): a warp takes each component of at most kWarpPairs (block, neighbour) pairs
+    // on its own, its distinct predecessors in a per-warp hash set; the CTA then takes the
+    // batch's larger components (and any whose set overflowed) one at a time as below
+    constexpr int kDepsWarps = 8;
+    constexpr int kWarpPairs = 256;
+    constexpr int kWarpHash = 256;
+    __shared__ int whash[kDepsWarps][kWarpHash];
+    __shared__ int s_big[kDepsWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int M = c->M_cur;
     const bool use_bits = M <= kDepsBits;
     if (use_bits)
         for (int t = threadIdx.x; t < (M + 31) / 32; t += blockDim.x) bits[t] = 0u;
-    for (int j = blockIdx.x; j < M; j += gridDim.x) {
-        if (threadIdx.x == 0) {
-            s_n = 0;
-            s_vmin = s_umin = 0x7fffffff;
-            s_vmax = s_umax = -1;
-        }
-        __syncthreads();
+    // one component by one warp; false: too many pairs or predecessors (left to the CTA)
+    auto warp_comp = [&](int j) -> bool {
         const int2 st = W.start[j], en = W.start[j + 1];
         const JImg& I = B.im[img_of_p(B, W.roots[j])];
         const int r = (I.S - 1) / 2;
         const int D = B.strict ? 2 * r : r;
         const int ND = (2 * D + 1) * (2 * D + 1);
         const int npairs = (en.y - st.y) * ND;
-#ifdef GLU_TRIAL_TRACE
-        if (it == 0 && threadIdx.x == 0 && j < kTraceMax) g_deps_t[j][0] = gtimer();
-#endif
-        // a large component's (block, neighbour) pairs name each block of its neighbourhood many
-        // times: mark them in a bitmap over the bounding box of its blocks dilated by D, then
-        // look up every marked block once
-        int nitems = npairs, BV0 = 0, BU0 = 0, BW = 1;
-        bool nbmap = false;
-        if (npairs > kNbMinPairs) {
-            // the component's blocks, staged in cand (free until the lookups) when they fit
-            const int nbq = en.y - st.y;
-            const bool staged = nbq <= kCandMax;
-            for (int t = (int)threadIdx.x; t < nbq; t += blockDim.x) {
-                const int lq = (int)((int64_t)W.qlist[st.y + t] - I.q0);
-                if (staged) cand[t] = lq;
-                const int v = lq / I.w, u = lq % I.w;
-                atomicMin(&s_vmin, v);
-                atomicMax(&s_vmax, v);
-                atomicMin(&s_umin, u);
-                atomicMax(&s_umax, u);
+        if (npairs > kWarpPairs) return false;
+        int* hs = whash[warp];
+        for (int t = lane; t < kWarpHash; t += 32) hs[t] = -1;
+        __syncwarp();
+        bool full = false;
+        auto insert = [&](int i) {
+            int h = hash_slot(i, kWarpHash - 1);
+            for (int k = 0; k < kWarpHash; ++k) {
+                const int old = atomicCAS(&hs[h], -1, i);
+                if (old == -1 || old == i) return;
+                h = (h + 1) & (kWarpHash - 1);
             }
-            __syncthreads();
-            BV0 = s_vmin - D;
-            BU0 = s_umin - D;
-            BW = s_umax - s_umin + 1 + 2 * D;
-            const int BH = s_vmax - s_vmin + 1 + 2 * D;
-            nbmap = (int64_t)BH * BW <= kNbBits;
-            if (nbmap) {
-                nitems = BH * BW;
-                for (int t = threadIdx.x; t < (nitems + 31) / 32; t += blockDim.x) nbits[t] = 0u;
-                __syncthreads();
-                if (staged) {
-                    // per (block, row of its neighbourhood): one run of 2D + 1 positions, at
-                    // most two bitmap words (D <= 8)
-                    const int NR = 2 * D + 1;
-                    for (int t = threadIdx.x; t < nbq * NR; t += blockDim.x) {
-                        const int lq = cand[t / NR];
-                        const int bv = lq / I.w + t % NR - D, qu = lq % I.w;
-                        if (bv < 0 || bv >= I.h) continue;
-                        const int row = (bv - BV0) * BW - BU0;
-                        const int b0 = row + max(qu - D, 0), b1 = row + min(qu + D, I.w - 1);
-                        const int w0 = b0 >> 5, w1 = b1 >> 5;
-                        if (w0 == w1) {
-                            atomicOr(&nbits[w0], (0xFFFFFFFFu >> (31 - (b1 & 31))) &
-                                                     (0xFFFFFFFFu << (b0 & 31)));
-                        } else {
-                            atomicOr(&nbits[w0], 0xFFFFFFFFu << (b0 & 31));
-                            for (int w = w0 + 1; w < w1; ++w) atomicOr(&nbits[w], 0xFFFFFFFFu);
-                            atomicOr(&nbits[w1], 0xFFFFFFFFu >> (31 - (b1 & 31)));
-                        }
-                    }
-                } else {
-                    for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
-                        const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
-                        const int nb = t % ND;
-                        const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
-                        const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
-                        if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
-                        const int idx = (bv - BV0) * BW + (bu - BU0);
-                        atomicOr(&nbits[idx >> 5], 1u << (idx & 31));
+            full = true;
+        };
+        for (int t = lane; t < npairs; t += 32) {
+            const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+            const int nb = t % ND;
+            const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+            const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+            if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
+            const int64_t bb = I.q0 + (int64_t)bv * I.w + bu;
+            if (W.ovf[bb]) {
+                // more components than owner slots: the block's pixel labels
+                const int ys = bv * I.s, xs = bu * I.s;
+                const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
+                int last = -1;
+                for (int e = 0; e < ey * ex; ++e) {
+                    const int i = W.lab[I.p0 + (int64_t)(ys + e / ex) * I.W + xs + e % ex];
+                    if (i >= 0 && i < j && i != last) {
+                        insert(i);
+                        last = i;
                     }
                 }
-                __syncthreads();
+            } else {
+                const int4* op = reinterpret_cast<const int4*>(W.own + bb * kOwnSlots);
+                const int4 o0 = op[0], o1 = op[1];
+                const int sl[kOwnSlots] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+                for (int e = 0; e < kOwnSlots; ++e) {
+                    if (sl[e] < 0) break;   // slots fill in order
+                    if (sl[e] < j) insert(sl[e]);
+                }
             }
         }
-        // one candidate predecessor i < j: with the bitmap, the first sighting records it (its
-        // edge is appended with the component's others, one slot reservation for all of them;
-        // past kCandMax records, at once)
-        auto offer = [&](int i) {
-            if (use_bits) {
-                const unsigned bit = 1u << (i & 31);
-                if (atomicOr(&bits[i >> 5], bit) & bit) return;
-                const int slot = atomicAdd(&s_n, 1);
-                if (slot < kCandMax) cand[slot] = i;
-                else add_edge(B, W, c, i, j);
-            } else {
-                const int slot = atomicAdd(&s_n, 1);
-                if (slot < kCandMax) cand[slot] = i;
+        if (__any_sync(0xffffffffu, full)) return false;
+        __syncwarp();
+        // the occupied slots (kWarpHash / 32 per lane) are the distinct predecessors: their edges
+        // with one slot reservation for the warp
+        constexpr int kPerLane = kWarpHash / 32;
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kPerLane; ++k) cnt += hs[lane * kPerLane + k] >= 0 ? 1 : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int n = __shfl_sync(0xffffffffu, incl, 31);
+        int e0 = 0;
+        if (lane == 0 && n) e0 = atomicAdd(&c->nedge, n);
+        e0 = __shfl_sync(0xffffffffu, e0, 0);
+        const int ecap = edge_cap(B);
+        int pos = e0 + incl - cnt;
+#pragma unroll
+        for (int k = 0; k < kPerLane; ++k) {
+            const int i = hs[lane * kPerLane + k];
+            if (i < 0) continue;
+            atomicAdd(&W.dag_cnt[i].x, 1);
+            if (pos < ecap) edge_list(W)[pos] = make_int2(i, j);
+            ++pos;
+        }
+        if (lane == 0) W.pend[j] = n;
+        return true;
+    };
+    for (int jb = blockIdx.x; jb < M; jb += gridDim.x * kDepsWarps) {
+        {
+            const int jw = jb + warp * gridDim.x;
+            const bool done = jw < M && warp_comp(jw);
+            if (lane == 0) s_big[warp] = jw < M && !done ? jw : -1;
+        }
+        __syncthreads();
+        for (int kb = 0; kb < kDepsWarps; ++kb) {
+            const int j = s_big[kb];
+            if (j < 0) continue;
+            if (threadIdx.x == 0) {
+                s_n = 0;
+                s_vmin = s_umin = 0x7fffffff;
+                s_vmax = s_umax = -1;
             }
-        };
-        // kDepsBatch items (pairs, or marked bitmap positions) per thread and round, their loads
-        // issued together (a block's overflow flag and its owner slots as two 16-byte loads): the
-        // largest components span hundreds of LR blocks, and their CTA sets the kernel's duration
-        constexpr int kDepsBatch = 4;
-        static_assert(kOwnSlots == 8, "owner slots are read as two int4");
-        auto run_items = [&](const short* plist, int n_items) {
-            for (int t0 = threadIdx.x * kDepsBatch; t0 < n_items; t0 += blockDim.x * kDepsBatch) {
-                int64_t bb[kDepsBatch];
-                int bvv[kDepsBatch], buu[kDepsBatch];
-#pragma unroll
-                for (int k = 0; k < kDepsBatch; ++k) {
-                    bb[k] = -1;
-                    const int t = t0 + k;
-                    if (t >= n_items) continue;
-                    if (plist) {
-                        const int pos = plist[t];
-                        bvv[k] = BV0 + pos / BW;
-                        buu[k] = BU0 + pos % BW;
-                    } else {
-                        const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
-                        const int nb = t % ND;
-                        bvv[k] = (int)(lq / I.w) + nb / (2 * D + 1) - D;
-                        buu[k] = (int)(lq % I.w) + nb % (2 * D + 1) - D;
-                        if (bvv[k] < 0 || bvv[k] >= I.h || buu[k] < 0 || buu[k] >= I.w) continue;
-                    }
-                    bb[k] = I.q0 + (int64_t)bvv[k] * I.w + buu[k];
+            __syncthreads();
+            const int2 st = W.start[j], en = W.start[j + 1];
+            const JImg& I = B.im[img_of_p(B, W.roots[j])];
+            const int r = (I.S - 1) / 2;
+            const int D = B.strict ? 2 * r : r;
+            const int ND = (2 * D + 1) * (2 * D + 1);
+            const int npairs = (en.y - st.y) * ND;
+#ifdef GLU_TRIAL_TRACE
+            if (it == 0 && threadIdx.x == 0 && j < kTraceMax) g_deps_t[j][0] = gtimer();
+#endif
+            // a large component's (block, neighbour) pairs name each block of its neighbourhood
+            // many times: mark them in a bitmap over the bounding box of its blocks dilated by D,
+            // then look up every marked block once
+            int nitems = npairs, BV0 = 0, BU0 = 0, BW = 1;
+            bool nbmap = false;
+            if (npairs > kNbMinPairs) {
+                // the component's blocks, staged in cand (free until the lookups) when they fit
+                const int nbq = en.y - st.y;
+                const bool staged = nbq <= kCandMax;
+                for (int t = (int)threadIdx.x; t < nbq; t += blockDim.x) {
+                    const int lq = (int)((int64_t)W.qlist[st.y + t] - I.q0);
+                    if (staged) cand[t] = lq;
+                    const int v = lq / I.w, u = lq % I.w;
+                    atomicMin(&s_vmin, v);
+                    atomicMax(&s_vmax, v);
+                    atomicMin(&s_umin, u);
+                    atomicMax(&s_umax, u);
                 }
-                uint8_t ov[kDepsBatch];
-                int4 o0[kDepsBatch], o1[kDepsBatch];
-#pragma unroll
-                for (int k = 0; k < kDepsBatch; ++k) {
-                    ov[k] = 0;
-                    o0[k] = o1[k] = make_int4(-1, -1, -1, -1);
-                    if (bb[k] < 0) continue;
-                    ov[k] = W.ovf[bb[k]];
-                    const int4* op = reinterpret_cast<const int4*>(W.own + bb[k] * kOwnSlots);
-                    o0[k] = op[0];
-                    o1[k] = op[1];
-                }
-#pragma unroll
-                for (int k = 0; k < kDepsBatch; ++k) {
-                    if (bb[k] < 0) continue;
-                    if (ov[k]) {
-                        // more components than owner slots: read the block's pixel labels
-                        const int ys = bvv[k] * I.s, xs = buu[k] * I.s;
-                        const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
-                        int last = -1;
-                        for (int e = 0; e < ey * ex; ++e) {
-                            const int i = W.lab[I.p0 + (int64_t)(ys + e / ex) * I.W + xs + e % ex];
-                            if (i >= 0 && i < j && i != last) {
-                                offer(i);
-                                last = i;
+                __syncthreads();
+                BV0 = s_vmin - D;
+                BU0 = s_umin - D;
+                BW = s_umax - s_umin + 1 + 2 * D;
+                const int BH = s_vmax - s_vmin + 1 + 2 * D;
+                nbmap = (int64_t)BH * BW <= kNbBits;
+                if (nbmap) {
+                    nitems = BH * BW;
+                    for (int t = threadIdx.x; t < (nitems + 31) / 32; t += blockDim.x)
+                        nbits[t] = 0u;
+                    __syncthreads();
+                    if (staged) {
+                        // per (block, row of its neighbourhood): one run of 2D + 1 positions, at
+                        // most two bitmap words (D <= 8)
+                        const int NR = 2 * D + 1;
+                        for (int t = threadIdx.x; t < nbq * NR; t += blockDim.x) {
+                            const int lq = cand[t / NR];
+                            const int bv = lq / I.w + t % NR - D, qu = lq % I.w;
+                            if (bv < 0 || bv >= I.h) continue;
+                            const int row = (bv - BV0) * BW - BU0;
+                            const int b0 = row + max(qu - D, 0), b1 = row + min(qu + D, I.w - 1);
+                            const int w0 = b0 >> 5, w1 = b1 >> 5;
+                            if (w0 == w1) {
+                                atomicOr(&nbits[w0], (0xFFFFFFFFu >> (31 - (b1 & 31))) &
+                                                         (0xFFFFFFFFu << (b0 & 31)));
+                            } else {
+                                atomicOr(&nbits[w0], 0xFFFFFFFFu << (b0 & 31));
+                                for (int w = w0 + 1; w < w1; ++w) atomicOr(&nbits[w], 0xFFFFFFFFu);
+                                atomicOr(&nbits[w1], 0xFFFFFFFFu >> (31 - (b1 & 31)));
                             }
                         }
                     } else {
-                        // slots fill in order: the first -1 ends the list
-                        const int sl[kOwnSlots] = {o0[k].x, o0[k].y, o0[k].z, o0[k].w,
-                                                   o1[k].x, o1[k].y, o1[k].z, o1[k].w};
+                        for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+                            const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+                            const int nb = t % ND;
+                            const int bv = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+                            const int bu = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+                            if (bv < 0 || bv >= I.h || bu < 0 || bu >= I.w) continue;
+                            const int idx = (bv - BV0) * BW + (bu - BU0);
+                            atomicOr(&nbits[idx >> 5], 1u << (idx & 31));
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // one candidate predecessor i < j: with the bitmap, the first sighting records it (its
+            // edge is appended with the component's others, one slot reservation for all of them;
+            // past kCandMax records, at once)
+            auto offer = [&](int i) {
+                if (use_bits) {
+                    const unsigned bit = 1u << (i & 31);
+                    if (atomicOr(&bits[i >> 5], bit) & bit) return;
+                    const int slot = atomicAdd(&s_n, 1);
+                    if (slot < kCandMax) cand[slot] = i;
+                    else add_edge(B, W, c, i, j);
+                } else {
+                    const int slot = atomicAdd(&s_n, 1);
+                    if (slot < kCandMax) cand[slot] = i;
+                }
+            };
+            // kDepsBatch items (pairs, or marked bitmap positions) per thread and round, their
+            // loads issued together (a block's overflow flag and its owner slots as two 16-byte
+            // loads): the largest components span hundreds of LR blocks, and their CTA sets the
+            // kernel's duration
+            constexpr int kDepsBatch = 4;
+            static_assert(kOwnSlots == 8, "owner slots are read as two int4");
+            auto run_items = [&](const short* plist, int n_items) {
+                for (int t0 = threadIdx.x * kDepsBatch; t0 < n_items;
+                     t0 += blockDim.x * kDepsBatch) {
+                    int64_t bb[kDepsBatch];
+                    int bvv[kDepsBatch], buu[kDepsBatch];
 #pragma unroll
-                        for (int e = 0; e < kOwnSlots; ++e) {
-                            if (sl[e] < 0) break;
-                            if (sl[e] < j) offer(sl[e]);
+                    for (int k = 0; k < kDepsBatch; ++k) {
+                        bb[k] = -1;
+                        const int t = t0 + k;
+                        if (t >= n_items) continue;
+                        if (plist) {
+                            const int pos = plist[t];
+                            bvv[k] = BV0 + pos / BW;
+                            buu[k] = BU0 + pos % BW;
+                        } else {
+                            const int64_t lq = (int64_t)W.qlist[st.y + t / ND] - I.q0;
+                            const int nb = t % ND;
+                            bvv[k] = (int)(lq / I.w) + nb / (2 * D + 1) - D;
+                            buu[k] = (int)(lq % I.w) + nb % (2 * D + 1) - D;
+                            if (bvv[k] < 0 || bvv[k] >= I.h || buu[k] < 0 || buu[k] >= I.w)
+                                continue;
+                        }
+                        bb[k] = I.q0 + (int64_t)bvv[k] * I.w + buu[k];
+                    }
+                    uint8_t ov[kDepsBatch];
+                    int4 o0[kDepsBatch], o1[kDepsBatch];
+#pragma unroll
+                    for (int k = 0; k < kDepsBatch; ++k) {
+                        ov[k] = 0;
+                        o0[k] = o1[k] = make_int4(-1, -1, -1, -1);
+                        if (bb[k] < 0) continue;
+                        ov[k] = W.ovf[bb[k]];
+                        const int4* op = reinterpret_cast<const int4*>(W.own + bb[k] * kOwnSlots);
+                        o0[k] = op[0];
+                        o1[k] = op[1];
+                    }
+#pragma unroll
+                    for (int k = 0; k < kDepsBatch; ++k) {
+                        if (bb[k] < 0) continue;
+                        if (ov[k]) {
+                            // more components than owner slots: read the block's pixel labels
+                            const int ys = bvv[k] * I.s, xs = buu[k] * I.s;
+                            const int ey = min(I.s, I.H - ys), ex = min(I.s, I.W - xs);
+                            int last = -1;
+                            for (int e = 0; e < ey * ex; ++e) {
+                                const int i =
+                                    W.lab[I.p0 + (int64_t)(ys + e / ex) * I.W + xs + e % ex];
+                                if (i >= 0 && i < j && i != last) {
+                                    offer(i);
+                                    last = i;
+                                }
+                            }
+                        } else {
+                            // slots fill in order: the first -1 ends the list
+                            const int sl[kOwnSlots] = {o0[k].x, o0[k].y, o0[k].z, o0[k].w,
+                                                       o1[k].x, o1[k].y, o1[k].z, o1[k].w};
+#pragma unroll
+                            for (int e = 0; e < kOwnSlots; ++e) {
+                                if (sl[e] < 0) break;
+                                if (sl[e] < j) offer(sl[e]);
+                            }
                         }
                     }
                 }
-            }
-        };
-        if (nbmap) {
-            // the marked positions only (the bounding box of a long component is mostly empty):
-            // each round compacts kDepsWords bitmap words into a list, then looks it up
-            const int nwords = (nitems + 31) / 32;
-            for (int w0 = 0; w0 < nwords; w0 += kDepsWords) {
-                const int w = w0 + (int)threadIdx.x;
-                const unsigned word = (threadIdx.x < kDepsWords && w < nwords) ? nbits[w] : 0u;
-                int ex;
-                const int tot = block_excl_scan_any(__popc(word), &ex, s_scan);
-                for (unsigned m = word; m; m &= m - 1) plist[ex++] = (short)(w * 32 + __ffs(m) - 1);
-                __syncthreads();
-                run_items(plist, tot);
-                __syncthreads();
-            }
-        } else {
-            run_items(nullptr, nitems);
-        }
-        __syncthreads();
-        const int n = s_n;
-        int npred;
-        if (use_bits) {
-            npred = n;
-            const int nrec = min(n, kCandMax);
-            if (threadIdx.x == 0) s_vmin = nrec ? atomicAdd(&c->nedge, nrec) : 0;
-            __syncthreads();
-            const int e0 = s_vmin, ecap = edge_cap(B);
-            for (int t = threadIdx.x; t < nrec; t += blockDim.x) {
-                const int i = cand[t];
-                atomicAdd(&W.dag_cnt[i].x, 1);
-                if (e0 + t < ecap) edge_list(W)[e0 + t] = make_int2(i, j);
-            }
-            // clear the bits this component set (every set bit is one of its predecessors)
-            if (n <= kCandMax) {
-                for (int t = threadIdx.x; t < n; t += blockDim.x) bits[cand[t] >> 5] = 0u;
+            };
+            if (nbmap) {
+                // the marked positions only (the bounding box of a long component is mostly empty):
+                // each round compacts kDepsWords bitmap words into a list, then looks it up
+                const int nwords = (nitems + 31) / 32;
+                for (int w0 = 0; w0 < nwords; w0 += kDepsWords) {
+                    const int w = w0 + (int)threadIdx.x;
+                    const unsigned word = (threadIdx.x < kDepsWords && w < nwords) ? nbits[w] : 0u;
+                    int ex;
+                    const int tot = block_excl_scan_any(__popc(word), &ex, s_scan);
+                    for (unsigned m = word; m; m &= m - 1) plist[ex++] = (short)(w * 32 + __ffs(m) - 1);
+                    __syncthreads();
+                    run_items(plist, tot);
+                    __syncthreads();
+                }
             } else {
-                for (int t = threadIdx.x; t < (M + 31) / 32; t += blockDim.x) bits[t] = 0u;
+                run_items(nullptr, nitems);
             }
-        } else {
-            if (n > kCandMax) {
-                if (threadIdx.x == 0) atomicExch(&c->dag_bad[it], 1);
+            __syncthreads();
+            const int n = s_n;
+            int npred;
+            if (use_bits) {
+                npred = n;
+                const int nrec = min(n, kCandMax);
+                if (threadIdx.x == 0) s_vmin = nrec ? atomicAdd(&c->nedge, nrec) : 0;
                 __syncthreads();
-                continue;
+                const int e0 = s_vmin, ecap = edge_cap(B);
+                for (int t = threadIdx.x; t < nrec; t += blockDim.x) {
+                    const int i = cand[t];
+                    atomicAdd(&W.dag_cnt[i].x, 1);
+                    if (e0 + t < ecap) edge_list(W)[e0 + t] = make_int2(i, j);
+                }
+                // clear the bits this component set (every set bit is one of its predecessors)
+                if (n <= kCandMax) {
+                    for (int t = threadIdx.x; t < n; t += blockDim.x) bits[cand[t] >> 5] = 0u;
+                } else {
+                    for (int t = threadIdx.x; t < (M + 31) / 32; t += blockDim.x) bits[t] = 0u;
+                }
+            } else {
+                if (n > kCandMax) {
+                    if (threadIdx.x == 0) atomicExch(&c->dag_bad[it], 1);
+                    __syncthreads();
+                    continue;
+                }
+                int n2 = 1;
+                while (n2 < n) n2 <<= 1;
+                for (int t = n + threadIdx.x; t < n2; t += blockDim.x) cand[t] = 0x7fffffff;
+                __syncthreads();
+                if (n > 1) bitonic_sort_smem(cand, n2);
+                if (threadIdx.x == 0) s_n = 0;
+                __syncthreads();
+                for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                    const int i = cand[t];
+                    if (t > 0 && cand[t - 1] == i) continue;   // distinct predecessors only
+                    atomicAdd(&s_n, 1);
+                    add_edge(B, W, c, i, j);
+                }
+                __syncthreads();
+                npred = s_n;
             }
-            int n2 = 1;
-            while (n2 < n) n2 <<= 1;
-            for (int t = n + threadIdx.x; t < n2; t += blockDim.x) cand[t] = 0x7fffffff;
-            __syncthreads();
-            if (n > 1) bitonic_sort_smem(cand, n2);
-            if (threadIdx.x == 0) s_n = 0;
-            __syncthreads();
-            for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                const int i = cand[t];
-                if (t > 0 && cand[t - 1] == i) continue;   // distinct predecessors only
-                atomicAdd(&s_n, 1);
-                add_edge(B, W, c, i, j);
-            }
-            __syncthreads();
-            npred = s_n;
-        }
-        if (threadIdx.x == 0) W.pend[j] = npred;
+            if (threadIdx.x == 0) W.pend[j] = npred;
 #ifdef GLU_TRIAL_TRACE
-        if (it == 0 && threadIdx.x == 0 && j < kTraceMax) {
-            g_deps_t[j][1] = gtimer();
-            g_deps_t[j][2] = (unsigned long long)nitems;
-            g_deps_t[j][3] = (unsigned long long)(nbmap ? 1 : 0) | ((unsigned long long)npairs << 8);
-            g_deps_t[j][4] = (unsigned long long)blockIdx.x;
-        }
+            if (it == 0 && threadIdx.x == 0 && j < kTraceMax) {
+                g_deps_t[j][1] = gtimer();
+                g_deps_t[j][2] = (unsigned long long)nitems;
+                g_deps_t[j][3] = (unsigned long long)(nbmap ? 1 : 0) | ((unsigned long long)npairs << 8);
+                g_deps_t[j][4] = (unsigned long long)blockIdx.x;
+            }
 #endif
-        __syncthreads();
+            __syncthreads();
+        }
+        __syncthreads();   // s_big and the warps' sets are rewritten by the next batch
     }
 }
 
@@ -1535,10 +1650,6 @@ __device__ __forceinline__ int img_of_q(const JBatch& B, int64_t q) {
     int i = 0;
     while (i + 1 < B.n && B.im[i + 1].q0 <= q) ++i;
     return i;
-}
-
-__device__ __forceinline__ int hash_slot(int key, int mask) {
-    return (int)(((unsigned)key * 2654435761u) >> 13) & mask;
 }
 
 // Chunked exclusive scan of n values in place (each thread a contiguous chunk); returns the total.

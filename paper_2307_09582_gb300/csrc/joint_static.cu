@@ -6,7 +6,7 @@
 // stall it. For them the joint optimisation's workspace is a fixed array in the library's own
 // device memory, GLU_JOINT_STATIC_BYTES (64 MiB) large. That holds the workspace of images up to
 // about 0.88 megapixels at scale 8 with a 5x5 window and 5 iterations: the largest 16:9 image
-// that fits is 1248 x 702 (63.4 MiB); 1024 x 768 fits (57.5 MiB); 1280 x 720 needs 66.3 MiB and
+// that fits is 1248 x 702 (63.5 MiB); 1024 x 768 fits (57.6 MiB); 1280 x 720 needs 66.4 MiB and
 // is refused. Every GPU that loads the library keeps this array until the process exits.
 //
 // The array is shared by all calls on a device and keeps the previous call's contents; the

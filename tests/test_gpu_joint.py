@@ -204,3 +204,27 @@ def test_joint_4k_workload_full_parity(api):
     # image bit-identical, every decision equal (or replayed within its tolerance), Theta / E as
     # for Algorithm 1
     assert rep["mode"] == "exact", rep
+
+
+@pytest.mark.parametrize("conn", [8, 4])
+def test_joint_dense_large_error_regions(api, conn):
+    """Dense large-error regions (uniform noise patches on a smooth gradient): full 32 x 32 tiles,
+    rows of many runs, and components that cross tile borders in both directions, for the tiled
+    component stage and its border merge. More than 4096 large-error pixels, so the first
+    iteration takes the multi-kernel path; its |E| and component count equal the oracle's, and
+    the whole run is compared element-wise."""
+    H, W = 120, 200
+    rng = np.random.Generator(np.random.PCG64(11 + conn))
+    yy, xx = np.mgrid[0:H, 0:W]
+    img = np.stack([xx * 255 // (W - 1), yy * 255 // (H - 1), (xx + yy) * 255 // (H + W - 2)],
+                   axis=-1).astype(np.uint8)
+    for y0, x0, h, w in [(3, 5, 40, 50), (30, 70, 64, 33), (90, 20, 25, 150), (0, 150, 120, 9),
+                         (60, 110, 7, 70)]:
+        img[y0:y0 + h, x0:x0 + w] = rng.integers(0, 256, (h, w, 3), dtype=np.uint8)
+    hr, lr, theta, err, st, ref = run_both(api, img, 4, 3, N=2, strict=True, conn=conn)
+    ri = [it for it in ref["iters"] if it["n_large"] > 0]
+    assert st["iters"][0]["n_large"] > 4096
+    assert (st["iters"][0]["n_large"], st["iters"][0]["M"]) == (ri[0]["n_large"], ri[0]["M"])
+    rep = compare(api, img, 4, 3, 2, True, lr, theta, err, st, ref)
+    print(f"\njoint dense conn={conn}: {st['iters']} {rep}")
+    assert rep["mode"] == "exact", rep
